@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Throughput of the batched checkerboard Metropolis sweep on GB300.
+
+Workload (synthetic, seeded): 512 Ising lattices with side L = 2^e, e uniform
+in {5..11}, beta ~ U(0.3, 0.55), h ~ N(0, 0.05), J = 1, int8 spins, random
+start; one step = one sweep (both checkerboard colours) of every lattice,
+about 4.1e8 site updates.  The default run is the whole 2000-sweep job.  The
+state (~409 MB, plus its ping-pong partner) is larger than the 129 MB L2, so
+no flush is needed between steps.
+
+One JSON line on stdout (rank 0):
+  value        site-updates/s of the batched, graph-replayed launch form
+  plain        the same workload in the plain per-lattice launch form
+  roofline     the batched sweep kernel: algorithmic 2 B per site update
+               (one int8 read, one write) / its CUDA-event launch time
+  cpu_baseline the CPU oracle on this host's cores, a bounded sample
+  e2e          end to end through the C ABI with host buffers: every step
+               uploads the spins from pinned host memory, sweeps, and reads
+               back the spins and that step's statistics
+--impl reference times the CPU oracle alone (the reference arm).
+Multi-GPU (torchrun): every rank runs its own 512-lattice batch (weak
+scaling, no data-path collective); time = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site-updates/s and % HBM roofline, batched vs plain launch on 1 GB300 (bit-exact)"
+UNIT = "site-updates/s"
+WORKLOAD = ("uneven512: 512 Ising lattices, L=2^e with e uniform in {5..11}, beta~U(0.3,0.55), "
+            "h~N(0,0.05), J=1, int8 spins, checkerboard Metropolis, one step = one sweep of all lattices")
+SEED = 0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=6)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--cpu-sweeps", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- CPU oracle
+def _oracle_lattice(args):
+    import numpy as np
+
+    import oracle
+    i, d, seed, sweeps = args
+    s = oracle.init_ising(d["L"], seed, i).copy()
+    t0 = time.perf_counter()
+    oracle.ising_run(s, d["beta"], d["J"], d["h"], seed, i, 0, sweeps, record=False)
+    return d["L"] * d["L"] * sweeps, time.perf_counter() - t0
+
+
+def cpu_oracle_rate(lats, sweeps, cores):
+    """The oracle as it stands, one lattice per task on `cores` processes."""
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    ctx = mp.get_context("spawn")
+    tasks = [(i, d, SEED, sweeps) for i, d in enumerate(lats)]
+    tasks.sort(key=lambda a: -a[1]["L"])
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_lattice, tasks, chunksize=1)
+    wall = time.perf_counter() - t0
+    updates = sum(r[0] for r in res)
+    return updates / wall, updates, wall
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0, period_ms=100):
+        self.lines = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 f"-lms", str(period_ms)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self):
+        return time.perf_counter()
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = [l for (t, l) in self.lines if t0 <= t <= t1] or [l for (_, l) in self.lines[-3:]]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            p = [x.strip() for x in r.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2304_01772_gb300", "csrc", "sweep_ising.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the batched Ising kernel from the committed ncu
+    summary, or None if absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "ising_fused_uneven512.txt")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_full_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def dist_setup(n):
+    if n <= 1 and "RANK" not in os.environ:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", n))
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", rank=rank, world_size=world)
+    return rank, world, dist
+
+
+def max_over_ranks(x, dist):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    import torch
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+# ----------------------------------------------------------------- arms
+def run_reference(args):
+    from paper_2304_01772_gb300 import workloads as wl
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return 0
+    lats = wl.uneven512()
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup and 0):
+        pass
+    rate, updates, wall = cpu_oracle_rate(lats, max(1, args.cpu_sweeps), cores)
+    sample = f"all 512 lattices of the workload, {max(1, args.cpu_sweeps)} sweep(s) each from the random start"
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": max(1, args.cpu_sweeps), "warmup": 0, "ms_per_step": wall * 1e3 / max(1, args.cpu_sweeps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+            "data": "synthetic", "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    from paper_2304_01772_gb300 import workloads as wl
+
+    lats = wl.uneven512()
+    sites = wl.site_count(lats)
+    cpu = None
+    rank0_single = args.gpus == 1 and int(os.environ.get("RANK", 0)) == 0
+    if rank0_single and not args.no_cpu:
+        # before the first GPU call: a process pool forked after it could hang
+        cores = os.cpu_count() or 1
+        rate, updates, wall = cpu_oracle_rate(lats, max(1, args.cpu_sweeps), cores)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"all 512 lattices, {max(1, args.cpu_sweeps)} sweep(s) each ({updates:.3e} updates, "
+                         f"{wall:.1f} s wall)"}
+
+    import torch
+    import paper_2304_01772_gb300 as sm
+    rank, world, dist = dist_setup(args.gpus)
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    stream = torch.cuda.current_stream()
+    sim = sm.Sim(sm.SPIN_ISING, lats, seed=SEED + rank, max_record=max(16, args.e2e_steps))
+    sim.set_launch(0, True, 0, 256)
+    sim.sweep(args.warmup)
+
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
+    time.sleep(0.3)
+    # ---- timed region: batched, graph-replayed
+    barrier(dist)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.perf_counter()
+    e0.record(stream)
+    sim.sweep(args.steps)
+    e1.record(stream)
+    barrier(dist)
+    t_wall1 = time.perf_counter()
+    launches = sim.gpu_launches
+    ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    clk = clocks.summary(t_wall0, t_wall1)
+
+    # ---- plain per-lattice launches on the same state, same results
+    sim.set_launch(1, True, 0, 256)
+    sim.sweep(2)
+    barrier(dist)
+    e0.record(stream)
+    sim.sweep(args.plain_steps)
+    e1.record(stream)
+    barrier(dist)
+    ms_plain = max_over_ranks(e0.elapsed_time(e1), dist)
+    sim.set_launch(0, True, 0, 256)
+
+    # ---- kernel time of the batched sweep kernel (CUDA events in the library)
+    nk = min(args.steps, 200)
+    sim.profile(True, nk)
+    sim.sweep(nk)
+    kms, kn = sim.profile_read()
+    sim.profile(False)
+    clocks.stop()
+
+    # ---- end to end through the C ABI with host buffers
+    span = sim.spins.numel()
+    host_in = torch.empty(span, dtype=torch.int8, pin_memory=True)
+    host_out = torch.empty(span, dtype=torch.int8, pin_memory=True)
+    host_in.copy_(sim.spins.cpu())
+    st_host = np.empty((1, len(lats), sim.width), dtype=np.int64)
+    E_host = np.empty((1, len(lats)), dtype=np.float32)
+    M_host = np.empty((1, len(lats)), dtype=np.float32)
+    import ctypes
+    L = sm.lib()
+    sptr = sm._stream(stream)
+
+    def e2e_step():
+        sm._check(L.spin_load_spins(sim.ctx, host_in.data_ptr(), sptr), sim.ctx, "load")
+        sm._check(L.spin_sweep(sim.ctx, 1, 1, sptr), sim.ctx, "sweep")
+        sm._check(L.spin_store_spins(sim.ctx, host_out.data_ptr(), sptr), sim.ctx, "store")
+        sm._check(L.spin_observables(sim.ctx, ctypes.c_int64(sim.n_records - 1), 1, st_host.ctypes.data,
+                                     E_host.ctypes.data, M_host.ctypes.data, sptr), sim.ctx, "obs")
+
+    e2e_step()
+    barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    barrier(dist)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+
+    if rank != 0:
+        return 0
+    value = world * sites * args.steps / (ms * 1e-3)
+    plain = world * sites * args.plain_steps / (ms_plain * 1e-3)
+    peak, peak_kind = measured_peaks()
+    alg_bytes = 2.0 * sites
+    achieved = alg_bytes / (kms / kn * 1e-3) / 1e9 if kn else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattices": len(lats), "sites_per_sweep": sites,
+                   "launch": "batched work-list kernel, one launch per sweep, CUDA graph replay",
+                   "l2": "inputs larger than L2 (state 409 MB + ping-pong buffer), no flush",
+                   "bit_exact": "spins identical to the CPU oracle and across launch forms (tests/)"},
+        "plain": {"value": plain, "unit": UNIT, "steps": args.plain_steps,
+                  "ms_per_step": ms_plain / args.plain_steps, "speedup_batched_vs_plain": value / plain},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": ncu_traffic(),
+                     "kernel": "ising_fused_kernel", "algorithmic_bytes_per_launch": alg_bytes,
+                     "launch_ms": kms / kn if kn else None, "timed_launches": kn,
+                     "peak_source": f"{peak_kind} hbm_gbs (copy)"},
+        "e2e": {"value": sites * args.e2e_steps * world / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": span, "d2h_bytes_per_step": span + st_host.nbytes + E_host.nbytes + M_host.nbytes},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

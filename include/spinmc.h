@@ -1,0 +1,230 @@
+/*
+ * spinmc.h -- C ABI of libspinmc.so: batched checkerboard Metropolis sweeps of
+ * 2D spin lattices (Ising, q-state Potts, cellular Potts) on one GB300 GPU,
+ * their observables, the fluctuation-estimator gradient and a small BF16 MLP
+ * surrogate.
+ *
+ * Method: "A differentiable programming framework for spin models" (Farias,
+ * Schultz, Mombach, Maziero, arXiv 2304.01772).  Alg. 1 (Metropolis-Hastings
+ * with the checkerboard decomposition), the Ising Hamiltonian (Sec. "Ising
+ * model"), the Potts Hamiltonian and proposal (Sec. "Potts model"), the
+ * cellular Potts Hamiltonian Eq. "h" and copy attempt (Sec. "Cellular Potts
+ * model"), and the parameters of Sec. "Results".
+ *
+ * Conventions (the paper prints H = sum J s s + sum B s with J < 0
+ * ferromagnetic; this library uses the equivalent standard signs):
+ *   Ising  H = -J sum_<ij> s_i s_j - h sum_i s_i,   s = +-1 stored as int8.
+ *   Potts  H = -J sum_<ij> delta(s_i, s_j),          s in [0, q) as uint8.
+ *   CPM    H = sum_<xy Moore> J[tau(x)][tau(y)] (1 - delta) + lambda sum (a - A)^2,
+ *          cell ids int32 (0 = medium, no area term), each unordered pair once.
+ * Bonds are counted once.  Lattices are L x L, row-major, periodic, L even.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = (seed low 32
+ * bits, seed high 32 bits), counter = (g, lattice index, sweep index, colour),
+ * where for a site (x, y) of colour c
+ *   Ising: k = (y L + x) >> 1, g = k >> 2, draw = lane k & 3;
+ *   Potts: k = (y L + x) >> 1, g = k >> 1, acceptance lane 2(k&1), choice lane 2(k&1)+1,
+ *          proposal s' = (s + 1 + floor(u1 (q - 1) / 2^32)) mod q;
+ *   CPM:   colour c = (x & 1) | ((y & 1) << 1), k = (y >> 1)(L/2) + (x >> 1),
+ *          g = k >> 1, lanes as Potts, neighbour = u1 >> 29 in the order
+ *          (-1,-1),(0,-1),(1,-1),(-1,0),(1,0),(-1,1),(0,1),(1,1).
+ * Ising/Potts sweep = colour (x + y) & 1 == 0 then 1; CPM step = colours 0..3.
+ * Acceptance (Alg. 1): dE <= 0 always, else u < max(floor(exp(-beta dE) 2^32), 1),
+ * with dE in double: Ising 2.0*s*((double)J*n + (double)h), Potts
+ * (double)J*(n_same_old - n_same_new), CPM integer dE with exp(-dE / (double)T).
+ * Because every draw is a function of (seed, lattice, sweep, colour, site)
+ * only, results do not depend on tiling, batching, launch form or resume.
+ *
+ * Ownership: spin buffers are device memory owned by the caller and borrowed
+ * by the context until spin_destroy; the context owns everything else it
+ * allocates (tables, a second spin buffer, statistics, work lists).  Streams
+ * are the caller's (void* = cudaStream_t, NULL = legacy default stream).
+ * Calls are asynchronous on the stream unless a host pointer is passed.
+ *
+ * Errors: every int-returning call returns SPIN_OK (0) or a negative code;
+ * spin_last_error(ctx) gives a message.  No exception crosses the ABI.
+ */
+#ifndef SPINMC_H
+#define SPINMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPIN_OK 0
+#define SPIN_EINVAL (-1)   /* bad argument: odd L, q out of [2,255], non-finite beta, ... */
+#define SPIN_ENOMEM (-2)   /* device or host allocation failed */
+#define SPIN_ECUDA (-3)    /* a CUDA runtime call failed */
+#define SPIN_ETIMEOUT (-4) /* a bounded device-side wait gave up */
+#define SPIN_ESTATE (-5)   /* call not valid in the context's current state */
+
+enum { SPIN_ISING = 0, SPIN_POTTS = 1, SPIN_CPM = 2 };
+
+/* One lattice of a batch (host array, copied by spin_init / spin_set_params).
+ * Sec. "Methods": the paper batches lattices in the B axis of a [B,C,H,W]
+ * tensor; here each lattice has its own size, temperature and couplings.   */
+typedef struct {
+    int32_t L;            /* side, even, >= 4 (a multiple of 16 takes the vectorised kernels) */
+    int32_t q;            /* Potts states in [2, 255]; ignored for Ising and CPM              */
+    float beta;           /* inverse temperature 1/T (finite, >= 0); ignored for CPM          */
+    float J;              /* coupling (Ising, Potts)                                          */
+    float h;              /* field (Ising); must be 0 for Potts                                */
+    int32_t reserved;     /* must be 0                                                         */
+    uint64_t spin_offset; /* element offset of this lattice in the caller's spin buffer       */
+} spin_lattice_desc;
+
+/* Cellular Potts parameters (Eq. "h", Sec. "Results": types medium/light/dark,
+ * symmetric adhesion table, target area, lambda, temperature k_B T).      */
+typedef struct {
+    int32_t n_types;          /* including the medium type 0; <= 8                      */
+    int32_t lambda;           /* area stiffness (integer energy units)                   */
+    int32_t target_area;      /* A, the same for every cell                              */
+    int32_t n_cells;          /* cell ids 1..n_cells; id 0 is the medium                 */
+    const int32_t *J_type;    /* host, n_types x n_types, symmetric, integer             */
+    const uint8_t *cell_type; /* host, [n_cells + 1] types (cell_type[0] = 0), or NULL
+                                 to draw 1 + (u >> 31) per cell at spin_init             */
+    float T;                  /* temperature (> 0)                                        */
+    int32_t init_side;        /* init_mode 2: side of the square cells                   */
+    int32_t init_cols;        /* init_mode 2: cells per row of the centred block         */
+    int32_t reserved;         /* must be 0                                               */
+} spin_cpm_params;
+
+typedef struct spin_ctx spin_ctx;
+
+/* Create a context for n_lattices lattices of one model.
+ * d_spins: caller's device buffer (int8 Ising, uint8 Potts, int32 CPM) that
+ *   holds every lattice at its spin_offset; borrowed until spin_destroy.
+ * init_mode: 0 = random state from the seed (Philox(seed; g = i >> 2, lattice,
+ *   0xFFFFFFFF, 0), lane i & 3 for site i = yL + x: Ising s = u>>31 ? +1 : -1,
+ *   Potts s = floor(u q / 2^32)); 1 = keep the caller's state; 2 = CPM square
+ *   cells (CPM only).  cpm must be non-NULL exactly for CPM (one lattice).
+ * max_record_sweeps: capacity of the per-sweep observable ring (0 = none).
+ * The sweep counter starts at 0.  Returns SPIN_OK and *out, or an error.  */
+int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
+              const spin_lattice_desc *lat, const spin_cpm_params *cpm, void *d_spins,
+              int32_t init_mode, int32_t max_record_sweeps, void *stream);
+
+/* Run n_sweeps sweeps (CPM: Monte Carlo steps) of every lattice (Alg. 1).
+ * On return (in stream order) the caller's buffer holds the new state.
+ * record != 0 appends the observables after each sweep to the ring.       */
+int spin_sweep(spin_ctx *ctx, int32_t n_sweeps, int32_t record, void *stream);
+
+/* Number of int64 statistics per lattice per sweep:
+ *   Ising 2: (M = sum s, B = sum_bonds s s');
+ *   Potts 1+q_max: (B_eq = #equal bonds, n_0 .. n_{q_max-1});
+ *   CPM n_types(n_types+1)/2 + 2: (C_ab for a <= b = #Moore contacts between
+ *       different cells of types a and b, V2 = sum_cells (a-A)^2, V1 = sum_cells (a-A)). */
+int spin_stats_width(const spin_ctx *ctx);
+
+/* Number of sweeps recorded so far (records are numbered from 0). */
+int64_t spin_num_records(const spin_ctx *ctx);
+
+/* Copy records [first, first + n) of the ring.  Any output may be NULL; each
+ * may be a device or a (pinned or pageable) host pointer.
+ *   stats [n][n_lattices][width] int64, exact;
+ *   E, M  [n][n_lattices] float: energy per site and magnetisation per site
+ *   (Ising: E = -J B - h M, M = sum s; Potts: E = -J B_eq,
+ *   M = (q max_k n_k - N)/(q - 1); CPM: E = total H, M = adhesion energy),
+ *   computed in double from the exact integers and rounded once.
+ * Only the last max_record_sweeps records are held (SPIN_EINVAL otherwise). */
+int spin_observables(spin_ctx *ctx, int64_t first, int32_t n, int64_t *stats, float *E,
+                     float *M, void *stream);
+
+/* Statistics of the current state, recomputed from the lattice
+ * ([n_lattices][width] int64, device or host pointer). */
+int spin_current_stats(spin_ctx *ctx, int64_t *stats, void *stream);
+
+/* Exact integer moments over records [first, first + n) per lattice:
+ * [n_lattices][n_mom] int64 with n_mom = 1 + w + w(w+1)/2 for w = width:
+ * (count, sum_i X_i, sum_{i<=j} X_i X_j) in row-major upper-triangle order.
+ * This is the adjoint reduction of the fluctuation estimator.             */
+int spin_moments(spin_ctx *ctx, int64_t first, int32_t n, int64_t *moments, void *stream);
+int spin_num_moments(const spin_ctx *ctx);
+
+/* Fluctuation estimator d<O>/dtheta = <dO/dtheta> - beta (<O dH/dtheta> - <O><dH/dtheta>)
+ * over records [first, first + n) (not in the paper, which differentiates
+ * relaxed Monte Carlo steps, Alg. 2; this is the exact identity for a
+ * Boltzmann law, evaluated from the recorded samples).  Integer moments are
+ * exact; the covariance is formed in FP64 on the device.
+ * Ising: observable 0 = E/N, 1 = M/N; out[l][0] = d/dJ, out[l][1] = d/dh.
+ * CPM:   observable 0 = adhesion energy per site; out[0][i] = d/dJ_ab for the
+ *        i-th pair a <= b, then d/dlambda, d/dA (beta = 1/T).
+ * pool != 0 pools the samples of all lattices (they must share theta) and
+ * writes one row.  out: device or host pointer, FP64.                    */
+int spin_grad(spin_ctx *ctx, int64_t first, int32_t n, int32_t observable, int32_t pool,
+              double *out, void *stream);
+int spin_num_grad(const spin_ctx *ctx);
+
+/* Replace temperatures/couplings (L, q and offsets must not change) and
+ * rebuild the acceptance tables; takes effect at the next sweep. */
+int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_params *cpm);
+
+/* Launch form.  mode: 0 = batched persistent work-list launch (default),
+ * 1 = plain per-lattice launches (two per lattice per sweep), 2 = resident
+ * (each lattice stays in shared memory for the whole call; small lattices).
+ * use_graph: capture the sweep loop in a CUDA graph.  tile_rows / threads:
+ * work-item height and CTA size for mode 0 (0 = keep).  Results do not
+ * depend on any of these. */
+int spin_set_launch(spin_ctx *ctx, int32_t mode, int32_t use_graph, int32_t tile_rows,
+                    int32_t threads);
+/* Time the launch forms and tile shapes on the current state (the state is
+ * saved and restored) and keep the fastest; the choice is cached per batch
+ * shape in the file named by $SPINMC_TUNE_CACHE when it is set.          */
+int spin_autotune(spin_ctx *ctx, int32_t sweeps_per_trial, void *stream);
+/* Current launch form as (mode, use_graph, tile_rows, threads). */
+int spin_get_launch(const spin_ctx *ctx, int32_t out[4]);
+
+/* Copy the spins between the context's device state and host memory. */
+int spin_load_spins(spin_ctx *ctx, const void *host, void *stream);
+int spin_store_spins(spin_ctx *ctx, void *host, void *stream);
+
+/* Checkpoint = (sweep counter, record count, CPM areas, spins).  With
+ * host_blob == NULL, *size receives the size needed. Restoring into a
+ * context of the same shape continues the chain bit-identically.       */
+int spin_checkpoint(spin_ctx *ctx, void *host_blob, size_t *size, void *stream);
+int spin_restore(spin_ctx *ctx, const void *host_blob, size_t size, void *stream);
+
+/* Kernel timing for roofline measurements.  While enabled (enable != 0),
+ * spin_sweep launches directly (no graph replay) and brackets each launch of
+ * the main sweep kernel (the batched work-list kernel, or the per-lattice
+ * kernels of the plain form) with CUDA events on the caller's stream, up to
+ * max_launches launches.  spin_profile_read synchronises the stream and
+ * returns the summed kernel time (ms) and the number of timed launches;
+ * enabling again resets the sums.  Not in the paper: measurement plumbing. */
+int spin_profile(spin_ctx *ctx, int32_t enable, int32_t max_launches);
+int spin_profile_read(spin_ctx *ctx, double *total_ms, int64_t *launches, void *stream);
+
+uint32_t spin_sweep_index(const spin_ctx *ctx);
+int32_t spin_gpu_launches(const spin_ctx *ctx); /* kernels launched by the last spin_sweep */
+const char *spin_last_error(const spin_ctx *ctx);
+void spin_destroy(spin_ctx *ctx);
+int spin_version(void);
+
+/* ------------------------------------------------------------------------
+ * BF16 MLP surrogate 3 -> 64 -> 64 -> 2 (ReLU) mapping (beta, J, h) to
+ * (<E>/N, <M>/N).  Not in the paper.  Weights live in one device buffer
+ * of spin_mlp_param_count() floats (FP32 master copy, layout W1[64][3],
+ * b1[64], W2[64][64], b2[64], W3[2][64], b3[2]); the kernels round weights
+ * and activations to BF16 and accumulate in FP32.  Inputs are normalised
+ * as x' = (x - mu) * inv_sigma (mu, inv_sigma: 3 floats each, device).
+ * ------------------------------------------------------------------------ */
+int spin_mlp_param_count(void);
+/* Y[n][2] = net(X[n][3]). All pointers device. */
+int spin_mlp_forward(const float *params, const float *mu, const float *inv_sigma,
+                     const float *X, int32_t n, float *Y, void *stream);
+/* Loss L = 1/(2n) sum |Y - T|^2; writes grad[param_count] (dL/dparams),
+ * loss[1] and, if dX != NULL, dX[n][3] = dL/dX.  All pointers device.   */
+int spin_mlp_backward(const float *params, const float *mu, const float *inv_sigma,
+                      const float *X, const float *T, int32_t n, float *grad, float *loss,
+                      float *dX, void *stream);
+/* Adam (Kingma & Ba) on params with moments m, v (device), step >= 1.    */
+int spin_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t step, float lr,
+                  float beta1, float beta2, float eps, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPINMC_H */

@@ -1,0 +1,1083 @@
+// abi.cpp -- host side of libspinmc.so: the C ABI declared in include/spinmc.h.
+//
+// Holds the per-context state (lattice descriptors, acceptance tables, the
+// second spin buffer, statistics), validates arguments, builds the work list
+// of the batched sweep, captures the sweep loop in CUDA graphs, and runs the
+// autotuner.  Every step of the Monte Carlo path runs in the kernels of the
+// .cu files; this file only plans and launches them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "spinmc.h"
+
+namespace spinmc {
+cudaError_t set_ising_fused_smem(size_t smem);
+cudaError_t set_potts_fused_smem(size_t smem);
+cudaError_t launch_cpm_types(uint8_t *type, int n_cells, uint32_t lat, uint32_t k0, uint32_t k1,
+                             cudaStream_t s);
+cudaError_t launch_moments_i128(const StatsBufs &st, int64_t first, int n, void *out,
+                                cudaStream_t s);
+cudaError_t launch_pool_moments(const void *in, int n_lat, int n_mom, void *out, cudaStream_t s);
+cudaError_t launch_i128_to_i64(const void *in, int64_t *out, int n, int *overflow, cudaStream_t s);
+cudaError_t launch_grad_i128(const void *moments, int rows, GradParams p, double *out,
+                             cudaStream_t s);
+cudaError_t launch_copy_lattices(const void *src, void *dst, const LatDev *lats, int n_lat,
+                                 int elem, cudaStream_t s);
+}  // namespace spinmc
+
+using namespace spinmc;
+
+namespace {
+
+constexpr int kMaxItemBytes = 65536;   // bounds the per-thread packed counters
+constexpr int kWholeMaxBytes = 16384;  // lattices up to 128 x 128 are one item
+constexpr int kMaxL = 32768;
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+};
+
+}  // namespace
+
+struct spin_ctx {
+    int model = 0;
+    uint64_t seed = 0;
+    uint32_t k0 = 0, k1 = 0;
+    int n_lat = 0;
+    std::vector<spin_lattice_desc> lat;
+    int maxL = 0;
+    size_t elem = 1;
+    // CPM
+    int n_types = 0, lambda = 0, target = 0, n_cells = 0, init_side = 0, init_cols = 0;
+    float T = 1.0f;
+    std::vector<int32_t> Jt;
+    // device buffers
+    void *spins = nullptr;    // caller's
+    void *spins2 = nullptr;   // ours (ping-pong partner)
+    size_t span_elems = 0;
+    LatDev *d_lats = nullptr;
+    TabEntry *d_tabs = nullptr;
+    Item *d_items = nullptr;
+    int n_items = 0;
+    int32_t *d_generic = nullptr;
+    int n_generic = 0, generic_maxL = 0;
+    std::vector<int> fast_ids;
+    DevState *d_state = nullptr;
+    StatsBufs st{};
+    int width = 0;
+    uint8_t *d_type = nullptr;
+    int32_t *d_J = nullptr;
+    int32_t *d_vol[2] = {nullptr, nullptr};
+    uint32_t *d_thr = nullptr;
+    int n_thr = 0;
+    double *d_latp = nullptr;   // [n_lat][4]
+    double *d_cpmJ = nullptr;   // [pairs]
+    void *d_scratch = nullptr;  // moments etc.
+    size_t scratch_bytes = 0;
+    int *d_flag = nullptr;
+    // host mirrors
+    uint32_t t = 0;
+    int64_t n_rec = 0;
+    // launch form
+    int mode = 0, use_graph = 1, tile_rows = 0, threads = 256;
+    int grid = 0;
+    size_t smem = 0;
+    int sm_count = 0;
+    cudaStream_t cap_stream = nullptr;
+    GraphCache graphs[2][2];    // [record][0: two-sweep ping-pong]
+    int last_launches = 0;
+    // kernel timing (spin_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_n = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(spin_ctx *c, int code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(spin_ctx *c, cudaError_t e, const char *where) {
+    return fail(c, SPIN_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
+    } while (0)
+
+cudaStream_t S(void *stream) { return static_cast<cudaStream_t>(stream); }
+
+// ---------------------------------------------------------------- tables
+// Number of accepted values of a uniform uint32 draw, minus one:
+// dE <= 0 -> all; else max(floor(exp(-beta dE) 2^32), 1) - 1.
+uint32_t thr_from(double beta, double dE) {
+    if (dE <= 0.0) return 0xFFFFFFFFu;
+    double k = std::floor(std::exp(-beta * dE) * 4294967296.0);
+    if (k < 1.0) k = 1.0;
+    if (k > 4294967296.0) k = 4294967296.0;
+    return (uint32_t)(k - 1.0);
+}
+
+void ising_table(const spin_lattice_desc &d, TabEntry *e) {
+    const double beta = (double)d.beta;
+    for (int c = 0; c < 2; ++c)
+        for (int dn = 0; dn <= 4; ++dn) {
+            const int s = c ? -1 : 1;
+            const int n = 4 - 2 * dn;
+            const double dE = 2.0 * (double)s * ((double)d.J * (double)n + (double)d.h);
+            TabEntry &x = e[dn + 5 * c];
+            x.thr = thr_from(beta, dE);
+            const int dM = -2 * s, dB = -2 * s * n;
+            x.delta = dB * 65536 + dM;
+        }
+}
+
+void potts_table(const spin_lattice_desc &d, TabEntry *e) {
+    const double beta = (double)d.beta;
+    for (int dd = -4; dd <= 4; ++dd) {
+        const double dE = (double)d.J * (double)dd;
+        e[dd + 4].thr = thr_from(beta, dE);
+        e[dd + 4].delta = -dd;
+    }
+}
+
+int stats_width(int model, const std::vector<spin_lattice_desc> &lat, int n_types) {
+    if (model == SPIN_ISING) return 2;
+    if (model == SPIN_POTTS) {
+        int q = 2;
+        for (auto &d : lat) q = std::max(q, d.q);
+        return 1 + q;
+    }
+    return n_types * (n_types + 1) / 2 + 2;
+}
+
+int validate(spin_ctx *ctx, int model, int n, const spin_lattice_desc *lat,
+             const spin_cpm_params *cpm) {
+    if (model < 0 || model > 2) return fail(ctx, SPIN_EINVAL, "unknown model");
+    if (n <= 0 || n > 65535 || !lat) return fail(ctx, SPIN_EINVAL, "n_lattices must be in [1, 65535]");
+    if ((model == SPIN_CPM) != (cpm != nullptr))
+        return fail(ctx, SPIN_EINVAL, "cpm parameters are required exactly for the CPM model");
+    if (model == SPIN_CPM && n != 1) return fail(ctx, SPIN_EINVAL, "the CPM model takes one lattice");
+    std::vector<std::pair<uint64_t, uint64_t>> spans;
+    for (int i = 0; i < n; ++i) {
+        const spin_lattice_desc &d = lat[i];
+        char buf[160];
+        if (d.L < 4 || (d.L & 1) || d.L > kMaxL) {
+            snprintf(buf, sizeof buf, "lattice %d: L=%d must be even and in [4, %d]", i, d.L, kMaxL);
+            return fail(ctx, SPIN_EINVAL, buf);
+        }
+        if (d.reserved != 0) return fail(ctx, SPIN_EINVAL, "reserved field must be 0");
+        if (model == SPIN_POTTS) {
+            if (d.q < 2 || d.q > 255) {
+                snprintf(buf, sizeof buf, "lattice %d: q=%d out of [2, 255]", i, d.q);
+                return fail(ctx, SPIN_EINVAL, buf);
+            }
+            if (d.h != 0.0f) return fail(ctx, SPIN_EINVAL, "Potts lattices take no field (h must be 0)");
+        }
+        if (model != SPIN_CPM) {
+            if (!std::isfinite(d.beta) || d.beta < 0.0f)
+                return fail(ctx, SPIN_EINVAL, "beta must be finite and >= 0");
+            if (!std::isfinite(d.J) || !std::isfinite(d.h))
+                return fail(ctx, SPIN_EINVAL, "J and h must be finite");
+        } else if (d.L % 4) {
+            return fail(ctx, SPIN_EINVAL, "CPM lattices need L % 4 == 0");
+        }
+        spans.push_back({d.spin_offset, d.spin_offset + (uint64_t)d.L * d.L});
+    }
+    std::sort(spans.begin(), spans.end());
+    for (size_t i = 1; i < spans.size(); ++i)
+        if (spans[i].first < spans[i - 1].second) return fail(ctx, SPIN_EINVAL, "lattices overlap");
+    if (cpm) {
+        if (cpm->n_types < 1 || cpm->n_types > 8 || !cpm->J_type)
+            return fail(ctx, SPIN_EINVAL, "CPM n_types must be in [1, 8] with a J table");
+        for (int a = 0; a < cpm->n_types; ++a)
+            for (int b = 0; b < cpm->n_types; ++b)
+                if (cpm->J_type[a * cpm->n_types + b] != cpm->J_type[b * cpm->n_types + a])
+                    return fail(ctx, SPIN_EINVAL, "CPM J table must be symmetric");
+        if (!(cpm->T > 0.0f) || !std::isfinite(cpm->T)) return fail(ctx, SPIN_EINVAL, "CPM T must be > 0");
+        if (cpm->n_cells < 1 || cpm->n_cells >= lat[0].L * lat[0].L)
+            return fail(ctx, SPIN_EINVAL, "CPM n_cells out of range");
+        if (cpm->lambda < 0 || cpm->target_area < 0) return fail(ctx, SPIN_EINVAL, "lambda and A must be >= 0");
+        if (cpm->reserved != 0) return fail(ctx, SPIN_EINVAL, "reserved field must be 0");
+        if (cpm->cell_type) {
+            if (cpm->cell_type[0] != 0) return fail(ctx, SPIN_EINVAL, "cell_type[0] must be 0 (medium)");
+            for (int c = 1; c <= cpm->n_cells; ++c)
+                if (cpm->cell_type[c] >= cpm->n_types) return fail(ctx, SPIN_EINVAL, "cell type out of range");
+        } else if (cpm->n_types < 3) {
+            return fail(ctx, SPIN_EINVAL, "drawn cell types need n_types >= 3");
+        }
+    }
+    return SPIN_OK;
+}
+
+int upload_tables(spin_ctx *ctx, cudaStream_t s) {
+    if (ctx->model == SPIN_CPM) {
+        std::vector<uint32_t> thr;
+        thr.push_back(0xFFFFFFFFu);  // dE = 0 (never read: dE <= 0 accepts)
+        for (int dE = 1; dE < (1 << 22); ++dE) {
+            const double k = std::floor(std::exp(-(double)dE / (double)ctx->T) * 4294967296.0);
+            if (k <= 1.0) break;
+            thr.push_back((uint32_t)(std::min(k, 4294967296.0) - 1.0));
+        }
+        if (ctx->d_thr) cudaFree(ctx->d_thr);
+        ctx->d_thr = nullptr;
+        CK(cudaMalloc(&ctx->d_thr, sizeof(uint32_t) * thr.size()));
+        CK(cudaMemcpy(ctx->d_thr, thr.data(), sizeof(uint32_t) * thr.size(), cudaMemcpyHostToDevice));
+        ctx->n_thr = (int)thr.size();
+        CK(cudaMemcpy(ctx->d_J, ctx->Jt.data(), sizeof(int32_t) * ctx->Jt.size(), cudaMemcpyHostToDevice));
+        // observables: J per pair (a <= b)
+        std::vector<double> pj;
+        for (int a = 0; a < ctx->n_types; ++a)
+            for (int b = a; b < ctx->n_types; ++b) pj.push_back((double)ctx->Jt[a * ctx->n_types + b]);
+        CK(cudaMemcpy(ctx->d_cpmJ, pj.data(), sizeof(double) * pj.size(), cudaMemcpyHostToDevice));
+        std::vector<double> lp = {0.0, 0.0, (double)ctx->lat[0].L * ctx->lat[0].L, 1.0 / (double)ctx->T};
+        CK(cudaMemcpy(ctx->d_latp, lp.data(), sizeof(double) * 4, cudaMemcpyHostToDevice));
+        return SPIN_OK;
+    }
+    std::vector<TabEntry> tab((size_t)ctx->n_lat * kTabStride, TabEntry{0u, 0});
+    std::vector<double> lp((size_t)ctx->n_lat * 4);
+    for (int i = 0; i < ctx->n_lat; ++i) {
+        const spin_lattice_desc &d = ctx->lat[i];
+        if (ctx->model == SPIN_ISING)
+            ising_table(d, &tab[(size_t)i * kTabStride]);
+        else
+            potts_table(d, &tab[(size_t)i * kTabStride]);
+        lp[4 * i] = d.J;
+        lp[4 * i + 1] = d.h;
+        lp[4 * i + 2] = (double)d.L * d.L;
+        lp[4 * i + 3] = ctx->model == SPIN_POTTS ? (double)d.q : (double)d.beta;
+    }
+    (void)s;
+    CK(cudaMemcpy(ctx->d_tabs, tab.data(), sizeof(TabEntry) * tab.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_latp, lp.data(), sizeof(double) * lp.size(), cudaMemcpyHostToDevice));
+    return SPIN_OK;
+}
+
+void drop_graphs(spin_ctx *ctx) {
+    for (auto &r : ctx->graphs)
+        for (auto &g : r) {
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+            g.launches = 0;
+        }
+}
+
+// Work list of the batched launch over the vectorisable lattices.
+int plan(spin_ctx *ctx) {
+    drop_graphs(ctx);
+    if (ctx->model == SPIN_CPM) return SPIN_OK;
+    std::vector<Item> items;
+    size_t smem = 16;
+    for (int id : ctx->fast_ids) {
+        const int L = ctx->lat[id].L;
+        if (L * L <= kWholeMaxBytes) {
+            items.push_back(Item{id, 0, L, 1});
+            smem = std::max(smem, (size_t)L * L);
+            continue;
+        }
+        int rows = ctx->tile_rows > 0 ? ctx->tile_rows : std::max(1, 32768 / L);
+        rows = std::min(rows, L);
+        rows = std::max(1, std::min(rows, kMaxItemBytes / L));
+        for (int r0 = 0; r0 < L; r0 += rows) {
+            const int nr = std::min(rows, L - r0);
+            items.push_back(Item{id, r0, nr, 0});
+        }
+        smem = std::max(smem, (size_t)(rows + 4) * L);
+    }
+    std::stable_sort(items.begin(), items.end(), [&](const Item &a, const Item &b) {
+        return (size_t)a.nrows * ctx->lat[a.lat].L > (size_t)b.nrows * ctx->lat[b.lat].L;
+    });
+    if (ctx->d_items) cudaFree(ctx->d_items);
+    ctx->d_items = nullptr;
+    ctx->n_items = (int)items.size();
+    if (!items.empty()) {
+        CK(cudaMalloc(&ctx->d_items, sizeof(Item) * items.size()));
+        CK(cudaMemcpy(ctx->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice));
+    }
+    if (smem > 200 * 1024) return fail(ctx, SPIN_EINVAL, "work item does not fit in shared memory");
+    ctx->smem = smem;
+    if (ctx->model == SPIN_ISING)
+        CK(set_ising_fused_smem(smem));
+    else if (ctx->model == SPIN_POTTS)
+        CK(set_potts_fused_smem(smem));
+    ctx->grid = std::max(1, std::min(ctx->n_items, ctx->sm_count * std::max(1, (int)(2048 / ctx->threads))));
+    // residency bound: at most as many blocks as fit on the GPU at once
+    const int per_sm_smem = (int)((228 * 1024) / (smem + 1024));
+    const int per_sm_thr = 2048 / ctx->threads;
+    const int per_sm = std::max(1, std::min(per_sm_smem, per_sm_thr));
+    ctx->grid = std::max(1, std::min(ctx->n_items, ctx->sm_count * per_sm));
+    return SPIN_OK;
+}
+
+// Event pair around one timed kernel launch (spin_profile).
+bool prof_begin(spin_ctx *ctx, cudaStream_t s) {
+    if (!ctx->prof || 2 * (ctx->prof_n + 1) > (int)ctx->prof_ev.size()) return false;
+    return cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], s) == cudaSuccess;
+}
+
+void prof_end(spin_ctx *ctx, cudaStream_t s) {
+    cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], s);
+    ++ctx->prof_n;
+}
+
+// One sweep of Ising/Potts lattices, src -> dst (batched) or in place (plain).
+int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s, int &launches) {
+    const int w = ctx->width;
+    if (ctx->mode == 1) {
+        for (int c = 0; c < 2; ++c) {
+            for (int id : ctx->fast_ids) {
+                const int L = ctx->lat[id].L;
+                const bool timed = prof_begin(ctx, s);
+                if (ctx->model == SPIN_ISING)
+                    CK(launch_ising_plain(static_cast<int8_t *>(src) + ctx->lat[id].spin_offset, ctx->d_lats,
+                                          id, L, ctx->d_tabs, ctx->k0, ctx->k1, ctx->d_state,
+                                          ctx->st.delta, c, s));
+                else
+                    CK(launch_potts_plain(static_cast<uint8_t *>(src) + ctx->lat[id].spin_offset, ctx->d_lats,
+                                          id, L, ctx->lat[id].q, ctx->d_tabs, ctx->k0, ctx->k1,
+                                          ctx->d_state, ctx->st.delta, w, c, s));
+                if (timed) prof_end(ctx, s);
+                ++launches;
+            }
+            if (ctx->n_generic) {
+                if (ctx->model == SPIN_ISING)
+                    CK(launch_ising_generic(static_cast<int8_t *>(src), static_cast<int8_t *>(src), ctx->d_generic,
+                                            ctx->n_generic, ctx->generic_maxL, ctx->d_lats, ctx->d_tabs,
+                                            ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, c, s));
+                else
+                    CK(launch_potts_generic(static_cast<uint8_t *>(src), static_cast<uint8_t *>(src), ctx->d_generic,
+                                            ctx->n_generic, ctx->generic_maxL, ctx->d_lats, ctx->d_tabs,
+                                            ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, w, c, s));
+                ++launches;
+            }
+        }
+    } else {
+        for (int c = 0; c < 2 && ctx->n_generic; ++c) {
+            if (ctx->model == SPIN_ISING)
+                CK(launch_ising_generic(static_cast<int8_t *>(src), static_cast<int8_t *>(dst), ctx->d_generic,
+                                        ctx->n_generic, ctx->generic_maxL, ctx->d_lats, ctx->d_tabs,
+                                        ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, c, s));
+            else
+                CK(launch_potts_generic(static_cast<uint8_t *>(src), static_cast<uint8_t *>(dst), ctx->d_generic,
+                                        ctx->n_generic, ctx->generic_maxL, ctx->d_lats, ctx->d_tabs,
+                                        ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, w, c, s));
+            ++launches;
+        }
+        if (ctx->n_items) {
+            const bool timed = prof_begin(ctx, s);
+            if (ctx->model == SPIN_ISING) {
+                IsingSweepArgs a{ctx->d_items, ctx->n_items, ctx->d_lats, ctx->d_tabs,
+                                 static_cast<const int8_t *>(src), static_cast<int8_t *>(dst),
+                                 ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta};
+                CK(launch_ising_fused(a, ctx->grid, ctx->threads, ctx->smem, s));
+            } else {
+                PottsSweepArgs a{ctx->d_items, ctx->n_items, ctx->d_lats, ctx->d_tabs,
+                                 static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst),
+                                 ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, w};
+                CK(launch_potts_fused(a, ctx->grid, ctx->threads, ctx->smem, s));
+            }
+            if (timed) prof_end(ctx, s);
+            ++launches;
+        }
+    }
+    CK(launch_finalize(ctx->d_state, ctx->st, record, s));
+    ++launches;
+    return SPIN_OK;
+}
+
+int launch_cpm_step(spin_ctx *ctx, int record, cudaStream_t s, int &launches) {
+    for (int c = 0; c < 4; ++c) {
+        CpmArgs a{static_cast<int32_t *>(ctx->spins), ctx->lat[0].L, 0u, ctx->d_type, ctx->d_J,
+                  ctx->n_types, ctx->n_cells, ctx->lambda, ctx->target, ctx->d_vol[0], ctx->d_vol[1],
+                  ctx->d_thr, ctx->n_thr, ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta};
+        CK(launch_cpm_substep(a, c, s));
+        CK(launch_cpm_finalize(ctx->d_vol[0], ctx->d_vol[1], ctx->n_cells, ctx->target,
+                               ctx->d_state, ctx->st, c, record, s));
+        launches += 2;
+    }
+    return SPIN_OK;
+}
+
+// Record `two sweeps` (A -> B -> A for the batched form) into a graph.
+int get_graph(spin_ctx *ctx, int record, GraphCache *&out) {
+    GraphCache &g = ctx->graphs[record ? 1 : 0][0];
+    if (!g.exec) {
+        if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        int launches = 0, rc = SPIN_OK;
+        if (ctx->model == SPIN_CPM) {
+            rc = launch_cpm_step(ctx, record, ctx->cap_stream, launches);
+        } else if (ctx->mode == 1) {
+            rc = launch_sweep(ctx, ctx->spins, ctx->spins, record, ctx->cap_stream, launches);
+            if (rc == SPIN_OK) rc = launch_sweep(ctx, ctx->spins, ctx->spins, record, ctx->cap_stream, launches);
+        } else {
+            rc = launch_sweep(ctx, ctx->spins, ctx->spins2, record, ctx->cap_stream, launches);
+            if (rc == SPIN_OK) rc = launch_sweep(ctx, ctx->spins2, ctx->spins, record, ctx->cap_stream, launches);
+        }
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+        if (rc != SPIN_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        g.launches = launches;
+    }
+    out = &g;
+    return SPIN_OK;
+}
+
+int run_sweeps(spin_ctx *ctx, int n, int record, cudaStream_t s) {
+    int launches = 0;
+    if (ctx->model == SPIN_CPM) {
+        int i = 0;
+        if (ctx->use_graph && !ctx->prof && n >= 1) {
+            GraphCache *g = nullptr;
+            int rc = get_graph(ctx, record, g);
+            if (rc) return rc;
+            for (; i < n; ++i) {
+                CK(cudaGraphLaunch(g->exec, s));
+                launches += g->launches;
+            }
+        }
+        for (; i < n; ++i) {
+            int rc = launch_cpm_step(ctx, record, s, launches);
+            if (rc) return rc;
+        }
+        ctx->last_launches = launches;
+        return SPIN_OK;
+    }
+    int i = 0;
+    if (ctx->use_graph && !ctx->prof && n >= 2) {
+        GraphCache *g = nullptr;
+        int rc = get_graph(ctx, record, g);
+        if (rc) return rc;
+        for (; i + 1 < n; i += 2) {
+            CK(cudaGraphLaunch(g->exec, s));
+            launches += g->launches;
+        }
+    }
+    for (; i < n; ++i) {
+        const bool even = (i & 1) == 0;
+        void *src = ctx->mode == 1 ? ctx->spins : (even ? ctx->spins : ctx->spins2);
+        void *dst = ctx->mode == 1 ? ctx->spins : (even ? ctx->spins2 : ctx->spins);
+        int rc = launch_sweep(ctx, src, dst, record, s, launches);
+        if (rc) return rc;
+    }
+    if (ctx->mode != 1 && (n & 1)) {
+        CK(launch_copy_lattices(ctx->spins2, ctx->spins, ctx->d_lats, ctx->n_lat, (int)ctx->elem, s));
+        ++launches;
+    }
+    ctx->last_launches = launches;
+    return SPIN_OK;
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int ensure_scratch(spin_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->scratch_bytes) return SPIN_OK;
+    if (ctx->d_scratch) cudaFree(ctx->d_scratch);
+    ctx->d_scratch = nullptr;
+    ctx->scratch_bytes = 0;
+    CK(cudaMalloc(&ctx->d_scratch, bytes));
+    ctx->scratch_bytes = bytes;
+    return SPIN_OK;
+}
+
+int check_records(spin_ctx *ctx, int64_t first, int32_t n) {
+    if (n < 0 || first < 0) return fail(ctx, SPIN_EINVAL, "negative record range");
+    if (first + n > ctx->n_rec) return fail(ctx, SPIN_EINVAL, "records beyond the last recorded sweep");
+    if (first < ctx->n_rec - ctx->st.cap) return fail(ctx, SPIN_EINVAL, "records already overwritten in the ring");
+    return SPIN_OK;
+}
+
+std::string shape_key(const spin_ctx *ctx) {
+    std::ostringstream o;
+    o << "m" << ctx->model << "_n" << ctx->n_lat;
+    uint64_t h = 1469598103934665603ull;
+    for (auto &d : ctx->lat) {
+        h ^= (uint64_t)d.L * 1315423911u + (uint64_t)d.q;
+        h *= 1099511628211ull;
+    }
+    o << "_h" << std::hex << h;
+    return o.str();
+}
+
+}  // namespace
+
+extern "C" {
+
+int spin_version(void) { return 1; }
+
+const char *spin_last_error(const spin_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int spin_stats_width(const spin_ctx *ctx) { return ctx ? ctx->width : SPIN_EINVAL; }
+
+int64_t spin_num_records(const spin_ctx *ctx) { return ctx ? ctx->n_rec : SPIN_EINVAL; }
+
+uint32_t spin_sweep_index(const spin_ctx *ctx) { return ctx ? ctx->t : 0u; }
+
+int32_t spin_gpu_launches(const spin_ctx *ctx) { return ctx ? ctx->last_launches : 0; }
+
+int spin_num_moments(const spin_ctx *ctx) {
+    if (!ctx) return SPIN_EINVAL;
+    const int w = ctx->width;
+    return 1 + w + w * (w + 1) / 2;
+}
+
+int spin_num_grad(const spin_ctx *ctx) {
+    if (!ctx) return SPIN_EINVAL;
+    return ctx->model == SPIN_ISING ? 2 : (ctx->model == SPIN_CPM ? ctx->width : SPIN_EINVAL);
+}
+
+void spin_destroy(spin_ctx *ctx) {
+    if (!ctx) return;
+    drop_graphs(ctx);
+    void *bufs[] = {ctx->spins2, ctx->d_lats, ctx->d_tabs, ctx->d_items, ctx->d_generic,
+                    ctx->d_state, ctx->st.cur, ctx->st.delta, ctx->st.ring, ctx->d_type,
+                    ctx->d_J, ctx->d_vol[0], ctx->d_vol[1], ctx->d_thr, ctx->d_latp,
+                    ctx->d_cpmJ, ctx->d_scratch, ctx->d_flag};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
+    delete ctx;
+}
+
+int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
+              const spin_lattice_desc *lat, const spin_cpm_params *cpm, void *d_spins,
+              int32_t init_mode, int32_t max_record_sweeps, void *stream) {
+    if (!out) return SPIN_EINVAL;
+    *out = nullptr;
+    spin_ctx *ctx = new spin_ctx();
+    auto bail = [&](int rc) {
+        spin_destroy(ctx);
+        return rc;
+    };
+    int rc = validate(ctx, model, n_lattices, lat, cpm);
+    if (rc) {
+        fprintf(stderr, "spin_init: %s\n", ctx->err.c_str());
+        return bail(rc);
+    }
+    if (!d_spins) return bail(SPIN_EINVAL);
+    if (!is_device_ptr(d_spins)) return bail(SPIN_EINVAL);
+    const bool mode_ok = model == SPIN_CPM ? (init_mode == 1 || init_mode == 2)
+                                           : (init_mode == 0 || init_mode == 1);
+    if (!mode_ok) return bail(fail(ctx, SPIN_EINVAL, "init_mode not valid for this model"));
+    if (max_record_sweeps < 0) return bail(SPIN_EINVAL);
+    cudaStream_t s = S(stream);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return bail(SPIN_ECUDA);
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    ctx->model = model;
+    ctx->seed = seed;
+    ctx->k0 = (uint32_t)(seed & 0xFFFFFFFFu);
+    ctx->k1 = (uint32_t)(seed >> 32);
+    ctx->n_lat = n_lattices;
+    ctx->lat.assign(lat, lat + n_lattices);
+    ctx->elem = model == SPIN_CPM ? 4 : 1;
+    ctx->spins = d_spins;
+    if (cpm) {
+        ctx->n_types = cpm->n_types;
+        ctx->lambda = cpm->lambda;
+        ctx->target = cpm->target_area;
+        ctx->n_cells = cpm->n_cells;
+        ctx->T = cpm->T;
+        ctx->init_side = cpm->init_side;
+        ctx->init_cols = cpm->init_cols;
+        ctx->Jt.assign(cpm->J_type, cpm->J_type + cpm->n_types * cpm->n_types);
+    }
+    ctx->width = stats_width(model, ctx->lat, ctx->n_types);
+    std::vector<LatDev> ld(n_lattices);
+    std::vector<int32_t> generic;
+    for (int i = 0; i < n_lattices; ++i) {
+        const auto &d = ctx->lat[i];
+        ld[i] = LatDev{d.spin_offset, d.L, model == SPIN_POTTS ? d.q : 2,
+                       (d.L % 16 == 0 && d.spin_offset % 16 == 0) ? 1 : 0, 0};
+        ctx->maxL = std::max(ctx->maxL, d.L);
+        ctx->span_elems = std::max<size_t>(ctx->span_elems, d.spin_offset + (size_t)d.L * d.L);
+        if (ld[i].fast)
+            ctx->fast_ids.push_back(i);
+        else {
+            generic.push_back(i);
+            ctx->generic_maxL = std::max(ctx->generic_maxL, d.L);
+        }
+    }
+    ctx->n_generic = (int)generic.size();
+    auto ckm = [&](cudaError_t e) { return e == cudaSuccess; };
+    const size_t w = (size_t)ctx->width;
+    if (!ckm(cudaMalloc(&ctx->d_lats, sizeof(LatDev) * n_lattices)) ||
+        !ckm(cudaMalloc(&ctx->d_tabs, sizeof(TabEntry) * kTabStride * n_lattices)) ||
+        !ckm(cudaMalloc(&ctx->d_state, sizeof(DevState))) ||
+        !ckm(cudaMalloc(&ctx->st.cur, sizeof(int64_t) * w * n_lattices)) ||
+        !ckm(cudaMalloc(&ctx->st.delta, sizeof(int64_t) * w * n_lattices)) ||
+        !ckm(cudaMalloc(&ctx->d_latp, sizeof(double) * 4 * n_lattices)) ||
+        !ckm(cudaMalloc(&ctx->d_cpmJ, sizeof(double) * 64)) ||
+        !ckm(cudaMalloc(&ctx->d_flag, sizeof(int))) ||
+        (max_record_sweeps > 0 &&
+         !ckm(cudaMalloc(&ctx->st.ring, sizeof(int64_t) * w * n_lattices * (size_t)max_record_sweeps))))
+        return bail(fail(ctx, SPIN_ENOMEM, "device allocation failed"));
+    if (model != SPIN_CPM && !ckm(cudaMalloc(&ctx->spins2, ctx->span_elems * ctx->elem)))
+        return bail(fail(ctx, SPIN_ENOMEM, "device allocation of the second spin buffer failed"));
+    if (ctx->n_generic) {
+        if (!ckm(cudaMalloc(&ctx->d_generic, sizeof(int32_t) * ctx->n_generic)))
+            return bail(SPIN_ENOMEM);
+        cudaMemcpy(ctx->d_generic, generic.data(), sizeof(int32_t) * generic.size(), cudaMemcpyHostToDevice);
+    }
+    ctx->st.cap = max_record_sweeps;
+    ctx->st.width = ctx->width;
+    ctx->st.n_lat = n_lattices;
+    if (cudaMemcpy(ctx->d_lats, ld.data(), sizeof(LatDev) * n_lattices, cudaMemcpyHostToDevice))
+        return bail(SPIN_ECUDA);
+    cudaMemset(ctx->st.delta, 0, sizeof(int64_t) * w * n_lattices);
+    DevState ds{0u, 0, 0};
+    cudaMemcpy(ctx->d_state, &ds, sizeof ds, cudaMemcpyHostToDevice);
+    if (model == SPIN_CPM) {
+        const int nc = ctx->n_cells;
+        if (!ckm(cudaMalloc(&ctx->d_type, nc + 1)) || !ckm(cudaMalloc(&ctx->d_J, sizeof(int32_t) * 64)) ||
+            !ckm(cudaMalloc(&ctx->d_vol[0], sizeof(int32_t) * (nc + 1))) ||
+            !ckm(cudaMalloc(&ctx->d_vol[1], sizeof(int32_t) * (nc + 1))))
+            return bail(SPIN_ENOMEM);
+    }
+    rc = upload_tables(ctx, s);
+    if (rc) return bail(rc);
+    // initial state
+    cudaError_t e = cudaSuccess;
+    if (init_mode == 0) {
+        e = launch_init_random(d_spins, model, ctx->d_lats, n_lattices, ctx->maxL, ctx->k0, ctx->k1, s);
+    } else if (init_mode == 2) {
+        const int L = ctx->lat[0].L;
+        const int rows = (ctx->n_cells + std::max(1, ctx->init_cols) - 1) / std::max(1, ctx->init_cols);
+        if (ctx->init_side < 1 || ctx->init_cols < 1 || ctx->init_cols * ctx->init_side > L ||
+            rows * ctx->init_side > L)
+            return bail(fail(ctx, SPIN_EINVAL, "initial cell block does not fit the lattice"));
+        e = launch_cpm_init_squares(static_cast<int32_t *>(d_spins) + ctx->lat[0].spin_offset, L,
+                                    ctx->n_cells, ctx->init_side, ctx->init_cols, s);
+    }
+    if (e) return bail(cuda_fail(ctx, e, "init"));
+    if (model == SPIN_CPM) {
+        if (cpm->cell_type) {
+            cudaMemcpyAsync(ctx->d_type, cpm->cell_type, ctx->n_cells + 1, cudaMemcpyHostToDevice, s);
+        } else {
+            e = launch_cpm_types(ctx->d_type, ctx->n_cells, 0u, ctx->k0, ctx->k1, s);
+            if (e) return bail(cuda_fail(ctx, e, "cpm types"));
+        }
+        // the CPM kernels address the lattice at offset 0 of the buffer
+        ctx->spins = static_cast<int32_t *>(d_spins) + ctx->lat[0].spin_offset;
+        cudaMemsetAsync(ctx->d_vol[0], 0, sizeof(int32_t) * (ctx->n_cells + 1), s);
+        e = launch_cpm_volumes(static_cast<int32_t *>(ctx->spins), ctx->lat[0].L, ctx->d_vol[0], ctx->n_cells, s);
+        if (e) return bail(cuda_fail(ctx, e, "cpm volumes"));
+        cudaMemcpyAsync(ctx->d_vol[1], ctx->d_vol[0], sizeof(int32_t) * (ctx->n_cells + 1),
+                        cudaMemcpyDeviceToDevice, s);
+    }
+    if (model != SPIN_CPM) {
+        // keep the bytes outside the lattices identical in both buffers
+        e = cudaMemcpyAsync(ctx->spins2, d_spins, ctx->span_elems * ctx->elem, cudaMemcpyDeviceToDevice, s);
+        if (e) return bail(cuda_fail(ctx, e, "copy"));
+    }
+    e = launch_stats_from_state(ctx->spins, model, ctx->d_lats, n_lattices, ctx->maxL, ctx->width,
+                                ctx->d_type, ctx->n_types, ctx->d_vol[0], ctx->n_cells, ctx->target,
+                                ctx->st.cur, s);
+    if (e) return bail(cuda_fail(ctx, e, "initial statistics"));
+    // CPM statistics read the single lattice at offset 0 of ctx->spins
+    rc = plan(ctx);
+    if (rc) return bail(rc);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return bail(SPIN_ECUDA);
+    *out = ctx;
+    return SPIN_OK;
+}
+
+int spin_sweep(spin_ctx *ctx, int32_t n_sweeps, int32_t record, void *stream) {
+    if (!ctx) return SPIN_EINVAL;
+    if (n_sweeps < 0) return fail(ctx, SPIN_EINVAL, "negative sweep count");
+    if ((uint64_t)ctx->t + (uint64_t)n_sweeps >= 0xFFFFFFFEull)
+        return fail(ctx, SPIN_ESTATE, "sweep counter would reach the values reserved for initialisation");
+    if (record && ctx->st.cap <= 0) return fail(ctx, SPIN_ESTATE, "no record ring (max_record_sweeps = 0)");
+    if (n_sweeps == 0) return SPIN_OK;
+    int rc = run_sweeps(ctx, n_sweeps, record ? 1 : 0, S(stream));
+    if (rc) return rc;
+    ctx->t += (uint32_t)n_sweeps;
+    if (record) ctx->n_rec += n_sweeps;
+    return SPIN_OK;
+}
+
+int spin_observables(spin_ctx *ctx, int64_t first, int32_t n, int64_t *stats, float *E, float *M,
+                     void *stream) {
+    if (!ctx) return SPIN_EINVAL;
+    int rc = check_records(ctx, first, n);
+    if (rc) return rc;
+    if (n == 0) return SPIN_OK;
+    cudaStream_t s = S(stream);
+    const size_t ns = (size_t)n * ctx->n_lat * ctx->width, nf = (size_t)n * ctx->n_lat;
+    const bool dev_s = !stats || is_device_ptr(stats), dev_e = !E || is_device_ptr(E),
+               dev_m = !M || is_device_ptr(M);
+    rc = ensure_scratch(ctx, sizeof(int64_t) * ns + 2 * sizeof(float) * nf + 64);
+    if (rc) return rc;
+    int64_t *ts = dev_s ? stats : static_cast<int64_t *>(ctx->d_scratch);
+    float *te = dev_e ? E : reinterpret_cast<float *>(static_cast<char *>(ctx->d_scratch) + sizeof(int64_t) * ns);
+    float *tm = dev_m ? M : te + nf;
+    ObsParams p{ctx->model, ctx->n_lat, ctx->width, ctx->d_latp, ctx->d_cpmJ, (double)ctx->lambda};
+    CK(launch_observables(ctx->st, first, n, p, ts, te, tm, s));
+    if (!dev_s) CK(cudaMemcpyAsync(stats, ts, sizeof(int64_t) * ns, cudaMemcpyDeviceToHost, s));
+    if (!dev_e) CK(cudaMemcpyAsync(E, te, sizeof(float) * nf, cudaMemcpyDeviceToHost, s));
+    if (!dev_m) CK(cudaMemcpyAsync(M, tm, sizeof(float) * nf, cudaMemcpyDeviceToHost, s));
+    if (!dev_s || !dev_e || !dev_m) CK(cudaStreamSynchronize(s));
+    return SPIN_OK;
+}
+
+int spin_current_stats(spin_ctx *ctx, int64_t *stats, void *stream) {
+    if (!ctx || !stats) return SPIN_EINVAL;
+    cudaStream_t s = S(stream);
+    const size_t ns = (size_t)ctx->n_lat * ctx->width;
+    const bool dev = is_device_ptr(stats);
+    int rc = ensure_scratch(ctx, sizeof(int64_t) * ns);
+    if (rc) return rc;
+    int64_t *t = dev ? stats : static_cast<int64_t *>(ctx->d_scratch);
+    CK(launch_stats_from_state(ctx->spins, ctx->model, ctx->d_lats, ctx->n_lat, ctx->maxL, ctx->width,
+                               ctx->d_type, ctx->n_types, ctx->d_vol[0], ctx->n_cells, ctx->target, t, s));
+    if (!dev) {
+        CK(cudaMemcpyAsync(stats, t, sizeof(int64_t) * ns, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return SPIN_OK;
+}
+
+int spin_moments(spin_ctx *ctx, int64_t first, int32_t n, int64_t *moments, void *stream) {
+    if (!ctx || !moments) return SPIN_EINVAL;
+    int rc = check_records(ctx, first, n);
+    if (rc) return rc;
+    cudaStream_t s = S(stream);
+    const int nm = spin_num_moments(ctx);
+    const size_t cnt = (size_t)nm * ctx->n_lat;
+    rc = ensure_scratch(ctx, 16 * cnt + sizeof(int64_t) * cnt + 64);
+    if (rc) return rc;
+    CK(launch_moments_i128(ctx->st, first, n, ctx->d_scratch, s));
+    const bool dev = is_device_ptr(moments);
+    int64_t *t = dev ? moments : reinterpret_cast<int64_t *>(static_cast<char *>(ctx->d_scratch) + 16 * cnt);
+    CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
+    CK(launch_i128_to_i64(ctx->d_scratch, t, (int)cnt, ctx->d_flag, s));
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (!dev) CK(cudaMemcpyAsync(moments, t, sizeof(int64_t) * cnt, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (flag) return fail(ctx, SPIN_EINVAL, "a moment does not fit in int64");
+    return SPIN_OK;
+}
+
+int spin_grad(spin_ctx *ctx, int64_t first, int32_t n, int32_t observable, int32_t pool, double *out,
+              void *stream) {
+    if (!ctx || !out) return SPIN_EINVAL;
+    if (ctx->model == SPIN_POTTS) return fail(ctx, SPIN_EINVAL, "no gradient for the Potts model");
+    if (ctx->model == SPIN_ISING && (observable < 0 || observable > 1))
+        return fail(ctx, SPIN_EINVAL, "Ising observable must be 0 (E/N) or 1 (M/N)");
+    if (ctx->model == SPIN_CPM && observable != 0) return fail(ctx, SPIN_EINVAL, "CPM observable must be 0");
+    int rc = check_records(ctx, first, n);
+    if (rc) return rc;
+    if (n < 2) return fail(ctx, SPIN_EINVAL, "need at least two records");
+    cudaStream_t s = S(stream);
+    const int nm = spin_num_moments(ctx);
+    const size_t cnt = (size_t)nm * ctx->n_lat;
+    const int rows = pool ? 1 : ctx->n_lat;
+    const int ng = spin_num_grad(ctx);
+    rc = ensure_scratch(ctx, 16 * cnt + 16 * (size_t)nm + sizeof(double) * rows * ng + 64);
+    if (rc) return rc;
+    char *base = static_cast<char *>(ctx->d_scratch);
+    CK(launch_moments_i128(ctx->st, first, n, base, s));
+    const void *mom = base;
+    if (pool) {
+        CK(launch_pool_moments(base, ctx->n_lat, nm, base + 16 * cnt, s));
+        mom = base + 16 * cnt;
+    }
+    GradParams p{ctx->model, ctx->n_lat, ctx->width, observable, pool ? 1 : 0, ctx->d_latp,
+                 ctx->d_cpmJ, (double)ctx->lambda, (double)ctx->T, ctx->width - 2};
+    const bool dev = is_device_ptr(out);
+    double *t = dev ? out : reinterpret_cast<double *>(base + 16 * cnt + 16 * (size_t)nm);
+    CK(launch_grad_i128(mom, rows, p, t, s));
+    if (!dev) {
+        CK(cudaMemcpyAsync(out, t, sizeof(double) * rows * ng, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return SPIN_OK;
+}
+
+int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_params *cpm) {
+    if (!ctx) return SPIN_EINVAL;
+    if (lat) {
+        if (ctx->model == SPIN_CPM) return fail(ctx, SPIN_EINVAL, "CPM contexts take only cpm parameters");
+        int rc = validate(ctx, ctx->model, ctx->n_lat, lat, nullptr);
+        if (rc) return rc;
+        for (int i = 0; i < ctx->n_lat; ++i)
+            if (lat[i].L != ctx->lat[i].L || lat[i].q != ctx->lat[i].q ||
+                lat[i].spin_offset != ctx->lat[i].spin_offset)
+                return fail(ctx, SPIN_EINVAL, "spin_set_params may not change L, q or offsets");
+        ctx->lat.assign(lat, lat + ctx->n_lat);
+    }
+    if (cpm) {
+        if (ctx->model != SPIN_CPM) return fail(ctx, SPIN_EINVAL, "not a CPM context");
+        for (int a = 0; a < cpm->n_types && cpm->J_type; ++a)
+            for (int b = 0; b < cpm->n_types; ++b)
+                if (cpm->J_type[a * cpm->n_types + b] != cpm->J_type[b * cpm->n_types + a])
+                    return fail(ctx, SPIN_EINVAL, "CPM J table must be symmetric");
+        if (!cpm->J_type || cpm->lambda < 0 || cpm->target_area < 0)
+            return fail(ctx, SPIN_EINVAL, "bad CPM parameters");
+        if (cpm->n_types != ctx->n_types || cpm->n_cells != ctx->n_cells)
+            return fail(ctx, SPIN_EINVAL, "spin_set_params may not change n_types or n_cells");
+        if (!(cpm->T > 0.0f)) return fail(ctx, SPIN_EINVAL, "CPM T must be > 0");
+        ctx->Jt.assign(cpm->J_type, cpm->J_type + ctx->n_types * ctx->n_types);
+        ctx->lambda = cpm->lambda;
+        ctx->target = cpm->target_area;
+        ctx->T = cpm->T;
+        drop_graphs(ctx);  // lambda / A are kernel arguments
+    }
+    CK(cudaDeviceSynchronize());
+    return upload_tables(ctx, nullptr);
+}
+
+int spin_set_launch(spin_ctx *ctx, int32_t mode, int32_t use_graph, int32_t tile_rows, int32_t threads) {
+    if (!ctx) return SPIN_EINVAL;
+    if (mode < 0 || mode > 1) return fail(ctx, SPIN_EINVAL, "launch mode must be 0 (batched) or 1 (plain)");
+    if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
+        return fail(ctx, SPIN_EINVAL, "threads must be 128, 256 or 512");
+    if (tile_rows < 0) return fail(ctx, SPIN_EINVAL, "tile_rows must be >= 0");
+    ctx->mode = mode;
+    ctx->use_graph = use_graph ? 1 : 0;
+    if (tile_rows) ctx->tile_rows = tile_rows;
+    if (threads) ctx->threads = threads;
+    return plan(ctx);
+}
+
+int spin_get_launch(const spin_ctx *ctx, int32_t out[4]) {
+    if (!ctx || !out) return SPIN_EINVAL;
+    out[0] = ctx->mode;
+    out[1] = ctx->use_graph;
+    out[2] = ctx->tile_rows;
+    out[3] = ctx->threads;
+    return SPIN_OK;
+}
+
+int spin_load_spins(spin_ctx *ctx, const void *host, void *stream) {
+    if (!ctx || !host) return SPIN_EINVAL;
+    char *base = static_cast<char *>(ctx->spins);
+    if (ctx->model == SPIN_CPM) {
+        CK(cudaMemcpyAsync(base, host, (size_t)ctx->lat[0].L * ctx->lat[0].L * 4, cudaMemcpyHostToDevice, S(stream)));
+        return SPIN_OK;
+    }
+    CK(cudaMemcpyAsync(base, host, ctx->span_elems * ctx->elem, cudaMemcpyHostToDevice, S(stream)));
+    return SPIN_OK;
+}
+
+int spin_store_spins(spin_ctx *ctx, void *host, void *stream) {
+    if (!ctx || !host) return SPIN_EINVAL;
+    const size_t bytes = ctx->model == SPIN_CPM ? (size_t)ctx->lat[0].L * ctx->lat[0].L * 4
+                                                : ctx->span_elems * ctx->elem;
+    CK(cudaMemcpyAsync(host, ctx->spins, bytes, cudaMemcpyDeviceToHost, S(stream)));
+    return SPIN_OK;
+}
+
+// Blob: header | cur stats | spins span | CPM areas.
+struct CkptHeader {
+    uint64_t magic;
+    int32_t model, n_lat, width, pad;
+    uint32_t t;
+    int32_t pad2;
+    int64_t n_rec;
+    uint64_t spin_bytes, vol_bytes;
+};
+
+int spin_checkpoint(spin_ctx *ctx, void *host_blob, size_t *size, void *stream) {
+    if (!ctx || !size) return SPIN_EINVAL;
+    const size_t spin_bytes = ctx->model == SPIN_CPM ? (size_t)ctx->lat[0].L * ctx->lat[0].L * 4
+                                                     : ctx->span_elems * ctx->elem;
+    const size_t vol_bytes = ctx->model == SPIN_CPM ? sizeof(int32_t) * (ctx->n_cells + 1) : 0;
+    const size_t stat_bytes = sizeof(int64_t) * ctx->n_lat * ctx->width;
+    const size_t need = sizeof(CkptHeader) + stat_bytes + spin_bytes + vol_bytes;
+    if (!host_blob) {
+        *size = need;
+        return SPIN_OK;
+    }
+    if (*size < need) return fail(ctx, SPIN_EINVAL, "checkpoint buffer too small");
+    cudaStream_t s = S(stream);
+    CkptHeader h{0x53504E4D434B5031ull, ctx->model, ctx->n_lat, ctx->width, 0, ctx->t, 0, ctx->n_rec,
+                 spin_bytes, vol_bytes};
+    char *p = static_cast<char *>(host_blob);
+    std::memcpy(p, &h, sizeof h);
+    CK(cudaMemcpyAsync(p + sizeof h, ctx->st.cur, stat_bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(p + sizeof h + stat_bytes, ctx->spins, spin_bytes, cudaMemcpyDeviceToHost, s));
+    if (vol_bytes)
+        CK(cudaMemcpyAsync(p + sizeof h + stat_bytes + spin_bytes, ctx->d_vol[0], vol_bytes,
+                           cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *size = need;
+    return SPIN_OK;
+}
+
+int spin_restore(spin_ctx *ctx, const void *host_blob, size_t size, void *stream) {
+    if (!ctx || !host_blob || size < sizeof(CkptHeader)) return SPIN_EINVAL;
+    CkptHeader h;
+    std::memcpy(&h, host_blob, sizeof h);
+    const size_t stat_bytes = sizeof(int64_t) * ctx->n_lat * ctx->width;
+    if (h.magic != 0x53504E4D434B5031ull || h.model != ctx->model || h.n_lat != ctx->n_lat ||
+        h.width != ctx->width || size < sizeof h + stat_bytes + h.spin_bytes + h.vol_bytes)
+        return fail(ctx, SPIN_EINVAL, "checkpoint does not match this context");
+    cudaStream_t s = S(stream);
+    const char *p = static_cast<const char *>(host_blob);
+    CK(cudaMemcpyAsync(ctx->st.cur, p + sizeof h, stat_bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->spins, p + sizeof h + stat_bytes, h.spin_bytes, cudaMemcpyHostToDevice, s));
+    if (ctx->model != SPIN_CPM)
+        CK(cudaMemcpyAsync(ctx->spins2, ctx->spins, h.spin_bytes, cudaMemcpyDeviceToDevice, s));
+    if (h.vol_bytes) {
+        CK(cudaMemcpyAsync(ctx->d_vol[0], p + sizeof h + stat_bytes + h.spin_bytes, h.vol_bytes,
+                           cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->d_vol[1], ctx->d_vol[0], h.vol_bytes, cudaMemcpyDeviceToDevice, s));
+    }
+    DevState ds{h.t, 0, h.n_rec};
+    CK(cudaMemcpyAsync(ctx->d_state, &ds, sizeof ds, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->st.delta, 0, stat_bytes, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->t = h.t;
+    ctx->n_rec = h.n_rec;
+    return SPIN_OK;
+}
+
+int spin_autotune(spin_ctx *ctx, int32_t sweeps_per_trial, void *stream) {
+    if (!ctx) return SPIN_EINVAL;
+    if (ctx->model == SPIN_CPM) return SPIN_OK;
+    if (sweeps_per_trial < 2) sweeps_per_trial = 2;
+    const std::string key = shape_key(ctx);
+    const char *cache = std::getenv("SPINMC_TUNE_CACHE");
+    if (cache) {
+        std::ifstream f(cache);
+        std::string k;
+        int m, g, tr, th;
+        while (f >> k >> m >> g >> tr >> th)
+            if (k == key) return spin_set_launch(ctx, m, g, tr, th);
+    }
+    cudaStream_t s = S(stream);
+    // save the chain state; trials advance it
+    size_t blob = 0;
+    spin_checkpoint(ctx, nullptr, &blob, stream);
+    std::vector<char> saved(blob);
+    int rc = spin_checkpoint(ctx, saved.data(), &blob, stream);
+    if (rc) return rc;
+    struct Cand { int mode, tile, threads; };
+    std::vector<Cand> cands;
+    for (int th : {128, 256, 512})
+        for (int tr : {8, 16, 32, 64}) cands.push_back({0, tr, th});
+    cands.push_back({1, 0, 256});
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    Cand bc = {0, 16, 256};
+    for (const Cand &c : cands) {
+        rc = spin_set_launch(ctx, c.mode, 1, c.tile, c.threads);
+        if (rc) continue;
+        rc = spin_sweep(ctx, 2, 0, stream);  // warm-up, graph capture
+        if (rc) return rc;
+        CK(cudaEventRecord(e0, s));
+        rc = spin_sweep(ctx, sweeps_per_trial, 0, stream);
+        if (rc) return rc;
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            bc = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    rc = spin_set_launch(ctx, bc.mode, 1, bc.tile, bc.threads);
+    if (rc) return rc;
+    rc = spin_restore(ctx, saved.data(), saved.size(), stream);
+    if (rc) return rc;
+    if (cache) {
+        std::ofstream f(cache, std::ios::app);
+        f << key << " " << bc.mode << " " << 1 << " " << bc.tile << " " << bc.threads << "\n";
+    }
+    return SPIN_OK;
+}
+
+int spin_profile(spin_ctx *ctx, int32_t enable, int32_t max_launches) {
+    if (!ctx) return SPIN_EINVAL;
+    if (max_launches < 0) return fail(ctx, SPIN_EINVAL, "max_launches must be >= 0");
+    ctx->prof = enable != 0;
+    ctx->prof_n = 0;
+    if (ctx->prof) {
+        while ((int)ctx->prof_ev.size() < 2 * max_launches) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            ctx->prof_ev.push_back(e);
+        }
+    }
+    return SPIN_OK;
+}
+
+int spin_profile_read(spin_ctx *ctx, double *total_ms, int64_t *launches, void *stream) {
+    if (!ctx || !total_ms || !launches) return SPIN_EINVAL;
+    CK(cudaStreamSynchronize(S(stream)));
+    double sum = 0.0;
+    for (int i = 0; i < ctx->prof_n; ++i) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]));
+        sum += ms;
+    }
+    *total_ms = sum;
+    *launches = ctx->prof_n;
+    return SPIN_OK;
+}
+
+// ------------------------------------------------------------------ MLP
+int spin_mlp_param_count(void) { return mlp_param_count(); }
+
+int spin_mlp_forward(const float *params, const float *mu, const float *inv_sigma, const float *X,
+                     int32_t n, float *Y, void *stream) {
+    if (!params || !mu || !inv_sigma || !X || !Y || n < 0) return SPIN_EINVAL;
+    return launch_mlp_forward(params, mu, inv_sigma, X, n, Y, S(stream)) == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
+}
+
+int spin_mlp_backward(const float *params, const float *mu, const float *inv_sigma, const float *X,
+                      const float *T, int32_t n, float *grad, float *loss, float *dX, void *stream) {
+    if (!params || !mu || !inv_sigma || !X || !T || !grad || n <= 0) return SPIN_EINVAL;
+    return launch_mlp_backward(params, mu, inv_sigma, X, T, n, grad, loss, dX, S(stream)) == cudaSuccess
+               ? SPIN_OK
+               : SPIN_ECUDA;
+}
+
+int spin_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t step, float lr,
+                  float beta1, float beta2, float eps, void *stream) {
+    if (!params || !grad || !m || !v || step < 1) return SPIN_EINVAL;
+    return launch_mlp_adam(params, grad, m, v, step, lr, beta1, beta2, eps, S(stream)) == cudaSuccess
+               ? SPIN_OK
+               : SPIN_ECUDA;
+}
+
+}  // extern "C"

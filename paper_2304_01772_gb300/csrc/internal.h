@@ -1,0 +1,202 @@
+// internal.h -- device data layouts and kernel launch wrappers shared by the
+// CUDA translation units and the host side of libspinmc.so.  Not installed.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace spinmc {
+
+// One lattice as the kernels see it.
+struct LatDev {
+    uint64_t offset;  // element offset in the spin buffers
+    int32_t L;
+    int32_t q;        // Potts states (2 for Ising)
+    int32_t fast;     // 1: L % 16 == 0 and offset % 16 == 0 -> vectorised kernels
+    int32_t pad;
+};
+
+// One work item of the batched sweep: rows [r0, r0 + nrows) of lattice `lat`.
+// whole = 1: the item is the entire lattice (no halo, periodic in shared memory).
+struct Item {
+    int32_t lat;
+    int32_t r0;
+    int32_t nrows;
+    int32_t whole;
+};
+
+// Acceptance table entry: accept a draw u iff u <= thr; `delta` is the packed
+// change of the statistics on acceptance (Ising: dB * 65536 + dM; Potts: dB_eq).
+struct TabEntry {
+    uint32_t thr;
+    int32_t delta;
+};
+constexpr int kTabStride = 16;     // entries per lattice (Ising uses 10, Potts 9)
+
+// Device-side counters advanced by the finalize kernels (so that captured
+// graphs need no per-sweep parameters).
+struct DevState {
+    uint32_t t;        // sweep index of the next sweep
+    int32_t substep;   // CPM colour within the current step
+    int64_t n_rec;     // records written so far
+};
+
+// Counters of one sweep.  Ising: delta[l][0..1] = (dM, dB); Potts:
+// delta[l][0..q] = (dB_eq, dn_0..); CPM: delta[0][pair] = contact changes.
+struct StatsBufs {
+    int64_t *cur;      // [n_lat][width] statistics of the current state
+    int64_t *delta;    // [n_lat][width] accumulated changes of the running sweep
+    int64_t *ring;     // [cap][n_lat][width] records
+    int32_t cap;       // ring capacity (sweeps)
+    int32_t width;
+    int32_t n_lat;
+    int32_t pad;
+};
+
+#ifdef __CUDACC__
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, SC'11.  Multipliers 0xD2511F53 / 0xCD9E8D57,
+// Weyl key increments 0x9E3779B9 / 0xBB67AE85, ten rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo_a = 0xD2511F53u * c.x, hi_a = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo_b = 0xCD9E8D57u * c.z, hi_b = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+    }
+    return c;
+}
+#endif  // __CUDACC__
+
+// -------------------------------------------------------------- launch wrappers
+// All return cudaGetLastError() after the launch.
+struct IsingSweepArgs {
+    const Item *items;
+    int n_items;
+    const LatDev *lats;
+    const TabEntry *tabs;
+    const int8_t *src;
+    int8_t *dst;
+    uint32_t k0, k1;
+    const DevState *state;
+    int64_t *delta;   // [n_lat][2]
+};
+
+cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, size_t smem,
+                               cudaStream_t s);
+cudaError_t launch_ising_plain(int8_t *spins, const LatDev *lat_dev, int lat, int L,
+                               const TabEntry *tabs, uint32_t k0, uint32_t k1,
+                               const DevState *state, int64_t *delta, int colour, cudaStream_t s);
+// Lattices whose side is not a multiple of 16: two passes, src -> dst (colour 0,
+// other sites copied) and dst in place (colour 1).  lat_ids: device list.
+cudaError_t launch_ising_generic(const int8_t *src, int8_t *dst, const int32_t *lat_ids, int n,
+                                 int maxL, const LatDev *lats, const TabEntry *tabs, uint32_t k0,
+                                 uint32_t k1, const DevState *state, int64_t *delta, int colour,
+                                 cudaStream_t s);
+cudaError_t launch_ising_resident(int8_t *spins, const LatDev *lats, int n_lat, int maxL,
+                                  const TabEntry *tabs, uint32_t k0, uint32_t k1, DevState *state,
+                                  StatsBufs st, int n_sweeps, int record, int threads,
+                                  cudaStream_t s);
+cudaError_t launch_init_random(void *spins, int model, const LatDev *lats, int n_lat, int maxL,
+                               uint32_t k0, uint32_t k1, cudaStream_t s);
+
+struct PottsSweepArgs {
+    const Item *items;
+    int n_items;
+    const LatDev *lats;
+    const TabEntry *tabs;
+    const uint8_t *src;
+    uint8_t *dst;
+    uint32_t k0, k1;
+    const DevState *state;
+    int64_t *delta;   // [n_lat][width]
+    int width;
+};
+cudaError_t launch_potts_fused(const PottsSweepArgs &a, int grid, int threads, size_t smem,
+                               cudaStream_t s);
+cudaError_t launch_potts_plain(uint8_t *spins, const LatDev *lat_dev, int lat, int L, int q,
+                               const TabEntry *tabs, uint32_t k0, uint32_t k1,
+                               const DevState *state, int64_t *delta, int width, int colour,
+                               cudaStream_t s);
+cudaError_t launch_potts_generic(const uint8_t *src, uint8_t *dst, const int32_t *lat_ids, int n,
+                                 int maxL, const LatDev *lats, const TabEntry *tabs, uint32_t k0,
+                                 uint32_t k1, const DevState *state, int64_t *delta, int width,
+                                 int colour, cudaStream_t s);
+
+struct CpmArgs {
+    int32_t *ids;
+    int L;
+    uint32_t lat;
+    const uint8_t *type;     // [n_cells + 1]
+    const int32_t *J;        // [n_types][n_types]
+    int n_types;
+    int n_cells;             // ids outside [0, n_cells] are left alone
+    int lambda, target;
+    const int32_t *vol_cur;  // snapshot areas
+    int32_t *vol_next;       // areas after this sub-step (starts equal to vol_cur)
+    const uint32_t *thr;     // thr[dE] for dE in [0, n_thr); beyond: 0
+    int n_thr;
+    uint32_t k0, k1;
+    const DevState *state;
+    int64_t *delta;          // [pairs] contact changes
+};
+cudaError_t launch_cpm_substep(const CpmArgs &a, int colour, cudaStream_t s);
+// After a CPM colour sub-step: vol_cur = vol_next, contacts += delta; after
+// colour 3 also V2/V1, record, t += 1.
+cudaError_t launch_cpm_finalize(int32_t *vol_cur, const int32_t *vol_next, int n_cells,
+                                int target, DevState *state, StatsBufs st, int colour, int record,
+                                cudaStream_t s);
+cudaError_t launch_cpm_init_squares(int32_t *ids, int L, int n_cells, int side, int cols,
+                                    cudaStream_t s);
+cudaError_t launch_cpm_volumes(const int32_t *ids, int L, int32_t *vol, int n_cells,
+                               cudaStream_t s);
+
+// Statistics of the current state of every lattice -> out[n_lat][width].
+cudaError_t launch_stats_from_state(const void *spins, int model, const LatDev *lats, int n_lat,
+                                    int maxL, int width, const uint8_t *cpm_type, int cpm_ntypes,
+                                    const int32_t *cpm_vol, int cpm_ncells, int cpm_target,
+                                    int64_t *out, cudaStream_t s);
+// cur += delta, delta = 0, record (if record) into ring slot n_rec % cap, t += 1.
+cudaError_t launch_finalize(DevState *state, StatsBufs st, int record, cudaStream_t s);
+// Moments of records [first, first + n) -> out[n_lat][n_mom].
+cudaError_t launch_moments(const StatsBufs &st, int64_t first, int n, int64_t *out,
+                           cudaStream_t s);
+// E and M per site from records [first, first + n).
+struct ObsParams {
+    int model;
+    int n_lat;
+    int width;
+    const double *lat_params;  // [n_lat][4]: J, h, N, q
+    const double *cpm_J;       // [pairs]
+    double cpm_lambda;
+};
+cudaError_t launch_observables(const StatsBufs &st, int64_t first, int n, ObsParams p,
+                               int64_t *stats_out, float *E, float *M, cudaStream_t s);
+// Fluctuation-estimator finaliser from moments (FP64 on the device).
+struct GradParams {
+    int model;
+    int n_lat;
+    int width;
+    int observable;
+    int pool;
+    const double *lat_params;  // [n_lat][4]: J, h, N, beta
+    const double *cpm_J;       // [pairs]
+    double cpm_lambda, cpm_T;
+    int n_pairs;
+};
+cudaError_t launch_grad(const int64_t *moments, GradParams p, double *out, cudaStream_t s);
+
+// MLP
+int mlp_param_count();
+cudaError_t launch_mlp_forward(const float *params, const float *mu, const float *inv_sigma,
+                               const float *X, int n, float *Y, cudaStream_t s);
+cudaError_t launch_mlp_backward(const float *params, const float *mu, const float *inv_sigma,
+                                const float *X, const float *T, int n, float *grad, float *loss,
+                                float *dX, cudaStream_t s);
+cudaError_t launch_mlp_adam(float *params, const float *grad, float *m, float *v, int step,
+                            float lr, float b1, float b2, float eps, cudaStream_t s);
+
+}  // namespace spinmc

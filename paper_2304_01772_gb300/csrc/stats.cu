@@ -1,0 +1,385 @@
+// stats.cu -- observables and the fluctuation-estimator gradient.
+//
+// Per-sweep statistics are exact integers (Ising M, B; Potts B_eq, n_k; CPM
+// contact counts C_ab and area sums V2, V1).  The sweep kernels accumulate
+// their changes in `delta`; launch_finalize folds them into `cur` and writes
+// a record.  The adjoint reduction forms exact moments sum X_i and
+// sum X_i X_j in 128-bit integers; the finaliser turns them into
+// d<O>/dtheta = <dO/dtheta> - beta Cov(O, dH/dtheta) in FP64.
+#include "internal.h"
+
+namespace spinmc {
+
+namespace {
+
+__device__ __forceinline__ int pair_idx(int a, int b, int n) {
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo * n - lo * (lo - 1) / 2 + (hi - lo);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void atomic_add_i64(int64_t *p, long long v) {
+    if (v) atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+}
+
+// Ising / Potts statistics recomputed from the lattice (right and down bonds).
+__global__ void stats_state_kernel(const void *spins, int model, const LatDev *lats, int width,
+                                   int64_t *out) {
+    __shared__ int shist[256];
+    __shared__ long long r0[32], r1[32];
+    const int lat = blockIdx.y;
+    const LatDev ld = lats[lat];
+    const int L = ld.L;
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) shist[k] = 0;
+    __syncthreads();
+    long long a0 = 0, a1 = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L * L; i += gridDim.x * blockDim.x) {
+        const int y = i / L, x = i - y * L;
+        const int ir = y * L + (x == L - 1 ? 0 : x + 1);
+        const int id = (y == L - 1 ? 0 : y + 1) * L + x;
+        if (model == 0) {
+            const int8_t *S = static_cast<const int8_t *>(spins) + ld.offset;
+            const int s = S[i];
+            a0 += s;
+            a1 += s * (S[ir] + S[id]);
+        } else {
+            const uint8_t *S = static_cast<const uint8_t *>(spins) + ld.offset;
+            const int s = S[i];
+            a0 += (s == S[ir]) + (s == S[id]);
+            atomicAdd(shist + s, 1);
+        }
+    }
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    if ((threadIdx.x & 31) == 0) {
+        r0[threadIdx.x >> 5] = a0;
+        r1[threadIdx.x >> 5] = a1;
+    }
+    __syncthreads();
+    int64_t *o = out + (size_t)width * lat;
+    if (threadIdx.x == 0) {
+        long long s0 = 0, s1 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            s0 += r0[w];
+            s1 += r1[w];
+        }
+        if (model == 0) {
+            atomic_add_i64(o, s0);
+            atomic_add_i64(o + 1, s1);
+        } else {
+            atomic_add_i64(o, s0);
+        }
+    }
+    if (model == 1)
+        for (int k = threadIdx.x; k < ld.q && k + 1 < width; k += blockDim.x)
+            atomic_add_i64(o + 1 + k, shist[k]);
+}
+
+// CPM contacts (right, down-left, down, down-right: each unordered Moore pair once).
+__global__ void stats_cpm_kernel(const int32_t *ids, int L, const uint8_t *type, int nt,
+                                 const int32_t *vol, int n_cells, int target, int width,
+                                 int64_t *out) {
+    __shared__ int scnt[36];
+    __shared__ long long r2[32], r1[32];
+    for (int k = threadIdx.x; k < 36; k += blockDim.x) scnt[k] = 0;
+    __syncthreads();
+    const int hx[4] = {1, -1, 0, 1}, hy[4] = {0, 1, 1, 1};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L * L; i += gridDim.x * blockDim.x) {
+        const int y = i / L, x = i - y * L;
+        const int a = ids[i];
+        if ((unsigned)a > (unsigned)n_cells) continue;
+        for (int k = 0; k < 4; ++k) {
+            int yy = y + hy[k], xx = x + hx[k];
+            yy = yy >= L ? yy - L : yy;
+            xx = xx < 0 ? xx + L : (xx >= L ? xx - L : xx);
+            const int b = ids[yy * L + xx];
+            if ((unsigned)b > (unsigned)n_cells) continue;
+            if (a != b) atomicAdd(scnt + pair_idx(type[a], type[b], nt), 1);
+        }
+    }
+    long long v2 = 0, v1 = 0;
+    if (blockIdx.x == 0) {
+        for (int c = 1 + threadIdx.x; c <= n_cells; c += blockDim.x) {
+            const long long d = (long long)vol[c] - target;
+            v2 += d * d;
+            v1 += d;
+        }
+    }
+    v2 = warp_sum(v2);
+    v1 = warp_sum(v1);
+    if ((threadIdx.x & 31) == 0) {
+        r2[threadIdx.x >> 5] = v2;
+        r1[threadIdx.x >> 5] = v1;
+    }
+    __syncthreads();
+    const int npair = nt * (nt + 1) / 2;
+    for (int k = threadIdx.x; k < npair; k += blockDim.x) atomic_add_i64(out + k, scnt[k]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        long long a2 = 0, a1 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a2 += r2[w];
+            a1 += r1[w];
+        }
+        out[npair] = a2;
+        out[npair + 1] = a1;
+    }
+}
+
+__global__ void __launch_bounds__(1024) finalize_kernel(DevState *state, StatsBufs st, int record) {
+    const long long slot = (record && st.cap > 0) ? state->n_rec % st.cap : -1;
+    const int n = st.n_lat * st.width;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int64_t v = st.cur[k] + st.delta[k];
+        st.cur[k] = v;
+        st.delta[k] = 0;
+        if (slot >= 0) st.ring[slot * n + k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        state->t += 1;
+        if (record) state->n_rec += 1;
+    }
+}
+
+// Exact moments over records: one block per lattice, threads split the
+// records; out is __int128 [n_lat][n_mom] with n_mom = 1 + w + w(w+1)/2.
+__global__ void __launch_bounds__(256) moments_kernel(const int64_t *ring, int cap, int n_lat,
+                                                      int width, long long first, int n,
+                                                      __int128 *out) {
+    __shared__ __int128 part[8];
+    const int lat = blockIdx.x;
+    const int n_mom = 1 + width + width * (width + 1) / 2;
+    for (int k = 0; k < n_mom; ++k) {
+        int ia = -1, ib = -1;
+        if (k >= 1 && k <= width) {
+            ia = k - 1;
+        } else if (k > width) {
+            int r = k - 1 - width, a = 0;
+            while (r >= width - a) {
+                r -= width - a;
+                ++a;
+            }
+            ia = a;
+            ib = a + r;
+        }
+        __int128 acc = 0;
+        for (int s = threadIdx.x; s < n; s += blockDim.x) {
+            const long long rec = first + s;
+            const int64_t *row = ring + ((rec % cap) * n_lat + lat) * (long long)width;
+            if (k == 0)
+                acc += 1;
+            else if (ib < 0)
+                acc += (__int128)row[ia];
+            else
+                acc += (__int128)row[ia] * (__int128)row[ib];
+        }
+        // warp reduction of a 128-bit value as two 64-bit halves with carry
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long lo = (unsigned long long)acc;
+            const long long hi = (long long)(acc >> 64);
+            const unsigned long long olo = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+            const long long ohi = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+            acc += (((__int128)ohi) << 64) | (__int128)olo;
+        }
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __int128 t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+            out[(size_t)lat * n_mom + k] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// Sum of moment rows over lattices (pooled samples of chains sharing theta).
+__global__ void pool_moments_kernel(const __int128 *in, int n_lat, int n_mom, __int128 *out) {
+    for (int k = threadIdx.x; k < n_mom; k += blockDim.x) {
+        __int128 t = 0;
+        for (int l = 0; l < n_lat; ++l) t += in[(size_t)l * n_mom + k];
+        out[k] = t;
+    }
+}
+
+__device__ __forceinline__ double i128_to_double(__int128 v) {
+    const bool neg = v < 0;
+    unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    const double d = (double)(unsigned long long)(u >> 64) * 18446744073709551616.0 +
+                     (double)(unsigned long long)(u & 0xFFFFFFFFFFFFFFFFull);
+    return neg ? -d : d;
+}
+
+__global__ void observables_kernel(const int64_t *ring, int cap, long long first, int n,
+                                   ObsParams p, int64_t *stats_out, float *E, float *M) {
+    const int total = n * p.n_lat;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int s = idx / p.n_lat, lat = idx - s * p.n_lat;
+        const long long rec = first + s;
+        const int64_t *row = ring + ((rec % cap) * p.n_lat + lat) * (long long)p.width;
+        if (stats_out)
+            for (int k = 0; k < p.width; ++k) stats_out[(size_t)idx * p.width + k] = row[k];
+        const double J = p.lat_params[4 * lat], h = p.lat_params[4 * lat + 1];
+        const double N = p.lat_params[4 * lat + 2];
+        double e, m;
+        if (p.model == 0) {
+            e = (-J * (double)row[1] - h * (double)row[0]) / N;
+            m = (double)row[0] / N;
+        } else if (p.model == 1) {
+            const int q = (int)p.lat_params[4 * lat + 3];
+            long long mx = 0;
+            for (int k = 0; k < q; ++k) mx = row[1 + k] > mx ? row[1 + k] : mx;
+            e = -J * (double)row[0] / N;
+            m = ((double)q * (double)mx - N) / ((double)(q - 1) * N);
+        } else {
+            const int npair = p.width - 2;
+            double adh = 0.0;
+            for (int k = 0; k < npair; ++k) adh += p.cpm_J[k] * (double)row[k];
+            e = (adh + p.cpm_lambda * (double)row[npair]) / N;
+            m = adh / N;
+        }
+        if (E) E[idx] = (float)e;
+        if (M) M[idx] = (float)m;
+    }
+}
+
+// Covariance of X_i, X_j from exact moments: (n S_ij - S_i S_j) / n^2.
+__device__ double cov_ij(const __int128 *mo, int width, int i, int j) {
+    if (i > j) {
+        const int t = i;
+        i = j;
+        j = t;
+    }
+    const __int128 n = mo[0];
+    const __int128 Si = mo[1 + i], Sj = mo[1 + j];
+    // index of (i, j) in the upper triangle
+    const int tri = i * width - i * (i - 1) / 2 + (j - i);
+    const __int128 Sij = mo[1 + width + tri];
+    const __int128 num = n * Sij - Si * Sj;
+    const double nd = (double)(long long)n;
+    return i128_to_double(num) / (nd * nd);
+}
+
+// One thread per output row; rows are lattices (or one pooled row), lat0 gives
+// the parameters of each row.
+__global__ void grad_kernel(const __int128 *moments, int rows, GradParams p, double *out) {
+    const int width = p.width;
+    const int n_mom = 1 + width + width * (width + 1) / 2;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= rows) return;
+    const __int128 *mo = moments + (size_t)row * n_mom;
+    const int lat0 = p.pool ? 0 : row;
+    const double nd = (double)(long long)mo[0];
+    if (p.model == 0) {
+        const double J = p.lat_params[4 * lat0], h = p.lat_params[4 * lat0 + 1];
+        const double N = p.lat_params[4 * lat0 + 2], beta = p.lat_params[4 * lat0 + 3];
+        const double cMM = cov_ij(mo, 2, 0, 0), cMB = cov_ij(mo, 2, 0, 1), cBB = cov_ij(mo, 2, 1, 1);
+        const double meanM = i128_to_double(mo[1]) / nd, meanB = i128_to_double(mo[2]) / nd;
+        double gJ, gh;
+        if (p.observable == 0) {
+            // O = (-J B - h M)/N; dO/dJ = -B/N, dO/dh = -M/N; dH/dJ = -B, dH/dh = -M
+            const double cOB = (-J * cBB - h * cMB) / N, cOM = (-J * cMB - h * cMM) / N;
+            gJ = -meanB / N - beta * (-cOB);
+            gh = -meanM / N - beta * (-cOM);
+        } else {
+            const double cOB = cMB / N, cOM = cMM / N;
+            gJ = -beta * (-cOB);
+            gh = -beta * (-cOM);
+        }
+        out[2 * row] = gJ;
+        out[2 * row + 1] = gh;
+    } else {
+        const int npair = p.n_pairs;
+        const double N = p.lat_params[2], beta = 1.0 / p.cpm_T;
+        // Cov(O, X_k) with O = sum_a J_a C_a / N
+        for (int k = 0; k < npair + 2; ++k) {
+            double c = 0.0;
+            for (int a = 0; a < npair; ++a) c += p.cpm_J[a] * cov_ij(mo, width, a, k);
+            c /= N;
+            double g;
+            if (k < npair)
+                g = i128_to_double(mo[1 + k]) / nd / N - beta * c;   // d/dJ_ab
+            else if (k == npair)
+                g = -beta * c;                                        // d/dlambda
+            else
+                g = -beta * (-2.0 * p.cpm_lambda * c);                // d/dA
+            out[(size_t)row * (npair + 2) + k] = g;
+        }
+    }
+}
+
+__global__ void i128_to_i64_kernel(const __int128 *in, int64_t *out, int n, int *overflow) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const __int128 v = in[i];
+        if (v > (__int128)0x7FFFFFFFFFFFFFFFll || v < -(__int128)0x7FFFFFFFFFFFFFFFll) atomicExch(overflow, 1);
+        out[i] = (int64_t)v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_stats_from_state(const void *spins, int model, const LatDev *lats, int n_lat,
+                                    int maxL, int width, const uint8_t *cpm_type, int cpm_ntypes,
+                                    const int32_t *cpm_vol, int cpm_ncells, int cpm_target,
+                                    int64_t *out, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int64_t) * (size_t)n_lat * width, s);
+    if (e) return e;
+    if (model == 2) {
+        const int blocks = (maxL * maxL + 255) / 256;
+        stats_cpm_kernel<<<blocks < 512 ? blocks : 512, 256, 0, s>>>(
+            static_cast<const int32_t *>(spins), maxL, cpm_type, cpm_ntypes, cpm_vol, cpm_ncells,
+            cpm_target, width, out);
+    } else {
+        const int blocks = (maxL * maxL + 255) / 256;
+        dim3 grid(blocks < 128 ? blocks : 128, n_lat);
+        stats_state_kernel<<<grid, 256, 0, s>>>(spins, model, lats, width, out);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(DevState *state, StatsBufs st, int record, cudaStream_t s) {
+    finalize_kernel<<<1, 1024, 0, s>>>(state, st, record);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_i128(const StatsBufs &st, int64_t first, int n, void *out,
+                                cudaStream_t s) {
+    moments_kernel<<<st.n_lat, 256, 0, s>>>(st.ring, st.cap, st.n_lat, st.width, first, n,
+                                            static_cast<__int128 *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pool_moments(const void *in, int n_lat, int n_mom, void *out, cudaStream_t s) {
+    pool_moments_kernel<<<1, 256, 0, s>>>(static_cast<const __int128 *>(in), n_lat, n_mom,
+                                          static_cast<__int128 *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_i128_to_i64(const void *in, int64_t *out, int n, int *overflow, cudaStream_t s) {
+    i128_to_i64_kernel<<<(n + 255) / 256, 256, 0, s>>>(static_cast<const __int128 *>(in), out, n,
+                                                       overflow);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observables(const StatsBufs &st, int64_t first, int n, ObsParams p,
+                               int64_t *stats_out, float *E, float *M, cudaStream_t s) {
+    const int total = n * p.n_lat;
+    int blocks = (total + 255) / 256;
+    blocks = blocks < 1 ? 1 : (blocks > 1024 ? 1024 : blocks);
+    observables_kernel<<<blocks, 256, 0, s>>>(st.ring, st.cap, first, n, p, stats_out, E, M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_i128(const void *moments, int rows, GradParams p, double *out,
+                             cudaStream_t s) {
+    grad_kernel<<<(rows + 63) / 64, 64, 0, s>>>(static_cast<const __int128 *>(moments), rows, p, out);
+    return cudaGetLastError();
+}
+
+}  // namespace spinmc

@@ -1,0 +1,220 @@
+// sweep_cpm.cu -- cellular Potts copy attempts (Sec. "Cellular Potts model"
+// of Farias et al., arXiv 2304.01772; Hamiltonian Eq. "h": adhesion between
+// different cells over the Moore neighbourhood plus lambda (a - A)^2).
+//
+// Sites are coloured c = (x & 1) | ((y & 1) << 1): no two sites of one colour
+// are Moore neighbours, so all sites of a colour attempt their copy at once.
+// One thread handles the two sites of one Philox group (x = 4m + (c&1) and
+// x + 2 in row y).  Area terms read the areas as they stood at the start of
+// the sub-step (vol_cur); accepted copies add +-1 to vol_next atomically, and
+// the finalize kernel makes vol_cur = vol_next before the next sub-step.
+// Acceptance: integer dE, thr[dE] = max(floor(exp(-dE/T) 2^32), 1) - 1 built
+// on the host; dE beyond the table accepts only u = 0 (probability 2^-32).
+#include "internal.h"
+
+namespace spinmc {
+
+namespace {
+
+__constant__ int8_t kMooreDx[8] = {-1, 0, 1, -1, 1, -1, 0, 1};
+__constant__ int8_t kMooreDy[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
+
+__device__ __forceinline__ int pair_index(int a, int b, int n) {
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo * n - lo * (lo - 1) / 2 + (hi - lo);
+}
+
+__global__ void __launch_bounds__(256) cpm_substep_kernel(CpmArgs a, int c) {
+    __shared__ int sJ[64];
+    __shared__ int scnt[36];
+    const int nt = a.n_types;
+    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) sJ[k] = a.J[k];
+    for (int k = threadIdx.x; k < 36; k += blockDim.x) scnt[k] = 0;
+    __syncthreads();
+    const int L = a.L, Lq = L >> 2;
+    const uint32_t t = a.state->t;
+    const int cx = c & 1, cy = c >> 1;
+    const int n_groups = (L >> 1) * Lq;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_groups; g += gridDim.x * blockDim.x) {
+        const int yh = g / Lq, m = g - yh * Lq;
+        const int y = 2 * yh + cy;
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)g, a.lat, t, (uint32_t)c), a.k0, a.k1);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int x = 4 * m + cx + 2 * half;
+            const uint32_t u0 = half ? r.z : r.x;
+            const uint32_t u1 = half ? r.w : r.y;
+            const int nbi = (int)(u1 >> 29);
+            const int site = y * L + x;
+            const int sg = a.ids[site];
+            int yy = y + kMooreDy[nbi], xx = x + kMooreDx[nbi];
+            yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
+            xx = xx < 0 ? xx + L : (xx >= L ? xx - L : xx);
+            const int sp = a.ids[yy * L + xx];
+            if (sp == sg) continue;
+            if ((unsigned)sg > (unsigned)a.n_cells || (unsigned)sp > (unsigned)a.n_cells) continue;
+            const int tg = a.type[sg], tp = a.type[sp];
+            int nz[8];
+            long long dH = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                int zy = y + kMooreDy[k], zx = x + kMooreDx[k];
+                zy = zy < 0 ? zy + L : (zy >= L ? zy - L : zy);
+                zx = zx < 0 ? zx + L : (zx >= L ? zx - L : zx);
+                int sz = a.ids[zy * L + zx];
+                sz = (unsigned)sz > (unsigned)a.n_cells ? 0 : sz;   // out-of-range ids read as medium
+                nz[k] = sz;
+                const int tz = a.type[sz];
+                if (sz != sp) dH += sJ[tp * nt + tz];
+                if (sz != sg) dH -= sJ[tg * nt + tz];
+            }
+            if (sp != 0) dH += (long long)a.lambda * (2ll * ((long long)a.vol_cur[sp] - a.target) + 1);
+            if (sg != 0) dH += (long long)a.lambda * (-2ll * ((long long)a.vol_cur[sg] - a.target) + 1);
+            bool acc;
+            if (dH <= 0)
+                acc = true;
+            else
+                acc = u0 <= (dH < a.n_thr ? a.thr[dH] : 0u);
+            if (acc) {
+                a.ids[site] = sp;
+                atomicAdd(a.vol_next + sp, 1);
+                atomicAdd(a.vol_next + sg, -1);
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int sz = nz[k];
+                    const int tz = a.type[sz];
+                    if (sz != sg) atomicAdd(scnt + pair_index(tg, tz, nt), -1);
+                    if (sz != sp) atomicAdd(scnt + pair_index(tp, tz, nt), 1);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int npair = nt * (nt + 1) / 2;
+    for (int k = threadIdx.x; k < npair; k += blockDim.x)
+        if (scnt[k]) atomicAdd(reinterpret_cast<unsigned long long *>(a.delta + k), (unsigned long long)(long long)scnt[k]);
+}
+
+// After colour sub-step `colour`: vol_cur = vol_next, contacts += delta.
+// After colour 3: V2 / V1 from the areas, record, advance the step counter.
+__global__ void __launch_bounds__(1024) cpm_finalize_kernel(int32_t *vol_cur,
+                                                            const int32_t *vol_next, int n_cells,
+                                                            int target, DevState *state,
+                                                            StatsBufs st, int colour, int record) {
+    __shared__ long long r2[32], r1[32];
+    long long v2 = 0, v1 = 0;
+    for (int k = threadIdx.x; k <= n_cells; k += blockDim.x) {
+        const int v = vol_next[k];
+        vol_cur[k] = v;
+        if (k > 0) {
+            const long long d = (long long)v - target;
+            v2 += d * d;
+            v1 += d;
+        }
+    }
+    const int npair = st.width - 2;
+    for (int k = threadIdx.x; k < npair; k += blockDim.x) {
+        st.cur[k] += st.delta[k];
+        st.delta[k] = 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v2 += __shfl_xor_sync(0xFFFFFFFFu, v2, o);
+        v1 += __shfl_xor_sync(0xFFFFFFFFu, v1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        r2[threadIdx.x >> 5] = v2;
+        r1[threadIdx.x >> 5] = v1;
+    }
+    __syncthreads();
+    if (colour != 3) return;
+    if (threadIdx.x == 0) {
+        long long a2 = 0, a1 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a2 += r2[w];
+            a1 += r1[w];
+        }
+        st.cur[npair] = a2;
+        st.cur[npair + 1] = a1;
+    }
+    __syncthreads();
+    if (record && st.cap > 0) {
+        const long long slot = state->n_rec % st.cap;
+        for (int k = threadIdx.x; k < st.width; k += blockDim.x)
+            st.ring[slot * st.width + k] = st.cur[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        state->t += 1;
+        if (record) state->n_rec += 1;
+    }
+}
+
+__global__ void cpm_init_squares_kernel(int32_t *ids, int L, int n_cells, int side, int cols) {
+    const int rows = (n_cells + cols - 1) / cols;
+    const int x0 = (L - cols * side) / 2, y0 = (L - rows * side) / 2;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L * L; i += gridDim.x * blockDim.x) {
+        const int y = i / L - y0, x = i % L - x0;
+        int id = 0;
+        if (x >= 0 && y >= 0 && x < cols * side && y < rows * side) {
+            const int cidx = (y / side) * cols + (x / side);
+            if (cidx < n_cells) id = cidx + 1;
+        }
+        ids[i] = id;
+    }
+}
+
+__global__ void cpm_volumes_kernel(const int32_t *ids, int L, int32_t *vol, int n_cells) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L * L; i += gridDim.x * blockDim.x) {
+        const int id = ids[i];
+        if ((unsigned)id <= (unsigned)n_cells) atomicAdd(vol + id, 1);
+    }
+}
+
+__global__ void cpm_types_kernel(uint8_t *type, int n_cells, uint32_t lat, uint32_t k0, uint32_t k1) {
+    for (int cidx = blockIdx.x * blockDim.x + threadIdx.x; cidx <= n_cells; cidx += gridDim.x * blockDim.x) {
+        if (cidx == 0) {
+            type[0] = 0;
+            continue;
+        }
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)cidx, lat, 0xFFFFFFFEu, 0u), k0, k1);
+        type[cidx] = (uint8_t)(1u + (r.x >> 31));
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_cpm_substep(const CpmArgs &a, int colour, cudaStream_t s) {
+    const int n_groups = (a.L >> 1) * (a.L >> 2);
+    int blocks = (n_groups + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    cpm_substep_kernel<<<blocks, 256, 0, s>>>(a, colour);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cpm_finalize(int32_t *vol_cur, const int32_t *vol_next, int n_cells,
+                                int target, DevState *state, StatsBufs st, int colour, int record,
+                                cudaStream_t s) {
+    cpm_finalize_kernel<<<1, 1024, 0, s>>>(vol_cur, vol_next, n_cells, target, state, st, colour,
+                                           record);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cpm_init_squares(int32_t *ids, int L, int n_cells, int side, int cols,
+                                    cudaStream_t s) {
+    cpm_init_squares_kernel<<<256, 256, 0, s>>>(ids, L, n_cells, side, cols);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cpm_volumes(const int32_t *ids, int L, int32_t *vol, int n_cells, cudaStream_t s) {
+    cpm_volumes_kernel<<<256, 256, 0, s>>>(ids, L, vol, n_cells);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cpm_types(uint8_t *type, int n_cells, uint32_t lat, uint32_t k0, uint32_t k1,
+                             cudaStream_t s) {
+    cpm_types_kernel<<<(n_cells + 256) / 256, 256, 0, s>>>(type, n_cells, lat, k0, k1);
+    return cudaGetLastError();
+}
+
+}  // namespace spinmc

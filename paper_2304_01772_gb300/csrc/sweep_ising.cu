@@ -1,0 +1,353 @@
+// sweep_ising.cu -- checkerboard Metropolis sweeps of batched 2D Ising lattices
+// (Alg. 1 of Farias et al., arXiv 2304.01772, with the 4-neighbour stencil of
+// Sec. "Ising model"), plus the random initial state.
+//
+// Spins are int8 +-1 (0x01 / 0xFF).  Bit 1 of a byte is set iff the spin is
+// -1, so (word & 0x02020202) gives twice the "down" indicator of four sites at
+// once, and four such words add without carries (at most 8 per byte).  The
+// per-site table key is d + 5 c (d = down neighbours, c = own spin down),
+// formed for four sites in one 32-bit word; each byte of
+//     key4 = 4 * (N2 + 5 * c2)    (N2 = 2 d, c2 = 2 c)
+// is directly the byte offset of the 8-byte table entry.
+//
+// Kernels:
+//  * ising_fused_kernel: one launch per sweep over a work list of items
+//    (whole small lattices, or row blocks of large ones).  Each item loads its
+//    rows plus a two-row halo into shared memory, updates colour 0 on the rows
+//    and the inner halo ring (recomputed: the draws depend only on the site),
+//    then colour 1 on its own rows, and writes the rows to the other buffer.
+//  * ising_plain_kernel: one lattice, one colour, in place (two launches per
+//    lattice per sweep: the plain launch form the batched one is compared to).
+//  * ising_generic_kernel: any even L (not a multiple of 16), one thread per site.
+#include "internal.h"
+
+namespace spinmc {
+
+namespace {
+
+constexpr uint32_t kDownMask = 0x02020202u;
+
+// Update the colour-`c` sites of one 16-byte row chunk.  C: the chunk; U, D: the
+// chunks above and below; lw / rw: the 32-bit words left and right of C in
+// the same row.  Philox groups g0 (bytes 0..7) and g0 + 1 (bytes 8..15); active
+// bytes of each word are p and p + 2.
+__device__ __forceinline__ uint4 ising_chunk(uint4 C, uint4 U, uint4 D, uint32_t lw, uint32_t rw,
+                                             uint32_t g0, int p, uint32_t lat, uint32_t t,
+                                             uint32_t c, uint32_t k0, uint32_t k1,
+                                             const TabEntry *stab, bool count, int &acc) {
+    const uint4 ra = philox4x32_10(make_uint4(g0, lat, t, c), k0, k1);
+    const uint4 rb = philox4x32_10(make_uint4(g0 + 1u, lat, t, c), k0, k1);
+    const uint32_t w[6] = {lw, C.x, C.y, C.z, C.w, rw};
+    const uint32_t up[4] = {U.x, U.y, U.z, U.w};
+    const uint32_t dn[4] = {D.x, D.y, D.z, D.w};
+    const uint32_t rnd[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+    uint32_t out[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t W = w[i + 1];
+        const uint32_t lf = __funnelshift_l(w[i], W, 8);      // left neighbours
+        const uint32_t rt = __funnelshift_r(W, w[i + 2], 8);  // right neighbours
+        const uint32_t n2 = (up[i] & kDownMask) + (dn[i] & kDownMask) + (lf & kDownMask) +
+                            (rt & kDownMask);
+        const uint32_t key4 = (n2 + (W & kDownMask) * 5u) << 2;
+        uint32_t nw = W;
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb) {
+            const int sh = 8 * (p + 2 * bb);
+            const uint32_t off = (key4 >> sh) & 0xFFu;
+            const TabEntry e =
+                *reinterpret_cast<const TabEntry *>(reinterpret_cast<const char *>(stab) + off);
+            if (rnd[2 * i + bb] <= e.thr) {
+                nw ^= 0xFEu << sh;
+                if (count) acc += e.delta;
+            }
+        }
+        out[i] = nw;
+    }
+    return make_uint4(out[0], out[1], out[2], out[3]);
+}
+
+// Packed (dB * 65536 + dM) per-thread sums -> block sums -> one atomic pair.
+template <int THREADS>
+__device__ __forceinline__ void flush_ising_acc(int acc, int64_t *delta_lat, int *red) {
+    int dm = (int)(int16_t)(acc & 0xFFFF);
+    int db = (acc - dm) >> 16;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dm += __shfl_xor_sync(0xFFFFFFFFu, dm, o);
+        db += __shfl_xor_sync(0xFFFFFFFFu, db, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[2 * warp] = dm;
+        red[2 * warp + 1] = db;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long sm = 0, sb = 0;
+        for (int k = 0; k < THREADS / 32; ++k) {
+            sm += red[2 * k];
+            sb += red[2 * k + 1];
+        }
+        if (sm) atomicAdd(reinterpret_cast<unsigned long long *>(delta_lat), (unsigned long long)sm);
+        if (sb)
+            atomicAdd(reinterpret_cast<unsigned long long *>(delta_lat + 1), (unsigned long long)sb);
+    }
+}
+
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) ising_fused_kernel(IsingSweepArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ TabEntry stab[kTabStride];
+    __shared__ int red[2 * (THREADS / 32)];
+    uint4 *sm4 = reinterpret_cast<uint4 *>(sm);
+    const uint32_t *sm32 = reinterpret_cast<const uint32_t *>(sm);
+    const uint32_t t = a.state->t;
+    for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+        const Item w = a.items[it];
+        const LatDev ld = a.lats[w.lat];
+        const int L = ld.L, Lv = L >> 4;
+        const int halo = w.whole ? 0 : 2;
+        const int nload = w.nrows + 2 * halo;
+        const uint4 *S = reinterpret_cast<const uint4 *>(a.src + ld.offset);
+        uint4 *Dg = reinterpret_cast<uint4 *>(a.dst + ld.offset);
+        for (int v = threadIdx.x; v < nload * Lv; v += THREADS) {
+            const int i = v / Lv, j = v - i * Lv;
+            int gy = w.r0 - halo + i;
+            gy = gy < 0 ? gy + L : (gy >= L ? gy - L : gy);
+            sm4[v] = __ldg(S + (size_t)gy * Lv + j);
+        }
+        if (threadIdx.x < kTabStride) stab[threadIdx.x] = a.tabs[w.lat * kTabStride + threadIdx.x];
+        __syncthreads();
+        int acc = 0;
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+            // colour 0 also on the inner halo ring (smem rows 1 and nrows + 2)
+            const int lo = w.whole ? 0 : (c == 0 ? 1 : 2);
+            const int hi = w.whole ? w.nrows : (c == 0 ? w.nrows + 3 : w.nrows + 2);
+            const int n_units = (hi - lo) * Lv;
+            for (int v = threadIdx.x; v < n_units; v += THREADS) {
+                const int i = lo + v / Lv, j = v % Lv;
+                const int iu = (i == 0) ? nload - 1 : i - 1;
+                const int id = (i == nload - 1) ? 0 : i + 1;
+                int gy = w.r0 - halo + i;
+                gy = gy < 0 ? gy + L : (gy >= L ? gy - L : gy);
+                const uint4 Cc = sm4[i * Lv + j];
+                const uint4 Uc = sm4[iu * Lv + j];
+                const uint4 Dc = sm4[id * Lv + j];
+                const uint32_t lw = sm32[(i * Lv + (j == 0 ? Lv - 1 : j - 1)) * 4 + 3];
+                const uint32_t rw = sm32[(i * Lv + (j == Lv - 1 ? 0 : j + 1)) * 4];
+                const bool count = (i >= halo) && (i < halo + w.nrows);
+                const uint32_t g0 = (uint32_t)gy * (uint32_t)(L >> 3) + 2u * (uint32_t)j;
+                sm4[i * Lv + j] = ising_chunk(Cc, Uc, Dc, lw, rw, g0, (c ^ gy) & 1, (uint32_t)w.lat,
+                                              t, (uint32_t)c, a.k0, a.k1, stab, count, acc);
+            }
+            __syncthreads();
+        }
+        for (int v = threadIdx.x; v < w.nrows * Lv; v += THREADS) {
+            const int i = v / Lv, j = v - i * Lv;
+            Dg[(size_t)(w.r0 + i) * Lv + j] = sm4[(halo + i) * Lv + j];
+        }
+        flush_ising_acc<THREADS>(acc, a.delta + 2 * w.lat, red);
+        __syncthreads();
+    }
+}
+
+// One lattice, one colour, in place, straight from global memory.
+__global__ void __launch_bounds__(256) ising_plain_kernel(int8_t *spins, int L, uint32_t lat,
+                                                          const TabEntry *tab, uint32_t k0,
+                                                          uint32_t k1, const DevState *state,
+                                                          int64_t *delta, int c) {
+    __shared__ TabEntry stab[kTabStride];
+    __shared__ int red[16];
+    if (threadIdx.x < kTabStride) stab[threadIdx.x] = tab[threadIdx.x];
+    __syncthreads();
+    const uint32_t t = state->t;
+    const int Lv = L >> 4;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    int acc = 0;
+    if (v < L * Lv) {
+        uint4 *S = reinterpret_cast<uint4 *>(spins);
+        const uint32_t *S32 = reinterpret_cast<const uint32_t *>(spins);
+        const int i = v / Lv, j = v - i * Lv;
+        const int iu = i == 0 ? L - 1 : i - 1, id = i == L - 1 ? 0 : i + 1;
+        const uint4 Cc = S[(size_t)i * Lv + j];
+        const uint4 Uc = S[(size_t)iu * Lv + j];
+        const uint4 Dc = S[(size_t)id * Lv + j];
+        const uint32_t lw = S32[((size_t)i * Lv + (j == 0 ? Lv - 1 : j - 1)) * 4 + 3];
+        const uint32_t rw = S32[((size_t)i * Lv + (j == Lv - 1 ? 0 : j + 1)) * 4];
+        const uint32_t g0 = (uint32_t)i * (uint32_t)(L >> 3) + 2u * (uint32_t)j;
+        S[(size_t)i * Lv + j] =
+            ising_chunk(Cc, Uc, Dc, lw, rw, g0, (c ^ i) & 1, lat, t, (uint32_t)c, k0, k1, stab,
+                        true, acc);
+    }
+    flush_ising_acc<256>(acc, delta + 2 * lat, red);
+}
+
+// Any even L: one thread per site.  colour 0 pass reads src and writes every
+// site of dst (colour-1 sites copied); colour 1 pass updates dst in place.
+__global__ void ising_generic_kernel(const int8_t *src, int8_t *dst, const int32_t *lat_ids,
+                                     const LatDev *lats, const TabEntry *tabs, uint32_t k0,
+                                     uint32_t k1, const DevState *state, int64_t *delta, int c) {
+    __shared__ int red[2 * 8];
+    const int lat = lat_ids[blockIdx.y];
+    const LatDev ld = lats[lat];
+    const int L = ld.L;
+    const int8_t *S = (c == 0 ? src : dst) + ld.offset;
+    int8_t *D = dst + ld.offset;
+    const uint32_t t = state->t;
+    int dm = 0, db = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L * L; i += gridDim.x * blockDim.x) {
+        const int y = i / L, x = i - y * L;
+        const int s = S[i];
+        if (((x + y) & 1) != c) {
+            if (c == 0) D[i] = (int8_t)s;
+            continue;
+        }
+        const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
+        const int xl = x == 0 ? L - 1 : x - 1, xr = x == L - 1 ? 0 : x + 1;
+        // down neighbours counted from the sign, so any byte value keeps the index in range
+        const int dcount = (S[yu * L + x] < 0) + (S[yd * L + x] < 0) + (S[y * L + xl] < 0) +
+                           (S[y * L + xr] < 0);
+        const int n = 4 - 2 * dcount;
+        const int cdown = s < 0 ? 1 : 0;
+        const TabEntry e = tabs[lat * kTabStride + dcount + 5 * cdown];
+        const uint32_t k = (uint32_t)i >> 1;
+        const uint4 r = philox4x32_10(make_uint4(k >> 2, (uint32_t)lat, t, (uint32_t)c), k0, k1);
+        const uint32_t lane = k & 3u;
+        const uint32_t u = lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
+        if (u <= e.thr) {
+            D[i] = (int8_t)(-s);
+            dm += -2 * s;
+            db += -2 * s * n;
+        } else if (c == 0) {
+            D[i] = (int8_t)s;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dm += __shfl_xor_sync(0xFFFFFFFFu, dm, o);
+        db += __shfl_xor_sync(0xFFFFFFFFu, db, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[2 * (threadIdx.x >> 5)] = dm;
+        red[2 * (threadIdx.x >> 5) + 1] = db;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long sm = 0, sb = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            sm += red[2 * k];
+            sb += red[2 * k + 1];
+        }
+        if (sm) atomicAdd(reinterpret_cast<unsigned long long *>(delta + 2 * lat), (unsigned long long)sm);
+        if (sb) atomicAdd(reinterpret_cast<unsigned long long *>(delta + 2 * lat + 1), (unsigned long long)sb);
+    }
+}
+
+// Random initial state: one Philox call per group of four consecutive sites.
+__global__ void init_random_kernel(void *spins, int model, const LatDev *lats, uint32_t k0,
+                                   uint32_t k1) {
+    const LatDev ld = lats[blockIdx.y];
+    const int groups = (ld.L * ld.L) >> 2;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x) {
+        const uint4 r =
+            philox4x32_10(make_uint4((uint32_t)g, blockIdx.y, 0xFFFFFFFFu, 0u), k0, k1);
+        const uint32_t u[4] = {r.x, r.y, r.z, r.w};
+        if (model == 0) {
+            int8_t *S = static_cast<int8_t *>(spins) + ld.offset + 4 * (size_t)g;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) S[l] = (u[l] >> 31) ? (int8_t)1 : (int8_t)-1;
+        } else {
+            uint8_t *S = static_cast<uint8_t *>(spins) + ld.offset + 4 * (size_t)g;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) S[l] = (uint8_t)__umulhi(u[l], (uint32_t)ld.q);
+        }
+    }
+}
+
+// Copy every lattice (L*L elements of `elem` bytes at its offset) src -> dst.
+__global__ void copy_lattices_kernel(const unsigned char *src, unsigned char *dst,
+                                     const LatDev *lats, int elem) {
+    const LatDev ld = lats[blockIdx.y];
+    const size_t base = ld.offset * (size_t)elem;
+    const size_t bytes = (size_t)ld.L * ld.L * elem;
+    if (((base | bytes) & 15) == 0) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src + base);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst + base);
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < bytes / 16;
+             i += (size_t)gridDim.x * blockDim.x)
+            d4[i] = s4[i];
+    } else {
+        for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < bytes;
+             i += (size_t)gridDim.x * blockDim.x)
+            dst[base + i] = src[base + i];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_copy_lattices(const void *src, void *dst, const LatDev *lats, int n_lat,
+                                 int elem, cudaStream_t s) {
+    dim3 grid(64, n_lat);
+    copy_lattices_kernel<<<grid, 256, 0, s>>>(static_cast<const unsigned char *>(src),
+                                              static_cast<unsigned char *>(dst), lats, elem);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, size_t smem,
+                               cudaStream_t s) {
+    switch (threads) {
+        case 128:
+            ising_fused_kernel<128><<<grid, 128, smem, s>>>(a);
+            break;
+        case 256:
+            ising_fused_kernel<256><<<grid, 256, smem, s>>>(a);
+            break;
+        case 512:
+            ising_fused_kernel<512><<<grid, 512, smem, s>>>(a);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t set_ising_fused_smem(size_t smem) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(ising_fused_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    if ((e = cudaFuncSetAttribute(ising_fused_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+    return cudaFuncSetAttribute(ising_fused_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+cudaError_t launch_ising_plain(int8_t *spins, const LatDev *, int lat, int L, const TabEntry *tabs,
+                               uint32_t k0, uint32_t k1, const DevState *state, int64_t *delta,
+                               int colour, cudaStream_t s) {
+    const int units = L * (L >> 4);
+    ising_plain_kernel<<<(units + 255) / 256, 256, 0, s>>>(
+        spins, L, (uint32_t)lat, tabs + lat * kTabStride, k0, k1, state, delta, colour);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ising_generic(const int8_t *src, int8_t *dst, const int32_t *lat_ids, int n,
+                                 int maxL, const LatDev *lats, const TabEntry *tabs, uint32_t k0,
+                                 uint32_t k1, const DevState *state, int64_t *delta, int colour,
+                                 cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int blocks = (maxL * maxL + 255) / 256;
+    dim3 grid(blocks < 64 ? blocks : 64, n);
+    ising_generic_kernel<<<grid, 256, 0, s>>>(src, dst, lat_ids, lats, tabs, k0, k1, state, delta,
+                                              colour);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_random(void *spins, int model, const LatDev *lats, int n_lat, int maxL,
+                               uint32_t k0, uint32_t k1, cudaStream_t s) {
+    const int groups = (maxL * maxL) >> 2;
+    const int bx = (groups + 255) / 256;
+    dim3 grid(bx < 256 ? bx : 256, n_lat);
+    init_random_kernel<<<grid, 256, 0, s>>>(spins, model, lats, k0, k1);
+    return cudaGetLastError();
+}
+
+}  // namespace spinmc

@@ -1,0 +1,81 @@
+"""CPU-side checks of the C ABI: the library loads, exports every symbol the
+header declares, and rejects invalid arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2304_01772_gb300 as sm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "spinmc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(spin_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = sm.lib()
+    names = declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert lib.spin_version() == 1
+    assert lib.spin_mlp_param_count() == 3 * 64 + 64 + 64 * 64 + 64 + 2 * 64 + 2
+
+
+def test_binding_covers_the_abi():
+    assert set(declared_symbols()) == set(sm._SIGS)
+
+
+def _init(model, descs, cpm=None):
+    arr = (sm.LatticeDesc * len(descs))(*descs)
+    ctx = ctypes.c_void_p()
+    rc = sm.lib().spin_init(ctypes.byref(ctx), model, 0, len(descs), arr,
+                            ctypes.byref(cpm) if cpm else None, ctypes.c_void_p(16), 0, 0, None)
+    return rc, ctx
+
+
+@pytest.mark.parametrize("desc,model", [
+    (sm.LatticeDesc(63, 2, 0.4, 1.0, 0.0, 0, 0), sm.SPIN_ISING),          # odd L
+    (sm.LatticeDesc(2, 2, 0.4, 1.0, 0.0, 0, 0), sm.SPIN_ISING),           # too small
+    (sm.LatticeDesc(64, 2, float("nan"), 1.0, 0.0, 0, 0), sm.SPIN_ISING),  # NaN beta
+    (sm.LatticeDesc(64, 2, -0.1, 1.0, 0.0, 0, 0), sm.SPIN_ISING),         # negative beta
+    (sm.LatticeDesc(64, 1, 0.4, 1.0, 0.0, 0, 0), sm.SPIN_POTTS),          # q < 2
+    (sm.LatticeDesc(64, 256, 0.4, 1.0, 0.0, 0, 0), sm.SPIN_POTTS),        # q > 255
+    (sm.LatticeDesc(64, 3, 0.4, 1.0, 0.1, 0, 0), sm.SPIN_POTTS),          # Potts with a field
+    (sm.LatticeDesc(64, 2, 0.4, 1.0, 0.0, 1, 0), sm.SPIN_ISING),          # reserved != 0
+])
+def test_invalid_lattices_rejected(desc, model):
+    rc, ctx = _init(model, [desc])
+    assert rc == -1 and not ctx.value
+
+
+def test_overlapping_lattices_rejected():
+    rc, _ = _init(sm.SPIN_ISING, [sm.LatticeDesc(16, 2, 0.4, 1.0, 0.0, 0, 0),
+                                  sm.LatticeDesc(16, 2, 0.4, 1.0, 0.0, 0, 100)])
+    assert rc == -1
+
+
+def test_cpm_parameter_checks():
+    J = (ctypes.c_int32 * 9)(0, 16, 16, 16, 2, 11, 16, 12, 14)   # not symmetric
+    cp = sm.CpmParams(3, 1, 400, 10, J, None, 10.0, 4, 5, 0)
+    rc, _ = _init(sm.SPIN_CPM, [sm.LatticeDesc(64, 2, 0.0, 0.0, 0.0, 0, 0)], cp)
+    assert rc == -1
+    Jok = (ctypes.c_int32 * 9)(0, 16, 16, 16, 2, 11, 16, 11, 14)
+    cp = sm.CpmParams(3, 1, 400, 10, Jok, None, 10.0, 4, 5, 0)
+    rc, _ = _init(sm.SPIN_CPM, [sm.LatticeDesc(66, 2, 0.0, 0.0, 0.0, 0, 0)], cp)   # L % 4 != 0
+    assert rc == -1
+    rc, _ = _init(sm.SPIN_ISING, [sm.LatticeDesc(64, 2, 0.4, 1.0, 0.0, 0, 0)], cp)  # cpm for Ising
+    assert rc == -1
+
+
+def test_pack_offsets_alignment():
+    off, total = sm.pack_offsets([32, 10, 2048, 4], elem=1, align=256)
+    assert all(o % 256 == 0 for o in off)
+    assert total == off[-1] + 16
+    off4, _ = sm.pack_offsets([8, 8], elem=4, align=256)
+    assert off4 == [0, 64]

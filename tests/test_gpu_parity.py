@@ -1,0 +1,281 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Spin configurations must match bit for bit after every sweep, integer
+statistics exactly, and FP32 observables to within 1e-6 relative (they are
+formed in double from the same integers and rounded once, so in practice
+they are equal).  Lattices are independent, so full-size batches are checked
+by running the oracle on a sample of their lattices.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2304_01772_gb300 as sm
+from paper_2304_01772_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x5EED1234ABCD
+
+
+def lattice_np(sim, i):
+    return sim.lattice(i).cpu().numpy().copy()
+
+
+def oracle_ising_chain(lats, seed, init, t0, n, idx=None):
+    """Run the oracle on lattices `idx` (their batch indices) from `init`."""
+    idx = range(len(lats)) if idx is None else idx
+    out, stats = {}, {}
+    for i in idx:
+        d = lats[i]
+        s = init[i].copy()
+        stats[i] = oracle.ising_run(s, d["beta"], d["J"], d["h"], seed, i, t0, n)
+        out[i] = s
+    return out, stats
+
+
+def make_ising(lats, seed=SEED, max_record=64, **kw):
+    return sm.Sim(sm.SPIN_ISING, lats, seed=seed, max_record=max_record, **kw)
+
+
+MIXED = [dict(L=L, beta=b, J=J, h=h) for L, b, J, h in [
+    (4, 0.3, 1.0, 0.0), (6, 0.5, -1.0, 0.1), (10, 0.44, 1.0, -0.2), (16, 0.2, 1.0, 0.05),
+    (32, 0.6, 1.0, 0.0), (48, 0.44, 0.7, 0.3), (64, 0.35, 1.0, -0.05), (128, 0.44, 1.0, 0.0),
+    (144, 0.5, 1.0, 0.02), (256, 0.41, 1.0, 0.0), (12, 0.0, 1.0, 0.0), (96, 3.0, 1.0, 0.0)]]
+
+
+def test_init_matches_oracle():
+    sim = make_ising(MIXED)
+    for i, d in enumerate(MIXED):
+        assert np.array_equal(lattice_np(sim, i), oracle.init_ising(d["L"], SEED, i))
+    st = sim.current_stats().cpu().numpy()
+    for i in range(len(MIXED)):
+        assert list(st[i]) == list(oracle.ising_stats(lattice_np(sim, i)))
+
+
+@pytest.mark.parametrize("mode,graph,tile,threads", [(0, False, 0, 256), (0, True, 0, 256),
+                                                     (0, True, 8, 128), (0, False, 64, 512),
+                                                     (1, False, 0, 256), (1, True, 0, 256)])
+def test_ising_mixed_batch_sweep_by_sweep(mode, graph, tile, threads):
+    sim = make_ising(MIXED)
+    sim.set_launch(mode, graph, tile, threads)
+    init = {i: lattice_np(sim, i) for i in range(len(MIXED))}
+    ref = {i: init[i].copy() for i in init}
+    for t in range(4):
+        sim.sweep(1, record=True)
+        for i, d in enumerate(MIXED):
+            oracle.ising_sweep(ref[i], d["beta"], d["J"], d["h"], SEED, i, t)
+            assert np.array_equal(lattice_np(sim, i), ref[i]), (t, i, d)
+    # longer stretch in one call (graph replay + odd remainder), then compare
+    sim.sweep(7, record=True)
+    got_st, E, M = sim.observables_host(0, 11)
+    for i, d in enumerate(MIXED):
+        st = oracle.ising_run(ref[i], d["beta"], d["J"], d["h"], SEED, i, 4, 7)
+        assert np.array_equal(lattice_np(sim, i), ref[i])
+        assert np.array_equal(got_st[4:, i, :], st)
+        N = d["L"] ** 2
+        Eo = (-float(np.float32(d["J"])) * st[:, 1] - float(np.float32(d["h"])) * st[:, 0]) / N
+        np.testing.assert_allclose(E[4:, i], Eo.astype(np.float32), rtol=1e-6, atol=1e-7)
+        np.testing.assert_allclose(M[4:, i], (st[:, 0] / N).astype(np.float32), rtol=1e-6, atol=1e-7)
+    assert sim.t == 11 and sim.n_records == 11
+
+
+def test_launch_forms_bit_identical():
+    lats = wl.uneven512(n=40, seed=3, emin=4, emax=9)
+    finals = []
+    for mode, graph, tile, threads in [(0, True, 0, 256), (0, False, 16, 128), (1, True, 0, 256),
+                                       (0, True, 64, 512)]:
+        sim = make_ising(lats, max_record=16)
+        sim.set_launch(mode, graph, tile, threads)
+        sim.sweep(9, record=True)
+        st, E, M = sim.observables(0, 9)
+        finals.append((sim.spins.cpu().numpy(), st.cpu().numpy()))
+        sim.close()
+    for s, st in finals[1:]:
+        assert np.array_equal(s, finals[0][0])
+        assert np.array_equal(st, finals[0][1])
+
+
+def test_checkpoint_resume_bit_identical():
+    lats = wl.uneven512(n=12, seed=5, emin=4, emax=8)
+    a = make_ising(lats)
+    a.sweep(5)
+    blob = a.checkpoint()
+    a.sweep(6, record=True)
+    b = make_ising(lats, seed=SEED)
+    b.restore(blob)
+    assert b.t == 5
+    b.sweep(6, record=True)
+    assert torch.equal(a.spins, b.spins)
+    assert np.array_equal(a.observables_host()[0], b.observables_host()[0])
+
+
+def test_ising_extremes_beta_zero_and_large():
+    lats = [dict(L=32, beta=0.0, J=1.0, h=0.0), dict(L=32, beta=50.0, J=1.0, h=0.0)]
+    sim = make_ising(lats)
+    init = [lattice_np(sim, i) for i in range(2)]
+    sim.sweep(1)
+    # beta = 0: every proposal accepted -> every spin flipped once
+    assert np.array_equal(lattice_np(sim, 0), -init[0])
+    ref = init[1].copy()
+    oracle.ising_sweep(ref, 50.0, 1.0, 0.0, SEED, 1, 0)
+    assert np.array_equal(lattice_np(sim, 1), ref)
+
+
+def test_stats_bookkeeping_matches_recount_large():
+    """Recorded statistics (accumulated from accepted flips) equal a recount
+    of the final state -- a property that holds at any size."""
+    lats = wl.uneven512(n=64, seed=9)
+    sim = make_ising(lats)
+    sim.sweep(5, record=True)
+    st, _, _ = sim.observables(4, 1)
+    assert torch.equal(st[0], sim.current_stats())
+
+
+# --------------------------------------------------------------------- Potts
+POTTS = [dict(L=L, q=q, beta=b, J=J) for L, q, b, J in [
+    (16, 2, 0.8, 1.0), (32, 3, 1.0, 1.0), (64, 8, 1.2, 1.0), (10, 3, 1.0, 1.0), (48, 5, 0.9, -1.0),
+    (128, 3, 1.005, 1.0), (256, 8, 1.2, 1.0), (32, 20, 2.0, 1.0), (8, 255, 1.0, 1.0)]]
+
+
+@pytest.mark.parametrize("mode,graph", [(0, True), (0, False), (1, True)])
+def test_potts_mixed_batch(mode, graph):
+    sim = sm.Sim(sm.SPIN_POTTS, POTTS, seed=SEED, max_record=32)
+    sim.set_launch(mode, graph, 0, 256)
+    init = {}
+    for i, d in enumerate(POTTS):
+        init[i] = lattice_np(sim, i)
+        assert np.array_equal(init[i], oracle.init_potts(d["L"], d["q"], SEED, i))
+    sim.sweep(1, record=True)
+    for i, d in enumerate(POTTS):
+        oracle.potts_sweep(init[i], d["q"], d["beta"], d["J"], SEED, i, 0)
+        assert np.array_equal(lattice_np(sim, i), init[i]), i
+    sim.sweep(6, record=True)
+    st, E, M = sim.observables_host(0, 7)
+    qmax = max(d["q"] for d in POTTS)
+    for i, d in enumerate(POTTS):
+        ref = oracle.potts_run(init[i], d["q"], d["beta"], d["J"], SEED, i, 1, 6)
+        assert np.array_equal(lattice_np(sim, i), init[i]), i
+        assert np.array_equal(st[1:, i, :d["q"] + 1], ref), i
+        assert not st[1:, i, d["q"] + 1:qmax + 1].any()
+        N = d["L"] ** 2
+        Mq = (d["q"] * ref[:, 1:].max(axis=1) - N) / ((d["q"] - 1) * N)
+        np.testing.assert_allclose(M[1:, i], Mq.astype(np.float32), rtol=1e-6, atol=1e-7)
+        np.testing.assert_allclose(E[1:, i], (-d["J"] * ref[:, 0] / N).astype(np.float32), rtol=1e-6, atol=1e-7)
+
+
+# ----------------------------------------------------------------------- CPM
+def cpm_sim(p, seed=SEED, max_record=32):
+    cpm = dict(J=p["J"], **{"lambda": p["lam"]}, target=p["target"], n_cells=p["n_cells"], T=p["T"],
+               side=p["side"], cols=p["cols"])
+    return sm.Sim(sm.SPIN_CPM, [dict(L=p["L"])], seed=seed, max_record=max_record, cpm=cpm)
+
+
+def oracle_cpm(p):
+    return oracle.CPM(L=p["L"], J=p["J"], lam=p["lam"], target=p["target"], n_cells=p["n_cells"],
+                      T=p["T"], side=p["side"], cols=p["cols"])
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_cpm_paper_setup_matches_oracle(graph):
+    p = wl.cpm_paper()
+    sim = cpm_sim(p)
+    sim.set_launch(0, graph)
+    op = oracle_cpm(p)
+    ids, types, vol = op.init(SEED, 0)
+    ids = ids.copy()
+    assert np.array_equal(lattice_np(sim, 0), ids)
+    sim.sweep(5, record=True)
+    ref = op.run(ids, vol, types, SEED, 0, 0, 5)
+    assert np.array_equal(lattice_np(sim, 0), ids)
+    st, E, M = sim.observables_host(0, 5)
+    assert np.array_equal(st[:, 0, :], ref)
+
+
+def test_cpm_full_size_two_steps_and_gradient():
+    p = wl.cpm1024()
+    sim = cpm_sim(p)
+    op = oracle_cpm(p)
+    ids, types, vol = op.init(SEED, 0)
+    ids = ids.copy()
+    sim.sweep(2, record=True)
+    ref = op.run(ids, vol, types, SEED, 0, 0, 2)
+    assert np.array_equal(lattice_np(sim, 0), ids)
+    st = sim.observables_host(0, 2)[0]
+    assert np.array_equal(st[:, 0, :], ref)
+
+
+# --------------------------------------------------------------- gradients
+def test_ising_grad_matches_oracle_estimator():
+    from oracle import estimator
+    lats = wl.fit256(n=4, L=32, beta=0.45, J=1.0, h=0.05)
+    sim = make_ising(lats, max_record=400)
+    sim.sweep(300, record=True)
+    st = sim.observables_host(0, 300)[0]          # [T, n_lat, 2]
+    b32 = float(np.float32(0.45))                 # the library takes beta as float
+    for obs, name in [(0, "E"), (1, "M")]:
+        g = sim.grad(100, 200, observable=obs).cpu().numpy()
+        gp = sim.grad(100, 200, observable=obs, pool=True).cpu().numpy()
+        for i in range(4):
+            ref = estimator.ising_grad(st[100:, i][None], b32, 1.0, float(np.float32(0.05)), 32 * 32)
+            np.testing.assert_allclose(g[i], [ref[(name, "J")], ref[(name, "h")]], rtol=1e-9, atol=1e-12)
+        refp = estimator.ising_grad(np.transpose(st[100:], (1, 0, 2)), b32, 1.0, float(np.float32(0.05)), 1024)
+        np.testing.assert_allclose(gp[0], [refp[(name, "J")], refp[(name, "h")]], rtol=1e-9, atol=1e-12)
+    mom = sim.moments(100, 200).cpu().numpy()
+    for i in range(4):
+        X = st[100:, i].astype(np.int64)
+        want = [len(X), X[:, 0].sum(), X[:, 1].sum(), (X[:, 0] ** 2).sum(), (X[:, 0] * X[:, 1]).sum(),
+                (X[:, 1] ** 2).sum()]
+        assert list(mom[i]) == want
+
+
+def test_cpm_grad_matches_oracle_estimator():
+    from oracle import estimator
+    p = wl.cpm_paper()
+    sim = cpm_sim(p, max_record=200)
+    sim.sweep(150, record=True)
+    st = sim.observables_host(0, 150)[0]
+    g = sim.grad(50, 100).cpu().numpy()[0]
+    ref = estimator.cpm_grad(st[50:, 0][None], p["J"], p["lam"], p["T"], p["L"] ** 2)
+    pairs = estimator.cpm_pairs(3)
+    want = [ref[("J", a, b)] for a, b in pairs] + [ref["lambda"], ref["A"]]
+    np.testing.assert_allclose(g, want, rtol=1e-9, atol=1e-12)
+    assert g[0] == 0.0  # J_00: medium-medium contacts never exist
+
+
+# --------------------------------------------- full-size configurations
+def test_uneven512_full_size_sampled():
+    """The batched launch form of the benchmark, at full size; the oracle
+    checks every lattice up to 256^2 and one lattice of each larger size."""
+    lats = wl.uneven512()
+    sim = make_ising(lats, max_record=8)
+    init_sample = {}
+    sizes_seen = {}
+    for i, d in enumerate(lats):
+        if d["L"] <= 256 or d["L"] not in sizes_seen:
+            sizes_seen.setdefault(d["L"], i)
+            init_sample[i] = lattice_np(sim, i)
+    sim.sweep(2, record=True)
+    st = sim.observables_host(0, 2)[0]
+    for i, s0 in init_sample.items():
+        d = lats[i]
+        ref = oracle.ising_run(s0, d["beta"], d["J"], d["h"], SEED, i, 0, 2)
+        assert np.array_equal(lattice_np(sim, i), s0), i
+        assert np.array_equal(st[:, i, :], ref), i
+    assert torch.equal(sim.observables(1, 1)[0][0], sim.current_stats())
+
+
+@pytest.mark.parametrize("q", [3, 8])
+def test_potts_full_size_sampled(q):
+    lats = wl.potts_batch(q)
+    sim = sm.Sim(sm.SPIN_POTTS, lats, seed=SEED, max_record=4)
+    pick = [0, 31, 63]
+    init = {i: lattice_np(sim, i) for i in pick}
+    sim.sweep(2, record=True)
+    st = sim.observables_host(0, 2)[0]
+    for i in pick:
+        d = lats[i]
+        ref = oracle.potts_run(init[i], q, d["beta"], d["J"], SEED, i, 0, 2)
+        assert np.array_equal(lattice_np(sim, i), init[i])
+        assert np.array_equal(st[:, i, :], ref)
