@@ -192,8 +192,12 @@ int spin_restore(spin_ctx *ctx, const void *host_blob, size_t size, void *stream
  * the main sweep kernel (the batched work-list kernel, or the per-lattice
  * kernels of the plain form) with CUDA events on the caller's stream, up to
  * max_launches launches.  spin_profile_read synchronises the stream and
- * returns the summed kernel time (ms) and the number of timed launches;
- * enabling again resets the sums.  Not in the paper: measurement plumbing. */
+ * writes, for the three kernel classes (0: shared-memory tile kernel of the
+ * batched form, 1: warp row-strip kernel of the batched form for L in
+ * {512, 1024, 2048}, 2: per-lattice kernels of the plain form), the summed
+ * kernel time in ms (total_ms[3]) and the number of timed launches
+ * (launches[3]); enabling again resets the sums.  Not in the paper:
+ * measurement plumbing. */
 int spin_profile(spin_ctx *ctx, int32_t enable, int32_t max_launches);
 int spin_profile_read(spin_ctx *ctx, double *total_ms, int64_t *launches, void *stream);
 

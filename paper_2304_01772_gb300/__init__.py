@@ -313,11 +313,11 @@ class Sim:
         _check(lib().spin_profile(self.ctx, 1 if enable else 0, int(max_launches)), self.ctx, "spin_profile")
 
     def profile_read(self, stream=None):
-        ms = ctypes.c_double(0.0)
-        n = ctypes.c_int64(0)
-        _check(lib().spin_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n), _stream(stream)), self.ctx,
-               "spin_profile_read")
-        return ms.value, n.value
+        """[(ms, launches)] for kernel classes 0 (tile), 1 (row strip), 2 (plain)."""
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_int64 * 3)()
+        _check(lib().spin_profile_read(self.ctx, ms, n, _stream(stream)), self.ctx, "spin_profile_read")
+        return [(ms[i], n[i]) for i in range(3)]
 
     # -- host transfers / checkpoint ---------------------------------------
     def load_spins(self, host, stream=None):

@@ -34,6 +34,7 @@ cudaError_t launch_grad_i128(const void *moments, int rows, GradParams p, double
                              cudaStream_t s);
 cudaError_t launch_copy_lattices(const void *src, void *dst, const LatDev *lats, int n_lat,
                                  int elem, cudaStream_t s);
+cudaError_t occupancy_ising_strip(int *blocks_per_sm, int warps);
 }  // namespace spinmc
 
 using namespace spinmc;
@@ -71,6 +72,8 @@ struct spin_ctx {
     TabEntry *d_tabs = nullptr;
     Item *d_items = nullptr;
     int n_items = 0;
+    Item *d_strip = nullptr;     // warp row-strip items (Ising, L in {512, 1024, 2048})
+    int n_strip = 0, strip_grid = 0, strip_warps = 8;
     int32_t *d_generic = nullptr;
     int n_generic = 0, generic_maxL = 0;
     std::vector<int> fast_ids;
@@ -92,6 +95,7 @@ struct spin_ctx {
     int64_t n_rec = 0;
     // launch form
     int mode = 0, use_graph = 1, tile_rows = 0, threads = 256;
+    int use_strip = 1;
     int grid = 0;
     size_t smem = 0;
     int sm_count = 0;
@@ -101,6 +105,7 @@ struct spin_ctx {
     // kernel timing (spin_profile)
     bool prof = false;
     std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_cls;
     int prof_n = 0;
     std::string err;
 };
@@ -283,10 +288,15 @@ void drop_graphs(spin_ctx *ctx) {
 int plan(spin_ctx *ctx) {
     drop_graphs(ctx);
     if (ctx->model == SPIN_CPM) return SPIN_OK;
-    std::vector<Item> items;
+    std::vector<Item> items, strip;
     size_t smem = 16;
     for (int id : ctx->fast_ids) {
         const int L = ctx->lat[id].L;
+        if (ctx->model == SPIN_ISING && ctx->use_strip && (L == 512 || L == 1024 || L == 2048)) {
+            const int rows = std::max(1, std::min(L, ctx->tile_rows > 0 ? ctx->tile_rows : 65536 / L));
+            for (int r0 = 0; r0 < L; r0 += rows) strip.push_back(Item{id, r0, std::min(rows, L - r0), 0});
+            continue;
+        }
         if (L * L <= kWholeMaxBytes) {
             items.push_back(Item{id, 0, L, 1});
             smem = std::max(smem, (size_t)L * L);
@@ -311,6 +321,18 @@ int plan(spin_ctx *ctx) {
         CK(cudaMalloc(&ctx->d_items, sizeof(Item) * items.size()));
         CK(cudaMemcpy(ctx->d_items, items.data(), sizeof(Item) * items.size(), cudaMemcpyHostToDevice));
     }
+    if (ctx->d_strip) cudaFree(ctx->d_strip);
+    ctx->d_strip = nullptr;
+    ctx->n_strip = (int)strip.size();
+    if (!strip.empty()) {
+        CK(cudaMalloc(&ctx->d_strip, sizeof(Item) * strip.size()));
+        CK(cudaMemcpy(ctx->d_strip, strip.data(), sizeof(Item) * strip.size(), cudaMemcpyHostToDevice));
+        ctx->strip_warps = ctx->threads >= 256 ? 8 : 4;
+        int per_sm = 0;
+        CK(occupancy_ising_strip(&per_sm, ctx->strip_warps));
+        ctx->strip_grid = std::max(1, std::min((ctx->n_strip + ctx->strip_warps - 1) / ctx->strip_warps,
+                                               ctx->sm_count * std::max(1, per_sm)));
+    }
     if (smem > 200 * 1024) return fail(ctx, SPIN_EINVAL, "work item does not fit in shared memory");
     ctx->smem = smem;
     if (ctx->model == SPIN_ISING)
@@ -327,8 +349,9 @@ int plan(spin_ctx *ctx) {
 }
 
 // Event pair around one timed kernel launch (spin_profile).
-bool prof_begin(spin_ctx *ctx, cudaStream_t s) {
+bool prof_begin(spin_ctx *ctx, cudaStream_t s, int cls) {
     if (!ctx->prof || 2 * (ctx->prof_n + 1) > (int)ctx->prof_ev.size()) return false;
+    ctx->prof_cls[ctx->prof_n] = cls;
     return cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], s) == cudaSuccess;
 }
 
@@ -344,7 +367,7 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
         for (int c = 0; c < 2; ++c) {
             for (int id : ctx->fast_ids) {
                 const int L = ctx->lat[id].L;
-                const bool timed = prof_begin(ctx, s);
+                const bool timed = prof_begin(ctx, s, 2);
                 if (ctx->model == SPIN_ISING)
                     CK(launch_ising_plain(static_cast<int8_t *>(src) + ctx->lat[id].spin_offset, ctx->d_lats,
                                           id, L, ctx->d_tabs, ctx->k0, ctx->k1, ctx->d_state,
@@ -381,7 +404,7 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
             ++launches;
         }
         if (ctx->n_items) {
-            const bool timed = prof_begin(ctx, s);
+            const bool timed = prof_begin(ctx, s, 0);
             if (ctx->model == SPIN_ISING) {
                 IsingSweepArgs a{ctx->d_items, ctx->n_items, ctx->d_lats, ctx->d_tabs,
                                  static_cast<const int8_t *>(src), static_cast<int8_t *>(dst),
@@ -393,6 +416,15 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                                  ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, w};
                 CK(launch_potts_fused(a, ctx->grid, ctx->threads, ctx->smem, s));
             }
+            if (timed) prof_end(ctx, s);
+            ++launches;
+        }
+        if (ctx->n_strip) {
+            const bool timed = prof_begin(ctx, s, 1);
+            IsingSweepArgs a{ctx->d_strip, ctx->n_strip, ctx->d_lats, ctx->d_tabs,
+                             static_cast<const int8_t *>(src), static_cast<int8_t *>(dst),
+                             ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta};
+            CK(launch_ising_strip(a, ctx->strip_grid, ctx->strip_warps, s));
             if (timed) prof_end(ctx, s);
             ++launches;
         }
@@ -560,7 +592,7 @@ int spin_num_grad(const spin_ctx *ctx) {
 void spin_destroy(spin_ctx *ctx) {
     if (!ctx) return;
     drop_graphs(ctx);
-    void *bufs[] = {ctx->spins2, ctx->d_lats, ctx->d_tabs, ctx->d_items, ctx->d_generic,
+    void *bufs[] = {ctx->spins2, ctx->d_lats, ctx->d_tabs, ctx->d_items, ctx->d_strip, ctx->d_generic,
                     ctx->d_state, ctx->st.cur, ctx->st.delta, ctx->st.ring, ctx->d_type,
                     ctx->d_J, ctx->d_vol[0], ctx->d_vol[1], ctx->d_thr, ctx->d_latp,
                     ctx->d_cpmJ, ctx->d_scratch, ctx->d_flag};
@@ -1037,6 +1069,7 @@ int spin_profile(spin_ctx *ctx, int32_t enable, int32_t max_launches) {
             CK(cudaEventCreate(&e));
             ctx->prof_ev.push_back(e);
         }
+        ctx->prof_cls.assign(ctx->prof_ev.size() / 2, 0);
     }
     return SPIN_OK;
 }
@@ -1044,14 +1077,16 @@ int spin_profile(spin_ctx *ctx, int32_t enable, int32_t max_launches) {
 int spin_profile_read(spin_ctx *ctx, double *total_ms, int64_t *launches, void *stream) {
     if (!ctx || !total_ms || !launches) return SPIN_EINVAL;
     CK(cudaStreamSynchronize(S(stream)));
-    double sum = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        total_ms[c] = 0.0;
+        launches[c] = 0;
+    }
     for (int i = 0; i < ctx->prof_n; ++i) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]));
-        sum += ms;
+        total_ms[ctx->prof_cls[i]] += ms;
+        launches[ctx->prof_cls[i]] += 1;
     }
-    *total_ms = sum;
-    *launches = ctx->prof_n;
     return SPIN_OK;
 }
 

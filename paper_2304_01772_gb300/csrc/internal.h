@@ -87,6 +87,8 @@ struct IsingSweepArgs {
 
 cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, size_t smem,
                                cudaStream_t s);
+// Warp-per-row-strip kernel for L in {512, 1024, 2048}; items are row blocks.
+cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, cudaStream_t s);
 cudaError_t launch_ising_plain(int8_t *spins, const LatDev *lat_dev, int lat, int L,
                                const TabEntry *tabs, uint32_t k0, uint32_t k1,
                                const DevState *state, int64_t *delta, int colour, cudaStream_t s);

@@ -266,6 +266,249 @@ __global__ void init_random_kernel(void *spins, int model, const LatDev *lats, u
     }
 }
 
+// ------------------------------------------------------------------ strip kernel
+// Lattices with L = 512, 1024 or 2048: one warp owns full rows [r0, r0 + R)
+// of one lattice and walks down them.  At step s it updates colour 0 on row
+// s and colour 1 on row s - 1 (whose neighbours on rows s - 2 and s already
+// carry their colour-0 updates), keeping rows s-2 .. s+1 in registers.  Rows -1 and R are the recomputed halo: their
+// colour-0 updates are needed by colour 1 of rows 0 and R - 1 and are drawn
+// from the same site-keyed Philox counters as in the neighbouring item.
+// Left / right neighbours come from the neighbouring lanes by shuffles (lane
+// l holds chunks l, l + 32, ..; the row wraps inside the warp), so the
+// kernel needs no block barrier.  In registers a spin is the byte 8 * [s < 0]
+// ("x8 form"): four neighbour bytes and 5x the centre byte add without
+// carries to 8 * (d + 5 c), the byte offset of the table entry.
+constexpr uint32_t kX8 = 0x08080808u;
+
+// Rounds 1 and 2 of Philox4x32-10 for counter (g, lat, t, c) have one
+// product each that does not depend on g; they are formed once per row phase.
+struct PhiloxPrefix {
+    uint32_t u0, u1, v0, v1, ck1;
+};
+
+__device__ __forceinline__ PhiloxPrefix philox_prefix(uint32_t lat, uint32_t t, uint32_t c,
+                                                      uint32_t k0, uint32_t k1) {
+    PhiloxPrefix P;
+    const uint64_t pb = (uint64_t)0xCD9E8D57u * t;
+    P.u0 = (uint32_t)(pb >> 32) ^ lat ^ k0;
+    P.u1 = (uint32_t)pb;
+    const uint64_t pa = (uint64_t)0xD2511F53u * P.u0;
+    P.v0 = (uint32_t)(pa >> 32);
+    P.v1 = (uint32_t)pa;
+    P.ck1 = c ^ k1;
+    return P;
+}
+
+__device__ __forceinline__ uint4 philox_from_prefix(uint32_t g, const PhiloxPrefix &P, uint32_t k0,
+                                                    uint32_t k1) {
+    const uint64_t pa = (uint64_t)0xD2511F53u * g;            // round 1
+    const uint32_t x2 = (uint32_t)(pa >> 32) ^ P.ck1;
+    const uint32_t x3 = (uint32_t)pa;
+    k0 += 0x9E3779B9u;                                          // round 2
+    k1 += 0xBB67AE85u;
+    const uint64_t pb = (uint64_t)0xCD9E8D57u * x2;
+    uint32_t c0 = (uint32_t)(pb >> 32) ^ P.u1 ^ k0, c1 = (uint32_t)pb, c2 = P.v0 ^ x3 ^ k1, c3 = P.v1;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {                              // rounds 3..10
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+        const uint64_t qa = (uint64_t)0xD2511F53u * c0;
+        const uint64_t qb = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(qb >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(qa >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)qb;
+        c3 = (uint32_t)qa;
+        c0 = n0;
+        c2 = n2;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ uint4 to_x8(uint4 v) {
+    return make_uint4(v.x & kX8, v.y & kX8, v.z & kX8, v.w & kX8);
+}
+
+__device__ __forceinline__ uint32_t from_x8(uint32_t w) { return ((w >> 3) * 0xFEu) + 0x01010101u; }
+
+// Colour sub-step of one 16-byte chunk in x8 form; active bytes P and P + 2.
+template <int P>
+__device__ __forceinline__ uint4 chunk_x8(uint4 C, uint4 U, uint4 D, uint32_t lw, uint32_t rw,
+                                          uint4 ra, uint4 rb, const TabEntry *stab, bool count,
+                                          int &acc) {
+    const uint32_t w[6] = {lw, C.x, C.y, C.z, C.w, rw};
+    const uint32_t up[4] = {U.x, U.y, U.z, U.w};
+    const uint32_t dn[4] = {D.x, D.y, D.z, D.w};
+    const uint32_t rnd[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+    uint32_t out[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t W = w[i + 1];
+        const uint32_t lf = __funnelshift_l(w[i], W, 8);
+        const uint32_t rt = __funnelshift_r(W, w[i + 2], 8);
+        const uint32_t key = up[i] + dn[i] + lf + rt + W * 5u;
+        uint32_t nw = W;
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb) {
+            const int sh = 8 * (P + 2 * bb);
+            const uint32_t off = (key >> sh) & 0xFFu;
+            const TabEntry e =
+                *reinterpret_cast<const TabEntry *>(reinterpret_cast<const char *>(stab) + off);
+            if (rnd[2 * i + bb] <= e.thr) {
+                nw ^= 8u << sh;
+                if (count) acc += e.delta;
+            }
+        }
+        out[i] = nw;
+    }
+    return make_uint4(out[0], out[1], out[2], out[3]);
+}
+
+// One colour on one row held in registers (x8 form).
+template <int CPL, int P>
+__device__ __forceinline__ void row_phase(uint4 (&row)[CPL], const uint4 (&up)[CPL],
+                                          const uint4 (&dn)[CPL], uint32_t gy_base, int lane,
+                                          const PhiloxPrefix &PP, uint32_t k0, uint32_t k1,
+                                          const TabEntry *stab, bool count, int &acc) {
+    uint32_t sl[CPL], sr[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        sl[k] = __shfl_sync(0xFFFFFFFFu, row[k].w, (lane + 31) & 31);
+        sr[k] = __shfl_sync(0xFFFFFFFFu, row[k].x, (lane + 1) & 31);
+    }
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        const uint32_t lw = lane == 0 ? sl[(k + CPL - 1) % CPL] : sl[k];
+        const uint32_t rw = lane == 31 ? sr[(k + 1) % CPL] : sr[k];
+        const uint32_t g0 = gy_base + 2u * (uint32_t)(lane + 32 * k);
+        const uint4 ra = philox_from_prefix(g0, PP, k0, k1);
+        const uint4 rb = philox_from_prefix(g0 + 1u, PP, k0, k1);
+        row[k] = chunk_x8<P>(row[k], up[k], dn[k], lw, rw, ra, rb, stab, count, acc);
+    }
+}
+
+template <int CPL>
+__device__ __forceinline__ void load_row(const uint4 *__restrict__ S, int y, int lane,
+                                         uint4 (&r)[CPL]) {
+    const uint4 *p = S + (size_t)y * (32 * CPL) + lane;
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) r[k] = to_x8(__ldg(p + 32 * k));
+}
+
+template <int CPL>
+__device__ __forceinline__ void store_row(uint4 *D, int y, int lane, const uint4 (&r)[CPL]) {
+    uint4 *p = D + (size_t)y * (32 * CPL) + lane;
+#pragma unroll
+    for (int k = 0; k < CPL; ++k)
+        p[32 * k] = make_uint4(from_x8(r[k].x), from_x8(r[k].y), from_x8(r[k].z), from_x8(r[k].w));
+}
+
+struct StripCtx {
+    const uint4 *S;
+    uint4 *D;
+    int L, r0, nrows, lane;
+    uint32_t lat, t, k0, k1;
+    PhiloxPrefix P0, P1;
+    const TabEntry *stab;
+};
+
+__device__ __forceinline__ int wrap_row(int y, int L) { return y < 0 ? y + L : (y >= L ? y - L : y); }
+
+// Step s: rows (a, b, c, d) = (s-2, s-1, s, s+1); d is loaded at the start of
+// the step into the registers that held row s-3.
+template <int CPL>
+__device__ __forceinline__ void strip_step(uint4 (&a)[CPL], uint4 (&b)[CPL], uint4 (&c)[CPL],
+                                           uint4 (&d)[CPL], int s, const StripCtx &x, int &acc) {
+    if (s > x.nrows) return;
+    load_row<CPL>(x.S, wrap_row(x.r0 + s + 1, x.L), x.lane, d);
+    const int y = wrap_row(x.r0 + s, x.L);
+    const uint32_t gyb = (uint32_t)y * (uint32_t)(x.L >> 3);
+    const bool cnt = s >= 0 && s < x.nrows;
+    if (y & 1)
+        row_phase<CPL, 1>(c, b, d, gyb, x.lane, x.P0, x.k0, x.k1, x.stab, cnt, acc);
+    else
+        row_phase<CPL, 0>(c, b, d, gyb, x.lane, x.P0, x.k0, x.k1, x.stab, cnt, acc);
+    if (s >= 1) {
+        const int y1 = wrap_row(x.r0 + s - 1, x.L);
+        const uint32_t gyb1 = (uint32_t)y1 * (uint32_t)(x.L >> 3);
+        if ((y1 & 1) == 0)   // colour-1 active bytes have parity (1 ^ y1) & 1
+            row_phase<CPL, 1>(b, a, c, gyb1, x.lane, x.P1, x.k0, x.k1, x.stab, true, acc);
+        else
+            row_phase<CPL, 0>(b, a, c, gyb1, x.lane, x.P1, x.k0, x.k1, x.stab, true, acc);
+        store_row<CPL>(x.D, y1, x.lane, b);
+    }
+}
+
+// Unpack the packed per-lane sums (dB * 65536 + dM) into 32-bit totals.
+__device__ __forceinline__ void drain_acc(int &acc, int &dm, int &db) {
+    const int m = (int)(int16_t)(acc & 0xFFFF);
+    dm += m;
+    db += (acc - m) >> 16;
+    acc = 0;
+}
+
+template <int CPL>
+__device__ void strip_item(const StripCtx &x, int &dm, int &db) {
+    uint4 A[CPL], B[CPL], C[CPL], D[CPL];
+    load_row<CPL>(x.S, wrap_row(x.r0 - 2, x.L), x.lane, B);
+    load_row<CPL>(x.S, wrap_row(x.r0 - 1, x.L), x.lane, C);
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) A[k] = make_uint4(0, 0, 0, 0);
+    int acc = 0;
+    for (int s = -1; s <= x.nrows; s += 4) {
+        strip_step<CPL>(A, B, C, D, s, x, acc);
+        strip_step<CPL>(B, C, D, A, s + 1, x, acc);
+        strip_step<CPL>(C, D, A, B, s + 2, x, acc);
+        strip_step<CPL>(D, A, B, C, s + 3, x, acc);
+        drain_acc(acc, dm, db);
+    }
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) ising_strip_kernel(IsingSweepArgs a) {
+    __shared__ TabEntry stabs[WARPS][kTabStride];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t t = a.state->t;
+    TabEntry *stab = stabs[warp];
+    const int gw = blockIdx.x * WARPS + warp, nw = gridDim.x * WARPS;
+    for (int it = gw; it < a.n_items; it += nw) {
+        const Item w = a.items[it];
+        const LatDev ld = a.lats[w.lat];
+        __syncwarp();
+        if (lane < kTabStride) stab[lane] = a.tabs[w.lat * kTabStride + lane];
+        __syncwarp();
+        StripCtx x;
+        x.S = reinterpret_cast<const uint4 *>(a.src + ld.offset);
+        x.D = reinterpret_cast<uint4 *>(a.dst + ld.offset);
+        x.L = ld.L;
+        x.r0 = w.r0;
+        x.nrows = w.nrows;
+        x.lane = lane;
+        x.lat = (uint32_t)w.lat;
+        x.t = t;
+        x.k0 = a.k0;
+        x.k1 = a.k1;
+        x.P0 = philox_prefix(x.lat, t, 0u, a.k0, a.k1);
+        x.P1 = philox_prefix(x.lat, t, 1u, a.k0, a.k1);
+        x.stab = stab;
+        int dm = 0, db = 0;
+        if (ld.L == 2048)
+            strip_item<4>(x, dm, db);
+        else if (ld.L == 1024)
+            strip_item<2>(x, dm, db);
+        else
+            strip_item<1>(x, dm, db);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dm += __shfl_xor_sync(0xFFFFFFFFu, dm, o);
+            db += __shfl_xor_sync(0xFFFFFFFFu, db, o);
+        }
+        if (lane == 0) {
+            if (dm) atomicAdd(reinterpret_cast<unsigned long long *>(a.delta + 2 * w.lat), (unsigned long long)(long long)dm);
+            if (db) atomicAdd(reinterpret_cast<unsigned long long *>(a.delta + 2 * w.lat + 1), (unsigned long long)(long long)db);
+        }
+    }
+}
+
 // Copy every lattice (L*L elements of `elem` bytes at its offset) src -> dst.
 __global__ void copy_lattices_kernel(const unsigned char *src, unsigned char *dst,
                                      const LatDev *lats, int elem) {
@@ -311,6 +554,26 @@ cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, s
             return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, cudaStream_t s) {
+    switch (warps) {
+        case 4:
+            ising_strip_kernel<4><<<grid, 128, 0, s>>>(a);
+            break;
+        case 8:
+            ising_strip_kernel<8><<<grid, 256, 0, s>>>(a);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t occupancy_ising_strip(int *blocks_per_sm, int warps) {
+    if (warps == 4)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<4>, 128, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<8>, 256, 0);
 }
 
 cudaError_t set_ising_fused_smem(size_t smem) {

@@ -97,6 +97,23 @@ def test_launch_forms_bit_identical():
         assert np.array_equal(st, finals[0][1])
 
 
+@pytest.mark.parametrize("rows,warps", [(0, 256), (1, 256), (5, 128), (7, 256), (32, 128)])
+def test_strip_kernel_rows_and_tail(rows, warps):
+    """Lattices of side 512, 1024 and 2048 take the warp row-strip kernel; item
+    heights that are not multiples of the 4-step unroll exercise its tail."""
+    lats = [dict(L=512, beta=0.44, J=1.0, h=0.03), dict(L=1024, beta=0.3, J=1.0, h=-0.1),
+            dict(L=2048, beta=0.5, J=-0.8, h=0.0), dict(L=64, beta=0.4, J=1.0, h=0.0)]
+    sim = make_ising(lats, max_record=8)
+    sim.set_launch(0, True, rows, warps)
+    init = [lattice_np(sim, i) for i in range(len(lats))]
+    sim.sweep(3, record=True)
+    st = sim.observables_host(0, 3)[0]
+    for i, d in enumerate(lats):
+        ref = oracle.ising_run(init[i], d["beta"], d["J"], d["h"], SEED, i, 0, 3)
+        assert np.array_equal(lattice_np(sim, i), init[i]), i
+        assert np.array_equal(st[:, i, :], ref), i
+
+
 def test_checkpoint_resume_bit_identical():
     lats = wl.uneven512(n=12, seed=5, emin=4, emax=8)
     a = make_ising(lats)
