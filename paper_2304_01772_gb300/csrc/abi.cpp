@@ -327,7 +327,7 @@ int plan(spin_ctx *ctx) {
     if (!strip.empty()) {
         CK(cudaMalloc(&ctx->d_strip, sizeof(Item) * strip.size()));
         CK(cudaMemcpy(ctx->d_strip, strip.data(), sizeof(Item) * strip.size(), cudaMemcpyHostToDevice));
-        ctx->strip_warps = ctx->threads >= 256 ? 8 : 4;
+        ctx->strip_warps = ctx->threads >= 512 ? 8 : 4;
         int per_sm = 0;
         CK(occupancy_ising_strip(&per_sm, ctx->strip_warps));
         ctx->strip_grid = std::max(1, std::min((ctx->n_strip + ctx->strip_warps - 1) / ctx->strip_warps,
@@ -408,7 +408,8 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
             if (ctx->model == SPIN_ISING) {
                 IsingSweepArgs a{ctx->d_items, ctx->n_items, ctx->d_lats, ctx->d_tabs,
                                  static_cast<const int8_t *>(src), static_cast<int8_t *>(dst),
-                                 ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta};
+                                 ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta,
+                                 philox_keys(ctx->k0, ctx->k1)};
                 CK(launch_ising_fused(a, ctx->grid, ctx->threads, ctx->smem, s));
             } else {
                 PottsSweepArgs a{ctx->d_items, ctx->n_items, ctx->d_lats, ctx->d_tabs,
@@ -423,7 +424,8 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
             const bool timed = prof_begin(ctx, s, 1);
             IsingSweepArgs a{ctx->d_strip, ctx->n_strip, ctx->d_lats, ctx->d_tabs,
                              static_cast<const int8_t *>(src), static_cast<int8_t *>(dst),
-                             ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta};
+                             ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta,
+                             philox_keys(ctx->k0, ctx->k1)};
             CK(launch_ising_strip(a, ctx->strip_grid, ctx->strip_warps, s));
             if (timed) prof_end(ctx, s);
             ++launches;

@@ -71,6 +71,21 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 }
 #endif  // __CUDACC__
 
+// Philox round keys (key + r * Weyl constant, r = 0..9), passed in the kernel
+// parameters so that every round reads its key from the constant bank.
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+};
+
+inline PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+    PhiloxKeys r;
+    for (int i = 0; i < 10; ++i) {
+        r.k0[i] = k0 + (uint32_t)i * 0x9E3779B9u;
+        r.k1[i] = k1 + (uint32_t)i * 0xBB67AE85u;
+    }
+    return r;
+}
+
 // -------------------------------------------------------------- launch wrappers
 // All return cudaGetLastError() after the launch.
 struct IsingSweepArgs {
@@ -83,6 +98,7 @@ struct IsingSweepArgs {
     uint32_t k0, k1;
     const DevState *state;
     int64_t *delta;   // [n_lat][2]
+    PhiloxKeys rk;
 };
 
 cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, size_t smem,

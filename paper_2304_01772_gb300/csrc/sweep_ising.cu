@@ -270,52 +270,55 @@ __global__ void init_random_kernel(void *spins, int model, const LatDev *lats, u
 // Lattices with L = 512, 1024 or 2048: one warp owns full rows [r0, r0 + R)
 // of one lattice and walks down them.  At step s it updates colour 0 on row
 // s and colour 1 on row s - 1 (whose neighbours on rows s - 2 and s already
-// carry their colour-0 updates), keeping rows s-2 .. s+1 in registers.  Rows -1 and R are the recomputed halo: their
-// colour-0 updates are needed by colour 1 of rows 0 and R - 1 and are drawn
-// from the same site-keyed Philox counters as in the neighbouring item.
-// Left / right neighbours come from the neighbouring lanes by shuffles (lane
-// l holds chunks l, l + 32, ..; the row wraps inside the warp), so the
-// kernel needs no block barrier.  In registers a spin is the byte 8 * [s < 0]
-// ("x8 form"): four neighbour bytes and 5x the centre byte add without
-// carries to 8 * (d + 5 c), the byte offset of the table entry.
+// carry their colour-0 updates).  Rows -1 and R are the recomputed halo:
+// their colour-0 updates are needed by colour 1 of rows 0 and R - 1 and come
+// from the same site-keyed Philox counters as in the neighbouring item, so
+// items never exchange data.  Each warp keeps rows s-2 .. s+2 in a five-slot
+// shared-memory ring; row s+2 streams in with cp.async while the warp works on
+// rows s-2 .. s+1.  Lane l handles chunks l, l + 32, ..; left / right
+// neighbours come from lane shuffles, the two words that cross a 32-chunk
+// boundary from shared memory.  No block barrier is needed.
+//
+// In the ring a spin is the byte 8 * [s < 0] ("x8 form"): four neighbour
+// bytes plus 5x the centre byte add without carries to 8 * (d + 5 c), the
+// byte offset of the table entry.
 constexpr uint32_t kX8 = 0x08080808u;
+constexpr int kRing = 5;          // row slots per warp
+constexpr int kRowChunks = 128;   // 16-byte chunks per slot (L <= 2048)
 
 // Rounds 1 and 2 of Philox4x32-10 for counter (g, lat, t, c) have one
-// product each that does not depend on g; they are formed once per row phase.
+// product each that does not depend on g; they are formed once per item.
 struct PhiloxPrefix {
-    uint32_t u0, u1, v0, v1, ck1;
+    uint32_t u0, u1k, v0k, v1, ck1;
 };
 
 __device__ __forceinline__ PhiloxPrefix philox_prefix(uint32_t lat, uint32_t t, uint32_t c,
-                                                      uint32_t k0, uint32_t k1) {
+                                                      const PhiloxKeys &rk) {
     PhiloxPrefix P;
     const uint64_t pb = (uint64_t)0xCD9E8D57u * t;
-    P.u0 = (uint32_t)(pb >> 32) ^ lat ^ k0;
-    P.u1 = (uint32_t)pb;
+    P.u0 = (uint32_t)(pb >> 32) ^ lat ^ rk.k0[0];
+    const uint32_t u1 = (uint32_t)pb;
     const uint64_t pa = (uint64_t)0xD2511F53u * P.u0;
-    P.v0 = (uint32_t)(pa >> 32);
+    P.u1k = u1 ^ rk.k0[1];
+    P.v0k = (uint32_t)(pa >> 32) ^ rk.k1[1];
     P.v1 = (uint32_t)pa;
-    P.ck1 = c ^ k1;
+    P.ck1 = c ^ rk.k1[0];
     return P;
 }
 
-__device__ __forceinline__ uint4 philox_from_prefix(uint32_t g, const PhiloxPrefix &P, uint32_t k0,
-                                                    uint32_t k1) {
+__device__ __forceinline__ uint4 philox_from_prefix(uint32_t g, const PhiloxPrefix &P,
+                                                    const PhiloxKeys &rk) {
     const uint64_t pa = (uint64_t)0xD2511F53u * g;            // round 1
     const uint32_t x2 = (uint32_t)(pa >> 32) ^ P.ck1;
-    const uint32_t x3 = (uint32_t)pa;
-    k0 += 0x9E3779B9u;                                          // round 2
-    k1 += 0xBB67AE85u;
-    const uint64_t pb = (uint64_t)0xCD9E8D57u * x2;
-    uint32_t c0 = (uint32_t)(pb >> 32) ^ P.u1 ^ k0, c1 = (uint32_t)pb, c2 = P.v0 ^ x3 ^ k1, c3 = P.v1;
+    const uint64_t pb = (uint64_t)0xCD9E8D57u * x2;            // round 2
+    uint32_t c0 = (uint32_t)(pb >> 32) ^ P.u1k, c1 = (uint32_t)pb;
+    uint32_t c2 = (uint32_t)pa ^ P.v0k, c3 = P.v1;
 #pragma unroll
     for (int r = 2; r < 10; ++r) {                              // rounds 3..10
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
         const uint64_t qa = (uint64_t)0xD2511F53u * c0;
         const uint64_t qb = (uint64_t)0xCD9E8D57u * c2;
-        const uint32_t n0 = (uint32_t)(qb >> 32) ^ c1 ^ k0;
-        const uint32_t n2 = (uint32_t)(qa >> 32) ^ c3 ^ k1;
+        const uint32_t n0 = (uint32_t)(qb >> 32) ^ c1 ^ rk.k0[r];
+        const uint32_t n2 = (uint32_t)(qa >> 32) ^ c3 ^ rk.k1[r];
         c1 = (uint32_t)qb;
         c3 = (uint32_t)qa;
         c0 = n0;
@@ -330,15 +333,24 @@ __device__ __forceinline__ uint4 to_x8(uint4 v) {
 
 __device__ __forceinline__ uint32_t from_x8(uint32_t w) { return ((w >> 3) * 0xFEu) + 0x01010101u; }
 
-// Colour sub-step of one 16-byte chunk in x8 form; active bytes P and P + 2.
-template <int P>
+// Byte selectors (PRMT) and flip masks of the two active bytes P and P + 2.
+struct RowPar {
+    uint32_t sel0, sel1, fm0, fm1;
+};
+
+__device__ __forceinline__ RowPar row_par(int P) {
+    return RowPar{0x4440u + (uint32_t)P, 0x4442u + (uint32_t)P, 8u << (8 * P), 8u << (8 * P + 16)};
+}
+
+// Colour sub-step of one 16-byte chunk in x8 form.
 __device__ __forceinline__ uint4 chunk_x8(uint4 C, uint4 U, uint4 D, uint32_t lw, uint32_t rw,
-                                          uint4 ra, uint4 rb, const TabEntry *stab, bool count,
-                                          int &acc) {
+                                          uint4 ra, uint4 rb, const RowPar &rp,
+                                          const TabEntry *stab, int &acc) {
     const uint32_t w[6] = {lw, C.x, C.y, C.z, C.w, rw};
     const uint32_t up[4] = {U.x, U.y, U.z, U.w};
     const uint32_t dn[4] = {D.x, D.y, D.z, D.w};
     const uint32_t rnd[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
+    const char *tb = reinterpret_cast<const char *>(stab);
     uint32_t out[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -346,96 +358,103 @@ __device__ __forceinline__ uint4 chunk_x8(uint4 C, uint4 U, uint4 D, uint32_t lw
         const uint32_t lf = __funnelshift_l(w[i], W, 8);
         const uint32_t rt = __funnelshift_r(W, w[i + 2], 8);
         const uint32_t key = up[i] + dn[i] + lf + rt + W * 5u;
+        const TabEntry e0 = *reinterpret_cast<const TabEntry *>(tb + __byte_perm(key, 0u, rp.sel0));
+        const TabEntry e1 = *reinterpret_cast<const TabEntry *>(tb + __byte_perm(key, 0u, rp.sel1));
         uint32_t nw = W;
-#pragma unroll
-        for (int bb = 0; bb < 2; ++bb) {
-            const int sh = 8 * (P + 2 * bb);
-            const uint32_t off = (key >> sh) & 0xFFu;
-            const TabEntry e =
-                *reinterpret_cast<const TabEntry *>(reinterpret_cast<const char *>(stab) + off);
-            if (rnd[2 * i + bb] <= e.thr) {
-                nw ^= 8u << sh;
-                if (count) acc += e.delta;
-            }
+        if (rnd[2 * i] <= e0.thr) {
+            nw ^= rp.fm0;
+            acc += e0.delta;
+        }
+        if (rnd[2 * i + 1] <= e1.thr) {
+            nw ^= rp.fm1;
+            acc += e1.delta;
         }
         out[i] = nw;
     }
     return make_uint4(out[0], out[1], out[2], out[3]);
 }
 
-// One colour on one row held in registers (x8 form).
-template <int CPL, int P>
-__device__ __forceinline__ void row_phase(uint4 (&row)[CPL], const uint4 (&up)[CPL],
-                                          const uint4 (&dn)[CPL], uint32_t gy_base, int lane,
-                                          const PhiloxPrefix &PP, uint32_t k0, uint32_t k1,
-                                          const TabEntry *stab, bool count, int &acc) {
-    uint32_t sl[CPL], sr[CPL];
-#pragma unroll
-    for (int k = 0; k < CPL; ++k) {
-        sl[k] = __shfl_sync(0xFFFFFFFFu, row[k].w, (lane + 31) & 31);
-        sr[k] = __shfl_sync(0xFFFFFFFFu, row[k].x, (lane + 1) & 31);
-    }
-#pragma unroll
-    for (int k = 0; k < CPL; ++k) {
-        const uint32_t lw = lane == 0 ? sl[(k + CPL - 1) % CPL] : sl[k];
-        const uint32_t rw = lane == 31 ? sr[(k + 1) % CPL] : sr[k];
-        const uint32_t g0 = gy_base + 2u * (uint32_t)(lane + 32 * k);
-        const uint4 ra = philox_from_prefix(g0, PP, k0, k1);
-        const uint4 rb = philox_from_prefix(g0 + 1u, PP, k0, k1);
-        row[k] = chunk_x8<P>(row[k], up[k], dn[k], lw, rw, ra, rb, stab, count, acc);
-    }
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-template <int CPL>
-__device__ __forceinline__ void load_row(const uint4 *__restrict__ S, int y, int lane,
-                                         uint4 (&r)[CPL]) {
-    const uint4 *p = S + (size_t)y * (32 * CPL) + lane;
-#pragma unroll
-    for (int k = 0; k < CPL; ++k) r[k] = to_x8(__ldg(p + 32 * k));
-}
-
-template <int CPL>
-__device__ __forceinline__ void store_row(uint4 *D, int y, int lane, const uint4 (&r)[CPL]) {
-    uint4 *p = D + (size_t)y * (32 * CPL) + lane;
-#pragma unroll
-    for (int k = 0; k < CPL; ++k)
-        p[32 * k] = make_uint4(from_x8(r[k].x), from_x8(r[k].y), from_x8(r[k].z), from_x8(r[k].w));
-}
+__device__ __forceinline__ int wrap_row(int y, int L) { return y < 0 ? y + L : (y >= L ? y - L : y); }
 
 struct StripCtx {
     const uint4 *S;
     uint4 *D;
-    int L, r0, nrows, lane;
-    uint32_t lat, t, k0, k1;
+    uint4 *ring;              // kRing * kRowChunks chunks of this warp
+    int L, Lv, cpl, r0, nrows, lane;
     PhiloxPrefix P0, P1;
-    const TabEntry *stab;
+    const TabEntry *tab_cnt;  // statistics deltas
+    const TabEntry *tab_halo; // same thresholds, zero deltas (recomputed halo rows)
 };
 
-__device__ __forceinline__ int wrap_row(int y, int L) { return y < 0 ? y + L : (y >= L ? y - L : y); }
+__device__ __forceinline__ uint4 *slot(const StripCtx &x, int r) {
+    return x.ring + ((r + 2) % kRing) * kRowChunks;
+}
 
-// Step s: rows (a, b, c, d) = (s-2, s-1, s, s+1); d is loaded at the start of
-// the step into the registers that held row s-3.
-template <int CPL>
-__device__ __forceinline__ void strip_step(uint4 (&a)[CPL], uint4 (&b)[CPL], uint4 (&c)[CPL],
-                                           uint4 (&d)[CPL], int s, const StripCtx &x, int &acc) {
-    if (s > x.nrows) return;
-    load_row<CPL>(x.S, wrap_row(x.r0 + s + 1, x.L), x.lane, d);
-    const int y = wrap_row(x.r0 + s, x.L);
-    const uint32_t gyb = (uint32_t)y * (uint32_t)(x.L >> 3);
-    const bool cnt = s >= 0 && s < x.nrows;
-    if (y & 1)
-        row_phase<CPL, 1>(c, b, d, gyb, x.lane, x.P0, x.k0, x.k1, x.stab, cnt, acc);
+__device__ __forceinline__ void issue_row(const StripCtx &x, int r) {
+    const uint4 *src = x.S + (size_t)wrap_row(x.r0 + r, x.L) * x.Lv;
+    uint4 *dst = slot(x, r);
+    for (int j = x.lane; j < x.Lv; j += 32) cp_async16(dst + j, src + j);
+}
+
+__device__ __forceinline__ void convert_row(const StripCtx &x, int r) {
+    uint4 *row = slot(x, r);
+    for (int j = x.lane; j < x.Lv; j += 32) row[j] = to_x8(row[j]);
+}
+
+// One chunk of one colour phase (see row_phase).
+__device__ __forceinline__ void phase_chunk(const StripCtx &x, int j, int colour, uint4 *rc,
+                                            const uint4 *ru, const uint4 *rd, uint4 *gout,
+                                            uint32_t gyb, const RowPar &rp, const PhiloxPrefix &PP,
+                                            const TabEntry *stab, const PhiloxKeys &rk, int &acc) {
+    const int mask = x.Lv - 1;
+    const uint4 C = rc[j];
+    const uint4 U = ru[j];
+    const uint4 Dn = rd[j];
+    uint32_t lw = __shfl_sync(0xFFFFFFFFu, C.w, (x.lane + 31) & 31);
+    uint32_t rw = __shfl_sync(0xFFFFFFFFu, C.x, (x.lane + 1) & 31);
+    if (x.lane == 0) lw = reinterpret_cast<const uint32_t *>(rc + ((j - 1) & mask))[3];
+    if (x.lane == 31) rw = reinterpret_cast<const uint32_t *>(rc + ((j + 1) & mask))[0];
+    const uint32_t g0 = gyb + 2u * (uint32_t)j;
+    const uint4 ra = philox_from_prefix(g0, PP, rk);
+    const uint4 rb = philox_from_prefix(g0 + 1u, PP, rk);
+    const uint4 N = chunk_x8(C, U, Dn, lw, rw, ra, rb, rp, stab, acc);
+    if (colour == 0)
+        rc[j] = N;
     else
-        row_phase<CPL, 0>(c, b, d, gyb, x.lane, x.P0, x.k0, x.k1, x.stab, cnt, acc);
-    if (s >= 1) {
-        const int y1 = wrap_row(x.r0 + s - 1, x.L);
-        const uint32_t gyb1 = (uint32_t)y1 * (uint32_t)(x.L >> 3);
-        if ((y1 & 1) == 0)   // colour-1 active bytes have parity (1 ^ y1) & 1
-            row_phase<CPL, 1>(b, a, c, gyb1, x.lane, x.P1, x.k0, x.k1, x.stab, true, acc);
-        else
-            row_phase<CPL, 0>(b, a, c, gyb1, x.lane, x.P1, x.k0, x.k1, x.stab, true, acc);
-        store_row<CPL>(x.D, y1, x.lane, b);
+        gout[j] = make_uint4(from_x8(N.x), from_x8(N.y), from_x8(N.z), from_x8(N.w));
+}
+
+// One colour on row r of the ring.  Colour 0 writes the row back to the ring;
+// colour 1 writes the final row (converted back to +-1 bytes) to global memory.
+// Rows of 1024 and 2048 bytes take two chunks per iteration (four independent
+// Philox chains per lane).
+__device__ __forceinline__ void row_phase(const StripCtx &x, int r, int colour,
+                                          const PhiloxKeys &rk, int &acc) {
+    const int y = wrap_row(x.r0 + r, x.L);
+    const RowPar rp = row_par((colour ^ y) & 1);
+    const PhiloxPrefix &PP = colour ? x.P1 : x.P0;
+    const TabEntry *stab = (r >= 0 && r < x.nrows) ? x.tab_cnt : x.tab_halo;
+    uint4 *rc = slot(x, r);
+    const uint4 *ru = slot(x, r - 1);
+    const uint4 *rd = slot(x, r + 1);
+    const uint32_t gyb = (uint32_t)y * (uint32_t)(x.L >> 3);
+    uint4 *gout = x.D + (size_t)y * x.Lv;
+    if (x.Lv >= 64) {
+        for (int j = x.lane; j < x.Lv; j += 64) {
+            phase_chunk(x, j, colour, rc, ru, rd, gout, gyb, rp, PP, stab, rk, acc);
+            phase_chunk(x, j + 32, colour, rc, ru, rd, gout, gyb, rp, PP, stab, rk, acc);
+        }
+    } else {
+        phase_chunk(x, x.lane, colour, rc, ru, rd, gout, gyb, rp, PP, stab, rk, acc);
     }
+    __syncwarp();
 }
 
 // Unpack the packed per-lane sums (dB * 65536 + dM) into 32-bit totals.
@@ -446,57 +465,65 @@ __device__ __forceinline__ void drain_acc(int &acc, int &dm, int &db) {
     acc = 0;
 }
 
-template <int CPL>
-__device__ void strip_item(const StripCtx &x, int &dm, int &db) {
-    uint4 A[CPL], B[CPL], C[CPL], D[CPL];
-    load_row<CPL>(x.S, wrap_row(x.r0 - 2, x.L), x.lane, B);
-    load_row<CPL>(x.S, wrap_row(x.r0 - 1, x.L), x.lane, C);
-#pragma unroll
-    for (int k = 0; k < CPL; ++k) A[k] = make_uint4(0, 0, 0, 0);
+__device__ void strip_item(const StripCtx &x, const PhiloxKeys &rk, int &dm, int &db) {
+    issue_row(x, -2);
+    cp_async_commit();
+    issue_row(x, -1);
+    cp_async_commit();
+    issue_row(x, 0);
+    cp_async_commit();
     int acc = 0;
-    for (int s = -1; s <= x.nrows; s += 4) {
-        strip_step<CPL>(A, B, C, D, s, x, acc);
-        strip_step<CPL>(B, C, D, A, s + 1, x, acc);
-        strip_step<CPL>(C, D, A, B, s + 2, x, acc);
-        strip_step<CPL>(D, A, B, C, s + 3, x, acc);
-        drain_acc(acc, dm, db);
+    for (int s = -1; s <= x.nrows; ++s) {
+        if (s + 2 <= x.nrows + 1) issue_row(x, s + 2);
+        cp_async_commit();
+        cp_async_wait1();           // every row up to s + 1 has landed
+        if (s == -1) {
+            convert_row(x, -2);
+            convert_row(x, -1);
+        }
+        convert_row(x, s + 1);
+        __syncwarp();
+        row_phase(x, s, 0, rk, acc);
+        if (s >= 1) row_phase(x, s - 1, 1, rk, acc);
+        if ((s & 7) == 7) drain_acc(acc, dm, db);
     }
+    drain_acc(acc, dm, db);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncwarp();
 }
 
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) ising_strip_kernel(IsingSweepArgs a) {
-    __shared__ TabEntry stabs[WARPS][kTabStride];
+__global__ void __launch_bounds__(WARPS * 32) ising_strip_kernel(IsingSweepArgs a) {
+    extern __shared__ __align__(16) uint4 ring_all[];
+    __shared__ TabEntry tabs[WARPS][2][kTabStride];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t t = a.state->t;
-    TabEntry *stab = stabs[warp];
     const int gw = blockIdx.x * WARPS + warp, nw = gridDim.x * WARPS;
     for (int it = gw; it < a.n_items; it += nw) {
         const Item w = a.items[it];
         const LatDev ld = a.lats[w.lat];
-        __syncwarp();
-        if (lane < kTabStride) stab[lane] = a.tabs[w.lat * kTabStride + lane];
+        if (lane < kTabStride) {
+            const TabEntry e = a.tabs[w.lat * kTabStride + lane];
+            tabs[warp][0][lane] = e;
+            tabs[warp][1][lane] = TabEntry{e.thr, 0};
+        }
         __syncwarp();
         StripCtx x;
         x.S = reinterpret_cast<const uint4 *>(a.src + ld.offset);
         x.D = reinterpret_cast<uint4 *>(a.dst + ld.offset);
+        x.ring = ring_all + (size_t)warp * kRing * kRowChunks;
         x.L = ld.L;
+        x.Lv = ld.L >> 4;
+        x.cpl = ld.L >> 9;
         x.r0 = w.r0;
         x.nrows = w.nrows;
         x.lane = lane;
-        x.lat = (uint32_t)w.lat;
-        x.t = t;
-        x.k0 = a.k0;
-        x.k1 = a.k1;
-        x.P0 = philox_prefix(x.lat, t, 0u, a.k0, a.k1);
-        x.P1 = philox_prefix(x.lat, t, 1u, a.k0, a.k1);
-        x.stab = stab;
+        x.P0 = philox_prefix((uint32_t)w.lat, t, 0u, a.rk);
+        x.P1 = philox_prefix((uint32_t)w.lat, t, 1u, a.rk);
+        x.tab_cnt = tabs[warp][0];
+        x.tab_halo = tabs[warp][1];
         int dm = 0, db = 0;
-        if (ld.L == 2048)
-            strip_item<4>(x, dm, db);
-        else if (ld.L == 1024)
-            strip_item<2>(x, dm, db);
-        else
-            strip_item<1>(x, dm, db);
+        strip_item(x, a.rk, dm, db);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             dm += __shfl_xor_sync(0xFFFFFFFFu, dm, o);
@@ -506,6 +533,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) ising_strip_kernel(Isi
             if (dm) atomicAdd(reinterpret_cast<unsigned long long *>(a.delta + 2 * w.lat), (unsigned long long)(long long)dm);
             if (db) atomicAdd(reinterpret_cast<unsigned long long *>(a.delta + 2 * w.lat + 1), (unsigned long long)(long long)db);
         }
+        __syncwarp();
     }
 }
 
@@ -556,13 +584,15 @@ cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, s
     return cudaGetLastError();
 }
 
+size_t strip_smem(int warps) { return sizeof(uint4) * (size_t)warps * kRing * kRowChunks; }
+
 cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, cudaStream_t s) {
     switch (warps) {
         case 4:
-            ising_strip_kernel<4><<<grid, 128, 0, s>>>(a);
+            ising_strip_kernel<4><<<grid, 128, strip_smem(4), s>>>(a);
             break;
         case 8:
-            ising_strip_kernel<8><<<grid, 256, 0, s>>>(a);
+            ising_strip_kernel<8><<<grid, 256, strip_smem(8), s>>>(a);
             break;
         default:
             return cudaErrorInvalidValue;
@@ -571,9 +601,14 @@ cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, cud
 }
 
 cudaError_t occupancy_ising_strip(int *blocks_per_sm, int warps) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(ising_strip_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip_smem(4))))
+        return e;
+    if ((e = cudaFuncSetAttribute(ising_strip_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip_smem(8))))
+        return e;
     if (warps == 4)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<4>, 128, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<8>, 256, 0);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<4>, 128, strip_smem(4));
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<8>, 256, strip_smem(8));
 }
 
 cudaError_t set_ising_fused_smem(size_t smem) {
