@@ -114,6 +114,19 @@ def test_strip_kernel_rows_and_tail(rows, warps):
         assert np.array_equal(st[:, i, :], ref), i
 
 
+def test_contexts_with_different_shared_memory_needs_coexist():
+    """A context planned later with smaller work items must not lower the
+    shared-memory limit that an earlier context's launches rely on."""
+    big = make_ising([dict(L=256, beta=0.44, J=1.0, h=0.0)], max_record=4)
+    big.set_launch(0, False, 200, 256)          # (200 + 4) * 256 B > 48 KB of shared memory
+    small = make_ising([dict(L=32, beta=0.44, J=1.0, h=0.0)], max_record=4)
+    small.sweep(1)
+    s0 = lattice_np(big, 0)
+    big.sweep(1)
+    oracle.ising_sweep(s0, 0.44, 1.0, 0.0, SEED, 0, 0)
+    assert np.array_equal(lattice_np(big, 0), s0)
+
+
 def test_checkpoint_resume_bit_identical():
     lats = wl.uneven512(n=12, seed=5, emin=4, emax=8)
     a = make_ising(lats)
