@@ -208,6 +208,31 @@ void spin_destroy(spin_ctx *ctx);
 int spin_version(void);
 
 /* ------------------------------------------------------------------------
+ * Allocation-free Ising sweep.  The paper has no counterpart: this entry point
+ * exists for callers that cannot call cudaMalloc (code running inside another
+ * framework's memory pool or allocator hook, processes whose device memory is
+ * reserved up front, embeddings that forbid allocation after start-up).
+ *
+ * Runs sweeps first_sweep .. first_sweep + n_sweeps - 1 of the Ising chain
+ * defined by (seed, lat) on the caller's int8 spins, exactly as spin_sweep
+ * would (bit-identical spins and statistics), without a context and without
+ * allocating: its scratch (second spin buffer, tables, work list, counters)
+ * is a static device array of SPIN_NOALLOC_SCRATCH_BYTES that every GPU which
+ * loads the library holds until exit.  The lattices' span (largest
+ * spin_offset + L*L) plus descriptors must fit in it, every L must be in
+ * [4, 4096] and n_lattices <= 4096; otherwise SPIN_EINVAL.
+ * d_stats: NULL or device int64 [n_sweeps][n_lattices][2] = (M, B) after
+ * each sweep.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and should come before any stream capture.
+ * Calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  Returns SPIN_OK, SPIN_EINVAL or SPIN_ECUDA.
+ * ------------------------------------------------------------------------ */
+#define SPIN_NOALLOC_SCRATCH_BYTES (16u << 20)
+int spin_ising_sweep_noalloc(uint64_t seed, int32_t n_lattices, const spin_lattice_desc *lat,
+                             void *d_spins, uint32_t first_sweep, int32_t n_sweeps,
+                             int64_t *d_stats, void *stream);
+
+/* ------------------------------------------------------------------------
  * BF16 MLP surrogate 3 -> 64 -> 64 -> 2 (ReLU) mapping (beta, J, h) to
  * (<E>/N, <M>/N).  Not in the paper.  Weights live in one device buffer
  * of spin_mlp_param_count() floats (FP32 master copy, layout W1[64][3],

@@ -73,6 +73,8 @@ _SIGS = {
     "spin_last_error": (ctypes.c_char_p, [_vp]),
     "spin_destroy": (None, [_vp]),
     "spin_version": (_i32, []),
+    "spin_ising_sweep_noalloc": (_i32, [ctypes.c_uint64, _i32, ctypes.POINTER(LatticeDesc), _vp, ctypes.c_uint32,
+                                        _i32, _vp, _vp]),
     "spin_mlp_param_count": (_i32, []),
     "spin_mlp_forward": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "spin_mlp_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),

@@ -566,6 +566,11 @@ std::string shape_key(const spin_ctx *ctx) {
 
 }  // namespace
 
+namespace spinmc {
+// Acceptance table of one Ising lattice, for the allocation-free entry point.
+void build_ising_table(const spin_lattice_desc &d, TabEntry *out) { ising_table(d, out); }
+}  // namespace spinmc
+
 extern "C" {
 
 int spin_version(void) { return 1; }
