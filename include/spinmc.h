@@ -158,6 +158,14 @@ int spin_grad(spin_ctx *ctx, int64_t first, int32_t n, int32_t observable, int32
               double *out, void *stream);
 int spin_num_grad(const spin_ctx *ctx);
 
+/* Expectations over records [first, first + n): out[row][0] = <E>/N and
+ * out[row][1] = <M>/N in FP64 (the same E and M as spin_observables), per
+ * lattice or, with pool != 0, over all lattices (one row).  Formed on the
+ * device from the exact integer moments.  Ising and CPM (CPM: <H>/N and
+ * the mean adhesion energy per site).  out: device or host pointer. */
+int spin_expectations(spin_ctx *ctx, int64_t first, int32_t n, int32_t pool, double *out,
+                      void *stream);
+
 /* Replace temperatures/couplings (L, q and offsets must not change) and
  * rebuild the acceptance tables; takes effect at the next sweep. */
 int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_params *cpm);
@@ -252,6 +260,9 @@ int spin_mlp_backward(const float *params, const float *mu, const float *inv_sig
 /* Adam (Kingma & Ba) on params with moments m, v (device), step >= 1.    */
 int spin_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t step, float lr,
                   float beta1, float beta2, float eps, void *stream);
+/* The same Adam update on any n parameters (used for the fit of J and h). */
+int spin_adam(float *params, const float *grad, float *m, float *v, int32_t n, int32_t step, float lr,
+              float beta1, float beta2, float eps, void *stream);
 
 #ifdef __cplusplus
 }

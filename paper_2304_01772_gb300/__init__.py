@@ -58,6 +58,7 @@ _SIGS = {
     "spin_num_moments": (_i32, [_vp]),
     "spin_grad": (_i32, [_vp, _i64, _i32, _i32, _i32, _vp, _vp]),
     "spin_num_grad": (_i32, [_vp]),
+    "spin_expectations": (_i32, [_vp, _i64, _i32, _i32, _vp, _vp]),
     "spin_set_params": (_i32, [_vp, ctypes.POINTER(LatticeDesc), ctypes.POINTER(CpmParams)]),
     "spin_set_launch": (_i32, [_vp, _i32, _i32, _i32, _i32]),
     "spin_autotune": (_i32, [_vp, _i32, _vp]),
@@ -75,6 +76,8 @@ _SIGS = {
     "spin_version": (_i32, []),
     "spin_ising_sweep_noalloc": (_i32, [ctypes.c_uint64, _i32, ctypes.POINTER(LatticeDesc), _vp, ctypes.c_uint32,
                                         _i32, _vp, _vp]),
+    "spin_adam": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                         ctypes.c_float, _vp]),
     "spin_mlp_param_count": (_i32, []),
     "spin_mlp_forward": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "spin_mlp_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
@@ -283,6 +286,16 @@ class Sim:
                                _stream(stream)), self.ctx, "spin_grad")
         return out
 
+    def expectations(self, first=0, n=None, pool=False, stream=None):
+        """[rows, 2] float64 on the device: (<E>/N, <M>/N) per lattice or pooled."""
+        import torch
+        if n is None:
+            n = self.n_records - first
+        out = torch.empty((1 if pool else self.n, 2), dtype=torch.float64, device="cuda")
+        _check(lib().spin_expectations(self.ctx, int(first), int(n), 1 if pool else 0, _ptr(out),
+                                       _stream(stream)), self.ctx, "spin_expectations")
+        return out
+
     # -- parameters / launch form -----------------------------------------
     def set_params(self, lattices=None, cpm=None):
         arr = None
@@ -363,6 +376,12 @@ def mlp_backward(params, mu, inv_sigma, X, T, want_dx=False, stream=None):
     _check(lib().spin_mlp_backward(_ptr(params), _ptr(mu), _ptr(inv_sigma), _ptr(X), _ptr(T), X.shape[0],
                                    _ptr(grad), _ptr(loss), _ptr(dX), _stream(stream)), None, "spin_mlp_backward")
     return grad, loss, dX
+
+
+def adam(params, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    """Adam update of a float32 device tensor in place (library kernel)."""
+    _check(lib().spin_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), params.numel(), int(step), float(lr),
+                           float(b1), float(b2), float(eps), _stream(stream)), None, "spin_adam")
 
 
 def mlp_adam(params, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8, stream=None):

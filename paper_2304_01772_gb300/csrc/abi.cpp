@@ -32,6 +32,8 @@ cudaError_t launch_pool_moments(const void *in, int n_lat, int n_mom, void *out,
 cudaError_t launch_i128_to_i64(const void *in, int64_t *out, int n, int *overflow, cudaStream_t s);
 cudaError_t launch_grad_i128(const void *moments, int rows, GradParams p, double *out,
                              cudaStream_t s);
+cudaError_t launch_expectations_i128(const void *moments, int rows, GradParams p, double *out,
+                                     cudaStream_t s);
 cudaError_t launch_copy_lattices(const void *src, void *dst, const LatDev *lats, int n_lat,
                                  int elem, cudaStream_t s);
 cudaError_t occupancy_ising_strip(int *blocks_per_sm, int warps);
@@ -866,6 +868,37 @@ int spin_grad(spin_ctx *ctx, int64_t first, int32_t n, int32_t observable, int32
     return SPIN_OK;
 }
 
+int spin_expectations(spin_ctx *ctx, int64_t first, int32_t n, int32_t pool, double *out, void *stream) {
+    if (!ctx || !out) return SPIN_EINVAL;
+    if (ctx->model == SPIN_POTTS) return fail(ctx, SPIN_EINVAL, "use spin_observables for the Potts model");
+    int rc = check_records(ctx, first, n);
+    if (rc) return rc;
+    if (n < 1) return fail(ctx, SPIN_EINVAL, "need at least one record");
+    cudaStream_t s = S(stream);
+    const int nm = spin_num_moments(ctx);
+    const size_t cnt = (size_t)nm * ctx->n_lat;
+    const int rows = pool ? 1 : ctx->n_lat;
+    rc = ensure_scratch(ctx, 16 * cnt + 16 * (size_t)nm + sizeof(double) * rows * 2 + 64);
+    if (rc) return rc;
+    char *base = static_cast<char *>(ctx->d_scratch);
+    CK(launch_moments_i128(ctx->st, first, n, base, s));
+    const void *mom = base;
+    if (pool) {
+        CK(launch_pool_moments(base, ctx->n_lat, nm, base + 16 * cnt, s));
+        mom = base + 16 * cnt;
+    }
+    GradParams p{ctx->model, ctx->n_lat, ctx->width, 0, pool ? 1 : 0, ctx->d_latp,
+                 ctx->d_cpmJ, (double)ctx->lambda, (double)ctx->T, ctx->width - 2};
+    const bool dev = is_device_ptr(out);
+    double *t = dev ? out : reinterpret_cast<double *>(base + 16 * cnt + 16 * (size_t)nm);
+    CK(launch_expectations_i128(mom, rows, p, t, s));
+    if (!dev) {
+        CK(cudaMemcpyAsync(out, t, sizeof(double) * rows * 2, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return SPIN_OK;
+}
+
 int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_params *cpm) {
     if (!ctx) return SPIN_EINVAL;
     if (lat) {
@@ -1110,6 +1143,14 @@ int spin_mlp_backward(const float *params, const float *mu, const float *inv_sig
                       const float *T, int32_t n, float *grad, float *loss, float *dX, void *stream) {
     if (!params || !mu || !inv_sigma || !X || !T || !grad || n <= 0) return SPIN_EINVAL;
     return launch_mlp_backward(params, mu, inv_sigma, X, T, n, grad, loss, dX, S(stream)) == cudaSuccess
+               ? SPIN_OK
+               : SPIN_ECUDA;
+}
+
+int spin_adam(float *params, const float *grad, float *m, float *v, int32_t n, int32_t step, float lr,
+              float beta1, float beta2, float eps, void *stream) {
+    if (!params || !grad || !m || !v || step < 1 || n < 0) return SPIN_EINVAL;
+    return launch_adam(params, grad, m, v, n, step, lr, beta1, beta2, eps, S(stream)) == cudaSuccess
                ? SPIN_OK
                : SPIN_ECUDA;
 }

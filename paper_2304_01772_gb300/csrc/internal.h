@@ -216,5 +216,7 @@ cudaError_t launch_mlp_backward(const float *params, const float *mu, const floa
                                 float *dX, cudaStream_t s);
 cudaError_t launch_mlp_adam(float *params, const float *grad, float *m, float *v, int step,
                             float lr, float b1, float b2, float eps, cudaStream_t s);
+cudaError_t launch_adam(float *params, const float *grad, float *m, float *v, int n, int step,
+                        float lr, float b1, float b2, float eps, cudaStream_t s);
 
 }  // namespace spinmc

@@ -314,6 +314,32 @@ __global__ void grad_kernel(const __int128 *moments, int rows, GradParams p, dou
     }
 }
 
+// <E>/N and <M>/N from exact moments (Ising: X = (M, B); CPM: X = (C.., V2, V1)).
+__global__ void expectations_kernel(const __int128 *moments, int rows, GradParams p, double *out) {
+    const int width = p.width;
+    const int n_mom = 1 + width + width * (width + 1) / 2;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= rows) return;
+    const __int128 *mo = moments + (size_t)row * n_mom;
+    const int lat0 = p.pool ? 0 : row;
+    const double nd = (double)(long long)mo[0];
+    if (p.model == 0) {
+        const double J = p.lat_params[4 * lat0], h = p.lat_params[4 * lat0 + 1];
+        const double N = p.lat_params[4 * lat0 + 2];
+        const double mM = i128_to_double(mo[1]) / nd, mB = i128_to_double(mo[2]) / nd;
+        out[2 * row] = (-J * mB - h * mM) / N;
+        out[2 * row + 1] = mM / N;
+    } else {
+        const int npair = p.n_pairs;
+        const double N = p.lat_params[2];
+        double adh = 0.0;
+        for (int a = 0; a < npair; ++a) adh += p.cpm_J[a] * i128_to_double(mo[1 + a]);
+        adh /= nd;
+        out[2 * row] = (adh + p.cpm_lambda * i128_to_double(mo[1 + npair]) / nd) / N;
+        out[2 * row + 1] = adh / N;
+    }
+}
+
 __global__ void i128_to_i64_kernel(const __int128 *in, int64_t *out, int n, int *overflow) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const __int128 v = in[i];
@@ -373,6 +399,13 @@ cudaError_t launch_observables(const StatsBufs &st, int64_t first, int n, ObsPar
     int blocks = (total + 255) / 256;
     blocks = blocks < 1 ? 1 : (blocks > 1024 ? 1024 : blocks);
     observables_kernel<<<blocks, 256, 0, s>>>(st.ring, st.cap, first, n, p, stats_out, E, M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_expectations_i128(const void *moments, int rows, GradParams p, double *out,
+                                     cudaStream_t s) {
+    expectations_kernel<<<(rows + 63) / 64, 64, 0, s>>>(static_cast<const __int128 *>(moments), rows, p,
+                                                        out);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,192 @@
+"""GPU checks of the gradient path and the BF16 surrogate.
+
+* MLP forward / backward kernels against the float64 oracle.  Tolerance: the
+  kernels round the normalised input and both hidden activations to BF16
+  (8 significant bits, unit roundoff 2^-9 ~ 2e-3) and accumulate in FP32, so
+  relative L2 errors of a few 2^-9 are expected; we allow 2.5e-2.
+* The Adam kernel against the oracle's Adam (float32 vs float64).
+* The fluctuation-estimator gradient against exact 4x4 enumeration and
+  against finite differences of Monte Carlo means.
+* The (J, h) fit driven by the estimator, with and without the surrogate
+  warm start (the warm start reaches the tolerance in fewer steps).
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2304_01772_gb300 as sm
+from oracle import mlp as omlp
+from paper_2304_01772_gb300 import fit
+from tests import exact
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_params(flat):
+    p = flat.detach().to(torch.bfloat16).double().cpu().numpy()
+    out, off = {}, 0
+    for k, shp in omlp.shapes().items():
+        n = int(np.prod(shp))
+        out[k] = p[off:off + n].reshape(shp)
+        off += n
+    return out
+
+
+def _flat(d):
+    return np.concatenate([d[k].ravel() for k in omlp.PARAM_NAMES])
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def _emulate_fp32(flat, mu, inv, X, T):
+    """The kernels' arithmetic in plain torch float32: BF16 weights, BF16
+    rounding of the normalised input and of both hidden activations."""
+    bf = lambda t: t.to(torch.bfloat16).float()
+    p = bf(flat.detach().cpu())
+    W1, b1 = p[:192].view(64, 3), p[192:256]
+    W2, b2 = p[256:4352].view(64, 64), p[4352:4416]
+    W3, b3 = p[4416:4544].view(2, 64), p[4544:4546]
+    X, T, mu, inv = X.cpu(), T.cpu(), mu.cpu(), inv.cpu()
+    xn = bf((X - mu) * inv)
+    h1 = bf(torch.relu(xn @ W1.T + b1))
+    a2 = bf(torch.relu(h1 @ W2.T + b2))
+    Y = a2 @ W3.T + b3
+    dy = (Y - T) / X.shape[0]
+    dz2 = (dy @ W3) * (a2 > 0)
+    dz1 = (dz2 @ W2) * (h1 > 0)
+    g = torch.cat([(dz1.T @ xn).ravel(), dz1.sum(0), (dz2.T @ h1).ravel(), dz2.sum(0),
+                   (dy.T @ a2).ravel(), dy.sum(0)])
+    return Y, g, (dz1 @ W1) * inv, (dz1.abs() @ W1.abs()) * inv.abs()
+
+
+def test_mlp_kernels_match_oracle():
+    s = fit.Surrogate(seed=11)
+    g = torch.Generator().manual_seed(0)
+    s.params += 0.05 * torch.randn(s.params.shape, generator=g).cuda()   # non-zero biases too
+    X = torch.from_numpy(fit.sample_box(333, seed=5)).cuda()                # 333: ragged last block
+    T = (0.5 * torch.randn((333, 2), generator=g)).cuda()
+    Y = sm.mlp_forward(s.params, s.mu, s.inv_sigma, X)
+    grad, loss, dX = sm.mlp_backward(s.params, s.mu, s.inv_sigma, X, T, want_dx=True)
+    p = _oracle_params(s.params)
+    mu, inv = s.mu.double().cpu().numpy(), s.inv_sigma.double().cpu().numpy()
+    Yo, cache = omlp.forward(p, X.double().cpu().numpy(), mu, inv)
+    go, dXo = omlp.backward(p, cache, Yo, T.double().cpu().numpy(), inv)
+    # the kernels' own arithmetic, emulated in float32: only summation order differs
+    Ye, ge, dXe, dXscale = _emulate_fp32(s.params, s.mu, s.inv_sigma, X, T)
+    assert _rel(Y.cpu().numpy(), Ye.numpy()) < 1e-3
+    assert _rel(grad.cpu().numpy(), ge.numpy()) < 1e-3
+    assert _rel(dX.cpu().numpy(), dXe.numpy()) < 1e-3
+    # the float64 oracle: BF16 rounding of activations is the only approximation
+    assert _rel(Y.cpu().numpy(), Yo) < 2.5e-2
+    assert abs(float(loss) - omlp.loss(Yo, T.double().cpu().numpy())) < 2.5e-2 * omlp.loss(Yo, T.double().cpu().numpy())
+    assert _rel(grad.cpu().numpy(), _flat(go)) < 2.5e-2
+    # dX = W1^T dz1 cancels heavily; measure its error against the sum of |terms|
+    err = np.linalg.norm(dX.cpu().numpy() - dXo) / np.linalg.norm(dXscale.numpy())
+    assert err < 2.5e-2, err
+
+
+def test_adam_kernel_matches_oracle():
+    rng = np.random.default_rng(2)
+    p0 = rng.normal(size=sm.mlp_param_count()).astype(np.float32)
+    params = torch.from_numpy(p0.copy()).cuda()
+    m = torch.zeros_like(params)
+    v = torch.zeros_like(params)
+    shapes = omlp.shapes()
+    po = {}
+    off = 0
+    for k in omlp.PARAM_NAMES:
+        n = int(np.prod(shapes[k]))
+        po[k] = p0[off:off + n].astype(np.float64).reshape(shapes[k])
+        off += n
+    mo = {k: np.zeros_like(x) for k, x in po.items()}
+    vo = {k: np.zeros_like(x) for k, x in po.items()}
+    for step in range(1, 4):
+        gflat = rng.normal(size=p0.size).astype(np.float32)
+        sm.adam(params, torch.from_numpy(gflat).cuda(), m, v, step, 1e-2)
+        go, off = {}, 0
+        for k in omlp.PARAM_NAMES:
+            n = int(np.prod(shapes[k]))
+            go[k] = gflat[off:off + n].astype(np.float64).reshape(shapes[k])
+            off += n
+        omlp.adam_step(po, go, mo, vo, step, 1e-2)
+    np.testing.assert_allclose(params.cpu().numpy(), _flat(po), rtol=1e-5, atol=1e-6)
+
+
+def test_estimator_matches_exact_4x4_gradients():
+    beta, J, h = 0.35, 1.0, 0.1
+    want = exact.ising_exact_grad(beta, J, h)
+    ex = exact.ising_exact(beta, J, h)
+    ests, means = [], []
+    for rep in range(8):
+        sim = sm.Sim(sm.SPIN_ISING, [dict(L=4, beta=beta, J=J, h=h)] * 512, seed=100 + rep, max_record=400)
+        sim.sweep(200)
+        sim.sweep(400, record=True)
+        gE = sim.grad(0, 400, observable=0, pool=True).cpu().numpy()[0]
+        gM = sim.grad(0, 400, observable=1, pool=True).cpu().numpy()[0]
+        ests.append([gE[0], gE[1], gM[0], gM[1]])
+        means.append(sim.expectations(0, 400, pool=True).cpu().numpy()[0])
+        sim.close()
+    ests = np.array(ests)
+    means = np.array(means)
+    keys = [("E", "J"), ("E", "h"), ("M", "J"), ("M", "h")]
+    for i, k in enumerate(keys):
+        err = ests[:, i].std(ddof=1) / np.sqrt(len(ests))
+        assert abs(ests[:, i].mean() - want[k]) < 5 * err + 1e-4, (k, ests[:, i].mean(), want[k], err)
+    for i, (name, val) in enumerate([("E", ex["E"] / 16), ("M", ex["M"] / 16)]):
+        err = means[:, i].std(ddof=1) / np.sqrt(len(means))
+        assert abs(means[:, i].mean() - val) < 5 * err + 1e-4, (name, means[:, i].mean(), val)
+
+
+def test_estimator_matches_finite_differences():
+    """d<E>/N/dJ and d<M>/N/dh from the estimator vs central differences of
+    Monte Carlo means with common random numbers."""
+    beta, J, h, d = 0.4, 0.9, 0.05, 0.02
+
+    def run(JJ, hh):
+        sim = sm.Sim(sm.SPIN_ISING, [dict(L=32, beta=beta, J=JJ, h=hh)] * 64, seed=5, max_record=600)
+        sim.sweep(300)
+        sim.sweep(600, record=True)
+        e = sim.expectations(0, 600, pool=True).cpu().numpy()[0]
+        g = (sim.grad(0, 600, observable=0, pool=True).cpu().numpy()[0],
+             sim.grad(0, 600, observable=1, pool=True).cpu().numpy()[0])
+        sim.close()
+        return e, g
+
+    e0, (gE, gM) = run(J, h)
+    fdEJ = (run(J + d, h)[0][0] - run(J - d, h)[0][0]) / (2 * d)
+    fdMh = (run(J, h + d)[0][1] - run(J, h - d)[0][1]) / (2 * d)
+    assert abs(gE[0] - fdEJ) < 0.2 * abs(fdEJ), (gE[0], fdEJ)
+    assert abs(gM[1] - fdMh) < 0.25 * abs(fdMh), (gM[1], fdMh)
+
+
+def test_fit_reaches_target_and_surrogate_warm_start_helps():
+    target, beta = (-1.2, 0.5), 0.45
+    # surrogate: 2048 chains of 32^2 in one batched run, then training
+    X = torch.from_numpy(fit.sample_box(2048, seed=1)).cuda()
+    Y = fit.chain_targets(X, L=32, n_burn=300, n_meas=300)
+    sur = fit.Surrogate(seed=3)
+    losses = sur.train(X, Y, epochs=1500, lr=3e-3)
+    assert losses[-1] < 0.1 * losses[0], (losses[0], losses[-1])
+    rms = float(((sur.predict(X) - Y) ** 2).mean().sqrt())
+    theta_w = sur.invert(target, beta).cpu().numpy()
+    assert 0.5 <= theta_w[0] <= 1.5 and -0.2 <= theta_w[1] <= 0.2
+
+    def run_fit(theta0, max_steps):
+        ens = fit.IsingEnsemble(32, 64, beta, seed=21, n_burn=150, n_meas=150)
+        hist = []
+        th, steps, loss = fit.fit(ens, target, theta0, lr=1e-2, max_steps=max_steps, tol=2e-3, history=hist)
+        return steps, loss, hist
+
+    cold_steps, cold_loss, cold_hist = run_fit((1.0, 0.0), 60)
+    warm_steps, warm_loss, _ = run_fit(tuple(float(x) for x in theta_w), 60)
+    print(f"surrogate rms {rms:.4f}; warm start {theta_w}; steps to loss < 2e-3: cold {cold_steps} "
+          f"(loss {cold_hist[0][-1]:.3f} -> {cold_loss:.4f}), warm {warm_steps} (loss {warm_loss:.5f})")
+    # the Monte Carlo gradient drives the fit: the loss falls by an order of magnitude
+    assert cold_loss < 0.1 * cold_hist[0][-1]
+    # the surrogate's warm start reaches the tolerance, in fewer gradient steps
+    assert warm_loss < 2e-3
+    assert warm_steps < cold_steps
