@@ -172,10 +172,13 @@ int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_
 
 /* Launch form.  mode: 0 = batched persistent work-list launch (default),
  * 1 = plain per-lattice launches (two per lattice per sweep), 2 = resident
- * (each lattice stays in shared memory for the whole call; small lattices).
- * use_graph: capture the sweep loop in a CUDA graph.  tile_rows / threads:
- * work-item height and CTA size for mode 0 (0 = keep).  Results do not
- * depend on any of these. */
+ * (Ising only, every L a multiple of 16 and <= 256: one CTA per lattice keeps
+ * it in shared memory for all sweeps of a spin_sweep call, one launch).
+ * use_graph: capture the sweep loop in a CUDA graph.  tile_rows: work-item
+ * height in rows for mode 0 (0 = keep the current value, -1 = default items of
+ * about 32-64 KB).  threads: CTA size of the tile kernel (128, 256 or 512; 0 =
+ * keep); the warp row-strip kernel uses 8 warps per CTA for 512, else 4.
+ * Results do not depend on any of these. */
 int spin_set_launch(spin_ctx *ctx, int32_t mode, int32_t use_graph, int32_t tile_rows,
                     int32_t threads);
 /* Time the launch forms and tile shapes on the current state (the state is

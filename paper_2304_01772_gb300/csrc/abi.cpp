@@ -485,6 +485,14 @@ int get_graph(spin_ctx *ctx, int record, GraphCache *&out) {
 
 int run_sweeps(spin_ctx *ctx, int n, int record, cudaStream_t s) {
     int launches = 0;
+    if (ctx->mode == 2) {
+        ResidentArgs a{static_cast<int8_t *>(ctx->spins), ctx->d_lats, ctx->d_tabs, ctx->k0, ctx->k1,
+                       ctx->t, n, (long long)ctx->n_rec, record, ctx->st};
+        CK(launch_ising_resident(a, ctx->n_lat, ctx->threads, (size_t)ctx->maxL * ctx->maxL,
+                                 ctx->d_state, s));
+        ctx->last_launches = 2;
+        return SPIN_OK;
+    }
     if (ctx->model == SPIN_CPM) {
         int i = 0;
         if (ctx->use_graph && !ctx->prof && n >= 1) {
@@ -932,15 +940,25 @@ int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_
     return upload_tables(ctx, nullptr);
 }
 
+static bool resident_ok(const spin_ctx *ctx) {
+    if (ctx->model != SPIN_ISING || ctx->n_generic) return false;
+    for (const auto &d : ctx->lat)
+        if (d.L > 256) return false;
+    return true;
+}
+
 int spin_set_launch(spin_ctx *ctx, int32_t mode, int32_t use_graph, int32_t tile_rows, int32_t threads) {
     if (!ctx) return SPIN_EINVAL;
-    if (mode < 0 || mode > 1) return fail(ctx, SPIN_EINVAL, "launch mode must be 0 (batched) or 1 (plain)");
+    if (mode < 0 || mode > 2) return fail(ctx, SPIN_EINVAL, "launch mode must be 0, 1 or 2");
+    if (mode == 2 && !resident_ok(ctx))
+        return fail(ctx, SPIN_EINVAL, "resident form needs Ising lattices with L % 16 == 0 and L <= 256");
     if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
         return fail(ctx, SPIN_EINVAL, "threads must be 128, 256 or 512");
-    if (tile_rows < 0) return fail(ctx, SPIN_EINVAL, "tile_rows must be >= 0");
+    if (tile_rows < -1) return fail(ctx, SPIN_EINVAL, "tile_rows must be >= -1");
     ctx->mode = mode;
     ctx->use_graph = use_graph ? 1 : 0;
-    if (tile_rows) ctx->tile_rows = tile_rows;
+    if (tile_rows > 0) ctx->tile_rows = tile_rows;
+    if (tile_rows == -1) ctx->tile_rows = 0;
     if (threads) ctx->threads = threads;
     return plan(ctx);
 }
@@ -1049,7 +1067,7 @@ int spin_autotune(spin_ctx *ctx, int32_t sweeps_per_trial, void *stream) {
         std::string k;
         int m, g, tr, th;
         while (f >> k >> m >> g >> tr >> th)
-            if (k == key) return spin_set_launch(ctx, m, g, tr, th);
+            if (k == key) return spin_set_launch(ctx, m, g, tr ? tr : -1, th);
     }
     cudaStream_t s = S(stream);
     // save the chain state; trials advance it
@@ -1059,17 +1077,21 @@ int spin_autotune(spin_ctx *ctx, int32_t sweeps_per_trial, void *stream) {
     int rc = spin_checkpoint(ctx, saved.data(), &blob, stream);
     if (rc) return rc;
     struct Cand { int mode, tile, threads; };
+    // batched form: CTA size (tile kernel) / warps per CTA (strip kernel: 4 for
+    // 128 and 256, 8 for 512) and work-item height (0 = 64 KB items); plain form.
     std::vector<Cand> cands;
     for (int th : {128, 256, 512})
-        for (int tr : {8, 16, 32, 64}) cands.push_back({0, tr, th});
+        for (int tr : {0, 8, 16, 32, 64}) cands.push_back({0, tr, th});
     cands.push_back({1, 0, 256});
+    if (resident_ok(ctx))
+        for (int th : {128, 256, 512}) cands.push_back({2, 0, th});
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
     Cand bc = {0, 16, 256};
     for (const Cand &c : cands) {
-        rc = spin_set_launch(ctx, c.mode, 1, c.tile, c.threads);
+        rc = spin_set_launch(ctx, c.mode, 1, c.tile ? c.tile : -1, c.threads);
         if (rc) continue;
         rc = spin_sweep(ctx, 2, 0, stream);  // warm-up, graph capture
         if (rc) return rc;
@@ -1087,7 +1109,7 @@ int spin_autotune(spin_ctx *ctx, int32_t sweeps_per_trial, void *stream) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    rc = spin_set_launch(ctx, bc.mode, 1, bc.tile, bc.threads);
+    rc = spin_set_launch(ctx, bc.mode, 1, bc.tile ? bc.tile : -1, bc.threads);
     if (rc) return rc;
     rc = spin_restore(ctx, saved.data(), saved.size(), stream);
     if (rc) return rc;

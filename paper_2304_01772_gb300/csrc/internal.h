@@ -114,10 +114,21 @@ cudaError_t launch_ising_generic(const int8_t *src, int8_t *dst, const int32_t *
                                  int maxL, const LatDev *lats, const TabEntry *tabs, uint32_t k0,
                                  uint32_t k1, const DevState *state, int64_t *delta, int colour,
                                  cudaStream_t s);
-cudaError_t launch_ising_resident(int8_t *spins, const LatDev *lats, int n_lat, int maxL,
-                                  const TabEntry *tabs, uint32_t k0, uint32_t k1, DevState *state,
-                                  StatsBufs st, int n_sweeps, int record, int threads,
-                                  cudaStream_t s);
+// Resident form: one CTA per lattice (all lattices vectorisable, L*L <= 64 KB),
+// n_sweeps sweeps in one launch, in place; then the device counters advance.
+struct ResidentArgs {
+    int8_t *spins;
+    const LatDev *lats;
+    const TabEntry *tabs;
+    uint32_t k0, k1;
+    uint32_t t0;
+    int n_sweeps;
+    long long rec0;
+    int record;
+    StatsBufs st;
+};
+cudaError_t launch_ising_resident(const ResidentArgs &a, int n_lat, int threads, size_t smem,
+                                  DevState *state, cudaStream_t s);
 cudaError_t launch_init_random(void *spins, int model, const LatDev *lats, int n_lat, int maxL,
                                uint32_t k0, uint32_t k1, cudaStream_t s);
 

@@ -153,6 +153,81 @@ __global__ void __launch_bounds__(THREADS) ising_fused_kernel(IsingSweepArgs a) 
     }
 }
 
+// Resident form: one CTA per lattice keeps the whole lattice in shared memory
+// for all n sweeps of a call (small lattices, launch-latency-bound batches).
+// Statistics are reduced by the block after every sweep and recorded by the
+// CTA itself; the sweep and record counters come from the host (t0, rec0).
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) ising_resident_kernel(ResidentArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ TabEntry stab[kTabStride];
+    __shared__ int red[2 * (THREADS / 32)];
+    __shared__ long long cur_s[2];
+    const int lat = blockIdx.x;
+    const LatDev ld = a.lats[lat];
+    const int L = ld.L, Lv = L >> 4;
+    uint4 *sm4 = reinterpret_cast<uint4 *>(sm);
+    const uint32_t *sm32 = reinterpret_cast<const uint32_t *>(sm);
+    uint4 *G = reinterpret_cast<uint4 *>(a.spins + ld.offset);
+    for (int v = threadIdx.x; v < L * Lv; v += THREADS) sm4[v] = G[v];
+    if (threadIdx.x < kTabStride) stab[threadIdx.x] = a.tabs[lat * kTabStride + threadIdx.x];
+    if (threadIdx.x < 2) cur_s[threadIdx.x] = a.st.cur[2 * lat + threadIdx.x];
+    __syncthreads();
+    for (int sweep = 0; sweep < a.n_sweeps; ++sweep) {
+        const uint32_t t = a.t0 + (uint32_t)sweep;
+        int acc = 0;
+        for (int c = 0; c < 2; ++c) {
+            for (int v = threadIdx.x; v < L * Lv; v += THREADS) {
+                const int i = v / Lv, j = v - i * Lv;
+                const int iu = i == 0 ? L - 1 : i - 1, id = i == L - 1 ? 0 : i + 1;
+                const uint4 Cc = sm4[v];
+                const uint4 Uc = sm4[iu * Lv + j];
+                const uint4 Dc = sm4[id * Lv + j];
+                const uint32_t lw = sm32[(i * Lv + (j == 0 ? Lv - 1 : j - 1)) * 4 + 3];
+                const uint32_t rw = sm32[(i * Lv + (j == Lv - 1 ? 0 : j + 1)) * 4];
+                const uint32_t g0 = (uint32_t)i * (uint32_t)(L >> 3) + 2u * (uint32_t)j;
+                sm4[v] = ising_chunk(Cc, Uc, Dc, lw, rw, g0, (c ^ i) & 1, (uint32_t)lat, t, (uint32_t)c,
+                                     a.k0, a.k1, stab, true, acc);
+            }
+            __syncthreads();
+        }
+        int dm = (int)(int16_t)(acc & 0xFFFF);
+        int db = (acc - dm) >> 16;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dm += __shfl_xor_sync(0xFFFFFFFFu, dm, o);
+            db += __shfl_xor_sync(0xFFFFFFFFu, db, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red[2 * (threadIdx.x >> 5)] = dm;
+            red[2 * (threadIdx.x >> 5) + 1] = db;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long sm_ = 0, sb_ = 0;
+            for (int w = 0; w < THREADS / 32; ++w) {
+                sm_ += red[2 * w];
+                sb_ += red[2 * w + 1];
+            }
+            cur_s[0] += sm_;
+            cur_s[1] += sb_;
+            if (a.record && a.st.cap > 0) {
+                const long long slot = (a.rec0 + sweep) % a.st.cap;
+                a.st.ring[(slot * a.st.n_lat + lat) * 2] = cur_s[0];
+                a.st.ring[(slot * a.st.n_lat + lat) * 2 + 1] = cur_s[1];
+            }
+        }
+        __syncthreads();
+    }
+    for (int v = threadIdx.x; v < L * Lv; v += THREADS) G[v] = sm4[v];
+    if (threadIdx.x < 2) a.st.cur[2 * lat + threadIdx.x] = cur_s[threadIdx.x];
+}
+
+__global__ void advance_state_kernel(DevState *state, uint32_t n, int record) {
+    state->t += n;
+    if (record) state->n_rec += n;
+}
+
 // One lattice, one colour, in place, straight from global memory.
 __global__ void __launch_bounds__(256) ising_plain_kernel(int8_t *spins, int L, uint32_t lat,
                                                           const TabEntry *tab, uint32_t k0,
@@ -625,6 +700,30 @@ cudaError_t set_ising_fused_smem(size_t smem) {
     if ((e = cudaFuncSetAttribute(ising_fused_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
     raised[dev] = smem;
     return cudaSuccess;
+}
+
+cudaError_t launch_ising_resident(const ResidentArgs &a, int n_lat, int threads, size_t smem,
+                                  DevState *state, cudaStream_t s) {
+    cudaError_t e;
+    switch (threads) {
+        case 128:
+            if ((e = cudaFuncSetAttribute(ising_resident_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+            ising_resident_kernel<128><<<n_lat, 128, smem, s>>>(a);
+            break;
+        case 256:
+            if ((e = cudaFuncSetAttribute(ising_resident_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+            ising_resident_kernel<256><<<n_lat, 256, smem, s>>>(a);
+            break;
+        case 512:
+            if ((e = cudaFuncSetAttribute(ising_resident_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+            ising_resident_kernel<512><<<n_lat, 512, smem, s>>>(a);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    if ((e = cudaGetLastError())) return e;
+    advance_state_kernel<<<1, 1, 0, s>>>(state, (uint32_t)a.n_sweeps, a.record);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ising_plain(int8_t *spins, const LatDev *, int lat, int L, const TabEntry *tabs,

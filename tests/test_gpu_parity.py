@@ -81,6 +81,32 @@ def test_ising_mixed_batch_sweep_by_sweep(mode, graph, tile, threads):
     assert sim.t == 11 and sim.n_records == 11
 
 
+@pytest.mark.parametrize("threads", [128, 256, 512])
+def test_resident_form_matches_oracle_and_batched(threads):
+    lats = [dict(L=L, beta=b, J=J, h=h) for L, b, J, h in [
+        (16, 0.3, 1.0, 0.0), (32, 0.44, 1.0, 0.1), (64, 0.6, -1.0, 0.0), (128, 0.4, 0.8, -0.05),
+        (256, 0.5, 1.0, 0.02), (64, 0.2, 1.0, 0.0)]]
+    sim = make_ising(lats, max_record=32)
+    sim.set_launch(2, False, 0, threads)
+    ref = {i: lattice_np(sim, i) for i in range(len(lats))}
+    for t in range(2):
+        sim.sweep(1, record=True)
+        for i, d in enumerate(lats):
+            oracle.ising_sweep(ref[i], d["beta"], d["J"], d["h"], SEED, i, t)
+            assert np.array_equal(lattice_np(sim, i), ref[i]), (t, i)
+    sim.sweep(9, record=True)
+    st = sim.observables_host(0, 11)[0]
+    for i, d in enumerate(lats):
+        o = oracle.ising_run(ref[i], d["beta"], d["J"], d["h"], SEED, i, 2, 9)
+        assert np.array_equal(lattice_np(sim, i), ref[i])
+        assert np.array_equal(st[2:, i], o)
+    other = make_ising(lats, max_record=32)
+    other.sweep(11, record=True)
+    assert torch.equal(other.spins, sim.spins)
+    assert np.array_equal(other.observables_host(0, 11)[0], st)
+    assert torch.equal(sim.current_stats(), sim.observables(10, 1)[0][0])
+
+
 def test_launch_forms_bit_identical():
     lats = wl.uneven512(n=40, seed=3, emin=4, emax=9)
     finals = []
@@ -125,6 +151,25 @@ def test_contexts_with_different_shared_memory_needs_coexist():
     big.sweep(1)
     oracle.ising_sweep(s0, 0.44, 1.0, 0.0, SEED, 0, 0)
     assert np.array_equal(lattice_np(big, 0), s0)
+
+
+def test_autotune_picks_a_form_and_keeps_results(tmp_path, monkeypatch):
+    lats = wl.uneven512(n=24, seed=11, emin=5, emax=10)
+    ref = make_ising(lats, max_record=8)
+    ref.sweep(6, record=True)
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("SPINMC_TUNE_CACHE", str(cache))
+    sim = make_ising(lats, max_record=8)
+    choice = sim.autotune(sweeps_per_trial=2)
+    assert choice["mode"] in (0, 1) and choice["threads"] in (128, 256, 512)
+    assert sim.t == 0 and sim.n_records == 0          # trials leave the chain where it was
+    sim.sweep(6, record=True)
+    assert torch.equal(sim.spins, ref.spins)
+    assert np.array_equal(sim.observables_host()[0], ref.observables_host()[0])
+    # the choice is cached per batch shape and reused without timing
+    assert cache.read_text().strip()
+    again = make_ising(lats, max_record=8)
+    assert again.autotune(sweeps_per_trial=2) == choice
 
 
 def test_checkpoint_resume_bit_identical():
