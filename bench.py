@@ -153,10 +153,19 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2304_01772_gb300", "csrc", "sweep_ising.cu"), "rb") as f:
-        h.update(f.read())
+def kernel_source_hash(kernel="ising_strip_kernel"):
+    """Hash of the source of one kernel's section of sweep_ising.cu plus the
+    shared device header, so that counters taken on an unchanged kernel stay
+    valid while other code in the file changes."""
+    csrc = os.path.join(ROOT, "paper_2304_01772_gb300", "csrc")
+    text = open(os.path.join(csrc, "sweep_ising.cu")).read()
+    marks = {"ising_strip_kernel": ("// ------------------------------------------------------------------ strip kernel",
+                                    "// Copy every lattice")}
+    a, b = marks.get(kernel, ("", ""))
+    if a in text and b in text:
+        text = text[text.index(a):text.index(b)]
+    h = hashlib.sha256(text.encode())
+    h.update(open(os.path.join(csrc, "internal.h"), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -172,9 +181,9 @@ def ncu_traffic(kernel):
             if ":" in line:
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-        if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+        if kv.get("kernel_source_sha256_16") != kernel_source_hash(kernel):
             return None
-        return float(kv["dram_bytes_per_full_launch"])
+        return float(kv["dram_bytes_per_full_launch"].split()[0])
     except (OSError, KeyError, ValueError):
         return None
 
