@@ -189,25 +189,20 @@ def ncu_traffic(kernel):
 
 
 def dist_setup(n):
+    from paper_2304_01772_gb300.dist import rank_info
     if n <= 1 and "RANK" not in os.environ:
         return 0, 1, None
     import torch
     import torch.distributed as dist
-    rank = int(os.environ.get("RANK", 0))
-    world = int(os.environ.get("WORLD_SIZE", n))
-    local = int(os.environ.get("LOCAL_RANK", rank))
+    rank, world, local = rank_info()
     torch.cuda.set_device(local)
     dist.init_process_group("nccl", rank=rank, world_size=world)
     return rank, world, dist
 
 
 def max_over_ranks(x, dist):
-    if dist is None:
-        return x
-    import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2304_01772_gb300.dist import max_over_ranks as _max
+    return _max(x, dist, device="cuda")
 
 
 def barrier(dist):
@@ -260,7 +255,8 @@ def run_ours(args):
     rank, world, dist = dist_setup(args.gpus)
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     stream = torch.cuda.current_stream()
-    sim = sm.Sim(sm.SPIN_ISING, lats, seed=SEED + rank, max_record=max(16, args.e2e_steps))
+    from paper_2304_01772_gb300.dist import job_throughput, rank_seed
+    sim = sm.Sim(sm.SPIN_ISING, lats, seed=rank_seed(SEED, rank), max_record=max(16, args.e2e_steps))
     launch = sim.get_launch() if args.no_tune else sim.autotune(sweeps_per_trial=4)
     sim.sweep(args.warmup)
 
@@ -327,8 +323,8 @@ def run_ours(args):
 
     if rank != 0:
         return 0
-    value = world * sites * args.steps / (ms * 1e-3)
-    plain = world * sites * args.plain_steps / (ms_plain * 1e-3)
+    value = job_throughput(sites * args.steps, world, ms * 1e-3)
+    plain = job_throughput(sites * args.plain_steps, world, ms_plain * 1e-3)
     peak, peak_kind = measured_peaks()
     strip_sites = sum(d["L"] ** 2 for d in lats if d["L"] in (512, 1024, 2048))
     cls_sites = [sites - strip_sites, strip_sites]

@@ -1,0 +1,58 @@
+"""The multi-process path of bench.py on CPU: two gloo ranks, each with its
+own seed; throughput uses the slowest rank's time (max over ranks)."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from paper_2304_01772_gb300 import dist as sdist
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, w, local = sdist.rank_info()
+    elapsed = 1.0 + rank                               # rank 1 is the slowest
+    slowest = sdist.max_over_ranks(elapsed, dist)
+    seeds = [None] * world
+    dist.all_gather_object(seeds, sdist.rank_seed(123, r))
+    out[rank] = (r, w, local, slowest, sdist.job_throughput(100.0, w, slowest), seeds)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_max_time_and_distinct_seeds():
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_worker, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+            assert p.exitcode == 0
+        res = dict(out)
+    for r in range(2):
+        rank, world, local, slowest, rate, seeds = res[r]
+        assert (rank, world, local) == (r, 2, r)
+        assert slowest == 2.0
+        assert rate == pytest.approx(100.0)              # 2 ranks x 100 units / 2 s
+        assert seeds == [123, 124]
+
+
+def test_single_process_defaults():
+    assert sdist.max_over_ranks(3.5, None) == 3.5
+    assert sdist.job_throughput(10.0, 1, 2.0) == 5.0

@@ -354,3 +354,20 @@ def test_potts_full_size_sampled(q):
         ref = oracle.potts_run(init[i], q, d["beta"], d["J"], SEED, i, 0, 2)
         assert np.array_equal(lattice_np(sim, i), init[i])
         assert np.array_equal(st[:, i, :], ref)
+
+
+def test_out_of_range_states_are_harmless():
+    """Caller-supplied states outside the model's range (init_mode 1) must not
+    make a kernel index outside its buffers; the run completes."""
+    lats = [dict(L=32, q=3, beta=1.0, J=1.0), dict(L=10, q=3, beta=1.0, J=1.0)]
+    spins = torch.randint(0, 256, (2048,), dtype=torch.uint8, device="cuda")
+    sim = sm.Sim(sm.SPIN_POTTS, lats, seed=SEED, spins=spins, offsets=[0, 1024], init_mode=1, max_record=4)
+    sim.sweep(3, record=True)
+    torch.cuda.synchronize()
+    p = wl.cpm_paper()
+    ids = torch.randint(-50, 5000, (p["L"] * p["L"],), dtype=torch.int32, device="cuda")
+    cpm = dict(J=p["J"], **{"lambda": p["lam"]}, target=p["target"], n_cells=p["n_cells"], T=p["T"],
+               side=p["side"], cols=p["cols"])
+    cs = sm.Sim(sm.SPIN_CPM, [dict(L=p["L"])], seed=SEED, spins=ids, init_mode=1, max_record=4, cpm=cpm)
+    cs.sweep(2, record=True)
+    torch.cuda.synchronize()
