@@ -26,7 +26,7 @@ struct Item {
 
 // Acceptance table entry: accept a draw u iff u <= thr; `delta` is the packed
 // change of the statistics on acceptance (Ising: dB * 65536 + dM; Potts: dB_eq).
-struct TabEntry {
+struct __align__(8) TabEntry {
     uint32_t thr;
     int32_t delta;
 };

@@ -55,12 +55,10 @@ __device__ __forceinline__ uint4 ising_chunk(uint4 C, uint4 U, uint4 D, uint32_t
         for (int bb = 0; bb < 2; ++bb) {
             const int sh = 8 * (p + 2 * bb);
             const uint32_t off = (key4 >> sh) & 0xFFu;
-            const TabEntry e =
-                *reinterpret_cast<const TabEntry *>(reinterpret_cast<const char *>(stab) + off);
-            if (rnd[2 * i + bb] <= e.thr) {
-                nw ^= 0xFEu << sh;
-                if (count) acc += e.delta;
-            }
+            const uint2 e = *reinterpret_cast<const uint2 *>(reinterpret_cast<const char *>(stab) + off);
+            const uint32_t m = 0u - (uint32_t)(rnd[2 * i + bb] <= e.x);   // branch-free acceptance
+            nw ^= m & (0xFEu << sh);
+            if (count) acc += (int)(m & e.y);
         }
         out[i] = nw;
     }
@@ -417,6 +415,17 @@ __device__ __forceinline__ RowPar row_par(int P) {
     return RowPar{0x4440u + (uint32_t)P, 0x4442u + (uint32_t)P, 8u << (8 * P), 8u << (8 * P + 16)};
 }
 
+// Metropolis decision of one site without a branch: if u <= thr, flip the
+// site's byte (xor with fm) and add the statistics delta (predicated ops).
+__device__ __forceinline__ void accept_site(uint32_t &w, int &acc, uint32_t u, uint2 e, uint32_t fm) {
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.le.u32 p, %2, %3;\n\t"
+        "@p xor.b32 %0, %0, %4;\n\t"
+        "@p add.s32 %1, %1, %5;\n\t}"
+        : "+r"(w), "+r"(acc)
+        : "r"(u), "r"(e.x), "r"(fm), "r"(e.y));
+}
+
 // Colour sub-step of one 16-byte chunk in x8 form.
 __device__ __forceinline__ uint4 chunk_x8(uint4 C, uint4 U, uint4 D, uint32_t lw, uint32_t rw,
                                           uint4 ra, uint4 rb, const RowPar &rp,
@@ -433,17 +442,12 @@ __device__ __forceinline__ uint4 chunk_x8(uint4 C, uint4 U, uint4 D, uint32_t lw
         const uint32_t lf = __funnelshift_l(w[i], W, 8);
         const uint32_t rt = __funnelshift_r(W, w[i + 2], 8);
         const uint32_t key = up[i] + dn[i] + lf + rt + W * 5u;
-        const TabEntry e0 = *reinterpret_cast<const TabEntry *>(tb + __byte_perm(key, 0u, rp.sel0));
-        const TabEntry e1 = *reinterpret_cast<const TabEntry *>(tb + __byte_perm(key, 0u, rp.sel1));
+        // table entries are 8-byte aligned: one 64-bit shared load each
+        const uint2 e0 = *reinterpret_cast<const uint2 *>(tb + __byte_perm(key, 0u, rp.sel0));
+        const uint2 e1 = *reinterpret_cast<const uint2 *>(tb + __byte_perm(key, 0u, rp.sel1));
         uint32_t nw = W;
-        if (rnd[2 * i] <= e0.thr) {
-            nw ^= rp.fm0;
-            acc += e0.delta;
-        }
-        if (rnd[2 * i + 1] <= e1.thr) {
-            nw ^= rp.fm1;
-            acc += e1.delta;
-        }
+        accept_site(nw, acc, rnd[2 * i], e0, rp.fm0);
+        accept_site(nw, acc, rnd[2 * i + 1], e1, rp.fm1);
         out[i] = nw;
     }
     return make_uint4(out[0], out[1], out[2], out[3]);
@@ -483,19 +487,14 @@ __device__ __forceinline__ void convert_row(const StripCtx &x, int r) {
     for (int j = x.lane; j < x.Lv; j += 32) row[j] = to_x8(row[j]);
 }
 
-// One chunk of one colour phase (see row_phase).
-__device__ __forceinline__ void phase_chunk(const StripCtx &x, int j, int colour, uint4 *rc,
-                                            const uint4 *ru, const uint4 *rd, uint4 *gout,
-                                            uint32_t gyb, const RowPar &rp, const PhiloxPrefix &PP,
+// One chunk of one colour phase given its neighbour words (see row_phase).
+__device__ __forceinline__ void phase_chunk(int j, int colour, uint4 *rc, const uint4 *ru,
+                                            const uint4 *rd, uint4 *gout, const uint4 &C,
+                                            uint32_t lw, uint32_t rw, uint32_t gyb,
+                                            const RowPar &rp, const PhiloxPrefix &PP,
                                             const TabEntry *stab, const PhiloxKeys &rk, int &acc) {
-    const int mask = x.Lv - 1;
-    const uint4 C = rc[j];
     const uint4 U = ru[j];
     const uint4 Dn = rd[j];
-    uint32_t lw = __shfl_sync(0xFFFFFFFFu, C.w, (x.lane + 31) & 31);
-    uint32_t rw = __shfl_sync(0xFFFFFFFFu, C.x, (x.lane + 1) & 31);
-    if (x.lane == 0) lw = reinterpret_cast<const uint32_t *>(rc + ((j - 1) & mask))[3];
-    if (x.lane == 31) rw = reinterpret_cast<const uint32_t *>(rc + ((j + 1) & mask))[0];
     const uint32_t g0 = gyb + 2u * (uint32_t)j;
     const uint4 ra = philox_from_prefix(g0, PP, rk);
     const uint4 rb = philox_from_prefix(g0 + 1u, PP, rk);
@@ -508,8 +507,11 @@ __device__ __forceinline__ void phase_chunk(const StripCtx &x, int j, int colour
 
 // One colour on row r of the ring.  Colour 0 writes the row back to the ring;
 // colour 1 writes the final row (converted back to +-1 bytes) to global memory.
-// Rows of 1024 and 2048 bytes take two chunks per iteration (four independent
-// Philox chains per lane).
+// Lanes hold chunks lane + 32 k; the words left and right of a chunk come from
+// the neighbouring lanes by shuffles, and for lanes 0 and 31 from the chunk
+// the next lane-31 / lane-0 holds (the previous iteration's, carried in a
+// register, or the next iteration's, one broadcast shared-memory load).  Rows
+// of 1024 and 2048 bytes take two chunks per iteration.
 __device__ __forceinline__ void row_phase(const StripCtx &x, int r, int colour,
                                           const PhiloxKeys &rk, int &acc) {
     const int y = wrap_row(x.r0 + r, x.L);
@@ -521,13 +523,32 @@ __device__ __forceinline__ void row_phase(const StripCtx &x, int r, int colour,
     const uint4 *rd = slot(x, r + 1);
     const uint32_t gyb = (uint32_t)y * (uint32_t)(x.L >> 3);
     uint4 *gout = x.D + (size_t)y * x.Lv;
+    const int lane = x.lane, mask = x.Lv - 1;
+    const bool first = lane == 0, last = lane == 31;
+    const int src_l = (lane + 31) & 31, src_r = (lane + 1) & 31;
+    // word 3 of the row's last chunk: left neighbour of chunk 0 (periodic)
+    uint32_t carry = reinterpret_cast<const uint32_t *>(rc + mask)[3];
     if (x.Lv >= 64) {
-        for (int j = x.lane; j < x.Lv; j += 64) {
-            phase_chunk(x, j, colour, rc, ru, rd, gout, gyb, rp, PP, stab, rk, acc);
-            phase_chunk(x, j + 32, colour, rc, ru, rd, gout, gyb, rp, PP, stab, rk, acc);
+        for (int j = lane; j < x.Lv; j += 64) {
+            const uint4 A = rc[j], B = rc[j + 32];
+            const uint32_t nxt = reinterpret_cast<const uint32_t *>(rc + ((j - lane + 64) & mask))[0];
+            const uint32_t al = __shfl_sync(0xFFFFFFFFu, A.w, src_l);
+            const uint32_t ar = __shfl_sync(0xFFFFFFFFu, A.x, src_r);
+            const uint32_t bl = __shfl_sync(0xFFFFFFFFu, B.w, src_l);
+            const uint32_t br = __shfl_sync(0xFFFFFFFFu, B.x, src_r);
+            const uint32_t a31 = __shfl_sync(0xFFFFFFFFu, A.w, 31);
+            const uint32_t b0 = __shfl_sync(0xFFFFFFFFu, B.x, 0);
+            const uint32_t lwA = first ? carry : al, rwA = last ? b0 : ar;
+            const uint32_t lwB = first ? a31 : bl, rwB = last ? nxt : br;
+            carry = __shfl_sync(0xFFFFFFFFu, B.w, 31);
+            phase_chunk(j, colour, rc, ru, rd, gout, A, lwA, rwA, gyb, rp, PP, stab, rk, acc);
+            phase_chunk(j + 32, colour, rc, ru, rd, gout, B, lwB, rwB, gyb, rp, PP, stab, rk, acc);
         }
     } else {
-        phase_chunk(x, x.lane, colour, rc, ru, rd, gout, gyb, rp, PP, stab, rk, acc);
+        const uint4 A = rc[lane];
+        const uint32_t al = __shfl_sync(0xFFFFFFFFu, A.w, src_l);
+        const uint32_t ar = __shfl_sync(0xFFFFFFFFu, A.x, src_r);
+        phase_chunk(lane, colour, rc, ru, rd, gout, A, al, ar, gyb, rp, PP, stab, rk, acc);
     }
     __syncwarp();
 }
