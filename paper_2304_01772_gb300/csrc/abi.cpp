@@ -102,6 +102,8 @@ struct spin_ctx {
     size_t smem = 0;
     int sm_count = 0;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t side = nullptr;          // tile kernel runs here, beside the strip kernel
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     GraphCache graphs[2][2];    // [record][0: two-sweep ping-pong]
     int last_launches = 0;
     // kernel timing (spin_profile)
@@ -405,21 +407,31 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                                         ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, w, c, s));
             ++launches;
         }
+        // The tile kernel (small lattices) and the strip kernel (L >= 512) touch
+        // disjoint lattices: fork the tile kernel onto a side stream and join
+        // before the finalize kernel (also inside a captured graph).
+        const bool fork = ctx->n_items && ctx->n_strip && ctx->side;
+        cudaStream_t ts = s;
+        if (fork) {
+            CK(cudaEventRecord(ctx->ev_fork, s));
+            CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+            ts = ctx->side;
+        }
         if (ctx->n_items) {
-            const bool timed = prof_begin(ctx, s, 0);
+            const bool timed = prof_begin(ctx, ts, 0);
             if (ctx->model == SPIN_ISING) {
                 IsingSweepArgs a{ctx->d_items, ctx->n_items, ctx->d_lats, ctx->d_tabs,
                                  static_cast<const int8_t *>(src), static_cast<int8_t *>(dst),
                                  ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta,
                                  philox_keys(ctx->k0, ctx->k1)};
-                CK(launch_ising_fused(a, ctx->grid, ctx->threads, ctx->smem, s));
+                CK(launch_ising_fused(a, ctx->grid, ctx->threads, ctx->smem, ts));
             } else {
                 PottsSweepArgs a{ctx->d_items, ctx->n_items, ctx->d_lats, ctx->d_tabs,
                                  static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst),
                                  ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, w};
-                CK(launch_potts_fused(a, ctx->grid, ctx->threads, ctx->smem, s));
+                CK(launch_potts_fused(a, ctx->grid, ctx->threads, ctx->smem, ts));
             }
-            if (timed) prof_end(ctx, s);
+            if (timed) prof_end(ctx, ts);
             ++launches;
         }
         if (ctx->n_strip) {
@@ -431,6 +443,10 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
             CK(launch_ising_strip(a, ctx->strip_grid, ctx->strip_warps, s));
             if (timed) prof_end(ctx, s);
             ++launches;
+        }
+        if (fork) {
+            CK(cudaEventRecord(ctx->ev_join, ctx->side));
+            CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
         }
     }
     CK(launch_finalize(ctx->d_state, ctx->st, record, s));
@@ -616,6 +632,9 @@ void spin_destroy(spin_ctx *ctx) {
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
     delete ctx;
 }
@@ -756,6 +775,11 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
                                 ctx->st.cur, s);
     if (e) return bail(cuda_fail(ctx, e, "initial statistics"));
     // CPM statistics read the single lattice at offset 0 of ctx->spins
+    if (model == SPIN_ISING &&
+        (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess))
+        return bail(fail(ctx, SPIN_ECUDA, "stream or event creation failed"));
     rc = plan(ctx);
     if (rc) return bail(rc);
     if (cudaStreamSynchronize(s) != cudaSuccess) return bail(SPIN_ECUDA);
