@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--workload", default="uneven512",
-                    choices=["uneven512", "potts_q3", "potts_q8", "cpm1024", "ising_small"])
+                    choices=["uneven512", "potts_q3", "potts_q8", "cpm1024", "ising_small", "grad", "mlp"])
     return ap.parse_args()
 
 
@@ -86,6 +86,85 @@ def cpu_oracle_rate(lats, sweeps, cores):
     wall = time.perf_counter() - t0
     updates = sum(r[0] for r in res)
     return updates / wall, updates, wall
+
+
+def _oracle_potts(args):
+    import oracle
+    i, d, seed, sweeps = args
+    s = oracle.init_potts(d["L"], d["q"], seed, i).copy()
+    t0 = time.perf_counter()
+    oracle.potts_run(s, d["q"], d["beta"], d["J"], seed, i, 0, sweeps, record=False)
+    return d["L"] * d["L"] * sweeps, time.perf_counter() - t0
+
+
+def cpu_oracle_pool(fn, tasks, cores):
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        res = pool.map(fn, tasks, chunksize=1)
+    wall = time.perf_counter() - t0
+    units = sum(r[0] for r in res)
+    return units / wall, units, wall
+
+
+def cpu_baseline_secondary(workload, cores):
+    """The oracle on a bounded sample of a secondary workload (before any GPU call)."""
+    import numpy as np
+
+    import oracle
+    from paper_2304_01772_gb300 import workloads as wl
+    if workload.startswith("potts"):
+        q = int(workload[-1])
+        lats = wl.potts_batch(q)
+        pick = list(range(0, 64, 64 // cores))[:cores]
+        rate, units, wall = cpu_oracle_pool(_oracle_potts, [(i, lats[i], SEED, 1) for i in pick], cores)
+        return {"value": rate, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+                "sample": f"{len(pick)} of the 64 lattices, one sweep each ({wall:.1f} s wall)"}
+    if workload == "cpm1024":
+        p = wl.cpm1024()
+        op = oracle.CPM(L=p["L"], J=p["J"], lam=p["lam"], target=p["target"], n_cells=p["n_cells"], T=p["T"],
+                        side=p["side"], cols=p["cols"])
+        ids, types, vol = op.init(SEED, 0)
+        ids = ids.copy()
+        t0 = time.perf_counter()
+        op.run(ids, vol, types, SEED, 0, 0, 2, record=False)
+        wall = time.perf_counter() - t0
+        return {"value": 2 * p["L"] ** 2 / wall, "unit": "copy-attempts/s", "cores": 1, "kind": "oracle",
+                "sample": f"2 Monte Carlo steps of the 1024^2 lattice, one core (a single chain) ({wall:.1f} s)"}
+    if workload == "ising_small":
+        lats = wl.ising_small()
+        rate, units, wall = cpu_oracle_rate(lats, 1000, min(cores, len(lats)))
+        return {"value": rate, "unit": "site-updates/s", "cores": min(cores, len(lats)), "kind": "oracle",
+                "sample": f"the whole job: 8 lattices x 1000 sweeps ({wall:.1f} s wall)"}
+    if workload == "grad":
+        from oracle import estimator
+        rng = np.random.default_rng(0)
+        st = np.stack([rng.integers(-65536, 65536, size=(128, 1000)),
+                       rng.integers(0, 131072, size=(128, 1000))], axis=-1)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            for i in range(128):
+                estimator.ising_grad(st[i:i + 1], 0.45, 1.0, 0.0, 65536)
+        wall = (time.perf_counter() - t0) / 3
+        return {"value": 128 * 1000 / wall, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                "sample": "estimator over 128 chains x 1000 recorded sweeps, per-chain gradients (numpy)"}
+    if workload == "mlp":
+        from oracle import mlp as omlp
+        rng = np.random.default_rng(0)
+        P = {k: rng.normal(0, 0.3, size=sh) for k, sh in omlp.shapes().items()}
+        X = rng.uniform(-1, 1, size=(10000, 3))
+        T = rng.normal(size=(10000, 2))
+        t0 = time.perf_counter()
+        for _ in range(5):
+            Y, c = omlp.forward(P, X, np.zeros(3), np.ones(3))
+            omlp.backward(P, c, Y, T, np.ones(3))
+        wall = (time.perf_counter() - t0) / 5
+        return {"value": 10000 / wall, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                "sample": "forward + backward of 10^4 samples in float64 numpy (BLAS threads)"}
+    return None
 
 
 # ----------------------------------------------------------------- clocks
@@ -390,11 +469,16 @@ def run_secondary(args):
     """Other configurations, one JSON line each (not the headline metric):
     potts_q3 / potts_q8: 64 Potts lattices 1024^2 at beta_c(q) * [0.8, 1.2];
     cpm1024: cellular Potts 1024^2, 2000 cells (a step = one Monte Carlo step);
-    ising_small: 8 Ising lattices 64^2, statistics recorded every sweep."""
+    ising_small: 8 Ising lattices 64^2, statistics recorded every sweep;
+    grad: the fluctuation-estimator gradient over recorded statistics;
+    mlp: one training step of the BF16 surrogate."""
+    cpu = None if args.no_cpu else cpu_baseline_secondary(args.workload, os.cpu_count() or 1)
     import torch
     import paper_2304_01772_gb300 as sm
     from paper_2304_01772_gb300 import workloads as wl
     stream = torch.cuda.current_stream()
+    if args.workload in ("grad", "mlp"):
+        return run_grad_mlp(args, cpu)
     record = False
     if args.workload.startswith("potts"):
         q = int(args.workload[-1])
@@ -442,6 +526,60 @@ def run_secondary(args):
                                 "kernel": "potts_fused_kernel", "launch_ms": kms / kn,
                                 "note": "64 MiB state + partner ~ L2 size: largely L2-resident",
                                 "peak_source": f"{kind} hbm_gbs"}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_grad_mlp(args, cpu):
+    """grad: the adjoint reduction (exact moments + FP64 covariance) over 128
+    chains x 1000 recorded sweeps of 256^2 lattices (the fit's shape); mlp: one
+    BF16 forward + backward of the surrogate on 10^4 samples."""
+    import numpy as np
+    import torch
+    import paper_2304_01772_gb300 as sm
+    from paper_2304_01772_gb300 import fit
+    from paper_2304_01772_gb300 import workloads as wl
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    if args.workload == "grad":
+        lats = wl.fit256()
+        sim = sm.Sim(sm.SPIN_ISING, lats, seed=SEED, max_record=1000)
+        sim.sweep(1000, record=True)
+        for _ in range(args.warmup):
+            sim.grad(0, 1000)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            sim.grad(0, 1000, observable=0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        units, unit = 128 * 1000, "samples/s"
+        desc = "fluctuation estimator d<E>/N / d(J, h) per chain: 128 chains of 256^2 x 1000 recorded sweeps"
+    else:
+        sur = fit.Surrogate(seed=3)
+        X = torch.from_numpy(fit.sample_box(10000, seed=1)).cuda()
+        T = torch.zeros((10000, 2), dtype=torch.float32, device="cuda")
+        for _ in range(args.warmup):
+            sm.mlp_backward(sur.params, sur.mu, sur.inv_sigma, X, T)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            g, loss, _ = sm.mlp_backward(sur.params, sur.mu, sur.inv_sigma, X, T)
+            sm.adam(sur.params, g, sur.m, sur.v, 1, 1e-3)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        units, unit = 10000, "samples/s"
+        desc = "BF16 MLP 3-64-64-2: forward + backward + Adam on 10^4 samples (one training step)"
+    line = {"metric": f"{unit} ({args.workload})", "value": units / (ms * 1e-3), "unit": unit, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "int64/fp64" if args.workload == "grad" else "bf16", "data": "synthetic",
+            "config": {"workload": desc}}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
     return 0
 
