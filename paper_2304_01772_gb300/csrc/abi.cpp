@@ -75,7 +75,7 @@ struct spin_ctx {
     Item *d_items = nullptr;
     int n_items = 0;
     Item *d_strip = nullptr;     // warp row-strip items (Ising, L in {512, 1024, 2048})
-    int n_strip = 0, strip_grid = 0, strip_warps = 8;
+    int n_strip = 0, strip_grid = 0, strip_warps = 8, strip_qbits = 2, strip_chunks = 128;
     int32_t *d_generic = nullptr;
     int n_generic = 0, generic_maxL = 0;
     std::vector<int> fast_ids;
@@ -293,12 +293,17 @@ int plan(spin_ctx *ctx) {
     drop_graphs(ctx);
     if (ctx->model == SPIN_CPM) return SPIN_OK;
     std::vector<Item> items, strip;
-    size_t smem = 16;
+    std::vector<int> strip_ids;
+    size_t smem = 16, strip_bytes = 0;
+    ctx->strip_qbits = 2;
     for (int id : ctx->fast_ids) {
         const int L = ctx->lat[id].L;
-        if (ctx->model == SPIN_ISING && ctx->use_strip && (L == 512 || L == 1024 || L == 2048)) {
-            const int rows = std::max(1, std::min(L, ctx->tile_rows > 0 ? ctx->tile_rows : 65536 / L));
-            for (int r0 = 0; r0 < L; r0 += rows) strip.push_back(Item{id, r0, std::min(rows, L - r0), 0});
+        const bool strip_L = L == 512 || L == 1024 || L == 2048;
+        const bool potts_strip = ctx->model == SPIN_POTTS && ctx->lat[id].q <= 8;
+        if (ctx->use_strip && strip_L && (ctx->model == SPIN_ISING || potts_strip)) {
+            strip_ids.push_back(id);
+            strip_bytes += (size_t)L * L;
+            if (ctx->model == SPIN_POTTS && ctx->lat[id].q > 4) ctx->strip_qbits = 3;
             continue;
         }
         if (L * L <= kWholeMaxBytes) {
@@ -327,13 +332,34 @@ int plan(spin_ctx *ctx) {
     }
     if (ctx->d_strip) cudaFree(ctx->d_strip);
     ctx->d_strip = nullptr;
-    ctx->n_strip = (int)strip.size();
-    if (!strip.empty()) {
-        CK(cudaMalloc(&ctx->d_strip, sizeof(Item) * strip.size()));
-        CK(cudaMemcpy(ctx->d_strip, strip.data(), sizeof(Item) * strip.size(), cudaMemcpyHostToDevice));
+    ctx->n_strip = 0;
+    if (!strip_ids.empty()) {
         ctx->strip_warps = ctx->threads >= 512 ? 8 : 4;
         int per_sm = 0;
-        CK(occupancy_ising_strip(&per_sm, ctx->strip_warps));
+        if (ctx->model == SPIN_ISING)
+            CK(occupancy_ising_strip(&per_sm, ctx->strip_warps));
+        else {
+            int maxL = 0;
+            for (int id : strip_ids) maxL = std::max(maxL, ctx->lat[id].L);
+            ctx->strip_chunks = maxL / 16;
+            CK(occupancy_potts_strip(&per_sm, ctx->strip_warps, ctx->strip_qbits, ctx->strip_chunks));
+        }
+        // Default row blocks: 64 KB for Ising.  Potts sites cost about twice as
+        // much and its batches are smaller, so its default spreads the strip
+        // lattices over the resident warps in about one wave (the recomputed
+        // halo costs one row per item, so items stay as tall as that allows).
+        const size_t slots = (size_t)ctx->sm_count * std::max(1, per_sm) * ctx->strip_warps;
+        for (int id : strip_ids) {
+            const int L = ctx->lat[id].L;
+            int def_rows = 65536 / L;
+            if (ctx->model == SPIN_POTTS)
+                def_rows = (int)std::min<size_t>(65536 / L, std::max<size_t>(4, (strip_bytes + slots * L - 1) / (slots * L)));
+            int rows = std::max(1, std::min(L, ctx->tile_rows > 0 ? ctx->tile_rows : def_rows));
+            for (int r0 = 0; r0 < L; r0 += rows) strip.push_back(Item{id, r0, std::min(rows, L - r0), 0});
+        }
+        ctx->n_strip = (int)strip.size();
+        CK(cudaMalloc(&ctx->d_strip, sizeof(Item) * strip.size()));
+        CK(cudaMemcpy(ctx->d_strip, strip.data(), sizeof(Item) * strip.size(), cudaMemcpyHostToDevice));
         ctx->strip_grid = std::max(1, std::min((ctx->n_strip + ctx->strip_warps - 1) / ctx->strip_warps,
                                                ctx->sm_count * std::max(1, per_sm)));
     }
@@ -436,11 +462,19 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
         }
         if (ctx->n_strip) {
             const bool timed = prof_begin(ctx, s, 1);
-            IsingSweepArgs a{ctx->d_strip, ctx->n_strip, ctx->d_lats, ctx->d_tabs,
-                             static_cast<const int8_t *>(src), static_cast<int8_t *>(dst),
-                             ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta,
-                             philox_keys(ctx->k0, ctx->k1)};
-            CK(launch_ising_strip(a, ctx->strip_grid, ctx->strip_warps, s));
+            if (ctx->model == SPIN_ISING) {
+                IsingSweepArgs a{ctx->d_strip, ctx->n_strip, ctx->d_lats, ctx->d_tabs,
+                                 static_cast<const int8_t *>(src), static_cast<int8_t *>(dst),
+                                 ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta,
+                                 philox_keys(ctx->k0, ctx->k1)};
+                CK(launch_ising_strip(a, ctx->strip_grid, ctx->strip_warps, s));
+            } else {
+                PottsStripArgs a{ctx->d_strip, ctx->n_strip, ctx->d_lats, ctx->d_tabs,
+                                 static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst),
+                                 ctx->d_state, ctx->st.delta, ctx->st.cur, w, ctx->strip_chunks,
+                                 philox_keys(ctx->k0, ctx->k1)};
+                CK(launch_potts_strip(a, ctx->strip_grid, ctx->strip_warps, ctx->strip_qbits, s));
+            }
             if (timed) prof_end(ctx, s);
             ++launches;
         }

@@ -146,6 +146,26 @@ struct PottsSweepArgs {
 };
 cudaError_t launch_potts_fused(const PottsSweepArgs &a, int grid, int threads, size_t smem,
                                cudaStream_t s);
+// Warp-per-row-strip kernel for q <= 8 and L in {512, 1024, 2048}.  `delta`
+// receives the change of every statistic; the state counts are counted on the
+// new rows, and the item holding row 0 subtracts `cur` (the old counts).
+struct PottsStripArgs {
+    const Item *items;
+    int n_items;
+    const LatDev *lats;
+    const TabEntry *tabs;
+    const uint8_t *src;
+    uint8_t *dst;
+    const DevState *state;
+    int64_t *delta;       // [n_lat][width]
+    const int64_t *cur;   // [n_lat][width]
+    int width;
+    int ring_chunks;      // 16-byte chunks per ring slot: L / 16 of the widest strip lattice
+    PhiloxKeys rk;
+};
+// qbits: 2 for q <= 4, 3 for q <= 8.
+cudaError_t launch_potts_strip(const PottsStripArgs &a, int grid, int warps, int qbits, cudaStream_t s);
+cudaError_t occupancy_potts_strip(int *blocks_per_sm, int warps, int qbits, int ring_chunks);
 cudaError_t launch_potts_plain(uint8_t *spins, const LatDev *lat_dev, int lat, int L, int q,
                                const TabEntry *tabs, uint32_t k0, uint32_t k1,
                                const DevState *state, int64_t *delta, int width, int colour,

@@ -1,0 +1,68 @@
+// strip.cuh -- pieces shared by the Ising and Potts strip kernels: the ring
+// geometry, cp.async helpers and the site-independent head of Philox4x32-10.
+//
+// A strip kernel gives one warp full rows [r0, r0 + R) of one lattice with
+// L = 512, 1024 or 2048 (whole 16-byte chunks per lane) and walks down them
+// with rows s-2 .. s+2 in a five-slot shared-memory ring per warp.
+#pragma once
+#include "internal.h"
+
+namespace spinmc {
+
+constexpr int kRing = 5;          // row slots per warp
+constexpr int kRowChunks = 128;   // 16-byte chunks per slot (L <= 2048)
+
+// Rounds 1 and 2 of Philox4x32-10 for counter (g, lat, t, c) have one
+// product each that does not depend on g; they are formed once per item.
+struct PhiloxPrefix {
+    uint32_t u0, u1k, v0k, v1, ck1;
+};
+
+__device__ __forceinline__ PhiloxPrefix philox_prefix(uint32_t lat, uint32_t t, uint32_t c,
+                                                      const PhiloxKeys &rk) {
+    PhiloxPrefix P;
+    const uint64_t pb = (uint64_t)0xCD9E8D57u * t;
+    P.u0 = (uint32_t)(pb >> 32) ^ lat ^ rk.k0[0];
+    const uint32_t u1 = (uint32_t)pb;
+    const uint64_t pa = (uint64_t)0xD2511F53u * P.u0;
+    P.u1k = u1 ^ rk.k0[1];
+    P.v0k = (uint32_t)(pa >> 32) ^ rk.k1[1];
+    P.v1 = (uint32_t)pa;
+    P.ck1 = c ^ rk.k1[0];
+    return P;
+}
+
+__device__ __forceinline__ uint4 philox_from_prefix(uint32_t g, const PhiloxPrefix &P,
+                                                    const PhiloxKeys &rk) {
+    const uint64_t pa = (uint64_t)0xD2511F53u * g;            // round 1
+    const uint32_t x2 = (uint32_t)(pa >> 32) ^ P.ck1;
+    const uint64_t pb = (uint64_t)0xCD9E8D57u * x2;            // round 2
+    uint32_t c0 = (uint32_t)(pb >> 32) ^ P.u1k, c1 = (uint32_t)pb;
+    uint32_t c2 = (uint32_t)pa ^ P.v0k, c3 = P.v1;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {                              // rounds 3..10
+        const uint64_t qa = (uint64_t)0xD2511F53u * c0;
+        const uint64_t qb = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(qb >> 32) ^ c1 ^ rk.k0[r];
+        const uint32_t n2 = (uint32_t)(qa >> 32) ^ c3 ^ rk.k1[r];
+        c1 = (uint32_t)qb;
+        c3 = (uint32_t)qa;
+        c0 = n0;
+        c2 = n2;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ int wrap_row(int y, int L) { return y < 0 ? y + L : (y >= L ? y - L : y); }
+
+inline size_t strip_ring_bytes(int warps) { return sizeof(uint4) * (size_t)warps * kRing * kRowChunks; }
+
+}  // namespace spinmc

@@ -20,6 +20,7 @@
 //    lattice per sweep: the plain launch form the batched one is compared to).
 //  * ising_generic_kernel: any even L (not a multiple of 16), one thread per site.
 #include "internal.h"
+#include "strip.cuh"
 
 namespace spinmc {
 
@@ -356,50 +357,6 @@ __global__ void init_random_kernel(void *spins, int model, const LatDev *lats, u
 // bytes plus 5x the centre byte add without carries to 8 * (d + 5 c), the
 // byte offset of the table entry.
 constexpr uint32_t kX8 = 0x08080808u;
-constexpr int kRing = 5;          // row slots per warp
-constexpr int kRowChunks = 128;   // 16-byte chunks per slot (L <= 2048)
-
-// Rounds 1 and 2 of Philox4x32-10 for counter (g, lat, t, c) have one
-// product each that does not depend on g; they are formed once per item.
-struct PhiloxPrefix {
-    uint32_t u0, u1k, v0k, v1, ck1;
-};
-
-__device__ __forceinline__ PhiloxPrefix philox_prefix(uint32_t lat, uint32_t t, uint32_t c,
-                                                      const PhiloxKeys &rk) {
-    PhiloxPrefix P;
-    const uint64_t pb = (uint64_t)0xCD9E8D57u * t;
-    P.u0 = (uint32_t)(pb >> 32) ^ lat ^ rk.k0[0];
-    const uint32_t u1 = (uint32_t)pb;
-    const uint64_t pa = (uint64_t)0xD2511F53u * P.u0;
-    P.u1k = u1 ^ rk.k0[1];
-    P.v0k = (uint32_t)(pa >> 32) ^ rk.k1[1];
-    P.v1 = (uint32_t)pa;
-    P.ck1 = c ^ rk.k1[0];
-    return P;
-}
-
-__device__ __forceinline__ uint4 philox_from_prefix(uint32_t g, const PhiloxPrefix &P,
-                                                    const PhiloxKeys &rk) {
-    const uint64_t pa = (uint64_t)0xD2511F53u * g;            // round 1
-    const uint32_t x2 = (uint32_t)(pa >> 32) ^ P.ck1;
-    const uint64_t pb = (uint64_t)0xCD9E8D57u * x2;            // round 2
-    uint32_t c0 = (uint32_t)(pb >> 32) ^ P.u1k, c1 = (uint32_t)pb;
-    uint32_t c2 = (uint32_t)pa ^ P.v0k, c3 = P.v1;
-#pragma unroll
-    for (int r = 2; r < 10; ++r) {                              // rounds 3..10
-        const uint64_t qa = (uint64_t)0xD2511F53u * c0;
-        const uint64_t qb = (uint64_t)0xCD9E8D57u * c2;
-        const uint32_t n0 = (uint32_t)(qb >> 32) ^ c1 ^ rk.k0[r];
-        const uint32_t n2 = (uint32_t)(qa >> 32) ^ c3 ^ rk.k1[r];
-        c1 = (uint32_t)qb;
-        c3 = (uint32_t)qa;
-        c0 = n0;
-        c2 = n2;
-    }
-    return make_uint4(c0, c1, c2, c3);
-}
-
 __device__ __forceinline__ uint4 to_x8(uint4 v) {
     return make_uint4(v.x & kX8, v.y & kX8, v.z & kX8, v.w & kX8);
 }
@@ -452,15 +409,6 @@ __device__ __forceinline__ uint4 chunk_x8(uint4 C, uint4 U, uint4 D, uint32_t lw
     }
     return make_uint4(out[0], out[1], out[2], out[3]);
 }
-
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-__device__ __forceinline__ int wrap_row(int y, int L) { return y < 0 ? y + L : (y >= L ? y - L : y); }
 
 struct StripCtx {
     const uint4 *S;
@@ -584,7 +532,7 @@ __device__ void strip_item(const StripCtx &x, const PhiloxKeys &rk, int &dm, int
         if ((s & 7) == 7) drain_acc(acc, dm, db);
     }
     drain_acc(acc, dm, db);
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    cp_async_wait_all();
     __syncwarp();
 }
 
@@ -680,7 +628,7 @@ cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, s
     return cudaGetLastError();
 }
 
-size_t strip_smem(int warps) { return sizeof(uint4) * (size_t)warps * kRing * kRowChunks; }
+size_t strip_smem(int warps) { return strip_ring_bytes(warps); }
 
 cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, cudaStream_t s) {
     switch (warps) {

@@ -12,6 +12,7 @@
 // each thread keeps the count changes in two 64-bit words of four signed
 // 16-bit fields; larger q use a shared-memory histogram.
 #include "internal.h"
+#include "strip.cuh"
 
 namespace spinmc {
 
@@ -187,6 +188,292 @@ __global__ void __launch_bounds__(THREADS) potts_fused_kernel(PottsSweepArgs a) 
     }
 }
 
+// ------------------------------------------------------------ strip kernel
+// Lattices with q <= 8 and L = 512, 1024 or 2048, one warp per block of full
+// rows, walked as in the Ising strip kernel: at step s colour 0 on row s and
+// colour 1 on row s - 1, rows s-2 .. s+2 in a five-slot shared-memory ring
+// (row s + 2 arriving by cp.async), rows -1 and R a recomputed colour-0 halo.
+//
+// A 32-bit word holds four sites; its two active bytes P and P + 2 (P the row
+// parity of the colour) use lanes (0, 1) and (2, 3) of one Philox draw, and
+// both are handled with byte-parallel (SWAR) arithmetic:
+//  * X1 = [U_P, D_P, U_P+2, D_P+2] and X2 = [L_P, R_P, L_P+2, R_P+2] gather
+//    the neighbours, S = [s_P, s_P, s_P+2, s_P+2], S' the proposals likewise;
+//  * for states below 8, (a ^ b) + 7 has bit 3 set exactly when a != b, so
+//    each pair flag 8 [a != b] costs three operations and never carries;
+//  * n1 + n2 + 16 - o1 - o2 holds per byte 8 (two neighbours' [!= s'] - [!= s]
+//    + 2); adding the word shifted up one byte leaves in bytes 1 and 3 the
+//    value 8 (n_same(s) - n_same(s') + 4): the byte offset of the site's
+//    8-byte table entry (index d + 4 for dE = J d).
+// Statistics: an accepted site adds its table delta (the change of the equal-
+// bond count); the state counts are taken on the finished rows (colour-1
+// phase) from bit-plane minterms in per-byte counters, and the item holding
+// row 0 subtracts the old counts, so that `delta` receives the change.
+constexpr uint32_t kOnes = 0x01010101u;
+
+// PRMT selectors and byte masks for active bytes P and P + 2 (P = row parity).
+struct PottsPar {
+    uint32_t sel_nb;   // [x_P, y_P, x_P+2, y_P+2] from (x, y)
+    uint32_t sel_s;    // [w_P, w_P, w_P+2, w_P+2]
+    uint32_t sel_x;    // bytes 0 and 2 moved to P and P + 2, zero elsewhere
+    uint32_t mP, mQ;   // byte masks of the two active sites
+};
+
+__device__ __forceinline__ PottsPar potts_par(int P) {
+    return P ? PottsPar{0x7351u, 0x3311u, 0x2404u, 0x0000FF00u, 0xFF000000u}
+             : PottsPar{0x6240u, 0x2200u, 0x4240u, 0x000000FFu, 0x00FF0000u};
+}
+
+// Every byte replaced by copies of its top bit (prmt with sign replication).
+__device__ __forceinline__ uint32_t byte_signs(uint32_t v) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(r) : "r"(v));
+    return r;
+}
+
+// If u <= thr: w ^= (xm & m) (the site takes its proposal) and acc += delta.
+__device__ __forceinline__ void potts_accept(uint32_t &w, int &acc, uint32_t u, uint2 e,
+                                             uint32_t xm, uint32_t m) {
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.le.u32 p, %2, %3;\n\t"
+        "@p lop3.b32 %0, %0, %4, %5, 0x78;\n\t"
+        "@p add.s32 %1, %1, %6;\n\t}"
+        : "+r"(w), "+r"(acc)
+        : "r"(u), "r"(e.x), "r"(xm), "r"(m), "r"(e.y));
+}
+
+__device__ __forceinline__ uint32_t pair_flags(uint32_t a, uint32_t b) {
+    return ((a ^ b) + 0x07070707u) & 0x08080808u;
+}
+
+// Colour sub-step of the two active sites of word W (left / right words wl, wr;
+// up / down words U, D; Philox draw r).  vadd = (0x81 - q) * kOnes.
+__device__ __forceinline__ uint32_t potts_word(uint32_t W, uint32_t U, uint32_t D, uint32_t wl,
+                                               uint32_t wr, uint4 r, const PottsPar &pp, uint32_t q1,
+                                               uint32_t vadd, const char *tb, int &acc) {
+    const uint32_t lf = __funnelshift_l(wl, W, 8);
+    const uint32_t rt = __funnelshift_r(W, wr, 8);
+    const uint32_t X1 = __byte_perm(U, D, pp.sel_nb);
+    const uint32_t X2 = __byte_perm(lf, rt, pp.sel_nb);
+    const uint32_t S = __byte_perm(W, 0u, pp.sel_s);
+    // proposals s + 1 + mulhi(u1, q - 1), reduced mod q (at most 2q - 2 < 16)
+    const uint32_t M = __byte_perm(__umulhi(r.y, q1), __umulhi(r.w, q1), 0x4400u);
+    const uint32_t raw = S + M + kOnes;
+    const uint32_t V = S + M + vadd;            // byte top bit set iff raw >= q
+    const uint32_t E = byte_signs(V);
+    const uint32_t SP = (V & 0x7F7F7F7Fu & E) | (raw & ~E);
+    const uint32_t K = pair_flags(X1, SP) + pair_flags(X2, SP) + 0x10101010u - pair_flags(X1, S) -
+                       pair_flags(X2, S);
+    const uint32_t KK = K + (K << 8);
+    const uint2 eP = *reinterpret_cast<const uint2 *>(tb + __byte_perm(KK, 0u, 0x4441u));
+    const uint2 eQ = *reinterpret_cast<const uint2 *>(tb + __byte_perm(KK, 0u, 0x4443u));
+    const uint32_t xm = __byte_perm(S ^ SP, 0u, pp.sel_x);
+    uint32_t nw = W;
+    potts_accept(nw, acc, r.x, eP, xm, pp.mP);
+    potts_accept(nw, acc, r.z, eQ, xm, pp.mQ);
+    return nw;
+}
+
+// Per-byte counters of the states 1 .. 2^QB - 1 in word w (bit-plane minterms;
+// state 0 is the remainder).
+template <int QB>
+__device__ __forceinline__ void count_states(uint32_t w, uint32_t (&h)[(1 << QB) - 1]) {
+    const uint32_t b0 = w & kOnes, b1 = (w >> 1) & kOnes;
+    const uint32_t b2 = QB > 2 ? (w >> 2) & kOnes : 0u;
+#pragma unroll
+    for (int k = 1; k < (1 << QB); ++k)
+        h[k - 1] += ((k & 1) ? b0 : ~b0) & ((k & 2) ? b1 : ~b1) & ((k & 4) ? b2 : ~b2);
+}
+
+template <int QB>
+struct PottsStrip {
+    const uint4 *S;
+    uint4 *D;
+    uint4 *ring;
+    int L, Lv, r0, nrows, lane, rchunks;
+    uint32_t q1, vadd;
+    PhiloxPrefix P0, P1;
+    const TabEntry *tab_cnt;
+    const TabEntry *tab_halo;
+};
+
+template <int QB>
+__device__ __forceinline__ uint4 *pslot(const PottsStrip<QB> &x, int r) {
+    return x.ring + ((r + 2) % kRing) * x.rchunks;
+}
+
+template <int QB>
+__device__ __forceinline__ void pissue_row(const PottsStrip<QB> &x, int r) {
+    const uint4 *src = x.S + (size_t)wrap_row(x.r0 + r, x.L) * x.Lv;
+    uint4 *dst = pslot(x, r);
+    for (int j = x.lane; j < x.Lv; j += 32) cp_async16(dst + j, src + j);
+}
+
+template <int QB, int COLOUR>
+__device__ __forceinline__ void potts_phase_chunk(const PottsStrip<QB> &x, int j, const PottsPar &pp, uint4 *rc,
+                                                  const uint4 *ru, const uint4 *rd, uint4 *gout,
+                                                  const uint4 &C, uint32_t lw, uint32_t rw,
+                                                  uint32_t gyb, const PhiloxPrefix &PP,
+                                                  const char *tb, const PhiloxKeys &rk, int &acc,
+                                                  uint32_t (&h)[(1 << QB) - 1]) {
+    const uint4 U = ru[j];
+    const uint4 Dn = rd[j];
+    const uint32_t g = gyb + 4u * (uint32_t)j;
+    const uint32_t w[6] = {lw, C.x, C.y, C.z, C.w, rw};
+    const uint32_t up[4] = {U.x, U.y, U.z, U.w};
+    const uint32_t dn[4] = {Dn.x, Dn.y, Dn.z, Dn.w};
+    uint32_t out[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint4 r = philox_from_prefix(g + (uint32_t)i, PP, rk);
+        out[i] = potts_word(w[i + 1], up[i], dn[i], w[i], w[i + 2], r, pp, x.q1, x.vadd, tb, acc);
+    }
+    const uint4 N = make_uint4(out[0], out[1], out[2], out[3]);
+    if (COLOUR == 0) {
+        rc[j] = N;
+    } else {
+        gout[j] = N;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) count_states<QB>(out[i], h);
+    }
+}
+
+// One colour on row r of the ring.  Lane l takes chunks l, l + 32, ..; the
+// word left of a chunk comes from lane l - 1 (lane 0: lane 31's previous
+// chunk), the word right of it from lane l + 1 (lane 31: the following
+// chunk's first word).  Rows of 1024 and 2048 bytes take two chunks per
+// iteration (eight independent Philox draws per lane).  Colour 0 writes the
+// row back to the ring, colour 1 to global memory.
+template <int QB, int COLOUR>
+__device__ __forceinline__ void potts_row_phase(const PottsStrip<QB> &x, int r, const PhiloxKeys &rk,
+                                                int &acc, uint32_t (&h)[(1 << QB) - 1]) {
+    const int y = wrap_row(x.r0 + r, x.L);
+    const PottsPar pp = potts_par((COLOUR ^ y) & 1);
+    const PhiloxPrefix &PP = COLOUR ? x.P1 : x.P0;
+    const char *tb = reinterpret_cast<const char *>((r >= 0 && r < x.nrows) ? x.tab_cnt : x.tab_halo);
+    uint4 *rc = pslot(x, r);
+    const uint4 *ru = pslot(x, r - 1);
+    const uint4 *rd = pslot(x, r + 1);
+    const uint32_t gyb = (uint32_t)y * (uint32_t)(x.L >> 2);
+    uint4 *gout = x.D + (size_t)y * x.Lv;
+    const int lane = x.lane, mask = x.Lv - 1;
+    const bool first = lane == 0, last = lane == 31;
+    const int src_l = (lane + 31) & 31, src_r = (lane + 1) & 31;
+    uint32_t carry = reinterpret_cast<const uint32_t *>(rc + mask)[3];
+    if (x.Lv >= 64) {
+        // two chunks per iteration: eight independent Philox chains per lane
+#pragma unroll 1
+        for (int j = lane; j < x.Lv; j += 64) {
+            const uint4 A = rc[j], B = rc[j + 32];
+            const uint32_t nxt = reinterpret_cast<const uint32_t *>(rc + ((j - lane + 64) & mask))[0];
+            const uint32_t al = __shfl_sync(0xFFFFFFFFu, A.w, src_l);
+            const uint32_t ar = __shfl_sync(0xFFFFFFFFu, A.x, src_r);
+            const uint32_t bl = __shfl_sync(0xFFFFFFFFu, B.w, src_l);
+            const uint32_t br = __shfl_sync(0xFFFFFFFFu, B.x, src_r);
+            const uint32_t a31 = __shfl_sync(0xFFFFFFFFu, A.w, 31);
+            const uint32_t b0 = __shfl_sync(0xFFFFFFFFu, B.x, 0);
+            const uint32_t lwA = first ? carry : al, rwA = last ? b0 : ar;
+            const uint32_t lwB = first ? a31 : bl, rwB = last ? nxt : br;
+            carry = __shfl_sync(0xFFFFFFFFu, B.w, 31);
+            potts_phase_chunk<QB, COLOUR>(x, j, pp, rc, ru, rd, gout, A, lwA, rwA, gyb, PP, tb, rk, acc, h);
+            potts_phase_chunk<QB, COLOUR>(x, j + 32, pp, rc, ru, rd, gout, B, lwB, rwB, gyb, PP, tb, rk, acc, h);
+        }
+    } else {
+        const uint4 A = rc[lane];
+        const uint32_t al = __shfl_sync(0xFFFFFFFFu, A.w, src_l);
+        const uint32_t ar = __shfl_sync(0xFFFFFFFFu, A.x, src_r);
+        potts_phase_chunk<QB, COLOUR>(x, lane, pp, rc, ru, rd, gout, A, al, ar, gyb, PP, tb, rk, acc, h);
+    }
+    __syncwarp();
+}
+
+// Per-byte counters -> the warp's totals in shared memory (lane 0 writes).
+template <int QB>
+__device__ __forceinline__ void drain_counts(uint32_t (&h)[(1 << QB) - 1], uint32_t *tot, int lane) {
+#pragma unroll
+    for (int k = 0; k < (1 << QB) - 1; ++k) {
+        const uint32_t v = __reduce_add_sync(0xFFFFFFFFu, __dp4a(h[k], kOnes, 0u));
+        if (lane == 0) tot[k] += v;
+        h[k] = 0u;
+    }
+}
+
+template <int WARPS, int QB>
+__global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) potts_strip_kernel(PottsStripArgs a) {
+    constexpr int NK = (1 << QB) - 1;
+    extern __shared__ __align__(16) uint4 ring_all[];
+    __shared__ TabEntry tabs[WARPS][2][kTabStride];
+    __shared__ uint32_t tots[WARPS][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t t = a.state->t;
+    const int gw = blockIdx.x * WARPS + warp, nw = gridDim.x * WARPS;
+    uint32_t *tot = tots[warp];
+    for (int it = gw; it < a.n_items; it += nw) {
+        const Item w = a.items[it];
+        const LatDev ld = a.lats[w.lat];
+        if (lane < kTabStride) {
+            const TabEntry e = a.tabs[w.lat * kTabStride + lane];
+            tabs[warp][0][lane] = e;
+            tabs[warp][1][lane] = TabEntry{e.thr, 0};
+        }
+        if (lane < 8) tot[lane] = 0u;
+        __syncwarp();
+        PottsStrip<QB> x;
+        x.S = reinterpret_cast<const uint4 *>(a.src + ld.offset);
+        x.D = reinterpret_cast<uint4 *>(a.dst + ld.offset);
+        x.ring = ring_all + (size_t)warp * kRing * a.ring_chunks;
+        x.L = ld.L;
+        x.Lv = ld.L >> 4;
+        x.r0 = w.r0;
+        x.nrows = w.nrows;
+        x.lane = lane;
+        x.rchunks = a.ring_chunks;
+        x.q1 = (uint32_t)ld.q - 1u;
+        x.vadd = (0x81u - (uint32_t)ld.q) * kOnes;
+        x.P0 = philox_prefix((uint32_t)w.lat, t, 0u, a.rk);
+        x.P1 = philox_prefix((uint32_t)w.lat, t, 1u, a.rk);
+        x.tab_cnt = tabs[warp][0];
+        x.tab_halo = tabs[warp][1];
+        int acc = 0;
+        uint32_t h[NK];
+#pragma unroll
+        for (int k = 0; k < NK; ++k) h[k] = 0u;
+        pissue_row(x, -2);
+        cp_async_commit();
+        pissue_row(x, -1);
+        cp_async_commit();
+        pissue_row(x, 0);
+        cp_async_commit();
+        for (int s = -1; s <= x.nrows; ++s) {
+            if (s + 2 <= x.nrows + 1) pissue_row(x, s + 2);
+            cp_async_commit();
+            cp_async_wait1();           // every row up to s + 1 has landed
+            __syncwarp();
+            potts_row_phase<QB, 0>(x, s, a.rk, acc, h);
+            if (s >= 1) potts_row_phase<QB, 1>(x, s - 1, a.rk, acc, h);
+            if ((s & 7) == 7) drain_counts<QB>(h, tot, lane);   // at most 8 rows x 16 words per byte
+        }
+        drain_counts<QB>(h, tot, lane);
+        cp_async_wait_all();
+        acc = (int)__reduce_add_sync(0xFFFFFFFFu, (uint32_t)acc);
+        __syncwarp();
+        // lane k adds the change of statistic k (0: B_eq, 1 + k: n_k)
+        long long own = 0, v = 0;
+#pragma unroll
+        for (int k = 0; k < NK; ++k) own += tot[k];
+        if (lane >= 2 && lane < NK + 2) v = tot[lane - 2];
+        if (lane == 0) v = acc;
+        if (lane == 1) v = (long long)w.nrows * ld.L - own;
+        const int stat = lane;                        // 0: B_eq, 1 + k: n_k
+        if (stat <= ld.q && stat < a.width) {
+            int64_t *dl = a.delta + (size_t)a.width * w.lat;
+            if (w.r0 == 0 && stat >= 1) v -= a.cur[(size_t)a.width * w.lat + stat];
+            if (v) atomicAdd(reinterpret_cast<unsigned long long *>(dl + stat), (unsigned long long)v);
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(256) potts_plain_kernel(uint8_t *spins, int L, uint32_t lat,
                                                           uint32_t q, const TabEntry *tab,
                                                           uint32_t k0, uint32_t k1,
@@ -326,6 +613,47 @@ cudaError_t launch_potts_generic(const uint8_t *src, uint8_t *dst, const int32_t
     dim3 grid(blocks < 64 ? blocks : 64, n);
     potts_generic_kernel<<<grid, 256, 0, s>>>(src, dst, lat_ids, lats, tabs, k0, k1, state, delta,
                                               width, colour);
+    return cudaGetLastError();
+}
+
+static size_t potts_ring_bytes(int warps, int ring_chunks) {
+    return sizeof(uint4) * (size_t)warps * kRing * (size_t)ring_chunks;
+}
+
+template <int QB>
+static cudaError_t potts_strip_attrs() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(potts_strip_kernel<4, QB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)strip_ring_bytes(4))))
+        return e;
+    return cudaFuncSetAttribute(potts_strip_kernel<8, QB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)strip_ring_bytes(8));
+}
+
+cudaError_t occupancy_potts_strip(int *blocks_per_sm, int warps, int qbits, int ring_chunks) {
+    cudaError_t e = qbits == 2 ? potts_strip_attrs<2>() : potts_strip_attrs<3>();
+    if (e) return e;
+    const size_t sm = potts_ring_bytes(warps, ring_chunks);
+    if (qbits == 2)
+        return warps == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, potts_strip_kernel<4, 2>, 128, sm)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, potts_strip_kernel<8, 2>, 256, sm);
+    return warps == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, potts_strip_kernel<4, 3>, 128, sm)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, potts_strip_kernel<8, 3>, 256, sm);
+}
+
+cudaError_t launch_potts_strip(const PottsStripArgs &a, int grid, int warps, int qbits, cudaStream_t s) {
+    if (a.ring_chunks != 32 && a.ring_chunks != 64 && a.ring_chunks != kRowChunks) return cudaErrorInvalidValue;
+    const size_t sm = potts_ring_bytes(warps, a.ring_chunks);
+    if (qbits == 2 && warps == 4)
+        potts_strip_kernel<4, 2><<<grid, 128, sm, s>>>(a);
+    else if (qbits == 2 && warps == 8)
+        potts_strip_kernel<8, 2><<<grid, 256, sm, s>>>(a);
+    else if (qbits == 3 && warps == 4)
+        potts_strip_kernel<4, 3><<<grid, 128, sm, s>>>(a);
+    else if (qbits == 3 && warps == 8)
+        potts_strip_kernel<8, 3><<<grid, 256, sm, s>>>(a);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -341,6 +341,41 @@ def test_uneven512_full_size_sampled():
     assert torch.equal(sim.observables(1, 1)[0][0], sim.current_stats())
 
 
+# Potts lattices on the strip kernel (q <= 8, L in {512, 1024, 2048}) next to
+# ones on the tile kernel (smaller L, or q > 8) in the same launch.
+POTTS_STRIP = [dict(L=L, q=q, beta=b, J=J) for L, q, b, J in [
+    (512, 2, 0.9, 1.0), (512, 3, 1.005, 1.0), (1024, 4, 1.1, 1.0), (512, 5, 1.2, -1.0),
+    (512, 8, 1.3, 1.0), (2048, 3, 0.8, 1.0), (512, 12, 1.5, 1.0), (64, 3, 1.0, 1.0),
+    (1024, 7, 0.0, 1.0), (512, 6, 4.0, 1.0)]]
+
+
+@pytest.mark.parametrize("tile,threads,graph", [(0, 256, True), (24, 512, False), (8, 256, False),
+                                                (64, 512, True), (1, 256, False)])
+def test_potts_strip_batch(tile, threads, graph):
+    sim = sm.Sim(sm.SPIN_POTTS, POTTS_STRIP, seed=SEED, max_record=8)
+    sim.set_launch(0, graph, tile, threads)
+    ref = {i: lattice_np(sim, i) for i in range(len(POTTS_STRIP))}
+    sim.sweep(1, record=True)
+    for i, d in enumerate(POTTS_STRIP):
+        oracle.potts_sweep(ref[i], d["q"], d["beta"], d["J"], SEED, i, 0)
+        assert np.array_equal(lattice_np(sim, i), ref[i]), (i, d)
+    sim.sweep(3, record=True)
+    st = sim.observables_host(0, 4)[0]
+    qmax = max(d["q"] for d in POTTS_STRIP)
+    for i, d in enumerate(POTTS_STRIP):
+        first = oracle.potts_stats(ref[i], d["q"])
+        rest = oracle.potts_run(ref[i], d["q"], d["beta"], d["J"], SEED, i, 1, 3)
+        assert np.array_equal(lattice_np(sim, i), ref[i]), (i, d)
+        assert np.array_equal(st[0, i, :d["q"] + 1], first), i
+        assert np.array_equal(st[1:, i, :d["q"] + 1], rest), i
+        assert not st[:, i, d["q"] + 1:qmax + 1].any()
+    # sweeps without records keep the running statistics exact as well
+    sim.sweep(3)
+    cur = sim.current_stats().cpu().numpy()
+    for i, d in enumerate(POTTS_STRIP):
+        assert np.array_equal(cur[i, :d["q"] + 1], oracle.potts_stats(lattice_np(sim, i), d["q"])), i
+
+
 @pytest.mark.parametrize("q", [3, 8])
 def test_potts_full_size_sampled(q):
     lats = wl.potts_batch(q)
