@@ -232,28 +232,37 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+KERNEL_SECTIONS = {
+    "ising_strip_kernel": ("sweep_ising.cu",
+                           "// ------------------------------------------------------------------ strip kernel",
+                           "// Copy every lattice"),
+    "potts_strip_kernel": ("sweep_potts.cu",
+                           "// ------------------------------------------------------------ strip kernel",
+                           "__global__ void __launch_bounds__(256) potts_plain_kernel("),
+}
+
+
 def kernel_source_hash(kernel="ising_strip_kernel"):
-    """Hash of the source of one kernel's section of sweep_ising.cu plus the
-    shared device header, so that counters taken on an unchanged kernel stay
+    """Hash of the source of one kernel's section of its .cu file plus the
+    shared device headers, so that counters taken on an unchanged kernel stay
     valid while other code in the file changes."""
     csrc = os.path.join(ROOT, "paper_2304_01772_gb300", "csrc")
-    text = open(os.path.join(csrc, "sweep_ising.cu")).read()
-    marks = {"ising_strip_kernel": ("// ------------------------------------------------------------------ strip kernel",
-                                    "// Copy every lattice")}
-    a, b = marks.get(kernel, ("", ""))
-    if a in text and b in text:
+    fname, a, b = KERNEL_SECTIONS.get(kernel, ("sweep_ising.cu", "", ""))
+    text = open(os.path.join(csrc, fname)).read()
+    if a and a in text and b in text:
         text = text[text.index(a):text.index(b)]
     h = hashlib.sha256(text.encode())
-    h.update(open(os.path.join(csrc, "internal.h"), "rb").read())
+    for hdr in ("internal.h", "strip.cuh"):
+        h.update(open(os.path.join(csrc, hdr), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
+def ncu_traffic(kernel, workload="uneven512"):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or
     None if absent or taken on a different kernel source."""
     if not kernel:
         return None
-    path = os.path.join(ROOT, "profiles", f"{kernel.replace('_kernel', '')}_uneven512.txt")
+    path = os.path.join(ROOT, "profiles", f"{kernel.replace('_kernel', '')}_{workload}.txt")
     try:
         kv = {}
         for line in open(path):
@@ -526,6 +535,7 @@ def run_secondary(args):
             peak, kind = measured_peaks()
             ach = 2.0 * units / (kms / kn * 1e-3) / 1e9
             line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                "traffic": ncu_traffic(kname, args.workload),
                                 "kernel": kname, "launch_ms": kms / kn,
                                 "note": "64 MiB state + partner ~ L2 size: largely L2-resident",
                                 "peak_source": f"{kind} hbm_gbs"}

@@ -334,7 +334,9 @@ int plan(spin_ctx *ctx) {
     ctx->d_strip = nullptr;
     ctx->n_strip = 0;
     if (!strip_ids.empty()) {
-        ctx->strip_warps = ctx->threads >= 512 ? 8 : 4;
+        // Ising: 8 warps per block from 512 threads; Potts (more registers,
+        // measured faster with 8) from 256.
+        ctx->strip_warps = ctx->threads >= (ctx->model == SPIN_ISING ? 512 : 256) ? 8 : 4;
         int per_sm = 0;
         if (ctx->model == SPIN_ISING)
             CK(occupancy_ising_strip(&per_sm, ctx->strip_warps));

@@ -24,72 +24,118 @@ __device__ __forceinline__ int pair_index(int a, int b, int n) {
     return lo * n - lo * (lo - 1) / 2 + (hi - lo);
 }
 
-__global__ void __launch_bounds__(256) cpm_substep_kernel(CpmArgs a, int c) {
+// Most copy attempts pick a neighbour of the same cell and change nothing.
+// A block therefore works in passes over kCpmGroupsPerThread Philox groups per
+// thread: phase 1 draws the randoms, reads the site and the chosen neighbour
+// and queues the attempts whose ids differ in shared memory; phase 2 spreads
+// the queued attempts over all threads for the full energy change.  Attempts
+// of one colour are independent (none is a Moore neighbour of another, and
+// areas come from the snapshot), and the area and contact updates are integer
+// additions, so the result does not depend on the order.
+constexpr int kCpmThreads = 256;
+constexpr int kCpmGroupsPerThread = 1;
+constexpr int kCpmQueue = 2 * kCpmThreads * kCpmGroupsPerThread;
+
+__device__ __forceinline__ int wrapc(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
+
+__global__ void __launch_bounds__(kCpmThreads) cpm_substep_kernel(CpmArgs a, int c) {
     __shared__ int sJ[64];
     __shared__ int scnt[36];
+    __shared__ int4 queue[kCpmQueue];   // (y << 16 | x, id of the site, id copied in, u0)
+    __shared__ int qn;
     const int nt = a.n_types;
     for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) sJ[k] = a.J[k];
     for (int k = threadIdx.x; k < 36; k += blockDim.x) scnt[k] = 0;
+    if (threadIdx.x == 0) qn = 0;
     __syncthreads();
     const int L = a.L, Lq = L >> 2;
     const uint32_t t = a.state->t;
     const int cx = c & 1, cy = c >> 1;
     const int n_groups = (L >> 1) * Lq;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n_groups; g += gridDim.x * blockDim.x) {
-        const int yh = g / Lq, m = g - yh * Lq;
-        const int y = 2 * yh + cy;
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)g, a.lat, t, (uint32_t)c), a.k0, a.k1);
+    const int per_pass = kCpmThreads * kCpmGroupsPerThread;
+    for (int base = blockIdx.x * per_pass; base < n_groups; base += gridDim.x * per_pass) {
+        // phase 1: candidates (all four id loads of a thread in flight at once)
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int x = 4 * m + cx + 2 * half;
-            const uint32_t u0 = half ? r.z : r.x;
-            const uint32_t u1 = half ? r.w : r.y;
-            const int nbi = (int)(u1 >> 29);
-            const int site = y * L + x;
-            const int sg = a.ids[site];
-            int yy = y + kMooreDy[nbi], xx = x + kMooreDx[nbi];
-            yy = yy < 0 ? yy + L : (yy >= L ? yy - L : yy);
-            xx = xx < 0 ? xx + L : (xx >= L ? xx - L : xx);
-            const int sp = a.ids[yy * L + xx];
-            if (sp == sg) continue;
-            if ((unsigned)sg > (unsigned)a.n_cells || (unsigned)sp > (unsigned)a.n_cells) continue;
+        for (int k = 0; k < kCpmGroupsPerThread; ++k) {
+            const int g = base + k * kCpmThreads + (int)threadIdx.x;
+            const bool live = g < n_groups;
+            const int gg = live ? g : 0;
+            const int yh = gg / Lq, m = gg - yh * Lq;
+            const int y = 2 * yh + cy;
+            const uint4 r = philox4x32_10(make_uint4((uint32_t)gg, a.lat, t, (uint32_t)c), a.k0, a.k1);
+            const int x0 = 4 * m + cx, x1 = x0 + 2;
+            const int n0 = (int)(r.y >> 29), n1 = (int)(r.w >> 29);
+            const int yn0 = wrapc(y + kMooreDy[n0], L), yn1 = wrapc(y + kMooreDy[n1], L);
+            const int xn0 = wrapc(x0 + kMooreDx[n0], L), xn1 = wrapc(x1 + kMooreDx[n1], L);
+            const int sg0 = a.ids[y * L + x0], sg1 = a.ids[y * L + x1];
+            const int sp0 = a.ids[yn0 * L + xn0], sp1 = a.ids[yn1 * L + xn1];
+            const unsigned nc = (unsigned)a.n_cells;
+            if (live && sp0 != sg0 && (unsigned)sg0 <= nc && (unsigned)sp0 <= nc)
+                queue[atomicAdd(&qn, 1)] = make_int4((y << 16) | x0, sg0, sp0, (int)r.x);
+            if (live && sp1 != sg1 && (unsigned)sg1 <= nc && (unsigned)sp1 <= nc)
+                queue[atomicAdd(&qn, 1)] = make_int4((y << 16) | x1, sg1, sp1, (int)r.z);
+        }
+        __syncthreads();
+        const int n = qn;
+        // phase 2: energy change and Metropolis decision of the queued attempts
+        for (int e = threadIdx.x; e < n; e += kCpmThreads) {
+            const int4 qe = queue[e];
+            const int y = qe.x >> 16, x = qe.x & 0xFFFF, sg = qe.y, sp = qe.z;
+            const uint32_t u0 = (uint32_t)qe.w;
             const int tg = a.type[sg], tp = a.type[sp];
-            int nz[8];
+            const int vp = a.vol_cur[sp], vg = a.vol_cur[sg];
+            int nz[8], tzs[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int sz = a.ids[wrapc(y + kMooreDy[k], L) * L + wrapc(x + kMooreDx[k], L)];
+                nz[k] = (unsigned)sz > (unsigned)a.n_cells ? 0 : sz;   // out-of-range ids read as medium
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) tzs[k] = a.type[nz[k]];
             long long dH = 0;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                int zy = y + kMooreDy[k], zx = x + kMooreDx[k];
-                zy = zy < 0 ? zy + L : (zy >= L ? zy - L : zy);
-                zx = zx < 0 ? zx + L : (zx >= L ? zx - L : zx);
-                int sz = a.ids[zy * L + zx];
-                sz = (unsigned)sz > (unsigned)a.n_cells ? 0 : sz;   // out-of-range ids read as medium
-                nz[k] = sz;
-                const int tz = a.type[sz];
-                if (sz != sp) dH += sJ[tp * nt + tz];
-                if (sz != sg) dH -= sJ[tg * nt + tz];
+                if (nz[k] != sp) dH += sJ[tp * nt + tzs[k]];
+                if (nz[k] != sg) dH -= sJ[tg * nt + tzs[k]];
             }
-            if (sp != 0) dH += (long long)a.lambda * (2ll * ((long long)a.vol_cur[sp] - a.target) + 1);
-            if (sg != 0) dH += (long long)a.lambda * (-2ll * ((long long)a.vol_cur[sg] - a.target) + 1);
+            if (sp != 0) dH += (long long)a.lambda * (2ll * ((long long)vp - a.target) + 1);
+            if (sg != 0) dH += (long long)a.lambda * (-2ll * ((long long)vg - a.target) + 1);
             bool acc;
             if (dH <= 0)
                 acc = true;
             else
                 acc = u0 <= (dH < a.n_thr ? a.thr[dH] : 0u);
             if (acc) {
-                a.ids[site] = sp;
+                a.ids[y * L + x] = sp;
                 atomicAdd(a.vol_next + sp, 1);
                 atomicAdd(a.vol_next + sg, -1);
+                if (nt <= 4) {
+                    // contacts lost (by sg) and gained (by sp) per neighbour type, one byte each
+                    uint32_t lost = 0, gained = 0;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int sz = nz[k];
-                    const int tz = a.type[sz];
-                    if (sz != sg) atomicAdd(scnt + pair_index(tg, tz, nt), -1);
-                    if (sz != sp) atomicAdd(scnt + pair_index(tp, tz, nt), 1);
+                    for (int k = 0; k < 8; ++k) {
+                        const uint32_t one = 1u << (8 * tzs[k]);
+                        lost += nz[k] != sg ? one : 0u;
+                        gained += nz[k] != sp ? one : 0u;
+                    }
+                    for (int tz = 0; tz < nt; ++tz) {
+                        const int l = (int)((lost >> (8 * tz)) & 0xFFu), gn = (int)((gained >> (8 * tz)) & 0xFFu);
+                        if (l) atomicAdd(scnt + pair_index(tg, tz, nt), -l);
+                        if (gn) atomicAdd(scnt + pair_index(tp, tz, nt), gn);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (nz[k] != sg) atomicAdd(scnt + pair_index(tg, tzs[k], nt), -1);
+                        if (nz[k] != sp) atomicAdd(scnt + pair_index(tp, tzs[k], nt), 1);
+                    }
                 }
             }
         }
+        __syncthreads();
+        if (threadIdx.x == 0) qn = 0;
+        __syncthreads();
     }
-    __syncthreads();
     const int npair = nt * (nt + 1) / 2;
     for (int k = threadIdx.x; k < npair; k += blockDim.x)
         if (scnt[k]) atomicAdd(reinterpret_cast<unsigned long long *>(a.delta + k), (unsigned long long)(long long)scnt[k]);
@@ -186,9 +232,10 @@ __global__ void cpm_types_kernel(uint8_t *type, int n_cells, uint32_t lat, uint3
 
 cudaError_t launch_cpm_substep(const CpmArgs &a, int colour, cudaStream_t s) {
     const int n_groups = (a.L >> 1) * (a.L >> 2);
-    int blocks = (n_groups + 255) / 256;
+    const int per_pass = kCpmThreads * kCpmGroupsPerThread;
+    int blocks = (n_groups + per_pass - 1) / per_pass;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    cpm_substep_kernel<<<blocks, 256, 0, s>>>(a, colour);
+    cpm_substep_kernel<<<blocks, kCpmThreads, 0, s>>>(a, colour);
     return cudaGetLastError();
 }
 
