@@ -52,6 +52,8 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _f = ctypes.c_float
 _i = ctypes.c_int
+_d = ctypes.c_double
+_dp = ctypes.POINTER(ctypes.c_double)
 _u32 = ctypes.c_uint32
 _u64 = ctypes.c_uint64
 
@@ -80,6 +82,11 @@ def _declare(L):
         "or_cpm_run": (None, [_i, _i, _i32p, _i, _i, _i, _u8p, _f, _u64, _u32, _u32, _i,
                               _i32p, _i32p, _i64p]),
         "or_cpm_energy": (ctypes.c_int64, [_i, _i, _i32p, _i, _i, _i, _u8p, _i32p]),
+        "or_dmc_substep": (None, [_i, _dp, _dp, _d, _d, _d, _u64, _u32, _u32, _i, _dp]),
+        "or_dmc_run": (None, [_i, _dp, _dp, _d, _d, _d, _u64, _u32, _u32, _i, _dp, _dp]),
+        "or_dmc_backward": (None, [_i, _dp, _dp, _d, _d, _d, _u64, _u32, _u32, _i, _dp, _dp, _dp, _dp]),
+        "or_dmc_loss": (_d, [_i, _dp, _dp, _dp]),
+        "or_dmc_discretize": (None, [_i, _dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

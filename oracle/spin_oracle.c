@@ -29,7 +29,9 @@
  *
  * parity pinned: Philox by published known-answer vectors; the chains by
  * exact enumeration (4x4), Onsager's solution, detailed balance, the q=2
- * Potts/Ising identity and CPM bookkeeping invariants (see tests/).
+ * Potts/Ising identity and CPM bookkeeping invariants; the differentiable
+ * Monte Carlo of Alg. 2 by finite differences of its forward pass, its
+ * alpha -> infinity Metropolis limit and a closed form (see tests/).
  */
 #include <math.h>
 #include <stdint.h>
@@ -437,4 +439,142 @@ int64_t or_cpm_energy(int L, int n_types, const int32_t *Jtab, int lambda, int t
     for (int c = 1; c <= n_cells; ++c) H += area_energy(&p, c, area[c]);
     free(area);
     return H;
+}
+
+/* ------------------------------------------------------------------ */
+/* Differentiable Monte Carlo (Alg. 2, Sec. "Methods"), Ising model    */
+/* with one exchange parameter per bond (the J_ij optimised in Sec.     */
+/* "Optimization of the exchange parameters").  Relaxed spins s in      */
+/* [-1, 1]; Jr[y*L+x] couples (x,y)-(x+1,y), Jd[y*L+x] couples          */
+/* (x,y)-(x,y+1), periodic.  Sub-step of colour c, every site i with    */
+/* (x+y)&1 == c at once (checkerboard):                                 */
+/*   n   = sum_j J_ij s_j            (weighted neighbour sum)           */
+/*   dE  = E(s') - E(s) = 2 s (n + h)  for the proposal s' = -s under   */
+/*         H = -sum_<ij> J_ij s_i s_j - h sum_i s_i                     */
+/*   p   = exp(-beta dE)             (not clipped: Alg. 2 takes it as is)*/
+/*   r   = (u >> 8) 2^-24, u the site's Philox lane (Ising layout)      */
+/*   q   = 1 / (1 + exp(-alpha (p - r)))                                */
+/*   s  <- q s' + (1 - q) s = s (1 - 2 q).                              */
+/* The reverse pass is the chain rule through these steps, written by   */
+/* hand: with w = dL/ds_new(i) * ds_new/dn,                              */
+/*   ds_new/ds = (1 - 2q) + 4 alpha beta p q (1-q) s (n + h)            */
+/*   ds_new/dn = 4 alpha beta p q (1-q) s^2                             */
+/*   dL/ds_old(j) += w J_ij, dL/dJ_ij += w s_j   (j a neighbour of i).   */
+/* parity pinned by central finite differences of the forward pass, the */
+/* alpha -> infinity limit (Metropolis with acceptance r < exp(-b dE)),  */
+/* and the J = h = 0 closed form (see tests/).                           */
+/* ------------------------------------------------------------------ */
+static double dmc_r(uint64_t seed, uint32_t lattice, uint32_t sweep, int colour, int L, int x, int y)
+{
+    uint32_t k = (uint32_t)(y * L + x) >> 1;
+    uint32_t r[4];
+    draw4(seed, k >> 2, lattice, sweep, (uint32_t)colour, r);
+    return (double)(r[k & 3u] >> 8) * (1.0 / 16777216.0);
+}
+
+/* Weighted neighbour sum n_i = sum_j J_ij s_j of site (x, y). */
+static double dmc_field(int L, const double *Jr, const double *Jd, const double *s, int x, int y)
+{
+    int xl = wrap(x - 1, L), xr = wrap(x + 1, L), yu = wrap(y - 1, L), yd = wrap(y + 1, L);
+    return Jr[y * L + x] * s[y * L + xr] + Jr[y * L + xl] * s[y * L + xl]
+         + Jd[y * L + x] * s[yd * L + x] + Jd[yu * L + x] * s[yu * L + x];
+}
+
+void or_dmc_substep(int L, const double *Jr, const double *Jd, double beta, double h, double alpha,
+                    uint64_t seed, uint32_t lattice, uint32_t sweep, int colour, double *s)
+{
+    for (int y = 0; y < L; ++y)
+        for (int x = 0; x < L; ++x) {
+            if (((x + y) & 1) != colour) continue;
+            double si = s[y * L + x];
+            double n = dmc_field(L, Jr, Jd, s, x, y);
+            double dE = 2.0 * si * (n + h);
+            double p = exp(-beta * dE);
+            double r = dmc_r(seed, lattice, sweep, colour, L, x, y);
+            double q = 1.0 / (1.0 + exp(-alpha * (p - r)));
+            s[y * L + x] = q * (-si) + (1.0 - q) * si;
+        }
+}
+
+/* n_sweeps sweeps (colour 0 then 1) starting at sweep index sweep0; tape */
+/* (nullable) receives the full state before each of the 2 n_sweeps       */
+/* sub-steps, [2 n_sweeps][L*L].                                           */
+void or_dmc_run(int L, const double *Jr, const double *Jd, double beta, double h, double alpha,
+                uint64_t seed, uint32_t lattice, uint32_t sweep0, int n_sweeps, double *s, double *tape)
+{
+    for (int t = 0; t < n_sweeps; ++t)
+        for (int c = 0; c < 2; ++c) {
+            if (tape) memcpy(tape + (size_t)(2 * t + c) * (size_t)(L * L), s, sizeof(double) * (size_t)(L * L));
+            or_dmc_substep(L, Jr, Jd, beta, h, alpha, seed, lattice, sweep0 + (uint32_t)t, c, s);
+        }
+}
+
+/* Reverse pass through the sub-steps recorded in `tape`.  g: on entry     */
+/* dL/ds after the last sub-step, on exit dL/ds before the first; gJr, gJd */
+/* receive dL/dJ (overwritten).                                            */
+void or_dmc_backward(int L, const double *Jr, const double *Jd, double beta, double h, double alpha,
+                     uint64_t seed, uint32_t lattice, uint32_t sweep0, int n_sweeps,
+                     const double *tape, double *g, double *gJr, double *gJd)
+{
+    size_t N = (size_t)(L * L);
+    double *w = (double *)calloc(N, sizeof(double));
+    memset(gJr, 0, sizeof(double) * N);
+    memset(gJd, 0, sizeof(double) * N);
+    for (int k = 2 * n_sweeps - 1; k >= 0; --k) {
+        const double *s = tape + (size_t)k * N;            /* state before sub-step k */
+        int colour = k & 1;
+        uint32_t sweep = sweep0 + (uint32_t)(k >> 1);
+        /* active sites: w_i and the direct term */
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                int i = y * L + x;
+                if (((x + y) & 1) != colour) { w[i] = 0.0; continue; }
+                double si = s[i];
+                double n = dmc_field(L, Jr, Jd, s, x, y);
+                double p = exp(-beta * 2.0 * si * (n + h));
+                double r = dmc_r(seed, lattice, sweep, colour, L, x, y);
+                double q = 1.0 / (1.0 + exp(-alpha * (p - r)));
+                double common = 4.0 * alpha * beta * p * q * (1.0 - q);
+                w[i] = g[i] * common * si * si;
+                g[i] = g[i] * ((1.0 - 2.0 * q) + common * si * (n + h));
+            }
+        /* bonds: one end is active (weight w), the other passive */
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                int i = y * L + x;
+                int ir = y * L + wrap(x + 1, L), id = wrap(y + 1, L) * L + x;
+                /* bond (i, ir) with coupling Jr[i]; bond (i, id) with Jd[i] */
+                gJr[i] += w[i] * s[ir] + w[ir] * s[i];
+                gJd[i] += w[i] * s[id] + w[id] * s[i];
+            }
+        /* passive sites: dL/ds_old(j) = dL/ds_new(j) + sum_i w_i J_ij */
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                if (((x + y) & 1) == colour) continue;
+                int j = y * L + x;
+                int xl = wrap(x - 1, L), xr = wrap(x + 1, L), yu = wrap(y - 1, L), yd = wrap(y + 1, L);
+                g[j] += w[y * L + xr] * Jr[j] + w[y * L + xl] * Jr[y * L + xl]
+                      + w[yd * L + x] * Jd[j] + w[yu * L + x] * Jd[yu * L + x];
+            }
+    }
+    free(w);
+}
+
+/* L = sum_i (target_i - s_i)^2 (Sec. "Optimization of the exchange       */
+/* parameters"); g = dL/ds = -2 (target - s).                             */
+double or_dmc_loss(int L, const double *s, const double *target, double *g)
+{
+    double loss = 0.0;
+    for (int i = 0; i < L * L; ++i) {
+        double d = target[i] - s[i];
+        loss += d * d;
+        if (g) g[i] = -2.0 * d;
+    }
+    return loss;
+}
+
+/* Discretisation after the parameter update: s <- -1 if s < 0, else +1. */
+void or_dmc_discretize(int n, double *s)
+{
+    for (int i = 0; i < n; ++i) s[i] = s[i] < 0.0 ? -1.0 : 1.0;
 }
