@@ -267,6 +267,51 @@ int spin_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t 
 int spin_adam(float *params, const float *grad, float *m, float *v, int32_t n, int32_t step, float lr,
               float beta1, float beta2, float eps, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Differentiable Monte Carlo (Alg. 2, Sec. "Methods"; used in Sec.
+ * "Optimization of the exchange parameters" to steer an Ising lattice
+ * towards a target pattern by optimising one exchange parameter per bond).
+ *
+ * Relaxed spins s in [-1, 1], float32.  A sweep is colour 0 then colour 1
+ * of the checkerboard ((x + y) & 1); in a sub-step every site of the colour
+ * takes, at once,
+ *   n = sum_j J_ij s_j,   dE = 2 s (n + h),   p = exp(-beta dE) (not clipped),
+ *   r = (u >> 8) * 2^-24, q = 1 / (1 + exp(-alpha (p - r))),
+ *   s <- q (-s) + (1 - q) s,
+ * for H = -sum_<ij> J_ij s_i s_j - h sum_i s_i.  u is the site's Philox4x32-10
+ * lane in the layout of the Ising sweep: key = (seed_lo, seed_hi), counter =
+ * (k >> 2, lattice, sweep, colour), lane k & 3, k = (y L + x) >> 1.  As alpha
+ * grows the update becomes Metropolis with acceptance r < exp(-beta dE).
+ *
+ * Layouts (device, float32, 16-byte aligned, caller-owned; nothing is
+ * allocated):  spins [n_lattices][L][L];  J [n_lattices][2][L][L] with
+ * J[l][0][y][x] the bond (x, y)-(x+1, y) and J[l][1][y][x] the bond
+ * (x, y)-(x, y+1), periodic;  tape [n_lattices][2 n_sweeps][L*L/2] (see
+ * spin_dmc_tape_floats).  Limits: 8 <= L <= 64, L % 8 == 0 (one lattice per
+ * thread block, held in shared memory); n_sweeps >= 1.  Return 0 or a
+ * negative SPIN_E* code (SPIN_EINVAL for arguments out of range).
+ * ------------------------------------------------------------------------ */
+/* Floats of the tape for n_lattices x n_sweeps sweeps; negative if invalid. */
+int64_t spin_dmc_tape_floats(int32_t n_lattices, int32_t L, int32_t n_sweeps);
+/* n_sweeps relaxed sweeps with sweep indices first_sweep, first_sweep + 1, ..
+ * on spins in place; tape receives the old values of each sub-step's active
+ * sites (compressed index k order).                                         */
+int spin_dmc_forward(uint64_t seed, int32_t n_lattices, int32_t L, float beta, float h, float alpha,
+                     const float *J, float *spins, uint32_t first_sweep, int32_t n_sweeps,
+                     float *tape, void *stream);
+/* Reverse pass of the same call.  spins: the state spin_dmc_forward left
+ * (read only); grad_spins: on entry dL/ds after the sweeps, on exit dL/ds
+ * before them; grad_J: dL/dJ, overwritten.                                  */
+int spin_dmc_backward(uint64_t seed, int32_t n_lattices, int32_t L, float beta, float h, float alpha,
+                      const float *J, const float *spins, const float *tape, uint32_t first_sweep,
+                      int32_t n_sweeps, float *grad_spins, float *grad_J, void *stream);
+/* Pattern loss per lattice, loss[l] = sum (target - s)^2 (float64), and
+ * grad_spins = -2 (target - s).                                              */
+int spin_dmc_loss(int32_t n_lattices, int32_t L, const float *spins, const float *target,
+                  float *grad_spins, double *loss, void *stream);
+/* Discretisation of n spins: s <- -1 if s < 0 else +1.                      */
+int spin_dmc_discretize(int64_t n, float *spins, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

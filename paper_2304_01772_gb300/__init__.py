@@ -78,6 +78,13 @@ _SIGS = {
                                         _i32, _vp, _vp]),
     "spin_adam": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                          ctypes.c_float, _vp]),
+    "spin_dmc_tape_floats": (ctypes.c_int64, [_i32, _i32, _i32]),
+    "spin_dmc_forward": (_i32, [ctypes.c_uint64, _i32, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                _vp, _vp, ctypes.c_uint32, _i32, _vp, _vp]),
+    "spin_dmc_backward": (_i32, [ctypes.c_uint64, _i32, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                 _vp, _vp, _vp, ctypes.c_uint32, _i32, _vp, _vp, _vp]),
+    "spin_dmc_loss": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp, _vp]),
+    "spin_dmc_discretize": (_i32, [ctypes.c_int64, _vp, _vp]),
     "spin_mlp_param_count": (_i32, []),
     "spin_mlp_forward": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "spin_mlp_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
@@ -387,3 +394,41 @@ def adam(params, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8, stream=None):
 def mlp_adam(params, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8, stream=None):
     _check(lib().spin_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr), float(b1),
                                float(b2), float(eps), _stream(stream)), None, "spin_mlp_adam")
+
+
+# --------------------------------------------------------------------------
+# differentiable Monte Carlo (Alg. 2): argument marshalling only
+# --------------------------------------------------------------------------
+def dmc_tape_floats(n_lattices, L, n_sweeps):
+    n = int(lib().spin_dmc_tape_floats(int(n_lattices), int(L), int(n_sweeps)))
+    if n < 0:
+        raise ValueError(f"spin_dmc_tape_floats: invalid geometry (L={L}, n_sweeps={n_sweeps})")
+    return n
+
+
+def dmc_forward(seed, J, spins, beta, h, alpha, first_sweep, n_sweeps, tape, stream=None):
+    """Relaxed sweeps in place on spins [B, L, L] (float32, device) with
+    couplings J [B, 2, L, L]; tape receives the active sites' old values."""
+    B, L = spins.shape[0], spins.shape[-1]
+    _check(lib().spin_dmc_forward(int(seed), B, L, float(beta), float(h), float(alpha), _ptr(J), _ptr(spins),
+                                  int(first_sweep), int(n_sweeps), _ptr(tape), _stream(stream)),
+           None, "spin_dmc_forward")
+
+
+def dmc_backward(seed, J, spins, tape, beta, h, alpha, first_sweep, n_sweeps, grad_spins, grad_J, stream=None):
+    """Reverse pass: grad_spins (in: dL/ds after, out: dL/ds before), grad_J out."""
+    B, L = spins.shape[0], spins.shape[-1]
+    _check(lib().spin_dmc_backward(int(seed), B, L, float(beta), float(h), float(alpha), _ptr(J), _ptr(spins),
+                                   _ptr(tape), int(first_sweep), int(n_sweeps), _ptr(grad_spins), _ptr(grad_J),
+                                   _stream(stream)), None, "spin_dmc_backward")
+
+
+def dmc_loss(spins, target, grad_spins, loss, stream=None):
+    B, L = spins.shape[0], spins.shape[-1]
+    _check(lib().spin_dmc_loss(B, L, _ptr(spins), _ptr(target), _ptr(grad_spins), _ptr(loss), _stream(stream)),
+           None, "spin_dmc_loss")
+
+
+def dmc_discretize(spins, stream=None):
+    _check(lib().spin_dmc_discretize(spins.numel(), _ptr(spins), _stream(stream)), None, "spin_dmc_discretize")
+

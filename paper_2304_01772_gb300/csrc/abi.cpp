@@ -1245,4 +1245,56 @@ int spin_mlp_adam(float *params, const float *grad, float *m, float *v, int32_t 
                : SPIN_ECUDA;
 }
 
+// ------------------------------------------------------------------ DMC
+static bool dmc_geom_ok(int32_t n_lattices, int32_t L, int32_t n_sweeps) {
+    return n_lattices >= 1 && L >= 8 && L <= 64 && L % 8 == 0 && n_sweeps >= 1 && n_sweeps <= (1 << 20);
+}
+
+static bool aligned16(const void *p) { return p && ((uintptr_t)p & 15u) == 0; }
+
+int64_t spin_dmc_tape_floats(int32_t n_lattices, int32_t L, int32_t n_sweeps) {
+    if (!dmc_geom_ok(n_lattices, L, n_sweeps)) return SPIN_EINVAL;
+    return (int64_t)n_lattices * 2 * n_sweeps * ((int64_t)L * L / 2);
+}
+
+static bool dmc_params_ok(float beta, float h, float alpha) {
+    return std::isfinite(beta) && std::isfinite(h) && std::isfinite(alpha) && beta >= 0.0f && alpha >= 0.0f;
+}
+
+int spin_dmc_forward(uint64_t seed, int32_t n_lattices, int32_t L, float beta, float h, float alpha,
+                     const float *J, float *spins, uint32_t first_sweep, int32_t n_sweeps, float *tape,
+                     void *stream) {
+    if (!dmc_geom_ok(n_lattices, L, n_sweeps) || !dmc_params_ok(beta, h, alpha)) return SPIN_EINVAL;
+    if (!aligned16(J) || !aligned16(spins) || !aligned16(tape)) return SPIN_EINVAL;
+    DmcArgs a{n_lattices, L, n_sweeps, first_sweep, beta, h, alpha, (uint32_t)seed, (uint32_t)(seed >> 32),
+              spins, J, tape, nullptr, nullptr};
+    return launch_dmc_forward(a, S(stream)) == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
+}
+
+int spin_dmc_backward(uint64_t seed, int32_t n_lattices, int32_t L, float beta, float h, float alpha,
+                      const float *J, const float *spins, const float *tape, uint32_t first_sweep,
+                      int32_t n_sweeps, float *grad_spins, float *grad_J, void *stream) {
+    if (!dmc_geom_ok(n_lattices, L, n_sweeps) || !dmc_params_ok(beta, h, alpha)) return SPIN_EINVAL;
+    if (!aligned16(J) || !aligned16(spins) || !aligned16(tape) || !aligned16(grad_spins) || !aligned16(grad_J))
+        return SPIN_EINVAL;
+    DmcArgs a{n_lattices, L, n_sweeps, first_sweep, beta, h, alpha, (uint32_t)seed, (uint32_t)(seed >> 32),
+              const_cast<float *>(spins), J, const_cast<float *>(tape), grad_spins, grad_J};
+    return launch_dmc_backward(a, S(stream)) == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
+}
+
+int spin_dmc_loss(int32_t n_lattices, int32_t L, const float *spins, const float *target, float *grad_spins,
+                  double *loss, void *stream) {
+    if (n_lattices < 1 || L < 2 || (int64_t)L * L > (1 << 30) || !spins || !target || !grad_spins || !loss)
+        return SPIN_EINVAL;
+    return launch_dmc_loss(n_lattices, L * L, spins, target, grad_spins, loss, S(stream)) == cudaSuccess
+               ? SPIN_OK
+               : SPIN_ECUDA;
+}
+
+int spin_dmc_discretize(int64_t n, float *spins, void *stream) {
+    if (n < 0 || (n > 0 && !spins)) return SPIN_EINVAL;
+    if (n == 0) return SPIN_OK;
+    return launch_dmc_discretize(n, spins, S(stream)) == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
+}
+
 }  // extern "C"

@@ -1,0 +1,239 @@
+// dmc.cu -- differentiable Monte Carlo (Alg. 2 of Farias et al., arXiv
+// 2304.01772, Sec. "Methods"): relaxed checkerboard sweeps of Ising lattices
+// with one exchange parameter per bond, their reverse pass, the L2 pattern
+// loss and the discretisation of Sec. "Optimization of the exchange
+// parameters".
+//
+// Sub-step of colour c, every site i with (x + y) & 1 == c at once:
+//   n = sum_j J_ij s_j,  dE = 2 s (n + h)  (proposal s' = -s under
+//   H = -sum J_ij s_i s_j - h sum s_i),  p = exp(-beta dE) (not clipped),
+//   r = (u >> 8) 2^-24 (u: the site's Philox lane, Ising layout: counter
+//   (k >> 2, lattice, sweep, c), lane k & 3, k = (y L + x) >> 1),
+//   q = 1 / (1 + exp(-alpha (p - r))),  s <- q s' + (1 - q) s.
+// Reverse pass, with w_i = dL/ds_new(i) * 4 alpha beta p q (1 - q) s_i^2:
+//   dL/ds_old(i) = dL/ds_new(i) ((1 - 2q) + 4 alpha beta p q (1 - q) s_i (n_i + h)),
+//   dL/ds_old(j) = dL/ds_new(j) + sum_i w_i J_ij  (j passive),
+//   dL/dJ_ij += w_i s_j.
+//
+// One block per lattice; the lattice (L <= 64, L % 8 == 0) lives in shared
+// memory for all sub-steps.  The forward pass records only the old values of
+// each sub-step's active sites (the passive ones do not change), so the tape
+// costs 2 B per site and sub-step; the reverse pass restores them in turn.
+// Each bond has exactly one passive end per sub-step, whose thread updates
+// its gradient: no atomics.  Arithmetic is float32 as in the paper's PyTorch
+// form; expf is CUDA's.
+#include "internal.h"
+
+namespace spinmc {
+
+namespace {
+
+constexpr int kDmcThreads = 256;
+
+struct DmcGeom {
+    int L, half, N;   // side, L / 2, L * L
+};
+
+// Active site of compressed index k for colour c: row y = k / half,
+// x = 2 (k % half) + ((y + c) & 1).
+__device__ __forceinline__ int dmc_site(const DmcGeom &g, int k, int c) {
+    const int y = k / g.half, m = k - y * g.half;
+    return y * g.L + 2 * m + ((y + c) & 1);
+}
+
+__device__ __forceinline__ float dmc_uniform(uint32_t u) { return (float)(u >> 8) * (1.0f / 16777216.0f); }
+
+// Weighted neighbour sum of site i = (x, y).
+__device__ __forceinline__ float dmc_field(const DmcGeom &g, const float *s, const float *Jr,
+                                           const float *Jd, int i) {
+    const int y = i / g.L, x = i - y * g.L;
+    const int xl = x == 0 ? g.L - 1 : x - 1, xr = x == g.L - 1 ? 0 : x + 1;
+    const int yu = y == 0 ? g.L - 1 : y - 1, yd = y == g.L - 1 ? 0 : y + 1;
+    return Jr[i] * s[y * g.L + xr] + Jr[y * g.L + xl] * s[y * g.L + xl] + Jd[i] * s[yd * g.L + x] +
+           Jd[yu * g.L + x] * s[yu * g.L + x];
+}
+
+__device__ __forceinline__ void load_f4(float *dst, const float *src, int n) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    for (int v = threadIdx.x; v < n / 4; v += blockDim.x) d4[v] = s4[v];
+}
+
+__device__ __forceinline__ void store_f4(float *dst, const float *src, int n) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    for (int v = threadIdx.x; v < n / 4; v += blockDim.x) d4[v] = s4[v];
+}
+
+__global__ void __launch_bounds__(kDmcThreads) dmc_forward_kernel(DmcArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    const DmcGeom g{a.L, a.L / 2, a.L * a.L};
+    float *s = sm, *Jr = sm + g.N, *Jd = sm + 2 * g.N;
+    const int n_sub = 2 * a.n_sweeps, ngroups = g.N / 8;
+    for (int lat = blockIdx.x; lat < a.n_lat; lat += gridDim.x) {
+        load_f4(s, a.spins + (size_t)lat * g.N, g.N);
+        load_f4(Jr, a.J + (size_t)lat * 2 * g.N, g.N);
+        load_f4(Jd, a.J + (size_t)lat * 2 * g.N + g.N, g.N);
+        __syncthreads();
+        float *tape = a.tape + (size_t)lat * n_sub * (g.N / 2);
+        for (int sub = 0; sub < n_sub; ++sub) {
+            const int c = sub & 1;
+            const uint32_t sweep = a.first_sweep + (uint32_t)(sub >> 1);
+            for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x) {
+                const uint4 r4 = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)lat, sweep, (uint32_t)c),
+                                               a.k0, a.k1);
+                const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
+                float old[4];
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    const int i = dmc_site(g, 4 * grp + l, c);
+                    const float si = s[i];
+                    const float n = dmc_field(g, s, Jr, Jd, i);
+                    const float p = expf(-a.beta * (2.0f * si * (n + a.h)));
+                    const float q = 1.0f / (1.0f + expf(-a.alpha * (p - dmc_uniform(rr[l]))));
+                    old[l] = si;
+                    s[i] = q * (-si) + (1.0f - q) * si;
+                }
+                reinterpret_cast<float4 *>(tape + (size_t)sub * (g.N / 2))[grp] =
+                    make_float4(old[0], old[1], old[2], old[3]);
+            }
+            __syncthreads();
+        }
+        store_f4(a.spins + (size_t)lat * g.N, s, g.N);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kDmcThreads) dmc_backward_kernel(DmcArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    const DmcGeom g{a.L, a.L / 2, a.L * a.L};
+    float *s = sm, *gs = sm + g.N, *Jr = sm + 2 * g.N, *Jd = sm + 3 * g.N;
+    float *gJr = sm + 4 * g.N, *gJd = sm + 5 * g.N, *w = sm + 6 * g.N;   // w: N / 2
+    const int n_sub = 2 * a.n_sweeps, ngroups = g.N / 8;
+    const float c4 = 4.0f * a.alpha * a.beta;
+    for (int lat = blockIdx.x; lat < a.n_lat; lat += gridDim.x) {
+        load_f4(s, a.spins + (size_t)lat * g.N, g.N);
+        load_f4(gs, a.grad_spins + (size_t)lat * g.N, g.N);
+        load_f4(Jr, a.J + (size_t)lat * 2 * g.N, g.N);
+        load_f4(Jd, a.J + (size_t)lat * 2 * g.N + g.N, g.N);
+        for (int i = threadIdx.x; i < g.N; i += blockDim.x) gJr[i] = gJd[i] = 0.0f;
+        __syncthreads();
+        const float *tape = a.tape + (size_t)lat * n_sub * (g.N / 2);
+        for (int sub = n_sub - 1; sub >= 0; --sub) {
+            const int c = sub & 1;
+            const uint32_t sweep = a.first_sweep + (uint32_t)(sub >> 1);
+            // active sites: restore the old value, form w and the direct term
+            for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x) {
+                const uint4 r4 = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)lat, sweep, (uint32_t)c),
+                                               a.k0, a.k1);
+                const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
+                const float4 o4 = reinterpret_cast<const float4 *>(tape + (size_t)sub * (g.N / 2))[grp];
+                const float old[4] = {o4.x, o4.y, o4.z, o4.w};
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    const int i = dmc_site(g, 4 * grp + l, c);
+                    const float si = old[l];
+                    const float n = dmc_field(g, s, Jr, Jd, i);
+                    const float p = expf(-a.beta * (2.0f * si * (n + a.h)));
+                    const float q = 1.0f / (1.0f + expf(-a.alpha * (p - dmc_uniform(rr[l]))));
+                    const float common = c4 * p * q * (1.0f - q);
+                    const float gi = gs[i];
+                    w[4 * grp + l] = gi * common * si * si;
+                    gs[i] = gi * ((1.0f - 2.0f * q) + common * si * (n + a.h));
+                    s[i] = si;
+                }
+            }
+            __syncthreads();
+            // passive sites: their adjoint gains sum_i w_i J_ij; their four bonds gain w_i s_j
+            for (int k = threadIdx.x; k < g.N / 2; k += blockDim.x) {
+                const int j = dmc_site(g, k, c ^ 1);
+                const int y = j / g.L, x = j - y * g.L;
+                const int xl = x == 0 ? g.L - 1 : x - 1, xr = x == g.L - 1 ? 0 : x + 1;
+                const int yu = y == 0 ? g.L - 1 : y - 1, yd = y == g.L - 1 ? 0 : y + 1;
+                const int iL = y * g.L + xl, iR = y * g.L + xr, iU = yu * g.L + x, iD = yd * g.L + x;
+                const float wl = w[iL >> 1], wr = w[iR >> 1], wu = w[iU >> 1], wd = w[iD >> 1];
+                const float sj = s[j];
+                gs[j] += wr * Jr[j] + wl * Jr[iL] + wd * Jd[j] + wu * Jd[iU];
+                gJr[j] += wr * sj;
+                gJr[iL] += wl * sj;
+                gJd[j] += wd * sj;
+                gJd[iU] += wu * sj;
+            }
+            __syncthreads();
+        }
+        store_f4(a.grad_spins + (size_t)lat * g.N, gs, g.N);
+        store_f4(a.grad_J + (size_t)lat * 2 * g.N, gJr, g.N);
+        store_f4(a.grad_J + (size_t)lat * 2 * g.N + g.N, gJd, g.N);
+        __syncthreads();
+    }
+}
+
+// loss[lat] = sum (target - s)^2 (double); grad = -2 (target - s).
+__global__ void __launch_bounds__(kDmcThreads) dmc_loss_kernel(int n_lat, int N, const float *spins,
+                                                               const float *target, float *grad,
+                                                               double *loss) {
+    __shared__ double red[kDmcThreads / 32];
+    for (int lat = blockIdx.x; lat < n_lat; lat += gridDim.x) {
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const size_t o = (size_t)lat * N + i;
+            const float d = target[o] - spins[o];
+            acc += (double)d * (double)d;
+            grad[o] = -2.0f * d;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < kDmcThreads / 32; ++k) t += red[k];
+            loss[lat] = t;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void dmc_discretize_kernel(int64_t n, float *s) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s[i] = s[i] < 0.0f ? -1.0f : 1.0f;
+}
+
+int dmc_grid(int n_lat, int per_sm) { return n_lat < 152 * per_sm ? n_lat : 152 * per_sm; }
+
+}  // namespace
+
+size_t dmc_forward_smem(int L) { return sizeof(float) * 3 * (size_t)L * L; }
+size_t dmc_backward_smem(int L) { return sizeof(float) * (6 * (size_t)L * L + (size_t)L * L / 2); }
+
+cudaError_t launch_dmc_forward(const DmcArgs &a, cudaStream_t s) {
+    const size_t sm = dmc_forward_smem(a.L);
+    cudaError_t e = cudaFuncSetAttribute(dmc_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e) return e;
+    dmc_forward_kernel<<<dmc_grid(a.n_lat, 4), kDmcThreads, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dmc_backward(const DmcArgs &a, cudaStream_t s) {
+    const size_t sm = dmc_backward_smem(a.L);
+    cudaError_t e = cudaFuncSetAttribute(dmc_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e) return e;
+    dmc_backward_kernel<<<dmc_grid(a.n_lat, 2), kDmcThreads, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dmc_loss(int n_lat, int N, const float *spins, const float *target, float *grad,
+                            double *loss, cudaStream_t s) {
+    dmc_loss_kernel<<<dmc_grid(n_lat, 8), kDmcThreads, 0, s>>>(n_lat, N, spins, target, grad, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dmc_discretize(int64_t n, float *spins, cudaStream_t s) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    dmc_discretize_kernel<<<blocks, 256, 0, s>>>(n, spins);
+    return cudaGetLastError();
+}
+
+}  // namespace spinmc

@@ -193,6 +193,28 @@ struct CpmArgs {
     int64_t *delta;          // [pairs] contact changes
 };
 cudaError_t launch_cpm_substep(const CpmArgs &a, int colour, cudaStream_t s);
+
+// Differentiable Monte Carlo (Alg. 2): relaxed sweeps with one coupling per
+// bond.  spins [n_lat][L*L]; J [n_lat][2][L*L] (right, down bonds); tape
+// [n_lat][2 n_sweeps][L*L/2] (old values of each sub-step's active sites).
+struct DmcArgs {
+    int n_lat, L, n_sweeps;
+    uint32_t first_sweep;
+    float beta, h, alpha;
+    uint32_t k0, k1;
+    float *spins;           // forward: in/out; backward: the state after the last sub-step
+    const float *J;
+    float *tape;            // forward: out; backward: in
+    float *grad_spins;      // backward: in dL/ds after, out dL/ds before
+    float *grad_J;          // backward: out
+};
+size_t dmc_forward_smem(int L);
+size_t dmc_backward_smem(int L);
+cudaError_t launch_dmc_forward(const DmcArgs &a, cudaStream_t s);
+cudaError_t launch_dmc_backward(const DmcArgs &a, cudaStream_t s);
+cudaError_t launch_dmc_loss(int n_lat, int N, const float *spins, const float *target, float *grad,
+                            double *loss, cudaStream_t s);
+cudaError_t launch_dmc_discretize(int64_t n, float *spins, cudaStream_t s);
 // After a CPM colour sub-step: vol_cur = vol_next, contacts += delta; after
 // colour 3 also V2/V1, record, t += 1.
 cudaError_t launch_cpm_finalize(int32_t *vol_cur, const int32_t *vol_next, int n_cells,

@@ -9,6 +9,7 @@ import pytest
 import paper_2304_01772_gb300 as sm
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+EINVAL = -1
 
 
 def declared_symbols():
@@ -79,3 +80,19 @@ def test_pack_offsets_alignment():
     assert total == off[-1] + 16
     off4, _ = sm.pack_offsets([8, 8], elem=4, align=256)
     assert off4 == [0, 64]
+
+
+def test_dmc_entry_points_reject_invalid_arguments_on_the_host():
+    lib = sm.lib()
+    assert lib.spin_dmc_tape_floats(4, 16, 3) == 4 * 2 * 3 * 16 * 16 // 2
+    for B, L, n in [(0, 16, 1), (1, 12, 1), (1, 72, 1), (1, 4, 1), (1, 16, 0)]:
+        assert lib.spin_dmc_tape_floats(B, L, n) == EINVAL
+    buf = ctypes.c_void_p(256)   # aligned but never dereferenced: rejected first
+    bad_geom = lib.spin_dmc_forward(1, 1, 12, 0.5, 0.0, 1.0, buf, buf, 0, 1, buf, None)
+    bad_beta = lib.spin_dmc_forward(1, 1, 16, float("nan"), 0.0, 1.0, buf, buf, 0, 1, buf, None)
+    misaligned = lib.spin_dmc_forward(1, 1, 16, 0.5, 0.0, 1.0, ctypes.c_void_p(260), buf, 0, 1, buf, None)
+    null_ptr = lib.spin_dmc_backward(1, 1, 16, 0.5, 0.0, 1.0, buf, buf, buf, 0, 1, None, buf, None)
+    assert bad_geom == bad_beta == misaligned == null_ptr == EINVAL
+    assert lib.spin_dmc_discretize(-1, buf, None) == EINVAL
+    assert lib.spin_dmc_discretize(0, None, None) == 0
+    assert lib.spin_dmc_loss(0, 16, buf, buf, buf, buf, None) == EINVAL

@@ -1,0 +1,136 @@
+"""GPU parity of the differentiable Monte Carlo kernels (Alg. 2) against the
+float64 oracle.
+
+Tolerance.  The kernels compute in float32 (the paper's PyTorch arithmetic;
+expf is CUDA's, within 2 ulp).  Each sub-step evaluates about ten float
+operations per site, so it injects a relative rounding error of order
+10 eps32 (eps32 = 2^-24); later sub-steps propagate earlier errors with the
+trajectory's own sensitivity.  That sensitivity is measured on the oracle by
+perturbing the start spins by 1e-9 and recording the largest growth `cond` of
+the difference over the run (a finite-difference condition number), so the
+bound used below is  tol = 10 eps32 * n_substeps * max(cond, 1) * scale  (scale
+the largest magnitude of the compared quantity), with a factor 4 of margin.
+Integer-valued results (discretisation) and the loss gradient -2 (t - s) are
+exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2304_01772_gb300 as sm
+from oracle import dmc as odmc
+from paper_2304_01772_gb300 import dmc as pdmc
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x5EEDD3C0FFEE
+EPS32 = 2.0 ** -24
+
+
+def f32(x):
+    return float(np.float32(x))
+
+
+def make_case(B, L, seed):
+    rng = np.random.default_rng(seed)
+    J = rng.uniform(0.5, 1.5, size=(B, 2, L, L)).astype(np.float32)
+    s0 = rng.uniform(-1, 1, size=(B, L, L)).astype(np.float32)
+    target = rng.choice([-1.0, 1.0], size=(B, L, L)).astype(np.float32)
+    return J, s0, target
+
+
+def oracle_run(J, s0, beta, h, alpha, lat, sweep0, n):
+    s = s0.astype(np.float64).copy()
+    tape = odmc.run(s, J.astype(np.float64), beta, h, alpha, SEED, lat, sweep0, n, tape=True)
+    return s, tape
+
+
+def condition(J, s0, beta, h, alpha, lat, sweep0, n):
+    base, _ = oracle_run(J, s0, beta, h, alpha, lat, sweep0, n)
+    d = 1e-9
+    pert = s0.astype(np.float64) + d * np.random.default_rng(lat).choice([-1.0, 1.0], size=s0.shape)
+    s = pert.copy()
+    odmc.run(s, J.astype(np.float64), beta, h, alpha, SEED, lat, sweep0, n)
+    return float(np.abs(s - base).max() / d)
+
+
+@pytest.mark.parametrize("B,L,n,alpha", [(3, 8, 3, 4.0), (2, 16, 2, 2.0), (2, 64, 2, 4.0), (5, 32, 1, 10.0)])
+def test_forward_and_tape_match_oracle(B, L, n, alpha):
+    beta, h = f32(0.8), f32(0.05)
+    J, s0, _ = make_case(B, L, 11 * L + n)
+    spins = torch.from_numpy(s0.copy()).cuda()
+    Jd = torch.from_numpy(J).cuda()
+    tape = torch.full((sm.dmc_tape_floats(B, L, n),), np.nan, dtype=torch.float32, device="cuda")
+    sm.dmc_forward(SEED, Jd, spins, beta, h, alpha, 7, n, tape)
+    got = spins.cpu().numpy()
+    gtape = tape.cpu().numpy().reshape(B, 2 * n, L * L // 2)
+    for b in range(B):
+        ref, rtape = oracle_run(J[b], s0[b], beta, h, alpha, b, 7, n)
+        cond = condition(J[b], s0[b], beta, h, alpha, b, 7, n)
+        tol = 4 * 10 * EPS32 * 2 * n * max(cond, 1.0)
+        err = np.abs(got[b] - ref).max()
+        assert err <= tol, (b, err, tol, cond)
+        # tape: old values of the active sites of each sub-step, compressed order
+        for k in range(2 * n):
+            c = k & 1
+            flat = rtape[k].reshape(-1)
+            active = np.array([y * L + x for y in range(L) for x in range(L) if (x + y) % 2 == c])
+            assert np.abs(gtape[b, k] - flat[active]).max() <= tol, (b, k)
+
+
+@pytest.mark.parametrize("B,L,n,alpha", [(2, 8, 2, 3.0), (2, 32, 2, 4.0), (1, 64, 1, 4.0)])
+def test_backward_matches_oracle(B, L, n, alpha):
+    beta, h = f32(0.7), f32(-0.1)
+    J, s0, target = make_case(B, L, 5 * L + n)
+    spins = torch.from_numpy(s0.copy()).cuda()
+    Jd = torch.from_numpy(J).cuda()
+    tape = torch.empty(sm.dmc_tape_floats(B, L, n), dtype=torch.float32, device="cuda")
+    sm.dmc_forward(SEED, Jd, spins, beta, h, alpha, 0, n, tape)
+    gs = torch.empty_like(spins)
+    loss = torch.empty(B, dtype=torch.float64, device="cuda")
+    sm.dmc_loss(spins, torch.from_numpy(target).cuda(), gs, loss)
+    gJ = torch.full_like(Jd, np.nan)
+    sm.dmc_backward(SEED, Jd, spins, tape, beta, h, alpha, 0, n, gs, gJ)
+    got_gs, got_gJ, got_loss = gs.cpu().numpy(), gJ.cpu().numpy(), loss.cpu().numpy()
+    for b in range(B):
+        ref, rtape = oracle_run(J[b], s0[b], beta, h, alpha, b, 0, n)
+        rloss, rg = odmc.loss(ref, target[b])
+        rgs, rgJ = odmc.backward(rtape, J[b].astype(np.float64), rg, beta, h, alpha, SEED, b, 0)
+        cond = condition(J[b], s0[b], beta, h, alpha, b, 0, n)
+        tol = 4 * 10 * EPS32 * 2 * n * max(cond, 1.0)
+        assert abs(got_loss[b] - rloss) <= tol * (1 + rloss) * 4, (b, got_loss[b], rloss)
+        assert np.abs(got_gJ[b] - rgJ).max() <= tol * max(1.0, np.abs(rgJ).max()) * 4, b
+        assert np.abs(got_gs[b] - rgs).max() <= tol * max(1.0, np.abs(rgs).max()) * 4, b
+
+
+def test_loss_gradient_and_discretisation_are_exact():
+    rng = np.random.default_rng(9)
+    s = rng.uniform(-1, 1, size=(4, 8, 8)).astype(np.float32)
+    s[0, 0, :4] = [0.0, -0.0, 1e-30, -1e-30]
+    t = rng.choice([-1.0, 1.0], size=s.shape).astype(np.float32)
+    sd, td = torch.from_numpy(s).cuda(), torch.from_numpy(t).cuda()
+    g = torch.empty_like(sd)
+    loss = torch.empty(4, dtype=torch.float64, device="cuda")
+    sm.dmc_loss(sd, td, g, loss)
+    np.testing.assert_array_equal(g.cpu().numpy(), np.float32(-2.0) * (t - s))
+    ref = ((t.astype(np.float64) - s.astype(np.float64)) ** 2).reshape(4, -1).sum(1)
+    np.testing.assert_allclose(loss.cpu().numpy(), ref, rtol=1e-6)
+    sm.dmc_discretize(sd)
+    np.testing.assert_array_equal(sd.cpu().numpy(), np.where(s < 0, -1.0, 1.0).astype(np.float32))
+
+
+def test_pattern_optimisation_lowers_the_loss():
+    """Alg. 2 as a training loop: the couplings steer lattices that start all
+    up towards striped targets (Sec. Optimization of the exchange parameters).
+    One relaxed sweep per iteration at T = 0.9, alpha = 10; the float64 oracle
+    running the same loop on one 32^2 lattice lowers the loss about tenfold in
+    150 iterations."""
+    B, L = 16, 32
+    y = np.arange(L)[:, None] * np.ones((1, L))
+    target = np.stack([np.where(((y // (2 + b % 4)) % 2) == 0, 1.0, -1.0) for b in range(B)]).astype(np.float32)
+    opt = pdmc.PatternOptimizer(torch.from_numpy(target).cuda(), beta=1 / 0.9, alpha=10.0, sweeps=1,
+                                seed=3, lr=5e-2)
+    hist = [opt.step().cpu().numpy().mean() for _ in range(150)]
+    first, last = np.mean(hist[:15]), np.mean(hist[-15:])
+    print(f"mean relaxed loss per lattice: first 15 iterations {first:.0f}, last 15 {last:.0f}")
+    assert last < 0.3 * first
