@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--workload", default="uneven512",
-                    choices=["uneven512", "potts_q3", "potts_q8", "cpm1024", "ising_small", "grad", "mlp"])
+                    choices=["uneven512", "potts_q3", "potts_q8", "cpm1024", "ising_small", "grad", "mlp", "dmc"])
     return ap.parse_args()
 
 
@@ -95,6 +95,40 @@ def _oracle_potts(args):
     t0 = time.perf_counter()
     oracle.potts_run(s, d["q"], d["beta"], d["J"], seed, i, 0, sweeps, record=False)
     return d["L"] * d["L"] * sweeps, time.perf_counter() - t0
+
+
+DMC_SHAPE = (1024, 64, 1)   # lattices, side, relaxed sweeps per optimisation iteration
+
+
+def dmc_targets(B, L):
+    """Synthetic +-1 patterns: horizontal stripes, vertical stripes and blocks of
+    widths 2..5 (the kind of target shown for the pattern optimisation)."""
+    import numpy as np
+    y = np.arange(L)[:, None] * np.ones((1, L))
+    x = y.T
+    out = np.empty((B, L, L), dtype=np.float32)
+    for b in range(B):
+        w = 2 + b % 4
+        kind = (b // 4) % 3
+        pat = (y // w) % 2 if kind == 0 else ((x // w) % 2 if kind == 1 else ((y // w + x // w) % 2))
+        out[b] = np.where(pat == 0, 1.0, -1.0)
+    return out
+
+
+def _oracle_dmc(args):
+    import numpy as np
+
+    from oracle import dmc as odmc
+    b0, n, L, K = args
+    targets = dmc_targets(b0 + n, L)[b0:].astype(np.float64)
+    t0 = time.perf_counter()
+    for i in range(n):
+        J = np.ones((2, L, L))
+        s = np.ones((L, L))
+        tape = odmc.run(s, J, 1 / 0.9, 0.0, 10.0, SEED, b0 + i, 0, K, tape=True)
+        _, g = odmc.loss(s, targets[i])
+        odmc.backward(tape, J, g, 1 / 0.9, 0.0, 10.0, SEED, b0 + i, 0)
+    return n * L * L * K, time.perf_counter() - t0
 
 
 def cpu_oracle_pool(fn, tasks, cores):
@@ -151,6 +185,13 @@ def cpu_baseline_secondary(workload, cores):
         wall = (time.perf_counter() - t0) / 3
         return {"value": 128 * 1000 / wall, "unit": "samples/s", "cores": 1, "kind": "oracle",
                 "sample": "estimator over 128 chains x 1000 recorded sweeps, per-chain gradients (numpy)"}
+    if workload == "dmc":
+        B, L, K = DMC_SHAPE
+        per = 48
+        rate, units, wall = cpu_oracle_pool(_oracle_dmc, [(b * per, per, L, K) for b in range(cores)], cores)
+        return {"value": rate, "unit": "site-sweeps/s", "cores": cores, "kind": "oracle",
+                "sample": f"{per * cores} of the {B} lattices, one iteration each (forward {K} sweep(s), loss, "
+                          f"reverse pass; float64) ({wall:.1f} s wall)"}
     if workload == "mlp":
         from oracle import mlp as omlp
         rng = np.random.default_rng(0)
@@ -488,6 +529,8 @@ def run_secondary(args):
     stream = torch.cuda.current_stream()
     if args.workload in ("grad", "mlp"):
         return run_grad_mlp(args, cpu)
+    if args.workload == "dmc":
+        return run_dmc(args, cpu)
     record = False
     if args.workload.startswith("potts"):
         q = int(args.workload[-1])
@@ -591,6 +634,69 @@ def run_grad_mlp(args, cpu):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "dtype": "int64/fp64" if args.workload == "grad" else "bf16", "data": "synthetic",
             "config": {"workload": desc}}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_dmc(args, cpu):
+    """Differentiable Monte Carlo pattern optimisation (Alg. 2): one step = one
+    iteration of relaxed sweeps, pattern loss, reverse pass, Adam on the bond
+    couplings and discretisation, for 1024 lattices of 64^2."""
+    import torch
+    from paper_2304_01772_gb300.dmc import PatternOptimizer
+    B, L, K = DMC_SHAPE
+    target = torch.from_numpy(dmc_targets(B, L)).cuda()
+    opt = PatternOptimizer(target, beta=1 / 0.9, alpha=10.0, sweeps=K, seed=SEED, lr=5e-2)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        opt.step()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        loss = opt.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the fused kernel alone, and the same iteration as five separate launches
+    def timed(fn, reps=20):
+        fn()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a0.record(stream)
+        for _ in range(reps):
+            fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1) / reps
+    kernels = {}
+    if opt.fused:
+        kms = timed(opt.step)
+        kernels["dmc_step_kernel"] = {"launch_ms": kms, "algorithmic_bytes_per_launch": 60 * B * L * L,
+                                      "achieved_gbs": 60 * B * L * L / (kms * 1e-3) / 1e9,
+                                      "bytes_per_site": "spins in + out, target, couplings and both Adam "
+                                                        "moments in + out (2 bonds x 3 x 8 B)"}
+    separate_ms = timed(opt.step_separate)
+    top = max(kernels, key=lambda k: kernels[k]["launch_ms"])
+    peak, kind = measured_peaks()
+    units = B * L * L * K
+    separate = {"ms_per_step": separate_ms, "value": units / (separate_ms * 1e-3),
+                "launches": "dmc_forward, dmc_loss, dmc_backward, adam, dmc_discretize (tape in HBM)"}
+    line = {"metric": "site-sweeps/s (dmc)", "value": units / (ms * 1e-3), "unit": "site-sweeps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"differentiable Monte Carlo pattern optimisation: {B} Ising lattices of "
+                                   f"{L}^2 with one coupling per bond, {K} relaxed sweep(s) per iteration, "
+                                   "beta = 1/0.9, alpha = 10, h = 0, Adam lr 5e-2, striped/block targets; "
+                                   "one step = forward + loss + reverse pass + Adam + discretisation",
+                       "mean_loss_last_step": float(loss.mean()), "fused": opt.fused,
+                       "separate_launches": separate},
+            "roofline": {"bound": "hbm", "achieved": kernels[top]["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": kernels[top]["achieved_gbs"] / peak, "traffic": None, "kernel": top,
+                         "peak_source": f"{kind} hbm_gbs", "kernels": kernels},
+            "gpu_launches": (1 if opt.fused else 5) * args.steps}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

@@ -311,6 +311,19 @@ int spin_dmc_loss(int32_t n_lattices, int32_t L, const float *spins, const float
                   float *grad_spins, double *loss, void *stream);
 /* Discretisation of n spins: s <- -1 if s < 0 else +1.                      */
 int spin_dmc_discretize(int64_t n, float *spins, void *stream);
+/* Largest n_sweeps spin_dmc_step accepts for side L (its tape stays in
+ * shared memory); SPIN_EINVAL for an invalid L.                             */
+int32_t spin_dmc_step_max_sweeps(int32_t L);
+/* One whole optimisation iteration in a single launch, identical in result
+ * to spin_dmc_forward + spin_dmc_loss + spin_dmc_backward + spin_adam (on J,
+ * step `step`) + spin_dmc_discretize: spins (in: start state; out: the
+ * discretised state), J, m, v ([n_lattices][2][L][L], Adam moments) updated
+ * in place, loss[l] (float64) of the relaxed state.  target as in
+ * spin_dmc_loss.  1 <= n_sweeps <= spin_dmc_step_max_sweeps(L).             */
+int spin_dmc_step(uint64_t seed, int32_t n_lattices, int32_t L, float beta, float h, float alpha,
+                  uint32_t first_sweep, int32_t n_sweeps, float *spins, float *J, float *m, float *v,
+                  const float *target, double *loss, int32_t step, float lr, float beta1, float beta2,
+                  float eps, void *stream);
 
 #ifdef __cplusplus
 }

@@ -85,6 +85,10 @@ _SIGS = {
                                  _vp, _vp, _vp, ctypes.c_uint32, _i32, _vp, _vp, _vp]),
     "spin_dmc_loss": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp, _vp]),
     "spin_dmc_discretize": (_i32, [ctypes.c_int64, _vp, _vp]),
+    "spin_dmc_step_max_sweeps": (_i32, [_i32]),
+    "spin_dmc_step": (_i32, [ctypes.c_uint64, _i32, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_uint32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, ctypes.c_float,
+                             ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp]),
     "spin_mlp_param_count": (_i32, []),
     "spin_mlp_forward": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "spin_mlp_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
@@ -431,4 +435,19 @@ def dmc_loss(spins, target, grad_spins, loss, stream=None):
 
 def dmc_discretize(spins, stream=None):
     _check(lib().spin_dmc_discretize(spins.numel(), _ptr(spins), _stream(stream)), None, "spin_dmc_discretize")
+
+
+def dmc_step_max_sweeps(L):
+    return int(lib().spin_dmc_step_max_sweeps(int(L)))
+
+
+def dmc_step(seed, J, spins, m, v, target, loss, beta, h, alpha, first_sweep, n_sweeps, step, lr,
+             b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    """One fused optimisation iteration (forward, loss, reverse pass, Adam on J,
+    discretisation) in a single launch."""
+    B, L = spins.shape[0], spins.shape[-1]
+    _check(lib().spin_dmc_step(int(seed), B, L, float(beta), float(h), float(alpha), int(first_sweep),
+                               int(n_sweeps), _ptr(spins), _ptr(J), _ptr(m), _ptr(v), _ptr(target), _ptr(loss),
+                               int(step), float(lr), float(b1), float(b2), float(eps), _stream(stream)),
+           None, "spin_dmc_step")
 

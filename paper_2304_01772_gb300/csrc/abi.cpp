@@ -1291,6 +1291,29 @@ int spin_dmc_loss(int32_t n_lattices, int32_t L, const float *spins, const float
                : SPIN_ECUDA;
 }
 
+int32_t spin_dmc_step_max_sweeps(int32_t L) {
+    if (!dmc_geom_ok(1, L, 1)) return SPIN_EINVAL;
+    const size_t budget = 226 * 1024;   // dynamic shared memory of one block, with room for the static part
+    int32_t k = 0;
+    while (dmc_step_smem(L, k + 1) <= budget && k < 4096) ++k;
+    return k;
+}
+
+int spin_dmc_step(uint64_t seed, int32_t n_lattices, int32_t L, float beta, float h, float alpha,
+                  uint32_t first_sweep, int32_t n_sweeps, float *spins, float *J, float *m, float *v,
+                  const float *target, double *loss, int32_t step, float lr, float beta1, float beta2, float eps,
+                  void *stream) {
+    if (!dmc_geom_ok(n_lattices, L, n_sweeps) || !dmc_params_ok(beta, h, alpha)) return SPIN_EINVAL;
+    if (n_sweeps > spin_dmc_step_max_sweeps(L) || step < 1 || !std::isfinite(lr)) return SPIN_EINVAL;
+    if (!aligned16(spins) || !aligned16(J) || !aligned16(m) || !aligned16(v) || !target || !loss)
+        return SPIN_EINVAL;
+    float c1, c2;
+    adam_bias(step, beta1, beta2, c1, c2);
+    DmcStepArgs a{n_lattices, L, n_sweeps, first_sweep, beta, h, alpha, (uint32_t)seed, (uint32_t)(seed >> 32),
+                  spins, J, m, v, target, loss, lr, beta1, beta2, eps, c1, c2};
+    return launch_dmc_step(a, S(stream)) == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
+}
+
 int spin_dmc_discretize(int64_t n, float *spins, void *stream) {
     if (n < 0 || (n > 0 && !spins)) return SPIN_EINVAL;
     if (n == 0) return SPIN_OK;

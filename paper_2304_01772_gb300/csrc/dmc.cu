@@ -65,40 +65,95 @@ __device__ __forceinline__ void store_f4(float *dst, const float *src, int n) {
     for (int v = threadIdx.x; v < n / 4; v += blockDim.x) d4[v] = s4[v];
 }
 
+// Forward sub-step `sub` of lattice `lat` on the block's shared copy; the
+// active sites' old values go to tape (N / 2 floats, compressed order; shared
+// or global memory).  Ends with a block barrier.
+__device__ __forceinline__ void dmc_forward_substep(const DmcGeom &g, float *s, const float *Jr, const float *Jd,
+                                                    float *tape, int lat, uint32_t sweep, int c, float beta,
+                                                    float h, float alpha, uint32_t k0, uint32_t k1) {
+    for (int grp = threadIdx.x; grp < g.N / 8; grp += blockDim.x) {
+        const uint4 r4 = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)lat, sweep, (uint32_t)c), k0, k1);
+        const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
+        float old[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int i = dmc_site(g, 4 * grp + l, c);
+            const float si = s[i];
+            const float n = dmc_field(g, s, Jr, Jd, i);
+            const float p = expf(-beta * (2.0f * si * (n + h)));
+            const float q = 1.0f / (1.0f + expf(-alpha * (p - dmc_uniform(rr[l]))));
+            old[l] = si;
+            s[i] = q * (-si) + (1.0f - q) * si;
+        }
+        reinterpret_cast<float4 *>(tape)[grp] = make_float4(old[0], old[1], old[2], old[3]);
+    }
+    __syncthreads();
+}
+
+// Reverse of sub-step `sub`: s holds the state after it and becomes the state
+// before it; gs likewise for the adjoint; gJr / gJd accumulate.  w: N / 2
+// floats of scratch; it may be the sub-step's own tape slot (each thread reads
+// its four old values before it writes their four w).  Ends with a block
+// barrier.
+__device__ __forceinline__ void dmc_backward_substep(const DmcGeom &g, float *s, float *gs, const float *Jr,
+                                                     const float *Jd, float *gJr, float *gJd, float *w,
+                                                     const float *tape, int lat, uint32_t sweep, int c,
+                                                     float beta, float h, float alpha, uint32_t k0,
+                                                     uint32_t k1) {
+    const float c4 = 4.0f * alpha * beta;
+    // active sites: restore the old value, form w and the direct term
+    for (int grp = threadIdx.x; grp < g.N / 8; grp += blockDim.x) {
+        const uint4 r4 = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)lat, sweep, (uint32_t)c), k0, k1);
+        const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
+        const float4 o4 = reinterpret_cast<const float4 *>(tape)[grp];
+        const float old[4] = {o4.x, o4.y, o4.z, o4.w};
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int i = dmc_site(g, 4 * grp + l, c);
+            const float si = old[l];
+            const float n = dmc_field(g, s, Jr, Jd, i);
+            const float p = expf(-beta * (2.0f * si * (n + h)));
+            const float q = 1.0f / (1.0f + expf(-alpha * (p - dmc_uniform(rr[l]))));
+            const float common = c4 * p * q * (1.0f - q);
+            const float gi = gs[i];
+            w[4 * grp + l] = gi * common * si * si;
+            gs[i] = gi * ((1.0f - 2.0f * q) + common * si * (n + h));
+            s[i] = si;
+        }
+    }
+    __syncthreads();
+    // passive sites: their adjoint gains sum_i w_i J_ij; their four bonds gain w_i s_j
+    for (int k = threadIdx.x; k < g.N / 2; k += blockDim.x) {
+        const int j = dmc_site(g, k, c ^ 1);
+        const int y = j / g.L, x = j - y * g.L;
+        const int xl = x == 0 ? g.L - 1 : x - 1, xr = x == g.L - 1 ? 0 : x + 1;
+        const int yu = y == 0 ? g.L - 1 : y - 1, yd = y == g.L - 1 ? 0 : y + 1;
+        const int iL = y * g.L + xl, iR = y * g.L + xr, iU = yu * g.L + x, iD = yd * g.L + x;
+        const float wl = w[iL >> 1], wr = w[iR >> 1], wu = w[iU >> 1], wd = w[iD >> 1];
+        const float sj = s[j];
+        gs[j] += wr * Jr[j] + wl * Jr[iL] + wd * Jd[j] + wu * Jd[iU];
+        gJr[j] += wr * sj;
+        gJr[iL] += wl * sj;
+        gJd[j] += wd * sj;
+        gJd[iU] += wu * sj;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kDmcThreads) dmc_forward_kernel(DmcArgs a) {
     extern __shared__ __align__(16) float sm[];
     const DmcGeom g{a.L, a.L / 2, a.L * a.L};
     float *s = sm, *Jr = sm + g.N, *Jd = sm + 2 * g.N;
-    const int n_sub = 2 * a.n_sweeps, ngroups = g.N / 8;
+    const int n_sub = 2 * a.n_sweeps;
     for (int lat = blockIdx.x; lat < a.n_lat; lat += gridDim.x) {
         load_f4(s, a.spins + (size_t)lat * g.N, g.N);
         load_f4(Jr, a.J + (size_t)lat * 2 * g.N, g.N);
         load_f4(Jd, a.J + (size_t)lat * 2 * g.N + g.N, g.N);
         __syncthreads();
         float *tape = a.tape + (size_t)lat * n_sub * (g.N / 2);
-        for (int sub = 0; sub < n_sub; ++sub) {
-            const int c = sub & 1;
-            const uint32_t sweep = a.first_sweep + (uint32_t)(sub >> 1);
-            for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x) {
-                const uint4 r4 = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)lat, sweep, (uint32_t)c),
-                                               a.k0, a.k1);
-                const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
-                float old[4];
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    const int i = dmc_site(g, 4 * grp + l, c);
-                    const float si = s[i];
-                    const float n = dmc_field(g, s, Jr, Jd, i);
-                    const float p = expf(-a.beta * (2.0f * si * (n + a.h)));
-                    const float q = 1.0f / (1.0f + expf(-a.alpha * (p - dmc_uniform(rr[l]))));
-                    old[l] = si;
-                    s[i] = q * (-si) + (1.0f - q) * si;
-                }
-                reinterpret_cast<float4 *>(tape + (size_t)sub * (g.N / 2))[grp] =
-                    make_float4(old[0], old[1], old[2], old[3]);
-            }
-            __syncthreads();
-        }
+        for (int sub = 0; sub < n_sub; ++sub)
+            dmc_forward_substep(g, s, Jr, Jd, tape + (size_t)sub * (g.N / 2), lat,
+                                a.first_sweep + (uint32_t)(sub >> 1), sub & 1, a.beta, a.h, a.alpha, a.k0, a.k1);
         store_f4(a.spins + (size_t)lat * g.N, s, g.N);
         __syncthreads();
     }
@@ -109,8 +164,7 @@ __global__ void __launch_bounds__(kDmcThreads) dmc_backward_kernel(DmcArgs a) {
     const DmcGeom g{a.L, a.L / 2, a.L * a.L};
     float *s = sm, *gs = sm + g.N, *Jr = sm + 2 * g.N, *Jd = sm + 3 * g.N;
     float *gJr = sm + 4 * g.N, *gJd = sm + 5 * g.N, *w = sm + 6 * g.N;   // w: N / 2
-    const int n_sub = 2 * a.n_sweeps, ngroups = g.N / 8;
-    const float c4 = 4.0f * a.alpha * a.beta;
+    const int n_sub = 2 * a.n_sweeps;
     for (int lat = blockIdx.x; lat < a.n_lat; lat += gridDim.x) {
         load_f4(s, a.spins + (size_t)lat * g.N, g.N);
         load_f4(gs, a.grad_spins + (size_t)lat * g.N, g.N);
@@ -119,51 +173,76 @@ __global__ void __launch_bounds__(kDmcThreads) dmc_backward_kernel(DmcArgs a) {
         for (int i = threadIdx.x; i < g.N; i += blockDim.x) gJr[i] = gJd[i] = 0.0f;
         __syncthreads();
         const float *tape = a.tape + (size_t)lat * n_sub * (g.N / 2);
-        for (int sub = n_sub - 1; sub >= 0; --sub) {
-            const int c = sub & 1;
-            const uint32_t sweep = a.first_sweep + (uint32_t)(sub >> 1);
-            // active sites: restore the old value, form w and the direct term
-            for (int grp = threadIdx.x; grp < ngroups; grp += blockDim.x) {
-                const uint4 r4 = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)lat, sweep, (uint32_t)c),
-                                               a.k0, a.k1);
-                const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
-                const float4 o4 = reinterpret_cast<const float4 *>(tape + (size_t)sub * (g.N / 2))[grp];
-                const float old[4] = {o4.x, o4.y, o4.z, o4.w};
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    const int i = dmc_site(g, 4 * grp + l, c);
-                    const float si = old[l];
-                    const float n = dmc_field(g, s, Jr, Jd, i);
-                    const float p = expf(-a.beta * (2.0f * si * (n + a.h)));
-                    const float q = 1.0f / (1.0f + expf(-a.alpha * (p - dmc_uniform(rr[l]))));
-                    const float common = c4 * p * q * (1.0f - q);
-                    const float gi = gs[i];
-                    w[4 * grp + l] = gi * common * si * si;
-                    gs[i] = gi * ((1.0f - 2.0f * q) + common * si * (n + a.h));
-                    s[i] = si;
-                }
-            }
-            __syncthreads();
-            // passive sites: their adjoint gains sum_i w_i J_ij; their four bonds gain w_i s_j
-            for (int k = threadIdx.x; k < g.N / 2; k += blockDim.x) {
-                const int j = dmc_site(g, k, c ^ 1);
-                const int y = j / g.L, x = j - y * g.L;
-                const int xl = x == 0 ? g.L - 1 : x - 1, xr = x == g.L - 1 ? 0 : x + 1;
-                const int yu = y == 0 ? g.L - 1 : y - 1, yd = y == g.L - 1 ? 0 : y + 1;
-                const int iL = y * g.L + xl, iR = y * g.L + xr, iU = yu * g.L + x, iD = yd * g.L + x;
-                const float wl = w[iL >> 1], wr = w[iR >> 1], wu = w[iU >> 1], wd = w[iD >> 1];
-                const float sj = s[j];
-                gs[j] += wr * Jr[j] + wl * Jr[iL] + wd * Jd[j] + wu * Jd[iU];
-                gJr[j] += wr * sj;
-                gJr[iL] += wl * sj;
-                gJd[j] += wd * sj;
-                gJd[iU] += wu * sj;
-            }
-            __syncthreads();
-        }
+        for (int sub = n_sub - 1; sub >= 0; --sub)
+            dmc_backward_substep(g, s, gs, Jr, Jd, gJr, gJd, w, tape + (size_t)sub * (g.N / 2), lat,
+                                 a.first_sweep + (uint32_t)(sub >> 1), sub & 1, a.beta, a.h, a.alpha, a.k0, a.k1);
         store_f4(a.grad_spins + (size_t)lat * g.N, gs, g.N);
         store_f4(a.grad_J + (size_t)lat * 2 * g.N, gJr, g.N);
         store_f4(a.grad_J + (size_t)lat * 2 * g.N + g.N, gJd, g.N);
+        __syncthreads();
+    }
+}
+
+// One whole optimisation iteration per lattice with everything in shared
+// memory: forward sweeps (tape kept on chip), loss and its gradient, reverse
+// pass, Adam on the couplings, and the discretised state written back.  HBM
+// traffic per site: spins and target in, spins out, couplings and both Adam
+// moments in and out.
+constexpr int kDmcStepThreads = 512;
+
+__global__ void __launch_bounds__(kDmcStepThreads, 2) dmc_step_kernel(DmcStepArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ double red[kDmcStepThreads / 32];
+    const DmcGeom g{a.L, a.L / 2, a.L * a.L};
+    float *s = sm, *gs = sm + g.N, *Jr = sm + 2 * g.N, *Jd = sm + 3 * g.N;
+    float *gJr = sm + 4 * g.N, *gJd = sm + 5 * g.N;
+    float *tape = sm + 6 * g.N;   // 2 n_sweeps x N / 2; the reverse pass reuses each slot for its w
+    const int n_sub = 2 * a.n_sweeps;
+    for (int lat = blockIdx.x; lat < a.n_lat; lat += gridDim.x) {
+        float *spins = a.spins + (size_t)lat * g.N;
+        float *J = a.J + (size_t)lat * 2 * g.N;
+        load_f4(s, spins, g.N);
+        load_f4(Jr, J, g.N);
+        load_f4(Jd, J + g.N, g.N);
+        __syncthreads();
+        for (int sub = 0; sub < n_sub; ++sub)
+            dmc_forward_substep(g, s, Jr, Jd, tape + (size_t)sub * (g.N / 2), lat,
+                                a.first_sweep + (uint32_t)(sub >> 1), sub & 1, a.beta, a.h, a.alpha, a.k0, a.k1);
+        // loss of the relaxed state, its gradient, and the discretised state
+        const float *target = a.target + (size_t)lat * g.N;
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < g.N; i += blockDim.x) {
+            const float si = s[i];
+            const float d = target[i] - si;
+            acc += (double)d * (double)d;
+            gs[i] = -2.0f * d;
+            spins[i] = si < 0.0f ? -1.0f : 1.0f;
+            gJr[i] = gJd[i] = 0.0f;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < kDmcStepThreads / 32; ++k) t += red[k];
+            a.loss[lat] = t;
+        }
+        for (int sub = n_sub - 1; sub >= 0; --sub) {
+            float *slot = tape + (size_t)sub * (g.N / 2);
+            dmc_backward_substep(g, s, gs, Jr, Jd, gJr, gJd, slot, slot, lat, a.first_sweep + (uint32_t)(sub >> 1),
+                                 sub & 1, a.beta, a.h, a.alpha, a.k0, a.k1);
+        }
+        // Adam on the 2N couplings of this lattice
+        float *m = a.m + (size_t)lat * 2 * g.N, *v = a.v + (size_t)lat * 2 * g.N;
+        for (int b = threadIdx.x; b < 2 * g.N; b += blockDim.x) {
+            float p = b < g.N ? Jr[b] : Jd[b - g.N];
+            float mm = m[b], vv = v[b];
+            adam_element(p, mm, vv, b < g.N ? gJr[b] : gJd[b - g.N], a.lr, a.b1, a.b2, a.eps, a.c1, a.c2);
+            m[b] = mm;
+            v[b] = vv;
+            J[b] = p;
+        }
         __syncthreads();
     }
 }
@@ -219,6 +298,19 @@ cudaError_t launch_dmc_backward(const DmcArgs &a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(dmc_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e) return e;
     dmc_backward_kernel<<<dmc_grid(a.n_lat, 2), kDmcThreads, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+size_t dmc_step_smem(int L, int n_sweeps) {
+    const size_t N = (size_t)L * L;
+    return sizeof(float) * (6 * N + (size_t)n_sweeps * N);
+}
+
+cudaError_t launch_dmc_step(const DmcStepArgs &a, cudaStream_t s) {
+    const size_t sm = dmc_step_smem(a.L, a.n_sweeps);
+    cudaError_t e = cudaFuncSetAttribute(dmc_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e) return e;
+    dmc_step_kernel<<<dmc_grid(a.n_lat, 2), kDmcStepThreads, sm, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // CUDA translation units and the host side of libspinmc.so.  Not installed.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace spinmc {
@@ -271,5 +272,41 @@ cudaError_t launch_mlp_adam(float *params, const float *grad, float *m, float *v
                             float lr, float b1, float b2, float eps, cudaStream_t s);
 cudaError_t launch_adam(float *params, const float *grad, float *m, float *v, int n, int step,
                         float lr, float b1, float b2, float eps, cudaStream_t s);
+
+#ifdef __CUDACC__
+// One Adam step of parameter p (Kingma & Ba) with bias corrections c1 = 1 -
+// b1^t, c2 = 1 - b2^t; shared by every kernel that applies Adam so that fused
+// and separate launches give identical results.
+__device__ __forceinline__ void adam_element(float &p, float &m, float &v, float g, float lr, float b1, float b2,
+                                             float eps, float c1, float c2) {
+    const float mm = b1 * m + (1.0f - b1) * g;
+    const float vv = b2 * v + (1.0f - b2) * g * g;
+    m = mm;
+    v = vv;
+    p -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+}
+#endif
+
+// Adam bias corrections for step t >= 1.
+inline void adam_bias(int step, float b1, float b2, float &c1, float &c2) {
+    c1 = 1.0f - powf(b1, (float)step);
+    c2 = 1.0f - powf(b2, (float)step);
+}
+
+// Fused differentiable Monte Carlo iteration: forward sweeps, loss, reverse
+// pass, Adam on the couplings, discretisation; tape in shared memory.
+struct DmcStepArgs {
+    int n_lat, L, n_sweeps;
+    uint32_t first_sweep;
+    float beta, h, alpha;
+    uint32_t k0, k1;
+    float *spins;          // in: start state; out: discretised state after the sweeps
+    float *J, *m, *v;      // [n_lat][2][L*L]: couplings and Adam moments, updated
+    const float *target;   // [n_lat][L*L]
+    double *loss;          // [n_lat]: loss of the relaxed state
+    float lr, b1, b2, eps, c1, c2;
+};
+size_t dmc_step_smem(int L, int n_sweeps);
+cudaError_t launch_dmc_step(const DmcStepArgs &a, cudaStream_t s);
 
 }  // namespace spinmc

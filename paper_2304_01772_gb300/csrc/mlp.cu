@@ -177,12 +177,11 @@ __global__ void mlp_reduce_kernel(const float *part, int nblk, float *grad, floa
 __global__ void mlp_adam_kernel(float *params, const float *grad, float *m, float *v, int n, float lr,
                                 float b1, float b2, float eps, float c1, float c2) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        const float g = grad[p];
-        const float mm = b1 * m[p] + (1.0f - b1) * g;
-        const float vv = b2 * v[p] + (1.0f - b2) * g * g;
+        float pp = params[p], mm = m[p], vv = v[p];
+        adam_element(pp, mm, vv, grad[p], lr, b1, b2, eps, c1, c2);
         m[p] = mm;
         v[p] = vv;
-        params[p] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+        params[p] = pp;
     }
 }
 
@@ -223,7 +222,8 @@ cudaError_t launch_mlp_backward(const float *params, const float *mu, const floa
 cudaError_t launch_adam(float *params, const float *grad, float *m, float *v, int n, int step,
                         float lr, float b1, float b2, float eps, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+    float c1, c2;
+    adam_bias(step, b1, b2, c1, c2);
     int blocks = (n + 255) / 256;
     blocks = blocks > 1024 ? 1024 : blocks;
     mlp_adam_kernel<<<blocks, 256, 0, s>>>(params, grad, m, v, n, lr, b1, b2, eps, c1, c2);

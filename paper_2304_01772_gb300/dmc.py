@@ -13,11 +13,12 @@ from __future__ import annotations
 
 import torch
 
-from . import adam, dmc_backward, dmc_discretize, dmc_forward, dmc_loss, dmc_tape_floats
+from . import (adam, dmc_backward, dmc_discretize, dmc_forward, dmc_loss, dmc_step, dmc_step_max_sweeps,
+               dmc_tape_floats)
 
 
 class PatternOptimizer:
-    def __init__(self, target, beta, alpha, sweeps, seed=0, h=0.0, J0=1.0, lr=1e-3, spins=None):
+    def __init__(self, target, beta, alpha, sweeps, seed=0, h=0.0, J0=1.0, lr=1e-3, spins=None, fused=True):
         """target: [B, L, L] float32 (+-1) on the device; spins: start state
         (default: all +1)."""
         self.target = target.contiguous()
@@ -36,10 +37,23 @@ class PatternOptimizer:
         self.loss = torch.zeros(B, dtype=torch.float64, device=dev)
         self.step_count = 0
         self.sweep = 0
+        self.fused = fused and sweeps <= dmc_step_max_sweeps(L)
 
     def step(self, stream=None):
         """One iteration; returns the per-lattice loss tensor (device, float64)
-        of the relaxed state before the update."""
+        of the relaxed state before the update.  A single fused launch when the
+        tape fits in shared memory, else the separate calls."""
+        if self.fused:
+            self.step_count += 1
+            dmc_step(self.seed, self.J, self.spins, self.m, self.v, self.target, self.loss, self.beta, self.h,
+                     self.alpha, self.sweep, self.sweeps, self.step_count, self.lr, stream=stream)
+            self.sweep += self.sweeps
+            return self.loss
+        return self.step_separate(stream)
+
+    def step_separate(self, stream=None):
+        """The same iteration as five launches (forward, loss, reverse pass,
+        Adam, discretisation) through a tape in device memory."""
         dmc_forward(self.seed, self.J, self.spins, self.beta, self.h, self.alpha, self.sweep, self.sweeps,
                     self.tape, stream)
         dmc_loss(self.spins, self.target, self.gs, self.loss, stream)

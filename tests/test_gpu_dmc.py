@@ -134,3 +134,24 @@ def test_pattern_optimisation_lowers_the_loss():
     first, last = np.mean(hist[:15]), np.mean(hist[-15:])
     print(f"mean relaxed loss per lattice: first 15 iterations {first:.0f}, last 15 {last:.0f}")
     assert last < 0.3 * first
+
+
+@pytest.mark.parametrize("B,L,K", [(4, 64, 1), (3, 32, 3), (2, 8, 2)])
+def test_fused_step_equals_the_separate_calls(B, L, K):
+    """spin_dmc_step (one launch, tape on chip) against forward + loss +
+    reverse pass + Adam + discretisation: same kernels' arithmetic, so the
+    spins, couplings and Adam moments agree bit for bit."""
+    rng = np.random.default_rng(L + K)
+    target = torch.from_numpy(rng.choice([-1.0, 1.0], size=(B, L, L)).astype(np.float32)).cuda()
+    start = torch.from_numpy(rng.choice([-1.0, 1.0], size=(B, L, L)).astype(np.float32)).cuda()
+    runs = []
+    for fused in (True, False):
+        opt = pdmc.PatternOptimizer(target, beta=1 / 0.9, alpha=10.0, sweeps=K, seed=7, lr=5e-2, spins=start,
+                                    fused=fused)
+        assert opt.fused == fused
+        losses = [opt.step().cpu().numpy().copy() for _ in range(3)]
+        runs.append((opt, losses))
+    (a, la), (b, lb) = runs
+    for name in ("spins", "J", "m", "v"):
+        assert torch.equal(getattr(a, name), getattr(b, name)), name
+    np.testing.assert_allclose(np.array(la), np.array(lb), rtol=1e-12)
