@@ -319,7 +319,8 @@ int32_t spin_dmc_step_max_sweeps(int32_t L);
  * step `step`) + spin_dmc_discretize: spins (in: start state; out: the
  * discretised state), J, m, v ([n_lattices][2][L][L], Adam moments) updated
  * in place, loss[l] (float64) of the relaxed state.  target as in
- * spin_dmc_loss.  1 <= n_sweeps <= spin_dmc_step_max_sweeps(L).             */
+ * spin_dmc_loss (16-byte aligned here).  1 <= n_sweeps <=
+ * spin_dmc_step_max_sweeps(L).                                              */
 int spin_dmc_step(uint64_t seed, int32_t n_lattices, int32_t L, float beta, float h, float alpha,
                   uint32_t first_sweep, int32_t n_sweeps, float *spins, float *J, float *m, float *v,
                   const float *target, double *loss, int32_t step, float lr, float beta1, float beta2,

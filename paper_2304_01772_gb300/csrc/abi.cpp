@@ -1305,7 +1305,7 @@ int spin_dmc_step(uint64_t seed, int32_t n_lattices, int32_t L, float beta, floa
                   void *stream) {
     if (!dmc_geom_ok(n_lattices, L, n_sweeps) || !dmc_params_ok(beta, h, alpha)) return SPIN_EINVAL;
     if (n_sweeps > spin_dmc_step_max_sweeps(L) || step < 1 || !std::isfinite(lr)) return SPIN_EINVAL;
-    if (!aligned16(spins) || !aligned16(J) || !aligned16(m) || !aligned16(v) || !target || !loss)
+    if (!aligned16(spins) || !aligned16(J) || !aligned16(m) || !aligned16(v) || !aligned16(target) || !loss)
         return SPIN_EINVAL;
     float c1, c2;
     adam_bias(step, beta1, beta2, c1, c2);

@@ -34,23 +34,19 @@ struct DmcGeom {
     int L, half, N;   // side, L / 2, L * L
 };
 
-// Active site of compressed index k for colour c: row y = k / half,
-// x = 2 (k % half) + ((y + c) & 1).
-__device__ __forceinline__ int dmc_site(const DmcGeom &g, int k, int c) {
-    const int y = k / g.half, m = k - y * g.half;
-    return y * g.L + 2 * m + ((y + c) & 1);
-}
-
 __device__ __forceinline__ float dmc_uniform(uint32_t u) { return (float)(u >> 8) * (1.0f / 16777216.0f); }
 
 // Weighted neighbour sum of site i = (x, y).
 __device__ __forceinline__ float dmc_field(const DmcGeom &g, const float *s, const float *Jr,
-                                           const float *Jd, int i) {
-    const int y = i / g.L, x = i - y * g.L;
+                                           const float *Jd, int i, int x, int y) {
     const int xl = x == 0 ? g.L - 1 : x - 1, xr = x == g.L - 1 ? 0 : x + 1;
     const int yu = y == 0 ? g.L - 1 : y - 1, yd = y == g.L - 1 ? 0 : y + 1;
     return Jr[i] * s[y * g.L + xr] + Jr[y * g.L + xl] * s[y * g.L + xl] + Jd[i] * s[yd * g.L + x] +
            Jd[yu * g.L + x] * s[yu * g.L + x];
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 __device__ __forceinline__ void load_f4(float *dst, const float *src, int n) {
@@ -71,17 +67,19 @@ __device__ __forceinline__ void store_f4(float *dst, const float *src, int n) {
 __device__ __forceinline__ void dmc_forward_substep(const DmcGeom &g, float *s, const float *Jr, const float *Jd,
                                                     float *tape, int lat, uint32_t sweep, int c, float beta,
                                                     float h, float alpha, uint32_t k0, uint32_t k1) {
+    const int gpr = g.half / 4;   // Philox groups per row: a group's four sites share a row
     for (int grp = threadIdx.x; grp < g.N / 8; grp += blockDim.x) {
         const uint4 r4 = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)lat, sweep, (uint32_t)c), k0, k1);
         const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
+        const int y = grp / gpr, x0 = 8 * (grp - y * gpr) + ((y + c) & 1);
         float old[4];
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
-            const int i = dmc_site(g, 4 * grp + l, c);
+            const int x = x0 + 2 * l, i = y * g.L + x;
             const float si = s[i];
-            const float n = dmc_field(g, s, Jr, Jd, i);
+            const float n = dmc_field(g, s, Jr, Jd, i, x, y);
             const float p = expf(-beta * (2.0f * si * (n + h)));
-            const float q = 1.0f / (1.0f + expf(-alpha * (p - dmc_uniform(rr[l]))));
+            const float q = __frcp_rn(1.0f + expf(-alpha * (p - dmc_uniform(rr[l]))));
             old[l] = si;
             s[i] = q * (-si) + (1.0f - q) * si;
         }
@@ -102,18 +100,20 @@ __device__ __forceinline__ void dmc_backward_substep(const DmcGeom &g, float *s,
                                                      uint32_t k1) {
     const float c4 = 4.0f * alpha * beta;
     // active sites: restore the old value, form w and the direct term
+    const int gpr = g.half / 4;
     for (int grp = threadIdx.x; grp < g.N / 8; grp += blockDim.x) {
         const uint4 r4 = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)lat, sweep, (uint32_t)c), k0, k1);
         const uint32_t rr[4] = {r4.x, r4.y, r4.z, r4.w};
         const float4 o4 = reinterpret_cast<const float4 *>(tape)[grp];
         const float old[4] = {o4.x, o4.y, o4.z, o4.w};
+        const int y = grp / gpr, x0 = 8 * (grp - y * gpr) + ((y + c) & 1);
 #pragma unroll
         for (int l = 0; l < 4; ++l) {
-            const int i = dmc_site(g, 4 * grp + l, c);
+            const int x = x0 + 2 * l, i = y * g.L + x;
             const float si = old[l];
-            const float n = dmc_field(g, s, Jr, Jd, i);
+            const float n = dmc_field(g, s, Jr, Jd, i, x, y);
             const float p = expf(-beta * (2.0f * si * (n + h)));
-            const float q = 1.0f / (1.0f + expf(-alpha * (p - dmc_uniform(rr[l]))));
+            const float q = __frcp_rn(1.0f + expf(-alpha * (p - dmc_uniform(rr[l]))));
             const float common = c4 * p * q * (1.0f - q);
             const float gi = gs[i];
             w[4 * grp + l] = gi * common * si * si;
@@ -124,8 +124,7 @@ __device__ __forceinline__ void dmc_backward_substep(const DmcGeom &g, float *s,
     __syncthreads();
     // passive sites: their adjoint gains sum_i w_i J_ij; their four bonds gain w_i s_j
     for (int k = threadIdx.x; k < g.N / 2; k += blockDim.x) {
-        const int j = dmc_site(g, k, c ^ 1);
-        const int y = j / g.L, x = j - y * g.L;
+        const int y = k / g.half, x = 2 * (k - y * g.half) + ((y + c + 1) & 1), j = y * g.L + x;
         const int xl = x == 0 ? g.L - 1 : x - 1, xr = x == g.L - 1 ? 0 : x + 1;
         const int yu = y == 0 ? g.L - 1 : y - 1, yd = y == g.L - 1 ? 0 : y + 1;
         const int iL = y * g.L + xl, iR = y * g.L + xr, iU = yu * g.L + x, iD = yd * g.L + x;
@@ -201,6 +200,20 @@ __global__ void __launch_bounds__(kDmcStepThreads, 2) dmc_step_kernel(DmcStepArg
     for (int lat = blockIdx.x; lat < a.n_lat; lat += gridDim.x) {
         float *spins = a.spins + (size_t)lat * g.N;
         float *J = a.J + (size_t)lat * 2 * g.N;
+        // pull this block's next lattice into L2 while this one is computed
+        const int nxt = lat + gridDim.x;
+        if (nxt < a.n_lat) {
+            const size_t o1 = (size_t)nxt * g.N, o2 = (size_t)nxt * 2 * g.N;
+            for (int line = threadIdx.x; line < g.N / 32; line += blockDim.x) {   // 128-byte lines
+                prefetch_l2(a.spins + o1 + 32 * line);
+                prefetch_l2(a.target + o1 + 32 * line);
+            }
+            for (int line = threadIdx.x; line < g.N / 16; line += blockDim.x) {
+                prefetch_l2(a.J + o2 + 32 * line);
+                prefetch_l2(a.m + o2 + 32 * line);
+                prefetch_l2(a.v + o2 + 32 * line);
+            }
+        }
         load_f4(s, spins, g.N);
         load_f4(Jr, J, g.N);
         load_f4(Jd, J + g.N, g.N);
@@ -209,15 +222,21 @@ __global__ void __launch_bounds__(kDmcStepThreads, 2) dmc_step_kernel(DmcStepArg
             dmc_forward_substep(g, s, Jr, Jd, tape + (size_t)sub * (g.N / 2), lat,
                                 a.first_sweep + (uint32_t)(sub >> 1), sub & 1, a.beta, a.h, a.alpha, a.k0, a.k1);
         // loss of the relaxed state, its gradient, and the discretised state
-        const float *target = a.target + (size_t)lat * g.N;
+        const float4 *t4 = reinterpret_cast<const float4 *>(a.target + (size_t)lat * g.N);
         double acc = 0.0;
-        for (int i = threadIdx.x; i < g.N; i += blockDim.x) {
-            const float si = s[i];
-            const float d = target[i] - si;
-            acc += (double)d * (double)d;
-            gs[i] = -2.0f * d;
-            spins[i] = si < 0.0f ? -1.0f : 1.0f;
-            gJr[i] = gJd[i] = 0.0f;
+        for (int i4 = threadIdx.x; i4 < g.N / 4; i4 += blockDim.x) {
+            const float4 tt = t4[i4];
+            const float4 ss = reinterpret_cast<const float4 *>(s)[i4];
+            const float d[4] = {tt.x - ss.x, tt.y - ss.y, tt.z - ss.z, tt.w - ss.w};
+            const float sv[4] = {ss.x, ss.y, ss.z, ss.w};
+#pragma unroll
+            for (int l = 0; l < 4; ++l) acc += (double)d[l] * (double)d[l];
+            reinterpret_cast<float4 *>(gs)[i4] = make_float4(-2.0f * d[0], -2.0f * d[1], -2.0f * d[2], -2.0f * d[3]);
+            reinterpret_cast<float4 *>(spins)[i4] =
+                make_float4(sv[0] < 0.0f ? -1.0f : 1.0f, sv[1] < 0.0f ? -1.0f : 1.0f, sv[2] < 0.0f ? -1.0f : 1.0f,
+                            sv[3] < 0.0f ? -1.0f : 1.0f);
+            reinterpret_cast<float4 *>(gJr)[i4] = make_float4(0.f, 0.f, 0.f, 0.f);
+            reinterpret_cast<float4 *>(gJd)[i4] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
@@ -234,14 +253,21 @@ __global__ void __launch_bounds__(kDmcStepThreads, 2) dmc_step_kernel(DmcStepArg
                                  sub & 1, a.beta, a.h, a.alpha, a.k0, a.k1);
         }
         // Adam on the 2N couplings of this lattice
-        float *m = a.m + (size_t)lat * 2 * g.N, *v = a.v + (size_t)lat * 2 * g.N;
-        for (int b = threadIdx.x; b < 2 * g.N; b += blockDim.x) {
-            float p = b < g.N ? Jr[b] : Jd[b - g.N];
-            float mm = m[b], vv = v[b];
-            adam_element(p, mm, vv, b < g.N ? gJr[b] : gJd[b - g.N], a.lr, a.b1, a.b2, a.eps, a.c1, a.c2);
-            m[b] = mm;
-            v[b] = vv;
-            J[b] = p;
+        // (Jr, Jd and gJr, gJd are adjacent in shared memory: bond b < 2N is Jr[b])
+        float4 *m4 = reinterpret_cast<float4 *>(a.m + (size_t)lat * 2 * g.N);
+        float4 *v4 = reinterpret_cast<float4 *>(a.v + (size_t)lat * 2 * g.N);
+        float4 *J4 = reinterpret_cast<float4 *>(J);
+        const float4 *P4 = reinterpret_cast<const float4 *>(Jr), *G4 = reinterpret_cast<const float4 *>(gJr);
+        for (int b = threadIdx.x; b < g.N / 2; b += blockDim.x) {
+            float4 p = P4[b], mm = m4[b], vv = v4[b];
+            const float4 gg = G4[b];
+            adam_element(p.x, mm.x, vv.x, gg.x, a.lr, a.b1, a.b2, a.eps, a.c1, a.c2);
+            adam_element(p.y, mm.y, vv.y, gg.y, a.lr, a.b1, a.b2, a.eps, a.c1, a.c2);
+            adam_element(p.z, mm.z, vv.z, gg.z, a.lr, a.b1, a.b2, a.eps, a.c1, a.c2);
+            adam_element(p.w, mm.w, vv.w, gg.w, a.lr, a.b1, a.b2, a.eps, a.c1, a.c2);
+            m4[b] = mm;
+            v4[b] = vv;
+            J4[b] = p;
         }
         __syncthreads();
     }
