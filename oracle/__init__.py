@@ -87,6 +87,8 @@ def _declare(L):
         "or_dmc_backward": (None, [_i, _dp, _dp, _d, _d, _d, _u64, _u32, _u32, _i, _dp, _dp, _dp, _dp]),
         "or_dmc_loss": (_d, [_i, _dp, _dp, _dp]),
         "or_dmc_discretize": (None, [_i, _dp]),
+        "or_dmc_energy": (_d, [_i, _dp, _dp, _d, _dp, _dp]),
+        "or_dmc_spin_step": (None, [_i, _dp, _dp, _d]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -63,3 +63,20 @@ def discretize(s):
     out = _c(s).copy()
     lib().or_dmc_discretize(out.size, _p(out, _D))
     return out
+
+
+def energy(s, J, h):
+    """(E, dE/ds) of relaxed spins under per-bond couplings."""
+    L = s.shape[0]
+    J = _c(J)
+    g = np.zeros((L, L))
+    E = lib().or_dmc_energy(L, _p(J[0], _D), _p(J[1], _D), h, _p(_c(s), _D), _p(g, _D))
+    return float(E), g
+
+
+def spin_step(s, g, eta):
+    """s <- clip(s - eta sign(g), -1, 1), returned as a new array."""
+    out = _c(s).copy()
+    lib().or_dmc_spin_step(out.size, _p(out, _D), _p(_c(g), _D), eta)
+    return out
+

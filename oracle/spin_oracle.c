@@ -578,3 +578,32 @@ void or_dmc_discretize(int n, double *s)
 {
     for (int i = 0; i < n; ++i) s[i] = s[i] < 0.0 ? -1.0 : 1.0;
 }
+
+/* Energy of relaxed spins under per-bond couplings (Sec. "Optimization of  */
+/* the spin values": the loss is the Hamiltonian itself),                   */
+/*   E = -sum_<ij> J_ij s_i s_j - h sum_i s_i  (each bond once),            */
+/* and g = dE/ds: g_i = -(n_i + h), n_i = sum_j J_ij s_j.                   */
+double or_dmc_energy(int L, const double *Jr, const double *Jd, double h, const double *s, double *g)
+{
+    double E = 0.0;
+    for (int y = 0; y < L; ++y)
+        for (int x = 0; x < L; ++x) {
+            int i = y * L + x;
+            E -= Jr[i] * s[i] * s[y * L + wrap(x + 1, L)];
+            E -= Jd[i] * s[i] * s[wrap(y + 1, L) * L + x];
+            E -= h * s[i];
+            if (g) g[i] = -(dmc_field(L, Jr, Jd, s, x, y) + h);
+        }
+    return E;
+}
+
+/* Spin-value step with a quantised gradient (reading of Sec. "Optimization */
+/* of the spin values"): s <- clip(s - eta * sign(g), -1, 1), sign(0) = 0.   */
+void or_dmc_spin_step(int n, double *s, const double *g, double eta)
+{
+    for (int i = 0; i < n; ++i) {
+        double sg = g[i] > 0.0 ? 1.0 : (g[i] < 0.0 ? -1.0 : 0.0);
+        double v = s[i] - eta * sg;
+        s[i] = v > 1.0 ? 1.0 : (v < -1.0 ? -1.0 : v);
+    }
+}

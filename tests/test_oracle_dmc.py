@@ -135,3 +135,25 @@ def test_loss_and_discretisation():
     assert v == pytest.approx(0.49 + 0.64 + 1.0 + 4.0)
     np.testing.assert_allclose(g, -2 * (t - s))
     np.testing.assert_array_equal(dmc.discretize(s), [[1.0, -1.0], [1.0, -1.0]])
+
+
+def test_energy_matches_the_bond_hamiltonian_and_its_gradient():
+    L, h = 6, 0.3
+    rng = np.random.default_rng(5)
+    J = rng.choice([-1.0, 1.0], size=(2, L, L))
+    s = rng.uniform(-1, 1, size=(L, L))
+    E, g = dmc.energy(s, J, h)
+    assert E == pytest.approx(hamiltonian(s, J, h), rel=1e-13)
+    eps = 1e-6
+    for idx in [(0, 0), (2, 5), (5, 1), (3, 3)]:
+        sp, sm = s.copy(), s.copy()
+        sp[idx] += eps
+        sm[idx] -= eps
+        fd = (hamiltonian(sp, J, h) - hamiltonian(sm, J, h)) / (2 * eps)
+        assert g[idx] == pytest.approx(fd, rel=1e-7, abs=1e-8)
+
+
+def test_spin_step_is_a_clipped_sign_step():
+    s = np.array([[0.9, -0.5], [0.0, -1.0]])
+    g = np.array([[-1.0, 2.0], [0.0, -0.1]])
+    np.testing.assert_array_equal(dmc.spin_step(s, g, 0.5), [[1.0, -1.0], [0.0, -0.5]])
