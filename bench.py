@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--workload", default="uneven512",
-                    choices=["uneven512", "potts_q3", "potts_q8", "cpm1024", "ising_small", "grad", "mlp", "dmc"])
+                    choices=["uneven512", "potts_q3", "potts_q8", "cpm1024", "ising_small", "grad", "mlp", "dmc",
+                             "spinglass"])
     return ap.parse_args()
 
 
@@ -131,6 +132,30 @@ def _oracle_dmc(args):
     return n * L * L * K, time.perf_counter() - t0
 
 
+def spinglass_couplings(B, L, seed=8):
+    import numpy as np
+    return np.random.default_rng(seed).choice([-1.0, 1.0], size=(B, 2, L, L)).astype(np.float32)
+
+
+def _oracle_spinglass(args):
+    import numpy as np
+
+    from oracle import dmc as odmc
+    b0, n = args
+    L = 64
+    J = spinglass_couplings(b0 + n, L)[b0:].astype(np.float64)
+    rng = np.random.default_rng(b0)
+    t0 = time.perf_counter()
+    for i in range(n):
+        s = rng.choice([-1.0, 1.0], size=(L, L))
+        relaxed = s.copy()
+        tape = odmc.run(relaxed, J[i], 2.0, 0.0, 10.0, SEED, b0 + i, 0, 1, tape=True)
+        _, gE = odmc.energy(relaxed, J[i], 0.0)
+        gs, _ = odmc.backward(tape, J[i], gE, 2.0, 0.0, 10.0, SEED, b0 + i, 0)
+        odmc.discretize(odmc.spin_step(s, gs, 2.0))
+    return n * L * L, time.perf_counter() - t0
+
+
 def cpu_oracle_pool(fn, tasks, cores):
     import multiprocessing as mp
 
@@ -185,6 +210,12 @@ def cpu_baseline_secondary(workload, cores):
         wall = (time.perf_counter() - t0) / 3
         return {"value": 128 * 1000 / wall, "unit": "samples/s", "cores": 1, "kind": "oracle",
                 "sample": "estimator over 128 chains x 1000 recorded sweeps, per-chain gradients (numpy)"}
+    if workload == "spinglass":
+        per = 32
+        rate, units, wall = cpu_oracle_pool(_oracle_spinglass, [(b * per, per) for b in range(cores)], cores)
+        return {"value": rate, "unit": "site-sweeps/s", "cores": cores, "kind": "oracle",
+                "sample": f"{per * cores} of the 1024 lattices, one spin-value iteration each (relaxed sweep, "
+                          f"energy, reverse pass, quantised step; float64) ({wall:.1f} s wall)"}
     if workload == "dmc":
         B, L, K = DMC_SHAPE
         per = 48
@@ -531,6 +562,8 @@ def run_secondary(args):
         return run_grad_mlp(args, cpu)
     if args.workload == "dmc":
         return run_dmc(args, cpu)
+    if args.workload == "spinglass":
+        return run_spinglass(args, cpu)
     record = False
     if args.workload.startswith("potts"):
         q = int(args.workload[-1])
@@ -697,6 +730,52 @@ def run_dmc(args, cpu):
                          "frac": kernels[top]["achieved_gbs"] / peak, "traffic": None, "kernel": top,
                          "peak_source": f"{kind} hbm_gbs", "kernels": kernels},
             "gpu_launches": (1 if opt.fused else 5) * args.steps}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_spinglass(args, cpu):
+    """Energy minimisation over spin values on 1024 +-J spin glasses of 64^2:
+    one step = one differentiable Monte Carlo iteration (relaxed sweep, energy
+    and its gradient, reverse pass, quantised spin step, discretisation).  The
+    final energies per spin of the three methods after equal iteration counts
+    go in config."""
+    import torch
+    from paper_2304_01772_gb300.dmc import SpinOptimizer
+    B, L = 1024, 64
+    J = torch.from_numpy(spinglass_couplings(B, L)).cuda()
+    g = torch.Generator().manual_seed(0)
+    s0 = (torch.randint(0, 2, (B, L, L), generator=g).float() * 2 - 1).cuda()
+    opt = SpinOptimizer(J, s0, seed=SEED)
+    stream = torch.cuda.current_stream()
+    opt.dmc(args.warmup, beta=2.0, alpha=10.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    trace = opt.dmc(args.steps, beta=2.0, alpha=10.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    n_it = 60
+    ann = SpinOptimizer(J, s0, seed=SEED).anneal([0.1 + 2.9 * k / (n_it - 1) for k in range(n_it)], 1)
+    grd = SpinOptimizer(J, s0, seed=SEED).gradient(n_it)
+    dmc = SpinOptimizer(J, s0, seed=SEED).dmc(n_it, beta=2.0, alpha=10.0)
+    units = B * L * L
+    line = {"metric": "site-sweeps/s (spinglass)", "value": units / (ms * 1e-3), "unit": "site-sweeps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"spin-value optimisation, {B} +-J spin glasses of {L}^2 (random bonds, "
+                                   "random start); one step = one differentiable Monte Carlo iteration "
+                                   "(relaxed sweep at beta 2, alpha 10, energy gradient, reverse pass, sign "
+                                   "step eta 2, discretisation)",
+                       "energy_per_spin_after_60_iterations": {
+                           "annealed_metropolis_beta_0.1_to_3": float(ann[-1].mean()),
+                           "gradient_only": float(grd[-1].mean()),
+                           "dmc_best": float(dmc.min(axis=0).mean())},
+                       "last_energy_per_spin": float(trace[-1].mean())},
+            "gpu_launches": 7 * args.steps}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

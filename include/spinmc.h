@@ -311,6 +311,14 @@ int spin_dmc_loss(int32_t n_lattices, int32_t L, const float *spins, const float
                   float *grad_spins, double *loss, void *stream);
 /* Discretisation of n spins: s <- -1 if s < 0 else +1.                      */
 int spin_dmc_discretize(int64_t n, float *spins, void *stream);
+/* Spin-value optimisation (Sec. "Optimization of the spin values"): the loss
+ * is the energy itself.  energy[l] = -sum_<ij> J_ij s_i s_j - h sum_i s_i
+ * (float64, each bond once); grad_spins (may be NULL) = dE/ds = -(n + h).   */
+int spin_dmc_energy(int32_t n_lattices, int32_t L, float h, const float *J, const float *spins,
+                    float *grad_spins, double *energy, void *stream);
+/* Quantised spin-value step: s <- clip(s - eta sign(grad), -1, 1), sign(0) = 0,
+ * over n spins.                                                             */
+int spin_dmc_spin_step(int64_t n, float *spins, const float *grad, float eta, void *stream);
 /* Largest n_sweeps spin_dmc_step accepts for side L (its tape stays in
  * shared memory); SPIN_EINVAL for an invalid L.                             */
 int32_t spin_dmc_step_max_sweeps(int32_t L);

@@ -86,6 +86,8 @@ _SIGS = {
     "spin_dmc_loss": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp, _vp]),
     "spin_dmc_discretize": (_i32, [ctypes.c_int64, _vp, _vp]),
     "spin_dmc_step_max_sweeps": (_i32, [_i32]),
+    "spin_dmc_energy": (_i32, [_i32, _i32, ctypes.c_float, _vp, _vp, _vp, _vp, _vp]),
+    "spin_dmc_spin_step": (_i32, [ctypes.c_int64, _vp, _vp, ctypes.c_float, _vp]),
     "spin_dmc_step": (_i32, [ctypes.c_uint64, _i32, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                              ctypes.c_uint32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, ctypes.c_float,
                              ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp]),
@@ -450,4 +452,15 @@ def dmc_step(seed, J, spins, m, v, target, loss, beta, h, alpha, first_sweep, n_
                                int(n_sweeps), _ptr(spins), _ptr(J), _ptr(m), _ptr(v), _ptr(target), _ptr(loss),
                                int(step), float(lr), float(b1), float(b2), float(eps), _stream(stream)),
            None, "spin_dmc_step")
+
+
+def dmc_energy(J, spins, h, energy, grad_spins=None, stream=None):
+    B, L = spins.shape[0], spins.shape[-1]
+    _check(lib().spin_dmc_energy(B, L, float(h), _ptr(J), _ptr(spins), _ptr(grad_spins), _ptr(energy),
+                                 _stream(stream)), None, "spin_dmc_energy")
+
+
+def dmc_spin_step(spins, grad, eta, stream=None):
+    _check(lib().spin_dmc_spin_step(spins.numel(), _ptr(spins), _ptr(grad), float(eta), _stream(stream)),
+           None, "spin_dmc_spin_step")
 

@@ -1314,6 +1314,19 @@ int spin_dmc_step(uint64_t seed, int32_t n_lattices, int32_t L, float beta, floa
     return launch_dmc_step(a, S(stream)) == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
 }
 
+int spin_dmc_energy(int32_t n_lattices, int32_t L, float h, const float *J, const float *spins, float *grad_spins,
+                    double *energy, void *stream) {
+    if (!dmc_geom_ok(n_lattices, L, 1) || !std::isfinite(h) || !J || !spins || !energy) return SPIN_EINVAL;
+    return launch_dmc_energy(n_lattices, L, J, spins, h, grad_spins, energy, S(stream)) == cudaSuccess ? SPIN_OK
+                                                                                                    : SPIN_ECUDA;
+}
+
+int spin_dmc_spin_step(int64_t n, float *spins, const float *grad, float eta, void *stream) {
+    if (n < 0 || (n > 0 && (!spins || !grad)) || !std::isfinite(eta)) return SPIN_EINVAL;
+    if (n == 0) return SPIN_OK;
+    return launch_dmc_spin_step(n, spins, grad, eta, S(stream)) == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
+}
+
 int spin_dmc_discretize(int64_t n, float *spins, void *stream) {
     if (n < 0 || (n > 0 && !spins)) return SPIN_EINVAL;
     if (n == 0) return SPIN_OK;

@@ -299,6 +299,46 @@ __global__ void __launch_bounds__(kDmcThreads) dmc_loss_kernel(int n_lat, int N,
     }
 }
 
+// energy[lat] = -sum_<ij> J_ij s_i s_j - h sum s_i (double); grad = -(n + h).
+__global__ void __launch_bounds__(kDmcThreads) dmc_energy_kernel(int n_lat, int L, const float *J,
+                                                                 const float *spins, float h, float *grad,
+                                                                 double *energy) {
+    __shared__ double red[kDmcThreads / 32];
+    const DmcGeom g{L, L / 2, L * L};
+    for (int lat = blockIdx.x; lat < n_lat; lat += gridDim.x) {
+        const float *s = spins + (size_t)lat * g.N;
+        const float *Jr = J + (size_t)lat * 2 * g.N, *Jd = Jr + g.N;
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < g.N; i += blockDim.x) {
+            const int y = i / L, x = i - y * L;
+            const int xr = x == L - 1 ? 0 : x + 1, yd = y == L - 1 ? 0 : y + 1;
+            const double si = s[i];
+            acc -= (double)Jr[i] * si * (double)s[y * L + xr] + (double)Jd[i] * si * (double)s[yd * L + x] +
+                   (double)h * si;
+            if (grad) grad[(size_t)lat * g.N + i] = -(dmc_field(g, s, Jr, Jd, i, x, y) + h);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < kDmcThreads / 32; ++k) t += red[k];
+            energy[lat] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// s <- clip(s - eta sign(g), -1, 1), sign(0) = 0.
+__global__ void dmc_spin_step_kernel(int64_t n, float *s, const float *g, float eta) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float v = s[i] - eta * (gi > 0.0f ? 1.0f : (gi < 0.0f ? -1.0f : 0.0f));
+        s[i] = fminf(1.0f, fmaxf(-1.0f, v));
+    }
+}
+
 __global__ void dmc_discretize_kernel(int64_t n, float *s) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         s[i] = s[i] < 0.0f ? -1.0f : 1.0f;
@@ -343,6 +383,20 @@ cudaError_t launch_dmc_step(const DmcStepArgs &a, cudaStream_t s) {
 cudaError_t launch_dmc_loss(int n_lat, int N, const float *spins, const float *target, float *grad,
                             double *loss, cudaStream_t s) {
     dmc_loss_kernel<<<dmc_grid(n_lat, 8), kDmcThreads, 0, s>>>(n_lat, N, spins, target, grad, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dmc_energy(int n_lat, int L, const float *J, const float *spins, float h, float *grad,
+                              double *energy, cudaStream_t s) {
+    dmc_energy_kernel<<<dmc_grid(n_lat, 8), kDmcThreads, 0, s>>>(n_lat, L, J, spins, h, grad, energy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dmc_spin_step(int64_t n, float *spins, const float *grad, float eta, cudaStream_t s) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    dmc_spin_step_kernel<<<blocks, 256, 0, s>>>(n, spins, grad, eta);
     return cudaGetLastError();
 }
 

@@ -216,6 +216,9 @@ cudaError_t launch_dmc_backward(const DmcArgs &a, cudaStream_t s);
 cudaError_t launch_dmc_loss(int n_lat, int N, const float *spins, const float *target, float *grad,
                             double *loss, cudaStream_t s);
 cudaError_t launch_dmc_discretize(int64_t n, float *spins, cudaStream_t s);
+cudaError_t launch_dmc_energy(int n_lat, int L, const float *J, const float *spins, float h, float *grad,
+                              double *energy, cudaStream_t s);
+cudaError_t launch_dmc_spin_step(int64_t n, float *spins, const float *grad, float eta, cudaStream_t s);
 // After a CPM colour sub-step: vol_cur = vol_next, contacts += delta; after
 // colour 3 also V2/V1, record, t += 1.
 cudaError_t launch_cpm_finalize(int32_t *vol_cur, const int32_t *vol_next, int n_cells,

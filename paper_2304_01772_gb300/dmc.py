@@ -1,5 +1,6 @@
-"""Differentiable Monte Carlo pattern optimisation (Alg. 2; Sec.
-"Optimization of the exchange parameters").
+"""Differentiable Monte Carlo (Alg. 2): pattern optimisation of the exchange
+parameters (Sec. "Optimization of the exchange parameters") and energy
+minimisation over the spin values (Sec. "Optimization of the spin values").
 
 A batch of Ising lattices with one exchange parameter per bond is steered
 towards target patterns: each iteration runs `sweeps` relaxed sweeps from the
@@ -13,8 +14,8 @@ from __future__ import annotations
 
 import torch
 
-from . import (adam, dmc_backward, dmc_discretize, dmc_forward, dmc_loss, dmc_step, dmc_step_max_sweeps,
-               dmc_tape_floats)
+from . import (adam, dmc_backward, dmc_discretize, dmc_energy, dmc_forward, dmc_loss, dmc_spin_step, dmc_step,
+               dmc_step_max_sweeps, dmc_tape_floats)
 
 
 class PatternOptimizer:
@@ -64,3 +65,71 @@ class PatternOptimizer:
         dmc_discretize(self.spins, stream)
         self.sweep += self.sweeps
         return self.loss
+
+
+class SpinOptimizer:
+    """Energy minimisation over the spin values (Sec. "Optimization of the spin
+    values") for B lattices with per-bond couplings J [B, 2, L, L] (J = 1: the
+    ferromagnet; random +-1: a spin glass).  Three methods:
+
+    * anneal: Metropolis sweeps (the relaxed update with alpha -> infinity) at
+      increasing beta;
+    * gradient: s <- discretise(clip(s - eta sign(dE/ds), -1, 1)), all sites at once;
+    * dmc: the spins are the parameters of the differentiable Monte Carlo
+      loss E(F(s)), F the relaxed sweeps of Alg. 2; each iteration
+      s <- discretise(clip(s - eta sign(d E(F(s)) / ds), -1, 1)), and the state
+      the simulation produced is discretise(F(s)).
+
+    Each method returns the energy per spin after every iteration (numpy).
+    """
+
+    def __init__(self, J, spins, h=0.0, seed=0):
+        self.J = J.contiguous()
+        self.spins = spins.clone().contiguous()
+        self.B, self.L = spins.shape[0], spins.shape[-1]
+        self.h, self.seed, self.sweep = h, seed, 0
+        self.energy = torch.zeros(self.B, dtype=torch.float64, device=spins.device)
+        self.grad = torch.zeros_like(self.spins)
+
+    def _trace(self, rows):
+        return (torch.stack(rows) / (self.L * self.L)).cpu().numpy()
+
+    def anneal(self, betas, sweeps_per_beta, stream=None):
+        tape = torch.empty(dmc_tape_floats(self.B, self.L, sweeps_per_beta), dtype=torch.float32,
+                           device=self.spins.device)
+        rows = []
+        for beta in betas:
+            dmc_forward(self.seed, self.J, self.spins, beta, self.h, 1e30, self.sweep, sweeps_per_beta, tape, stream)
+            self.sweep += sweeps_per_beta
+            dmc_energy(self.J, self.spins, self.h, self.energy, None, stream)
+            rows.append(self.energy.clone())
+        return self._trace(rows)
+
+    def gradient(self, steps, eta=2.0, stream=None):
+        rows = []
+        for _ in range(steps):
+            dmc_energy(self.J, self.spins, self.h, self.energy, self.grad, stream)
+            dmc_spin_step(self.spins, self.grad, eta, stream)
+            dmc_discretize(self.spins, stream)
+            dmc_energy(self.J, self.spins, self.h, self.energy, None, stream)
+            rows.append(self.energy.clone())
+        return self._trace(rows)
+
+    def dmc(self, steps, beta, alpha, eta=2.0, sweeps=1, stream=None):
+        tape = torch.empty(dmc_tape_floats(self.B, self.L, sweeps), dtype=torch.float32, device=self.spins.device)
+        relaxed = torch.empty_like(self.spins)
+        gJ = torch.empty_like(self.J)
+        rows = []
+        for _ in range(steps):
+            relaxed.copy_(self.spins)
+            dmc_forward(self.seed, self.J, relaxed, beta, self.h, alpha, self.sweep, sweeps, tape, stream)
+            dmc_energy(self.J, relaxed, self.h, self.energy, self.grad, stream)
+            dmc_backward(self.seed, self.J, relaxed, tape, beta, self.h, alpha, self.sweep, sweeps, self.grad, gJ,
+                         stream)
+            self.sweep += sweeps
+            dmc_spin_step(self.spins, self.grad, eta, stream)
+            dmc_discretize(self.spins, stream)
+            dmc_discretize(relaxed, stream)
+            dmc_energy(self.J, relaxed, self.h, self.energy, None, stream)
+            rows.append(self.energy.clone())
+        return self._trace(rows)
