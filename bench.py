@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--workload", default="uneven512",
                     choices=["uneven512", "potts_q3", "potts_q8", "cpm1024", "ising_small", "grad", "mlp", "dmc",
-                             "spinglass"])
+                             "spinglass", "cpm_batch"])
     return ap.parse_args()
 
 
@@ -156,6 +156,21 @@ def _oracle_spinglass(args):
     return n * L * L, time.perf_counter() - t0
 
 
+def _oracle_cpm_batch(args):
+    import oracle
+    from paper_2304_01772_gb300 import workloads as wl
+    b0, n = args
+    p = wl.cpm_paper()
+    op = oracle.CPM(L=p["L"], J=p["J"], lam=p["lam"], target=p["target"], n_cells=p["n_cells"], T=p["T"],
+                    side=p["side"], cols=p["cols"])
+    t0 = time.perf_counter()
+    for b in range(b0, b0 + n):
+        ids, types, vol = op.init(SEED, b)
+        ids = ids.copy()
+        op.run(ids, vol, types, SEED, b, 0, 2, record=False)
+    return n * 2 * p["L"] ** 2, time.perf_counter() - t0
+
+
 def cpu_oracle_pool(fn, tasks, cores):
     import multiprocessing as mp
 
@@ -210,6 +225,11 @@ def cpu_baseline_secondary(workload, cores):
         wall = (time.perf_counter() - t0) / 3
         return {"value": 128 * 1000 / wall, "unit": "samples/s", "cores": 1, "kind": "oracle",
                 "sample": "estimator over 128 chains x 1000 recorded sweeps, per-chain gradients (numpy)"}
+    if workload == "cpm_batch":
+        per = 16
+        rate, units, wall = cpu_oracle_pool(_oracle_cpm_batch, [(b * per, per) for b in range(cores)], cores)
+        return {"value": rate, "unit": "copy-attempts/s", "cores": cores, "kind": "oracle",
+                "sample": f"{per * cores} of the 4096 lattices, two Monte Carlo steps each ({wall:.1f} s wall)"}
     if workload == "spinglass":
         per = 32
         rate, units, wall = cpu_oracle_pool(_oracle_spinglass, [(b * per, per) for b in range(cores)], cores)
@@ -564,6 +584,8 @@ def run_secondary(args):
         return run_dmc(args, cpu)
     if args.workload == "spinglass":
         return run_spinglass(args, cpu)
+    if args.workload == "cpm_batch":
+        return run_cpm_batch(args, cpu)
     record = False
     if args.workload.startswith("potts"):
         q = int(args.workload[-1])
@@ -776,6 +798,49 @@ def run_spinglass(args, cpu):
                            "dmc_best": float(dmc.min(axis=0).mean())},
                        "last_energy_per_spin": float(trace[-1].mean())},
             "gpu_launches": 7 * args.steps}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_cpm_batch(args, cpu):
+    """The paper's cell-sorting setup (64^2, 36 cells + medium, T = 8, A = 25,
+    lambda = 1) on 4096 lattices at once; one step = one Monte Carlo step of
+    every lattice, all steps of the timed region in one launch."""
+    import torch
+    import paper_2304_01772_gb300 as sm
+    from paper_2304_01772_gb300 import workloads as wl
+    p = wl.cpm_paper()
+    B = 4096
+    batch = sm.CPMBatch(B, p["L"], dict(J=p["J"], **{"lambda": p["lam"]}, target=p["target"], n_cells=p["n_cells"],
+                                        T=p["T"], side=p["side"], cols=p["cols"]), seed=SEED)
+    stream = torch.cuda.current_stream()
+    batch.run(args.warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    batch.run(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the same steps one launch each, with statistics recorded every step
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    for _ in range(20):
+        batch.run(1, record=True)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    ms_rec = r0.elapsed_time(r1) / 20
+    units = B * p["L"] ** 2
+    line = {"metric": "copy-attempts/s (cpm_batch)", "value": units / (ms * 1e-3), "unit": "copy-attempts/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"batched cellular Potts, the paper's cell-sorting setup: {B} lattices of "
+                                   "64^2, 36 cells of 5x5 + medium, J = [[0,16,16],[16,2,11],[16,11,14]], A = 25, "
+                                   "lambda = 1, T = 8; all timed steps in one launch",
+                       "one_launch_per_step_with_statistics_ms": ms_rec},
+            "gpu_launches": 1}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

@@ -244,6 +244,36 @@ int spin_ising_sweep_noalloc(uint64_t seed, int32_t n_lattices, const spin_latti
                              int64_t *d_stats, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Batched cellular Potts model (Sec. "Cellular Potts model"; the paper's
+ * cell-sorting setup: 36 cells + medium, T = 8, A = 25, lambda = 1).  Many
+ * independent lattices of one side L, each run by one thread block for all
+ * Monte Carlo steps of a call; caller-owned buffers, nothing allocated:
+ *   ids   int32 [n_lattices][L][L] (cell ids, 0 = medium),
+ *   types uint8 [n_lattices][n_cells + 1] (type of each id),
+ *   areas int32 [n_lattices][n_cells + 1] (sites per id),
+ *   stats int64 [n_steps][n_lattices][n_types (n_types + 1) / 2 + 2] or NULL:
+ *         after every step, C_ab (a <= b, unordered Moore contacts between
+ *         different cells), V2 = sum (a_c - A)^2 and V1 = sum (a_c - A),
+ *   workspace: spin_cpm_batch_workspace_bytes(cpm) bytes of device memory
+ *         (16-byte aligned) for J and the acceptance table.
+ * A step is the four colour sub-steps of the single-lattice model, with the
+ * same random numbers (the batch index is the lattice word of the counter),
+ * so lattice l follows the chain of a one-lattice context with lattice index
+ * l.  Limits: L % 4 == 0, 8 <= L <= 128, 1 <= n_cells < L*L,
+ * n_cells + 1 <= 4096, n_types in [1, 8], J symmetric, T > 0.
+ * ------------------------------------------------------------------------ */
+int64_t spin_cpm_batch_workspace_bytes(const spin_cpm_params *cpm);
+/* Square cells (cpm->init_side, cpm->init_cols) in every lattice, types from
+ * cpm->cell_type (host, shared by all lattices) or drawn per lattice, areas. */
+int spin_cpm_batch_init(uint64_t seed, int32_t n_lattices, int32_t L, const spin_cpm_params *cpm, int32_t *ids,
+                        uint8_t *types, int32_t *areas, void *stream);
+/* n_steps Monte Carlo steps with step indices first_step, first_step + 1, ..
+ * Calls that share a workspace must be ordered on one stream.               */
+int spin_cpm_batch_run(uint64_t seed, int32_t n_lattices, int32_t L, const spin_cpm_params *cpm, int32_t *ids,
+                       const uint8_t *types, int32_t *areas, uint32_t first_step, int32_t n_steps, int64_t *stats,
+                       void *workspace, void *stream);
+
+/* ------------------------------------------------------------------------
  * BF16 MLP surrogate 3 -> 64 -> 64 -> 2 (ReLU) mapping (beta, J, h) to
  * (<E>/N, <M>/N).  Not in the paper.  Weights live in one device buffer
  * of spin_mlp_param_count() floats (FP32 master copy, layout W1[64][3],

@@ -91,6 +91,10 @@ _SIGS = {
     "spin_dmc_step": (_i32, [ctypes.c_uint64, _i32, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                              ctypes.c_uint32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _i32, ctypes.c_float,
                              ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp]),
+    "spin_cpm_batch_workspace_bytes": (ctypes.c_int64, [ctypes.POINTER(CpmParams)]),
+    "spin_cpm_batch_init": (_i32, [ctypes.c_uint64, _i32, _i32, ctypes.POINTER(CpmParams), _vp, _vp, _vp, _vp]),
+    "spin_cpm_batch_run": (_i32, [ctypes.c_uint64, _i32, _i32, ctypes.POINTER(CpmParams), _vp, _vp, _vp,
+                                  ctypes.c_uint32, _i32, _vp, _vp, _vp]),
     "spin_mlp_param_count": (_i32, []),
     "spin_mlp_forward": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "spin_mlp_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
@@ -463,4 +467,52 @@ def dmc_energy(J, spins, h, energy, grad_spins=None, stream=None):
 def dmc_spin_step(spins, grad, eta, stream=None):
     _check(lib().spin_dmc_spin_step(spins.numel(), _ptr(spins), _ptr(grad), float(eta), _stream(stream)),
            None, "spin_dmc_spin_step")
+
+
+# --------------------------------------------------------------------------
+# batched cellular Potts: argument marshalling only
+# --------------------------------------------------------------------------
+class CPMBatch:
+    """n_lattices independent cellular Potts lattices of side L sharing the
+    parameters `cpm` (dict: J, lambda, target, n_cells, T, side, cols and
+    optionally cell_type).  Holds the caller-owned buffers of the batched ABI:
+    ids [B, L, L] int32, types [B, n_cells + 1] uint8, areas [B, n_cells + 1]
+    int32 and the workspace."""
+
+    def __init__(self, n_lattices, L, cpm, seed=0, stream=None):
+        import torch
+        J = np.ascontiguousarray(np.asarray(cpm["J"], dtype=np.int32))
+        ct = cpm.get("cell_type")
+        self._J = J
+        self._types_host = None if ct is None else np.ascontiguousarray(np.asarray(ct, dtype=np.uint8))
+        self.params = CpmParams(J.shape[0], int(cpm["lambda"]), int(cpm["target"]), int(cpm["n_cells"]),
+                                J.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                None if self._types_host is None else
+                                self._types_host.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                float(cpm["T"]), int(cpm.get("side", 0)), int(cpm.get("cols", 0)), 0)
+        self.B, self.L, self.seed = int(n_lattices), int(L), int(seed)
+        nc1 = int(cpm["n_cells"]) + 1
+        self.width = J.shape[0] * (J.shape[0] + 1) // 2 + 2
+        self.ids = torch.empty((self.B, L, L), dtype=torch.int32, device="cuda")
+        self.types = torch.empty((self.B, nc1), dtype=torch.uint8, device="cuda")
+        self.areas = torch.empty((self.B, nc1), dtype=torch.int32, device="cuda")
+        nbytes = int(lib().spin_cpm_batch_workspace_bytes(ctypes.byref(self.params)))
+        if nbytes < 0:
+            raise SpinError("spin_cpm_batch_workspace_bytes: invalid parameters")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.step = 0
+        _check(lib().spin_cpm_batch_init(self.seed, self.B, self.L, ctypes.byref(self.params), _ptr(self.ids),
+                                         _ptr(self.types), _ptr(self.areas), _stream(stream)), None,
+               "spin_cpm_batch_init")
+
+    def run(self, n_steps, record=False, stream=None):
+        """n_steps Monte Carlo steps; with record=True returns the statistics
+        [n_steps, B, width] (int64, device)."""
+        import torch
+        stats = (torch.empty((n_steps, self.B, self.width), dtype=torch.int64, device="cuda") if record else None)
+        _check(lib().spin_cpm_batch_run(self.seed, self.B, self.L, ctypes.byref(self.params), _ptr(self.ids),
+                                        _ptr(self.types), _ptr(self.areas), self.step, int(n_steps), _ptr(stats),
+                                        _ptr(self.workspace), _stream(stream)), None, "spin_cpm_batch_run")
+        self.step += int(n_steps)
+        return stats
 

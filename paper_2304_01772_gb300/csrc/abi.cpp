@@ -1212,6 +1212,83 @@ int spin_profile_read(spin_ctx *ctx, double *total_ms, int64_t *launches, void *
     return SPIN_OK;
 }
 
+// ------------------------------------------------------------------ batched CPM
+static bool aligned16(const void *p);
+
+static std::vector<uint32_t> cpm_thresholds(float T) {
+    std::vector<uint32_t> thr;
+    thr.push_back(0xFFFFFFFFu);  // dE = 0 (never read: dE <= 0 accepts)
+    for (int dE = 1; dE < (1 << 22); ++dE) {
+        const double k = std::floor(std::exp(-(double)dE / (double)T) * 4294967296.0);
+        if (k <= 1.0) break;
+        thr.push_back((uint32_t)(std::min(k, 4294967296.0) - 1.0));
+    }
+    return thr;
+}
+
+static int cpm_batch_check(int32_t n_lattices, int32_t L, const spin_cpm_params *cpm) {
+    if (!cpm || n_lattices < 1 || L < 8 || L > 128 || L % 4) return SPIN_EINVAL;
+    if (cpm->n_types < 1 || cpm->n_types > 8 || !cpm->J_type || cpm->reserved != 0) return SPIN_EINVAL;
+    for (int a = 0; a < cpm->n_types; ++a)
+        for (int b = 0; b < cpm->n_types; ++b)
+            if (cpm->J_type[a * cpm->n_types + b] != cpm->J_type[b * cpm->n_types + a]) return SPIN_EINVAL;
+    if (!(cpm->T > 0.0f) || !std::isfinite(cpm->T) || cpm->lambda < 0 || cpm->target_area < 0) return SPIN_EINVAL;
+    if (cpm->n_cells < 1 || cpm->n_cells >= L * L || cpm->n_cells + 1 > 4096) return SPIN_EINVAL;
+    return SPIN_OK;
+}
+
+int64_t spin_cpm_batch_workspace_bytes(const spin_cpm_params *cpm) {
+    if (!cpm || !(cpm->T > 0.0f) || !std::isfinite(cpm->T)) return SPIN_EINVAL;
+    return 256 + 4 * (int64_t)cpm_thresholds(cpm->T).size();
+}
+
+int spin_cpm_batch_init(uint64_t seed, int32_t n_lattices, int32_t L, const spin_cpm_params *cpm, int32_t *ids,
+                        uint8_t *types, int32_t *areas, void *stream) {
+    if (cpm_batch_check(n_lattices, L, cpm) || !ids || !types || !areas) return SPIN_EINVAL;
+    const int rows = (cpm->n_cells + std::max(1, cpm->init_cols) - 1) / std::max(1, cpm->init_cols);
+    if (cpm->init_side < 1 || cpm->init_cols < 1 || cpm->init_cols * cpm->init_side > L || rows * cpm->init_side > L)
+        return SPIN_EINVAL;
+    cudaStream_t s = S(stream);
+    uint8_t *given = nullptr;
+    if (cpm->cell_type) {
+        if (cpm->cell_type[0] != 0) return SPIN_EINVAL;
+        for (int c = 1; c <= cpm->n_cells; ++c)
+            if (cpm->cell_type[c] >= cpm->n_types) return SPIN_EINVAL;
+        // the caller's types go to lattice 0's slot first and are read from there by every lattice
+        if (cudaMemcpyAsync(types, cpm->cell_type, (size_t)cpm->n_cells + 1, cudaMemcpyHostToDevice, s))
+            return SPIN_ECUDA;
+        given = types;
+    } else if (cpm->n_types < 3) {
+        return SPIN_EINVAL;
+    }
+    return launch_cpm_batch_init(n_lattices, L, cpm->n_cells, cpm->init_side, cpm->init_cols, given,
+                                 (uint32_t)seed, (uint32_t)(seed >> 32), ids, types, areas, s) == cudaSuccess
+               ? SPIN_OK
+               : SPIN_ECUDA;
+}
+
+int spin_cpm_batch_run(uint64_t seed, int32_t n_lattices, int32_t L, const spin_cpm_params *cpm, int32_t *ids,
+                       const uint8_t *types, int32_t *areas, uint32_t first_step, int32_t n_steps, int64_t *stats,
+                       void *workspace, void *stream) {
+    if (cpm_batch_check(n_lattices, L, cpm) || !ids || !types || !areas || n_steps < 1 || !aligned16(workspace))
+        return SPIN_EINVAL;
+    if ((uint64_t)first_step + (uint64_t)n_steps >= 0xFFFFFFFEull) return SPIN_EINVAL;
+    cudaStream_t s = S(stream);
+    const std::vector<uint32_t> thr = cpm_thresholds(cpm->T);
+    std::vector<int32_t> J(64, 0);
+    for (int k = 0; k < cpm->n_types * cpm->n_types; ++k) J[k] = cpm->J_type[k];
+    char *ws = static_cast<char *>(workspace);
+    // pageable sources: the runtime has copied them when these calls return
+    if (cudaMemcpyAsync(ws, J.data(), 256, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(ws + 256, thr.data(), 4 * thr.size(), cudaMemcpyHostToDevice, s))
+        return SPIN_ECUDA;
+    CpmBatchArgs a{n_lattices, L, cpm->n_types, cpm->n_cells, cpm->lambda, cpm->target_area, (int)thr.size(),
+                   cpm->n_types * (cpm->n_types + 1) / 2 + 2, first_step, n_steps, (uint32_t)seed,
+                   (uint32_t)(seed >> 32), ids, types, areas, reinterpret_cast<const int32_t *>(ws),
+                   reinterpret_cast<const uint32_t *>(ws + 256), stats};
+    return launch_cpm_batch(a, s) == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
+}
+
 // ------------------------------------------------------------------ MLP
 int spin_mlp_param_count(void) { return mlp_param_count(); }
 

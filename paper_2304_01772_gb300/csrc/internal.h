@@ -310,6 +310,26 @@ struct DmcStepArgs {
     float lr, b1, b2, eps, c1, c2;
 };
 size_t dmc_step_smem(int L, int n_sweeps);
+
+// Batched cellular Potts: many independent lattices of one side L, each held
+// by one thread block for all sub-steps of the call.
+struct CpmBatchArgs {
+    int n_lat, L, n_types, n_cells, lambda, target, n_thr, width;
+    uint32_t first_step;
+    int n_steps;
+    uint32_t k0, k1;
+    int32_t *ids;            // [n_lat][L*L]
+    const uint8_t *types;    // [n_lat][n_cells + 1]
+    int32_t *areas;          // [n_lat][n_cells + 1]
+    const int32_t *J;        // [n_types][n_types]
+    const uint32_t *thr;     // [n_thr]
+    int64_t *stats;          // [n_steps][n_lat][width] or null
+};
+size_t cpm_batch_smem(int L, int n_cells, int n_thr);
+cudaError_t launch_cpm_batch(const CpmBatchArgs &a, cudaStream_t s);
+cudaError_t launch_cpm_batch_init(int n_lat, int L, int n_cells, int side, int cols, const uint8_t *host_types_dev,
+                                  uint32_t k0, uint32_t k1, int32_t *ids, uint8_t *types, int32_t *areas,
+                                  cudaStream_t s);
 cudaError_t launch_dmc_step(const DmcStepArgs &a, cudaStream_t s);
 
 }  // namespace spinmc

@@ -10,6 +10,8 @@
 // the finalize kernel makes vol_cur = vol_next before the next sub-step.
 // Acceptance: integer dE, thr[dE] = max(floor(exp(-dE/T) 2^32), 1) - 1 built
 // on the host; dE beyond the table accepts only u = 0 (probability 2^-32).
+#include <algorithm>
+
 #include "internal.h"
 
 namespace spinmc {
@@ -228,7 +230,225 @@ __global__ void cpm_types_kernel(uint8_t *type, int n_cells, uint32_t lat, uint3
     }
 }
 
+// ------------------------------------------------------------ batched CPM
+// One block per lattice (grid-stride over the batch); ids, the two area
+// arrays (snapshot and running), cell types, J and the acceptance table live
+// in shared memory for all steps of the call.  Sub-step semantics are those of
+// cpm_substep_kernel (snapshot areas, same Philox counters with the batch index
+// as the lattice word), so each lattice follows its single-lattice chain.
+constexpr int kCpmBatchThreads = 256;
+constexpr int kCpmBatchSmemThr = 4096;   // larger tables stay in global memory
+
+// Periodic index: a mask when L is a power of two, else a compare.
+template <bool POW2>
+__device__ __forceinline__ int wrapb(int v, int L) {
+    return POW2 ? (v & (L - 1)) : (v < 0 ? v + L : (v >= L ? v - L : v));
+}
+
+template <bool POW2>
+__global__ void __launch_bounds__(kCpmBatchThreads) cpm_batch_kernel(CpmBatchArgs a) {
+    extern __shared__ __align__(16) int32_t csm[];
+    __shared__ int4 queue[2 * kCpmBatchThreads];   // live attempts of one pass: (y << 16 | x, sg, sp, u0)
+    __shared__ int qn;
+    const int L = a.L, N = L * L, nc1 = a.n_cells + 1, nt = a.n_types;
+    int32_t *ids = csm, *snap = csm + N, *next = snap + nc1, *Js = next + nc1;
+    int32_t *cnt = Js + 64;                                   // contact counters (<= 36)
+    uint32_t *thr_s = reinterpret_cast<uint32_t *>(cnt + 40);
+    uint8_t *type = reinterpret_cast<uint8_t *>(thr_s + (a.n_thr <= kCpmBatchSmemThr ? a.n_thr : 0));
+    const uint32_t *thr = a.n_thr <= kCpmBatchSmemThr ? thr_s : a.thr;
+    const int npair = nt * (nt + 1) / 2;
+    const unsigned ncu = (unsigned)a.n_cells;
+    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) Js[k] = a.J[k];
+    if (a.n_thr <= kCpmBatchSmemThr)
+        for (int k = threadIdx.x; k < a.n_thr; k += blockDim.x) thr_s[k] = a.thr[k];
+    if (threadIdx.x == 0) qn = 0;
+    const int half = L / 2, ngroups = N / 8;
+    for (int lat = blockIdx.x; lat < a.n_lat; lat += gridDim.x) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) ids[i] = a.ids[(size_t)lat * N + i];
+        for (int c = threadIdx.x; c < nc1; c += blockDim.x) {
+            snap[c] = next[c] = a.areas[(size_t)lat * nc1 + c];
+            const uint8_t tp = a.types[(size_t)lat * nc1 + c];
+            type[c] = tp < nt ? tp : 0;   // out-of-range types read as medium: J stays in bounds
+        }
+        __syncthreads();
+        for (int step = 0; step < a.n_steps; ++step) {
+            const uint32_t t = a.first_step + (uint32_t)step;
+            for (int col = 0; col < 4; ++col) {
+                const int cx = col & 1, cy = col >> 1;
+                // passes of one Philox group per thread: draw and read, queue the live
+                // attempts (ids differ), then spread them over the block
+                for (int base = 0; base < ngroups; base += blockDim.x) {
+                    const int g = base + (int)threadIdx.x;
+                    if (g < ngroups) {
+                        const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)lat, t, (uint32_t)col),
+                                                      a.k0, a.k1);
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            const int k = 2 * g + j, yh = k / half;
+                            const int y = 2 * yh + cy, x = 2 * (k - yh * half) + cx;
+                            const int nbi = (int)((j ? r.w : r.y) >> 29);
+                            const int sg = ids[y * L + x];
+                            const int sp = ids[wrapb<POW2>(y + kMooreDy[nbi], L) * L + wrapb<POW2>(x + kMooreDx[nbi], L)];
+                            if (sp != sg && (unsigned)sg <= ncu && (unsigned)sp <= ncu)
+                                queue[atomicAdd(&qn, 1)] = make_int4((y << 16) | x, sg, sp, (int)(j ? r.z : r.x));
+                        }
+                    }
+                    __syncthreads();
+                    const int n = qn;
+                    __syncthreads();                 // every thread has read the count ...
+                    if (threadIdx.x == 0) qn = 0;    // ... before it is reset for the next pass
+                    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+                        const int4 q4 = queue[e];
+                        const int y = q4.x >> 16, x = q4.x & 0xFFFF, sg = q4.y, sp = q4.z;
+                        const uint32_t u0 = (uint32_t)q4.w;
+                        const int tg = type[sg], tp = type[sp];
+                        long long dH = 0;
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            int sz = ids[wrapb<POW2>(y + kMooreDy[q], L) * L + wrapb<POW2>(x + kMooreDx[q], L)];
+                            sz = (unsigned)sz > ncu ? 0 : sz;
+                            const int tz = type[sz];
+                            if (sz != sp) dH += Js[tp * nt + tz];
+                            if (sz != sg) dH -= Js[tg * nt + tz];
+                        }
+                        if (sp != 0) dH += (long long)a.lambda * (2ll * ((long long)snap[sp] - a.target) + 1);
+                        if (sg != 0) dH += (long long)a.lambda * (-2ll * ((long long)snap[sg] - a.target) + 1);
+                        if (dH <= 0 || u0 <= (dH < a.n_thr ? thr[dH] : 0u)) {
+                            ids[y * L + x] = sp;
+                            atomicAdd(next + sp, 1);
+                            atomicAdd(next + sg, -1);
+                        }
+                    }
+                    __syncthreads();
+                }
+                for (int c = threadIdx.x; c < nc1; c += blockDim.x) snap[c] = next[c];
+                __syncthreads();
+            }
+            if (a.stats) {
+                // statistics of the state after the step, recounted on chip
+                for (int k = threadIdx.x; k < 40; k += blockDim.x) cnt[k] = 0;
+                __syncthreads();
+                long long v2 = 0, v1 = 0;
+                for (int i = threadIdx.x; i < N; i += blockDim.x) {
+                    const int y = i / L, x = i - y * L;
+                    const int ia = ids[i];
+                    const int ta = type[(unsigned)ia > ncu ? 0 : ia];
+                    const int hx[4] = {1, -1, 0, 1}, hy[4] = {0, 1, 1, 1};
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        const int ib = ids[wrapb<POW2>(y + hy[d], L) * L + wrapb<POW2>(x + hx[d], L)];
+                        if (ia == ib) continue;
+                        const int tb = type[(unsigned)ib > ncu ? 0 : ib];
+                        atomicAdd(cnt + pair_index(ta, tb, nt), 1);
+                    }
+                }
+                for (int c = 1 + threadIdx.x; c < nc1; c += blockDim.x) {
+                    const long long d = (long long)snap[c] - a.target;
+                    v2 += d * d;
+                    v1 += d;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    v2 += __shfl_xor_sync(0xFFFFFFFFu, v2, o);
+                    v1 += __shfl_xor_sync(0xFFFFFFFFu, v1, o);
+                }
+                __shared__ long long r2[kCpmBatchThreads / 32], r1[kCpmBatchThreads / 32];
+                if ((threadIdx.x & 31) == 0) {
+                    r2[threadIdx.x >> 5] = v2;
+                    r1[threadIdx.x >> 5] = v1;
+                }
+                __syncthreads();
+                int64_t *out = a.stats + ((size_t)step * a.n_lat + lat) * a.width;
+                for (int k = threadIdx.x; k < npair; k += blockDim.x) out[k] = cnt[k];
+                if (threadIdx.x == 0) {
+                    long long s2 = 0, s1 = 0;
+                    for (int w = 0; w < kCpmBatchThreads / 32; ++w) {
+                        s2 += r2[w];
+                        s1 += r1[w];
+                    }
+                    out[npair] = s2;
+                    out[npair + 1] = s1;
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < N; i += blockDim.x) a.ids[(size_t)lat * N + i] = ids[i];
+        for (int c = threadIdx.x; c < nc1; c += blockDim.x) a.areas[(size_t)lat * nc1 + c] = snap[c];
+        __syncthreads();
+    }
+}
+
+// Batch initial state: every lattice gets the square-cell layout, its own cell
+// types (Philox with the batch index, or the caller's types for all) and areas.
+__global__ void cpm_batch_init_kernel(int n_lat, int L, int n_cells, int side, int cols, const uint8_t *given,
+                                      uint32_t k0, uint32_t k1, int32_t *ids, uint8_t *types, int32_t *areas) {
+    const int N = L * L, nc1 = n_cells + 1;
+    const int rows = (n_cells + cols - 1) / cols;
+    const int x0 = (L - cols * side) / 2, y0 = (L - rows * side) / 2;
+    for (int lat = blockIdx.x; lat < n_lat; lat += gridDim.x) {
+        for (int c = threadIdx.x; c < nc1; c += blockDim.x) {
+            uint8_t tp = 0;
+            if (c > 0) {
+                if (given) {
+                    tp = given[c];
+                } else {
+                    const uint4 r = philox4x32_10(make_uint4((uint32_t)c, (uint32_t)lat, 0xFFFFFFFEu, 0u), k0, k1);
+                    tp = (uint8_t)(1u + (r.x >> 31));
+                }
+            }
+            types[(size_t)lat * nc1 + c] = tp;
+            areas[(size_t)lat * nc1 + c] = 0;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const int y = i / L - y0, x = i % L - x0;
+            int id = 0;
+            if (x >= 0 && y >= 0 && x < cols * side && y < rows * side) {
+                const int cidx = (y / side) * cols + (x / side);
+                if (cidx < n_cells) id = cidx + 1;
+            }
+            ids[(size_t)lat * N + i] = id;
+            atomicAdd(areas + (size_t)lat * nc1 + id, 1);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+size_t cpm_batch_smem(int L, int n_cells, int n_thr) {
+    const size_t nc1 = (size_t)n_cells + 1;
+    return sizeof(int32_t) * ((size_t)L * L + 2 * nc1 + 64 + 40) +
+           sizeof(uint32_t) * (size_t)(n_thr <= kCpmBatchSmemThr ? n_thr : 0) + ((nc1 + 15) & ~(size_t)15);
+}
+
+template <bool POW2>
+static cudaError_t launch_cpm_batch_t(const CpmBatchArgs &a, size_t sm, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(cpm_batch_kernel<POW2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cpm_batch_kernel<POW2>, kCpmBatchThreads, sm);
+    if (e) return e;
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(a.n_lat, sms * std::max(1, per_sm)));
+    cpm_batch_kernel<POW2><<<grid, kCpmBatchThreads, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cpm_batch(const CpmBatchArgs &a, cudaStream_t s) {
+    const size_t sm = cpm_batch_smem(a.L, a.n_cells, a.n_thr);
+    return (a.L & (a.L - 1)) == 0 ? launch_cpm_batch_t<true>(a, sm, s) : launch_cpm_batch_t<false>(a, sm, s);
+}
+
+cudaError_t launch_cpm_batch_init(int n_lat, int L, int n_cells, int side, int cols, const uint8_t *given,
+                                  uint32_t k0, uint32_t k1, int32_t *ids, uint8_t *types, int32_t *areas,
+                                  cudaStream_t s) {
+    const int grid = n_lat < 152 * 8 ? n_lat : 152 * 8;
+    cpm_batch_init_kernel<<<grid, 256, 0, s>>>(n_lat, L, n_cells, side, cols, given, k0, k1, ids, types, areas);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_cpm_substep(const CpmArgs &a, int colour, cudaStream_t s) {
     const int n_groups = (a.L >> 1) * (a.L >> 2);

@@ -96,3 +96,20 @@ def test_dmc_entry_points_reject_invalid_arguments_on_the_host():
     assert lib.spin_dmc_discretize(-1, buf, None) == EINVAL
     assert lib.spin_dmc_discretize(0, None, None) == 0
     assert lib.spin_dmc_loss(0, 16, buf, buf, buf, buf, None) == EINVAL
+
+
+def test_cpm_batch_entry_points_reject_invalid_arguments_on_the_host():
+    lib = sm.lib()
+    J = (ctypes.c_int32 * 9)(0, 16, 16, 16, 2, 11, 16, 11, 14)
+    good = sm.CpmParams(3, 1, 25, 36, J, None, 8.0, 5, 6, 0)
+    assert lib.spin_cpm_batch_workspace_bytes(ctypes.byref(good)) > 256
+    buf = ctypes.c_void_p(256)
+    assert lib.spin_cpm_batch_run(1, 4, 66, ctypes.byref(good), buf, buf, buf, 0, 1, None, buf, None) == EINVAL
+    assert lib.spin_cpm_batch_run(1, 4, 64, ctypes.byref(good), buf, buf, buf, 0, 0, None, buf, None) == EINVAL
+    assert lib.spin_cpm_batch_run(1, 4, 64, ctypes.byref(good), buf, buf, buf, 0, 1, None,
+                                  ctypes.c_void_p(260), None) == EINVAL
+    asym = (ctypes.c_int32 * 9)(0, 16, 15, 16, 2, 11, 16, 11, 14)
+    bad = sm.CpmParams(3, 1, 25, 36, asym, None, 8.0, 5, 6, 0)
+    assert lib.spin_cpm_batch_init(1, 4, 64, ctypes.byref(bad), buf, buf, buf, None) == EINVAL
+    big = sm.CpmParams(3, 1, 25, 36, J, None, 8.0, 20, 6, 0)   # 6 x 20 > 64: does not fit
+    assert lib.spin_cpm_batch_init(1, 4, 64, ctypes.byref(big), buf, buf, buf, None) == EINVAL
