@@ -82,6 +82,10 @@ def _declare(L):
         "or_cpm_run": (None, [_i, _i, _i32p, _i, _i, _i, _u8p, _f, _u64, _u32, _u32, _i,
                               _i32p, _i32p, _i64p]),
         "or_cpm_energy": (ctypes.c_int64, [_i, _i, _i32p, _i, _i, _i, _u8p, _i32p]),
+        "or_tri_substep": (None, [_i, _f, _f, _f, _u64, _u32, _u32, _i, _i8p]),
+        "or_tri_sweep": (None, [_i, _f, _f, _f, _u64, _u32, _u32, _i8p]),
+        "or_tri_stats": (None, [_i, _i8p, _i64p]),
+        "or_tri_run": (None, [_i, _f, _f, _f, _u64, _u32, _u32, _i, _i8p, _i64p]),
         "or_dmc_substep": (None, [_i, _dp, _dp, _d, _d, _d, _u64, _u32, _u32, _i, _dp]),
         "or_dmc_run": (None, [_i, _dp, _dp, _d, _d, _d, _u64, _u32, _u32, _i, _dp, _dp]),
         "or_dmc_backward": (None, [_i, _dp, _dp, _d, _d, _d, _u64, _u32, _u32, _i, _dp, _dp, _dp, _dp]),
@@ -156,6 +160,29 @@ def ising_run(s, beta, J, h, seed, lattice, sweep0, nsweeps, record=True):
 # --------------------------------------------------------------------------
 # Potts
 # --------------------------------------------------------------------------
+def tri_substep(s, beta, J, h, seed, lattice, sweep, colour):
+    """Triangular-lattice Ising colour sub-step in place (s int8 [L, L], L % 3 == 0)."""
+    lib().or_tri_substep(s.shape[0], beta, J, h, seed, lattice, sweep, colour, _p(s, ctypes.c_int8))
+
+
+def tri_sweep(s, beta, J, h, seed, lattice, sweep):
+    lib().or_tri_sweep(s.shape[0], beta, J, h, seed, lattice, sweep, _p(s, ctypes.c_int8))
+
+
+def tri_stats(s):
+    out = np.zeros(2, dtype=np.int64)
+    lib().or_tri_stats(s.shape[0], _p(np.ascontiguousarray(s), ctypes.c_int8), _p(out, ctypes.c_int64))
+    return out
+
+
+def tri_run(s, beta, J, h, seed, lattice, sweep0, nsweeps, record=True):
+    """Run nsweeps in place; stats [nsweeps, 2] = (M, B) after each sweep."""
+    st = np.zeros((nsweeps, 2), dtype=np.int64) if record else None
+    lib().or_tri_run(s.shape[0], beta, J, h, seed, lattice, sweep0, nsweeps, _p(s, ctypes.c_int8),
+                     _p(st, ctypes.c_int64) if record else None)
+    return st
+
+
 def init_potts(L, q, seed, lattice=0):
     s = np.zeros(L * L, dtype=np.uint8)
     lib().or_init_potts(L, q, seed, lattice, _p(s, ctypes.c_uint8))

@@ -607,3 +607,65 @@ void or_dmc_spin_step(int n, double *s, const double *g, double eta)
         s[i] = v > 1.0 ? 1.0 : (v < -1.0 ? -1.0 : v);
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Ising model on the triangular lattice (Sec. "Ising model": other     */
+/* connectivities through a kernel matching the lattice geometry).  The */
+/* triangular lattice is stored on the square grid with six neighbours  */
+/* (x+-1, y), (x, y+-1), (x+1, y-1), (x-1, y+1), periodic; every bond is */
+/* counted once through (x+1, y), (x, y+1), (x-1, y+1).  Three colours   */
+/* c = (x - y) mod 3 (no bond joins two sites of one colour; L % 3 == 0) */
+/* replace the two of the checkerboard, updated in the order 0, 1, 2.    */
+/* The draw of site (x, y) of colour c: k = y (L/3) + (x div 3),         */
+/* Philox(seed; k >> 2, lattice, sweep, c), lane k & 3.                  */
+/* ------------------------------------------------------------------ */
+static int tri_nsum(int L, const int8_t *s, int x, int y)
+{
+    int xl = wrap(x - 1, L), xr = wrap(x + 1, L), yu = wrap(y - 1, L), yd = wrap(y + 1, L);
+    return s[y * L + xl] + s[y * L + xr] + s[yu * L + x] + s[yd * L + x] + s[yu * L + xr] + s[yd * L + xl];
+}
+
+void or_tri_substep(int L, float beta, float J, float h, uint64_t seed, uint32_t lattice, uint32_t sweep,
+                    int colour, int8_t *s)
+{
+    double beta_d = (double)beta;
+    for (int y = 0; y < L; ++y)
+        for (int x = 0; x < L; ++x) {
+            if (((x - y) % 3 + 3) % 3 != colour) continue;
+            int sig = s[y * L + x];
+            int n = tri_nsum(L, s, x, y);
+            double dE = 2.0 * (double)sig * ((double)J * (double)n + (double)h);
+            uint32_t k = (uint32_t)(y * (L / 3) + x / 3);
+            uint32_t r[4];
+            draw4(seed, k >> 2, lattice, sweep, (uint32_t)colour, r);
+            if (or_accept(beta_d, dE, r[k & 3u])) s[y * L + x] = (int8_t)(-sig);
+        }
+}
+
+void or_tri_sweep(int L, float beta, float J, float h, uint64_t seed, uint32_t lattice, uint32_t sweep, int8_t *s)
+{
+    for (int c = 0; c < 3; ++c) or_tri_substep(L, beta, J, h, seed, lattice, sweep, c, s);
+}
+
+/* out[0] = M = sum s, out[1] = B = sum over bonds of s_i s_j (3 per site). */
+void or_tri_stats(int L, const int8_t *s, int64_t out[2])
+{
+    int64_t M = 0, B = 0;
+    for (int y = 0; y < L; ++y)
+        for (int x = 0; x < L; ++x) {
+            int v = s[y * L + x];
+            M += v;
+            B += v * (s[y * L + wrap(x + 1, L)] + s[wrap(y + 1, L) * L + x] + s[wrap(y + 1, L) * L + wrap(x - 1, L)]);
+        }
+    out[0] = M;
+    out[1] = B;
+}
+
+void or_tri_run(int L, float beta, float J, float h, uint64_t seed, uint32_t lattice, uint32_t sweep0,
+                int nsweeps, int8_t *s, int64_t *stats)
+{
+    for (int t = 0; t < nsweeps; ++t) {
+        or_tri_sweep(L, beta, J, h, seed, lattice, sweep0 + (uint32_t)t, s);
+        if (stats) or_tri_stats(L, s, stats + 2 * (size_t)t);
+    }
+}
