@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--workload", default="uneven512",
                     choices=["uneven512", "potts_q3", "potts_q8", "cpm1024", "ising_small", "grad", "mlp", "dmc",
-                             "spinglass", "cpm_batch"])
+                             "spinglass", "cpm_batch", "triangular"])
     return ap.parse_args()
 
 
@@ -171,6 +171,16 @@ def _oracle_cpm_batch(args):
     return n * 2 * p["L"] ** 2, time.perf_counter() - t0
 
 
+def _oracle_tri(args):
+    import oracle
+    b0, n = args
+    t0 = time.perf_counter()
+    for b in range(b0, b0 + n):
+        s = oracle.init_ising(192, SEED, b).copy()
+        oracle.tri_run(s, 0.2 + 0.15 * b / 255, 1.0, 0.0, SEED, b, 0, 1, record=False)
+    return n * 192 * 192, time.perf_counter() - t0
+
+
 def cpu_oracle_pool(fn, tasks, cores):
     import multiprocessing as mp
 
@@ -208,6 +218,12 @@ def cpu_baseline_secondary(workload, cores):
         wall = time.perf_counter() - t0
         return {"value": 2 * p["L"] ** 2 / wall, "unit": "copy-attempts/s", "cores": 1, "kind": "oracle",
                 "sample": f"2 Monte Carlo steps of the 1024^2 lattice, one core (a single chain) ({wall:.1f} s)"}
+    if workload == "triangular":
+        import numpy as np
+        per = 2
+        rate, units, wall = cpu_oracle_pool(_oracle_tri, [(b * per, per) for b in range(cores)], cores)
+        return {"value": rate, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+                "sample": f"{per * cores} of the 256 lattices, one sweep each ({wall:.1f} s wall)"}
     if workload == "ising_small":
         lats = wl.ising_small()
         rate, units, wall = cpu_oracle_rate(lats, 1000, min(cores, len(lats)))
@@ -593,6 +609,12 @@ def run_secondary(args):
         sim = sm.Sim(sm.SPIN_POTTS, lats, seed=SEED, max_record=16)
         units, unit = wl.site_count(lats), "site-updates/s"
         desc = f"64 q={q} Potts lattices 1024^2, beta = ln(1+sqrt(q)) * linspace(0.8, 1.2, 64), uint8"
+    elif args.workload == "triangular":
+        lats = [dict(L=192, beta=0.2 + 0.15 * k / 255, J=1.0, h=0.0, geometry=1) for k in range(256)]
+        sim = sm.Sim(sm.SPIN_ISING, lats, seed=SEED, max_record=16)
+        units, unit = wl.site_count(lats), "site-updates/s"
+        desc = ("256 triangular-lattice Ising lattices 192^2 (six neighbours, three colours), "
+                "beta = linspace(0.2, 0.35, 256) across beta_c = ln(3)/4")
     elif args.workload == "cpm1024":
         p = wl.cpm1024()
         sim = sm.Sim(sm.SPIN_CPM, [dict(L=p["L"])], seed=SEED, max_record=16,

@@ -72,7 +72,10 @@ typedef struct {
     float beta;           /* inverse temperature 1/T (finite, >= 0); ignored for CPM          */
     float J;              /* coupling (Ising, Potts)                                          */
     float h;              /* field (Ising); must be 0 for Potts                                */
-    int32_t reserved;     /* must be 0                                                         */
+    int32_t geometry;     /* 0: square lattice, 4 neighbours (Sec. "Ising model", kernel K);
+                             1: triangular lattice, 6 neighbours (x+-1, y), (x, y+-1), (x+1, y-1),
+                             (x-1, y+1) on the square grid, three colours c = (x - y) mod 3 updated
+                             in order; Ising only, L % 6 == 0                                   */
     uint64_t spin_offset; /* element offset of this lattice in the caller's spin buffer       */
 } spin_lattice_desc;
 

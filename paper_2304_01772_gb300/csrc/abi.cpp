@@ -77,6 +77,8 @@ struct spin_ctx {
     Item *d_strip = nullptr;     // warp row-strip items (Ising, L in {512, 1024, 2048})
     int n_strip = 0, strip_grid = 0, strip_warps = 8, strip_qbits = 2, strip_chunks = 128;
     int32_t *d_generic = nullptr;
+    int32_t *d_tri = nullptr;   // triangular lattices (geometry 1)
+    int n_tri = 0, tri_maxL = 0;
     int n_generic = 0, generic_maxL = 0;
     std::vector<int> fast_ids;
     DevState *d_state = nullptr;
@@ -158,6 +160,20 @@ void ising_table(const spin_lattice_desc &d, TabEntry *e) {
         }
 }
 
+// Triangular lattice: entry dn + 7 c, dn = down neighbours of six, n = 6 - 2 dn.
+void tri_table(const spin_lattice_desc &d, TabEntry *e) {
+    const double beta = (double)d.beta;
+    for (int c = 0; c < 2; ++c)
+        for (int dn = 0; dn <= 6; ++dn) {
+            const int s = c ? -1 : 1;
+            const int n = 6 - 2 * dn;
+            const double dE = 2.0 * (double)s * ((double)d.J * (double)n + (double)d.h);
+            TabEntry &x = e[dn + 7 * c];
+            x.thr = thr_from(beta, dE);
+            x.delta = (-2 * s * n) * 65536 + (-2 * s);
+        }
+}
+
 void potts_table(const spin_lattice_desc &d, TabEntry *e) {
     const double beta = (double)d.beta;
     for (int dd = -4; dd <= 4; ++dd) {
@@ -192,7 +208,9 @@ int validate(spin_ctx *ctx, int model, int n, const spin_lattice_desc *lat,
             snprintf(buf, sizeof buf, "lattice %d: L=%d must be even and in [4, %d]", i, d.L, kMaxL);
             return fail(ctx, SPIN_EINVAL, buf);
         }
-        if (d.reserved != 0) return fail(ctx, SPIN_EINVAL, "reserved field must be 0");
+        if (d.geometry != 0 && d.geometry != 1) return fail(ctx, SPIN_EINVAL, "geometry must be 0 or 1");
+        if (d.geometry == 1 && (model != SPIN_ISING || d.L % 6 != 0))
+            return fail(ctx, SPIN_EINVAL, "the triangular lattice needs the Ising model and L % 6 == 0");
         if (model == SPIN_POTTS) {
             if (d.q < 2 || d.q > 255) {
                 snprintf(buf, sizeof buf, "lattice %d: q=%d out of [2, 255]", i, d.q);
@@ -264,7 +282,9 @@ int upload_tables(spin_ctx *ctx, cudaStream_t s) {
     std::vector<double> lp((size_t)ctx->n_lat * 4);
     for (int i = 0; i < ctx->n_lat; ++i) {
         const spin_lattice_desc &d = ctx->lat[i];
-        if (ctx->model == SPIN_ISING)
+        if (ctx->model == SPIN_ISING && d.geometry == 1)
+            tri_table(d, &tab[(size_t)i * kTabStride]);
+        else if (ctx->model == SPIN_ISING)
             ising_table(d, &tab[(size_t)i * kTabStride]);
         else
             potts_table(d, &tab[(size_t)i * kTabStride]);
@@ -411,6 +431,13 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                 if (timed) prof_end(ctx, s);
                 ++launches;
             }
+            if (ctx->n_tri && c == 0)
+                for (int tc = 0; tc < 3; ++tc) {
+                    CK(launch_ising_tri(static_cast<int8_t *>(src), static_cast<int8_t *>(src), ctx->d_tri, ctx->n_tri,
+                                        ctx->tri_maxL, ctx->d_lats, ctx->d_tabs, ctx->k0, ctx->k1, ctx->d_state,
+                                        ctx->st.delta, tc, s));
+                    ++launches;
+                }
             if (ctx->n_generic) {
                 if (ctx->model == SPIN_ISING)
                     CK(launch_ising_generic(static_cast<int8_t *>(src), static_cast<int8_t *>(src), ctx->d_generic,
@@ -424,6 +451,12 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
             }
         }
     } else {
+        for (int tc = 0; tc < 3 && ctx->n_tri; ++tc) {
+            CK(launch_ising_tri(static_cast<int8_t *>(src), static_cast<int8_t *>(dst), ctx->d_tri, ctx->n_tri,
+                                ctx->tri_maxL, ctx->d_lats, ctx->d_tabs, ctx->k0, ctx->k1, ctx->d_state,
+                                ctx->st.delta, tc, s));
+            ++launches;
+        }
         for (int c = 0; c < 2 && ctx->n_generic; ++c) {
             if (ctx->model == SPIN_ISING)
                 CK(launch_ising_generic(static_cast<int8_t *>(src), static_cast<int8_t *>(dst), ctx->d_generic,
@@ -661,7 +694,7 @@ int spin_num_grad(const spin_ctx *ctx) {
 void spin_destroy(spin_ctx *ctx) {
     if (!ctx) return;
     drop_graphs(ctx);
-    void *bufs[] = {ctx->spins2, ctx->d_lats, ctx->d_tabs, ctx->d_items, ctx->d_strip, ctx->d_generic,
+    void *bufs[] = {ctx->spins2, ctx->d_lats, ctx->d_tabs, ctx->d_items, ctx->d_strip, ctx->d_generic, ctx->d_tri,
                     ctx->d_state, ctx->st.cur, ctx->st.delta, ctx->st.ring, ctx->d_type,
                     ctx->d_J, ctx->d_vol[0], ctx->d_vol[1], ctx->d_thr, ctx->d_latp,
                     ctx->d_cpmJ, ctx->d_scratch, ctx->d_flag};
@@ -720,14 +753,18 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
     }
     ctx->width = stats_width(model, ctx->lat, ctx->n_types);
     std::vector<LatDev> ld(n_lattices);
-    std::vector<int32_t> generic;
+    std::vector<int32_t> generic, tri;
     for (int i = 0; i < n_lattices; ++i) {
         const auto &d = ctx->lat[i];
+        const int geom = model == SPIN_CPM ? 0 : d.geometry;
         ld[i] = LatDev{d.spin_offset, d.L, model == SPIN_POTTS ? d.q : 2,
-                       (d.L % 16 == 0 && d.spin_offset % 16 == 0) ? 1 : 0, 0};
+                       (geom == 0 && d.L % 16 == 0 && d.spin_offset % 16 == 0) ? 1 : 0, geom};
         ctx->maxL = std::max(ctx->maxL, d.L);
         ctx->span_elems = std::max<size_t>(ctx->span_elems, d.spin_offset + (size_t)d.L * d.L);
-        if (ld[i].fast)
+        if (geom == 1) {
+            tri.push_back(i);
+            ctx->tri_maxL = std::max(ctx->tri_maxL, d.L);
+        } else if (ld[i].fast)
             ctx->fast_ids.push_back(i);
         else {
             generic.push_back(i);
@@ -735,6 +772,7 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
         }
     }
     ctx->n_generic = (int)generic.size();
+    ctx->n_tri = (int)tri.size();
     auto ckm = [&](cudaError_t e) { return e == cudaSuccess; };
     const size_t w = (size_t)ctx->width;
     if (!ckm(cudaMalloc(&ctx->d_lats, sizeof(LatDev) * n_lattices)) ||
@@ -754,6 +792,10 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
         if (!ckm(cudaMalloc(&ctx->d_generic, sizeof(int32_t) * ctx->n_generic)))
             return bail(SPIN_ENOMEM);
         cudaMemcpy(ctx->d_generic, generic.data(), sizeof(int32_t) * generic.size(), cudaMemcpyHostToDevice);
+    }
+    if (ctx->n_tri) {
+        if (!ckm(cudaMalloc(&ctx->d_tri, sizeof(int32_t) * ctx->n_tri))) return bail(SPIN_ENOMEM);
+        cudaMemcpy(ctx->d_tri, tri.data(), sizeof(int32_t) * tri.size(), cudaMemcpyHostToDevice);
     }
     ctx->st.cap = max_record_sweeps;
     ctx->st.width = ctx->width;
@@ -975,8 +1017,8 @@ int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_
         if (rc) return rc;
         for (int i = 0; i < ctx->n_lat; ++i)
             if (lat[i].L != ctx->lat[i].L || lat[i].q != ctx->lat[i].q ||
-                lat[i].spin_offset != ctx->lat[i].spin_offset)
-                return fail(ctx, SPIN_EINVAL, "spin_set_params may not change L, q or offsets");
+                lat[i].spin_offset != ctx->lat[i].spin_offset || lat[i].geometry != ctx->lat[i].geometry)
+                return fail(ctx, SPIN_EINVAL, "spin_set_params may not change L, q, geometry or offsets");
         ctx->lat.assign(lat, lat + ctx->n_lat);
     }
     if (cpm) {
@@ -1001,7 +1043,7 @@ int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_
 }
 
 static bool resident_ok(const spin_ctx *ctx) {
-    if (ctx->model != SPIN_ISING || ctx->n_generic) return false;
+    if (ctx->model != SPIN_ISING || ctx->n_generic || ctx->n_tri) return false;
     for (const auto &d : ctx->lat)
         if (d.L > 256) return false;
     return true;

@@ -13,7 +13,7 @@ struct LatDev {
     int32_t L;
     int32_t q;        // Potts states (2 for Ising)
     int32_t fast;     // 1: L % 16 == 0 and offset % 16 == 0 -> vectorised kernels
-    int32_t pad;
+    int32_t geom;     // 0: square lattice, 1: triangular (Ising)
 };
 
 // One work item of the batched sweep: rows [r0, r0 + nrows) of lattice `lat`.
@@ -111,6 +111,12 @@ cudaError_t launch_ising_plain(int8_t *spins, const LatDev *lat_dev, int lat, in
                                const DevState *state, int64_t *delta, int colour, cudaStream_t s);
 // Lattices whose side is not a multiple of 16: two passes, src -> dst (colour 0,
 // other sites copied) and dst in place (colour 1).  lat_ids: device list.
+// Triangular-lattice Ising (geometry 1), one colour of three over the listed
+// lattices: colour 0 reads src and writes dst (copying the other sites),
+// colours 1 and 2 work in place on dst.
+cudaError_t launch_ising_tri(const int8_t *src, int8_t *dst, const int32_t *lat_ids, int n, int maxL,
+                             const LatDev *lats, const TabEntry *tabs, uint32_t k0, uint32_t k1,
+                             const DevState *state, int64_t *delta, int colour, cudaStream_t s);
 cudaError_t launch_ising_generic(const int8_t *src, int8_t *dst, const int32_t *lat_ids, int n,
                                  int maxL, const LatDev *lats, const TabEntry *tabs, uint32_t k0,
                                  uint32_t k1, const DevState *state, int64_t *delta, int colour,

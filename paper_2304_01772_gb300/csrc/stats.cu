@@ -48,6 +48,8 @@ __global__ void stats_state_kernel(const void *spins, int model, const LatDev *l
             const int s = S[i];
             a0 += s;
             a1 += s * (S[ir] + S[id]);
+            if (ld.geom == 1)   // triangular: the third bond direction (x - 1, y + 1)
+                a1 += s * S[(y == L - 1 ? 0 : y + 1) * L + (x == 0 ? L - 1 : x - 1)];
         } else {
             const uint8_t *S = static_cast<const uint8_t *>(spins) + ld.offset;
             const int s = S[i];

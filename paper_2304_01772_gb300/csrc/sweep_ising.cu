@@ -260,6 +260,70 @@ __global__ void __launch_bounds__(256) ising_plain_kernel(int8_t *spins, int L, 
 
 // Any even L: one thread per site.  colour 0 pass reads src and writes every
 // site of dst (colour-1 sites copied); colour 1 pass updates dst in place.
+// Triangular lattice (geometry 1): six neighbours (x+-1, y), (x, y+-1),
+// (x+1, y-1), (x-1, y+1); colour (x - y) mod 3; table entry dcount + 7 cdown
+// (dcount = down neighbours of 6, n = 6 - 2 dcount); the draw of a site is
+// lane k & 3 of group k >> 2, k = y (L/3) + x div 3 (one compressed index per
+// site of a colour).  One thread per site.
+__global__ void ising_tri_kernel(const int8_t *src, int8_t *dst, const int32_t *lat_ids, const LatDev *lats,
+                                 const TabEntry *tabs, uint32_t k0, uint32_t k1, const DevState *state,
+                                 int64_t *delta, int c) {
+    __shared__ int red[2 * 8];
+    const int lat = lat_ids[blockIdx.y];
+    const LatDev ld = lats[lat];
+    const int L = ld.L;
+    const int8_t *S = (c == 0 ? src : dst) + ld.offset;
+    int8_t *D = dst + ld.offset;
+    const uint32_t t = state->t;
+    int dm = 0, db = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L * L; i += gridDim.x * blockDim.x) {
+        const int y = i / L, x = i - y * L;
+        const int s = S[i];
+        if ((x - y + 3 * L) % 3 != c) {
+            if (c == 0) D[i] = (int8_t)s;
+            continue;
+        }
+        const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
+        const int xl = x == 0 ? L - 1 : x - 1, xr = x == L - 1 ? 0 : x + 1;
+        const int dcount = (S[y * L + xl] < 0) + (S[y * L + xr] < 0) + (S[yu * L + x] < 0) + (S[yd * L + x] < 0) +
+                           (S[yu * L + xr] < 0) + (S[yd * L + xl] < 0);
+        const int n = 6 - 2 * dcount;
+        const int cdown = s < 0 ? 1 : 0;
+        const TabEntry e = tabs[lat * kTabStride + dcount + 7 * cdown];
+        const uint32_t k = (uint32_t)(y * (L / 3) + x / 3);
+        const uint4 r = philox4x32_10(make_uint4(k >> 2, (uint32_t)lat, t, (uint32_t)c), k0, k1);
+        const uint32_t lane = k & 3u;
+        const uint32_t u = lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
+        const int sv = s < 0 ? -1 : 1;
+        if (u <= e.thr) {
+            D[i] = (int8_t)(-sv);
+            dm += -2 * sv;
+            db += -2 * sv * n;
+        } else if (c == 0) {
+            D[i] = (int8_t)s;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dm += __shfl_xor_sync(0xFFFFFFFFu, dm, o);
+        db += __shfl_xor_sync(0xFFFFFFFFu, db, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[2 * (threadIdx.x >> 5)] = dm;
+        red[2 * (threadIdx.x >> 5) + 1] = db;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long sm = 0, sb = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            sm += red[2 * k];
+            sb += red[2 * k + 1];
+        }
+        if (sm) atomicAdd(reinterpret_cast<unsigned long long *>(delta + 2 * lat), (unsigned long long)sm);
+        if (sb) atomicAdd(reinterpret_cast<unsigned long long *>(delta + 2 * lat + 1), (unsigned long long)sb);
+    }
+}
+
 __global__ void ising_generic_kernel(const int8_t *src, int8_t *dst, const int32_t *lat_ids,
                                      const LatDev *lats, const TabEntry *tabs, uint32_t k0,
                                      uint32_t k1, const DevState *state, int64_t *delta, int c) {
@@ -701,6 +765,16 @@ cudaError_t launch_ising_plain(int8_t *spins, const LatDev *, int lat, int L, co
     const int units = L * (L >> 4);
     ising_plain_kernel<<<(units + 255) / 256, 256, 0, s>>>(
         spins, L, (uint32_t)lat, tabs + lat * kTabStride, k0, k1, state, delta, colour);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ising_tri(const int8_t *src, int8_t *dst, const int32_t *lat_ids, int n, int maxL,
+                             const LatDev *lats, const TabEntry *tabs, uint32_t k0, uint32_t k1,
+                             const DevState *state, int64_t *delta, int colour, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int blocks = (maxL * maxL + 255) / 256;
+    dim3 grid(blocks < 64 ? blocks : 64, n);
+    ising_tri_kernel<<<grid, 256, 0, s>>>(src, dst, lat_ids, lats, tabs, k0, k1, state, delta, colour);
     return cudaGetLastError();
 }
 

@@ -113,3 +113,13 @@ def test_cpm_batch_entry_points_reject_invalid_arguments_on_the_host():
     assert lib.spin_cpm_batch_init(1, 4, 64, ctypes.byref(bad), buf, buf, buf, None) == EINVAL
     big = sm.CpmParams(3, 1, 25, 36, J, None, 8.0, 20, 6, 0)   # 6 x 20 > 64: does not fit
     assert lib.spin_cpm_batch_init(1, 4, 64, ctypes.byref(big), buf, buf, buf, None) == EINVAL
+
+
+@pytest.mark.parametrize("desc,model", [
+    (sm.LatticeDesc(48, 2, 0.4, 1.0, 0.0, 2, 0), sm.SPIN_ISING),   # unknown geometry
+    (sm.LatticeDesc(64, 2, 0.4, 1.0, 0.0, 1, 0), sm.SPIN_ISING),   # triangular needs L % 6 == 0
+    (sm.LatticeDesc(48, 3, 0.4, 1.0, 0.0, 1, 0), sm.SPIN_POTTS),   # triangular is Ising only
+])
+def test_geometry_is_validated(desc, model):
+    rc, _ = _init(model, [desc])
+    assert rc == EINVAL

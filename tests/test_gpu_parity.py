@@ -406,3 +406,29 @@ def test_out_of_range_states_are_harmless():
     cs = sm.Sim(sm.SPIN_CPM, [dict(L=p["L"])], seed=SEED, spins=ids, init_mode=1, max_record=4, cpm=cpm)
     cs.sweep(2, record=True)
     torch.cuda.synchronize()
+
+
+# ------------------------------------------------------------ triangular lattice
+TRI = [dict(L=L, beta=b, J=J, h=h, geometry=1) for L, b, J, h in [
+    (6, 0.3, 1.0, 0.0), (12, 0.27, 1.0, 0.05), (48, 0.35, -1.0, 0.1), (96, 0.27, 1.0, 0.0)]]
+
+
+@pytest.mark.parametrize("mode,graph", [(0, True), (0, False), (1, False)])
+def test_triangular_lattices_next_to_square_ones(mode, graph):
+    lats = TRI + [dict(L=64, beta=0.44, J=1.0, h=0.0), dict(L=10, beta=0.3, J=1.0, h=0.02)]
+    sim = make_ising(lats, max_record=16)
+    sim.set_launch(mode, graph, 0, 256)
+    init = {i: lattice_np(sim, i) for i in range(len(lats))}
+    st0 = sim.current_stats().cpu().numpy()
+    for i, d in enumerate(lats):
+        ref = oracle.tri_stats(init[i]) if d.get("geometry") else oracle.ising_stats(init[i])
+        assert np.array_equal(st0[i], ref), i
+    sim.sweep(1, record=True)
+    sim.sweep(4, record=True)
+    st = sim.observables_host(0, 5)[0]
+    for i, d in enumerate(lats):
+        s = init[i].copy()
+        run = oracle.tri_run if d.get("geometry") else oracle.ising_run
+        ref = run(s, d["beta"], d["J"], d["h"], SEED, i, 0, 5)
+        assert np.array_equal(lattice_np(sim, i), s), (i, d)
+        assert np.array_equal(st[:, i, :], ref), (i, d)
