@@ -344,6 +344,8 @@ KERNEL_SECTIONS = {
     "ising_strip_kernel": ("sweep_ising.cu",
                            "// ------------------------------------------------------------------ strip kernel",
                            "// Copy every lattice"),
+    "dmc_step_kernel": ("dmc.cu", "// One whole optimisation iteration per lattice",
+                        "// loss[lat] = sum (target - s)^2"),
     "potts_strip_kernel": ("sweep_potts.cu",
                            "// ------------------------------------------------------------ strip kernel",
                            "__global__ void __launch_bounds__(256) potts_plain_kernel("),
@@ -771,7 +773,7 @@ def run_dmc(args, cpu):
                        "mean_loss_last_step": float(loss.mean()), "fused": opt.fused,
                        "separate_launches": separate},
             "roofline": {"bound": "hbm", "achieved": kernels[top]["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                         "frac": kernels[top]["achieved_gbs"] / peak, "traffic": None, "kernel": top,
+                         "frac": kernels[top]["achieved_gbs"] / peak, "traffic": ncu_traffic(top, "dmc"), "kernel": top,
                          "peak_source": f"{kind} hbm_gbs", "kernels": kernels},
             "gpu_launches": (1 if opt.fused else 5) * args.steps}
     if cpu is not None:
