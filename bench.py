@@ -545,11 +545,19 @@ def run_ours(args):
             b = 2.0 * cls_sites[cls]
             kernels[name] = {"launch_ms": kms / kn, "launches": kn, "algorithmic_bytes_per_launch": b,
                              "achieved_gbs": b / (kms / kn * 1e-3) / 1e9, "share_of_kernel_time": 0.0}
+    overlapped = len(kernels) == 2   # the tile kernel runs on a side stream, concurrently with the strip kernel
     tot = sum(prof[c][0] for c in (0, 1)) or 1.0
     for cls, name in ((0, "ising_fused_kernel"), (1, "ising_strip_kernel")):
         if name in kernels:
             kernels[name]["share_of_kernel_time"] = prof[cls][0] / tot
-    dom = max(kernels, key=lambda k: kernels[k]["share_of_kernel_time"]) if kernels else None
+    if overlapped:
+        # its events then bracket co-running wall time, not its own cost; the ncu launch
+        # list (serialised) gives its cost: about 0.023 ms per launch
+        kernels["ising_fused_kernel"]["share_of_kernel_time"] = None
+        kernels["ising_fused_kernel"]["stream"] = "side stream, overlaps ising_strip_kernel"
+        kernels["ising_strip_kernel"]["share_of_kernel_time"] = None
+    dom = ("ising_strip_kernel" if overlapped else
+           (max(kernels, key=lambda k: kernels[k]["share_of_kernel_time"]) if kernels else None))
     achieved = kernels[dom]["achieved_gbs"] if dom else None
     alg_bytes = kernels[dom]["algorithmic_bytes_per_launch"] if dom else None
     kms_dom = kernels[dom]["launch_ms"] if dom else None
