@@ -341,29 +341,35 @@ def measured_peaks():
 
 
 KERNEL_SECTIONS = {
+    # kernel: (file, section start, section end, end of the part of internal.h it depends on)
     "ising_strip_kernel": ("sweep_ising.cu",
                            "// ------------------------------------------------------------------ strip kernel",
-                           "// Copy every lattice"),
+                           "// Copy every lattice", "cudaError_t launch_ising_strip("),
     "dmc_step_kernel": ("dmc.cu", "// One whole optimisation iteration per lattice",
-                        "// loss[lat] = sum (target - s)^2"),
+                        "// loss[lat] = sum (target - s)^2", "cudaError_t launch_dmc_step("),
     "potts_strip_kernel": ("sweep_potts.cu",
                            "// ------------------------------------------------------------ strip kernel",
-                           "__global__ void __launch_bounds__(256) potts_plain_kernel("),
+                           "__global__ void __launch_bounds__(256) potts_plain_kernel(",
+                           "cudaError_t launch_potts_strip("),
 }
 
 
 def kernel_source_hash(kernel="ising_strip_kernel"):
-    """Hash of the source of one kernel's section of its .cu file plus the
-    shared device headers, so that counters taken on an unchanged kernel stay
-    valid while other code in the file changes."""
+    """Hash of the source of one kernel's section of its .cu file, the strip
+    helpers and the part of internal.h the kernel depends on (up to its launch
+    declaration), so that counters taken on an unchanged kernel stay valid while
+    other code changes."""
     csrc = os.path.join(ROOT, "paper_2304_01772_gb300", "csrc")
-    fname, a, b = KERNEL_SECTIONS.get(kernel, ("sweep_ising.cu", "", ""))
+    fname, a, b, hdr_end = KERNEL_SECTIONS.get(kernel, ("sweep_ising.cu", "", "", ""))
     text = open(os.path.join(csrc, fname)).read()
     if a and a in text and b in text:
         text = text[text.index(a):text.index(b)]
+    hdr = open(os.path.join(csrc, "internal.h")).read()
+    if hdr_end and hdr_end in hdr:
+        hdr = hdr[:hdr.index(hdr_end)]
     h = hashlib.sha256(text.encode())
-    for hdr in ("internal.h", "strip.cuh"):
-        h.update(open(os.path.join(csrc, hdr), "rb").read())
+    h.update(hdr.encode())
+    h.update(open(os.path.join(csrc, "strip.cuh"), "rb").read())
     return h.hexdigest()[:16]
 
 
