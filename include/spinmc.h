@@ -191,7 +191,10 @@ int spin_autotune(spin_ctx *ctx, int32_t sweeps_per_trial, void *stream);
 /* Current launch form as (mode, use_graph, tile_rows, threads). */
 int spin_get_launch(const spin_ctx *ctx, int32_t out[4]);
 
-/* Copy the spins between the context's device state and host memory. */
+/* Copy the spins between the context's device state and host memory (the
+ * span of all lattices, element type of the model).  A load also recomputes
+ * the running statistics (and, for CPM, the cell areas) from the loaded
+ * state, so records taken after it describe the new chain.               */
 int spin_load_spins(spin_ctx *ctx, const void *host, void *stream);
 int spin_store_spins(spin_ctx *ctx, void *host, void *stream);
 

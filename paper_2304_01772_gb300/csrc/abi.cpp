@@ -1077,11 +1077,19 @@ int spin_get_launch(const spin_ctx *ctx, int32_t out[4]) {
 int spin_load_spins(spin_ctx *ctx, const void *host, void *stream) {
     if (!ctx || !host) return SPIN_EINVAL;
     char *base = static_cast<char *>(ctx->spins);
+    cudaStream_t s = S(stream);
     if (ctx->model == SPIN_CPM) {
-        CK(cudaMemcpyAsync(base, host, (size_t)ctx->lat[0].L * ctx->lat[0].L * 4, cudaMemcpyHostToDevice, S(stream)));
-        return SPIN_OK;
+        CK(cudaMemcpyAsync(base, host, (size_t)ctx->lat[0].L * ctx->lat[0].L * 4, cudaMemcpyHostToDevice, s));
+        // the areas and the running statistics follow the loaded state
+        const size_t vb = sizeof(int32_t) * (ctx->n_cells + 1);
+        CK(cudaMemsetAsync(ctx->d_vol[0], 0, vb, s));
+        CK(launch_cpm_volumes(static_cast<int32_t *>(ctx->spins), ctx->lat[0].L, ctx->d_vol[0], ctx->n_cells, s));
+        CK(cudaMemcpyAsync(ctx->d_vol[1], ctx->d_vol[0], vb, cudaMemcpyDeviceToDevice, s));
+    } else {
+        CK(cudaMemcpyAsync(base, host, ctx->span_elems * ctx->elem, cudaMemcpyHostToDevice, s));
     }
-    CK(cudaMemcpyAsync(base, host, ctx->span_elems * ctx->elem, cudaMemcpyHostToDevice, S(stream)));
+    CK(launch_stats_from_state(ctx->spins, ctx->model, ctx->d_lats, ctx->n_lat, ctx->maxL, ctx->width, ctx->d_type,
+                               ctx->n_types, ctx->d_vol[0], ctx->n_cells, ctx->target, ctx->st.cur, s));
     return SPIN_OK;
 }
 

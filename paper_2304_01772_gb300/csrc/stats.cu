@@ -39,6 +39,33 @@ __global__ void stats_state_kernel(const void *spins, int model, const LatDev *l
     for (int k = threadIdx.x; k < 256; k += blockDim.x) shist[k] = 0;
     __syncthreads();
     long long a0 = 0, a1 = 0;
+    if (model == 0 && ld.fast && ld.geom == 0) {
+        // +-1 bytes (0x01 / 0xFF): bit 7 marks -1, and bit 7 of a ^ b marks a
+        // neighbour pair of opposite spins.  16 sites per thread: M = N - 2 n_down,
+        // B = 2N - 2 n_unequal (right and down bonds).
+        const uint4 *S4 = reinterpret_cast<const uint4 *>(static_cast<const int8_t *>(spins) + ld.offset);
+        const int Lv = L >> 4;
+        long long down = 0, uneq = 0;
+        for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < L * Lv; v += gridDim.x * blockDim.x) {
+            const int y = v / Lv, j = v - y * Lv;
+            const uint4 C = S4[v];
+            const uint4 D = S4[(y == L - 1 ? 0 : y + 1) * Lv + j];
+            const uint32_t nx = reinterpret_cast<const uint32_t *>(S4 + y * Lv + (j == Lv - 1 ? 0 : j + 1))[0];
+            const uint32_t w[5] = {C.x, C.y, C.z, C.w, nx};
+            const uint32_t d[4] = {D.x, D.y, D.z, D.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t r = __funnelshift_r(w[q], w[q + 1], 8);   // right neighbours
+                down += __popc(w[q] & 0x80808080u);
+                uneq += __popc((w[q] ^ r) & 0x80808080u) + __popc((w[q] ^ d[q]) & 0x80808080u);
+            }
+        }
+        const long long n_site = 16ll * ((L * Lv - 1 - (blockIdx.x * blockDim.x + threadIdx.x)) /
+                                         (gridDim.x * blockDim.x) + 1);
+        const bool any = (int)(blockIdx.x * blockDim.x + threadIdx.x) < L * Lv;
+        a0 = any ? n_site - 2 * down : 0;
+        a1 = any ? 2 * n_site - 2 * uneq : 0;
+    } else
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L * L; i += gridDim.x * blockDim.x) {
         const int y = i / L, x = i - y * L;
         const int ir = y * L + (x == L - 1 ? 0 : x + 1);

@@ -432,3 +432,40 @@ def test_triangular_lattices_next_to_square_ones(mode, graph):
         ref = run(s, d["beta"], d["J"], d["h"], SEED, i, 0, 5)
         assert np.array_equal(lattice_np(sim, i), s), (i, d)
         assert np.array_equal(st[:, i, :], ref), (i, d)
+
+
+def test_load_recomputes_the_running_statistics():
+    """spin_load_spins recounts the statistics of the loaded state: storing and
+    loading back reproduces the sweeps' bookkeeping exactly (this pins the
+    byte-parallel recount of the vectorisable lattices), and after loading an
+    unrelated state the records follow the oracle chain from that state."""
+    lats = wl.uneven512(n=48, seed=4) + [dict(L=10, beta=0.3, J=1.0, h=0.05),
+                                         dict(L=48, beta=0.3, J=1.0, h=0.0, geometry=1)]
+    sim = make_ising(lats, max_record=8)
+    sim.sweep(5, record=True)
+    torch.cuda.synchronize()
+    kept = sim.current_stats().clone()
+    span = int(sim.spins.numel())
+    host = torch.zeros(span, dtype=torch.int8).pin_memory()
+    sim.store_spins(host)
+    sim.load_spins(host)
+    torch.cuda.synchronize()
+    assert torch.equal(sim.current_stats(), kept)
+    rng = np.random.default_rng(3)
+    new = torch.from_numpy(rng.choice(np.array([-1, 1], dtype=np.int8), size=span)).pin_memory()
+    sim.load_spins(new)
+    torch.cuda.synchronize()
+    cur = sim.current_stats().cpu().numpy()
+    pick = [0, 17, 47, len(lats) - 2, len(lats) - 1]
+    init = {i: lattice_np(sim, i) for i in pick}
+    for i in pick:
+        stats = oracle.tri_stats if lats[i].get("geometry") else oracle.ising_stats
+        assert np.array_equal(cur[i], stats(init[i])), i
+    first = sim.n_records
+    sim.sweep(2, record=True)
+    st = sim.observables_host(first, 2)[0]
+    for i in pick:
+        d = lats[i]
+        run = oracle.tri_run if d.get("geometry") else oracle.ising_run
+        ref = run(init[i], d["beta"], d["J"], d["h"], SEED, i, 5, 2)
+        assert np.array_equal(st[:, i, :], ref), i
