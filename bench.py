@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=6)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plain-steps", type=int, default=20)
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=24)
     ap.add_argument("--cpu-sweeps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
@@ -507,26 +507,43 @@ def run_ours(args):
     span = sim.spins.numel()
     host_in = torch.empty(span, dtype=torch.int8, pin_memory=True)
     host_in.copy_(sim.spins.cpu())
-    host_out = [torch.empty(span, dtype=torch.int8, pin_memory=True) for _ in range(2)]
-    sims = [sim, sm.Sim(sm.SPIN_ISING, lats, seed=rank_seed(SEED, rank) + 7919, max_record=4)]
-    sims[1].set_launch(launch["mode"], True, launch["tile_rows"] or -1, launch["threads"])
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    d_stats = [torch.empty((1, len(lats), sim.width), dtype=torch.int64, device="cuda") for _ in range(2)]
-    h_stats = [torch.empty((1, len(lats), sim.width), dtype=torch.int64, pin_memory=True) for _ in range(2)]
+    NB = 3   # contexts in flight
+    host_out = [torch.empty(span, dtype=torch.int8, pin_memory=True) for _ in range(NB)]
+    sims = [sim] + [sm.Sim(sm.SPIN_ISING, lats, seed=rank_seed(SEED, rank) + 7919 * b, max_record=4)
+                    for b in range(1, NB)]
+    for x in sims[1:]:
+        x.set_launch(launch["mode"], True, launch["tile_rows"] or -1, launch["threads"])
+    streams = [torch.cuda.Stream() for _ in range(NB)]
+    d_stats = [torch.empty((1, len(lats), sim.width), dtype=torch.int64, device="cuda") for _ in range(NB)]
+    h_stats = [torch.empty((1, len(lats), sim.width), dtype=torch.int64, pin_memory=True) for _ in range(NB)]
+
+    # NB contexts round robin; copies in each direction run first in, first out across
+    # the streams (an upload waits for the previous upload, a download for the previous
+    # download), so step k's upload overlaps step k-1's download instead of sharing
+    # bandwidth with another upload, and a stream's next upload does not wait for its
+    # own download of NB steps ago
+    ev_up = [torch.cuda.Event() for _ in range(NB)]
+    ev_down = [torch.cuda.Event() for _ in range(NB)]
 
     def e2e_step(k):
-        x, st = sims[k % 2], streams[k % 2]
+        x, st = sims[k % NB], streams[k % NB]
         sp = ctypes.c_void_p(st.cuda_stream)
+        if k > 0:
+            st.wait_event(ev_up[(k - 1) % NB])
         sm._check(L.spin_load_spins(x.ctx, host_in.data_ptr(), sp), x.ctx, "load")
+        ev_up[k % NB].record(st)
         sm._check(L.spin_sweep(x.ctx, 1, 1, sp), x.ctx, "sweep")
-        sm._check(L.spin_store_spins(x.ctx, host_out[k % 2].data_ptr(), sp), x.ctx, "store")
-        sm._check(L.spin_observables(x.ctx, ctypes.c_int64(x.n_records - 1), 1, d_stats[k % 2].data_ptr(),
+        if k > 0:
+            st.wait_event(ev_down[(k - 1) % NB])
+        sm._check(L.spin_store_spins(x.ctx, host_out[k % NB].data_ptr(), sp), x.ctx, "store")
+        ev_down[k % NB].record(st)
+        sm._check(L.spin_observables(x.ctx, ctypes.c_int64(x.n_records - 1), 1, d_stats[k % NB].data_ptr(),
                                      None, None, sp), x.ctx, "obs")
         with torch.cuda.stream(st):
-            h_stats[k % 2].copy_(d_stats[k % 2], non_blocking=True)
+            h_stats[k % NB].copy_(d_stats[k % NB], non_blocking=True)
 
-    e2e_step(0)
-    e2e_step(1)
+    for k in range(NB):
+        e2e_step(k)
     barrier(dist)
     t0 = time.perf_counter()
     for k in range(args.e2e_steps):
@@ -586,7 +603,8 @@ def run_ours(args):
                      "peak_source": f"{peak_kind} hbm_gbs (copy)", "kernels": kernels},
         "e2e": {"value": sites * args.e2e_steps * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": span, "d2h_bytes_per_step": span + st_host.numel() * 8,
-                "pipeline": "two contexts on two streams, upload of step k+1 overlaps step k"},
+                "pipeline": "three contexts on three streams; uploads and downloads each first in, first "
+                            "out, so the upload of step k+1 overlaps the download of step k"},
         "gpu_launches": launches,
         "clocks": clk,
     }
