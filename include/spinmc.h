@@ -355,6 +355,17 @@ int spin_dmc_energy(int32_t n_lattices, int32_t L, float h, const float *J, cons
 /* Quantised spin-value step: s <- clip(s - eta sign(grad), -1, 1), sign(0) = 0,
  * over n spins.                                                             */
 int spin_dmc_spin_step(int64_t n, float *spins, const float *grad, float eta, void *stream);
+/* One spin-value iteration of the differentiable Monte Carlo in a single
+ * launch, identical in result to: copy s, spin_dmc_forward on the copy,
+ * spin_dmc_energy (gradient) of the relaxed copy, spin_dmc_backward to
+ * dE(F(s))/ds, spin_dmc_spin_step(eta) and spin_dmc_discretize on s.  spins:
+ * +-1 in, the updated discretised spins out; energy[l] (float64): the energy
+ * of the discretised relaxed state.  1 <= n_sweeps <=
+ * spin_dmc_spin_iter_max_sweeps(L).                                         */
+int spin_dmc_spin_iter(uint64_t seed, int32_t n_lattices, int32_t L, float beta, float h, float alpha, float eta,
+                       uint32_t first_sweep, int32_t n_sweeps, const float *J, float *spins, double *energy,
+                       void *stream);
+int32_t spin_dmc_spin_iter_max_sweeps(int32_t L);
 /* Largest n_sweeps spin_dmc_step accepts for side L (its tape stays in
  * shared memory); SPIN_EINVAL for an invalid L.                             */
 int32_t spin_dmc_step_max_sweeps(int32_t L);

@@ -86,6 +86,9 @@ _SIGS = {
     "spin_dmc_loss": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp, _vp]),
     "spin_dmc_discretize": (_i32, [ctypes.c_int64, _vp, _vp]),
     "spin_dmc_step_max_sweeps": (_i32, [_i32]),
+    "spin_dmc_spin_iter": (_i32, [ctypes.c_uint64, _i32, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                  ctypes.c_float, ctypes.c_uint32, _i32, _vp, _vp, _vp, _vp]),
+    "spin_dmc_spin_iter_max_sweeps": (_i32, [_i32]),
     "spin_dmc_energy": (_i32, [_i32, _i32, ctypes.c_float, _vp, _vp, _vp, _vp, _vp]),
     "spin_dmc_spin_step": (_i32, [ctypes.c_int64, _vp, _vp, ctypes.c_float, _vp]),
     "spin_dmc_step": (_i32, [ctypes.c_uint64, _i32, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -517,4 +520,16 @@ class CPMBatch:
                                         _ptr(self.workspace), _stream(stream)), None, "spin_cpm_batch_run")
         self.step += int(n_steps)
         return stats
+
+
+def dmc_spin_iter(seed, J, spins, energy, beta, h, alpha, eta, first_sweep, n_sweeps, stream=None):
+    """One fused spin-value iteration of the differentiable Monte Carlo."""
+    B, L = spins.shape[0], spins.shape[-1]
+    _check(lib().spin_dmc_spin_iter(int(seed), B, L, float(beta), float(h), float(alpha), float(eta),
+                                    int(first_sweep), int(n_sweeps), _ptr(J), _ptr(spins), _ptr(energy),
+                                    _stream(stream)), None, "spin_dmc_spin_iter")
+
+
+def dmc_spin_iter_max_sweeps(L):
+    return int(lib().spin_dmc_spin_iter_max_sweeps(int(L)))
 

@@ -1454,6 +1454,26 @@ int spin_dmc_spin_step(int64_t n, float *spins, const float *grad, float eta, vo
     return launch_dmc_spin_step(n, spins, grad, eta, S(stream)) == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
 }
 
+int32_t spin_dmc_spin_iter_max_sweeps(int32_t L) {
+    if (!dmc_geom_ok(1, L, 1)) return SPIN_EINVAL;
+    const size_t budget = 226 * 1024;
+    int32_t k = 0;
+    while (dmc_spin_iter_smem(L, k + 1) <= budget && k < 4096) ++k;
+    return k;
+}
+
+int spin_dmc_spin_iter(uint64_t seed, int32_t n_lattices, int32_t L, float beta, float h, float alpha, float eta,
+                       uint32_t first_sweep, int32_t n_sweeps, const float *J, float *spins, double *energy,
+                       void *stream) {
+    if (!dmc_geom_ok(n_lattices, L, n_sweeps) || !dmc_params_ok(beta, h, alpha) || !std::isfinite(eta))
+        return SPIN_EINVAL;
+    if (n_sweeps > spin_dmc_spin_iter_max_sweeps(L) || !aligned16(J) || !aligned16(spins) || !energy)
+        return SPIN_EINVAL;
+    DmcSpinIterArgs a{n_lattices, L, n_sweeps, first_sweep, beta, h, alpha, eta, (uint32_t)seed,
+                      (uint32_t)(seed >> 32), spins, J, energy};
+    return launch_dmc_spin_iter(a, S(stream)) == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
+}
+
 int spin_dmc_discretize(int64_t n, float *spins, void *stream) {
     if (n < 0 || (n > 0 && !spins)) return SPIN_EINVAL;
     if (n == 0) return SPIN_OK;

@@ -93,6 +93,7 @@ __device__ __forceinline__ void dmc_forward_substep(const DmcGeom &g, float *s, 
 // floats of scratch; it may be the sub-step's own tape slot (each thread reads
 // its four old values before it writes their four w).  Ends with a block
 // barrier.
+template <bool GJ = true>
 __device__ __forceinline__ void dmc_backward_substep(const DmcGeom &g, float *s, float *gs, const float *Jr,
                                                      const float *Jd, float *gJr, float *gJd, float *w,
                                                      const float *tape, int lat, uint32_t sweep, int c,
@@ -131,10 +132,12 @@ __device__ __forceinline__ void dmc_backward_substep(const DmcGeom &g, float *s,
         const float wl = w[iL >> 1], wr = w[iR >> 1], wu = w[iU >> 1], wd = w[iD >> 1];
         const float sj = s[j];
         gs[j] += wr * Jr[j] + wl * Jr[iL] + wd * Jd[j] + wu * Jd[iU];
-        gJr[j] += wr * sj;
-        gJr[iL] += wl * sj;
-        gJd[j] += wd * sj;
-        gJd[iU] += wu * sj;
+        if (GJ) {
+            gJr[j] += wr * sj;
+            gJr[iL] += wl * sj;
+            gJd[j] += wd * sj;
+            gJd[iU] += wu * sj;
+        }
     }
     __syncthreads();
 }
@@ -273,6 +276,65 @@ __global__ void __launch_bounds__(kDmcStepThreads, 2) dmc_step_kernel(DmcStepArg
     }
 }
 
+// One iteration of the spin-value optimisation by differentiable Monte Carlo
+// per lattice, in shared memory: relaxed sweeps F from the spins s, the energy
+// gradient of F(s), the reverse pass to dE(F(s))/ds (no coupling gradients),
+// then s <- discretise(clip(s - eta sign(.), -1, 1)); energy[lat] = E of
+// discretise(F(s)), the state the simulation produced.
+__global__ void __launch_bounds__(kDmcStepThreads, 2) dmc_spin_iter_kernel(DmcSpinIterArgs a) {
+    extern __shared__ __align__(16) float sm[];
+    __shared__ double red[kDmcStepThreads / 32];
+    const DmcGeom g{a.L, a.L / 2, a.L * a.L};
+    float *s0 = sm, *s = sm + g.N, *gs = sm + 2 * g.N, *Jr = sm + 3 * g.N, *Jd = sm + 4 * g.N;
+    float *tape = sm + 5 * g.N;   // 2 n_sweeps x N / 2; the reverse pass reuses each slot for its w
+    const int n_sub = 2 * a.n_sweeps;
+    for (int lat = blockIdx.x; lat < a.n_lat; lat += gridDim.x) {
+        float *spins = a.spins + (size_t)lat * g.N;
+        const float *J = a.J + (size_t)lat * 2 * g.N;
+        load_f4(s0, spins, g.N);
+        load_f4(s, spins, g.N);
+        load_f4(Jr, J, g.N);
+        load_f4(Jd, J + g.N, g.N);
+        __syncthreads();
+        for (int sub = 0; sub < n_sub; ++sub)
+            dmc_forward_substep(g, s, Jr, Jd, tape + (size_t)sub * (g.N / 2), lat,
+                                a.first_sweep + (uint32_t)(sub >> 1), sub & 1, a.beta, a.h, a.alpha, a.k0, a.k1);
+        // dE/ds of the relaxed state, and the energy of its discretisation
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < g.N; i += blockDim.x) {
+            const int y = i / g.L, x = i - y * g.L;
+            gs[i] = -(dmc_field(g, s, Jr, Jd, i, x, y) + a.h);
+            const int xr = x == g.L - 1 ? 0 : x + 1, yd = y == g.L - 1 ? 0 : y + 1;
+            const double di = s[i] < 0.0f ? -1.0 : 1.0;
+            const double dr = s[y * g.L + xr] < 0.0f ? -1.0 : 1.0, dd = s[yd * g.L + x] < 0.0f ? -1.0 : 1.0;
+            acc -= (double)Jr[i] * di * dr + (double)Jd[i] * di * dd + (double)a.h * di;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < kDmcStepThreads / 32; ++k) t += red[k];
+            a.energy[lat] = t;
+        }
+        for (int sub = n_sub - 1; sub >= 0; --sub) {
+            float *slot = tape + (size_t)sub * (g.N / 2);
+            dmc_backward_substep<false>(g, s, gs, Jr, Jd, nullptr, nullptr, slot, slot, lat,
+                                        a.first_sweep + (uint32_t)(sub >> 1), sub & 1, a.beta, a.h, a.alpha,
+                                        a.k0, a.k1);
+        }
+        // quantised step on the start spins, then discretisation
+        for (int i = threadIdx.x; i < g.N; i += blockDim.x) {
+            const float gi = gs[i];
+            const float v = s0[i] - a.eta * (gi > 0.0f ? 1.0f : (gi < 0.0f ? -1.0f : 0.0f));
+            const float c = fminf(1.0f, fmaxf(-1.0f, v));
+            spins[i] = c < 0.0f ? -1.0f : 1.0f;
+        }
+        __syncthreads();
+    }
+}
+
 // loss[lat] = sum (target - s)^2 (double); grad = -2 (target - s).
 __global__ void __launch_bounds__(kDmcThreads) dmc_loss_kernel(int n_lat, int N, const float *spins,
                                                                const float *target, float *grad,
@@ -377,6 +439,19 @@ cudaError_t launch_dmc_step(const DmcStepArgs &a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(dmc_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e) return e;
     dmc_step_kernel<<<dmc_grid(a.n_lat, 2), kDmcStepThreads, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+size_t dmc_spin_iter_smem(int L, int n_sweeps) {
+    const size_t N = (size_t)L * L;
+    return sizeof(float) * (5 * N + (size_t)n_sweeps * N);
+}
+
+cudaError_t launch_dmc_spin_iter(const DmcSpinIterArgs &a, cudaStream_t s) {
+    const size_t sm = dmc_spin_iter_smem(a.L, a.n_sweeps);
+    cudaError_t e = cudaFuncSetAttribute(dmc_spin_iter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e) return e;
+    dmc_spin_iter_kernel<<<dmc_grid(a.n_lat, 2), kDmcStepThreads, sm, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -316,6 +316,18 @@ struct DmcStepArgs {
     float lr, b1, b2, eps, c1, c2;
 };
 size_t dmc_step_smem(int L, int n_sweeps);
+// Fused spin-value iteration of the differentiable Monte Carlo (see dmc.cu).
+struct DmcSpinIterArgs {
+    int n_lat, L, n_sweeps;
+    uint32_t first_sweep;
+    float beta, h, alpha, eta;
+    uint32_t k0, k1;
+    float *spins;          // in: +-1 spins; out: the updated, discretised spins
+    const float *J;        // [n_lat][2][L*L]
+    double *energy;        // [n_lat]: energy of the discretised relaxed state
+};
+size_t dmc_spin_iter_smem(int L, int n_sweeps);
+cudaError_t launch_dmc_spin_iter(const DmcSpinIterArgs &a, cudaStream_t s);
 
 // Batched cellular Potts: many independent lattices of one side L, each held
 // by one thread block for all sub-steps of the call.

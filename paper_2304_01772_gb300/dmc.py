@@ -14,8 +14,8 @@ from __future__ import annotations
 
 import torch
 
-from . import (adam, dmc_backward, dmc_discretize, dmc_energy, dmc_forward, dmc_loss, dmc_spin_step, dmc_step,
-               dmc_step_max_sweeps, dmc_tape_floats)
+from . import (adam, dmc_backward, dmc_discretize, dmc_energy, dmc_forward, dmc_loss, dmc_spin_iter,
+               dmc_spin_iter_max_sweeps, dmc_spin_step, dmc_step, dmc_step_max_sweeps, dmc_tape_floats)
 
 
 class PatternOptimizer:
@@ -115,7 +115,15 @@ class SpinOptimizer:
             rows.append(self.energy.clone())
         return self._trace(rows)
 
-    def dmc(self, steps, beta, alpha, eta=2.0, sweeps=1, stream=None):
+    def dmc(self, steps, beta, alpha, eta=2.0, sweeps=1, stream=None, fused=True):
+        if fused and sweeps <= dmc_spin_iter_max_sweeps(self.L):
+            rows = []
+            for _ in range(steps):
+                dmc_spin_iter(self.seed, self.J, self.spins, self.energy, beta, self.h, alpha, eta, self.sweep,
+                              sweeps, stream)
+                self.sweep += sweeps
+                rows.append(self.energy.clone())
+            return self._trace(rows)
         tape = torch.empty(dmc_tape_floats(self.B, self.L, sweeps), dtype=torch.float32, device=self.spins.device)
         relaxed = torch.empty_like(self.spins)
         gJ = torch.empty_like(self.J)

@@ -196,3 +196,17 @@ def test_spin_value_optimisation_three_methods():
     assert e_mc < -1.3
     assert e_dm < e_gd - 0.1
     assert e_gd < -0.8
+
+
+@pytest.mark.parametrize("L,K", [(64, 1), (32, 3)])
+def test_fused_spin_iteration_equals_the_separate_calls(L, K):
+    B = 4
+    rng = np.random.default_rng(L * K)
+    J = torch.from_numpy(rng.choice([-1.0, 1.0], size=(B, 2, L, L)).astype(np.float32)).cuda()
+    s0 = torch.from_numpy(rng.choice([-1.0, 1.0], size=(B, L, L)).astype(np.float32)).cuda()
+    a = pdmc.SpinOptimizer(J, s0, seed=5)
+    b = pdmc.SpinOptimizer(J, s0, seed=5)
+    ea = a.dmc(4, beta=2.0, alpha=10.0, sweeps=K, fused=True)
+    eb = b.dmc(4, beta=2.0, alpha=10.0, sweeps=K, fused=False)
+    assert torch.equal(a.spins, b.spins)
+    np.testing.assert_array_equal(ea, eb)
