@@ -169,6 +169,20 @@ int spin_num_grad(const spin_ctx *ctx);
 int spin_expectations(spin_ctx *ctx, int64_t first, int32_t n, int32_t pool, double *out,
                       void *stream);
 
+/* Exchange step of the gradient when the chains that share theta are spread
+ * over several processes (one per GPU): each process pools the exact integer
+ * moments of its lattices over records [first, first + n) into limbs
+ * [n_mom][4] (int64, device): the int128 value l0 + l1 2^32 + l2 2^64 + l3 2^96
+ * with l0..l2 in [0, 2^32) and l3 signed, so that an element-wise SUM over
+ * processes (an all-reduce) stays exact.  spin_grad_from_limbs turns summed
+ * limbs into the pooled gradient (spin_num_grad doubles) and/or the pooled
+ * expectations (2 doubles), as spin_grad / spin_expectations with pool != 0
+ * would over all processes' samples; theta (and, for the estimator's
+ * prefactors, N and beta) is taken from lattice 0 of ctx.  Device pointers. */
+int spin_pooled_limbs(spin_ctx *ctx, int64_t first, int32_t n, int64_t *limbs, void *stream);
+int spin_grad_from_limbs(spin_ctx *ctx, const int64_t *limbs, int32_t observable, double *grad, double *expect,
+                         void *stream);
+
 /* Replace temperatures/couplings (L, q and offsets must not change) and
  * rebuild the acceptance tables; takes effect at the next sweep. */
 int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_params *cpm);

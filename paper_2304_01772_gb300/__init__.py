@@ -98,6 +98,8 @@ _SIGS = {
     "spin_cpm_batch_init": (_i32, [ctypes.c_uint64, _i32, _i32, ctypes.POINTER(CpmParams), _vp, _vp, _vp, _vp]),
     "spin_cpm_batch_run": (_i32, [ctypes.c_uint64, _i32, _i32, ctypes.POINTER(CpmParams), _vp, _vp, _vp,
                                   ctypes.c_uint32, _i32, _vp, _vp, _vp]),
+    "spin_pooled_limbs": (_i32, [_vp, ctypes.c_int64, _i32, _vp, _vp]),
+    "spin_grad_from_limbs": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp]),
     "spin_mlp_param_count": (_i32, []),
     "spin_mlp_forward": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp]),
     "spin_mlp_backward": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
@@ -306,6 +308,26 @@ class Sim:
         _check(lib().spin_grad(self.ctx, int(first), int(n), int(observable), 1 if pool else 0, _ptr(out),
                                _stream(stream)), self.ctx, "spin_grad")
         return out
+
+    def pooled_limbs(self, first=0, n=None, stream=None):
+        """[n_mom, 4] int64 device tensor: this context's pooled moments as limbs
+        whose element-wise sum over processes is exact (see spin_pooled_limbs)."""
+        import torch
+        if n is None:
+            n = self.n_records - first
+        out = torch.empty((lib().spin_num_moments(self.ctx), 4), dtype=torch.int64, device="cuda")
+        _check(lib().spin_pooled_limbs(self.ctx, int(first), int(n), _ptr(out), _stream(stream)), self.ctx,
+               "spin_pooled_limbs")
+        return out
+
+    def grad_from_limbs(self, limbs, observable=0, stream=None):
+        """(pooled gradient [1, n_grad], pooled expectations [1, 2]) from summed limbs."""
+        import torch
+        g = torch.empty((1, lib().spin_num_grad(self.ctx)), dtype=torch.float64, device="cuda")
+        e = torch.empty((1, 2), dtype=torch.float64, device="cuda")
+        _check(lib().spin_grad_from_limbs(self.ctx, _ptr(limbs.contiguous()), int(observable), _ptr(g), _ptr(e),
+                                          _stream(stream)), self.ctx, "spin_grad_from_limbs")
+        return g, e
 
     def expectations(self, first=0, n=None, pool=False, stream=None):
         """[rows, 2] float64 on the device: (<E>/N, <M>/N) per lattice or pooled."""

@@ -30,6 +30,8 @@ cudaError_t launch_moments_i128(const StatsBufs &st, int64_t first, int n, void 
                                 cudaStream_t s);
 cudaError_t launch_pool_moments(const void *in, int n_lat, int n_mom, void *out, cudaStream_t s);
 cudaError_t launch_i128_to_i64(const void *in, int64_t *out, int n, int *overflow, cudaStream_t s);
+cudaError_t launch_i128_to_limbs(const void *in, int n, int64_t *limbs, cudaStream_t s);
+cudaError_t launch_limbs_to_i128(const int64_t *limbs, int n, void *out, cudaStream_t s);
 cudaError_t launch_grad_i128(const void *moments, int rows, GradParams p, double *out,
                              cudaStream_t s);
 cudaError_t launch_expectations_i128(const void *moments, int rows, GradParams p, double *out,
@@ -975,6 +977,46 @@ int spin_grad(spin_ctx *ctx, int64_t first, int32_t n, int32_t observable, int32
         CK(cudaMemcpyAsync(out, t, sizeof(double) * rows * ng, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
     }
+    return SPIN_OK;
+}
+
+int spin_pooled_limbs(spin_ctx *ctx, int64_t first, int32_t n, int64_t *limbs, void *stream) {
+    if (!ctx || !limbs) return SPIN_EINVAL;
+    if (ctx->model == SPIN_POTTS) return fail(ctx, SPIN_EINVAL, "no gradient for the Potts model");
+    int rc = check_records(ctx, first, n);
+    if (rc) return rc;
+    if (n < 1) return fail(ctx, SPIN_EINVAL, "need at least one record");
+    if (!is_device_ptr(limbs)) return fail(ctx, SPIN_EINVAL, "limbs must be device memory");
+    cudaStream_t s = S(stream);
+    const int nm = spin_num_moments(ctx);
+    const size_t cnt = (size_t)nm * ctx->n_lat;
+    rc = ensure_scratch(ctx, 16 * cnt + 16 * (size_t)nm + 64);
+    if (rc) return rc;
+    char *base = static_cast<char *>(ctx->d_scratch);
+    CK(launch_moments_i128(ctx->st, first, n, base, s));
+    CK(launch_pool_moments(base, ctx->n_lat, nm, base + 16 * cnt, s));
+    CK(launch_i128_to_limbs(base + 16 * cnt, nm, limbs, s));
+    return SPIN_OK;
+}
+
+int spin_grad_from_limbs(spin_ctx *ctx, const int64_t *limbs, int32_t observable, double *grad, double *expect,
+                         void *stream) {
+    if (!ctx || !limbs || (!grad && !expect)) return SPIN_EINVAL;
+    if (ctx->model == SPIN_POTTS) return fail(ctx, SPIN_EINVAL, "no gradient for the Potts model");
+    if (ctx->model == SPIN_ISING && (observable < 0 || observable > 1))
+        return fail(ctx, SPIN_EINVAL, "Ising observable must be 0 (E/N) or 1 (M/N)");
+    if (ctx->model == SPIN_CPM && observable != 0) return fail(ctx, SPIN_EINVAL, "CPM observable must be 0");
+    if (!is_device_ptr(limbs) || (grad && !is_device_ptr(grad)) || (expect && !is_device_ptr(expect)))
+        return fail(ctx, SPIN_EINVAL, "limbs and outputs must be device memory");
+    cudaStream_t s = S(stream);
+    const int nm = spin_num_moments(ctx);
+    int rc = ensure_scratch(ctx, 16 * (size_t)nm + 64);
+    if (rc) return rc;
+    CK(launch_limbs_to_i128(limbs, nm, ctx->d_scratch, s));
+    GradParams p{ctx->model, ctx->n_lat, ctx->width, observable, 1, ctx->d_latp, ctx->d_cpmJ, (double)ctx->lambda,
+                 (double)ctx->T, ctx->width - 2};
+    if (grad) CK(launch_grad_i128(ctx->d_scratch, 1, p, grad, s));
+    if (expect) CK(launch_expectations_i128(ctx->d_scratch, 1, p, expect, s));
     return SPIN_OK;
 }
 

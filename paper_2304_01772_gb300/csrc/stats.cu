@@ -237,6 +237,31 @@ __global__ void pool_moments_kernel(const __int128 *in, int n_lat, int n_mom, __
     }
 }
 
+// Pooled int128 moments <-> four 32-bit limbs held in int64 words,
+// v = l0 + l1 2^32 + l2 2^64 + l3 2^96 with l0..l2 in [0, 2^32) and l3
+// signed, so that an element-wise integer sum over ranks stays exact; the
+// recombination accepts any int64 limbs (the carries of such a sum).
+__global__ void i128_to_limbs_kernel(const __int128 *in, int n, int64_t *limbs) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const __int128 v = in[k];
+        const unsigned __int128 u = (unsigned __int128)v;
+        limbs[4 * k] = (int64_t)(uint32_t)(u & 0xFFFFFFFFu);
+        limbs[4 * k + 1] = (int64_t)(uint32_t)((u >> 32) & 0xFFFFFFFFu);
+        limbs[4 * k + 2] = (int64_t)(uint32_t)((u >> 64) & 0xFFFFFFFFu);
+        limbs[4 * k + 3] = (int64_t)(v >> 96);
+    }
+}
+
+__global__ void limbs_to_i128_kernel(const int64_t *limbs, int n, __int128 *out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        __int128 v = (__int128)limbs[4 * k + 3];
+        v = v * ((__int128)1 << 32) + (__int128)limbs[4 * k + 2];
+        v = v * ((__int128)1 << 32) + (__int128)limbs[4 * k + 1];
+        v = v * ((__int128)1 << 32) + (__int128)limbs[4 * k];
+        out[k] = v;
+    }
+}
+
 __device__ __forceinline__ double i128_to_double(__int128 v) {
     const bool neg = v < 0;
     unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
@@ -413,6 +438,16 @@ cudaError_t launch_moments_i128(const StatsBufs &st, int64_t first, int n, void 
 cudaError_t launch_pool_moments(const void *in, int n_lat, int n_mom, void *out, cudaStream_t s) {
     pool_moments_kernel<<<1, 256, 0, s>>>(static_cast<const __int128 *>(in), n_lat, n_mom,
                                           static_cast<__int128 *>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_i128_to_limbs(const void *in, int n, int64_t *limbs, cudaStream_t s) {
+    i128_to_limbs_kernel<<<(n + 255) / 256, 256, 0, s>>>(static_cast<const __int128 *>(in), n, limbs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_limbs_to_i128(const int64_t *limbs, int n, void *out, cudaStream_t s) {
+    limbs_to_i128_kernel<<<(n + 255) / 256, 256, 0, s>>>(limbs, n, static_cast<__int128 *>(out));
     return cudaGetLastError();
 }
 

@@ -56,3 +56,48 @@ def test_two_gloo_ranks_max_time_and_distinct_seeds():
 def test_single_process_defaults():
     assert sdist.max_over_ranks(3.5, None) == 3.5
     assert sdist.job_throughput(10.0, 1, 2.0) == 5.0
+
+
+def to_limbs(v):
+    """The limb layout of spin_pooled_limbs for one int128 value (test-local)."""
+    u = v & ((1 << 128) - 1)
+    l3 = v >> 96                                  # arithmetic shift: signed top limb
+    return [u & 0xFFFFFFFF, (u >> 32) & 0xFFFFFFFF, (u >> 64) & 0xFFFFFFFF, l3]
+
+
+def from_limbs(l):
+    return l[0] + (l[1] << 32) + (l[2] << 64) + (l[3] << 96)
+
+
+VALUES = [[7, -5, 2 ** 64 + 3, -(2 ** 100) + 17], [2 ** 63 - 1, -(2 ** 63), 2 ** 70, 2 ** 100 - 1]]
+
+
+def _limb_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    limbs = torch.tensor([to_limbs(v) for v in VALUES[rank]], dtype=torch.int64)
+    sdist.allreduce_limbs(limbs, dist)
+    out[rank] = [from_limbs([int(x) for x in row]) for row in limbs.tolist()]
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_moment_limbs_sum_exactly_over_two_gloo_ranks():
+    """The gradient's exchange step: int128 moments split into 32-bit limbs
+    (int64 words) are summed element-wise by the all-reduce; recombining the
+    sum gives the exact total, carries and negative values included."""
+    for v in sum(VALUES, []):
+        assert from_limbs(to_limbs(v)) == v
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_limb_worker, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=120)
+            assert p.exitcode == 0
+        want = [a + b for a, b in zip(*VALUES)]
+        assert out[0] == want and out[1] == want

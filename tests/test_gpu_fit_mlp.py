@@ -190,3 +190,30 @@ def test_fit_reaches_target_and_surrogate_warm_start_helps():
     # the surrogate's warm start reaches the tolerance, in fewer gradient steps
     assert warm_loss < 2e-3
     assert warm_steps < cold_steps
+
+
+def test_pooled_gradient_over_two_contexts_via_limbs():
+    """The multi-GPU exchange emulated with two contexts (two ranks' chains
+    sharing theta): their limbs summed element-wise give the estimator over
+    both sample sets, as the float64 oracle computes it from the records."""
+    from oracle import estimator
+    beta, J, h, L, n = 0.42, 1.0, 0.03, 32, 300
+    sims = [sm.Sim(sm.SPIN_ISING, [dict(L=L, beta=beta, J=J, h=h)] * 16, seed=s, max_record=n) for s in (11, 12)]
+    recs = []
+    for x in sims:
+        x.sweep(50)
+        x.sweep(n, record=True)
+        recs.append(x.observables_host(0, n)[0])          # [n, lattices, 2]
+    limbs = sims[0].pooled_limbs(0, n) + sims[1].pooled_limbs(0, n)
+    g, e = sims[0].grad_from_limbs(limbs, observable=0)
+    gm, _ = sims[0].grad_from_limbs(limbs, observable=1)
+    st = np.concatenate([r.transpose(1, 0, 2) for r in recs], axis=0)   # [chains, n, 2]
+    ref = estimator.ising_grad(st, np.float32(beta), np.float32(J), np.float32(h), L * L)
+    np.testing.assert_allclose(g.cpu().numpy()[0], [ref[("E", "J")], ref[("E", "h")]], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(gm.cpu().numpy()[0], [ref[("M", "J")], ref[("M", "h")]], rtol=1e-9, atol=1e-12)
+    Ms = st[..., 0].astype(np.float64) / (L * L)
+    Es = (-float(np.float32(J)) * st[..., 1] - float(np.float32(h)) * st[..., 0]) / (L * L)
+    np.testing.assert_allclose(e.cpu().numpy()[0], [Es.mean(), Ms.mean()], rtol=1e-12)
+    # one context's limbs alone reproduce its own pooled gradient exactly
+    g0, _ = sims[0].grad_from_limbs(sims[0].pooled_limbs(0, n), observable=0)
+    assert torch.equal(g0, sims[0].grad(0, n, observable=0, pool=True))
