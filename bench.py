@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--workload", default="uneven512",
                     choices=["uneven512", "potts_q3", "potts_q8", "cpm1024", "ising_small", "grad", "mlp", "dmc",
-                             "spinglass", "cpm_batch", "triangular"])
+                             "spinglass", "cpm_batch", "triangular", "fit"])
     return ap.parse_args()
 
 
@@ -171,6 +171,14 @@ def _oracle_cpm_batch(args):
     return n * 2 * p["L"] ** 2, time.perf_counter() - t0
 
 
+def _oracle_fit_chain(i):
+    import oracle
+    s = oracle.init_ising(256, SEED, i).copy()
+    t0 = time.perf_counter()
+    oracle.ising_run(s, 0.45, 1.0, 0.0, SEED, i, 0, 100)
+    return 256 * 256 * 100, time.perf_counter() - t0
+
+
 def _oracle_tri(args):
     import oracle
     b0, n = args
@@ -218,6 +226,11 @@ def cpu_baseline_secondary(workload, cores):
         wall = time.perf_counter() - t0
         return {"value": 2 * p["L"] ** 2 / wall, "unit": "copy-attempts/s", "cores": 1, "kind": "oracle",
                 "sample": f"2 Monte Carlo steps of the 1024^2 lattice, one core (a single chain) ({wall:.1f} s)"}
+    if workload == "fit":
+        rate, units, wall = cpu_oracle_pool(_oracle_fit_chain, list(range(cores)), cores)
+        return {"value": rate, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+                "sample": f"{cores} of the 128 chains of 256^2, 100 of the 2000 sweeps of a gradient step each, "
+                          f"with per-sweep statistics ({wall:.1f} s wall)"}
     if workload == "triangular":
         import numpy as np
         per = 2
@@ -632,6 +645,8 @@ def run_secondary(args):
         return run_grad_mlp(args, cpu)
     if args.workload == "dmc":
         return run_dmc(args, cpu)
+    if args.workload == "fit":
+        return run_fit(args, cpu)
     if args.workload == "spinglass":
         return run_spinglass(args, cpu)
     if args.workload == "cpm_batch":
@@ -897,6 +912,63 @@ def run_cpm_batch(args, cpu):
                                    "lambda = 1, T = 8; all timed steps in one launch",
                        "one_launch_per_step_with_statistics_ms": ms_rec},
             "gpu_launches": 1}
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_fit(args, cpu):
+    """The differentiable fit at its stated size: 128 chains of 256^2 at beta =
+    0.45, targets <E>/N = -1.2 and <M>/N = 0.5; a gradient step = 1000 burn-in
+    + 1000 recorded sweeps, the fluctuation-estimator gradient and an Adam step.
+    value = gradient steps per second; the BF16 surrogate (trained on 10^4
+    chains of 64^2) and the steps to tolerance from the cold and the warm start
+    go in config."""
+    import torch
+    from paper_2304_01772_gb300 import fit
+    target, beta = (-1.2, 0.5), 0.45
+    ens = fit.IsingEnsemble(128, 256, beta, seed=SEED, n_burn=1000, n_meas=1000)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fit.fit(ens, target, (1.0, 0.0), lr=1e-2, max_steps=args.warmup, tol=0.0)
+    torch.cuda.synchronize()
+    e0.record()
+    fit.fit(ens, target, (1.0, 0.0), lr=1e-2, max_steps=args.steps, tol=0.0)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # per step: two sweep calls of 1000 sweeps (spin_gpu_launches counts the last call),
+    # moments + pooling + expectations, two gradients (3 kernels each), one Adam step
+    launches = args.steps * (2 * ens.sim.gpu_launches + 3 + 6 + 1)
+    # surrogate warm start
+    t0 = time.perf_counter()
+    X = torch.from_numpy(fit.sample_box(10000, seed=1)).cuda()
+    Y = fit.chain_targets(X, L=64, n_burn=300, n_meas=300)
+    torch.cuda.synchronize()
+    t_chains = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sur = fit.Surrogate(seed=3)
+    losses = sur.train(X, Y, epochs=1500, lr=3e-3)
+    theta_w = [float(v) for v in sur.invert(target, beta).cpu()]
+    t_train = time.perf_counter() - t0
+    runs = {}
+    for name, th0 in (("cold", (1.0, 0.0)), ("warm", tuple(theta_w))):
+        e = fit.IsingEnsemble(128, 256, beta, seed=SEED + 1, n_burn=1000, n_meas=1000)
+        th, steps, loss = fit.fit(e, target, th0, lr=1e-2, max_steps=40, tol=2e-3)
+        runs[name] = {"steps": steps, "final_loss": loss, "theta": [float(v) for v in th.cpu()]}
+    line = {"metric": "gradient steps/s (fit)", "value": 1e3 / ms, "unit": "gradient steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "int8 spins, int64 moments, f64 covariance", "data": "synthetic",
+            "config": {"workload": "differentiable fit: Ising 256^2, 128 chains, beta = 0.45, targets <E>/N = -1.2, "
+                                   "<M>/N = 0.5; one step = 1000 burn-in + 1000 recorded sweeps, fluctuation "
+                                   "gradient, Adam (lr 1e-2)",
+                       "site_updates_per_step": 128 * 256 * 256 * 2000,
+                       "surrogate": {"chains": "10^4 (beta, J, h) from the box, 64^2, 300 + 300 sweeps",
+                                     "chain_targets_s": t_chains, "train_1500_epochs_and_invert_s": t_train,
+                                     "loss_first_last": [float(losses[0]), float(losses[-1])],
+                                     "warm_start_theta": theta_w},
+                       "steps_to_loss_2e-3": runs},
+            "gpu_launches": launches}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
