@@ -963,6 +963,7 @@ def run_fit(args, cpu):
                                    "<M>/N = 0.5; one step = 1000 burn-in + 1000 recorded sweeps, fluctuation "
                                    "gradient, Adam (lr 1e-2)",
                        "site_updates_per_step": 128 * 256 * 256 * 2000,
+                       "launch": ens.sim.get_launch(),
                        "surrogate": {"chains": "10^4 (beta, J, h) from the box, 64^2, 300 + 300 sweeps",
                                      "chain_targets_s": t_chains, "train_1500_epochs_and_invert_s": t_train,
                                      "loss_first_last": [float(losses[0]), float(losses[-1])],

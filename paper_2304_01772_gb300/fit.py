@@ -37,11 +37,16 @@ class IsingEnsemble:
     float64 on the device.
     """
 
-    def __init__(self, n_chains, L, beta, J=1.0, h=0.0, seed=0, n_burn=200, n_meas=200):
+    def __init__(self, n_chains, L, beta, J=1.0, h=0.0, seed=0, n_burn=200, n_meas=200, tune=True):
         self.lats = [dict(L=L, beta=beta, J=J, h=h) for _ in range(n_chains)]
         self.beta = beta
         self.n_burn, self.n_meas = n_burn, n_meas
         self.sim = Sim(SPIN_ISING, self.lats, seed=seed, max_record=n_meas)
+        if tune:
+            # pick the fastest launch form on this batch (a few trial sweeps; the chain
+            # advances, but the draws depend only on the sweep index, so results do not
+            # depend on the form chosen)
+            self.sim.autotune(4)
         self.sweeps = 0
 
     def run(self, J, h):
