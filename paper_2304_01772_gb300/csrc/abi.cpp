@@ -575,8 +575,11 @@ int run_sweeps(spin_ctx *ctx, int n, int record, cudaStream_t s) {
     if (ctx->mode == 2) {
         ResidentArgs a{static_cast<int8_t *>(ctx->spins), ctx->d_lats, ctx->d_tabs, ctx->k0, ctx->k1,
                        ctx->t, n, (long long)ctx->n_rec, record, ctx->st};
-        CK(launch_ising_resident(a, ctx->n_lat, ctx->threads, (size_t)ctx->maxL * ctx->maxL,
-                                 ctx->d_state, s));
+        if (ctx->n_tri == ctx->n_lat)
+            CK(launch_ising_tri_resident(a, ctx->n_lat, (size_t)ctx->maxL * ctx->maxL, ctx->d_state, s));
+        else
+            CK(launch_ising_resident(a, ctx->n_lat, ctx->threads, (size_t)ctx->maxL * ctx->maxL,
+                                     ctx->d_state, s));
         ctx->last_launches = 2;
         return SPIN_OK;
     }
@@ -1085,7 +1088,13 @@ int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_
 }
 
 static bool resident_ok(const spin_ctx *ctx) {
-    if (ctx->model != SPIN_ISING || ctx->n_generic || ctx->n_tri) return false;
+    if (ctx->model != SPIN_ISING || ctx->n_generic) return false;
+    if (ctx->n_tri) {   // all triangular: the triangular resident kernel
+        if (ctx->n_tri != ctx->n_lat) return false;
+        for (const auto &d : ctx->lat)
+            if (d.L > 240) return false;
+        return true;
+    }
     for (const auto &d : ctx->lat)
         if (d.L > 256) return false;
     return true;
@@ -1095,7 +1104,8 @@ int spin_set_launch(spin_ctx *ctx, int32_t mode, int32_t use_graph, int32_t tile
     if (!ctx) return SPIN_EINVAL;
     if (mode < 0 || mode > 2) return fail(ctx, SPIN_EINVAL, "launch mode must be 0, 1 or 2");
     if (mode == 2 && !resident_ok(ctx))
-        return fail(ctx, SPIN_EINVAL, "resident form needs Ising lattices with L % 16 == 0 and L <= 256");
+        return fail(ctx, SPIN_EINVAL, "resident form needs Ising lattices with L % 16 == 0 and L <= 256, "
+                                      "or only triangular lattices with L <= 240");
     if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
         return fail(ctx, SPIN_EINVAL, "threads must be 128, 256 or 512");
     if (tile_rows < -1) return fail(ctx, SPIN_EINVAL, "tile_rows must be >= -1");

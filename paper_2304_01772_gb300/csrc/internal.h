@@ -136,6 +136,9 @@ struct ResidentArgs {
 };
 cudaError_t launch_ising_resident(const ResidentArgs &a, int n_lat, int threads, size_t smem,
                                   DevState *state, cudaStream_t s);
+// The same for batches made only of triangular lattices (L <= 240).
+cudaError_t launch_ising_tri_resident(const ResidentArgs &a, int n_lat, size_t smem, DevState *state,
+                                      cudaStream_t s);
 cudaError_t launch_init_random(void *spins, int model, const LatDev *lats, int n_lat, int maxL,
                                uint32_t k0, uint32_t k1, cudaStream_t s);
 

@@ -222,6 +222,84 @@ __global__ void __launch_bounds__(THREADS) ising_resident_kernel(ResidentArgs a)
     if (threadIdx.x < 2) a.st.cur[2 * lat + threadIdx.x] = cur_s[threadIdx.x];
 }
 
+// Triangular lattices (geometry 1) resident in shared memory for all sweeps
+// of a call, one block per lattice; per sweep three colour passes, each
+// thread taking one Philox group (four consecutive compressed sites of the
+// colour, k = y (L/3) + x div 3).  Records as ising_resident_kernel.
+constexpr int kTriResThreads = 512;
+
+__global__ void __launch_bounds__(kTriResThreads) ising_tri_resident_kernel(ResidentArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    int8_t *S = reinterpret_cast<int8_t *>(sm);
+    __shared__ TabEntry stab[kTabStride];
+    __shared__ int red[2 * (kTriResThreads / 32)];
+    __shared__ long long cur_s[2];
+    const int lat = blockIdx.x;
+    const LatDev ld = a.lats[lat];
+    const int L = ld.L, N = L * L, third = L / 3, nk = N / 3;
+    int8_t *G = a.spins + ld.offset;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) S[i] = G[i];
+    if (threadIdx.x < kTabStride) stab[threadIdx.x] = a.tabs[lat * kTabStride + threadIdx.x];
+    if (threadIdx.x < 2) cur_s[threadIdx.x] = a.st.cur[2 * lat + threadIdx.x];
+    __syncthreads();
+    for (int sweep = 0; sweep < a.n_sweeps; ++sweep) {
+        const uint32_t t = a.t0 + (uint32_t)sweep;
+        int acc = 0;
+        for (int c = 0; c < 3; ++c) {
+            for (int grp = threadIdx.x; 4 * grp < nk; grp += blockDim.x) {
+                const uint4 r = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)lat, t, (uint32_t)c), a.k0, a.k1);
+                const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    const int k = 4 * grp + l;
+                    if (k >= nk) break;
+                    const int y = k / third, x = 3 * (k - y * third) + (c + y) % 3;
+                    const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
+                    const int xl = x == 0 ? L - 1 : x - 1, xr = x == L - 1 ? 0 : x + 1;
+                    const int dcount = (S[y * L + xl] < 0) + (S[y * L + xr] < 0) + (S[yu * L + x] < 0) +
+                                       (S[yd * L + x] < 0) + (S[yu * L + xr] < 0) + (S[yd * L + xl] < 0);
+                    const int sv = S[y * L + x] < 0 ? -1 : 1;
+                    const TabEntry e = stab[dcount + 7 * (sv < 0 ? 1 : 0)];
+                    if (rr[l] <= e.thr) {
+                        S[y * L + x] = (int8_t)(-sv);
+                        acc += e.delta;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        int dm = (int)(int16_t)(acc & 0xFFFF);
+        int db = (acc - dm) >> 16;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dm += __shfl_xor_sync(0xFFFFFFFFu, dm, o);
+            db += __shfl_xor_sync(0xFFFFFFFFu, db, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red[2 * (threadIdx.x >> 5)] = dm;
+            red[2 * (threadIdx.x >> 5) + 1] = db;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long sm_ = 0, sb_ = 0;
+            for (int w = 0; w < kTriResThreads / 32; ++w) {
+                sm_ += red[2 * w];
+                sb_ += red[2 * w + 1];
+            }
+            cur_s[0] += sm_;
+            cur_s[1] += sb_;
+            if (a.record && a.st.cap > 0) {
+                const long long slot = (a.rec0 + sweep) % a.st.cap;
+                a.st.ring[(slot * a.st.n_lat + lat) * 2] = cur_s[0];
+                a.st.ring[(slot * a.st.n_lat + lat) * 2 + 1] = cur_s[1];
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) G[i] = S[i];
+    if (threadIdx.x < 2) a.st.cur[2 * lat + threadIdx.x] = cur_s[threadIdx.x];
+}
+
 __global__ void advance_state_kernel(DevState *state, uint32_t n, int record) {
     state->t += n;
     if (record) state->n_rec += n;
@@ -754,6 +832,17 @@ cudaError_t launch_ising_resident(const ResidentArgs &a, int n_lat, int threads,
         default:
             return cudaErrorInvalidValue;
     }
+    if ((e = cudaGetLastError())) return e;
+    advance_state_kernel<<<1, 1, 0, s>>>(state, (uint32_t)a.n_sweeps, a.record);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ising_tri_resident(const ResidentArgs &a, int n_lat, size_t smem, DevState *state,
+                                      cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(ising_tri_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    ising_tri_resident_kernel<<<n_lat, kTriResThreads, smem, s>>>(a);
     if ((e = cudaGetLastError())) return e;
     advance_state_kernel<<<1, 1, 0, s>>>(state, (uint32_t)a.n_sweeps, a.record);
     return cudaGetLastError();

@@ -469,3 +469,22 @@ def test_load_recomputes_the_running_statistics():
         run = oracle.tri_run if d.get("geometry") else oracle.ising_run
         ref = run(init[i], d["beta"], d["J"], d["h"], SEED, i, 5, 2)
         assert np.array_equal(st[:, i, :], ref), i
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_triangular_resident_form(graph):
+    """Batches of triangular lattices only may run resident in shared memory
+    (launch mode 2): the same chain, records every sweep."""
+    lats = TRI + [dict(L=192, beta=0.3, J=1.0, h=-0.02, geometry=1)]
+    sim = make_ising(lats, max_record=16)
+    sim.set_launch(2, graph, 0, 512)
+    init = {i: lattice_np(sim, i) for i in range(len(lats))}
+    sim.sweep(3, record=True)
+    sim.sweep(2, record=True)
+    st = sim.observables_host(0, 5)[0]
+    for i, d in enumerate(lats):
+        s = init[i].copy()
+        ref = oracle.tri_run(s, d["beta"], d["J"], d["h"], SEED, i, 0, 5)
+        assert np.array_equal(lattice_np(sim, i), s), i
+        assert np.array_equal(st[:, i, :], ref), i
+    assert np.array_equal(sim.current_stats().cpu().numpy()[:, :], st[-1])
