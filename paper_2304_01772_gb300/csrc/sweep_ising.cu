@@ -249,11 +249,18 @@ __global__ void __launch_bounds__(kTriResThreads) ising_tri_resident_kernel(Resi
             for (int grp = threadIdx.x; 4 * grp < nk; grp += blockDim.x) {
                 const uint4 r = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)lat, t, (uint32_t)c), a.k0, a.k1);
                 const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+                // row and colour offset once per group; a group's sites rarely cross a row
+                int y = (4 * grp) / third, m = 4 * grp - y * third, off = (c + y) % 3;
 #pragma unroll
                 for (int l = 0; l < 4; ++l) {
-                    const int k = 4 * grp + l;
-                    if (k >= nk) break;
-                    const int y = k / third, x = 3 * (k - y * third) + (c + y) % 3;
+                    if (4 * grp + l >= nk) break;
+                    if (m == third) {
+                        m = 0;
+                        ++y;
+                        off = off == 2 ? 0 : off + 1;
+                    }
+                    const int x = 3 * m + off;
+                    ++m;
                     const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
                     const int xl = x == 0 ? L - 1 : x - 1, xr = x == L - 1 ? 0 : x + 1;
                     const int dcount = (S[y * L + xl] < 0) + (S[y * L + xr] < 0) + (S[yu * L + x] < 0) +
