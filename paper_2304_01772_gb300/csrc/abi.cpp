@@ -88,7 +88,8 @@ struct spin_ctx {
     int width = 0;
     uint8_t *d_type = nullptr;
     int32_t *d_J = nullptr;
-    int32_t *d_vol[2] = {nullptr, nullptr};
+    int32_t *d_vol[2] = {nullptr, nullptr};   // CPM areas: [0] after a Monte Carlo step, [1] alternate
+    int32_t *d_dvol[2] = {nullptr, nullptr};  // CPM area changes of the last two sub-steps
     uint32_t *d_thr = nullptr;
     int n_thr = 0;
     double *d_latp = nullptr;   // [n_lat][4]
@@ -528,13 +529,15 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
 int launch_cpm_step(spin_ctx *ctx, int record, cudaStream_t s, int &launches) {
     for (int c = 0; c < 4; ++c) {
         CpmArgs a{static_cast<int32_t *>(ctx->spins), ctx->lat[0].L, 0u, ctx->d_type, ctx->d_J,
-                  ctx->n_types, ctx->n_cells, ctx->lambda, ctx->target, ctx->d_vol[0], ctx->d_vol[1],
-                  ctx->d_thr, ctx->n_thr, ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta};
+                  ctx->n_types, ctx->n_cells, ctx->lambda, ctx->target, ctx->d_vol[c & 1], ctx->d_vol[(c + 1) & 1],
+                  ctx->d_dvol[c & 1], ctx->d_dvol[(c + 1) & 1], ctx->d_thr, ctx->n_thr, ctx->k0, ctx->k1,
+                  ctx->d_state, ctx->st.delta};
         CK(launch_cpm_substep(a, c, s));
-        CK(launch_cpm_finalize(ctx->d_vol[0], ctx->d_vol[1], ctx->n_cells, ctx->target,
-                               ctx->d_state, ctx->st, c, record, s));
-        launches += 2;
+        launches += 1;
     }
+    // after colour 3, d_vol[0] holds the areas after the step
+    CK(launch_cpm_finalize(ctx->d_vol[0], ctx->n_cells, ctx->target, ctx->d_state, ctx->st, record, s));
+    launches += 1;
     return SPIN_OK;
 }
 
@@ -700,6 +703,7 @@ void spin_destroy(spin_ctx *ctx) {
     if (!ctx) return;
     drop_graphs(ctx);
     void *bufs[] = {ctx->spins2, ctx->d_lats, ctx->d_tabs, ctx->d_items, ctx->d_strip, ctx->d_generic, ctx->d_tri,
+                    ctx->d_dvol[0], ctx->d_dvol[1],
                     ctx->d_state, ctx->st.cur, ctx->st.delta, ctx->st.ring, ctx->d_type,
                     ctx->d_J, ctx->d_vol[0], ctx->d_vol[1], ctx->d_thr, ctx->d_latp,
                     ctx->d_cpmJ, ctx->d_scratch, ctx->d_flag};
@@ -814,7 +818,9 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
         const int nc = ctx->n_cells;
         if (!ckm(cudaMalloc(&ctx->d_type, nc + 1)) || !ckm(cudaMalloc(&ctx->d_J, sizeof(int32_t) * 64)) ||
             !ckm(cudaMalloc(&ctx->d_vol[0], sizeof(int32_t) * (nc + 1))) ||
-            !ckm(cudaMalloc(&ctx->d_vol[1], sizeof(int32_t) * (nc + 1))))
+            !ckm(cudaMalloc(&ctx->d_vol[1], sizeof(int32_t) * (nc + 1))) ||
+            !ckm(cudaMalloc(&ctx->d_dvol[0], sizeof(int32_t) * (nc + 1))) ||
+            !ckm(cudaMalloc(&ctx->d_dvol[1], sizeof(int32_t) * (nc + 1))))
             return bail(SPIN_ENOMEM);
     }
     rc = upload_tables(ctx, s);
@@ -847,6 +853,8 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
         if (e) return bail(cuda_fail(ctx, e, "cpm volumes"));
         cudaMemcpyAsync(ctx->d_vol[1], ctx->d_vol[0], sizeof(int32_t) * (ctx->n_cells + 1),
                         cudaMemcpyDeviceToDevice, s);
+        cudaMemsetAsync(ctx->d_dvol[0], 0, sizeof(int32_t) * (ctx->n_cells + 1), s);
+        cudaMemsetAsync(ctx->d_dvol[1], 0, sizeof(int32_t) * (ctx->n_cells + 1), s);
     }
     if (model != SPIN_CPM) {
         // keep the bytes outside the lattices identical in both buffers
@@ -1137,6 +1145,8 @@ int spin_load_spins(spin_ctx *ctx, const void *host, void *stream) {
         CK(cudaMemsetAsync(ctx->d_vol[0], 0, vb, s));
         CK(launch_cpm_volumes(static_cast<int32_t *>(ctx->spins), ctx->lat[0].L, ctx->d_vol[0], ctx->n_cells, s));
         CK(cudaMemcpyAsync(ctx->d_vol[1], ctx->d_vol[0], vb, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(ctx->d_dvol[0], 0, vb, s));
+        CK(cudaMemsetAsync(ctx->d_dvol[1], 0, vb, s));
     } else {
         CK(cudaMemcpyAsync(base, host, ctx->span_elems * ctx->elem, cudaMemcpyHostToDevice, s));
     }
@@ -1208,6 +1218,8 @@ int spin_restore(spin_ctx *ctx, const void *host_blob, size_t size, void *stream
         CK(cudaMemcpyAsync(ctx->d_vol[0], p + sizeof h + stat_bytes + h.spin_bytes, h.vol_bytes,
                            cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(ctx->d_vol[1], ctx->d_vol[0], h.vol_bytes, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(ctx->d_dvol[0], 0, h.vol_bytes, s));
+        CK(cudaMemsetAsync(ctx->d_dvol[1], 0, h.vol_bytes, s));
     }
     DevState ds{h.t, 0, h.n_rec};
     CK(cudaMemcpyAsync(ctx->d_state, &ds, sizeof ds, cudaMemcpyHostToDevice, s));

@@ -194,8 +194,10 @@ struct CpmArgs {
     int n_types;
     int n_cells;             // ids outside [0, n_cells] are left alone
     int lambda, target;
-    const int32_t *vol_cur;  // snapshot areas
-    int32_t *vol_next;       // areas after this sub-step (starts equal to vol_cur)
+    const int32_t *vol_cur;  // snapshot areas: the areas after the previous sub-step
+    int32_t *vol_next;       // becomes the areas after this sub-step (see sweep_cpm.cu)
+    int32_t *dvol_cur;       // this sub-step's area changes (zero on entry)
+    int32_t *dvol_prev;      // the previous sub-step's area changes, folded into vol_next and cleared
     const uint32_t *thr;     // thr[dE] for dE in [0, n_thr); beyond: 0
     int n_thr;
     uint32_t k0, k1;
@@ -228,11 +230,10 @@ cudaError_t launch_dmc_discretize(int64_t n, float *spins, cudaStream_t s);
 cudaError_t launch_dmc_energy(int n_lat, int L, const float *J, const float *spins, float h, float *grad,
                               double *energy, cudaStream_t s);
 cudaError_t launch_dmc_spin_step(int64_t n, float *spins, const float *grad, float eta, cudaStream_t s);
-// After a CPM colour sub-step: vol_cur = vol_next, contacts += delta; after
-// colour 3 also V2/V1, record, t += 1.
-cudaError_t launch_cpm_finalize(int32_t *vol_cur, const int32_t *vol_next, int n_cells,
-                                int target, DevState *state, StatsBufs st, int colour, int record,
-                                cudaStream_t s);
+// After the four colour sub-steps of a CPM Monte Carlo step: contacts
+// cur += delta, V2 / V1 from the areas after the step, record, t += 1.
+cudaError_t launch_cpm_finalize(const int32_t *vol, int n_cells, int target, DevState *state, StatsBufs st,
+                                int record, cudaStream_t s);
 cudaError_t launch_cpm_init_squares(int32_t *ids, int L, int n_cells, int side, int cols,
                                     cudaStream_t s);
 cudaError_t launch_cpm_volumes(const int32_t *ids, int L, int32_t *vol, int n_cells,

@@ -6,8 +6,13 @@
 // are Moore neighbours, so all sites of a colour attempt their copy at once.
 // One thread handles the two sites of one Philox group (x = 4m + (c&1) and
 // x + 2 in row y).  Area terms read the areas as they stood at the start of
-// the sub-step (vol_cur); accepted copies add +-1 to vol_next atomically, and
-// the finalize kernel makes vol_cur = vol_next before the next sub-step.
+// the sub-step.  Two area arrays and two change arrays alternate so that no
+// copy is needed between sub-steps: sub-step k reads V[k%2] (the areas after
+// k-1) and adds its accepted copies atomically to V[(k+1)%2] and to D[k%2];
+// V[(k+1)%2] held the areas after k-2, so the sub-step also folds in
+// D[(k+1)%2] (the changes of k-1) and clears it.  After sub-step k,
+// V[(k+1)%2] is the areas after k.  The finalize kernel runs once per Monte
+// Carlo step (statistics and the record).
 // Acceptance: integer dE, thr[dE] = max(floor(exp(-dE/T) 2^32), 1) - 1 built
 // on the host; dE beyond the table accepts only u = 0 (probability 2^-32).
 #include <algorithm>
@@ -55,6 +60,15 @@ __global__ void __launch_bounds__(kCpmThreads) cpm_substep_kernel(CpmArgs a, int
     const int cx = c & 1, cy = c >> 1;
     const int n_groups = (L >> 1) * Lq;
     const int per_pass = kCpmThreads * kCpmGroupsPerThread;
+    // fold the previous sub-step's area changes into vol_next (atomically: this
+    // sub-step's copies land there at the same time) and clear them
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= a.n_cells; k += gridDim.x * blockDim.x) {
+        const int d = a.dvol_prev[k];
+        if (d) {
+            atomicAdd(a.vol_next + k, d);
+            a.dvol_prev[k] = 0;
+        }
+    }
     for (int base = blockIdx.x * per_pass; base < n_groups; base += gridDim.x * per_pass) {
         // phase 1: candidates (all four id loads of a thread in flight at once)
 #pragma unroll
@@ -111,6 +125,8 @@ __global__ void __launch_bounds__(kCpmThreads) cpm_substep_kernel(CpmArgs a, int
                 a.ids[y * L + x] = sp;
                 atomicAdd(a.vol_next + sp, 1);
                 atomicAdd(a.vol_next + sg, -1);
+                atomicAdd(a.dvol_cur + sp, 1);
+                atomicAdd(a.dvol_cur + sg, -1);
                 if (nt <= 4) {
                     // contacts lost (by sg) and gained (by sp) per neighbour type, one byte each
                     uint32_t lost = 0, gained = 0;
@@ -143,22 +159,16 @@ __global__ void __launch_bounds__(kCpmThreads) cpm_substep_kernel(CpmArgs a, int
         if (scnt[k]) atomicAdd(reinterpret_cast<unsigned long long *>(a.delta + k), (unsigned long long)(long long)scnt[k]);
 }
 
-// After colour sub-step `colour`: vol_cur = vol_next, contacts += delta.
-// After colour 3: V2 / V1 from the areas, record, advance the step counter.
-__global__ void __launch_bounds__(1024) cpm_finalize_kernel(int32_t *vol_cur,
-                                                            const int32_t *vol_next, int n_cells,
-                                                            int target, DevState *state,
-                                                            StatsBufs st, int colour, int record) {
+// After the four sub-steps of a Monte Carlo step: contacts cur += delta, V2
+// and V1 from the areas after the step, the record, and the step counter.
+__global__ void __launch_bounds__(1024) cpm_finalize_kernel(const int32_t *vol, int n_cells, int target,
+                                                            DevState *state, StatsBufs st, int record) {
     __shared__ long long r2[32], r1[32];
     long long v2 = 0, v1 = 0;
-    for (int k = threadIdx.x; k <= n_cells; k += blockDim.x) {
-        const int v = vol_next[k];
-        vol_cur[k] = v;
-        if (k > 0) {
-            const long long d = (long long)v - target;
-            v2 += d * d;
-            v1 += d;
-        }
+    for (int k = 1 + threadIdx.x; k <= n_cells; k += blockDim.x) {
+        const long long d = (long long)vol[k] - target;
+        v2 += d * d;
+        v1 += d;
     }
     const int npair = st.width - 2;
     for (int k = threadIdx.x; k < npair; k += blockDim.x) {
@@ -175,7 +185,6 @@ __global__ void __launch_bounds__(1024) cpm_finalize_kernel(int32_t *vol_cur,
         r1[threadIdx.x >> 5] = v1;
     }
     __syncthreads();
-    if (colour != 3) return;
     if (threadIdx.x == 0) {
         long long a2 = 0, a1 = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
@@ -459,11 +468,9 @@ cudaError_t launch_cpm_substep(const CpmArgs &a, int colour, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_cpm_finalize(int32_t *vol_cur, const int32_t *vol_next, int n_cells,
-                                int target, DevState *state, StatsBufs st, int colour, int record,
-                                cudaStream_t s) {
-    cpm_finalize_kernel<<<1, 1024, 0, s>>>(vol_cur, vol_next, n_cells, target, state, st, colour,
-                                           record);
+cudaError_t launch_cpm_finalize(const int32_t *vol, int n_cells, int target, DevState *state, StatsBufs st,
+                                int record, cudaStream_t s) {
+    cpm_finalize_kernel<<<1, 1024, 0, s>>>(vol, n_cells, target, state, st, record);
     return cudaGetLastError();
 }
 
