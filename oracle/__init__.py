@@ -86,6 +86,10 @@ def _declare(L):
         "or_tri_sweep": (None, [_i, _f, _f, _f, _u64, _u32, _u32, _i8p]),
         "or_tri_stats": (None, [_i, _i8p, _i64p]),
         "or_tri_run": (None, [_i, _f, _f, _f, _u64, _u32, _u32, _i, _i8p, _i64p]),
+        "or_nnn_substep": (None, [_i, _f, _f, _f, _f, _u64, _u32, _u32, _i, _i8p]),
+        "or_nnn_sweep": (None, [_i, _f, _f, _f, _f, _u64, _u32, _u32, _i8p]),
+        "or_nnn_stats": (None, [_i, _i8p, _i64p]),
+        "or_nnn_run": (None, [_i, _f, _f, _f, _f, _u64, _u32, _u32, _i, _i8p, _i64p]),
         "or_dmc_substep": (None, [_i, _dp, _dp, _d, _d, _d, _u64, _u32, _u32, _i, _dp]),
         "or_dmc_run": (None, [_i, _dp, _dp, _d, _d, _d, _u64, _u32, _u32, _i, _dp, _dp]),
         "or_dmc_backward": (None, [_i, _dp, _dp, _d, _d, _d, _u64, _u32, _u32, _i, _dp, _dp, _dp, _dp]),
@@ -179,6 +183,30 @@ def tri_run(s, beta, J, h, seed, lattice, sweep0, nsweeps, record=True):
     """Run nsweeps in place; stats [nsweeps, 2] = (M, B) after each sweep."""
     st = np.zeros((nsweeps, 2), dtype=np.int64) if record else None
     lib().or_tri_run(s.shape[0], beta, J, h, seed, lattice, sweep0, nsweeps, _p(s, ctypes.c_int8),
+                     _p(st, ctypes.c_int64) if record else None)
+    return st
+
+
+def nnn_substep(s, beta, J, J2, h, seed, lattice, sweep, colour):
+    """First-and-second-neighbour Ising colour sub-step in place (s int8 [L, L], L even)."""
+    lib().or_nnn_substep(s.shape[0], beta, J, J2, h, seed, lattice, sweep, colour, _p(s, ctypes.c_int8))
+
+
+def nnn_sweep(s, beta, J, J2, h, seed, lattice, sweep):
+    lib().or_nnn_sweep(s.shape[0], beta, J, J2, h, seed, lattice, sweep, _p(s, ctypes.c_int8))
+
+
+def nnn_stats(s):
+    """(M, B, B2): magnetisation, nearest- and diagonal-bond sums."""
+    out = np.zeros(3, dtype=np.int64)
+    lib().or_nnn_stats(s.shape[0], _p(np.ascontiguousarray(s), ctypes.c_int8), _p(out, ctypes.c_int64))
+    return out
+
+
+def nnn_run(s, beta, J, J2, h, seed, lattice, sweep0, nsweeps, record=True):
+    """Run nsweeps in place; stats [nsweeps, 3] = (M, B, B2) after each sweep."""
+    st = np.zeros((nsweeps, 3), dtype=np.int64) if record else None
+    lib().or_nnn_run(s.shape[0], beta, J, J2, h, seed, lattice, sweep0, nsweeps, _p(s, ctypes.c_int8),
                      _p(st, ctypes.c_int64) if record else None)
     return st
 

@@ -55,6 +55,22 @@ def ising_grad(stats, beta, J, h, N, burn_in=0):
     return out
 
 
+def nnn_grad(stats, beta, J, J2, h, N, burn_in=0):
+    """First and second neighbours (H = -J B - J2 B2 - h M): stats [..., T, 3]
+    integer (M, B, B2) per sweep; dH/dJ2 = -B2 and, for O = E/N, dO/dJ2 = -B2/N.
+
+    Returns {(O, theta)} for O in ('E', 'M') and theta in ('J', 'h', 'J2')."""
+    st = np.asarray(stats)
+    st = st.reshape(-1, st.shape[-2], st.shape[-1])[:, burn_in:, :].reshape(-1, 3)
+    M, B, B2 = (st[:, k].astype(np.float64) for k in range(3))
+    E = -float(J) * B - float(J2) * B2 - float(h) * M
+    out = {}
+    for name, X in (("J", B), ("h", M), ("J2", B2)):
+        out[("E", name)] = fluctuation_grad(E / N, -X / N, -X, beta)
+        out[("M", name)] = fluctuation_grad(M / N, None, -X, beta)
+    return out
+
+
 def cpm_pairs(n_types):
     return [(a, b) for a in range(n_types) for b in range(a, n_types)]
 

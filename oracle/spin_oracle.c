@@ -31,7 +31,9 @@
  * exact enumeration (4x4), Onsager's solution, detailed balance, the q=2
  * Potts/Ising identity and CPM bookkeeping invariants; the differentiable
  * Monte Carlo of Alg. 2 by finite differences of its forward pass, its
- * alpha -> infinity Metropolis limit and a closed form (see tests/).
+ * alpha -> infinity Metropolis limit and a closed form; the triangular and
+ * the first-and-second-neighbour lattices by brute-force replicas over
+ * independently built bond lists and exact enumeration (see tests/).
  */
 #include <math.h>
 #include <stdint.h>
@@ -667,5 +669,75 @@ void or_tri_run(int L, float beta, float J, float h, uint64_t seed, uint32_t lat
     for (int t = 0; t < nsweeps; ++t) {
         or_tri_sweep(L, beta, J, h, seed, lattice, sweep0 + (uint32_t)t, s);
         if (stats) or_tri_stats(L, s, stats + 2 * (size_t)t);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Ising model with first and second neighbours (Sec. "Ising model": the */
+/* checkerboard update serves any order of neighbourhood as long as a    */
+/* site's colour differs from the colours of all its neighbours).        */
+/* H = -J sum_nn s s - J2 sum_nnn s s - h sum s over the four nearest    */
+/* neighbours (x+-1, y), (x, y+-1) and the four diagonal ones            */
+/* (x+-1, y+-1), periodic; every bond counted once (nearest through      */
+/* (x+1, y), (x, y+1); diagonal through (x+1, y+1), (x+1, y-1)).  Four   */
+/* colours c = (x & 1) | ((y & 1) << 1), updated in the order 0..3       */
+/* (L even).  A flip changes the energy by dE = 2 s (J n1 + J2 n2 + h),  */
+/* n1 and n2 the sums of the nearest and of the diagonal neighbours.     */
+/* The draw of site (x, y) of colour c: k = (y >> 1)(L/2) + (x >> 1),    */
+/* Philox(seed; k >> 2, lattice, sweep, c), lane k & 3.                  */
+/* ------------------------------------------------------------------ */
+static void nnn_sums(int L, const int8_t *s, int x, int y, int *n1, int *n2)
+{
+    int xl = wrap(x - 1, L), xr = wrap(x + 1, L), yu = wrap(y - 1, L), yd = wrap(y + 1, L);
+    *n1 = s[y * L + xl] + s[y * L + xr] + s[yu * L + x] + s[yd * L + x];
+    *n2 = s[yu * L + xl] + s[yu * L + xr] + s[yd * L + xl] + s[yd * L + xr];
+}
+
+void or_nnn_substep(int L, float beta, float J, float J2, float h, uint64_t seed, uint32_t lattice,
+                    uint32_t sweep, int colour, int8_t *s)
+{
+    double beta_d = (double)beta;
+    for (int y = 0; y < L; ++y)
+        for (int x = 0; x < L; ++x) {
+            if (((x & 1) | ((y & 1) << 1)) != colour) continue;
+            int sig = s[y * L + x], n1, n2;
+            nnn_sums(L, s, x, y, &n1, &n2);
+            double dE = 2.0 * (double)sig * ((double)J * (double)n1 + (double)J2 * (double)n2 + (double)h);
+            uint32_t k = (uint32_t)((y >> 1) * (L / 2) + (x >> 1));
+            uint32_t r[4];
+            draw4(seed, k >> 2, lattice, sweep, (uint32_t)colour, r);
+            if (or_accept(beta_d, dE, r[k & 3u])) s[y * L + x] = (int8_t)(-sig);
+        }
+}
+
+void or_nnn_sweep(int L, float beta, float J, float J2, float h, uint64_t seed, uint32_t lattice,
+                  uint32_t sweep, int8_t *s)
+{
+    for (int c = 0; c < 4; ++c) or_nnn_substep(L, beta, J, J2, h, seed, lattice, sweep, c, s);
+}
+
+/* out[0] = M = sum s, out[1] = B = sum over nearest-neighbour bonds of s s,
+ * out[2] = B2 = sum over diagonal bonds of s s (two of each per site).      */
+void or_nnn_stats(int L, const int8_t *s, int64_t out[3])
+{
+    int64_t M = 0, B = 0, B2 = 0;
+    for (int y = 0; y < L; ++y)
+        for (int x = 0; x < L; ++x) {
+            int v = s[y * L + x], xr = wrap(x + 1, L), yd = wrap(y + 1, L), yu = wrap(y - 1, L);
+            M += v;
+            B += v * (s[y * L + xr] + s[yd * L + x]);
+            B2 += v * (s[yd * L + xr] + s[yu * L + xr]);
+        }
+    out[0] = M;
+    out[1] = B;
+    out[2] = B2;
+}
+
+void or_nnn_run(int L, float beta, float J, float J2, float h, uint64_t seed, uint32_t lattice,
+                uint32_t sweep0, int nsweeps, int8_t *s, int64_t *stats)
+{
+    for (int t = 0; t < nsweeps; ++t) {
+        or_nnn_sweep(L, beta, J, J2, h, seed, lattice, sweep0 + (uint32_t)t, s);
+        if (stats) or_nnn_stats(L, s, stats + 3 * (size_t)t);
     }
 }
