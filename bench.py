@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--workload", default="uneven512",
                     choices=["uneven512", "potts_q3", "potts_q8", "cpm1024", "ising_small", "grad", "mlp", "dmc",
-                             "spinglass", "cpm_batch", "triangular", "fit"])
+                             "spinglass", "cpm_batch", "triangular", "nnn", "fit"])
     return ap.parse_args()
 
 
@@ -189,6 +189,19 @@ def _oracle_tri(args):
     return n * 192 * 192, time.perf_counter() - t0
 
 
+def _oracle_nnn(args):
+    import oracle
+    from paper_2304_01772_gb300 import workloads as wl
+    b0, n = args
+    lats = wl.nnn256()
+    t0 = time.perf_counter()
+    for b in range(b0, b0 + n):
+        d = lats[b]
+        s = oracle.init_ising(d["L"], SEED, b).copy()
+        oracle.nnn_run(s, d["beta"], d["J"], d["J2"], d["h"], SEED, b, 0, 1, record=False)
+    return n * 256 * 256, time.perf_counter() - t0
+
+
 def cpu_oracle_pool(fn, tasks, cores):
     import multiprocessing as mp
 
@@ -235,6 +248,11 @@ def cpu_baseline_secondary(workload, cores):
         import numpy as np
         per = 2
         rate, units, wall = cpu_oracle_pool(_oracle_tri, [(b * per, per) for b in range(cores)], cores)
+        return {"value": rate, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
+                "sample": f"{per * cores} of the 256 lattices, one sweep each ({wall:.1f} s wall)"}
+    if workload == "nnn":
+        per = max(1, 256 // cores)
+        rate, units, wall = cpu_oracle_pool(_oracle_nnn, [(b * per, per) for b in range(cores)], cores)
         return {"value": rate, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
                 "sample": f"{per * cores} of the 256 lattices, one sweep each ({wall:.1f} s wall)"}
     if workload == "ising_small":
@@ -713,6 +731,12 @@ def run_secondary(args):
         units, unit = wl.site_count(lats), "site-updates/s"
         desc = ("256 triangular-lattice Ising lattices 192^2 (six neighbours, three colours), "
                 "beta = linspace(0.2, 0.35, 256) across beta_c = ln(3)/4")
+    elif args.workload == "nnn":
+        lats = wl.nnn256()
+        sim = sm.Sim(sm.SPIN_ISING, lats, seed=SEED, max_record=16)
+        units, unit = wl.site_count(lats), "site-updates/s"
+        desc = ("256 Ising lattices 256^2 with first and second neighbours (four colours), J = 1, "
+                "J2 ~ U(-0.5, 0.5), beta ~ U(0.2, 0.45), h ~ N(0, 0.05)")
     elif args.workload == "cpm1024":
         p = wl.cpm1024()
         sim = sm.Sim(sm.SPIN_CPM, [dict(L=p["L"])], seed=SEED, max_record=16,

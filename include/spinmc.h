@@ -75,7 +75,15 @@ typedef struct {
     int32_t geometry;     /* 0: square lattice, 4 neighbours (Sec. "Ising model", kernel K);
                              1: triangular lattice, 6 neighbours (x+-1, y), (x, y+-1), (x+1, y-1),
                              (x-1, y+1) on the square grid, three colours c = (x - y) mod 3 updated
-                             in order; Ising only, L % 6 == 0                                   */
+                             in order; Ising only, L % 6 == 0;
+                             2: square lattice with first and second neighbours (Sec. "Related
+                             Work": the checkerboard serves any order of neighbourhood once a
+                             site's colour differs from all its neighbours'), H = -J sum_nn s s
+                             - J2 sum_diag s s - h sum s, four colours c = (x & 1) | ((y & 1) << 1)
+                             updated in order, draw of site (x, y): k = (y >> 1)(L/2) + (x >> 1),
+                             lane k & 3 of Philox group k >> 2; Ising only, and a context holds
+                             either only such lattices or none; statistics (M, B, B2)            */
+    float J2;             /* second-neighbour (diagonal) coupling, geometry 2; otherwise 0    */
     uint64_t spin_offset; /* element offset of this lattice in the caller's spin buffer       */
 } spin_lattice_desc;
 
@@ -116,7 +124,8 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
 int spin_sweep(spin_ctx *ctx, int32_t n_sweeps, int32_t record, void *stream);
 
 /* Number of int64 statistics per lattice per sweep:
- *   Ising 2: (M = sum s, B = sum_bonds s s');
+ *   Ising 2: (M = sum s, B = sum_bonds s s'); with second neighbours 3:
+ *       (M, B over nearest-neighbour bonds, B2 over diagonal bonds);
  *   Potts 1+q_max: (B_eq = #equal bonds, n_0 .. n_{q_max-1});
  *   CPM n_types(n_types+1)/2 + 2: (C_ab for a <= b = #Moore contacts between
  *       different cells of types a and b, V2 = sum_cells (a-A)^2, V1 = sum_cells (a-A)). */
@@ -129,7 +138,7 @@ int64_t spin_num_records(const spin_ctx *ctx);
  * may be a device or a (pinned or pageable) host pointer.
  *   stats [n][n_lattices][width] int64, exact;
  *   E, M  [n][n_lattices] float: energy per site and magnetisation per site
- *   (Ising: E = -J B - h M, M = sum s; Potts: E = -J B_eq,
+ *   (Ising: E = -J B - J2 B2 - h M, M = sum s; Potts: E = -J B_eq,
  *   M = (q max_k n_k - N)/(q - 1); CPM: E = total H, M = adhesion energy),
  *   computed in double from the exact integers and rounded once.
  * Only the last max_record_sweeps records are held (SPIN_EINVAL otherwise). */
@@ -152,7 +161,8 @@ int spin_num_moments(const spin_ctx *ctx);
  * relaxed Monte Carlo steps, Alg. 2; this is the exact identity for a
  * Boltzmann law, evaluated from the recorded samples).  Integer moments are
  * exact; the covariance is formed in FP64 on the device.
- * Ising: observable 0 = E/N, 1 = M/N; out[l][0] = d/dJ, out[l][1] = d/dh.
+ * Ising: observable 0 = E/N, 1 = M/N; out[l][0] = d/dJ, out[l][1] = d/dh,
+ *        and with second neighbours (geometry 2) out[l][2] = d/dJ2.
  * CPM:   observable 0 = adhesion energy per site; out[0][i] = d/dJ_ab for the
  *        i-th pair a <= b, then d/dlambda, d/dA (beta = 1/T).
  * pool != 0 pools the samples of all lattices (they must share theta) and

@@ -81,6 +81,8 @@ struct spin_ctx {
     int32_t *d_generic = nullptr;
     int32_t *d_tri = nullptr;   // triangular lattices (geometry 1)
     int n_tri = 0, tri_maxL = 0;
+    uint32_t *d_nnn_thr = nullptr;   // first and second neighbours (geometry 2): [n_lat][kNnnTab]
+    int n_nnn = 0, nnn_maxL = 0;
     int n_generic = 0, generic_maxL = 0;
     std::vector<int> fast_ids;
     DevState *d_state = nullptr;
@@ -92,7 +94,7 @@ struct spin_ctx {
     int32_t *d_dvol[2] = {nullptr, nullptr};  // CPM area changes of the last two sub-steps
     uint32_t *d_thr = nullptr;
     int n_thr = 0;
-    double *d_latp = nullptr;   // [n_lat][4]
+    double *d_latp = nullptr;   // [n_lat][kLatParams]
     double *d_cpmJ = nullptr;   // [pairs]
     void *d_scratch = nullptr;  // moments etc.
     size_t scratch_bytes = 0;
@@ -177,6 +179,20 @@ void tri_table(const spin_lattice_desc &d, TabEntry *e) {
         }
 }
 
+// First and second neighbours: entry 25 cdown + 5 d1 + d2 (d1, d2 = down
+// spins among the four nearest and the four diagonal neighbours).
+void nnn_table(const spin_lattice_desc &d, uint32_t *thr) {
+    const double beta = (double)d.beta;
+    for (int c = 0; c < 2; ++c)
+        for (int d1 = 0; d1 <= 4; ++d1)
+            for (int d2 = 0; d2 <= 4; ++d2) {
+                const int s = c ? -1 : 1;
+                const int n1 = 4 - 2 * d1, n2 = 4 - 2 * d2;
+                const double dE = 2.0 * (double)s * ((double)d.J * (double)n1 + (double)d.J2 * (double)n2 + (double)d.h);
+                thr[25 * c + 5 * d1 + d2] = thr_from(beta, dE);
+            }
+}
+
 void potts_table(const spin_lattice_desc &d, TabEntry *e) {
     const double beta = (double)d.beta;
     for (int dd = -4; dd <= 4; ++dd) {
@@ -187,7 +203,7 @@ void potts_table(const spin_lattice_desc &d, TabEntry *e) {
 }
 
 int stats_width(int model, const std::vector<spin_lattice_desc> &lat, int n_types) {
-    if (model == SPIN_ISING) return 2;
+    if (model == SPIN_ISING) return lat[0].geometry == 2 ? 3 : 2;   // (M, B[, B2])
     if (model == SPIN_POTTS) {
         int q = 2;
         for (auto &d : lat) q = std::max(q, d.q);
@@ -211,9 +227,19 @@ int validate(spin_ctx *ctx, int model, int n, const spin_lattice_desc *lat,
             snprintf(buf, sizeof buf, "lattice %d: L=%d must be even and in [4, %d]", i, d.L, kMaxL);
             return fail(ctx, SPIN_EINVAL, buf);
         }
-        if (d.geometry != 0 && d.geometry != 1) return fail(ctx, SPIN_EINVAL, "geometry must be 0 or 1");
-        if (d.geometry == 1 && (model != SPIN_ISING || d.L % 6 != 0))
-            return fail(ctx, SPIN_EINVAL, "the triangular lattice needs the Ising model and L % 6 == 0");
+        if (model != SPIN_CPM) {
+            if (d.geometry < 0 || d.geometry > 2) return fail(ctx, SPIN_EINVAL, "geometry must be 0, 1 or 2");
+            if (d.geometry == 1 && (model != SPIN_ISING || d.L % 6 != 0))
+                return fail(ctx, SPIN_EINVAL, "the triangular lattice needs the Ising model and L % 6 == 0");
+            if (d.geometry == 2 && model != SPIN_ISING)
+                return fail(ctx, SPIN_EINVAL, "second neighbours need the Ising model");
+            if ((d.geometry == 2) != (lat[0].geometry == 2))
+                return fail(ctx, SPIN_EINVAL, "lattices with second neighbours cannot share a context with others");
+            if (!std::isfinite(d.J2) || (d.geometry != 2 && d.J2 != 0.0f))
+                return fail(ctx, SPIN_EINVAL, "J2 must be finite, and 0 unless geometry is 2");
+        } else if (d.geometry != 0 || d.J2 != 0.0f) {
+            return fail(ctx, SPIN_EINVAL, "CPM lattices take geometry 0 and J2 = 0");
+        }
         if (model == SPIN_POTTS) {
             if (d.q < 2 || d.q > 255) {
                 snprintf(buf, sizeof buf, "lattice %d: q=%d out of [2, 255]", i, d.q);
@@ -277,12 +303,13 @@ int upload_tables(spin_ctx *ctx, cudaStream_t s) {
         for (int a = 0; a < ctx->n_types; ++a)
             for (int b = a; b < ctx->n_types; ++b) pj.push_back((double)ctx->Jt[a * ctx->n_types + b]);
         CK(cudaMemcpy(ctx->d_cpmJ, pj.data(), sizeof(double) * pj.size(), cudaMemcpyHostToDevice));
-        std::vector<double> lp = {0.0, 0.0, (double)ctx->lat[0].L * ctx->lat[0].L, 1.0 / (double)ctx->T};
-        CK(cudaMemcpy(ctx->d_latp, lp.data(), sizeof(double) * 4, cudaMemcpyHostToDevice));
+        std::vector<double> lp = {0.0, 0.0, (double)ctx->lat[0].L * ctx->lat[0].L, 1.0 / (double)ctx->T, 0.0};
+        CK(cudaMemcpy(ctx->d_latp, lp.data(), sizeof(double) * kLatParams, cudaMemcpyHostToDevice));
         return SPIN_OK;
     }
     std::vector<TabEntry> tab((size_t)ctx->n_lat * kTabStride, TabEntry{0u, 0});
-    std::vector<double> lp((size_t)ctx->n_lat * 4);
+    std::vector<double> lp((size_t)ctx->n_lat * kLatParams);
+    std::vector<uint32_t> nnn(ctx->n_nnn ? (size_t)ctx->n_lat * kNnnTab : 0);
     for (int i = 0; i < ctx->n_lat; ++i) {
         const spin_lattice_desc &d = ctx->lat[i];
         if (ctx->model == SPIN_ISING && d.geometry == 1)
@@ -291,13 +318,18 @@ int upload_tables(spin_ctx *ctx, cudaStream_t s) {
             ising_table(d, &tab[(size_t)i * kTabStride]);
         else
             potts_table(d, &tab[(size_t)i * kTabStride]);
-        lp[4 * i] = d.J;
-        lp[4 * i + 1] = d.h;
-        lp[4 * i + 2] = (double)d.L * d.L;
-        lp[4 * i + 3] = ctx->model == SPIN_POTTS ? (double)d.q : (double)d.beta;
+        if (ctx->model == SPIN_ISING && d.geometry == 2) nnn_table(d, &nnn[(size_t)i * kNnnTab]);
+        double *l = &lp[(size_t)kLatParams * i];
+        l[0] = d.J;
+        l[1] = d.h;
+        l[2] = (double)d.L * d.L;
+        l[3] = ctx->model == SPIN_POTTS ? (double)d.q : (double)d.beta;
+        l[4] = d.geometry == 2 ? (double)d.J2 : 0.0;
     }
     (void)s;
     CK(cudaMemcpy(ctx->d_tabs, tab.data(), sizeof(TabEntry) * tab.size(), cudaMemcpyHostToDevice));
+    if (!nnn.empty())
+        CK(cudaMemcpy(ctx->d_nnn_thr, nnn.data(), sizeof(uint32_t) * nnn.size(), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_latp, lp.data(), sizeof(double) * lp.size(), cudaMemcpyHostToDevice));
     return SPIN_OK;
 }
@@ -434,6 +466,13 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                 if (timed) prof_end(ctx, s);
                 ++launches;
             }
+            if (ctx->n_nnn && c == 0)
+                for (int nc = 0; nc < 4; ++nc) {
+                    CK(launch_ising_nnn(static_cast<int8_t *>(src), static_cast<int8_t *>(src), ctx->n_nnn,
+                                        ctx->nnn_maxL, ctx->d_lats, ctx->d_nnn_thr, ctx->k0, ctx->k1, ctx->d_state,
+                                        ctx->st.delta, nc, s));
+                    ++launches;
+                }
             if (ctx->n_tri && c == 0)
                 for (int tc = 0; tc < 3; ++tc) {
                     CK(launch_ising_tri(static_cast<int8_t *>(src), static_cast<int8_t *>(src), ctx->d_tri, ctx->n_tri,
@@ -454,6 +493,13 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
             }
         }
     } else {
+        for (int nc = 0; nc < 4 && ctx->n_nnn; ++nc) {
+            const bool timed = prof_begin(ctx, s, 3);
+            CK(launch_ising_nnn(static_cast<int8_t *>(src), static_cast<int8_t *>(dst), ctx->n_nnn, ctx->nnn_maxL,
+                                ctx->d_lats, ctx->d_nnn_thr, ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, nc, s));
+            if (timed) prof_end(ctx, s);
+            ++launches;
+        }
         for (int tc = 0; tc < 3 && ctx->n_tri; ++tc) {
             CK(launch_ising_tri(static_cast<int8_t *>(src), static_cast<int8_t *>(dst), ctx->d_tri, ctx->n_tri,
                                 ctx->tri_maxL, ctx->d_lats, ctx->d_tabs, ctx->k0, ctx->k1, ctx->d_state,
@@ -578,7 +624,10 @@ int run_sweeps(spin_ctx *ctx, int n, int record, cudaStream_t s) {
     if (ctx->mode == 2) {
         ResidentArgs a{static_cast<int8_t *>(ctx->spins), ctx->d_lats, ctx->d_tabs, ctx->k0, ctx->k1,
                        ctx->t, n, (long long)ctx->n_rec, record, ctx->st};
-        if (ctx->n_tri == ctx->n_lat)
+        if (ctx->n_nnn == ctx->n_lat)
+            CK(launch_ising_nnn_resident(a, ctx->d_nnn_thr, ctx->n_lat, (size_t)ctx->maxL * ctx->maxL,
+                                         ctx->d_state, s));
+        else if (ctx->n_tri == ctx->n_lat)
             CK(launch_ising_tri_resident(a, ctx->n_lat, (size_t)ctx->maxL * ctx->maxL, ctx->d_state, s));
         else
             CK(launch_ising_resident(a, ctx->n_lat, ctx->threads, (size_t)ctx->maxL * ctx->maxL,
@@ -660,7 +709,7 @@ std::string shape_key(const spin_ctx *ctx) {
     o << "m" << ctx->model << "_n" << ctx->n_lat;
     uint64_t h = 1469598103934665603ull;
     for (auto &d : ctx->lat) {
-        h ^= (uint64_t)d.L * 1315423911u + (uint64_t)d.q;
+        h ^= (uint64_t)d.L * 1315423911u + (uint64_t)d.q + ((uint64_t)d.geometry << 40);
         h *= 1099511628211ull;
     }
     o << "_h" << std::hex << h;
@@ -696,13 +745,14 @@ int spin_num_moments(const spin_ctx *ctx) {
 
 int spin_num_grad(const spin_ctx *ctx) {
     if (!ctx) return SPIN_EINVAL;
-    return ctx->model == SPIN_ISING ? 2 : (ctx->model == SPIN_CPM ? ctx->width : SPIN_EINVAL);
+    return ctx->model == SPIN_ISING ? ctx->width : (ctx->model == SPIN_CPM ? ctx->width : SPIN_EINVAL);
 }
 
 void spin_destroy(spin_ctx *ctx) {
     if (!ctx) return;
     drop_graphs(ctx);
     void *bufs[] = {ctx->spins2, ctx->d_lats, ctx->d_tabs, ctx->d_items, ctx->d_strip, ctx->d_generic, ctx->d_tri,
+                    ctx->d_nnn_thr,
                     ctx->d_dvol[0], ctx->d_dvol[1],
                     ctx->d_state, ctx->st.cur, ctx->st.delta, ctx->st.ring, ctx->d_type,
                     ctx->d_J, ctx->d_vol[0], ctx->d_vol[1], ctx->d_thr, ctx->d_latp,
@@ -763,6 +813,7 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
     ctx->width = stats_width(model, ctx->lat, ctx->n_types);
     std::vector<LatDev> ld(n_lattices);
     std::vector<int32_t> generic, tri;
+    ctx->n_nnn = 0;
     for (int i = 0; i < n_lattices; ++i) {
         const auto &d = ctx->lat[i];
         const int geom = model == SPIN_CPM ? 0 : d.geometry;
@@ -770,7 +821,10 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
                        (geom == 0 && d.L % 16 == 0 && d.spin_offset % 16 == 0) ? 1 : 0, geom};
         ctx->maxL = std::max(ctx->maxL, d.L);
         ctx->span_elems = std::max<size_t>(ctx->span_elems, d.spin_offset + (size_t)d.L * d.L);
-        if (geom == 1) {
+        if (geom == 2) {
+            ++ctx->n_nnn;
+            ctx->nnn_maxL = std::max(ctx->nnn_maxL, d.L);
+        } else if (geom == 1) {
             tri.push_back(i);
             ctx->tri_maxL = std::max(ctx->tri_maxL, d.L);
         } else if (ld[i].fast)
@@ -789,7 +843,7 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
         !ckm(cudaMalloc(&ctx->d_state, sizeof(DevState))) ||
         !ckm(cudaMalloc(&ctx->st.cur, sizeof(int64_t) * w * n_lattices)) ||
         !ckm(cudaMalloc(&ctx->st.delta, sizeof(int64_t) * w * n_lattices)) ||
-        !ckm(cudaMalloc(&ctx->d_latp, sizeof(double) * 4 * n_lattices)) ||
+        !ckm(cudaMalloc(&ctx->d_latp, sizeof(double) * kLatParams * n_lattices)) ||
         !ckm(cudaMalloc(&ctx->d_cpmJ, sizeof(double) * 64)) ||
         !ckm(cudaMalloc(&ctx->d_flag, sizeof(int))) ||
         (max_record_sweeps > 0 &&
@@ -802,6 +856,8 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
             return bail(SPIN_ENOMEM);
         cudaMemcpy(ctx->d_generic, generic.data(), sizeof(int32_t) * generic.size(), cudaMemcpyHostToDevice);
     }
+    if (ctx->n_nnn && !ckm(cudaMalloc(&ctx->d_nnn_thr, sizeof(uint32_t) * kNnnTab * n_lattices)))
+        return bail(SPIN_ENOMEM);
     if (ctx->n_tri) {
         if (!ckm(cudaMalloc(&ctx->d_tri, sizeof(int32_t) * ctx->n_tri))) return bail(SPIN_ENOMEM);
         cudaMemcpy(ctx->d_tri, tri.data(), sizeof(int32_t) * tri.size(), cudaMemcpyHostToDevice);
@@ -1097,6 +1153,11 @@ int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_
 
 static bool resident_ok(const spin_ctx *ctx) {
     if (ctx->model != SPIN_ISING || ctx->n_generic) return false;
+    if (ctx->n_nnn) {   // first and second neighbours (a context holds only these)
+        for (const auto &d : ctx->lat)
+            if (d.L > 256) return false;
+        return true;
+    }
     if (ctx->n_tri) {   // all triangular: the triangular resident kernel
         if (ctx->n_tri != ctx->n_lat) return false;
         for (const auto &d : ctx->lat)
@@ -1113,7 +1174,8 @@ int spin_set_launch(spin_ctx *ctx, int32_t mode, int32_t use_graph, int32_t tile
     if (mode < 0 || mode > 2) return fail(ctx, SPIN_EINVAL, "launch mode must be 0, 1 or 2");
     if (mode == 2 && !resident_ok(ctx))
         return fail(ctx, SPIN_EINVAL, "resident form needs Ising lattices with L % 16 == 0 and L <= 256, "
-                                      "or only triangular lattices with L <= 240");
+                                      "only triangular lattices with L <= 240, or second-neighbour "
+                                      "lattices with L <= 256");
     if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
         return fail(ctx, SPIN_EINVAL, "threads must be 128, 256 or 512");
     if (tile_rows < -1) return fail(ctx, SPIN_EINVAL, "tile_rows must be >= -1");

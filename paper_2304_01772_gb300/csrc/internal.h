@@ -13,7 +13,7 @@ struct LatDev {
     int32_t L;
     int32_t q;        // Potts states (2 for Ising)
     int32_t fast;     // 1: L % 16 == 0 and offset % 16 == 0 -> vectorised kernels
-    int32_t geom;     // 0: square lattice, 1: triangular (Ising)
+    int32_t geom;     // 0: square lattice, 1: triangular, 2: first and second neighbours (Ising)
 };
 
 // One work item of the batched sweep: rows [r0, r0 + nrows) of lattice `lat`.
@@ -32,6 +32,13 @@ struct __align__(8) TabEntry {
     int32_t delta;
 };
 constexpr int kTabStride = 16;     // entries per lattice (Ising uses 10, Potts 9)
+// First-and-second-neighbour Ising: thresholds per lattice indexed
+// cdown * 25 + d1 * 5 + d2 (d1, d2 = down spins among the four nearest and
+// the four diagonal neighbours).
+constexpr int kNnnTab = 50;
+// Per-lattice doubles of the observables and estimator kernels:
+// J, h, N, beta (Ising) or q (Potts), J2.
+constexpr int kLatParams = 5;
 
 // Device-side counters advanced by the finalize kernels (so that captured
 // graphs need no per-sweep parameters).
@@ -139,6 +146,16 @@ cudaError_t launch_ising_resident(const ResidentArgs &a, int n_lat, int threads,
 // The same for batches made only of triangular lattices (L <= 240).
 cudaError_t launch_ising_tri_resident(const ResidentArgs &a, int n_lat, size_t smem, DevState *state,
                                       cudaStream_t s);
+// Ising with first and second neighbours (geometry 2; a context holds only
+// such lattices, statistics (M, B, B2)), one colour of four over all lattices:
+// colour 0 reads src and writes dst (each thread also copies the three other
+// sites of its 2x2 block), colours 1..3 work in place on dst.  thr: [n][kNnnTab].
+cudaError_t launch_ising_nnn(const int8_t *src, int8_t *dst, int n, int maxL, const LatDev *lats,
+                             const uint32_t *thr, uint32_t k0, uint32_t k1, const DevState *state,
+                             int64_t *delta, int colour, cudaStream_t s);
+// Resident form of the same (L <= 256; a.tabs unused).
+cudaError_t launch_ising_nnn_resident(const ResidentArgs &a, const uint32_t *thr, int n_lat, size_t smem,
+                                      DevState *state, cudaStream_t s);
 cudaError_t launch_init_random(void *spins, int model, const LatDev *lats, int n_lat, int maxL,
                                uint32_t k0, uint32_t k1, cudaStream_t s);
 
@@ -254,7 +271,7 @@ struct ObsParams {
     int model;
     int n_lat;
     int width;
-    const double *lat_params;  // [n_lat][4]: J, h, N, q
+    const double *lat_params;  // [n_lat][kLatParams]
     const double *cpm_J;       // [pairs]
     double cpm_lambda;
 };
@@ -267,7 +284,7 @@ struct GradParams {
     int width;
     int observable;
     int pool;
-    const double *lat_params;  // [n_lat][4]: J, h, N, beta
+    const double *lat_params;  // [n_lat][kLatParams]
     const double *cpm_J;       // [pairs]
     double cpm_lambda, cpm_T;
     int n_pairs;

@@ -78,7 +78,7 @@ extern "C" int spin_ising_sweep_noalloc(uint64_t seed, int32_t n_lattices,
     size_t smem = 16;
     for (int i = 0; i < n_lattices; ++i) {
         const spin_lattice_desc &d = lat[i];
-        if (d.L < 4 || (d.L & 1) || d.L > 4096 || d.geometry != 0) return SPIN_EINVAL;
+        if (d.L < 4 || (d.L & 1) || d.L > 4096 || d.geometry != 0 || d.J2 != 0.0f) return SPIN_EINVAL;
         if (!(d.beta >= 0.0f) || !(d.beta < 3.0e38f) || !(d.J == d.J) || !(d.h == d.h)) return SPIN_EINVAL;
         const bool fast = d.L % 16 == 0 && d.spin_offset % 16 == 0;
         g_lat_stage[i] = LatDev{d.spin_offset, d.L, 2, fast ? 1 : 0, 0};

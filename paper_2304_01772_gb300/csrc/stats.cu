@@ -32,13 +32,13 @@ __device__ __forceinline__ void atomic_add_i64(int64_t *p, long long v) {
 __global__ void stats_state_kernel(const void *spins, int model, const LatDev *lats, int width,
                                    int64_t *out) {
     __shared__ int shist[256];
-    __shared__ long long r0[32], r1[32];
+    __shared__ long long r0[32], r1[32], r2[32];
     const int lat = blockIdx.y;
     const LatDev ld = lats[lat];
     const int L = ld.L;
     for (int k = threadIdx.x; k < 256; k += blockDim.x) shist[k] = 0;
     __syncthreads();
-    long long a0 = 0, a1 = 0;
+    long long a0 = 0, a1 = 0, a2 = 0;
     if (model == 0 && ld.fast && ld.geom == 0) {
         // +-1 bytes (0x01 / 0xFF): bit 7 marks -1, and bit 7 of a ^ b marks a
         // neighbour pair of opposite spins.  16 sites per thread: M = N - 2 n_down,
@@ -77,6 +77,10 @@ __global__ void stats_state_kernel(const void *spins, int model, const LatDev *l
             a1 += s * (S[ir] + S[id]);
             if (ld.geom == 1)   // triangular: the third bond direction (x - 1, y + 1)
                 a1 += s * S[(y == L - 1 ? 0 : y + 1) * L + (x == 0 ? L - 1 : x - 1)];
+            if (ld.geom == 2) {   // diagonal bonds through (x + 1, y + 1) and (x + 1, y - 1)
+                const int xr = x == L - 1 ? 0 : x + 1;
+                a2 += s * (S[(y == L - 1 ? 0 : y + 1) * L + xr] + S[(y == 0 ? L - 1 : y - 1) * L + xr]);
+            }
         } else {
             const uint8_t *S = static_cast<const uint8_t *>(spins) + ld.offset;
             const int s = S[i];
@@ -86,21 +90,25 @@ __global__ void stats_state_kernel(const void *spins, int model, const LatDev *l
     }
     a0 = warp_sum(a0);
     a1 = warp_sum(a1);
+    a2 = warp_sum(a2);
     if ((threadIdx.x & 31) == 0) {
         r0[threadIdx.x >> 5] = a0;
         r1[threadIdx.x >> 5] = a1;
+        r2[threadIdx.x >> 5] = a2;
     }
     __syncthreads();
     int64_t *o = out + (size_t)width * lat;
     if (threadIdx.x == 0) {
-        long long s0 = 0, s1 = 0;
+        long long s0 = 0, s1 = 0, s2 = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
             s0 += r0[w];
             s1 += r1[w];
+            s2 += r2[w];
         }
         if (model == 0) {
             atomic_add_i64(o, s0);
             atomic_add_i64(o + 1, s1);
+            if (width > 2) atomic_add_i64(o + 2, s2);
         } else {
             atomic_add_i64(o, s0);
         }
@@ -279,14 +287,15 @@ __global__ void observables_kernel(const int64_t *ring, int cap, long long first
         const int64_t *row = ring + ((rec % cap) * p.n_lat + lat) * (long long)p.width;
         if (stats_out)
             for (int k = 0; k < p.width; ++k) stats_out[(size_t)idx * p.width + k] = row[k];
-        const double J = p.lat_params[4 * lat], h = p.lat_params[4 * lat + 1];
-        const double N = p.lat_params[4 * lat + 2];
+        const double *lp = p.lat_params + kLatParams * lat;
+        const double J = lp[0], h = lp[1], N = lp[2];
         double e, m;
         if (p.model == 0) {
-            e = (-J * (double)row[1] - h * (double)row[0]) / N;
+            const double b2 = p.width > 2 ? lp[4] * (double)row[2] : 0.0;
+            e = (-J * (double)row[1] - b2 - h * (double)row[0]) / N;
             m = (double)row[0] / N;
         } else if (p.model == 1) {
-            const int q = (int)p.lat_params[4 * lat + 3];
+            const int q = (int)lp[3];
             long long mx = 0;
             for (int k = 0; k < q; ++k) mx = row[1 + k] > mx ? row[1 + k] : mx;
             e = -J * (double)row[0] / N;
@@ -331,23 +340,24 @@ __global__ void grad_kernel(const __int128 *moments, int rows, GradParams p, dou
     const int lat0 = p.pool ? 0 : row;
     const double nd = (double)(long long)mo[0];
     if (p.model == 0) {
-        const double J = p.lat_params[4 * lat0], h = p.lat_params[4 * lat0 + 1];
-        const double N = p.lat_params[4 * lat0 + 2], beta = p.lat_params[4 * lat0 + 3];
-        const double cMM = cov_ij(mo, 2, 0, 0), cMB = cov_ij(mo, 2, 0, 1), cBB = cov_ij(mo, 2, 1, 1);
-        const double meanM = i128_to_double(mo[1]) / nd, meanB = i128_to_double(mo[2]) / nd;
-        double gJ, gh;
-        if (p.observable == 0) {
-            // O = (-J B - h M)/N; dO/dJ = -B/N, dO/dh = -M/N; dH/dJ = -B, dH/dh = -M
-            const double cOB = (-J * cBB - h * cMB) / N, cOM = (-J * cMB - h * cMM) / N;
-            gJ = -meanB / N - beta * (-cOB);
-            gh = -meanM / N - beta * (-cOM);
-        } else {
-            const double cOB = cMB / N, cOM = cMM / N;
-            gJ = -beta * (-cOB);
-            gh = -beta * (-cOM);
+        // X = (M, B[, B2]); theta = (J, h[, J2]) with dH/dtheta = -X_{(1, 0, 2)}.
+        // O = E/N = (-J B - h M - J2 B2)/N (explicit dO/dtheta = -X_theta / N) or M/N.
+        const double *lp = p.lat_params + kLatParams * lat0;
+        const double J = lp[0], h = lp[1], N = lp[2], beta = lp[3], J2 = lp[4];
+        const int xi[3] = {1, 0, 2};
+        for (int j = 0; j < width; ++j) {
+            const int k = xi[j];
+            double cOX;   // Cov(O, X_k)
+            if (p.observable == 0) {
+                cOX = -J * cov_ij(mo, width, 1, k) - h * cov_ij(mo, width, 0, k);
+                if (width > 2) cOX -= J2 * cov_ij(mo, width, 2, k);
+                cOX /= N;
+            } else {
+                cOX = cov_ij(mo, width, 0, k) / N;
+            }
+            const double explicit_term = p.observable == 0 ? -i128_to_double(mo[1 + k]) / nd / N : 0.0;
+            out[(size_t)width * row + j] = explicit_term - beta * (-cOX);
         }
-        out[2 * row] = gJ;
-        out[2 * row + 1] = gh;
     } else {
         const int npair = p.n_pairs;
         const double N = p.lat_params[2], beta = 1.0 / p.cpm_T;
@@ -378,10 +388,11 @@ __global__ void expectations_kernel(const __int128 *moments, int rows, GradParam
     const int lat0 = p.pool ? 0 : row;
     const double nd = (double)(long long)mo[0];
     if (p.model == 0) {
-        const double J = p.lat_params[4 * lat0], h = p.lat_params[4 * lat0 + 1];
-        const double N = p.lat_params[4 * lat0 + 2];
+        const double *lp = p.lat_params + kLatParams * lat0;
+        const double J = lp[0], h = lp[1], N = lp[2];
         const double mM = i128_to_double(mo[1]) / nd, mB = i128_to_double(mo[2]) / nd;
-        out[2 * row] = (-J * mB - h * mM) / N;
+        const double mB2 = width > 2 ? i128_to_double(mo[3]) / nd : 0.0;
+        out[2 * row] = (-J * mB - lp[4] * mB2 - h * mM) / N;
         out[2 * row + 1] = mM / N;
     } else {
         const int npair = p.n_pairs;

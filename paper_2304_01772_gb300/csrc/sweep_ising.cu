@@ -307,6 +307,161 @@ __global__ void __launch_bounds__(kTriResThreads) ising_tri_resident_kernel(Resi
     if (threadIdx.x < 2) a.st.cur[2 * lat + threadIdx.x] = cur_s[threadIdx.x];
 }
 
+// ---------------------------------------------------------------------------
+// Ising with first and second neighbours (geometry 2):
+// H = -J sum_nn s s - J2 sum_diag s s - h sum s.  The eight neighbours of a
+// site carry the three other colours of c = (x & 1) | ((y & 1) << 1), so each
+// colour's sites update at once.  Sites of colour c are (2m + (c & 1),
+// 2Y + (c >> 1)), compressed index k = Y (L/2) + m; the draw of a site is
+// lane k & 3 of Philox group k >> 2.  Statistics (M, B, B2).
+
+// Down spins among the four nearest (d1) and the four diagonal (d2) neighbours.
+__device__ __forceinline__ void nnn_counts(const int8_t *S, int L, int x, int y, int &d1, int &d2) {
+    const int yu = (y == 0 ? L - 1 : y - 1) * L, yc = y * L, yd = (y == L - 1 ? 0 : y + 1) * L;
+    const int xl = x == 0 ? L - 1 : x - 1, xr = x == L - 1 ? 0 : x + 1;
+    d1 = (S[yc + xl] < 0) + (S[yc + xr] < 0) + (S[yu + x] < 0) + (S[yd + x] < 0);
+    d2 = (S[yu + xl] < 0) + (S[yu + xr] < 0) + (S[yd + xl] < 0) + (S[yd + xr] < 0);
+}
+
+// One Philox group (four consecutive compressed sites of colour c) of one
+// lattice: S is read, D written (S == D in place).  copy_block: colour 0 from
+// src to dst, where the thread also copies the three other sites of each of
+// its sites' 2x2 blocks (every block holds one site of each colour).
+template <bool COPY>
+__device__ __forceinline__ void nnn_group(const int8_t *S, int8_t *D, int L, int half, int nk, int g,
+                                          int c, uint4 r, const uint32_t *tab, int &dm, int &db,
+                                          int &db2) {
+    const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+    int Y = (4 * g) / half, m = 4 * g - Y * half;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        if (4 * g + l >= nk) break;
+        if (m == half) {
+            m = 0;
+            ++Y;
+        }
+        const int x = 2 * m + (c & 1), y = 2 * Y + (c >> 1);
+        ++m;
+        int d1, d2;
+        nnn_counts(S, L, x, y, d1, d2);
+        const int i = y * L + x;
+        const int sv = S[i] < 0 ? -1 : 1;
+        if (COPY) {
+            D[i + 1] = S[i + 1];
+            D[i + L] = S[i + L];
+            D[i + L + 1] = S[i + L + 1];
+        }
+        if (rr[l] <= tab[(sv < 0 ? 25 : 0) + 5 * d1 + d2]) {
+            D[i] = (int8_t)(-sv);
+            dm -= 2 * sv;
+            db -= 2 * sv * (4 - 2 * d1);
+            db2 -= 2 * sv * (4 - 2 * d2);
+        } else if (COPY) {
+            D[i] = (int8_t)sv;
+        }
+    }
+}
+
+// Block sum of three per-thread counters into red[3][warps]; thread 0 gets the totals.
+template <int THREADS>
+__device__ __forceinline__ void block_sum3(int a0, int a1, int a2, int *red, long long out[3]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xFFFFFFFFu, a0, o);
+        a1 += __shfl_xor_sync(0xFFFFFFFFu, a1, o);
+        a2 += __shfl_xor_sync(0xFFFFFFFFu, a2, o);
+    }
+    constexpr int W = THREADS / 32;
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = a0;
+        red[W + (threadIdx.x >> 5)] = a1;
+        red[2 * W + (threadIdx.x >> 5)] = a2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out[0] = out[1] = out[2] = 0;
+        for (int w = 0; w < W; ++w) {
+            out[0] += red[w];
+            out[1] += red[W + w];
+            out[2] += red[2 * W + w];
+        }
+    }
+}
+
+constexpr int kNnnThreads = 256;
+
+__global__ void __launch_bounds__(kNnnThreads) ising_nnn_kernel(const int8_t *src, int8_t *dst, const LatDev *lats,
+                                                                const uint32_t *thr, uint32_t k0, uint32_t k1,
+                                                                const DevState *state, int64_t *delta, int c) {
+    __shared__ uint32_t tab[kNnnTab];
+    __shared__ int red[3 * (kNnnThreads / 32)];
+    const int lat = blockIdx.y;
+    const LatDev ld = lats[lat];
+    const int L = ld.L, half = L >> 1, nk = half * half;
+    if (threadIdx.x < kNnnTab) tab[threadIdx.x] = thr[lat * kNnnTab + threadIdx.x];
+    __syncthreads();
+    const int8_t *S = (c == 0 ? src : dst) + ld.offset;
+    int8_t *D = dst + ld.offset;
+    const uint32_t t = state->t;
+    int dm = 0, db = 0, db2 = 0;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; 4 * g < nk; g += gridDim.x * blockDim.x) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)lat, t, (uint32_t)c), k0, k1);
+        if (c == 0)
+            nnn_group<true>(S, D, L, half, nk, g, c, r, tab, dm, db, db2);
+        else
+            nnn_group<false>(S, D, L, half, nk, g, c, r, tab, dm, db, db2);
+    }
+    long long tot[3];
+    block_sum3<kNnnThreads>(dm, db, db2, red, tot);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k)
+            if (tot[k]) atomicAdd(reinterpret_cast<unsigned long long *>(delta + 3 * lat + k), (unsigned long long)tot[k]);
+}
+
+// Resident form: one block per lattice keeps it in shared memory for all
+// sweeps of the call; per sweep four colour passes; records as
+// ising_resident_kernel with three statistics.
+constexpr int kNnnResThreads = 512;
+
+__global__ void __launch_bounds__(kNnnResThreads) ising_nnn_resident_kernel(ResidentArgs a, const uint32_t *thr) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    int8_t *S = reinterpret_cast<int8_t *>(sm);
+    __shared__ uint32_t tab[kNnnTab];
+    __shared__ int red[3 * (kNnnResThreads / 32)];
+    __shared__ long long cur_s[3];
+    const int lat = blockIdx.x;
+    const LatDev ld = a.lats[lat];
+    const int L = ld.L, N = L * L, half = L >> 1, nk = N >> 2;
+    int8_t *G = a.spins + ld.offset;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) S[i] = G[i];
+    if (threadIdx.x < kNnnTab) tab[threadIdx.x] = thr[lat * kNnnTab + threadIdx.x];
+    if (threadIdx.x < 3) cur_s[threadIdx.x] = a.st.cur[3 * lat + threadIdx.x];
+    __syncthreads();
+    for (int sweep = 0; sweep < a.n_sweeps; ++sweep) {
+        const uint32_t t = a.t0 + (uint32_t)sweep;
+        int dm = 0, db = 0, db2 = 0;
+        for (int c = 0; c < 4; ++c) {
+            for (int g = threadIdx.x; 4 * g < nk; g += blockDim.x) {
+                const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)lat, t, (uint32_t)c), a.k0, a.k1);
+                nnn_group<false>(S, S, L, half, nk, g, c, r, tab, dm, db, db2);
+            }
+            __syncthreads();
+        }
+        long long tot[3];
+        block_sum3<kNnnResThreads>(dm, db, db2, red, tot);
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < 3; ++k) cur_s[k] += tot[k];
+            if (a.record && a.st.cap > 0) {
+                const long long slot = (a.rec0 + sweep) % a.st.cap;
+                for (int k = 0; k < 3; ++k) a.st.ring[(slot * a.st.n_lat + lat) * 3 + k] = cur_s[k];
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) G[i] = S[i];
+    if (threadIdx.x < 3) a.st.cur[3 * lat + threadIdx.x] = cur_s[threadIdx.x];
+}
+
 __global__ void advance_state_kernel(DevState *state, uint32_t n, int record) {
     state->t += n;
     if (record) state->n_rec += n;
@@ -871,6 +1026,28 @@ cudaError_t launch_ising_tri(const int8_t *src, int8_t *dst, const int32_t *lat_
     const int blocks = (maxL * maxL + 255) / 256;
     dim3 grid(blocks < 64 ? blocks : 64, n);
     ising_tri_kernel<<<grid, 256, 0, s>>>(src, dst, lat_ids, lats, tabs, k0, k1, state, delta, colour);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ising_nnn(const int8_t *src, int8_t *dst, int n, int maxL, const LatDev *lats,
+                             const uint32_t *thr, uint32_t k0, uint32_t k1, const DevState *state,
+                             int64_t *delta, int colour, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int groups = ((maxL / 2) * (maxL / 2) + 3) / 4;
+    const int blocks = (groups + kNnnThreads - 1) / kNnnThreads;
+    dim3 grid(blocks < 64 ? blocks : 64, n);
+    ising_nnn_kernel<<<grid, kNnnThreads, 0, s>>>(src, dst, lats, thr, k0, k1, state, delta, colour);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ising_nnn_resident(const ResidentArgs &a, const uint32_t *thr, int n_lat, size_t smem,
+                                      DevState *state, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(ising_nnn_resident_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+        return e;
+    ising_nnn_resident_kernel<<<n_lat, kNnnResThreads, smem, s>>>(a, thr);
+    if ((e = cudaGetLastError())) return e;
+    advance_state_kernel<<<1, 1, 0, s>>>(state, (uint32_t)a.n_sweeps, a.record);
     return cudaGetLastError();
 }
 

@@ -12,6 +12,8 @@ Configurations (sizes and parameter ranges of the paper's workloads, Sec.
   uneven512      512 Ising lattices, L = 2^e with e uniform in {5..11},
                  beta ~ U(0.3, 0.55), h ~ N(0, 0.05)
   fit256         128 Ising chains 256x256 at beta = 0.45
+  nnn256         256 Ising lattices 256x256 with first and second neighbours:
+                 J = 1, J2 ~ U(-0.5, 0.5), beta ~ U(0.2, 0.45), h ~ N(0, 0.05)
   cpm1024        cellular Potts 1024x1024, 2000 cells of 20x20 in 50 columns,
                  J = [[0,16,16],[16,2,11],[16,11,14]], A = 400, lambda = 1, T = 10
 """
@@ -74,6 +76,17 @@ def uneven512(n=512, seed=0, emin=5, emax=11):
         beta = 0.3 + 0.25 * r.uniform()
         h = 0.05 * r.normal()
         out.append(dict(L=1 << e, beta=beta, J=1.0, h=h))
+    return out
+
+
+def nnn256(n=256, L=256, seed=0):
+    r = SplitMix64(seed)
+    out = []
+    for _ in range(n):
+        beta = 0.2 + 0.25 * r.uniform()
+        J2 = -0.5 + r.uniform()
+        h = 0.05 * r.normal()
+        out.append(dict(L=L, beta=beta, J=1.0, J2=J2, h=h, geometry=2))
     return out
 
 

@@ -27,7 +27,7 @@ LATS = [dict(L=4, beta=0.3, J=1.0, h=0.0), dict(L=10, beta=0.44, J=-1.0, h=0.1),
 def _descs(lats, offsets):
     arr = (sm.LatticeDesc * len(lats))()
     for i, d in enumerate(lats):
-        arr[i] = sm.LatticeDesc(d["L"], 2, d["beta"], d["J"], d["h"], 0, offsets[i])
+        arr[i] = sm.LatticeDesc(d["L"], 2, d["beta"], d["J"], d["h"], 0, 0.0, offsets[i])
     return arr
 
 
