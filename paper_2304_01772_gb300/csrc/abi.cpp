@@ -92,13 +92,16 @@ struct spin_ctx {
     int32_t *d_J = nullptr;
     int32_t *d_vol[2] = {nullptr, nullptr};   // CPM areas: [0] after a Monte Carlo step, [1] alternate
     int32_t *d_dvol[2] = {nullptr, nullptr};  // CPM area changes of the last two sub-steps
+    int64_t *d_cpm_acc = nullptr;             // CPM persistent form: contact changes per step parity
+    unsigned int *d_cpm_bar = nullptr;        // CPM persistent form: grid barrier words
+    int cpm_grid = 0;                         // blocks of the CPM persistent form (0: unavailable)
     uint32_t *d_thr = nullptr;
     int n_thr = 0;
     double *d_latp = nullptr;   // [n_lat][kLatParams]
     double *d_cpmJ = nullptr;   // [pairs]
     void *d_scratch = nullptr;  // moments etc.
     size_t scratch_bytes = 0;
-    int *d_flag = nullptr;
+    int *d_flag = nullptr;      // [0] moment overflow, [1] a device wait gave up
     // host mirrors
     uint32_t t = 0;
     int64_t n_rec = 0;
@@ -621,9 +624,30 @@ int get_graph(spin_ctx *ctx, int record, GraphCache *&out) {
 
 int run_sweeps(spin_ctx *ctx, int n, int record, cudaStream_t s) {
     int launches = 0;
+    if (ctx->model == SPIN_CPM && ctx->mode == 2) {
+        CpmPersistArgs p{};
+        p.a = CpmArgs{static_cast<int32_t *>(ctx->spins), ctx->lat[0].L, 0u, ctx->d_type, ctx->d_J, ctx->n_types,
+                      ctx->n_cells, ctx->lambda, ctx->target, nullptr, nullptr, nullptr, nullptr, ctx->d_thr,
+                      ctx->n_thr, ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta};
+        p.vol[0] = ctx->d_vol[0];
+        p.vol[1] = ctx->d_vol[1];
+        p.dvol[0] = ctx->d_dvol[0];
+        p.dvol[1] = ctx->d_dvol[1];
+        p.n_steps = n;
+        p.t0 = ctx->t;
+        p.rec0 = (long long)ctx->n_rec;
+        p.record = record;
+        p.st = ctx->st;
+        p.acc = ctx->d_cpm_acc;
+        p.bar = ctx->d_cpm_bar;
+        p.err = ctx->d_flag + 1;
+        CK(launch_cpm_persistent(p, ctx->cpm_grid, ctx->d_state, s));
+        ctx->last_launches = 2;
+        return SPIN_OK;
+    }
     if (ctx->mode == 2) {
         ResidentArgs a{static_cast<int8_t *>(ctx->spins), ctx->d_lats, ctx->d_tabs, ctx->k0, ctx->k1,
-                       ctx->t, n, (long long)ctx->n_rec, record, ctx->st};
+                       ctx->t, n, (long long)ctx->n_rec, record, ctx->st, philox_keys(ctx->k0, ctx->k1)};
         if (ctx->n_nnn == ctx->n_lat)
             CK(launch_ising_nnn_resident(a, ctx->d_nnn_thr, ctx->n_lat, (size_t)ctx->maxL * ctx->maxL,
                                          ctx->d_state, s));
@@ -756,7 +780,7 @@ void spin_destroy(spin_ctx *ctx) {
                     ctx->d_dvol[0], ctx->d_dvol[1],
                     ctx->d_state, ctx->st.cur, ctx->st.delta, ctx->st.ring, ctx->d_type,
                     ctx->d_J, ctx->d_vol[0], ctx->d_vol[1], ctx->d_thr, ctx->d_latp,
-                    ctx->d_cpmJ, ctx->d_scratch, ctx->d_flag};
+                    ctx->d_cpmJ, ctx->d_scratch, ctx->d_flag, ctx->d_cpm_acc, ctx->d_cpm_bar};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -845,7 +869,7 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
         !ckm(cudaMalloc(&ctx->st.delta, sizeof(int64_t) * w * n_lattices)) ||
         !ckm(cudaMalloc(&ctx->d_latp, sizeof(double) * kLatParams * n_lattices)) ||
         !ckm(cudaMalloc(&ctx->d_cpmJ, sizeof(double) * 64)) ||
-        !ckm(cudaMalloc(&ctx->d_flag, sizeof(int))) ||
+        !ckm(cudaMalloc(&ctx->d_flag, 2 * sizeof(int))) || !ckm(cudaMemset(ctx->d_flag, 0, 2 * sizeof(int))) ||
         (max_record_sweeps > 0 &&
          !ckm(cudaMalloc(&ctx->st.ring, sizeof(int64_t) * w * n_lattices * (size_t)max_record_sweeps))))
         return bail(fail(ctx, SPIN_ENOMEM, "device allocation failed"));
@@ -876,8 +900,13 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
             !ckm(cudaMalloc(&ctx->d_vol[0], sizeof(int32_t) * (nc + 1))) ||
             !ckm(cudaMalloc(&ctx->d_vol[1], sizeof(int32_t) * (nc + 1))) ||
             !ckm(cudaMalloc(&ctx->d_dvol[0], sizeof(int32_t) * (nc + 1))) ||
-            !ckm(cudaMalloc(&ctx->d_dvol[1], sizeof(int32_t) * (nc + 1))))
+            !ckm(cudaMalloc(&ctx->d_dvol[1], sizeof(int32_t) * (nc + 1))) ||
+            !ckm(cudaMalloc(&ctx->d_cpm_acc, sizeof(int64_t) * 2 * kCpmAccStride)) ||
+            !ckm(cudaMemset(ctx->d_cpm_acc, 0, sizeof(int64_t) * 2 * kCpmAccStride)) ||
+            !ckm(cudaMalloc(&ctx->d_cpm_bar, 2 * sizeof(unsigned int))))
             return bail(SPIN_ENOMEM);
+        // the persistent form (one cooperative launch per call): launch mode 2
+        ctx->cpm_grid = cpm_persistent_grid();
     }
     rc = upload_tables(ctx, s);
     if (rc) return bail(rc);
@@ -968,7 +997,12 @@ int spin_observables(spin_ctx *ctx, int64_t first, int32_t n, int64_t *stats, fl
     if (!dev_s) CK(cudaMemcpyAsync(stats, ts, sizeof(int64_t) * ns, cudaMemcpyDeviceToHost, s));
     if (!dev_e) CK(cudaMemcpyAsync(E, te, sizeof(float) * nf, cudaMemcpyDeviceToHost, s));
     if (!dev_m) CK(cudaMemcpyAsync(M, tm, sizeof(float) * nf, cudaMemcpyDeviceToHost, s));
-    if (!dev_s || !dev_e || !dev_m) CK(cudaStreamSynchronize(s));
+    if (!dev_s || !dev_e || !dev_m) {
+        int timed_out = 0;
+        CK(cudaMemcpyAsync(&timed_out, ctx->d_flag + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (timed_out) return fail(ctx, SPIN_ETIMEOUT, "a device-side wait of a sweep gave up");
+    }
     return SPIN_OK;
 }
 
@@ -1003,11 +1037,12 @@ int spin_moments(spin_ctx *ctx, int64_t first, int32_t n, int64_t *moments, void
     int64_t *t = dev ? moments : reinterpret_cast<int64_t *>(static_cast<char *>(ctx->d_scratch) + 16 * cnt);
     CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
     CK(launch_i128_to_i64(ctx->d_scratch, t, (int)cnt, ctx->d_flag, s));
-    int flag = 0;
-    CK(cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int flag[2] = {0, 0};
+    CK(cudaMemcpyAsync(flag, ctx->d_flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     if (!dev) CK(cudaMemcpyAsync(moments, t, sizeof(int64_t) * cnt, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (flag) return fail(ctx, SPIN_EINVAL, "a moment does not fit in int64");
+    if (flag[1]) return fail(ctx, SPIN_ETIMEOUT, "a device-side wait of a sweep gave up");
+    if (flag[0]) return fail(ctx, SPIN_EINVAL, "a moment does not fit in int64");
     return SPIN_OK;
 }
 
@@ -1152,6 +1187,7 @@ int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_
 }
 
 static bool resident_ok(const spin_ctx *ctx) {
+    if (ctx->model == SPIN_CPM) return ctx->cpm_grid > 0;   // the persistent cooperative form
     if (ctx->model != SPIN_ISING || ctx->n_generic) return false;
     if (ctx->n_nnn) {   // first and second neighbours (a context holds only these)
         for (const auto &d : ctx->lat)
@@ -1174,8 +1210,9 @@ int spin_set_launch(spin_ctx *ctx, int32_t mode, int32_t use_graph, int32_t tile
     if (mode < 0 || mode > 2) return fail(ctx, SPIN_EINVAL, "launch mode must be 0, 1 or 2");
     if (mode == 2 && !resident_ok(ctx))
         return fail(ctx, SPIN_EINVAL, "resident form needs Ising lattices with L % 16 == 0 and L <= 256, "
-                                      "only triangular lattices with L <= 240, or second-neighbour "
-                                      "lattices with L <= 256");
+                                      "only triangular lattices with L <= 240, only second-neighbour "
+                                      "lattices with L <= 256, or a CPM context on a device with "
+                                      "cooperative launch");
     if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
         return fail(ctx, SPIN_EINVAL, "threads must be 128, 256 or 512");
     if (tile_rows < -1) return fail(ctx, SPIN_EINVAL, "tile_rows must be >= -1");

@@ -140,6 +140,7 @@ struct ResidentArgs {
     long long rec0;
     int record;
     StatsBufs st;
+    PhiloxKeys rk;   // round keys of (k0, k1)
 };
 cudaError_t launch_ising_resident(const ResidentArgs &a, int n_lat, int threads, size_t smem,
                                   DevState *state, cudaStream_t s);
@@ -222,6 +223,29 @@ struct CpmArgs {
     int64_t *delta;          // [pairs] contact changes
 };
 cudaError_t launch_cpm_substep(const CpmArgs &a, int colour, cudaStream_t s);
+// Persistent form: n_steps Monte Carlo steps in one cooperative launch (grid
+// barriers between sub-steps), then the device counters advance.  a.vol_*,
+// a.dvol_* and a.state are unused; contact changes go to acc[step & 1]
+// ([2][kCpmAccStride] int64, zero on entry and on return); bar: two words,
+// cleared by the launcher; err: set to 1 if a barrier wait ran out.
+constexpr int kCpmAccStride = 64;
+struct CpmPersistArgs {
+    CpmArgs a;
+    int32_t *vol[2];
+    int32_t *dvol[2];
+    int n_steps;
+    uint32_t t0;
+    long long rec0;
+    int record;
+    StatsBufs st;
+    int64_t *acc;
+    unsigned int *bar;
+    int *err;
+};
+// Blocks that a cooperative launch of the persistent kernel may use (0: the
+// device has no cooperative launch).
+int cpm_persistent_grid();
+cudaError_t launch_cpm_persistent(const CpmPersistArgs &p, int max_grid, DevState *state, cudaStream_t s);
 
 // Differentiable Monte Carlo (Alg. 2): relaxed sweeps with one coupling per
 // bond.  spins [n_lat][L*L]; J [n_lat][2][L*L] (right, down bonds); tape

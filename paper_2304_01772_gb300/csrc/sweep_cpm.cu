@@ -45,18 +45,41 @@ constexpr int kCpmQueue = 2 * kCpmThreads * kCpmGroupsPerThread;
 
 __device__ __forceinline__ int wrapc(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
 
-__global__ void __launch_bounds__(kCpmThreads) cpm_substep_kernel(CpmArgs a, int c) {
-    __shared__ int sJ[64];
-    __shared__ int scnt[36];
-    __shared__ int4 queue[kCpmQueue];   // (y << 16 | x, id of the site, id copied in, u0)
-    __shared__ int qn;
-    const int nt = a.n_types;
-    for (int k = threadIdx.x; k < nt * nt; k += blockDim.x) sJ[k] = a.J[k];
-    for (int k = threadIdx.x; k < 36; k += blockDim.x) scnt[k] = 0;
-    if (threadIdx.x == 0) qn = 0;
+// Shared-memory working set of one block of the sub-step.
+struct CpmShared {
+    int sJ[64];
+    int scnt[36];                 // contact changes of this block, per type pair
+    int4 queue[kCpmQueue];        // (y << 16 | x, id of the site, id copied in, u0)
+    int qn;
+};
+
+// Load J and clear the block's contact counters.
+__device__ __forceinline__ void cpm_block_setup(const CpmArgs &a, CpmShared &sh) {
+    for (int k = threadIdx.x; k < a.n_types * a.n_types; k += blockDim.x) sh.sJ[k] = a.J[k];
+    for (int k = threadIdx.x; k < 36; k += blockDim.x) sh.scnt[k] = 0;
+    if (threadIdx.x == 0) sh.qn = 0;
     __syncthreads();
+}
+
+// Add the block's contact changes to out[pair] and clear them.
+__device__ __forceinline__ void cpm_block_flush(const CpmArgs &a, CpmShared &sh, int64_t *out) {
+    __syncthreads();
+    const int npair = a.n_types * (a.n_types + 1) / 2;
+    for (int k = threadIdx.x; k < npair; k += blockDim.x)
+        if (sh.scnt[k]) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(out + k), (unsigned long long)(long long)sh.scnt[k]);
+            sh.scnt[k] = 0;
+        }
+    __syncthreads();
+}
+
+// One colour sub-step of sweep t over this block's share of the Philox groups.
+__device__ void cpm_substep_body(const CpmArgs &a, int c, uint32_t t, CpmShared &sh) {
+    int *sJ = sh.sJ, *scnt = sh.scnt;
+    int4 *queue = sh.queue;
+    int &qn = sh.qn;
+    const int nt = a.n_types;
     const int L = a.L, Lq = L >> 2;
-    const uint32_t t = a.state->t;
     const int cx = c & 1, cy = c >> 1;
     const int n_groups = (L >> 1) * Lq;
     const int per_pass = kCpmThreads * kCpmGroupsPerThread;
@@ -154,9 +177,138 @@ __global__ void __launch_bounds__(kCpmThreads) cpm_substep_kernel(CpmArgs a, int
         if (threadIdx.x == 0) qn = 0;
         __syncthreads();
     }
-    const int npair = nt * (nt + 1) / 2;
-    for (int k = threadIdx.x; k < npair; k += blockDim.x)
-        if (scnt[k]) atomicAdd(reinterpret_cast<unsigned long long *>(a.delta + k), (unsigned long long)(long long)scnt[k]);
+}
+
+__global__ void __launch_bounds__(kCpmThreads) cpm_substep_kernel(CpmArgs a, int c) {
+    __shared__ CpmShared sh;
+    cpm_block_setup(a, sh);
+    cpm_substep_body(a, c, a.state->t, sh);
+    cpm_block_flush(a, sh, a.delta);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent form: every Monte Carlo step of a call in one cooperative launch
+// (all blocks resident), the four sub-steps separated by grid barriers instead
+// of kernel boundaries.  Block 0 finishes step s (V2, V1, contacts, record)
+// at the start of step s + 1: sub-step 0 of s + 1 only reads the areas V[0]
+// that the finish reads, and its contact changes go to the other of two
+// accumulators (acc[(s + 1) & 1]), so the barrier that ends sub-step 0 orders
+// the finish before anything it reads is written again.
+
+__device__ __forceinline__ uint64_t cpm_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t kCpmWaitNs = 1000000000ull;   // a barrier wait gives up after 1 s
+
+// Grid barrier: bar[0] counts arrivals, bar[1] is the generation.  Thread 0
+// of each block reads the generation, arrives, and the last arrival resets
+// the count and advances the generation; the others wait (bounded) for the
+// advance.  False (for the whole block) if a wait ran out or another block
+// has reported one in *err.
+__device__ bool cpm_grid_sync(unsigned int *bar, int *err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = bar + 1;
+        const unsigned int gen = *vgen;
+        int good = 1;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const uint64_t t0 = cpm_ns();
+            while (*vgen == gen) {
+                if (cpm_ns() - t0 > kCpmWaitNs) {
+                    atomicExch(err, 1);
+                    good = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        if (*(volatile int *)err) good = 0;
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Statistics after a step (block-wide): V2, V1 from the areas, contacts
+// cur += acc (acc cleared), and the record.
+__device__ void cpm_finish_step(const int32_t *vol, int n_cells, int target, const StatsBufs &st, int64_t *acc,
+                                int record, long long rec) {
+    __shared__ long long r2[kCpmThreads / 32], r1[kCpmThreads / 32];
+    long long v2 = 0, v1 = 0;
+    for (int k = 1 + threadIdx.x; k <= n_cells; k += blockDim.x) {
+        const long long d = (long long)vol[k] - target;
+        v2 += d * d;
+        v1 += d;
+    }
+    const int npair = st.width - 2;
+    for (int k = threadIdx.x; k < npair; k += blockDim.x) {
+        st.cur[k] += acc[k];
+        acc[k] = 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v2 += __shfl_xor_sync(0xFFFFFFFFu, v2, o);
+        v1 += __shfl_xor_sync(0xFFFFFFFFu, v1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        r2[threadIdx.x >> 5] = v2;
+        r1[threadIdx.x >> 5] = v1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long a2 = 0, a1 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a2 += r2[w];
+            a1 += r1[w];
+        }
+        st.cur[npair] = a2;
+        st.cur[npair + 1] = a1;
+    }
+    __syncthreads();
+    if (record && st.cap > 0) {
+        const long long slot = rec % st.cap;
+        for (int k = threadIdx.x; k < st.width; k += blockDim.x) st.ring[slot * st.width + k] = st.cur[k];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kCpmThreads) cpm_persistent_kernel(CpmPersistArgs p) {
+    __shared__ CpmShared sh;
+    CpmArgs a = p.a;
+    cpm_block_setup(a, sh);
+    for (int step = 0; step < p.n_steps; ++step) {
+        const uint32_t t = p.t0 + (uint32_t)step;
+        for (int c = 0; c < 4; ++c) {
+            if (c == 0 && step > 0 && blockIdx.x == 0)
+                cpm_finish_step(p.vol[0], a.n_cells, a.target, p.st, p.acc + kCpmAccStride * ((step - 1) & 1),
+                                p.record, p.rec0 + step - 1);
+            a.vol_cur = p.vol[c & 1];
+            a.vol_next = p.vol[(c + 1) & 1];
+            a.dvol_cur = p.dvol[c & 1];
+            a.dvol_prev = p.dvol[(c + 1) & 1];
+            cpm_substep_body(a, c, t, sh);
+            cpm_block_flush(a, sh, p.acc + kCpmAccStride * (step & 1));
+            if (!cpm_grid_sync(p.bar, p.err)) return;
+        }
+    }
+    if (blockIdx.x == 0 && p.n_steps > 0)
+        cpm_finish_step(p.vol[0], a.n_cells, a.target, p.st, p.acc + kCpmAccStride * ((p.n_steps - 1) & 1),
+                        p.record, p.rec0 + p.n_steps - 1);
+}
+
+__global__ void cpm_advance_kernel(DevState *state, uint32_t n, int record) {
+    state->t += n;
+    if (record) state->n_rec += n;
 }
 
 // After the four sub-steps of a Monte Carlo step: contacts cur += delta, V2
@@ -465,6 +617,30 @@ cudaError_t launch_cpm_substep(const CpmArgs &a, int colour, cudaStream_t s) {
     int blocks = (n_groups + per_pass - 1) / per_pass;
     if (blocks > 152 * 8) blocks = 152 * 8;
     cpm_substep_kernel<<<blocks, kCpmThreads, 0, s>>>(a, colour);
+    return cudaGetLastError();
+}
+
+int cpm_persistent_grid() {
+    int occ = 0, sms = 0, dev = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cpm_persistent_kernel, kCpmThreads, 0))
+        return 0;
+    return occ * sms;
+}
+
+cudaError_t launch_cpm_persistent(const CpmPersistArgs &p, int max_grid, DevState *state, cudaStream_t s) {
+    const int n_groups = (p.a.L >> 1) * (p.a.L >> 2);
+    const int per_pass = kCpmThreads * kCpmGroupsPerThread;
+    const int grid = std::max(1, std::min(max_grid, (n_groups + per_pass - 1) / per_pass));
+    cudaError_t e = cudaMemsetAsync(p.bar, 0, 2 * sizeof(unsigned int), s);
+    if (e) return e;
+    CpmPersistArgs q = p;
+    void *args[] = {&q};
+    e = cudaLaunchCooperativeKernel((const void *)cpm_persistent_kernel, dim3(grid), dim3(kCpmThreads), args, 0, s);
+    if (e) return e;
+    cpm_advance_kernel<<<1, 1, 0, s>>>(state, (uint32_t)p.n_steps, p.record);
     return cudaGetLastError();
 }
 

@@ -362,6 +362,58 @@ __device__ __forceinline__ void nnn_group(const int8_t *S, int8_t *D, int L, int
     }
 }
 
+// Per-byte down indicators (bit 7 of a +-1 byte) of eight sites.
+__device__ __forceinline__ uint64_t down8(uint64_t w) { return (w >> 7) & 0x0101010101010101ull; }
+
+// Lane p of the result: down(p - 1) + down(p + 1) within the word, with the
+// indicator de of the byte just outside it (left of lane 0 for CX = 0, right
+// of lane 7 for CX = 1), the one edge the sites of lanes CX + 2j need.
+template <int CX>
+__device__ __forceinline__ uint64_t horiz8(uint64_t D, uint32_t de) {
+    return (D << 8) + (D >> 8) + (CX ? (uint64_t)de << 56 : (uint64_t)de);
+}
+
+// nnn_group for a lattice in shared memory with L % 8 == 0, in place: the
+// group's four sites are lanes CX, CX + 2, CX + 4, CX + 6 of one 8-byte word
+// of row y, so three word loads (rows y - 1, y, y + 1) and three edge bytes
+// give every neighbour; per lane the table key 25 cdown + 5 d1 + d2 (<= 49)
+// is formed bytewise without carries.  Accepted flips are one xor with 0xFE
+// per byte (0x01 <-> 0xFF) and one store of the word, which no other thread
+// of this colour pass reads or writes except for unchanged bytes.  ss, sd1,
+// sd2 accumulate s, s d1, s d2 over accepted sites (s the old spin).
+template <int CX>
+__device__ __forceinline__ void nnn_group8(int8_t *S, int L, int half, int g, int cy, uint4 r,
+                                           const uint32_t *tab, int &ss, int &sd1, int &sd2) {
+    const int Y = (4 * g) / half, m0 = 4 * g - Y * half;
+    const int y = 2 * Y + cy, base = 2 * m0;
+    const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
+    const int xe = CX ? (base + 8 == L ? 0 : base + 8) : (base == 0 ? L - 1 : base - 1);
+    int8_t *r0 = S + y * L;
+    const int8_t *rm = S + yu * L, *rp = S + yd * L;
+    const uint64_t W0 = *reinterpret_cast<const uint64_t *>(r0 + base);
+    const uint64_t Dm = down8(*reinterpret_cast<const uint64_t *>(rm + base));
+    const uint64_t D0 = down8(W0);
+    const uint64_t Dp = down8(*reinterpret_cast<const uint64_t *>(rp + base));
+    const uint64_t Hm = horiz8<CX>(Dm, rm[xe] < 0), H0 = horiz8<CX>(D0, r0[xe] < 0);
+    const uint64_t Hp = horiz8<CX>(Dp, rp[xe] < 0);
+    const uint64_t A1 = H0 + Dm + Dp, A2 = Hm + Hp;       // d1, d2 per lane (<= 4)
+    const uint64_t K = (A1 << 2) + A1 + A2 + D0 * 25u;     // 25 cdown + 5 d1 + d2
+    const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
+    uint64_t flip = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int p = 8 * (CX + 2 * j);
+        if (rr[j] <= tab[(uint32_t)(K >> p) & 0xFFu]) {
+            flip |= 0xFEull << p;
+            const int sv = 1 - 2 * (int)((D0 >> p) & 1u);
+            ss += sv;
+            sd1 += sv * (int)((A1 >> p) & 0xFFu);
+            sd2 += sv * (int)((A2 >> p) & 0xFFu);
+        }
+    }
+    if (flip) *reinterpret_cast<uint64_t *>(r0 + base) = W0 ^ flip;
+}
+
 // Block sum of three per-thread counters into red[3][warps]; thread 0 gets the totals.
 template <int THREADS>
 __device__ __forceinline__ void block_sum3(int a0, int a1, int a2, int *red, long long out[3]) {
@@ -440,12 +492,31 @@ __global__ void __launch_bounds__(kNnnResThreads) ising_nnn_resident_kernel(Resi
     for (int sweep = 0; sweep < a.n_sweeps; ++sweep) {
         const uint32_t t = a.t0 + (uint32_t)sweep;
         int dm = 0, db = 0, db2 = 0;
-        for (int c = 0; c < 4; ++c) {
-            for (int g = threadIdx.x; 4 * g < nk; g += blockDim.x) {
-                const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)lat, t, (uint32_t)c), a.k0, a.k1);
-                nnn_group<false>(S, S, L, half, nk, g, c, r, tab, dm, db, db2);
+        if ((L & 7) == 0) {
+            int ss = 0, sd1 = 0, sd2 = 0;
+            for (int c = 0; c < 4; ++c) {
+                const PhiloxPrefix P = philox_prefix((uint32_t)lat, t, (uint32_t)c, a.rk);
+                for (int g = threadIdx.x; 4 * g < nk; g += blockDim.x) {
+                    const uint4 r = philox_from_prefix((uint32_t)g, P, a.rk);
+                    if (c & 1)
+                        nnn_group8<1>(S, L, half, g, c >> 1, r, tab, ss, sd1, sd2);
+                    else
+                        nnn_group8<0>(S, L, half, g, c >> 1, r, tab, ss, sd1, sd2);
+                }
+                __syncthreads();
             }
-            __syncthreads();
+            // dM = -2 s, dB = -2 s (4 - 2 d1), dB2 = -2 s (4 - 2 d2) per accepted site
+            dm = -2 * ss;
+            db = -8 * ss + 4 * sd1;
+            db2 = -8 * ss + 4 * sd2;
+        } else {
+            for (int c = 0; c < 4; ++c) {
+                for (int g = threadIdx.x; 4 * g < nk; g += blockDim.x) {
+                    const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)lat, t, (uint32_t)c), a.k0, a.k1);
+                    nnn_group<false>(S, S, L, half, nk, g, c, r, tab, dm, db, db2);
+                }
+                __syncthreads();
+            }
         }
         long long tot[3];
         block_sum3<kNnnResThreads>(dm, db, db2, red, tot);

@@ -252,11 +252,11 @@ def oracle_cpm(p):
                       T=p["T"], side=p["side"], cols=p["cols"])
 
 
-@pytest.mark.parametrize("graph", [True, False])
-def test_cpm_paper_setup_matches_oracle(graph):
+@pytest.mark.parametrize("mode,graph", [(0, True), (0, False), (2, True)])
+def test_cpm_paper_setup_matches_oracle(mode, graph):
     p = wl.cpm_paper()
     sim = cpm_sim(p)
-    sim.set_launch(0, graph)
+    sim.set_launch(mode, graph)
     op = oracle_cpm(p)
     ids, types, vol = op.init(SEED, 0)
     ids = ids.copy()
@@ -279,6 +279,26 @@ def test_cpm_full_size_two_steps_and_gradient():
     assert np.array_equal(lattice_np(sim, 0), ids)
     st = sim.observables_host(0, 2)[0]
     assert np.array_equal(st[:, 0, :], ref)
+
+
+def test_cpm_launch_forms_hand_over_the_chain():
+    """Persistent (one cooperative launch per call, grid barriers between the
+    sub-steps) and per-sub-step launches alternate within one chain: the
+    areas, their pending changes, the contact counters and the records carry
+    over, so the chain is the oracle's throughout."""
+    p = wl.cpm1024()
+    sim = cpm_sim(p)
+    op = oracle_cpm(p)
+    ids, types, vol = op.init(SEED, 0)
+    ids = ids.copy()
+    for mode, n in [(2, 2), (0, 1), (2, 3), (0, 2)]:
+        sim.set_launch(mode, True)
+        sim.sweep(n, record=True)
+    ref = op.run(ids, vol, types, SEED, 0, 0, 8)
+    assert np.array_equal(lattice_np(sim, 0), ids)
+    st = sim.observables_host(0, 8)[0]
+    assert np.array_equal(st[:, 0, :], ref)
+    assert np.array_equal(sim.current_stats().cpu().numpy()[0], ref[-1])
 
 
 # --------------------------------------------------------------- gradients
