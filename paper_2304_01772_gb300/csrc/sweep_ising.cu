@@ -373,19 +373,23 @@ __device__ __forceinline__ uint64_t horiz8(uint64_t D, uint32_t de) {
     return (D << 8) + (D >> 8) + (CX ? (uint64_t)de << 56 : (uint64_t)de);
 }
 
+// Sum of the eight bytes of x.
+__device__ __forceinline__ uint32_t byte_sum8(uint64_t x) {
+    return __dp4a((uint32_t)x, 0x01010101u, __dp4a((uint32_t)(x >> 32), 0x01010101u, 0u));
+}
+
 // nnn_group for a lattice in shared memory with L % 8 == 0, in place: the
-// group's four sites are lanes CX, CX + 2, CX + 4, CX + 6 of one 8-byte word
-// of row y, so three word loads (rows y - 1, y, y + 1) and three edge bytes
-// give every neighbour; per lane the table key 25 cdown + 5 d1 + d2 (<= 49)
-// is formed bytewise without carries.  Accepted flips are one xor with 0xFE
-// per byte (0x01 <-> 0xFF) and one store of the word, which no other thread
-// of this colour pass reads or writes except for unchanged bytes.  ss, sd1,
-// sd2 accumulate s, s d1, s d2 over accepted sites (s the old spin).
+// group's four sites are lanes CX, CX + 2, CX + 4, CX + 6 of the 8-byte word
+// at column base of row y, so three word loads (rows y - 1, y, y + 1) and
+// three edge bytes give every neighbour; per lane the table key
+// 25 cdown + 5 d1 + d2 (<= 49) is formed bytewise without carries.  Accepted
+// flips are one xor with 0xFE per byte (0x01 <-> 0xFF) and one store of the
+// word, which no other thread of this colour pass reads or writes except for
+// unchanged bytes.  ss, sd1, sd2 accumulate s, s d1, s d2 over accepted sites
+// (s the old spin), from byte masks of the accepted and the accepted-down lanes.
 template <int CX>
-__device__ __forceinline__ void nnn_group8(int8_t *S, int L, int half, int g, int cy, uint4 r,
-                                           const uint32_t *tab, int &ss, int &sd1, int &sd2) {
-    const int Y = (4 * g) / half, m0 = 4 * g - Y * half;
-    const int y = 2 * Y + cy, base = 2 * m0;
+__device__ __forceinline__ void nnn_group8(int8_t *S, int L, int y, int base, uint4 r, const uint32_t *tab,
+                                           int &ss, int &sd1, int &sd2) {
     const int yu = y == 0 ? L - 1 : y - 1, yd = y == L - 1 ? 0 : y + 1;
     const int xe = CX ? (base + 8 == L ? 0 : base + 8) : (base == 0 ? L - 1 : base - 1);
     int8_t *r0 = S + y * L;
@@ -399,19 +403,20 @@ __device__ __forceinline__ void nnn_group8(int8_t *S, int L, int half, int g, in
     const uint64_t A1 = H0 + Dm + Dp, A2 = Hm + Hp;       // d1, d2 per lane (<= 4)
     const uint64_t K = (A1 << 2) + A1 + A2 + D0 * 25u;     // 25 cdown + 5 d1 + d2
     const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
-    uint64_t flip = 0;
+    uint64_t accm = 0;                                     // 0xFF in the accepted lanes
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int p = 8 * (CX + 2 * j);
-        if (rr[j] <= tab[(uint32_t)(K >> p) & 0xFFu]) {
-            flip |= 0xFEull << p;
-            const int sv = 1 - 2 * (int)((D0 >> p) & 1u);
-            ss += sv;
-            sd1 += sv * (int)((A1 >> p) & 0xFFu);
-            sd2 += sv * (int)((A2 >> p) & 0xFFu);
-        }
+        if (rr[j] <= tab[(uint32_t)(K >> p) & 0xFFu]) accm |= 0xFFull << p;
     }
-    if (flip) *reinterpret_cast<uint64_t *>(r0 + base) = W0 ^ flip;
+    if (accm) {
+        *reinterpret_cast<uint64_t *>(r0 + base) = W0 ^ (accm & 0xFEFEFEFEFEFEFEFEull);
+        const uint64_t dn = accm & (D0 * 0xFFu);           // accepted lanes whose spin was down
+        const int na = __popcll(accm) >> 3, nd = __popcll(dn) >> 3;
+        ss += na - 2 * nd;
+        sd1 += (int)byte_sum8(A1 & accm) - 2 * (int)byte_sum8(A1 & dn);
+        sd2 += (int)byte_sum8(A2 & accm) - 2 * (int)byte_sum8(A2 & dn);
+    }
 }
 
 // Block sum of three per-thread counters into red[3][warps]; thread 0 gets the totals.
@@ -493,15 +498,28 @@ __global__ void __launch_bounds__(kNnnResThreads) ising_nnn_resident_kernel(Resi
         const uint32_t t = a.t0 + (uint32_t)sweep;
         int dm = 0, db = 0, db2 = 0;
         if ((L & 7) == 0) {
+            // group g of a colour: row pair Y = g / gpr, first column 8 (g % gpr);
+            // the thread's groups advance by blockDim.x without a division
+            const int gpr = L >> 3;
+            const int Y0 = (int)threadIdx.x / gpr, q0 = (int)threadIdx.x - Y0 * gpr;
+            const int dY = (int)blockDim.x / gpr, dq = (int)blockDim.x - dY * gpr;
             int ss = 0, sd1 = 0, sd2 = 0;
             for (int c = 0; c < 4; ++c) {
                 const PhiloxPrefix P = philox_prefix((uint32_t)lat, t, (uint32_t)c, a.rk);
+                int Y = Y0, q = q0;
                 for (int g = threadIdx.x; 4 * g < nk; g += blockDim.x) {
                     const uint4 r = philox_from_prefix((uint32_t)g, P, a.rk);
+                    const int y = 2 * Y + (c >> 1);
                     if (c & 1)
-                        nnn_group8<1>(S, L, half, g, c >> 1, r, tab, ss, sd1, sd2);
+                        nnn_group8<1>(S, L, y, 8 * q, r, tab, ss, sd1, sd2);
                     else
-                        nnn_group8<0>(S, L, half, g, c >> 1, r, tab, ss, sd1, sd2);
+                        nnn_group8<0>(S, L, y, 8 * q, r, tab, ss, sd1, sd2);
+                    Y += dY;
+                    q += dq;
+                    if (q >= gpr) {
+                        q -= gpr;
+                        ++Y;
+                    }
                 }
                 __syncthreads();
             }

@@ -210,3 +210,34 @@ def test_fused_spin_iteration_equals_the_separate_calls(L, K):
     eb = b.dmc(4, beta=2.0, alpha=10.0, sweeps=K, fused=False)
     assert torch.equal(a.spins, b.spins)
     np.testing.assert_array_equal(ea, eb)
+
+
+def test_benchmark_shape_sampled():
+    """The benchmark's shape (1024 lattices of 64^2, one relaxed sweep per
+    iteration) in the fused launch it times: equal bit for bit to the separate
+    calls at full size, and the relaxed forward pass of sampled lattices within
+    the oracle's tolerance above."""
+    B, L, K = 1024, 64, 1
+    rng = np.random.default_rng(2024)
+    target = torch.from_numpy(rng.choice([-1.0, 1.0], size=(B, L, L)).astype(np.float32)).cuda()
+    start = torch.from_numpy(rng.choice([-1.0, 1.0], size=(B, L, L)).astype(np.float32)).cuda()
+    runs = []
+    for fused in (True, False):
+        opt = pdmc.PatternOptimizer(target, beta=1 / 0.9, alpha=10.0, sweeps=K, seed=7, lr=5e-2, spins=start,
+                                    fused=fused)
+        for _ in range(2):
+            opt.step()
+        runs.append(opt)
+    for name in ("spins", "J", "m", "v"):
+        assert torch.equal(getattr(runs[0], name), getattr(runs[1], name)), name
+    beta, h, alpha = f32(0.8), f32(0.05), 4.0
+    J, s0, _ = make_case(B, L, 99)
+    spins = torch.from_numpy(s0.copy()).cuda()
+    tape = torch.empty((sm.dmc_tape_floats(B, L, K),), dtype=torch.float32, device="cuda")
+    sm.dmc_forward(SEED, torch.from_numpy(J).cuda(), spins, beta, h, alpha, 3, K, tape)
+    got = spins.cpu().numpy()
+    for b in (0, 517, 1023):
+        ref, _ = oracle_run(J[b], s0[b], beta, h, alpha, b, 3, K)
+        cond = condition(J[b], s0[b], beta, h, alpha, b, 3, K)
+        tol = 4 * 10 * EPS32 * 2 * K * max(cond, 1.0)
+        assert np.abs(got[b] - ref).max() <= tol, b
