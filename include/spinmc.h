@@ -242,6 +242,17 @@ int spin_restore(spin_ctx *ctx, const void *host_blob, size_t size, void *stream
 int spin_profile(spin_ctx *ctx, int32_t enable, int32_t max_launches);
 int spin_profile_read(spin_ctx *ctx, double *total_ms, int64_t *launches, void *stream);
 
+/* Self-test of the bounded grid barrier of the CPM persistent form (failure
+ * detection without a GPU fault): one cooperative launch of `blocks` blocks
+ * (1 <= blocks <= the SM count) runs `rounds` barriers that complete after
+ * blocks + missing arrivals (0 <= missing <= blocks).  With missing = 0 every
+ * barrier completes and the call returns SPIN_OK; with missing > 0 no barrier
+ * can complete, every block gives up after the bounded wait (1 s) and the call
+ * returns SPIN_ETIMEOUT with the device still usable.  Synchronises the
+ * stream.  SPIN_EINVAL for arguments out of range or a device without
+ * cooperative launch. */
+int spin_barrier_selftest(int32_t blocks, int32_t missing, int32_t rounds, void *stream);
+
 uint32_t spin_sweep_index(const spin_ctx *ctx);
 int32_t spin_gpu_launches(const spin_ctx *ctx); /* kernels launched by the last spin_sweep */
 const char *spin_last_error(const spin_ctx *ctx);

@@ -69,6 +69,7 @@ _SIGS = {
     "spin_restore": (_i32, [_vp, _vp, ctypes.c_size_t, _vp]),
     "spin_profile": (_i32, [_vp, _i32, _i32]),
     "spin_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _vp]),
+    "spin_barrier_selftest": (_i32, [_i32, _i32, _i32, _vp]),
     "spin_sweep_index": (ctypes.c_uint32, [_vp]),
     "spin_gpu_launches": (_i32, [_vp]),
     "spin_last_error": (ctypes.c_char_p, [_vp]),
@@ -395,6 +396,12 @@ class Sim:
     def restore(self, blob, stream=None):
         blob = np.ascontiguousarray(blob, dtype=np.uint8)
         _check(lib().spin_restore(self.ctx, _ptr(blob), blob.size, _stream(stream)), self.ctx, "restore")
+
+
+def barrier_selftest(blocks, missing=0, rounds=1, stream=None):
+    """Run the bounded grid barrier of the CPM persistent form as a self-test;
+    returns SPIN_OK (0) or SPIN_ETIMEOUT (-4) (see spin_barrier_selftest)."""
+    return int(lib().spin_barrier_selftest(int(blocks), int(missing), int(rounds), _stream(stream)))
 
 
 # --------------------------------------------------------------------------

@@ -497,10 +497,8 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
         }
     } else {
         for (int nc = 0; nc < 4 && ctx->n_nnn; ++nc) {
-            const bool timed = prof_begin(ctx, s, 3);
             CK(launch_ising_nnn(static_cast<int8_t *>(src), static_cast<int8_t *>(dst), ctx->n_nnn, ctx->nnn_maxL,
                                 ctx->d_lats, ctx->d_nnn_thr, ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, nc, s));
-            if (timed) prof_end(ctx, s);
             ++launches;
         }
         for (int tc = 0; tc < 3 && ctx->n_tri; ++tc) {
@@ -1393,6 +1391,30 @@ int spin_autotune(spin_ctx *ctx, int32_t sweeps_per_trial, void *stream) {
     return SPIN_OK;
 }
 
+int spin_barrier_selftest(int32_t blocks, int32_t missing, int32_t rounds, void *stream) {
+    if (blocks < 1 || missing < 0 || missing > blocks || rounds < 1) return SPIN_EINVAL;
+    int dev = 0, coop = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SPIN_ECUDA;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!coop || blocks > sms) return SPIN_EINVAL;
+    cudaStream_t s = S(stream);
+    void *buf = nullptr;
+    if (cudaMalloc(&buf, 16) != cudaSuccess) return SPIN_ENOMEM;
+    unsigned int *bar = static_cast<unsigned int *>(buf);
+    int *err = reinterpret_cast<int *>(bar + 2);
+    int flag = 0, rc = SPIN_OK;
+    if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess ||
+        launch_grid_barrier_probe(bar, err, blocks, missing, rounds, s) != cudaSuccess ||
+        cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        rc = SPIN_ECUDA;
+    else if (flag)
+        rc = SPIN_ETIMEOUT;
+    cudaFree(buf);
+    return rc;
+}
+
 int spin_profile(spin_ctx *ctx, int32_t enable, int32_t max_launches) {
     if (!ctx) return SPIN_EINVAL;
     if (max_launches < 0) return fail(ctx, SPIN_EINVAL, "max_launches must be >= 0");
@@ -1418,9 +1440,11 @@ int spin_profile_read(spin_ctx *ctx, double *total_ms, int64_t *launches, void *
     }
     for (int i = 0; i < ctx->prof_n; ++i) {
         float ms = 0.f;
+        const int c = ctx->prof_cls[i];
+        if (c < 0 || c > 2) continue;
         CK(cudaEventElapsedTime(&ms, ctx->prof_ev[2 * i], ctx->prof_ev[2 * i + 1]));
-        total_ms[ctx->prof_cls[i]] += ms;
-        launches[ctx->prof_cls[i]] += 1;
+        total_ms[c] += ms;
+        launches[c] += 1;
     }
     return SPIN_OK;
 }

@@ -246,6 +246,11 @@ struct CpmPersistArgs {
 // device has no cooperative launch).
 int cpm_persistent_grid();
 cudaError_t launch_cpm_persistent(const CpmPersistArgs &p, int max_grid, DevState *state, cudaStream_t s);
+// Cooperative launch of `blocks` blocks running `rounds` grid barriers of the
+// persistent form that wait for blocks + missing arrivals (err: set to 1 when
+// a wait gives up).
+cudaError_t launch_grid_barrier_probe(unsigned int *bar, int *err, int blocks, int missing, int rounds,
+                                      cudaStream_t s);
 
 // Differentiable Monte Carlo (Alg. 2): relaxed sweeps with one coupling per
 // bond.  spins [n_lat][L*L]; J [n_lat][2][L*L] (right, down bonds); tape

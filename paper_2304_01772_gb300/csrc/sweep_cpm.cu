@@ -204,11 +204,11 @@ __device__ __forceinline__ uint64_t cpm_ns() {
 constexpr uint64_t kCpmWaitNs = 1000000000ull;   // a barrier wait gives up after 1 s
 
 // Grid barrier: bar[0] counts arrivals, bar[1] is the generation.  Thread 0
-// of each block reads the generation, arrives, and the last arrival resets
-// the count and advances the generation; the others wait (bounded) for the
-// advance.  False (for the whole block) if a wait ran out or another block
-// has reported one in *err.
-__device__ bool cpm_grid_sync(unsigned int *bar, int *err) {
+// of each block reads the generation, arrives, and the arrival that makes the
+// count `expected` (gridDim.x in use) resets the count and advances the
+// generation; the others wait (bounded) for the advance.  False (for the whole
+// block) if a wait ran out or another block has reported one in *err.
+__device__ bool cpm_grid_sync(unsigned int *bar, int *err, unsigned int expected) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -216,7 +216,7 @@ __device__ bool cpm_grid_sync(unsigned int *bar, int *err) {
         const unsigned int gen = *vgen;
         int good = 1;
         __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+        if (atomicAdd(bar, 1u) == expected - 1) {
             atomicExch(bar, 0u);
             __threadfence();
             atomicAdd(bar + 1, 1u);
@@ -298,12 +298,20 @@ __global__ void __launch_bounds__(kCpmThreads) cpm_persistent_kernel(CpmPersistA
             a.dvol_prev = p.dvol[(c + 1) & 1];
             cpm_substep_body(a, c, t, sh);
             cpm_block_flush(a, sh, p.acc + kCpmAccStride * (step & 1));
-            if (!cpm_grid_sync(p.bar, p.err)) return;
+            if (!cpm_grid_sync(p.bar, p.err, gridDim.x)) return;
         }
     }
     if (blockIdx.x == 0 && p.n_steps > 0)
         cpm_finish_step(p.vol[0], a.n_cells, a.target, p.st, p.acc + kCpmAccStride * ((p.n_steps - 1) & 1),
                         p.record, p.rec0 + p.n_steps - 1);
+}
+
+// Self-test of the grid barrier: `rounds` barriers that complete after
+// `expected` arrivals (expected > gridDim.x: they cannot complete, and every
+// block must give up after the bounded wait).
+__global__ void grid_barrier_probe_kernel(unsigned int *bar, int *err, unsigned int expected, int rounds) {
+    for (int r = 0; r < rounds; ++r)
+        if (!cpm_grid_sync(bar, err, expected)) return;
 }
 
 __global__ void cpm_advance_kernel(DevState *state, uint32_t n, int record) {
@@ -642,6 +650,16 @@ cudaError_t launch_cpm_persistent(const CpmPersistArgs &p, int max_grid, DevStat
     if (e) return e;
     cpm_advance_kernel<<<1, 1, 0, s>>>(state, (uint32_t)p.n_steps, p.record);
     return cudaGetLastError();
+}
+
+cudaError_t launch_grid_barrier_probe(unsigned int *bar, int *err, int blocks, int missing, int rounds,
+                                      cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned int), s);
+    if (e) return e;
+    unsigned int expected = (unsigned int)(blocks + missing);
+    void *args[] = {&bar, &err, &expected, &rounds};
+    return cudaLaunchCooperativeKernel((const void *)grid_barrier_probe_kernel, dim3(blocks), dim3(kCpmThreads),
+                                       args, 0, s);
 }
 
 cudaError_t launch_cpm_finalize(const int32_t *vol, int n_cells, int target, DevState *state, StatsBufs st,

@@ -140,3 +140,9 @@ def test_second_neighbour_lattices_do_not_share_a_context():
 def test_lattice_desc_layout_matches_the_header():
     assert ctypes.sizeof(sm.LatticeDesc) == 40
     assert sm.LatticeDesc.J2.offset == 24 and sm.LatticeDesc.spin_offset.offset == 32
+
+
+def test_barrier_selftest_rejects_invalid_arguments_on_the_host():
+    lib = sm.lib()
+    for blocks, missing, rounds in [(0, 0, 1), (4, -1, 1), (4, 5, 1), (4, 0, 0)]:
+        assert lib.spin_barrier_selftest(blocks, missing, rounds, None) == EINVAL
