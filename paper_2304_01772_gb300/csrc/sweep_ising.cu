@@ -32,12 +32,8 @@ constexpr uint32_t kDownMask = 0x02020202u;
 // chunks above and below; lw / rw: the 32-bit words left and right of C in
 // the same row.  Philox groups g0 (bytes 0..7) and g0 + 1 (bytes 8..15); active
 // bytes of each word are p and p + 2.
-__device__ __forceinline__ uint4 ising_chunk(uint4 C, uint4 U, uint4 D, uint32_t lw, uint32_t rw,
-                                             uint32_t g0, int p, uint32_t lat, uint32_t t,
-                                             uint32_t c, uint32_t k0, uint32_t k1,
-                                             const TabEntry *stab, bool count, int &acc) {
-    const uint4 ra = philox4x32_10(make_uint4(g0, lat, t, c), k0, k1);
-    const uint4 rb = philox4x32_10(make_uint4(g0 + 1u, lat, t, c), k0, k1);
+__device__ __forceinline__ uint4 ising_chunk_r(uint4 C, uint4 U, uint4 D, uint32_t lw, uint32_t rw, int p,
+                                               uint4 ra, uint4 rb, const TabEntry *stab, bool count, int &acc) {
     const uint32_t w[6] = {lw, C.x, C.y, C.z, C.w, rw};
     const uint32_t up[4] = {U.x, U.y, U.z, U.w};
     const uint32_t dn[4] = {D.x, D.y, D.z, D.w};
@@ -64,6 +60,15 @@ __device__ __forceinline__ uint4 ising_chunk(uint4 C, uint4 U, uint4 D, uint32_t
         out[i] = nw;
     }
     return make_uint4(out[0], out[1], out[2], out[3]);
+}
+
+__device__ __forceinline__ uint4 ising_chunk(uint4 C, uint4 U, uint4 D, uint32_t lw, uint32_t rw,
+                                             uint32_t g0, int p, uint32_t lat, uint32_t t,
+                                             uint32_t c, uint32_t k0, uint32_t k1,
+                                             const TabEntry *stab, bool count, int &acc) {
+    const uint4 ra = philox4x32_10(make_uint4(g0, lat, t, c), k0, k1);
+    const uint4 rb = philox4x32_10(make_uint4(g0 + 1u, lat, t, c), k0, k1);
+    return ising_chunk_r(C, U, D, lw, rw, p, ra, rb, stab, count, acc);
 }
 
 // Packed (dB * 65536 + dM) per-thread sums -> block sums -> one atomic pair.
@@ -176,6 +181,7 @@ __global__ void __launch_bounds__(THREADS) ising_resident_kernel(ResidentArgs a)
         const uint32_t t = a.t0 + (uint32_t)sweep;
         int acc = 0;
         for (int c = 0; c < 2; ++c) {
+            const PhiloxPrefix P = philox_prefix((uint32_t)lat, t, (uint32_t)c, a.rk);
             for (int v = threadIdx.x; v < L * Lv; v += THREADS) {
                 const int i = v / Lv, j = v - i * Lv;
                 const int iu = i == 0 ? L - 1 : i - 1, id = i == L - 1 ? 0 : i + 1;
@@ -185,8 +191,8 @@ __global__ void __launch_bounds__(THREADS) ising_resident_kernel(ResidentArgs a)
                 const uint32_t lw = sm32[(i * Lv + (j == 0 ? Lv - 1 : j - 1)) * 4 + 3];
                 const uint32_t rw = sm32[(i * Lv + (j == Lv - 1 ? 0 : j + 1)) * 4];
                 const uint32_t g0 = (uint32_t)i * (uint32_t)(L >> 3) + 2u * (uint32_t)j;
-                sm4[v] = ising_chunk(Cc, Uc, Dc, lw, rw, g0, (c ^ i) & 1, (uint32_t)lat, t, (uint32_t)c,
-                                     a.k0, a.k1, stab, true, acc);
+                sm4[v] = ising_chunk_r(Cc, Uc, Dc, lw, rw, (c ^ i) & 1, philox_from_prefix(g0, P, a.rk),
+                                       philox_from_prefix(g0 + 1u, P, a.rk), stab, true, acc);
             }
             __syncthreads();
         }
@@ -246,8 +252,9 @@ __global__ void __launch_bounds__(kTriResThreads) ising_tri_resident_kernel(Resi
         const uint32_t t = a.t0 + (uint32_t)sweep;
         int acc = 0;
         for (int c = 0; c < 3; ++c) {
+            const PhiloxPrefix P = philox_prefix((uint32_t)lat, t, (uint32_t)c, a.rk);
             for (int grp = threadIdx.x; 4 * grp < nk; grp += blockDim.x) {
-                const uint4 r = philox4x32_10(make_uint4((uint32_t)grp, (uint32_t)lat, t, (uint32_t)c), a.k0, a.k1);
+                const uint4 r = philox_from_prefix((uint32_t)grp, P, a.rk);
                 const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
                 // row and colour offset once per group; a group's sites rarely cross a row
                 int y = (4 * grp) / third, m = 4 * grp - y * third, off = (c + y) % 3;
