@@ -199,12 +199,17 @@ int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_
 
 /* Launch form.  mode: 0 = batched persistent work-list launch (default),
  * 1 = plain per-lattice launches (two per lattice per sweep), 2 = resident
- * (Ising only, every L a multiple of 16 and <= 256: one CTA per lattice keeps
- * it in shared memory for all sweeps of a spin_sweep call, one launch).
+ * (Ising only, every L a multiple of 16 and <= 256, or only triangular
+ * lattices with L <= 240, or only second-neighbour lattices with L <= 256: one
+ * CTA per lattice keeps it in shared memory for all sweeps of a spin_sweep
+ * call, one launch; for a CPM context on a device with cooperative launch,
+ * the persistent form: all Monte Carlo steps of a call in one cooperative
+ * launch with bounded grid barriers between the sub-steps).
  * use_graph: capture the sweep loop in a CUDA graph.  tile_rows: work-item
  * height in rows for mode 0 (0 = keep the current value, -1 = default items of
  * about 32-64 KB).  threads: CTA size of the tile kernel (128, 256 or 512; 0 =
- * keep); the warp row-strip kernel uses 8 warps per CTA for 512, else 4.
+ * keep) and of the square-lattice resident kernel (also 1024 there); the warp
+ * row-strip kernel uses 8 warps per CTA for 512, else 4.
  * Results do not depend on any of these. */
 int spin_set_launch(spin_ctx *ctx, int32_t mode, int32_t use_graph, int32_t tile_rows,
                     int32_t threads);

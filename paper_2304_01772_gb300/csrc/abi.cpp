@@ -1211,14 +1211,15 @@ int spin_set_launch(spin_ctx *ctx, int32_t mode, int32_t use_graph, int32_t tile
                                       "only triangular lattices with L <= 240, only second-neighbour "
                                       "lattices with L <= 256, or a CPM context on a device with "
                                       "cooperative launch");
-    if (threads != 0 && threads != 128 && threads != 256 && threads != 512)
-        return fail(ctx, SPIN_EINVAL, "threads must be 128, 256 or 512");
+    if (threads != 0 && threads != 128 && threads != 256 && threads != 512 && !(threads == 1024 && mode == 2))
+        return fail(ctx, SPIN_EINVAL, "threads must be 128, 256 or 512 (or 1024 in the resident form)");
     if (tile_rows < -1) return fail(ctx, SPIN_EINVAL, "tile_rows must be >= -1");
     ctx->mode = mode;
     ctx->use_graph = use_graph ? 1 : 0;
     if (tile_rows > 0) ctx->tile_rows = tile_rows;
     if (tile_rows == -1) ctx->tile_rows = 0;
     if (threads) ctx->threads = threads;
+    if (ctx->mode != 2 && ctx->threads > 512) ctx->threads = 512;   // 1024 exists in the resident form only
     return plan(ctx);
 }
 
@@ -1355,7 +1356,7 @@ int spin_autotune(spin_ctx *ctx, int32_t sweeps_per_trial, void *stream) {
         for (int tr : {0, 8, 16, 32, 64}) cands.push_back({0, tr, th});
     cands.push_back({1, 0, 256});
     if (resident_ok(ctx))
-        for (int th : {128, 256, 512}) cands.push_back({2, 0, th});
+        for (int th : {128, 256, 512, 1024}) cands.push_back({2, 0, th});
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));

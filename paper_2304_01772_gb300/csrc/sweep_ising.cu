@@ -1087,6 +1087,10 @@ cudaError_t launch_ising_resident(const ResidentArgs &a, int n_lat, int threads,
             if ((e = cudaFuncSetAttribute(ising_resident_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
             ising_resident_kernel<512><<<n_lat, 512, smem, s>>>(a);
             break;
+        case 1024:
+            if ((e = cudaFuncSetAttribute(ising_resident_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
+            ising_resident_kernel<1024><<<n_lat, 1024, smem, s>>>(a);
+            break;
         default:
             return cudaErrorInvalidValue;
     }

@@ -508,3 +508,21 @@ def test_triangular_resident_form(graph):
         assert np.array_equal(lattice_np(sim, i), s), i
         assert np.array_equal(st[:, i, :], ref), i
     assert np.array_equal(sim.current_stats().cpu().numpy()[:, :], st[-1])
+
+
+def test_resident_form_with_1024_threads():
+    """The square-lattice resident kernel also runs 1024-thread blocks (one
+    lattice per SM with twice the warps); the chain is the oracle's."""
+    lats = wl.fit256(n=6, L=64, beta=0.44, J=1.0, h=0.02) + [dict(L=256, beta=0.3, J=1.0, h=0.0)]
+    sim = make_ising(lats, max_record=8)
+    sim.set_launch(2, True, 0, 1024)
+    assert sim.get_launch()["threads"] == 1024
+    init = {i: lattice_np(sim, i) for i in range(len(lats))}
+    sim.sweep(3, record=True)
+    out, stats = oracle_ising_chain(lats, SEED, init, 0, 3)
+    st = sim.observables_host(0, 3)[0]
+    for i in range(len(lats)):
+        assert np.array_equal(lattice_np(sim, i), out[i]), i
+        assert np.array_equal(st[:, i, :], stats[i]), i
+    sim.set_launch(0, True, 0, 0)       # back to the batched form: threads fall back to 512
+    assert sim.get_launch()["threads"] == 512
