@@ -103,7 +103,9 @@ extern "C" int spin_ising_sweep_noalloc(uint64_t seed, int32_t n_lattices,
         }
         smem = smem > (size_t)(rows + 4) * d.L ? smem : (size_t)(rows + 4) * d.L;
     }
-    if (smem > 48 * 1024) return SPIN_EINVAL;
+    // the tile kernel runs without a raised shared-memory limit here: its dynamic
+    // share plus its static tables must stay within the default 48 KB
+    if (smem > 47 * 1024) return SPIN_EINVAL;
     // scratch layout: state | lattices | tables | items | generic ids | cur | delta | spins2
     const size_t o_lat = 256;
     const size_t o_tab = align256(o_lat + sizeof(LatDev) * n_lattices);

@@ -1057,13 +1057,15 @@ cudaError_t occupancy_ising_strip(int *blocks_per_sm, int warps) {
 
 // The dynamic shared-memory limit of a kernel is process-wide state: it is
 // only ever raised (per device), so one caller can never lower it below what
-// another caller's launches need.  48 KB needs no opt-in.
+// another caller's launches need.
 cudaError_t set_ising_fused_smem(size_t smem) {
     static size_t raised[64] = {0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e) return e;
-    if (smem <= 48 * 1024 || dev < 0 || dev >= 64 || smem <= raised[dev]) return cudaSuccess;
+    // (the static shared memory of the kernel counts against the default 48 KB
+    // too, so the limit is raised for any size above what was set before)
+    if (dev < 0 || dev >= 64 || smem <= raised[dev]) return cudaSuccess;
     if ((e = cudaFuncSetAttribute(ising_fused_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
     if ((e = cudaFuncSetAttribute(ising_fused_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
     if ((e = cudaFuncSetAttribute(ising_fused_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;

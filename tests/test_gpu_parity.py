@@ -526,3 +526,29 @@ def test_resident_form_with_1024_threads():
         assert np.array_equal(st[:, i, :], stats[i]), i
     sim.set_launch(0, True, 0, 0)       # back to the batched form: threads fall back to 512
     assert sim.get_launch()["threads"] == 512
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_large_lattices_against_the_oracle(mode):
+    """Lattices far above the strip sizes (4096^2 and 8192^2 Ising, 4096^2 Potts
+    with q = 5): work items with recomputed halos in the batched form and
+    per-lattice launches in the plain form, two sweeps against the oracle."""
+    lats = [dict(L=4096, beta=0.44, J=1.0, h=0.01), dict(L=8192, beta=0.3, J=1.0, h=0.0)]
+    sim = make_ising(lats, max_record=4)
+    sim.set_launch(mode, True, 0, 256)
+    init = {i: lattice_np(sim, i) for i in range(len(lats))}
+    sim.sweep(2, record=True)
+    out, stats = oracle_ising_chain(lats, SEED, init, 0, 2)
+    st = sim.observables_host(0, 2)[0]
+    for i in range(len(lats)):
+        assert np.array_equal(lattice_np(sim, i), out[i]), i
+        assert np.array_equal(st[:, i, :], stats[i]), i
+    del sim
+    pl = [dict(L=4096, q=5, beta=1.1, J=1.0)]
+    ps = sm.Sim(sm.SPIN_POTTS, pl, seed=SEED, max_record=4)
+    ps.set_launch(mode, True, 0, 256)
+    p0 = ps.lattice(0).cpu().numpy().copy()
+    ps.sweep(2, record=True)
+    ref = oracle.potts_run(p0, 5, 1.1, 1.0, SEED, 0, 0, 2)
+    assert np.array_equal(ps.lattice(0).cpu().numpy(), p0)
+    assert np.array_equal(ps.observables_host(0, 2)[0][:, 0, :], ref)
