@@ -585,9 +585,17 @@ cudaError_t set_potts_fused_smem(size_t smem) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e) return e;
-    // (the static shared memory of the kernel counts against the default 48 KB
-    // too, so the limit is raised for any size above what was set before)
+    // Raised only when the dynamic share plus the kernel's static tables exceed
+    // the default 48 KB: setting the limit without need was measured to slow the
+    // sweep (the tile kernel shares the SMs with the strip kernel).
     if (dev < 0 || dev >= 64 || smem <= raised[dev]) return cudaSuccess;
+    size_t stat = 0;
+    for (const void *k : {(const void *)potts_fused_kernel<128>, (const void *)potts_fused_kernel<256>, (const void *)potts_fused_kernel<512>}) {
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, k))) return e;
+        stat = fa.sharedSizeBytes > stat ? fa.sharedSizeBytes : stat;
+    }
+    if (smem + stat <= 48 * 1024) return cudaSuccess;
     if ((e = cudaFuncSetAttribute(potts_fused_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
     if ((e = cudaFuncSetAttribute(potts_fused_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
     if ((e = cudaFuncSetAttribute(potts_fused_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
