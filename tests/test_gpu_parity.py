@@ -552,3 +552,23 @@ def test_large_lattices_against_the_oracle(mode):
     ref = oracle.potts_run(p0, 5, 1.1, 1.0, SEED, 0, 0, 2)
     assert np.array_equal(ps.lattice(0).cpu().numpy(), p0)
     assert np.array_equal(ps.observables_host(0, 2)[0][:, 0, :], ref)
+
+
+def test_empty_calls_change_nothing():
+    """Zero sweeps, zero records and zero-length reads are valid no-ops; a
+    gradient needs two records."""
+    lats = [dict(L=16, beta=0.4, J=1.0, h=0.0), dict(L=512, beta=0.3, J=1.0, h=0.1)]
+    sim = make_ising(lats, max_record=4)
+    before = [lattice_np(sim, i) for i in range(2)]
+    st0 = sim.current_stats().clone()
+    sim.sweep(0, record=True)
+    assert sim.t == 0 and sim.n_records == 0
+    assert all(np.array_equal(lattice_np(sim, i), before[i]) for i in range(2))
+    assert torch.equal(sim.current_stats(), st0)
+    st, E, M = sim.observables_host(0, 0)
+    assert st.shape == (0, 2, 2) and E.size == 0 and M.size == 0
+    sim.sweep(1, record=True)
+    with pytest.raises(sm.SpinError):
+        sim.grad(0, 1)
+    mom = sim.moments(0, 1).cpu().numpy()
+    assert list(mom[:, 0]) == [1, 1]            # one sample per lattice
