@@ -404,9 +404,9 @@ def kernel_source_hash(kernel="ising_strip_kernel"):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, workload="uneven512"):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None if absent or taken on a different kernel source."""
+def ncu_value(kernel, workload, key):
+    """A per-launch counter (`key`) of `kernel` from the committed ncu summary,
+    or None if absent or taken on a different kernel source."""
     if not kernel:
         return None
     path = os.path.join(ROOT, "profiles", f"{kernel.replace('_kernel', '')}_{workload}.txt")
@@ -418,9 +418,32 @@ def ncu_traffic(kernel, workload="uneven512"):
                 kv[k.strip()] = v.strip()
         if kv.get("kernel_source_sha256_16") != kernel_source_hash(kernel):
             return None
-        return float(kv["dram_bytes_per_full_launch"].split()[0])
+        return float(kv[key].split()[0])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def ncu_traffic(kernel, workload="uneven512"):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)."""
+    return ncu_value(kernel, workload, "dram_bytes_per_full_launch")
+
+
+def issue_roofline(kernel, workload, launch_ms, sm_mhz):
+    """The binding resource of the integer-bound sweep kernels: warp-instruction
+    issue.  achieved = the launch's executed warp instructions (ncu
+    smsp__inst_executed.sum of the same launch, current source) / its CUDA-event
+    time; peak = SMs x 4 schedulers x one warp instruction per cycle x the SM
+    clock sampled during the timed region."""
+    import torch
+    inst = ncu_value(kernel, workload, "warp_instructions_per_full_launch")
+    if not inst or not launch_ms or not sm_mhz:
+        return None
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 4 * sm_mhz * 1e6
+    ach = inst / (launch_ms * 1e-3)
+    return {"bound": "issue", "achieved": ach, "peak": peak, "unit": "warp-instructions/s", "frac": ach / peak,
+            "instructions_per_launch": inst, "sm_mhz": sm_mhz,
+            "peak_source": f"{sms} SMs x 4 schedulers x 1 warp instruction per cycle at the sampled clock"}
 
 
 def dist_setup(n):
@@ -680,7 +703,8 @@ def run_ours(args):
                      "frac": (achieved / peak) if achieved else None, "traffic": ncu_traffic(dom),
                      "kernel": dom, "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": kms_dom, "timed_launches": kn,
-                     "peak_source": f"{peak_kind} hbm_gbs (copy)", "kernels": kernels},
+                     "peak_source": f"{peak_kind} hbm_gbs (copy)", "kernels": kernels,
+                     "issue": issue_roofline(dom, "uneven512", kms_dom, clk.get("sm_mhz") if clk else None)},
         "e2e": {"value": sites * args.e2e_steps * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": span, "d2h_bytes_per_step": span + st_host.numel() * 8,
                 "pipeline": "three contexts on three streams; uploads and downloads each first in, first "
@@ -766,10 +790,15 @@ def run_secondary(args):
             "config": {"workload": desc, "launch": launch}, "gpu_launches": sim.gpu_launches}
     if args.workload.startswith("potts"):
         nk = min(args.steps, 100)
+        clocks = ClockSampler(0)
+        time.sleep(0.3)
+        tc0 = time.perf_counter()
         sim.profile(True, 2 * nk)
         sim.sweep(nk)
         prof = sim.profile_read()
         sim.profile(False)
+        clk = clocks.summary(tc0, time.perf_counter())
+        clocks.stop()
         cls = 1 if prof[1][1] else 0          # the strip kernel when the batch uses it
         kms, kn = prof[cls]
         kname = "potts_strip_kernel" if cls == 1 else "potts_fused_kernel"
@@ -780,7 +809,9 @@ def run_secondary(args):
                                 "traffic": ncu_traffic(kname, args.workload),
                                 "kernel": kname, "launch_ms": kms / kn,
                                 "note": "64 MiB state + partner ~ L2 size: largely L2-resident",
-                                "peak_source": f"{kind} hbm_gbs"}
+                                "peak_source": f"{kind} hbm_gbs",
+                                "issue": issue_roofline(kname, args.workload, kms / kn,
+                                                        clk["sm_mhz"] if clk else None)}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
