@@ -876,22 +876,25 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
     if (ctx->n_generic) {
         if (!ckm(cudaMalloc(&ctx->d_generic, sizeof(int32_t) * ctx->n_generic)))
             return bail(SPIN_ENOMEM);
-        cudaMemcpy(ctx->d_generic, generic.data(), sizeof(int32_t) * generic.size(), cudaMemcpyHostToDevice);
+        if (!ckm(cudaMemcpy(ctx->d_generic, generic.data(), sizeof(int32_t) * generic.size(), cudaMemcpyHostToDevice)))
+            return bail(SPIN_ECUDA);
     }
     if (ctx->n_nnn && !ckm(cudaMalloc(&ctx->d_nnn_thr, sizeof(uint32_t) * kNnnTab * n_lattices)))
         return bail(SPIN_ENOMEM);
     if (ctx->n_tri) {
         if (!ckm(cudaMalloc(&ctx->d_tri, sizeof(int32_t) * ctx->n_tri))) return bail(SPIN_ENOMEM);
-        cudaMemcpy(ctx->d_tri, tri.data(), sizeof(int32_t) * tri.size(), cudaMemcpyHostToDevice);
+        if (!ckm(cudaMemcpy(ctx->d_tri, tri.data(), sizeof(int32_t) * tri.size(), cudaMemcpyHostToDevice)))
+            return bail(SPIN_ECUDA);
     }
     ctx->st.cap = max_record_sweeps;
     ctx->st.width = ctx->width;
     ctx->st.n_lat = n_lattices;
     if (cudaMemcpy(ctx->d_lats, ld.data(), sizeof(LatDev) * n_lattices, cudaMemcpyHostToDevice))
         return bail(SPIN_ECUDA);
-    cudaMemset(ctx->st.delta, 0, sizeof(int64_t) * w * n_lattices);
     DevState ds{0u, 0, 0};
-    cudaMemcpy(ctx->d_state, &ds, sizeof ds, cudaMemcpyHostToDevice);
+    if (!ckm(cudaMemset(ctx->st.delta, 0, sizeof(int64_t) * w * n_lattices)) ||
+        !ckm(cudaMemcpy(ctx->d_state, &ds, sizeof ds, cudaMemcpyHostToDevice)))
+        return bail(SPIN_ECUDA);
     if (model == SPIN_CPM) {
         const int nc = ctx->n_cells;
         if (!ckm(cudaMalloc(&ctx->d_type, nc + 1)) || !ckm(cudaMalloc(&ctx->d_J, sizeof(int32_t) * 64)) ||
@@ -924,20 +927,21 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
     if (e) return bail(cuda_fail(ctx, e, "init"));
     if (model == SPIN_CPM) {
         if (cpm->cell_type) {
-            cudaMemcpyAsync(ctx->d_type, cpm->cell_type, ctx->n_cells + 1, cudaMemcpyHostToDevice, s);
+            e = cudaMemcpyAsync(ctx->d_type, cpm->cell_type, ctx->n_cells + 1, cudaMemcpyHostToDevice, s);
+            if (e) return bail(cuda_fail(ctx, e, "cell types"));
         } else {
             e = launch_cpm_types(ctx->d_type, ctx->n_cells, 0u, ctx->k0, ctx->k1, s);
             if (e) return bail(cuda_fail(ctx, e, "cpm types"));
         }
         // the CPM kernels address the lattice at offset 0 of the buffer
         ctx->spins = static_cast<int32_t *>(d_spins) + ctx->lat[0].spin_offset;
-        cudaMemsetAsync(ctx->d_vol[0], 0, sizeof(int32_t) * (ctx->n_cells + 1), s);
-        e = launch_cpm_volumes(static_cast<int32_t *>(ctx->spins), ctx->lat[0].L, ctx->d_vol[0], ctx->n_cells, s);
-        if (e) return bail(cuda_fail(ctx, e, "cpm volumes"));
-        cudaMemcpyAsync(ctx->d_vol[1], ctx->d_vol[0], sizeof(int32_t) * (ctx->n_cells + 1),
-                        cudaMemcpyDeviceToDevice, s);
-        cudaMemsetAsync(ctx->d_dvol[0], 0, sizeof(int32_t) * (ctx->n_cells + 1), s);
-        cudaMemsetAsync(ctx->d_dvol[1], 0, sizeof(int32_t) * (ctx->n_cells + 1), s);
+        const size_t vb = sizeof(int32_t) * (ctx->n_cells + 1);
+        e = cudaMemsetAsync(ctx->d_vol[0], 0, vb, s);
+        if (!e) e = launch_cpm_volumes(static_cast<int32_t *>(ctx->spins), ctx->lat[0].L, ctx->d_vol[0], ctx->n_cells, s);
+        if (!e) e = cudaMemcpyAsync(ctx->d_vol[1], ctx->d_vol[0], vb, cudaMemcpyDeviceToDevice, s);
+        if (!e) e = cudaMemsetAsync(ctx->d_dvol[0], 0, vb, s);
+        if (!e) e = cudaMemsetAsync(ctx->d_dvol[1], 0, vb, s);
+        if (e) return bail(cuda_fail(ctx, e, "cpm areas"));
     }
     if (model != SPIN_CPM) {
         // keep the bytes outside the lattices identical in both buffers
