@@ -217,3 +217,22 @@ def test_pooled_gradient_over_two_contexts_via_limbs():
     # one context's limbs alone reproduce its own pooled gradient exactly
     g0, _ = sims[0].grad_from_limbs(sims[0].pooled_limbs(0, n), observable=0)
     assert torch.equal(g0, sims[0].grad(0, n, observable=0, pool=True))
+
+
+def test_observables_fn_backward_is_the_estimator_jacobian():
+    """The torch.autograd.Function around the ensemble: forward returns the
+    pooled expectations of the recorded samples, backward returns the upstream
+    gradient times the pooled fluctuation-estimator Jacobian of the same samples
+    (checked against spin_grad on a second ensemble with the same seed)."""
+    ens = fit.IsingEnsemble(8, 32, 0.44, seed=11, n_burn=50, n_meas=100, tune=False)
+    theta = torch.tensor([0.9, 0.05], dtype=torch.float64, device="cuda", requires_grad=True)
+    out = fit.ObservablesFn.apply(theta, ens)
+    w = torch.tensor([0.7, -1.3], dtype=torch.float64, device="cuda")
+    (out * w).sum().backward()
+    ref = sm.Sim(sm.SPIN_ISING, [dict(L=32, beta=0.44, J=0.9, h=0.05)] * 8, seed=11, max_record=100)
+    ref.sweep(50)
+    ref.sweep(100, record=True)
+    e = ref.expectations(0, 100, pool=True)[0]
+    jac = torch.stack([ref.grad(0, 100, observable=0, pool=True)[0], ref.grad(0, 100, observable=1, pool=True)[0]])
+    assert torch.allclose(out.detach(), e, rtol=1e-12, atol=0)
+    assert torch.allclose(theta.grad, w @ jac, rtol=1e-12, atol=1e-15)
