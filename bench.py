@@ -910,6 +910,10 @@ def run_dmc(args, cpu):
                                                         "moments in + out (2 bonds x 3 x 8 B)"}
     separate_ms = timed(opt.step_separate)
     top = max(kernels, key=lambda k: kernels[k]["launch_ms"])
+    # the temperature study: coupling-gradient size of one iteration from the ordered start
+    from paper_2304_01772_gb300.dmc import gradient_by_temperature
+    temps = [0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0, 6.0, 8.0, 12.0, 20.0, 40.0]
+    study = gradient_by_temperature(target, temps, alpha=10.0, sweeps=K, seed=SEED)
     peak, kind = measured_peaks()
     units = B * L * L * K
     separate = {"ms_per_step": separate_ms, "value": units / (separate_ms * 1e-3),
@@ -922,7 +926,11 @@ def run_dmc(args, cpu):
                                    "beta = 1/0.9, alpha = 10, h = 0, Adam lr 5e-2, striped/block targets; "
                                    "one step = forward + loss + reverse pass + Adam + discretisation",
                        "mean_loss_last_step": float(loss.mean()), "fused": opt.fused,
-                       "separate_launches": separate},
+                       "separate_launches": separate,
+                       "gradient_by_temperature": {
+                           "T": temps, "mean_abs_dL_dJ": [g for _, g, _ in study],
+                           "argmax_T": max(study, key=lambda r: r[1])[0],
+                           "start": "couplings 1, spins all +1, one iteration per T"}},
             "roofline": {"bound": "hbm", "achieved": kernels[top]["achieved_gbs"], "peak": peak, "unit": "GB/s",
                          "frac": kernels[top]["achieved_gbs"] / peak, "traffic": ncu_traffic(top, "dmc"), "kernel": top,
                          "peak_source": f"{kind} hbm_gbs", "kernels": kernels},

@@ -67,6 +67,28 @@ class PatternOptimizer:
         return self.loss
 
 
+def gradient_by_temperature(target, temperatures, alpha=10.0, sweeps=1, seed=0, h=0.0, J0=1.0, spins=None,
+                            stream=None):
+    """The temperature study of Sec. "Optimization of the exchange parameters":
+    the size of the coupling gradient depends on T (at low T few spins move,
+    at high T the moves hardly depend on the couplings), so there is a
+    temperature where the optimisation learns fastest.  For each T (beta = 1/T)
+    one iteration from the same start (couplings J0, spins all +1 unless
+    given): `sweeps` relaxed sweeps, the L2 loss to the target and the reverse
+    pass.  Returns [(T, mean |dL/dJ| over all bonds of all lattices, mean
+    loss)]; the sweeps, loss and reverse pass run in the library's kernels."""
+    out = []
+    for T in temperatures:
+        opt = PatternOptimizer(target, beta=1.0 / float(T), alpha=alpha, sweeps=sweeps, seed=seed, h=h, J0=J0,
+                               spins=spins, fused=False)
+        dmc_forward(opt.seed, opt.J, opt.spins, opt.beta, opt.h, opt.alpha, 0, opt.sweeps, opt.tape, stream)
+        dmc_loss(opt.spins, opt.target, opt.gs, opt.loss, stream)
+        dmc_backward(opt.seed, opt.J, opt.spins, opt.tape, opt.beta, opt.h, opt.alpha, 0, opt.sweeps, opt.gs,
+                     opt.gJ, stream)
+        out.append((float(T), float(opt.gJ.abs().mean()), float(opt.loss.mean())))
+    return out
+
+
 class SpinOptimizer:
     """Energy minimisation over the spin values (Sec. "Optimization of the spin
     values") for B lattices with per-bond couplings J [B, 2, L, L] (J = 1: the

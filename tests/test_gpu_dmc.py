@@ -241,3 +241,31 @@ def test_benchmark_shape_sampled():
         cond = condition(J[b], s0[b], beta, h, alpha, b, 3, K)
         tol = 4 * 10 * EPS32 * 2 * K * max(cond, 1.0)
         assert np.abs(got[b] - ref).max() <= tol, b
+
+
+def test_gradient_by_temperature_matches_the_oracle():
+    """The temperature study (coupling-gradient size for one relaxed sweep from
+    the ordered start, per T) on the GPU against the float64 oracle, and its
+    maximum at an intermediate temperature."""
+    L = 16
+    y = np.arange(L)[:, None] * np.ones((1, L))
+    pats = ([np.where((y // w) % 2 == 0, 1.0, -1.0) for w in (2, 3, 4)] +
+            [np.where((y.T // w) % 2 == 0, 1.0, -1.0) for w in (2, 3)])
+    target = torch.from_numpy(np.array(pats, dtype=np.float32)).cuda()
+    Ts = [0.5, 1.0, 2.0, 4.0, 6.0, 10.0, 30.0, 100.0]
+    got = pdmc.gradient_by_temperature(target, Ts, alpha=10.0, sweeps=1, seed=SEED)
+    sizes = [g for _, g, _ in got]
+    k = int(np.argmax(sizes))
+    assert 0 < k < len(Ts) - 1, sizes
+    for T, g, _ in got:
+        ref = []
+        for b, t in enumerate(pats):
+            s = np.ones((L, L))
+            J = np.ones((2, L, L))
+            beta = f32(1.0 / T)
+            tape = odmc.run(s, J, beta, 0.0, 10.0, SEED, b, 0, 1, tape=True)
+            _, gs = odmc.loss(s, t)
+            _, gJ = odmc.backward(tape, J, gs, beta, 0.0, 10.0, SEED, b, 0)
+            ref.append(gJ)
+        want = float(np.abs(np.array(ref)).mean())
+        assert abs(g - want) <= 1e-4 * max(want, 1e-3), (T, g, want)

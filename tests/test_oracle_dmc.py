@@ -157,3 +157,44 @@ def test_spin_step_is_a_clipped_sign_step():
     s = np.array([[0.9, -0.5], [0.0, -1.0]])
     g = np.array([[-1.0, 2.0], [0.0, -0.1]])
     np.testing.assert_array_equal(dmc.spin_step(s, g, 0.5), [[1.0, -1.0], [0.0, -0.5]])
+
+
+def _stripes(L, widths=(2, 3, 4)):
+    y = np.arange(L)[:, None] * np.ones((1, L))
+    return ([np.where((y // w) % 2 == 0, 1.0, -1.0) for w in widths] +
+            [np.where((y.T // w) % 2 == 0, 1.0, -1.0) for w in widths[:2]])
+
+
+def _grad_size(T, J0, L=16, alpha=10.0, seed=7):
+    """Mean |dL/dJ| of one relaxed sweep from all +1 with couplings J0 (the
+    temperature study of Sec. "Optimization of the exchange parameters")."""
+    out = []
+    for b, t in enumerate(_stripes(L)):
+        s = np.ones((L, L))
+        J = np.full((2, L, L), J0)
+        tape = dmc.run(s, J, 1.0 / T, 0.0, alpha, seed, b, 0, 1, tape=True)
+        _, g = dmc.loss(s, t)
+        _, gJ = dmc.backward(tape, J, g, 1.0 / T, 0.0, alpha, seed, b, 0)
+        out.append(gJ)
+    return np.abs(np.array(out)).mean()
+
+
+def test_gradient_size_depends_on_temperature_through_beta_J():
+    """With h = 0 the relaxed dynamics depend on beta J only: doubling T and the
+    couplings gives the same trajectory (same draws, same acceptance values) and
+    halves dL/dJ exactly -- in binary floating point, since the factor is a
+    power of two.  A misplaced beta or J in the forward or reverse pass breaks
+    this."""
+    for T in (0.7, 2.0, 5.0):
+        assert _grad_size(2 * T, 2.0) == _grad_size(T, 1.0) / 2
+
+
+def test_gradient_size_peaks_at_an_intermediate_temperature():
+    """From the ordered start the gradient vanishes at low T (nothing moves)
+    and at high T (the moves no longer depend on the couplings); it is largest
+    in between, the behaviour the paper reports for its pattern optimisation."""
+    Ts = [0.5, 1.0, 2.0, 4.0, 6.0, 10.0, 30.0, 100.0]
+    g = [_grad_size(T, 1.0) for T in Ts]
+    k = int(np.argmax(g))
+    assert 0 < k < len(Ts) - 1, g
+    assert g[0] < 0.01 * g[k] and g[-1] < 0.1 * g[k], g
