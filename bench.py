@@ -15,8 +15,9 @@ One JSON line on stdout (rank 0):
                (one int8 read, one write) / its CUDA-event launch time
   cpu_baseline the CPU oracle on this host's cores, a bounded sample
   e2e          end to end through the C ABI with host buffers: every step
-               uploads the spins from pinned host memory, sweeps, and reads
-               back the spins and that step's statistics
+               uploads the spins from pinned host memory (one bit per spin;
+               int8 spins under e2e.int8_spins), sweeps, and reads back the
+               spins and that step's statistics
 --impl reference times the CPU oracle alone (the reference arm).
 Multi-GPU (torchrun): every rank runs its own 512-lattice batch (weak
 scaling, no data-path collective); time = max over ranks.
@@ -603,8 +604,8 @@ def run_ours(args):
 
     # ---- end to end through the C ABI with host buffers.  Every step is a job:
     # upload the spins from pinned host memory, one sweep, read back the spins
-    # and that sweep's statistics.  Two contexts on two streams double-buffer,
-    # so the upload of step k+1 overlaps the sweep and download of step k.
+    # and that sweep's statistics.  Three contexts on three streams, so the
+    # upload of step k+1 overlaps the sweep and download of step k.
     import ctypes
     L = sm.lib()
     span = sim.spins.numel()
@@ -628,33 +629,53 @@ def run_ours(args):
     ev_up = [torch.cuda.Event() for _ in range(NB)]
     ev_down = [torch.cuda.Event() for _ in range(NB)]
 
-    def e2e_step(k):
+    # the same with one bit per spin on the host (spin_load_spins_packed /
+    # spin_store_spins_packed: unpack and pack kernels around the sweep)
+    nw = sim.packed_words
+    pin_in = torch.empty(nw, dtype=torch.int32, pin_memory=True)
+    pin_out = [torch.empty(nw, dtype=torch.int32, pin_memory=True) for _ in range(NB)]
+    sim.store_spins_packed(pin_in)
+    torch.cuda.synchronize()
+
+    def e2e_step(k, packed):
         x, st = sims[k % NB], streams[k % NB]
         sp = ctypes.c_void_p(st.cuda_stream)
         if k > 0:
             st.wait_event(ev_up[(k - 1) % NB])
-        sm._check(L.spin_load_spins(x.ctx, host_in.data_ptr(), sp), x.ctx, "load")
+        if packed:
+            sm._check(L.spin_load_spins_packed(x.ctx, pin_in.data_ptr(), sp), x.ctx, "load")
+        else:
+            sm._check(L.spin_load_spins(x.ctx, host_in.data_ptr(), sp), x.ctx, "load")
         ev_up[k % NB].record(st)
         sm._check(L.spin_sweep(x.ctx, 1, 1, sp), x.ctx, "sweep")
         if k > 0:
             st.wait_event(ev_down[(k - 1) % NB])
-        sm._check(L.spin_store_spins(x.ctx, host_out[k % NB].data_ptr(), sp), x.ctx, "store")
+        if packed:
+            sm._check(L.spin_store_spins_packed(x.ctx, pin_out[k % NB].data_ptr(), sp), x.ctx, "store")
+        else:
+            sm._check(L.spin_store_spins(x.ctx, host_out[k % NB].data_ptr(), sp), x.ctx, "store")
         ev_down[k % NB].record(st)
         sm._check(L.spin_observables(x.ctx, ctypes.c_int64(x.n_records - 1), 1, d_stats[k % NB].data_ptr(),
                                      None, None, sp), x.ctx, "obs")
         with torch.cuda.stream(st):
             h_stats[k % NB].copy_(d_stats[k % NB], non_blocking=True)
 
-    for k in range(NB):
-        e2e_step(k)
-    barrier(dist)
-    t0 = time.perf_counter()
-    for k in range(args.e2e_steps):
-        e2e_step(k)
-    for st in streams:
-        st.synchronize()
-    barrier(dist)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    def e2e_run(packed):
+        for k in range(NB):
+            e2e_step(k, packed)
+        for st in streams:
+            st.synchronize()
+        barrier(dist)
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            e2e_step(k, packed)
+        for st in streams:
+            st.synchronize()
+        barrier(dist)
+        return max_over_ranks(time.perf_counter() - t0, dist)
+
+    e2e_int8_s = e2e_run(False)
+    e2e_s = e2e_run(True)
     st_host = h_stats[0]
 
     if rank != 0:
@@ -706,9 +727,14 @@ def run_ours(args):
                      "peak_source": f"{peak_kind} hbm_gbs (copy)", "kernels": kernels,
                      "issue": issue_roofline(dom, "uneven512", kms_dom, clk.get("sm_mhz") if clk else None)},
         "e2e": {"value": sites * args.e2e_steps * world / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": span, "d2h_bytes_per_step": span + st_host.numel() * 8,
+                "h2d_bytes_per_step": 4 * nw, "d2h_bytes_per_step": 4 * nw + st_host.numel() * 8,
+                "transfer": "one bit per spin: spin_load_spins_packed uploads the packed state from pinned "
+                            "host memory and unpacks it, one sweep, spin_store_spins_packed packs and "
+                            "downloads the new state, then that sweep's statistics",
                 "pipeline": "three contexts on three streams; uploads and downloads each first in, first "
-                            "out, so the upload of step k+1 overlaps the download of step k"},
+                            "out, so the upload of step k+1 overlaps the download of step k",
+                "int8_spins": {"value": sites * args.e2e_steps * world / e2e_int8_s, "unit": UNIT,
+                               "h2d_bytes_per_step": span, "d2h_bytes_per_step": span + st_host.numel() * 8}},
         "gpu_launches": launches,
         "clocks": clk,
     }

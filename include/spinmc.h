@@ -227,6 +227,18 @@ int spin_get_launch(const spin_ctx *ctx, int32_t out[4]);
 int spin_load_spins(spin_ctx *ctx, const void *host, void *stream);
 int spin_store_spins(spin_ctx *ctx, void *host, void *stream);
 
+/* The same for Ising contexts with one bit per spin on the host: bit e of the
+ * packed buffer (32-bit words, bit e % 32 of word e / 32) is 1 where element e
+ * of the spin span holds -1.  Every lattice's spin_offset must be a multiple of
+ * 32 (the binding aligns offsets to 256); otherwise SPIN_EINVAL.  A load
+ * unpacks the lattices' elements only (other bytes of the span keep their
+ * values) and recomputes the running statistics; a store writes
+ * spin_packed_words(ctx) words, with 0 for the bits outside the lattices.
+ * Not in the paper: an eightfold smaller host transfer than int8 spins. */
+int32_t spin_packed_words(const spin_ctx *ctx);
+int spin_load_spins_packed(spin_ctx *ctx, const uint32_t *host, void *stream);
+int spin_store_spins_packed(spin_ctx *ctx, uint32_t *host, void *stream);
+
 /* Checkpoint = (sweep counter, record count, CPM areas, spins).  With
  * host_blob == NULL, *size receives the size needed. Restoring into a
  * context of the same shape continues the chain bit-identically.       */

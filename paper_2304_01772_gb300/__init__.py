@@ -70,6 +70,9 @@ _SIGS = {
     "spin_profile": (_i32, [_vp, _i32, _i32]),
     "spin_profile_read": (_i32, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64), _vp]),
     "spin_barrier_selftest": (_i32, [_i32, _i32, _i32, _vp]),
+    "spin_packed_words": (_i32, [_vp]),
+    "spin_load_spins_packed": (_i32, [_vp, _vp, _vp]),
+    "spin_store_spins_packed": (_i32, [_vp, _vp, _vp]),
     "spin_sweep_index": (ctypes.c_uint32, [_vp]),
     "spin_gpu_launches": (_i32, [_vp]),
     "spin_last_error": (ctypes.c_char_p, [_vp]),
@@ -385,6 +388,19 @@ class Sim:
 
     def store_spins(self, host, stream=None):
         _check(lib().spin_store_spins(self.ctx, _ptr(host), _stream(stream)), self.ctx, "spin_store_spins")
+
+    @property
+    def packed_words(self):
+        """Words of the bit-packed host buffer (Ising contexts)."""
+        return int(lib().spin_packed_words(self.ctx))
+
+    def load_spins_packed(self, host, stream=None):
+        """Load from one bit per spin (bit e = element e is -1; uint32 / int32 words)."""
+        _check(lib().spin_load_spins_packed(self.ctx, _ptr(host), _stream(stream)), self.ctx, "spin_load_spins_packed")
+
+    def store_spins_packed(self, host, stream=None):
+        _check(lib().spin_store_spins_packed(self.ctx, _ptr(host), _stream(stream)), self.ctx,
+               "spin_store_spins_packed")
 
     def checkpoint(self, stream=None):
         size = ctypes.c_size_t(0)

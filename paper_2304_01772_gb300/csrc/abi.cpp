@@ -101,7 +101,8 @@ struct spin_ctx {
     double *d_cpmJ = nullptr;   // [pairs]
     void *d_scratch = nullptr;  // moments etc.
     size_t scratch_bytes = 0;
-    int *d_flag = nullptr;      // [0] moment overflow, [1] a device wait gave up
+    int *d_flag = nullptr;
+    uint32_t *d_packed = nullptr;   // bit-packed transfer buffer (allocated at first use)      // [0] moment overflow, [1] a device wait gave up
     // host mirrors
     uint32_t t = 0;
     int64_t n_rec = 0;
@@ -778,7 +779,7 @@ void spin_destroy(spin_ctx *ctx) {
                     ctx->d_dvol[0], ctx->d_dvol[1],
                     ctx->d_state, ctx->st.cur, ctx->st.delta, ctx->st.ring, ctx->d_type,
                     ctx->d_J, ctx->d_vol[0], ctx->d_vol[1], ctx->d_thr, ctx->d_latp,
-                    ctx->d_cpmJ, ctx->d_scratch, ctx->d_flag, ctx->d_cpm_acc, ctx->d_cpm_bar};
+                    ctx->d_cpmJ, ctx->d_scratch, ctx->d_flag, ctx->d_cpm_acc, ctx->d_cpm_bar, ctx->d_packed};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -1254,6 +1255,47 @@ int spin_load_spins(spin_ctx *ctx, const void *host, void *stream) {
     }
     CK(launch_stats_from_state(ctx->spins, ctx->model, ctx->d_lats, ctx->n_lat, ctx->maxL, ctx->width, ctx->d_type,
                                ctx->n_types, ctx->d_vol[0], ctx->n_cells, ctx->target, ctx->st.cur, s));
+    return SPIN_OK;
+}
+
+int32_t spin_packed_words(const spin_ctx *ctx) {
+    if (!ctx || ctx->model != SPIN_ISING) return SPIN_EINVAL;
+    return (int32_t)((ctx->span_elems + 31) / 32);
+}
+
+static int packed_ready(spin_ctx *ctx) {
+    if (ctx->model != SPIN_ISING) return fail(ctx, SPIN_EINVAL, "bit-packed transfer is for Ising contexts");
+    for (const auto &d : ctx->lat)
+        if (d.spin_offset % 32) return fail(ctx, SPIN_EINVAL, "bit-packed transfer needs spin_offset % 32 == 0");
+    if (!ctx->d_packed && cudaMalloc(&ctx->d_packed, sizeof(uint32_t) * ((ctx->span_elems + 31) / 32)) != cudaSuccess) {
+        ctx->d_packed = nullptr;
+        return fail(ctx, SPIN_ENOMEM, "packed transfer buffer");
+    }
+    return SPIN_OK;
+}
+
+int spin_load_spins_packed(spin_ctx *ctx, const uint32_t *host, void *stream) {
+    if (!ctx || !host) return SPIN_EINVAL;
+    int rc = packed_ready(ctx);
+    if (rc) return rc;
+    cudaStream_t s = S(stream);
+    const size_t nw = (ctx->span_elems + 31) / 32;
+    CK(cudaMemcpyAsync(ctx->d_packed, host, sizeof(uint32_t) * nw, cudaMemcpyHostToDevice, s));
+    CK(launch_unpack_spins(ctx->d_packed, static_cast<int8_t *>(ctx->spins), ctx->d_lats, ctx->n_lat, ctx->maxL, s));
+    CK(launch_stats_from_state(ctx->spins, ctx->model, ctx->d_lats, ctx->n_lat, ctx->maxL, ctx->width, ctx->d_type,
+                               ctx->n_types, ctx->d_vol[0], ctx->n_cells, ctx->target, ctx->st.cur, s));
+    return SPIN_OK;
+}
+
+int spin_store_spins_packed(spin_ctx *ctx, uint32_t *host, void *stream) {
+    if (!ctx || !host) return SPIN_EINVAL;
+    int rc = packed_ready(ctx);
+    if (rc) return rc;
+    cudaStream_t s = S(stream);
+    const size_t nw = (ctx->span_elems + 31) / 32;
+    CK(launch_pack_spins(static_cast<const int8_t *>(ctx->spins), ctx->d_packed, nw, ctx->d_lats, ctx->n_lat,
+                         ctx->maxL, s));
+    CK(cudaMemcpyAsync(host, ctx->d_packed, sizeof(uint32_t) * nw, cudaMemcpyDeviceToHost, s));
     return SPIN_OK;
 }
 

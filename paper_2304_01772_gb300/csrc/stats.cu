@@ -490,4 +490,80 @@ cudaError_t launch_grad_i128(const void *moments, int rows, GradParams p, double
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------ bit-packed host transfer
+namespace {
+
+// Four sign bits (bit 7 of each byte) gathered into a nibble: the products of
+// the masked bits with 1 + 2^7 + 2^14 + 2^21 land on distinct positions, so
+// bits 28..31 are the four signs in byte order.
+__device__ __forceinline__ uint32_t sign_nibble(uint32_t w) { return ((w & 0x80808080u) * 0x00204081u) >> 28; }
+
+// The inverse: four bits -> four bytes 0x01 (bit 0) / 0xFF (bit 1).
+__device__ __forceinline__ uint32_t nibble_bytes(uint32_t n) {
+    const uint32_t spread = (n * 0x00204081u) & 0x01010101u;
+    return 0x01010101u + spread * 0xFEu;
+}
+
+// One thread per 32-bit word of the packed buffer overlapping lattice
+// blockIdx.y (offsets are multiples of 32, so no word holds two lattices).
+__global__ void pack_spins_kernel(const int8_t *spins, uint32_t *words, const LatDev *lats) {
+    const LatDev ld = lats[blockIdx.y];
+    const size_t o = ld.offset, end = o + (size_t)ld.L * ld.L;
+    for (size_t w = (o >> 5) + blockIdx.x * (size_t)blockDim.x + threadIdx.x; (w << 5) < end;
+         w += (size_t)gridDim.x * blockDim.x) {
+        const size_t e0 = w << 5;
+        uint32_t bits = 0;
+        if (e0 + 32 <= end && ((reinterpret_cast<uintptr_t>(spins + e0) & 15) == 0)) {
+            const uint4 a = *reinterpret_cast<const uint4 *>(spins + e0);
+            const uint4 b = *reinterpret_cast<const uint4 *>(spins + e0 + 16);
+            const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) bits |= sign_nibble(v[k]) << (4 * k);
+        } else {
+            for (int i = 0; i < 32 && e0 + i < end; ++i)
+                if (spins[e0 + i] < 0) bits |= 1u << i;
+        }
+        words[w] = bits;
+    }
+}
+
+__global__ void unpack_spins_kernel(const uint32_t *words, int8_t *spins, const LatDev *lats) {
+    const LatDev ld = lats[blockIdx.y];
+    const size_t o = ld.offset, end = o + (size_t)ld.L * ld.L;
+    for (size_t w = (o >> 5) + blockIdx.x * (size_t)blockDim.x + threadIdx.x; (w << 5) < end;
+         w += (size_t)gridDim.x * blockDim.x) {
+        const size_t e0 = w << 5;
+        const uint32_t bits = words[w];
+        if (e0 + 32 <= end && ((reinterpret_cast<uintptr_t>(spins + e0) & 15) == 0)) {
+            uint32_t v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = nibble_bytes((bits >> (4 * k)) & 0xFu);
+            *reinterpret_cast<uint4 *>(spins + e0) = make_uint4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<uint4 *>(spins + e0 + 16) = make_uint4(v[4], v[5], v[6], v[7]);
+        } else {
+            for (int i = 0; i < 32 && e0 + i < end; ++i) spins[e0 + i] = ((bits >> i) & 1u) ? -1 : 1;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_unpack_spins(const uint32_t *words, int8_t *spins, const LatDev *lats, int n_lat, int maxL,
+                                cudaStream_t s) {
+    const int wpl = (int)(((size_t)maxL * maxL + 31) / 32) + 1;
+    dim3 grid((wpl + 255) / 256 < 64 ? (wpl + 255) / 256 : 64, n_lat);
+    unpack_spins_kernel<<<grid, 256, 0, s>>>(words, spins, lats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_spins(const int8_t *spins, uint32_t *words, size_t n_words, const LatDev *lats, int n_lat,
+                              int maxL, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(words, 0, n_words * sizeof(uint32_t), s);
+    if (e) return e;
+    const int wpl = (int)(((size_t)maxL * maxL + 31) / 32) + 1;
+    dim3 grid((wpl + 255) / 256 < 64 ? (wpl + 255) / 256 : 64, n_lat);
+    pack_spins_kernel<<<grid, 256, 0, s>>>(spins, words, lats);
+    return cudaGetLastError();
+}
+
 }  // namespace spinmc

@@ -572,3 +572,47 @@ def test_empty_calls_change_nothing():
         sim.grad(0, 1)
     mom = sim.moments(0, 1).cpu().numpy()
     assert list(mom[:, 0]) == [1, 1]            # one sample per lattice
+
+
+def test_bit_packed_transfer():
+    """One bit per spin on the host: a store packs exactly the lattices'
+    signs (bits outside them 0), a load unpacks into the lattices only (other
+    bytes of the span untouched), recounts the statistics, and the chain from the
+    loaded state is the oracle's."""
+    lats = MIXED[:8]
+    sim = make_ising(lats, max_record=8)
+    sim.sweep(3, record=True)
+    nw = sim.packed_words
+    span = int(sim.spins.numel())
+    assert nw == (span + 31) // 32
+    words = torch.zeros(nw, dtype=torch.int32).pin_memory()
+    sim.store_spins_packed(words)
+    torch.cuda.synchronize()
+    full = sim.spins.cpu().numpy()
+    inside = np.zeros(nw * 32, dtype=bool)
+    for off, d in zip(sim.offsets, lats):
+        inside[off:off + d["L"] ** 2] = True
+    bits = np.zeros(nw * 32, dtype=np.uint8)
+    bits[:span] = (full < 0) & inside[:span]
+    assert np.array_equal(words.numpy().view(np.uint8), np.packbits(bits, bitorder="little"))
+    rng = np.random.default_rng(8)
+    new = torch.from_numpy(rng.integers(-2 ** 31, 2 ** 31, nw, dtype=np.int64).astype(np.int32)).pin_memory()
+    before = sim.spins.cpu().numpy()
+    sim.load_spins_packed(new)
+    torch.cuda.synchronize()
+    after = sim.spins.cpu().numpy()
+    nb = np.unpackbits(new.numpy().view(np.uint8), bitorder="little")[:span]
+    want = np.where(nb == 1, -1, 1).astype(np.int8)
+    assert np.array_equal(after[inside[:span]], want[inside[:span]])
+    assert np.array_equal(after[~inside[:span]], before[~inside[:span]])
+    init = {i: lattice_np(sim, i) for i in range(len(lats))}
+    cur = sim.current_stats().cpu().numpy()
+    for i in range(len(lats)):
+        assert list(cur[i]) == list(oracle.ising_stats(init[i])), i
+    first = sim.n_records
+    sim.sweep(2, record=True)
+    out, stats = oracle_ising_chain(lats, SEED, init, 3, 2)
+    st = sim.observables_host(first, 2)[0]
+    for i in range(len(lats)):
+        assert np.array_equal(lattice_np(sim, i), out[i]), i
+        assert np.array_equal(st[:, i, :], stats[i]), i
