@@ -1281,9 +1281,15 @@ int spin_load_spins_packed(spin_ctx *ctx, const uint32_t *host, void *stream) {
     cudaStream_t s = S(stream);
     const size_t nw = (ctx->span_elems + 31) / 32;
     CK(cudaMemcpyAsync(ctx->d_packed, host, sizeof(uint32_t) * nw, cudaMemcpyHostToDevice, s));
-    CK(launch_unpack_spins(ctx->d_packed, static_cast<int8_t *>(ctx->spins), ctx->d_lats, ctx->n_lat, ctx->maxL, s));
-    CK(launch_stats_from_state(ctx->spins, ctx->model, ctx->d_lats, ctx->n_lat, ctx->maxL, ctx->width, ctx->d_type,
-                               ctx->n_types, ctx->d_vol[0], ctx->n_cells, ctx->target, ctx->st.cur, s));
+    // square lattices: the statistics of the loaded state are counted from the bits
+    // while unpacking; other geometries are recounted from the unpacked state
+    bool square = true;
+    for (const auto &d : ctx->lat) square = square && d.geometry == 0;
+    CK(launch_unpack_spins(ctx->d_packed, static_cast<int8_t *>(ctx->spins), ctx->d_lats, ctx->n_lat, ctx->maxL,
+                           square ? ctx->st.cur : nullptr, s));
+    if (!square)
+        CK(launch_stats_from_state(ctx->spins, ctx->model, ctx->d_lats, ctx->n_lat, ctx->maxL, ctx->width,
+                                   ctx->d_type, ctx->n_types, ctx->d_vol[0], ctx->n_cells, ctx->target, ctx->st.cur, s));
     return SPIN_OK;
 }
 

@@ -401,10 +401,12 @@ cudaError_t launch_cpm_batch_init(int n_lat, int L, int n_cells, int side, int c
 cudaError_t launch_dmc_step(const DmcStepArgs &a, cudaStream_t s);
 
 // One bit per Ising spin on the host side (bit e of words[] = element e is -1):
-// unpack the lattices' elements from words (other bytes untouched) / pack them
-// into words (bits outside the lattices 0).  Lattice offsets are multiples of 32.
+// unpack the lattices' elements from words (other bytes untouched), counting
+// the loaded state's statistics into cur [n_lat][2] = (M, B) of square lattices
+// when cur is not null / pack them into
+// words (bits outside the lattices 0).  Lattice offsets are multiples of 32.
 cudaError_t launch_unpack_spins(const uint32_t *words, int8_t *spins, const LatDev *lats, int n_lat, int maxL,
-                                cudaStream_t s);
+                                int64_t *cur, cudaStream_t s);
 cudaError_t launch_pack_spins(const int8_t *spins, uint32_t *words, size_t n_words, const LatDev *lats, int n_lat,
                               int maxL, cudaStream_t s);
 

@@ -527,9 +527,24 @@ __global__ void pack_spins_kernel(const int8_t *spins, uint32_t *words, const La
     }
 }
 
-__global__ void unpack_spins_kernel(const uint32_t *words, int8_t *spins, const LatDev *lats) {
-    const LatDev ld = lats[blockIdx.y];
-    const size_t o = ld.offset, end = o + (size_t)ld.L * ld.L;
+// Bit of element e (1: the spin is -1).
+__device__ __forceinline__ int packed_bit(const uint32_t *words, size_t e) { return (words[e >> 5] >> (e & 31)) & 1; }
+
+// Unpack, and count the statistics of the loaded state on the way (cur must be
+// zero on entry): M = sum s, B = sum over right and down bonds of s s'.  Rows
+// of 32k spins are whole words: a word's right neighbours are its bits shifted
+// by one with bit 0 of the next word of the row (or of the row's first word),
+// its down neighbours the word of the next row, and unequal pairs are popcounts
+// of xors.  Other sides count bond by bond.
+__global__ void unpack_spins_kernel(const uint32_t *words, int8_t *spins, const LatDev *lats, int64_t *cur) {
+    __shared__ long long red[2][8];
+    const int lat = blockIdx.y;
+    const LatDev ld = lats[lat];
+    const int L = ld.L;
+    const size_t o = ld.offset, end = o + (size_t)L * L;
+    const bool rows_whole = (L & 31) == 0;
+    const int wpr = L >> 5;   // words per row when rows_whole
+    long long m = 0, b = 0;
     for (size_t w = (o >> 5) + blockIdx.x * (size_t)blockDim.x + threadIdx.x; (w << 5) < end;
          w += (size_t)gridDim.x * blockDim.x) {
         const size_t e0 = w << 5;
@@ -543,16 +558,60 @@ __global__ void unpack_spins_kernel(const uint32_t *words, int8_t *spins, const 
         } else {
             for (int i = 0; i < 32 && e0 + i < end; ++i) spins[e0 + i] = ((bits >> i) & 1u) ? -1 : 1;
         }
+        if (!cur) continue;
+        if (rows_whole) {
+            const size_t wl = w - (o >> 5);              // word index within the lattice
+            const int r = (int)(wl / wpr), q = (int)(wl - (size_t)r * wpr);
+            const size_t row0 = (o >> 5) + (size_t)r * wpr;
+            const uint32_t nxt = words[row0 + (q + 1 == wpr ? 0 : q + 1)];
+            const uint32_t right = (bits >> 1) | (nxt << 31);
+            const uint32_t down = words[(o >> 5) + (size_t)(r + 1 == L ? 0 : r + 1) * wpr + q];
+            m += 32 - 2 * __popc(bits);
+            b += 64 - 2 * (__popc(bits ^ right) + __popc(bits ^ down));
+        } else {
+            for (int i = 0; i < 32 && e0 + i < end; ++i) {
+                const size_t e = e0 + i, k = e - o;
+                const int y = (int)(k / L), x = (int)(k - (size_t)y * L);
+                const int sb = packed_bit(words, e);
+                const int rb = packed_bit(words, o + (size_t)y * L + (x + 1 == L ? 0 : x + 1));
+                const int db = packed_bit(words, o + (size_t)(y + 1 == L ? 0 : y + 1) * L + x);
+                m += 1 - 2 * sb;
+                b += (sb == rb ? 1 : -1) + (sb == db ? 1 : -1);
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        m += __shfl_xor_sync(0xFFFFFFFFu, m, off);
+        b += __shfl_xor_sync(0xFFFFFFFFu, b, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = m;
+        red[1][threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && cur) {
+        long long tm = 0, tb = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            tm += red[0][k];
+            tb += red[1][k];
+        }
+        if (tm) atomicAdd(reinterpret_cast<unsigned long long *>(cur + 2 * lat), (unsigned long long)tm);
+        if (tb) atomicAdd(reinterpret_cast<unsigned long long *>(cur + 2 * lat + 1), (unsigned long long)tb);
     }
 }
 
 }  // namespace
 
 cudaError_t launch_unpack_spins(const uint32_t *words, int8_t *spins, const LatDev *lats, int n_lat, int maxL,
-                                cudaStream_t s) {
+                                int64_t *cur, cudaStream_t s) {
+    if (cur) {
+        cudaError_t e = cudaMemsetAsync(cur, 0, sizeof(int64_t) * 2 * (size_t)n_lat, s);
+        if (e) return e;
+    }
     const int wpl = (int)(((size_t)maxL * maxL + 31) / 32) + 1;
     dim3 grid((wpl + 255) / 256 < 64 ? (wpl + 255) / 256 : 64, n_lat);
-    unpack_spins_kernel<<<grid, 256, 0, s>>>(words, spins, lats);
+    unpack_spins_kernel<<<grid, 256, 0, s>>>(words, spins, lats, cur);
     return cudaGetLastError();
 }
 
