@@ -385,12 +385,18 @@ KERNEL_SECTIONS = {
                            "cudaError_t launch_potts_strip("),
 }
 
+# the host code that cuts a kernel's launch into work items (its counters depend on it)
+PLANNER_SECTIONS = {
+    "ising_strip_kernel": ("// Ising strip items:", "// Work list of the batched launch"),
+}
+
 
 def kernel_source_hash(kernel="ising_strip_kernel"):
     """Hash of the source of one kernel's section of its .cu file, the strip
-    helpers and the part of internal.h the kernel depends on (up to its launch
-    declaration), so that counters taken on an unchanged kernel stay valid while
-    other code changes."""
+    helpers, the part of internal.h the kernel depends on (up to its launch
+    declaration) and the host code that cuts its launch into items, so that
+    counters taken on an unchanged kernel and work list stay valid while other
+    code changes."""
     csrc = os.path.join(ROOT, "paper_2304_01772_gb300", "csrc")
     fname, a, b, hdr_end = KERNEL_SECTIONS.get(kernel, ("sweep_ising.cu", "", "", ""))
     text = open(os.path.join(csrc, fname)).read()
@@ -402,6 +408,11 @@ def kernel_source_hash(kernel="ising_strip_kernel"):
     h = hashlib.sha256(text.encode())
     h.update(hdr.encode())
     h.update(open(os.path.join(csrc, "strip.cuh"), "rb").read())
+    if kernel in PLANNER_SECTIONS:   # how the launch's rows are cut into items
+        pa, pb = PLANNER_SECTIONS[kernel]
+        plan = open(os.path.join(csrc, "abi.cpp")).read()
+        if pa in plan and pb in plan:
+            h.update(plan[plan.index(pa):plan.index(pb)].encode())
     return h.hexdigest()[:16]
 
 

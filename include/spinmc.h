@@ -206,8 +206,10 @@ int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_
  * the persistent form: all Monte Carlo steps of a call in one cooperative
  * launch with bounded grid barriers between the sub-steps).
  * use_graph: capture the sweep loop in a CUDA graph.  tile_rows: work-item
- * height in rows for mode 0 (0 = keep the current value, -1 = default items of
- * about 32-64 KB).  threads: CTA size of the tile kernel (128, 256 or 512; 0 =
+ * height in rows for mode 0 (0 = keep the current value, -1 = default items:
+ * about 32 KB for the tile kernel; for the Ising row-strip kernel each strip
+ * lattice cut into equal row ranges, at most one item per resident warp of the
+ * launch and each as small as that allows, at least 8 rows).  threads: CTA size of the tile kernel (128, 256 or 512; 0 =
  * keep) and of the square-lattice resident kernel (also 1024 there); the warp
  * row-strip kernel uses 8 warps per CTA for 512, else 4.
  * Results do not depend on any of these. */

@@ -347,6 +347,38 @@ void drop_graphs(spin_ctx *ctx) {
         }
 }
 
+// Ising strip items: warps take items round robin, so the launch lasts as long
+// as the warp with the most rows.  Items are cut so that their count fits the
+// resident warps `budget` (times the rounds), each lattice into equal row
+// ranges of at most the smallest per-item site count that allows, and never
+// thinner than kStripMinRows (every item recomputes a halo row per colour).
+constexpr int kStripRounds = 1;
+constexpr int kStripMinRows = 8;
+
+void balanced_strip_items(const spin_ctx *ctx, const std::vector<int> &ids, size_t budget,
+                          std::vector<Item> &out) {
+    auto pieces = [&](int L, size_t per) {
+        const size_t k = ((size_t)L * L + per - 1) / per;
+        return (int)std::min<size_t>(k, (size_t)std::max(1, L / kStripMinRows));
+    };
+    size_t lo = 1, hi = 1;
+    for (int id : ids) hi = std::max(hi, (size_t)ctx->lat[id].L * ctx->lat[id].L);
+    while (lo < hi) {   // smallest per-item site count whose pieces fit the budget
+        const size_t mid = lo + (hi - lo) / 2;
+        size_t n = 0;
+        for (int id : ids) n += (size_t)pieces(ctx->lat[id].L, mid);
+        if (n <= budget) hi = mid;
+        else lo = mid + 1;
+    }
+    for (int id : ids) {
+        const int L = ctx->lat[id].L, k = pieces(L, lo);
+        for (int i = 0; i < k; ++i) {
+            const int r0 = (int)((int64_t)i * L / k), r1 = (int)((int64_t)(i + 1) * L / k);
+            out.push_back(Item{id, r0, r1 - r0, 0});
+        }
+    }
+}
+
 // Work list of the batched launch over the vectorisable lattices.
 int plan(spin_ctx *ctx) {
     drop_graphs(ctx);
@@ -410,13 +442,17 @@ int plan(spin_ctx *ctx) {
         // lattices over the resident warps in about one wave (the recomputed
         // halo costs one row per item, so items stay as tall as that allows).
         const size_t slots = (size_t)ctx->sm_count * std::max(1, per_sm) * ctx->strip_warps;
-        for (int id : strip_ids) {
-            const int L = ctx->lat[id].L;
-            int def_rows = 65536 / L;
-            if (ctx->model == SPIN_POTTS)
-                def_rows = (int)std::min<size_t>(65536 / L, std::max<size_t>(4, (strip_bytes + slots * L - 1) / (slots * L)));
-            int rows = std::max(1, std::min(L, ctx->tile_rows > 0 ? ctx->tile_rows : def_rows));
-            for (int r0 = 0; r0 < L; r0 += rows) strip.push_back(Item{id, r0, std::min(rows, L - r0), 0});
+        if (ctx->model == SPIN_ISING && ctx->tile_rows <= 0) {
+            balanced_strip_items(ctx, strip_ids, slots * kStripRounds, strip);
+        } else {
+            for (int id : strip_ids) {
+                const int L = ctx->lat[id].L;
+                int def_rows = 65536 / L;
+                if (ctx->model == SPIN_POTTS)
+                    def_rows = (int)std::min<size_t>(65536 / L, std::max<size_t>(4, (strip_bytes + slots * L - 1) / (slots * L)));
+                int rows = std::max(1, std::min(L, ctx->tile_rows > 0 ? ctx->tile_rows : def_rows));
+                for (int r0 = 0; r0 < L; r0 += rows) strip.push_back(Item{id, r0, std::min(rows, L - r0), 0});
+            }
         }
         ctx->n_strip = (int)strip.size();
         CK(cudaMalloc(&ctx->d_strip, sizeof(Item) * strip.size()));
@@ -1402,7 +1438,8 @@ int spin_autotune(spin_ctx *ctx, int32_t sweeps_per_trial, void *stream) {
     if (rc) return rc;
     struct Cand { int mode, tile, threads; };
     // batched form: CTA size (tile kernel) / warps per CTA (strip kernel: 4 for
-    // 128 and 256, 8 for 512) and work-item height (0 = 64 KB items); plain form.
+    // 128 and 256, 8 for 512) and work-item height (0 = the default items: for
+    // the Ising strip kernel one per resident warp); plain form.
     std::vector<Cand> cands;
     for (int th : {128, 256, 512})
         for (int tr : {0, 8, 16, 32, 64}) cands.push_back({0, tr, th});
