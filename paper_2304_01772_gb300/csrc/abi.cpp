@@ -1451,18 +1451,26 @@ int spin_autotune(spin_ctx *ctx, int32_t sweeps_per_trial, void *stream) {
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
     Cand bc = {0, 16, 256};
+    // a trial lasts at least about kMinTrialMs: short ones (small batches,
+    // microseconds per sweep) are repeated with proportionally more sweeps
+    constexpr float kMinTrialMs = 1.0f;
     for (const Cand &c : cands) {
         rc = spin_set_launch(ctx, c.mode, 1, c.tile ? c.tile : -1, c.threads);
         if (rc) continue;
         rc = spin_sweep(ctx, 2, 0, stream);  // warm-up, graph capture
         if (rc) return rc;
-        CK(cudaEventRecord(e0, s));
-        rc = spin_sweep(ctx, sweeps_per_trial, 0, stream);
-        if (rc) return rc;
-        CK(cudaEventRecord(e1, s));
-        CK(cudaEventSynchronize(e1));
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        for (int n = sweeps_per_trial, k = 0;; ++k) {
+            CK(cudaEventRecord(e0, s));
+            rc = spin_sweep(ctx, n, 0, stream);
+            if (rc) return rc;
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= (float)n;                    // per sweep
+            if (ms * n >= 0.5f * kMinTrialMs || n >= 4096 || k == 3) break;
+            n = std::min(4096, ((int)(kMinTrialMs / std::max(ms, 1e-4f)) + 2) & ~1);   // even: whole graphs
+        }
         if (ms < best) {
             best = ms;
             bc = c;

@@ -157,77 +157,6 @@ __global__ void __launch_bounds__(THREADS) ising_fused_kernel(IsingSweepArgs a) 
     }
 }
 
-// Resident form: one CTA per lattice keeps the whole lattice in shared memory
-// for all n sweeps of a call (small lattices, launch-latency-bound batches).
-// Statistics are reduced by the block after every sweep and recorded by the
-// CTA itself; the sweep and record counters come from the host (t0, rec0).
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) ising_resident_kernel(ResidentArgs a) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ TabEntry stab[kTabStride];
-    __shared__ int red[2 * (THREADS / 32)];
-    __shared__ long long cur_s[2];
-    const int lat = blockIdx.x;
-    const LatDev ld = a.lats[lat];
-    const int L = ld.L, Lv = L >> 4;
-    uint4 *sm4 = reinterpret_cast<uint4 *>(sm);
-    const uint32_t *sm32 = reinterpret_cast<const uint32_t *>(sm);
-    uint4 *G = reinterpret_cast<uint4 *>(a.spins + ld.offset);
-    for (int v = threadIdx.x; v < L * Lv; v += THREADS) sm4[v] = G[v];
-    if (threadIdx.x < kTabStride) stab[threadIdx.x] = a.tabs[lat * kTabStride + threadIdx.x];
-    if (threadIdx.x < 2) cur_s[threadIdx.x] = a.st.cur[2 * lat + threadIdx.x];
-    __syncthreads();
-    for (int sweep = 0; sweep < a.n_sweeps; ++sweep) {
-        const uint32_t t = a.t0 + (uint32_t)sweep;
-        int acc = 0;
-        for (int c = 0; c < 2; ++c) {
-            const PhiloxPrefix P = philox_prefix((uint32_t)lat, t, (uint32_t)c, a.rk);
-            for (int v = threadIdx.x; v < L * Lv; v += THREADS) {
-                const int i = v / Lv, j = v - i * Lv;
-                const int iu = i == 0 ? L - 1 : i - 1, id = i == L - 1 ? 0 : i + 1;
-                const uint4 Cc = sm4[v];
-                const uint4 Uc = sm4[iu * Lv + j];
-                const uint4 Dc = sm4[id * Lv + j];
-                const uint32_t lw = sm32[(i * Lv + (j == 0 ? Lv - 1 : j - 1)) * 4 + 3];
-                const uint32_t rw = sm32[(i * Lv + (j == Lv - 1 ? 0 : j + 1)) * 4];
-                const uint32_t g0 = (uint32_t)i * (uint32_t)(L >> 3) + 2u * (uint32_t)j;
-                sm4[v] = ising_chunk_r(Cc, Uc, Dc, lw, rw, (c ^ i) & 1, philox_from_prefix(g0, P, a.rk),
-                                       philox_from_prefix(g0 + 1u, P, a.rk), stab, true, acc);
-            }
-            __syncthreads();
-        }
-        int dm = (int)(int16_t)(acc & 0xFFFF);
-        int db = (acc - dm) >> 16;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            dm += __shfl_xor_sync(0xFFFFFFFFu, dm, o);
-            db += __shfl_xor_sync(0xFFFFFFFFu, db, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            red[2 * (threadIdx.x >> 5)] = dm;
-            red[2 * (threadIdx.x >> 5) + 1] = db;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            long long sm_ = 0, sb_ = 0;
-            for (int w = 0; w < THREADS / 32; ++w) {
-                sm_ += red[2 * w];
-                sb_ += red[2 * w + 1];
-            }
-            cur_s[0] += sm_;
-            cur_s[1] += sb_;
-            if (a.record && a.st.cap > 0) {
-                const long long slot = (a.rec0 + sweep) % a.st.cap;
-                a.st.ring[(slot * a.st.n_lat + lat) * 2] = cur_s[0];
-                a.st.ring[(slot * a.st.n_lat + lat) * 2 + 1] = cur_s[1];
-            }
-        }
-        __syncthreads();
-    }
-    for (int v = threadIdx.x; v < L * Lv; v += THREADS) G[v] = sm4[v];
-    if (threadIdx.x < 2) a.st.cur[2 * lat + threadIdx.x] = cur_s[threadIdx.x];
-}
-
 // Triangular lattices (geometry 1) resident in shared memory for all sweeps
 // of a call, one block per lattice; per sweep three colour passes, each
 // thread taking one Philox group (four consecutive compressed sites of the
@@ -764,12 +693,22 @@ __device__ __forceinline__ uint4 to_x8(uint4 v) {
 __device__ __forceinline__ uint32_t from_x8(uint32_t w) { return ((w >> 3) * 0xFEu) + 0x01010101u; }
 
 // Byte selectors (PRMT) and flip masks of the two active bytes P and P + 2.
+// A selector takes the site's key byte as byte 0 and bytes 1..3 from the
+// table's shared-memory address, whose byte 0 is zero: the result is the
+// address of the site's table entry.
 struct RowPar {
     uint32_t sel0, sel1, fm0, fm1;
 };
 
 __device__ __forceinline__ RowPar row_par(int P) {
-    return RowPar{0x4440u + (uint32_t)P, 0x4442u + (uint32_t)P, 8u << (8 * P), 8u << (8 * P + 16)};
+    return RowPar{0x7650u + (uint32_t)P, 0x7652u + (uint32_t)P, 8u << (8 * P), 8u << (8 * P + 16)};
+}
+
+// One 8-byte table entry at a shared-memory address.
+__device__ __forceinline__ uint2 lds_entry(uint32_t addr) {
+    uint2 v;
+    asm("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+    return v;
 }
 
 // Metropolis decision of one site without a branch: if u <= thr, flip the
@@ -786,12 +725,11 @@ __device__ __forceinline__ void accept_site(uint32_t &w, int &acc, uint32_t u, u
 // Colour sub-step of one 16-byte chunk in x8 form.
 __device__ __forceinline__ uint4 chunk_x8(uint4 C, uint4 U, uint4 D, uint32_t lw, uint32_t rw,
                                           uint4 ra, uint4 rb, const RowPar &rp,
-                                          const TabEntry *stab, int &acc) {
+                                          uint32_t stab, int &acc) {
     const uint32_t w[6] = {lw, C.x, C.y, C.z, C.w, rw};
     const uint32_t up[4] = {U.x, U.y, U.z, U.w};
     const uint32_t dn[4] = {D.x, D.y, D.z, D.w};
     const uint32_t rnd[8] = {ra.x, ra.y, ra.z, ra.w, rb.x, rb.y, rb.z, rb.w};
-    const char *tb = reinterpret_cast<const char *>(stab);
     uint32_t out[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -800,8 +738,8 @@ __device__ __forceinline__ uint4 chunk_x8(uint4 C, uint4 U, uint4 D, uint32_t lw
         const uint32_t rt = __funnelshift_r(W, w[i + 2], 8);
         const uint32_t key = up[i] + dn[i] + lf + rt + W * 5u;
         // table entries are 8-byte aligned: one 64-bit shared load each
-        const uint2 e0 = *reinterpret_cast<const uint2 *>(tb + __byte_perm(key, 0u, rp.sel0));
-        const uint2 e1 = *reinterpret_cast<const uint2 *>(tb + __byte_perm(key, 0u, rp.sel1));
+        const uint2 e0 = lds_entry(__byte_perm(key, stab, rp.sel0));
+        const uint2 e1 = lds_entry(__byte_perm(key, stab, rp.sel1));
         uint32_t nw = W;
         accept_site(nw, acc, rnd[2 * i], e0, rp.fm0);
         accept_site(nw, acc, rnd[2 * i + 1], e1, rp.fm1);
@@ -816,8 +754,8 @@ struct StripCtx {
     uint4 *ring;              // kRing * kRowChunks chunks of this warp
     int L, Lv, cpl, r0, nrows, lane;
     PhiloxPrefix P0, P1;
-    const TabEntry *tab_cnt;  // statistics deltas
-    const TabEntry *tab_halo; // same thresholds, zero deltas (recomputed halo rows)
+    uint32_t tab_cnt;         // shared address (byte 0 zero) of the table with statistics deltas
+    uint32_t tab_halo;        // same thresholds, zero deltas (recomputed halo rows)
 };
 
 __device__ __forceinline__ uint4 *slot(const StripCtx &x, int r) {
@@ -840,7 +778,7 @@ __device__ __forceinline__ void phase_chunk(int j, int colour, uint4 *rc, const 
                                             const uint4 *rd, uint4 *gout, const uint4 &C,
                                             uint32_t lw, uint32_t rw, uint32_t gyb,
                                             const RowPar &rp, const PhiloxPrefix &PP,
-                                            const TabEntry *stab, const PhiloxKeys &rk, int &acc) {
+                                            uint32_t stab, const PhiloxKeys &rk, int &acc) {
     const uint4 U = ru[j];
     const uint4 Dn = rd[j];
     const uint32_t g0 = gyb + 2u * (uint32_t)j;
@@ -865,7 +803,7 @@ __device__ __forceinline__ void row_phase(const StripCtx &x, int r, int colour,
     const int y = wrap_row(x.r0 + r, x.L);
     const RowPar rp = row_par((colour ^ y) & 1);
     const PhiloxPrefix &PP = colour ? x.P1 : x.P0;
-    const TabEntry *stab = (r >= 0 && r < x.nrows) ? x.tab_cnt : x.tab_halo;
+    const uint32_t stab = (r >= 0 && r < x.nrows) ? x.tab_cnt : x.tab_halo;
     uint4 *rc = slot(x, r);
     const uint4 *ru = slot(x, r - 1);
     const uint4 *rd = slot(x, r + 1);
@@ -939,7 +877,8 @@ __device__ void strip_item(const StripCtx &x, const PhiloxKeys &rk, int &dm, int
 template <int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) ising_strip_kernel(IsingSweepArgs a) {
     extern __shared__ __align__(16) uint4 ring_all[];
-    __shared__ TabEntry tabs[WARPS][2][kTabStride];
+    // 256-byte tables: an entry's address is the table's with byte 0 replaced
+    __shared__ __align__(256) TabEntry tabs[WARPS][2][256 / sizeof(TabEntry)];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t t = a.state->t;
     const int gw = blockIdx.x * WARPS + warp, nw = gridDim.x * WARPS;
@@ -964,8 +903,8 @@ __global__ void __launch_bounds__(WARPS * 32) ising_strip_kernel(IsingSweepArgs 
         x.lane = lane;
         x.P0 = philox_prefix((uint32_t)w.lat, t, 0u, a.rk);
         x.P1 = philox_prefix((uint32_t)w.lat, t, 1u, a.rk);
-        x.tab_cnt = tabs[warp][0];
-        x.tab_halo = tabs[warp][1];
+        x.tab_cnt = (uint32_t)__cvta_generic_to_shared(tabs[warp][0]);
+        x.tab_halo = (uint32_t)__cvta_generic_to_shared(tabs[warp][1]);
         int dm = 0, db = 0;
         strip_item(x, a.rk, dm, db);
 #pragma unroll
@@ -998,6 +937,94 @@ __global__ void copy_lattices_kernel(const unsigned char *src, unsigned char *ds
              i += (size_t)gridDim.x * blockDim.x)
             dst[base + i] = src[base + i];
     }
+}
+
+// Resident form: one CTA per lattice keeps the whole lattice in shared memory
+// for all n sweeps of a call (small lattices, launch-latency-bound batches),
+// in the x8 form of the strip kernel (a spin is the byte 8 [s < 0]; table
+// entries addressed by PRMT).  Statistics are reduced by the block after every
+// sweep and recorded by the CTA itself; the sweep and record counters come
+// from the host (t0, rec0).
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) ising_resident_kernel(ResidentArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ __align__(256) TabEntry stab[256 / sizeof(TabEntry)];
+    __shared__ int red[2 * (THREADS / 32)];
+    __shared__ long long cur_s[2];
+    const int lat = blockIdx.x;
+    const LatDev ld = a.lats[lat];
+    const int L = ld.L, Lv = L >> 4;
+    uint4 *sm4 = reinterpret_cast<uint4 *>(sm);
+    const uint32_t *sm32 = reinterpret_cast<const uint32_t *>(sm);
+    uint4 *G = reinterpret_cast<uint4 *>(a.spins + ld.offset);
+    for (int v = threadIdx.x; v < L * Lv; v += THREADS) sm4[v] = to_x8(G[v]);
+    if (threadIdx.x < kTabStride) stab[threadIdx.x] = a.tabs[lat * kTabStride + threadIdx.x];
+    if (threadIdx.x < 2) cur_s[threadIdx.x] = a.st.cur[2 * lat + threadIdx.x];
+    const uint32_t tb = (uint32_t)__cvta_generic_to_shared(stab);
+    // chunk v = threadIdx.x + k THREADS is (row i, column j); the walk adds
+    // (di, dj) = THREADS as rows and columns instead of dividing
+    const int di = THREADS / Lv, dj = THREADS - di * Lv;
+    const int i0 = (int)threadIdx.x / Lv, j0 = (int)threadIdx.x - i0 * Lv;
+    __syncthreads();
+    for (int sweep = 0; sweep < a.n_sweeps; ++sweep) {
+        const uint32_t t = a.t0 + (uint32_t)sweep;
+        int acc = 0;
+        for (int c = 0; c < 2; ++c) {
+            const PhiloxPrefix P = philox_prefix((uint32_t)lat, t, (uint32_t)c, a.rk);
+            int i = i0, j = j0;
+            for (int v = threadIdx.x; v < L * Lv; v += THREADS) {
+                const int iu = i == 0 ? L - 1 : i - 1, id = i == L - 1 ? 0 : i + 1;
+                const int row = i * Lv;
+                const uint4 Cc = sm4[v];
+                const uint4 Uc = sm4[iu * Lv + j];
+                const uint4 Dc = sm4[id * Lv + j];
+                const uint32_t lw = sm32[(row + (j == 0 ? Lv - 1 : j - 1)) * 4 + 3];
+                const uint32_t rw = sm32[(row + (j == Lv - 1 ? 0 : j + 1)) * 4];
+                const uint32_t g0 = (uint32_t)i * (uint32_t)(L >> 3) + 2u * (uint32_t)j;
+                sm4[v] = chunk_x8(Cc, Uc, Dc, lw, rw, philox_from_prefix(g0, P, a.rk),
+                                  philox_from_prefix(g0 + 1u, P, a.rk), row_par((c ^ i) & 1), tb, acc);
+                i += di;
+                j += dj;
+                if (j >= Lv) {
+                    j -= Lv;
+                    ++i;
+                }
+            }
+            __syncthreads();
+        }
+        int dm = (int)(int16_t)(acc & 0xFFFF);
+        int db = (acc - dm) >> 16;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dm += __shfl_xor_sync(0xFFFFFFFFu, dm, o);
+            db += __shfl_xor_sync(0xFFFFFFFFu, db, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red[2 * (threadIdx.x >> 5)] = dm;
+            red[2 * (threadIdx.x >> 5) + 1] = db;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long sm_ = 0, sb_ = 0;
+            for (int w = 0; w < THREADS / 32; ++w) {
+                sm_ += red[2 * w];
+                sb_ += red[2 * w + 1];
+            }
+            cur_s[0] += sm_;
+            cur_s[1] += sb_;
+            if (a.record && a.st.cap > 0) {
+                const long long slot = (a.rec0 + sweep) % a.st.cap;
+                a.st.ring[(slot * a.st.n_lat + lat) * 2] = cur_s[0];
+                a.st.ring[(slot * a.st.n_lat + lat) * 2 + 1] = cur_s[1];
+            }
+        }
+        __syncthreads();
+    }
+    for (int v = threadIdx.x; v < L * Lv; v += THREADS) {
+        const uint4 w = sm4[v];
+        G[v] = make_uint4(from_x8(w.x), from_x8(w.y), from_x8(w.z), from_x8(w.w));
+    }
+    if (threadIdx.x < 2) a.st.cur[2 * lat + threadIdx.x] = cur_s[threadIdx.x];
 }
 
 }  // namespace
