@@ -99,64 +99,6 @@ __device__ __forceinline__ void flush_ising_acc(int acc, int64_t *delta_lat, int
     }
 }
 
-template <int THREADS>
-__global__ void __launch_bounds__(THREADS) ising_fused_kernel(IsingSweepArgs a) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    __shared__ TabEntry stab[kTabStride];
-    __shared__ int red[2 * (THREADS / 32)];
-    uint4 *sm4 = reinterpret_cast<uint4 *>(sm);
-    const uint32_t *sm32 = reinterpret_cast<const uint32_t *>(sm);
-    const uint32_t t = a.state->t;
-    for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
-        const Item w = a.items[it];
-        const LatDev ld = a.lats[w.lat];
-        const int L = ld.L, Lv = L >> 4;
-        const int halo = w.whole ? 0 : 2;
-        const int nload = w.nrows + 2 * halo;
-        const uint4 *S = reinterpret_cast<const uint4 *>(a.src + ld.offset);
-        uint4 *Dg = reinterpret_cast<uint4 *>(a.dst + ld.offset);
-        for (int v = threadIdx.x; v < nload * Lv; v += THREADS) {
-            const int i = v / Lv, j = v - i * Lv;
-            int gy = w.r0 - halo + i;
-            gy = gy < 0 ? gy + L : (gy >= L ? gy - L : gy);
-            sm4[v] = __ldg(S + (size_t)gy * Lv + j);
-        }
-        if (threadIdx.x < kTabStride) stab[threadIdx.x] = a.tabs[w.lat * kTabStride + threadIdx.x];
-        __syncthreads();
-        int acc = 0;
-#pragma unroll 1
-        for (int c = 0; c < 2; ++c) {
-            // colour 0 also on the inner halo ring (smem rows 1 and nrows + 2)
-            const int lo = w.whole ? 0 : (c == 0 ? 1 : 2);
-            const int hi = w.whole ? w.nrows : (c == 0 ? w.nrows + 3 : w.nrows + 2);
-            const int n_units = (hi - lo) * Lv;
-            for (int v = threadIdx.x; v < n_units; v += THREADS) {
-                const int i = lo + v / Lv, j = v % Lv;
-                const int iu = (i == 0) ? nload - 1 : i - 1;
-                const int id = (i == nload - 1) ? 0 : i + 1;
-                int gy = w.r0 - halo + i;
-                gy = gy < 0 ? gy + L : (gy >= L ? gy - L : gy);
-                const uint4 Cc = sm4[i * Lv + j];
-                const uint4 Uc = sm4[iu * Lv + j];
-                const uint4 Dc = sm4[id * Lv + j];
-                const uint32_t lw = sm32[(i * Lv + (j == 0 ? Lv - 1 : j - 1)) * 4 + 3];
-                const uint32_t rw = sm32[(i * Lv + (j == Lv - 1 ? 0 : j + 1)) * 4];
-                const bool count = (i >= halo) && (i < halo + w.nrows);
-                const uint32_t g0 = (uint32_t)gy * (uint32_t)(L >> 3) + 2u * (uint32_t)j;
-                sm4[i * Lv + j] = ising_chunk(Cc, Uc, Dc, lw, rw, g0, (c ^ gy) & 1, (uint32_t)w.lat,
-                                              t, (uint32_t)c, a.k0, a.k1, stab, count, acc);
-            }
-            __syncthreads();
-        }
-        for (int v = threadIdx.x; v < w.nrows * Lv; v += THREADS) {
-            const int i = v / Lv, j = v - i * Lv;
-            Dg[(size_t)(w.r0 + i) * Lv + j] = sm4[(halo + i) * Lv + j];
-        }
-        flush_ising_acc<THREADS>(acc, a.delta + 2 * w.lat, red);
-        __syncthreads();
-    }
-}
-
 // Triangular lattices (geometry 1) resident in shared memory for all sweeps
 // of a call, one block per lattice; per sweep three colour passes, each
 // thread taking one Philox group (four consecutive compressed sites of the
@@ -936,6 +878,106 @@ __global__ void copy_lattices_kernel(const unsigned char *src, unsigned char *ds
         for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < bytes;
              i += (size_t)gridDim.x * blockDim.x)
             dst[base + i] = src[base + i];
+    }
+}
+
+// Tile kernel: a CTA takes work items (a whole small lattice, or a block of
+// rows with a two-row halo on each side) into shared memory in the x8 form,
+// updates colour 0 on the item and its inner halo rows (their updates use the
+// same site-keyed draws as the neighbouring item's), then colour 1 on the
+// item, and writes the item's rows back as +-1 bytes.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS) ising_fused_kernel(IsingSweepArgs a) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    // [0]: statistics deltas; [1]: zero deltas (recomputed halo rows)
+    __shared__ __align__(256) TabEntry stab[2][256 / sizeof(TabEntry)];
+    __shared__ int red[2 * (THREADS / 32)];
+    uint4 *sm4 = reinterpret_cast<uint4 *>(sm);
+    const uint32_t *sm32 = reinterpret_cast<const uint32_t *>(sm);
+    const uint32_t t = a.state->t;
+    const uint32_t tb_cnt = (uint32_t)__cvta_generic_to_shared(stab[0]);
+    const uint32_t tb_halo = (uint32_t)__cvta_generic_to_shared(stab[1]);
+    for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+        const Item w = a.items[it];
+        const LatDev ld = a.lats[w.lat];
+        const int L = ld.L, Lv = L >> 4;
+        const int halo = w.whole ? 0 : 2;
+        const int nload = w.nrows + 2 * halo;
+        const uint4 *S = reinterpret_cast<const uint4 *>(a.src + ld.offset);
+        uint4 *Dg = reinterpret_cast<uint4 *>(a.dst + ld.offset);
+        // chunk v = threadIdx.x + k THREADS of a row range is (row i, column j);
+        // the walk adds (di, dj) = THREADS as rows and columns
+        const int di = THREADS / Lv, dj = THREADS - di * Lv;
+        const int i0 = (int)threadIdx.x / Lv, j0 = (int)threadIdx.x - i0 * Lv;
+        {
+            int i = i0, j = j0;
+            for (int v = threadIdx.x; v < nload * Lv; v += THREADS) {
+                int gy = w.r0 - halo + i;
+                gy = gy < 0 ? gy + L : (gy >= L ? gy - L : gy);
+                sm4[v] = to_x8(__ldg(S + (size_t)gy * Lv + j));
+                i += di;
+                j += dj;
+                if (j >= Lv) {
+                    j -= Lv;
+                    ++i;
+                }
+            }
+        }
+        if (threadIdx.x < kTabStride) {
+            const TabEntry e = a.tabs[w.lat * kTabStride + threadIdx.x];
+            stab[0][threadIdx.x] = e;
+            stab[1][threadIdx.x] = TabEntry{e.thr, 0};
+        }
+        __syncthreads();
+        int acc = 0;
+#pragma unroll 1
+        for (int c = 0; c < 2; ++c) {
+            // colour 0 also on the inner halo ring (smem rows 1 and nrows + 2)
+            const int lo = w.whole ? 0 : (c == 0 ? 1 : 2);
+            const int hi = w.whole ? w.nrows : (c == 0 ? w.nrows + 3 : w.nrows + 2);
+            const int n_units = (hi - lo) * Lv;
+            const PhiloxPrefix P = philox_prefix((uint32_t)w.lat, t, (uint32_t)c, a.rk);
+            int i = lo + i0, j = j0;
+            for (int v = threadIdx.x; v < n_units; v += THREADS) {
+                const int iu = (i == 0) ? nload - 1 : i - 1;
+                const int id = (i == nload - 1) ? 0 : i + 1;
+                int gy = w.r0 - halo + i;
+                gy = gy < 0 ? gy + L : (gy >= L ? gy - L : gy);
+                const int row = i * Lv;
+                const uint4 Cc = sm4[row + j];
+                const uint4 Uc = sm4[iu * Lv + j];
+                const uint4 Dc = sm4[id * Lv + j];
+                const uint32_t lw = sm32[(row + (j == 0 ? Lv - 1 : j - 1)) * 4 + 3];
+                const uint32_t rw = sm32[(row + (j == Lv - 1 ? 0 : j + 1)) * 4];
+                const bool count = (i >= halo) && (i < halo + w.nrows);
+                const uint32_t g0 = (uint32_t)gy * (uint32_t)(L >> 3) + 2u * (uint32_t)j;
+                sm4[row + j] = chunk_x8(Cc, Uc, Dc, lw, rw, philox_from_prefix(g0, P, a.rk),
+                                        philox_from_prefix(g0 + 1u, P, a.rk), row_par((c ^ gy) & 1),
+                                        count ? tb_cnt : tb_halo, acc);
+                i += di;
+                j += dj;
+                if (j >= Lv) {
+                    j -= Lv;
+                    ++i;
+                }
+            }
+            __syncthreads();
+        }
+        {
+            int i = i0, j = j0;
+            for (int v = threadIdx.x; v < w.nrows * Lv; v += THREADS) {
+                const uint4 x8 = sm4[(halo + i) * Lv + j];
+                Dg[(size_t)(w.r0 + i) * Lv + j] = make_uint4(from_x8(x8.x), from_x8(x8.y), from_x8(x8.z), from_x8(x8.w));
+                i += di;
+                j += dj;
+                if (j >= Lv) {
+                    j -= Lv;
+                    ++i;
+                }
+            }
+        }
+        flush_ising_acc<THREADS>(acc, a.delta + 2 * w.lat, red);
+        __syncthreads();
     }
 }
 
