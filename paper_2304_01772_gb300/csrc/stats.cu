@@ -544,9 +544,22 @@ __global__ void unpack_spins_kernel(const uint32_t *words, int8_t *spins, const 
     const size_t o = ld.offset, end = o + (size_t)L * L;
     const bool rows_whole = (L & 31) == 0;
     const int wpr = L >> 5;   // words per row when rows_whole
-    long long m = 0, b = 0;
-    for (size_t w = (o >> 5) + blockIdx.x * (size_t)blockDim.x + threadIdx.x; (w << 5) < end;
-         w += (size_t)gridDim.x * blockDim.x) {
+    // spin_offset % 32 == 0: word wl of the lattice is global word (o >> 5) + wl.
+    // (r, q) = (row, word in the row) of wl, advanced by the grid stride as rows
+    // and words instead of dividing
+    const uint32_t n_wl = (uint32_t)(((size_t)L * L + 31) >> 5);
+    const uint32_t stride = gridDim.x * blockDim.x;
+    uint32_t wl = blockIdx.x * blockDim.x + threadIdx.x;
+    int r = 0, q = 0, dr = 0, dq = 0;
+    if (rows_whole) {
+        r = (int)(wl / (uint32_t)wpr);
+        q = (int)wl - r * wpr;
+        dr = (int)(stride / (uint32_t)wpr);
+        dq = (int)stride - dr * wpr;
+    }
+    int m = 0, b = 0;   // at most 32 (m) and 64 (b) per word, a few thousand words per thread
+    for (; wl < n_wl; wl += stride) {
+        const size_t w = (o >> 5) + wl;
         const size_t e0 = w << 5;
         const uint32_t bits = words[w];
         if (e0 + 32 <= end && ((reinterpret_cast<uintptr_t>(spins + e0) & 15) == 0)) {
@@ -560,14 +573,18 @@ __global__ void unpack_spins_kernel(const uint32_t *words, int8_t *spins, const 
         }
         if (!cur) continue;
         if (rows_whole) {
-            const size_t wl = w - (o >> 5);              // word index within the lattice
-            const int r = (int)(wl / wpr), q = (int)(wl - (size_t)r * wpr);
             const size_t row0 = (o >> 5) + (size_t)r * wpr;
             const uint32_t nxt = words[row0 + (q + 1 == wpr ? 0 : q + 1)];
             const uint32_t right = (bits >> 1) | (nxt << 31);
             const uint32_t down = words[(o >> 5) + (size_t)(r + 1 == L ? 0 : r + 1) * wpr + q];
             m += 32 - 2 * __popc(bits);
             b += 64 - 2 * (__popc(bits ^ right) + __popc(bits ^ down));
+            r += dr;
+            q += dq;
+            if (q >= wpr) {
+                q -= wpr;
+                ++r;
+            }
         } else {
             for (int i = 0; i < 32 && e0 + i < end; ++i) {
                 const size_t e = e0 + i, k = e - o;

@@ -574,6 +574,29 @@ def test_empty_calls_change_nothing():
     assert list(mom[:, 0]) == [1, 1]            # one sample per lattice
 
 
+def test_bit_packed_load_of_large_lattices():
+    """The unpack kernel's row walk over several grid strides: lattices of 2048
+    and 1056 (33 words per row, so a stride is not a whole number of rows) and
+    96; the loaded spins are the bits and the recounted statistics the
+    oracle's."""
+    lats = [dict(L=L, beta=0.44, J=1.0, h=0.0) for L in (2048, 1056, 96)]
+    sim = make_ising(lats, max_record=4)
+    nw = sim.packed_words
+    span = int(sim.spins.numel())
+    rng = np.random.default_rng(9)
+    new = torch.from_numpy(rng.integers(-2 ** 31, 2 ** 31, nw, dtype=np.int64).astype(np.int32)).pin_memory()
+    sim.load_spins_packed(new)
+    torch.cuda.synchronize()
+    nb = np.unpackbits(new.numpy().view(np.uint8), bitorder="little")[:span]
+    cur = sim.current_stats().cpu().numpy()
+    for i, (off, d) in enumerate(zip(sim.offsets, lats)):
+        L = d["L"]
+        want = np.where(nb[off:off + L * L] == 1, -1, 1).astype(np.int8).reshape(L, L)
+        got = lattice_np(sim, i)
+        assert np.array_equal(got, want), L
+        assert list(cur[i]) == list(oracle.ising_stats(want)), L
+
+
 def test_bit_packed_transfer():
     """One bit per spin on the host: a store packs exactly the lattices'
     signs (bits outside them 0), a load unpacks into the lattices only (other
