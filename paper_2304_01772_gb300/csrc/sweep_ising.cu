@@ -118,17 +118,34 @@ __global__ void __launch_bounds__(kTriResThreads) ising_tri_resident_kernel(Resi
     for (int i = threadIdx.x; i < N; i += blockDim.x) S[i] = G[i];
     if (threadIdx.x < kTabStride) stab[threadIdx.x] = a.tabs[lat * kTabStride + threadIdx.x];
     if (threadIdx.x < 2) cur_s[threadIdx.x] = a.st.cur[2 * lat + threadIdx.x];
+    // a thread's groups start kTriResThreads groups apart: the first site of the
+    // next group is (dy, dm) rows and compressed columns further, so the walk
+    // adds instead of dividing
+    constexpr int kStep = 4 * kTriResThreads;
+    const int dy = kStep / third, dm = kStep - dy * third, doff = dy % 3;
+    const int y00 = (4 * (int)threadIdx.x) / third, m00 = 4 * (int)threadIdx.x - y00 * third;
     __syncthreads();
     for (int sweep = 0; sweep < a.n_sweeps; ++sweep) {
         const uint32_t t = a.t0 + (uint32_t)sweep;
         int acc = 0;
         for (int c = 0; c < 3; ++c) {
             const PhiloxPrefix P = philox_prefix((uint32_t)lat, t, (uint32_t)c, a.rk);
-            for (int grp = threadIdx.x; 4 * grp < nk; grp += blockDim.x) {
+            int gy = y00, gm = m00, goff = (c + y00) % 3;
+            for (int grp = threadIdx.x; 4 * grp < nk; grp += kTriResThreads) {
                 const uint4 r = philox_from_prefix((uint32_t)grp, P, a.rk);
                 const uint32_t rr[4] = {r.x, r.y, r.z, r.w};
-                // row and colour offset once per group; a group's sites rarely cross a row
-                int y = (4 * grp) / third, m = 4 * grp - y * third, off = (c + y) % 3;
+                // row, compressed column and colour offset of the group's first site;
+                // a group's sites rarely cross a row
+                int y = gy, m = gm, off = goff;
+                gy += dy;
+                gm += dm;
+                goff += doff;
+                if (gm >= third) {
+                    gm -= third;
+                    ++gy;
+                    ++goff;
+                }
+                if (goff >= 3) goff -= 3;
 #pragma unroll
                 for (int l = 0; l < 4; ++l) {
                     if (4 * grp + l >= nk) break;
