@@ -217,7 +217,9 @@ int spin_set_launch(spin_ctx *ctx, int32_t mode, int32_t use_graph, int32_t tile
                     int32_t threads);
 /* Time the launch forms and tile shapes on the current state (the state is
  * saved and restored) and keep the fastest; the choice is cached per batch
- * shape in the file named by $SPINMC_TUNE_CACHE when it is set.          */
+ * shape in the file named by $SPINMC_TUNE_CACHE when it is set.  A trial
+ * runs sweeps_per_trial sweeps (at least 2), repeated with more sweeps (up to
+ * 4096) while it lasts under about a millisecond.                          */
 int spin_autotune(spin_ctx *ctx, int32_t sweeps_per_trial, void *stream);
 /* Current launch form as (mode, use_graph, tile_rows, threads). */
 int spin_get_launch(const spin_ctx *ctx, int32_t out[4]);
