@@ -1,9 +1,10 @@
 """GPU checks of the gradient path and the BF16 surrogate.
 
-* MLP forward / backward kernels against the float64 oracle.  Tolerance: the
-  kernels round the normalised input and both hidden activations to BF16
-  (8 significant bits, unit roundoff 2^-9 ~ 2e-3) and accumulate in FP32, so
-  relative L2 errors of a few 2^-9 are expected; we allow 2.5e-2.
+* MLP forward / backward kernels against the float64 oracle, element by
+  element: the kernels round the normalised input and both hidden
+  activations to BF16 (8 significant bits) and accumulate in FP32; every
+  element must lie within K error scales propagated from those roundings
+  (tests/mlp_bounds.py).
 * The Adam kernel against the oracle's Adam (float32 vs float64).
 * The fluctuation-estimator gradient against exact 4x4 enumeration and
   against finite differences of Monte Carlo means.
@@ -36,34 +37,12 @@ def _flat(d):
     return np.concatenate([d[k].ravel() for k in omlp.PARAM_NAMES])
 
 
-def _rel(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-
-
-def _emulate_fp32(flat, mu, inv, X, T):
-    """The kernels' arithmetic in plain torch float32: BF16 weights, BF16
-    rounding of the normalised input and of both hidden activations."""
-    bf = lambda t: t.to(torch.bfloat16).float()
-    p = bf(flat.detach().cpu())
-    W1, b1 = p[:192].view(64, 3), p[192:256]
-    W2, b2 = p[256:4352].view(64, 64), p[4352:4416]
-    W3, b3 = p[4416:4544].view(2, 64), p[4544:4546]
-    X, T, mu, inv = X.cpu(), T.cpu(), mu.cpu(), inv.cpu()
-    xn = bf((X - mu) * inv)
-    h1 = bf(torch.relu(xn @ W1.T + b1))
-    a2 = bf(torch.relu(h1 @ W2.T + b2))
-    Y = a2 @ W3.T + b3
-    dy = (Y - T) / X.shape[0]
-    dz2 = (dy @ W3) * (a2 > 0)
-    dz1 = (dz2 @ W2) * (h1 > 0)
-    g = torch.cat([(dz1.T @ xn).ravel(), dz1.sum(0), (dz2.T @ h1).ravel(), dz2.sum(0),
-                   (dy.T @ a2).ravel(), dy.sum(0)])
-    return Y, g, (dz1 @ W1) * inv, (dz1.abs() @ W1.abs()) * inv.abs()
-
-
 def test_mlp_kernels_match_oracle():
+    """Every output element, gradient entry and input gradient of the kernels
+    lies within K = 8 error scales of the float64 oracle's (BF16 roundings
+    of the normalised input and both hidden activations, FP32 accumulation;
+    the scales and their calibration are in tests/mlp_bounds.py)."""
+    from tests import mlp_bounds as mb
     s = fit.Surrogate(seed=11)
     g = torch.Generator().manual_seed(0)
     s.params += 0.05 * torch.randn(s.params.shape, generator=g).cuda()   # non-zero biases too
@@ -72,21 +51,23 @@ def test_mlp_kernels_match_oracle():
     Y = sm.mlp_forward(s.params, s.mu, s.inv_sigma, X)
     grad, loss, dX = sm.mlp_backward(s.params, s.mu, s.inv_sigma, X, T, want_dx=True)
     p = _oracle_params(s.params)
-    mu, inv = s.mu.double().cpu().numpy(), s.inv_sigma.double().cpu().numpy()
-    Yo, cache = omlp.forward(p, X.double().cpu().numpy(), mu, inv)
-    go, dXo = omlp.backward(p, cache, Yo, T.double().cpu().numpy(), inv)
-    # the kernels' own arithmetic, emulated in float32: only summation order differs
-    Ye, ge, dXe, dXscale = _emulate_fp32(s.params, s.mu, s.inv_sigma, X, T)
-    assert _rel(Y.cpu().numpy(), Ye.numpy()) < 1e-3
-    assert _rel(grad.cpu().numpy(), ge.numpy()) < 1e-3
-    assert _rel(dX.cpu().numpy(), dXe.numpy()) < 1e-3
-    # the float64 oracle: BF16 rounding of activations is the only approximation
-    assert _rel(Y.cpu().numpy(), Yo) < 2.5e-2
-    assert abs(float(loss) - omlp.loss(Yo, T.double().cpu().numpy())) < 2.5e-2 * omlp.loss(Yo, T.double().cpu().numpy())
-    assert _rel(grad.cpu().numpy(), _flat(go)) < 2.5e-2
-    # dX = W1^T dz1 cancels heavily; measure its error against the sum of |terms|
-    err = np.linalg.norm(dX.cpu().numpy() - dXo) / np.linalg.norm(dXscale.numpy())
-    assert err < 2.5e-2, err
+    mu, inv = s.mu.cpu().numpy(), s.inv_sigma.cpu().numpy()
+    Xh, Th = X.cpu().numpy(), T.cpu().numpy()
+    vals, sc = mb.scales(p, Xh, mu, inv, Th)
+    gflat = grad.cpu().numpy().astype(np.float64)
+    got, off = {"Y": Y.cpu().numpy(), "dX": dX.cpu().numpy()}, 0
+    for k, shp in omlp.shapes().items():
+        n = int(np.prod(shp))
+        got[k] = gflat[off:off + n].reshape(shp)
+        off += n
+    assert mb.violations(got, vals, sc) == {}, mb.worst_ratio(got, vals, sc)
+    # the loss: one FP32 sum of n squared errors, each off by its Y scale
+    Lo = omlp.loss(vals["Y"], Th)
+    s_loss = np.sqrt(np.sum((np.abs(vals["Y"] - Th) * sc["Y"]) ** 2)) / 333 + 333 * 2.0 ** -24 * Lo
+    assert abs(float(loss) - Lo) <= mb.K_DEFAULT * s_loss, (float(loss), Lo, s_loss)
+    # the same arithmetic emulated in float32 on the CPU agrees as closely
+    em = mb.emulate_fp32(p, Xh, mu, inv, Th)
+    assert mb.violations(em, vals, sc) == {}
 
 
 def test_adam_kernel_matches_oracle():
