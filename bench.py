@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--workload", default="uneven512",
                     choices=["uneven512", "potts_q3", "potts_q8", "cpm1024", "ising_small", "grad", "mlp", "dmc",
-                             "spinglass", "cpm_batch", "triangular", "nnn", "fit"])
+                             "spinglass", "cpm_batch", "triangular", "nnn", "fit", "rng"])
     return ap.parse_args()
 
 
@@ -203,6 +203,14 @@ def _oracle_nnn(args):
     return n * 256 * 256, time.perf_counter() - t0
 
 
+def _oracle_rng(args):
+    import oracle
+    g0, n = args
+    t0 = time.perf_counter()
+    oracle.philox_xor(SEED, 0, 0, 0, g0, n)
+    return 4 * n, time.perf_counter() - t0
+
+
 def cpu_oracle_pool(fn, tasks, cores):
     import multiprocessing as mp
 
@@ -229,6 +237,11 @@ def cpu_baseline_secondary(workload, cores):
         rate, units, wall = cpu_oracle_pool(_oracle_potts, [(i, lats[i], SEED, 1) for i in pick], cores)
         return {"value": rate, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
                 "sample": f"{len(pick)} of the 64 lattices, one sweep each ({wall:.1f} s wall)"}
+    if workload == "rng":
+        n = 1 << 25
+        rate, units, wall = cpu_oracle_pool(_oracle_rng, [(i * n, n) for i in range(cores)], cores)
+        return {"value": rate, "unit": "draws/s", "cores": cores, "kind": "oracle",
+                "sample": f"{cores} x 2^25 Philox4x32-10 blocks, one range per core ({wall:.1f} s wall)"}
     if workload == "cpm1024":
         p = wl.cpm1024()
         op = oracle.CPM(L=p["L"], J=p["J"], lam=p["lam"], target=p["target"], n_cells=p["n_cells"], T=p["T"],
@@ -456,6 +469,37 @@ def issue_roofline(kernel, workload, launch_ms, sm_mhz):
     return {"bound": "issue", "achieved": ach, "peak": peak, "unit": "warp-instructions/s", "frac": ach / peak,
             "instructions_per_launch": inst, "sm_mhz": sm_mhz,
             "peak_source": f"{sms} SMs x 4 schedulers x 1 warp instruction per cycle at the sampled clock"}
+
+
+def rng_ceiling(draws_per_update, updates_per_s, peak_gbs, bytes_per_update=2.0):
+    """The random-number ceiling of a sweep on this GPU: spin_philox_xor (the
+    sweeps' own Philox4x32-10 code, reduced to a digest) over 2^28 blocks =
+    2^30 draws, best of 5 launches by CUDA events.  An Ising update consumes
+    one 32-bit draw, a Potts update two, so no sweep on this stream can update
+    faster than draws/s / draws_per_update."""
+    import torch
+    import paper_2304_01772_gb300 as sm
+    n = 1 << 28
+    out = torch.empty(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        sm.philox_xor(SEED, 0, 0, 0, 0, n, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(5):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sm.philox_xor(SEED, 0, 0, 0, 0, n, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    draws = 4.0 * n / (best * 1e-3)
+    ceil = draws / draws_per_update
+    return {"draws_per_s": draws, "draws_per_update": draws_per_update, "ceiling_updates_per_s": ceil,
+            "ceiling_frac_of_hbm": ceil * bytes_per_update / 1e9 / peak_gbs,
+            "kernel_updates_per_s": updates_per_s,
+            "kernel_frac_of_ceiling": (updates_per_s / ceil) if updates_per_s else None,
+            "source": "spin_philox_xor over 2^28 Philox4x32-10 blocks, best of 5, CUDA events"}
 
 
 def dist_setup(n):
@@ -692,6 +736,9 @@ def run_ours(args):
     if rank != 0:
         return 0
     value = job_throughput(sites * args.steps, world, ms * 1e-3)
+    strip_ms = prof[1][0] / prof[1][1] if prof[1][1] else None
+    rng = rng_ceiling(1, (sum(d["L"] ** 2 for d in lats if d["L"] in (512, 1024, 2048)) / (strip_ms * 1e-3))
+                      if strip_ms else None, measured_peaks()[0])
     plain = job_throughput(sites * args.plain_steps, world, ms_plain * 1e-3)
     peak, peak_kind = measured_peaks()
     strip_sites = sum(d["L"] ** 2 for d in lats if d["L"] in (512, 1024, 2048))
@@ -736,7 +783,8 @@ def run_ours(args):
                      "kernel": dom, "algorithmic_bytes_per_launch": alg_bytes,
                      "launch_ms": kms_dom, "timed_launches": kn,
                      "peak_source": f"{peak_kind} hbm_gbs (copy)", "kernels": kernels,
-                     "issue": issue_roofline(dom, "uneven512", kms_dom, clk.get("sm_mhz") if clk else None)},
+                     "issue": issue_roofline(dom, "uneven512", kms_dom, clk.get("sm_mhz") if clk else None),
+                     "rng": rng},
         "e2e": {"value": sites * args.e2e_steps * world / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 4 * nw, "d2h_bytes_per_step": 4 * nw + st_host.numel() * 8,
                 "transfer": "one bit per spin: spin_load_spins_packed uploads the packed state from pinned "
@@ -779,6 +827,18 @@ def run_secondary(args):
         return run_spinglass(args, cpu)
     if args.workload == "cpm_batch":
         return run_cpm_batch(args, cpu)
+    if args.workload == "rng":
+        peak, kind = measured_peaks()
+        r = rng_ceiling(1, None, peak)
+        line = {"metric": "Philox4x32-10 draws/s (rng)", "value": r["draws_per_s"], "unit": "draws/s",
+                "n_gpus": 1, "steps": 5, "warmup": 2, "higher_is_better": True, "dtype": "u32",
+                "data": "synthetic", "config": {"workload": "rng: the sweeps' Philox4x32-10 stream alone, "
+                                                            "2^28 blocks per launch reduced to an XOR digest"},
+                "gpu_launches": 1, "rng": r}
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+        return 0
     record = False
     if args.workload.startswith("potts"):
         q = int(args.workload[-1])
@@ -848,7 +908,8 @@ def run_secondary(args):
                                 "note": "64 MiB state + partner ~ L2 size: largely L2-resident",
                                 "peak_source": f"{kind} hbm_gbs",
                                 "issue": issue_roofline(kname, args.workload, kms / kn,
-                                                        clk["sm_mhz"] if clk else None)}
+                                                        clk["sm_mhz"] if clk else None),
+                                "rng": rng_ceiling(2, units / (kms / kn * 1e-3), peak)}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

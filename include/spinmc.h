@@ -274,6 +274,18 @@ int spin_profile_read(spin_ctx *ctx, double *total_ms, int64_t *launches, void *
  * cooperative launch. */
 int spin_barrier_selftest(int32_t blocks, int32_t missing, int32_t rounds, void *stream);
 
+/* The random stream by itself (the RNG paragraph above; Alg. 1 draws one
+ * uniform number per proposal, and this library draws it from Philox4x32-10):
+ * *out (device, 4 bytes) = XOR of all four 32-bit words of the blocks for
+ * counters (g, lattice, sweep, colour), g = g0 .. g0 + n_groups - 1, under
+ * seed's key.  The blocks come from the same device code as the sweeps'
+ * draws, so the digest checks that code against another implementation, and
+ * the call's duration bounds the rate of any sweep on this stream (an Ising
+ * update consumes one word, a Potts or CPM update two).  Asynchronous.
+ * SPIN_EINVAL if out is NULL or g0 + n_groups > 2^32.                        */
+int spin_philox_xor(uint64_t seed, uint32_t lattice, uint32_t sweep, uint32_t colour, uint32_t g0,
+                    uint32_t n_groups, uint32_t *out, void *stream);
+
 uint32_t spin_sweep_index(const spin_ctx *ctx);
 int32_t spin_gpu_launches(const spin_ctx *ctx); /* kernels launched by the last spin_sweep */
 const char *spin_last_error(const spin_ctx *ctx);

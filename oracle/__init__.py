@@ -61,6 +61,7 @@ _u64 = ctypes.c_uint64
 def _declare(L):
     sig = {
         "or_philox4x32_10": (None, [_u32p, _u32p, _u32p]),
+        "or_philox_xor": (_u32, [_u64, _u32, _u32, _u32, _u32, _u32]),
         "or_accept_count": (ctypes.c_double, [ctypes.c_double, ctypes.c_double]),
         "or_accept": (_i, [ctypes.c_double, ctypes.c_double, _u32]),
         "or_init_ising": (None, [_i, _u64, _u32, _i8p]),
@@ -119,6 +120,12 @@ def philox4x32_10(ctr, key):
     lib().or_philox4x32_10(_p(c, ctypes.c_uint32), _p(k, ctypes.c_uint32),
                            _p(out, ctypes.c_uint32))
     return out
+
+
+def philox_xor(seed, lattice, sweep, colour, g0, n):
+    """XOR of every word of the Philox blocks for counters (g, lattice, sweep,
+    colour), g in [g0, g0 + n), under the seed's key."""
+    return int(lib().or_philox_xor(seed, lattice, sweep, colour, g0, n))
 
 
 def accept_count(beta: float, dE: float) -> float:

@@ -78,6 +78,20 @@ static void draw4(uint64_t seed, uint32_t g, uint32_t lattice, uint32_t sweep,
     or_philox4x32_10(ctr, key, out);
 }
 
+/* XOR of all four words of the blocks for counters (g, lattice, sweep,
+ * colour), g = g0 .. g0 + n - 1: a digest of one stretch of the random
+ * stream that the sweeps draw from. */
+uint32_t or_philox_xor(uint64_t seed, uint32_t lattice, uint32_t sweep, uint32_t colour,
+                       uint32_t g0, uint32_t n)
+{
+    uint32_t acc = 0, out[4];
+    for (uint32_t i = 0; i < n; ++i) {
+        draw4(seed, g0 + i, lattice, sweep, colour, out);
+        acc ^= out[0] ^ out[1] ^ out[2] ^ out[3];
+    }
+    return acc;
+}
+
 /* floor(u * m / 2^32): an index in [0, m) from a uniform uint32. */
 static uint32_t mulhi32(uint32_t u, uint32_t m)
 {

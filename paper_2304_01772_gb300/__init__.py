@@ -78,6 +78,8 @@ _SIGS = {
     "spin_last_error": (ctypes.c_char_p, [_vp]),
     "spin_destroy": (None, [_vp]),
     "spin_version": (_i32, []),
+    "spin_philox_xor": (_i32, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                               ctypes.c_uint32, _vp, _vp]),
     "spin_ising_sweep_noalloc": (_i32, [ctypes.c_uint64, _i32, ctypes.POINTER(LatticeDesc), _vp, ctypes.c_uint32,
                                         _i32, _vp, _vp]),
     "spin_adam": (_i32, [_vp, _vp, _vp, _vp, _i32, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
@@ -418,6 +420,18 @@ def barrier_selftest(blocks, missing=0, rounds=1, stream=None):
     """Run the bounded grid barrier of the CPM persistent form as a self-test;
     returns SPIN_OK (0) or SPIN_ETIMEOUT (-4) (see spin_barrier_selftest)."""
     return int(lib().spin_barrier_selftest(int(blocks), int(missing), int(rounds), _stream(stream)))
+
+
+def philox_xor(seed, lattice, sweep, colour, g0, n_groups, out=None, stream=None):
+    """XOR digest of the Philox blocks (g, lattice, sweep, colour), g in
+    [g0, g0 + n_groups), computed on the device (see spin_philox_xor).
+    Returns the one-element uint32-in-int32 device tensor it wrote."""
+    import torch
+    if out is None:
+        out = torch.empty(1, dtype=torch.int32, device="cuda")
+    _check(lib().spin_philox_xor(int(seed), int(lattice), int(sweep), int(colour), int(g0), int(n_groups),
+                                 _ptr(out), _stream(stream)), None, "spin_philox_xor")
+    return out
 
 
 # --------------------------------------------------------------------------

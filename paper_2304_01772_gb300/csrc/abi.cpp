@@ -1759,6 +1759,15 @@ int spin_dmc_spin_iter(uint64_t seed, int32_t n_lattices, int32_t L, float beta,
     return launch_dmc_spin_iter(a, S(stream)) == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
 }
 
+int spin_philox_xor(uint64_t seed, uint32_t lattice, uint32_t sweep, uint32_t colour, uint32_t g0,
+                    uint32_t n_groups, uint32_t *out, void *stream) {
+    if (!out || (uint64_t)g0 + (uint64_t)n_groups > ((uint64_t)1 << 32)) return SPIN_EINVAL;
+    return launch_philox_xor(g0, n_groups, lattice, sweep, colour, (uint32_t)seed, (uint32_t)(seed >> 32), out,
+                             S(stream)) == cudaSuccess
+               ? SPIN_OK
+               : SPIN_ECUDA;
+}
+
 int spin_dmc_discretize(int64_t n, float *spins, void *stream) {
     if (n < 0 || (n > 0 && !spins)) return SPIN_EINVAL;
     if (n == 0) return SPIN_OK;

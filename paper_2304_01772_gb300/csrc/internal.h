@@ -159,6 +159,10 @@ cudaError_t launch_ising_nnn_resident(const ResidentArgs &a, const uint32_t *thr
                                       DevState *state, cudaStream_t s);
 cudaError_t launch_init_random(void *spins, int model, const LatDev *lats, int n_lat, int maxL,
                                uint32_t k0, uint32_t k1, cudaStream_t s);
+// XOR of every word of the Philox blocks for counters (g, lat, t, c),
+// g in [g0, g0 + n), into *out (zeroed first).
+cudaError_t launch_philox_xor(uint32_t g0, uint32_t n, uint32_t lat, uint32_t t, uint32_t c,
+                              uint32_t k0, uint32_t k1, uint32_t *out, cudaStream_t s);
 
 struct PottsSweepArgs {
     const Item *items;

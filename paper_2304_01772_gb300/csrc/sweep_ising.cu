@@ -19,6 +19,8 @@
 //  * ising_plain_kernel: one lattice, one colour, in place (two launches per
 //    lattice per sweep: the plain launch form the batched one is compared to).
 //  * ising_generic_kernel: any even L (not a multiple of 16), one thread per site.
+#include <stdlib.h>
+
 #include "internal.h"
 #include "strip.cuh"
 
@@ -879,6 +881,263 @@ __global__ void __launch_bounds__(WARPS * 32) ising_strip_kernel(IsingSweepArgs 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Row-strip kernel in the split form (Alg. 1 on the square-lattice stencil).
+//
+// The walk of ising_strip_kernel, with each ring row stored as its two
+// colour-compressed halves in the x8 form: half 0 holds the sites of even x,
+// half 1 those of odd x (site x of a row is byte x >> 1 of half x & 1).  For
+// colour c on row y the active sites are half p = (c + y) & 1, and all four
+// bytes of a 32-bit word of that half are active: a word's up and down
+// neighbours are the aligned word of half p of rows y -+ 1, its left and right
+// neighbours the aligned word of the other half and that word shifted by one
+// byte (left for p = 0, right for p = 1).  The four draws of one Philox block
+// (g = (y L / 2 + m) / 4) belong to the four sites of one word.
+//
+// At step s, colour 0 on row s and colour 1 on row s - 1 have the same p and
+// touch the same word positions: colour 1's up row is row s - 2, its down row
+// is row s (just updated) and its own sites are colour 0's up row.  So both
+// updates run per word in one pass with no exchange between lanes; only the
+// other-half word across a lane's chunk edge comes from shared memory.  Row
+// s - 1 is then final and is written to the destination buffer in the int8
+// form, re-interleaved by one sign-replicating byte permutation per word.
+//
+// Shared memory per warp: four split rows (s - 2 .. s + 1) and one landing
+// slot where the raw row s + 2 arrives by cp.async while step s computes.
+namespace split {
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+template <int NW>
+struct Words {
+    uint32_t w[NW];
+};
+
+template <int NW>
+__device__ __forceinline__ Words<NW> ld_words(const unsigned char *half, int c) {
+    Words<NW> r;
+    if constexpr (NW == 4) {
+        const uint4 v = reinterpret_cast<const uint4 *>(half)[c];
+        r.w[0] = v.x, r.w[1] = v.y, r.w[2] = v.z, r.w[3] = v.w;
+    } else {
+        const uint2 v = reinterpret_cast<const uint2 *>(half)[c];
+        r.w[0] = v.x, r.w[1] = v.y;
+    }
+    return r;
+}
+
+template <int NW>
+__device__ __forceinline__ void st_words(unsigned char *half, int c, const Words<NW> &r) {
+    if constexpr (NW == 4)
+        reinterpret_cast<uint4 *>(half)[c] = make_uint4(r.w[0], r.w[1], r.w[2], r.w[3]);
+    else
+        reinterpret_cast<uint2 *>(half)[c] = make_uint2(r.w[0], r.w[1]);
+}
+
+// Raw row (L int8 spins, +1 = 0x01, -1 = 0xFF) at src -> split x8 row at dst
+// (dst != src), one 16-byte raw chunk per lane at a time.
+__device__ __forceinline__ void split_row(const unsigned char *src, unsigned char *dst, int L, int lane) {
+    uint2 *E = reinterpret_cast<uint2 *>(dst);
+    uint2 *O = reinterpret_cast<uint2 *>(dst + (L >> 1));
+#pragma unroll 1
+    for (int k = lane; k < (L >> 4); k += 32) {
+        const uint4 v = reinterpret_cast<const uint4 *>(src)[k];
+        const uint32_t a = v.x & kX8, b = v.y & kX8, c = v.z & kX8, d = v.w & kX8;
+        E[k] = make_uint2(__byte_perm(a, b, 0x6420), __byte_perm(c, d, 0x6420));
+        O[k] = make_uint2(__byte_perm(a, b, 0x7531), __byte_perm(c, d, 0x7531));
+    }
+}
+
+__device__ __forceinline__ void issue_raw(unsigned char *dst, const uint4 *S, int y, int L, int lane) {
+    const uint4 *src = S + (size_t)y * (L >> 4);
+    for (int j = lane; j < (L >> 4); j += 32) cp_async16(reinterpret_cast<uint4 *>(dst) + j, src + j);
+}
+
+// Metropolis update of the active words `act` given the other half's words
+// `oth` (plus `edge`, the other-half word just outside the chunk: before it
+// for p = 0, after it for p = 1), the aligned words of the rows above and
+// below, and the Philox blocks g .. g + NW - 1.
+template <int NW>
+__device__ __forceinline__ void update(Words<NW> &act, const Words<NW> &oth, uint32_t edge, const Words<NW> &up,
+                                       const Words<NW> &dn, uint32_t g, const PhiloxPrefix &P,
+                                       const PhiloxKeys &rk, int p, uint32_t selH, uint32_t stab, int &acc) {
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+        const uint32_t nb = p ? (i + 1 < NW ? oth.w[i + 1] : edge) : (i > 0 ? oth.w[i - 1] : edge);
+        // the horizontal neighbours are oth (one side) and this shifted copy (other side)
+        const uint32_t H = prmt(oth.w[i], nb, selH);
+        const uint32_t key = up.w[i] + dn.w[i] + oth.w[i] + H + act.w[i] * 5u;
+        const uint4 r = philox_from_prefix(g + (uint32_t)i, P, rk);
+        uint32_t w = act.w[i];
+        accept_site(w, acc, r.x, lds_entry(prmt(key, stab, 0x7650u)), 0x00000008u);
+        accept_site(w, acc, r.y, lds_entry(prmt(key, stab, 0x7651u)), 0x00000800u);
+        accept_site(w, acc, r.z, lds_entry(prmt(key, stab, 0x7652u)), 0x00080000u);
+        accept_site(w, acc, r.w, lds_entry(prmt(key, stab, 0x7653u)), 0x08000000u);
+        act.w[i] = w;
+    }
+}
+
+// Final row: active half `act` and other half `oth` (x8 form) -> int8 spins.
+// Inputs shifted left by 4 carry the spin in each byte's sign bit; sel0 / sel1
+// interleave the halves and replicate those bits (0xFF or 0x00); OR 0x01.
+template <int NW>
+__device__ __forceinline__ void store_raw(uint4 *Drow, int c, const Words<NW> &act, const Words<NW> &oth,
+                                          uint32_t sel0, uint32_t sel1) {
+    uint32_t o[2 * NW];
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+        const uint32_t a = act.w[i] << 4, b = oth.w[i] << 4;
+        o[2 * i] = prmt(a, b, sel0) | 0x01010101u;
+        o[2 * i + 1] = prmt(a, b, sel1) | 0x01010101u;
+    }
+    if constexpr (NW == 4) {
+        Drow[2 * c] = make_uint4(o[0], o[1], o[2], o[3]);
+        Drow[2 * c + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+    } else {
+        Drow[c] = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+struct Walk {
+    const uint4 *S;
+    uint4 *D;
+    unsigned char *ring;   // 5 * L bytes of this warp: 4 split rows + landing
+    int L, r0, nrows, lane;
+    PhiloxPrefix P0, P1;
+    uint32_t tab_cnt, tab_halo;
+};
+
+// One item: rows [r0, r0 + nrows) of one lattice, with the recomputed halo
+// rows r0 - 1 and r0 + nrows (colour 0 only, no statistics).  NW: words of a
+// half row per lane chunk (2 for L = 512, else 4).
+template <int NW>
+__device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
+    const int L = x.L, half = L >> 1, nw = L >> 3, nc = nw / (32 * NW), lane = x.lane;
+    unsigned char *q0 = x.ring + 3 * L, *q1 = x.ring, *q2 = x.ring + L, *q3 = x.ring + 2 * L;
+    unsigned char *land = x.ring + 4 * L;
+    // rows -2 and -1 land in q0 (free until step -1 ends) and the landing
+    // slot and are split into q1 and q2; then row 0 (via q0) into q3, and
+    // row 1 stays in flight in the landing slot
+    issue_raw(q0, x.S, wrap_row(x.r0 - 2, L), L, lane);
+    issue_raw(land, x.S, wrap_row(x.r0 - 1, L), L, lane);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncwarp();
+    split_row(q0, q1, L, lane);
+    split_row(land, q2, L, lane);
+    __syncwarp();
+    issue_raw(q0, x.S, wrap_row(x.r0, L), L, lane);
+    cp_async_commit();
+    issue_raw(land, x.S, wrap_row(x.r0 + 1, L), L, lane);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncwarp();
+    split_row(q0, q3, L, lane);
+    __syncwarp();
+    int acc = 0;
+    for (int s = -1; s <= x.nrows; ++s) {
+        // q0..q3 hold rows s - 2 .. s + 1
+        const int yA = wrap_row(x.r0 + s, L), yB = yA == 0 ? L - 1 : yA - 1;
+        const int p = yA & 1;
+        const uint32_t selH = p ? 0x4321u : 0x2107u;
+        const uint32_t selO0 = p ? 0x9D8Cu : 0xD9C8u, selO1 = p ? 0xBFAEu : 0xFBEAu;
+        const uint32_t tabA = (s >= 0 && s < x.nrows) ? x.tab_cnt : x.tab_halo;
+        const int hp = p * half, ho = half - hp;
+        const uint32_t gA = (uint32_t)yA * (uint32_t)(L >> 3), gB = (uint32_t)yB * (uint32_t)(L >> 3);
+        uint4 *Drow = x.D + (size_t)yB * (L >> 4);
+        const int eoff = p ? NW : -1;
+        for (int j = 0; j < nc; ++j) {
+            const int c = lane + 32 * j;
+            const int we = (NW * c + eoff) & (nw - 1);
+            const uint32_t eA = reinterpret_cast<const uint32_t *>(q2 + ho)[we];
+            Words<NW> act = ld_words<NW>(q2 + hp, c);
+            const Words<NW> oth = ld_words<NW>(q2 + ho, c);
+            Words<NW> upA = ld_words<NW>(q1 + hp, c);
+            const Words<NW> dnA = ld_words<NW>(q3 + hp, c);
+            update<NW>(act, oth, eA, upA, dnA, gA + (uint32_t)(NW * c), x.P0, rk, p, selH, tabA, acc);
+            st_words<NW>(q2 + hp, c, act);
+            if (s >= 1) {
+                const uint32_t gBc = gB + (uint32_t)(NW * c);
+                const uint32_t eB = reinterpret_cast<const uint32_t *>(q1 + ho)[we];
+                const Words<NW> othB = ld_words<NW>(q1 + ho, c);
+                const Words<NW> upB = ld_words<NW>(q0 + hp, c);
+                update<NW>(upA, othB, eB, upB, act, gBc, x.P1, rk, p, selH, x.tab_cnt, acc);
+                store_raw<NW>(Drow, c, upA, othB, selO0, selO1);
+            }
+        }
+        if ((s & 7) == 7) drain_acc(acc, dm, db);
+        __syncwarp();
+        if (s + 2 <= x.nrows + 1) {
+            cp_async_wait_all();
+            __syncwarp();
+            split_row(land, q0, L, lane);          // row s + 2 into the slot of row s - 2
+            __syncwarp();
+            if (s + 3 <= x.nrows + 1) {
+                issue_raw(land, x.S, wrap_row(x.r0 + s + 3, L), L, lane);
+                cp_async_commit();
+            }
+        }
+        unsigned char *t = q0;
+        q0 = q1;
+        q1 = q2;
+        q2 = q3;
+        q3 = t;
+    }
+    drain_acc(acc, dm, db);
+}
+
+}  // namespace split
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) ising_split_kernel(IsingSweepArgs a) {
+    extern __shared__ __align__(16) unsigned char ring_bytes[];
+    __shared__ __align__(256) TabEntry tabs[WARPS][2][256 / sizeof(TabEntry)];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t t = a.state->t;
+    const int gw = blockIdx.x * WARPS + warp, nw = gridDim.x * WARPS;
+    for (int it = gw; it < a.n_items; it += nw) {
+        const Item w = a.items[it];
+        const LatDev ld = a.lats[w.lat];
+        if (lane < kTabStride) {
+            const TabEntry e = a.tabs[w.lat * kTabStride + lane];
+            tabs[warp][0][lane] = e;
+            tabs[warp][1][lane] = TabEntry{e.thr, 0};
+        }
+        __syncwarp();
+        split::Walk x;
+        x.S = reinterpret_cast<const uint4 *>(a.src + ld.offset);
+        x.D = reinterpret_cast<uint4 *>(a.dst + ld.offset);
+        x.ring = ring_bytes + (size_t)warp * kRing * kRowChunks * 16;
+        x.L = ld.L;
+        x.r0 = w.r0;
+        x.nrows = w.nrows;
+        x.lane = lane;
+        x.P0 = philox_prefix((uint32_t)w.lat, t, 0u, a.rk);
+        x.P1 = philox_prefix((uint32_t)w.lat, t, 1u, a.rk);
+        x.tab_cnt = (uint32_t)__cvta_generic_to_shared(tabs[warp][0]);
+        x.tab_halo = (uint32_t)__cvta_generic_to_shared(tabs[warp][1]);
+        int dm = 0, db = 0;
+        if (ld.L == 512)
+            split::item<2>(x, a.rk, dm, db);
+        else
+            split::item<4>(x, a.rk, dm, db);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dm += __shfl_xor_sync(0xFFFFFFFFu, dm, o);
+            db += __shfl_xor_sync(0xFFFFFFFFu, db, o);
+        }
+        if (lane == 0) {
+            if (dm) atomicAdd(reinterpret_cast<unsigned long long *>(a.delta + 2 * w.lat), (unsigned long long)(long long)dm);
+            if (db) atomicAdd(reinterpret_cast<unsigned long long *>(a.delta + 2 * w.lat + 1), (unsigned long long)(long long)db);
+        }
+        __syncwarp();
+    }
+}
+
 // Copy every lattice (L*L elements of `elem` bytes at its offset) src -> dst.
 __global__ void copy_lattices_kernel(const unsigned char *src, unsigned char *dst,
                                      const LatDev *lats, int elem) {
@@ -1116,13 +1375,21 @@ cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, s
 
 size_t strip_smem(int warps) { return strip_ring_bytes(warps); }
 
+static bool old_strip() {
+    static int v = -1;
+    if (v < 0) v = getenv("SPINMC_OLD_STRIP") ? 1 : 0;
+    return v == 1;
+}
+
 cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, cudaStream_t s) {
     switch (warps) {
         case 4:
-            ising_strip_kernel<4><<<grid, 128, strip_smem(4), s>>>(a);
+            if (old_strip()) ising_strip_kernel<4><<<grid, 128, strip_smem(4), s>>>(a);
+            else ising_split_kernel<4><<<grid, 128, strip_smem(4), s>>>(a);
             break;
         case 8:
-            ising_strip_kernel<8><<<grid, 256, strip_smem(8), s>>>(a);
+            if (old_strip()) ising_strip_kernel<8><<<grid, 256, strip_smem(8), s>>>(a);
+            else ising_split_kernel<8><<<grid, 256, strip_smem(8), s>>>(a);
             break;
         default:
             return cudaErrorInvalidValue;
@@ -1136,9 +1403,18 @@ cudaError_t occupancy_ising_strip(int *blocks_per_sm, int warps) {
         return e;
     if ((e = cudaFuncSetAttribute(ising_strip_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip_smem(8))))
         return e;
+    if ((e = cudaFuncSetAttribute(ising_split_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip_smem(4))))
+        return e;
+    if ((e = cudaFuncSetAttribute(ising_split_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip_smem(8))))
+        return e;
+    if (old_strip()) {
+        if (warps == 4)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<4>, 128, strip_smem(4));
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<8>, 256, strip_smem(8));
+    }
     if (warps == 4)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<4>, 128, strip_smem(4));
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<8>, 256, strip_smem(8));
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_split_kernel<4>, 128, strip_smem(4));
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_split_kernel<8>, 256, strip_smem(8));
 }
 
 // The dynamic shared-memory limit of a kernel is process-wide state: it is

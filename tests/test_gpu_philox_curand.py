@@ -78,3 +78,19 @@ def test_oracle_philox_equals_curand(curand_lib):
         key = [int(seed[i]) & 0xFFFFFFFF, int(seed[i]) >> 32]
         want = oracle.philox4x32_10([int(g[i]), int(lat[i]), int(t[i]), int(c[i])], key)
         assert np.array_equal(out[i], want), i
+
+
+@pytest.mark.parametrize("g0,n", [(0, 1), (12345, 100003), (2**32 - 4099, 4099), (7, 0)])
+def test_philox_stream_digest_matches_the_oracle(g0, n):
+    """The library's stream code (the sweeps' Philox path with its hoisted
+    products) against the oracle's Philox, through a digest of every word."""
+    import paper_2304_01772_gb300 as sm
+    seed, lat, t, c = 0xFEEDFACE12345678, 300, 4242, 1
+    got = int(sm.philox_xor(seed, lat, t, c, g0, n).cpu().numpy().view(np.uint32)[0])
+    assert got == oracle.philox_xor(seed, lat, t, c, g0, n)
+
+
+def test_philox_stream_digest_rejects_ranges_past_the_counter():
+    import paper_2304_01772_gb300 as sm
+    with pytest.raises(sm.SpinError):
+        sm.philox_xor(1, 0, 0, 0, 2**32 - 10, 11)

@@ -79,3 +79,19 @@ def test_accept_decision_matches_count():
         k = int(oracle.accept_count(beta, dE))
         assert oracle.lib().or_accept(beta, dE, k - 1) == 1
         assert oracle.lib().or_accept(beta, dE, k) == 0
+
+
+@pytest.mark.parametrize("g0,n", [(0, 0), (0, 1), (12345, 517), (2**32 - 300, 300)])
+def test_philox_xor_digest_equals_the_blocks_it_covers(g0, n):
+    """The stream digest (XOR of every word of blocks g0 .. g0 + n - 1) equals
+    the XOR of the known-answer-pinned single blocks, in any order."""
+    seed, lat, t, c = 0x0123456789ABCDEF, 7, 99, 1
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    want = 0
+    for g in range(g0, g0 + n):
+        r = oracle.philox4x32_10([g, lat, t, c], key)
+        want ^= int(r[0]) ^ int(r[1]) ^ int(r[2]) ^ int(r[3])
+    assert oracle.philox_xor(seed, lat, t, c, g0, n) == want
+    if n > 1:   # a split range XORs to the whole
+        h = n // 2
+        assert oracle.philox_xor(seed, lat, t, c, g0, h) ^ oracle.philox_xor(seed, lat, t, c, g0 + h, n - h) == want
