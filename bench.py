@@ -388,7 +388,7 @@ def measured_peaks():
 KERNEL_SECTIONS = {
     # kernel: (file, section start, section end, end of the part of internal.h it depends on)
     "ising_strip_kernel": ("sweep_ising.cu",
-                           "// ------------------------------------------------------------------ strip kernel",
+                           "// Row-strip kernel in the split form",
                            "// Copy every lattice", "cudaError_t launch_ising_strip("),
     "dmc_step_kernel": ("dmc.cu", "// One whole optimisation iteration per lattice",
                         "// loss[lat] = sum (target - s)^2", "cudaError_t launch_dmc_step("),

@@ -19,8 +19,6 @@
 //  * ising_plain_kernel: one lattice, one colour, in place (two launches per
 //    lattice per sweep: the plain launch form the batched one is compared to).
 //  * ising_generic_kernel: any even L (not a multiple of 16), one thread per site.
-#include <stdlib.h>
-
 #include "internal.h"
 #include "strip.cuh"
 
@@ -630,22 +628,13 @@ __global__ void init_random_kernel(void *spins, int model, const LatDev *lats, u
     }
 }
 
-// ------------------------------------------------------------------ strip kernel
-// Lattices with L = 512, 1024 or 2048: one warp owns full rows [r0, r0 + R)
-// of one lattice and walks down them.  At step s it updates colour 0 on row
-// s and colour 1 on row s - 1 (whose neighbours on rows s - 2 and s already
-// carry their colour-0 updates).  Rows -1 and R are the recomputed halo:
-// their colour-0 updates are needed by colour 1 of rows 0 and R - 1 and come
-// from the same site-keyed Philox counters as in the neighbouring item, so
-// items never exchange data.  Each warp keeps rows s-2 .. s+2 in a five-slot
-// shared-memory ring; row s+2 streams in with cp.async while the warp works on
-// rows s-2 .. s+1.  Lane l handles chunks l, l + 32, ..; left / right
-// neighbours come from lane shuffles, the two words that cross a 32-chunk
-// boundary from shared memory.  No block barrier is needed.
-//
-// In the ring a spin is the byte 8 * [s < 0] ("x8 form"): four neighbour
+// ------------------------------------------------------------- the x8 form
+// In shared memory a spin is the byte 8 * [s < 0] ("x8 form"): four neighbour
 // bytes plus 5x the centre byte add without carries to 8 * (d + 5 c), the
-// byte offset of the table entry.
+// byte offset of the site's 8-byte table entry (d = down neighbours, c = the
+// site itself down).  The tile and resident kernels update 16-byte row chunks
+// in this form (chunk_x8); the row-strip kernel below keeps its rows split
+// by column parity.
 constexpr uint32_t kX8 = 0x08080808u;
 __device__ __forceinline__ uint4 to_x8(uint4 v) {
     return make_uint4(v.x & kX8, v.y & kX8, v.z & kX8, v.w & kX8);
@@ -709,97 +698,6 @@ __device__ __forceinline__ uint4 chunk_x8(uint4 C, uint4 U, uint4 D, uint32_t lw
     return make_uint4(out[0], out[1], out[2], out[3]);
 }
 
-struct StripCtx {
-    const uint4 *S;
-    uint4 *D;
-    uint4 *ring;              // kRing * kRowChunks chunks of this warp
-    int L, Lv, cpl, r0, nrows, lane;
-    PhiloxPrefix P0, P1;
-    uint32_t tab_cnt;         // shared address (byte 0 zero) of the table with statistics deltas
-    uint32_t tab_halo;        // same thresholds, zero deltas (recomputed halo rows)
-};
-
-__device__ __forceinline__ uint4 *slot(const StripCtx &x, int r) {
-    return x.ring + ((r + 2) % kRing) * kRowChunks;
-}
-
-__device__ __forceinline__ void issue_row(const StripCtx &x, int r) {
-    const uint4 *src = x.S + (size_t)wrap_row(x.r0 + r, x.L) * x.Lv;
-    uint4 *dst = slot(x, r);
-    for (int j = x.lane; j < x.Lv; j += 32) cp_async16(dst + j, src + j);
-}
-
-__device__ __forceinline__ void convert_row(const StripCtx &x, int r) {
-    uint4 *row = slot(x, r);
-    for (int j = x.lane; j < x.Lv; j += 32) row[j] = to_x8(row[j]);
-}
-
-// One chunk of one colour phase given its neighbour words (see row_phase).
-__device__ __forceinline__ void phase_chunk(int j, int colour, uint4 *rc, const uint4 *ru,
-                                            const uint4 *rd, uint4 *gout, const uint4 &C,
-                                            uint32_t lw, uint32_t rw, uint32_t gyb,
-                                            const RowPar &rp, const PhiloxPrefix &PP,
-                                            uint32_t stab, const PhiloxKeys &rk, int &acc) {
-    const uint4 U = ru[j];
-    const uint4 Dn = rd[j];
-    const uint32_t g0 = gyb + 2u * (uint32_t)j;
-    const uint4 ra = philox_from_prefix(g0, PP, rk);
-    const uint4 rb = philox_from_prefix(g0 + 1u, PP, rk);
-    const uint4 N = chunk_x8(C, U, Dn, lw, rw, ra, rb, rp, stab, acc);
-    if (colour == 0)
-        rc[j] = N;
-    else
-        gout[j] = make_uint4(from_x8(N.x), from_x8(N.y), from_x8(N.z), from_x8(N.w));
-}
-
-// One colour on row r of the ring.  Colour 0 writes the row back to the ring;
-// colour 1 writes the final row (converted back to +-1 bytes) to global memory.
-// Lanes hold chunks lane + 32 k; the words left and right of a chunk come from
-// the neighbouring lanes by shuffles, and for lanes 0 and 31 from the chunk
-// the next lane-31 / lane-0 holds (the previous iteration's, carried in a
-// register, or the next iteration's, one broadcast shared-memory load).  Rows
-// of 1024 and 2048 bytes take two chunks per iteration.
-__device__ __forceinline__ void row_phase(const StripCtx &x, int r, int colour,
-                                          const PhiloxKeys &rk, int &acc) {
-    const int y = wrap_row(x.r0 + r, x.L);
-    const RowPar rp = row_par((colour ^ y) & 1);
-    const PhiloxPrefix &PP = colour ? x.P1 : x.P0;
-    const uint32_t stab = (r >= 0 && r < x.nrows) ? x.tab_cnt : x.tab_halo;
-    uint4 *rc = slot(x, r);
-    const uint4 *ru = slot(x, r - 1);
-    const uint4 *rd = slot(x, r + 1);
-    const uint32_t gyb = (uint32_t)y * (uint32_t)(x.L >> 3);
-    uint4 *gout = x.D + (size_t)y * x.Lv;
-    const int lane = x.lane, mask = x.Lv - 1;
-    const bool first = lane == 0, last = lane == 31;
-    const int src_l = (lane + 31) & 31, src_r = (lane + 1) & 31;
-    // word 3 of the row's last chunk: left neighbour of chunk 0 (periodic)
-    uint32_t carry = reinterpret_cast<const uint32_t *>(rc + mask)[3];
-    if (x.Lv >= 64) {
-        for (int j = lane; j < x.Lv; j += 64) {
-            const uint4 A = rc[j], B = rc[j + 32];
-            const uint32_t nxt = reinterpret_cast<const uint32_t *>(rc + ((j - lane + 64) & mask))[0];
-            const uint32_t al = __shfl_sync(0xFFFFFFFFu, A.w, src_l);
-            const uint32_t ar = __shfl_sync(0xFFFFFFFFu, A.x, src_r);
-            const uint32_t bl = __shfl_sync(0xFFFFFFFFu, B.w, src_l);
-            const uint32_t br = __shfl_sync(0xFFFFFFFFu, B.x, src_r);
-            const uint32_t a31 = __shfl_sync(0xFFFFFFFFu, A.w, 31);
-            const uint32_t b0 = __shfl_sync(0xFFFFFFFFu, B.x, 0);
-            const uint32_t lwA = first ? carry : al, rwA = last ? b0 : ar;
-            const uint32_t lwB = first ? a31 : bl, rwB = last ? nxt : br;
-            carry = __shfl_sync(0xFFFFFFFFu, B.w, 31);
-            phase_chunk(j, colour, rc, ru, rd, gout, A, lwA, rwA, gyb, rp, PP, stab, rk, acc);
-            phase_chunk(j + 32, colour, rc, ru, rd, gout, B, lwB, rwB, gyb, rp, PP, stab, rk, acc);
-        }
-    } else {
-        const uint4 A = rc[lane];
-        const uint32_t al = __shfl_sync(0xFFFFFFFFu, A.w, src_l);
-        const uint32_t ar = __shfl_sync(0xFFFFFFFFu, A.x, src_r);
-        phase_chunk(lane, colour, rc, ru, rd, gout, A, al, ar, gyb, rp, PP, stab, rk, acc);
-    }
-    __syncwarp();
-}
-
 // Unpack the packed per-lane sums (dB * 65536 + dM) into 32-bit totals.
 __device__ __forceinline__ void drain_acc(int &acc, int &dm, int &db) {
     const int m = (int)(int16_t)(acc & 0xFFFF);
@@ -808,84 +706,19 @@ __device__ __forceinline__ void drain_acc(int &acc, int &dm, int &db) {
     acc = 0;
 }
 
-__device__ void strip_item(const StripCtx &x, const PhiloxKeys &rk, int &dm, int &db) {
-    issue_row(x, -2);
-    cp_async_commit();
-    issue_row(x, -1);
-    cp_async_commit();
-    issue_row(x, 0);
-    cp_async_commit();
-    int acc = 0;
-    for (int s = -1; s <= x.nrows; ++s) {
-        if (s + 2 <= x.nrows + 1) issue_row(x, s + 2);
-        cp_async_commit();
-        cp_async_wait1();           // every row up to s + 1 has landed
-        if (s == -1) {
-            convert_row(x, -2);
-            convert_row(x, -1);
-        }
-        convert_row(x, s + 1);
-        __syncwarp();
-        row_phase(x, s, 0, rk, acc);
-        if (s >= 1) row_phase(x, s - 1, 1, rk, acc);
-        if ((s & 7) == 7) drain_acc(acc, dm, db);
-    }
-    drain_acc(acc, dm, db);
-    cp_async_wait_all();
-    __syncwarp();
-}
-
-template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) ising_strip_kernel(IsingSweepArgs a) {
-    extern __shared__ __align__(16) uint4 ring_all[];
-    // 256-byte tables: an entry's address is the table's with byte 0 replaced
-    __shared__ __align__(256) TabEntry tabs[WARPS][2][256 / sizeof(TabEntry)];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t t = a.state->t;
-    const int gw = blockIdx.x * WARPS + warp, nw = gridDim.x * WARPS;
-    for (int it = gw; it < a.n_items; it += nw) {
-        const Item w = a.items[it];
-        const LatDev ld = a.lats[w.lat];
-        if (lane < kTabStride) {
-            const TabEntry e = a.tabs[w.lat * kTabStride + lane];
-            tabs[warp][0][lane] = e;
-            tabs[warp][1][lane] = TabEntry{e.thr, 0};
-        }
-        __syncwarp();
-        StripCtx x;
-        x.S = reinterpret_cast<const uint4 *>(a.src + ld.offset);
-        x.D = reinterpret_cast<uint4 *>(a.dst + ld.offset);
-        x.ring = ring_all + (size_t)warp * kRing * kRowChunks;
-        x.L = ld.L;
-        x.Lv = ld.L >> 4;
-        x.cpl = ld.L >> 9;
-        x.r0 = w.r0;
-        x.nrows = w.nrows;
-        x.lane = lane;
-        x.P0 = philox_prefix((uint32_t)w.lat, t, 0u, a.rk);
-        x.P1 = philox_prefix((uint32_t)w.lat, t, 1u, a.rk);
-        x.tab_cnt = (uint32_t)__cvta_generic_to_shared(tabs[warp][0]);
-        x.tab_halo = (uint32_t)__cvta_generic_to_shared(tabs[warp][1]);
-        int dm = 0, db = 0;
-        strip_item(x, a.rk, dm, db);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            dm += __shfl_xor_sync(0xFFFFFFFFu, dm, o);
-            db += __shfl_xor_sync(0xFFFFFFFFu, db, o);
-        }
-        if (lane == 0) {
-            if (dm) atomicAdd(reinterpret_cast<unsigned long long *>(a.delta + 2 * w.lat), (unsigned long long)(long long)dm);
-            if (db) atomicAdd(reinterpret_cast<unsigned long long *>(a.delta + 2 * w.lat + 1), (unsigned long long)(long long)db);
-        }
-        __syncwarp();
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Row-strip kernel in the split form (Alg. 1 on the square-lattice stencil).
 //
-// The walk of ising_strip_kernel, with each ring row stored as its two
-// colour-compressed halves in the x8 form: half 0 holds the sites of even x,
+// Lattices with L = 512, 1024 or 2048: one warp owns full rows [r0, r0 + R)
+// of one lattice and walks down them.  At step s it updates colour 0 on row
+// s and colour 1 on row s - 1 (whose neighbours on rows s - 2 and s already
+// carry their colour-0 updates).  Rows -1 and R are the recomputed halo:
+// their colour-0 updates are needed by colour 1 of rows 0 and R - 1 and come
+// from the same site-keyed Philox counters as in the neighbouring item, so
+// items never exchange data and no block barrier is needed.
+//
+// Each ring row is stored as its two colour-compressed halves in the x8
+// form: half 0 holds the sites of even x,
 // half 1 those of odd x (site x of a row is byte x >> 1 of half x & 1).  For
 // colour c on row y the active sites are half p = (c + y) & 1, and all four
 // bytes of a 32-bit word of that half are active: a word's up and down
@@ -1093,7 +926,7 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
 }  // namespace split
 
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) ising_split_kernel(IsingSweepArgs a) {
+__global__ void __launch_bounds__(WARPS * 32) ising_strip_kernel(IsingSweepArgs a) {
     extern __shared__ __align__(16) unsigned char ring_bytes[];
     __shared__ __align__(256) TabEntry tabs[WARPS][2][256 / sizeof(TabEntry)];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1375,21 +1208,13 @@ cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, s
 
 size_t strip_smem(int warps) { return strip_ring_bytes(warps); }
 
-static bool old_strip() {
-    static int v = -1;
-    if (v < 0) v = getenv("SPINMC_OLD_STRIP") ? 1 : 0;
-    return v == 1;
-}
-
 cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, cudaStream_t s) {
     switch (warps) {
         case 4:
-            if (old_strip()) ising_strip_kernel<4><<<grid, 128, strip_smem(4), s>>>(a);
-            else ising_split_kernel<4><<<grid, 128, strip_smem(4), s>>>(a);
+            ising_strip_kernel<4><<<grid, 128, strip_smem(4), s>>>(a);
             break;
         case 8:
-            if (old_strip()) ising_strip_kernel<8><<<grid, 256, strip_smem(8), s>>>(a);
-            else ising_split_kernel<8><<<grid, 256, strip_smem(8), s>>>(a);
+            ising_strip_kernel<8><<<grid, 256, strip_smem(8), s>>>(a);
             break;
         default:
             return cudaErrorInvalidValue;
@@ -1403,18 +1228,9 @@ cudaError_t occupancy_ising_strip(int *blocks_per_sm, int warps) {
         return e;
     if ((e = cudaFuncSetAttribute(ising_strip_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip_smem(8))))
         return e;
-    if ((e = cudaFuncSetAttribute(ising_split_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip_smem(4))))
-        return e;
-    if ((e = cudaFuncSetAttribute(ising_split_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip_smem(8))))
-        return e;
-    if (old_strip()) {
-        if (warps == 4)
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<4>, 128, strip_smem(4));
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<8>, 256, strip_smem(8));
-    }
     if (warps == 4)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_split_kernel<4>, 128, strip_smem(4));
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_split_kernel<8>, 256, strip_smem(8));
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<4>, 128, strip_smem(4));
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<8>, 256, strip_smem(8));
 }
 
 // The dynamic shared-memory limit of a kernel is process-wide state: it is
