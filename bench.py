@@ -19,8 +19,10 @@ One JSON line on stdout (rank 0):
                int8 spins under e2e.int8_spins), sweeps, and reads back the
                spins and that step's statistics
 --impl reference times the CPU oracle alone (the reference arm).
-Multi-GPU (torchrun): every rank runs its own 512-lattice batch (weak
-scaling, no data-path collective); time = max over ranks.
+Multi-GPU (torchrun): the 512-lattice batch is split over the ranks by
+site count (strong scaling: every lattice keeps the Philox stream it has in
+the one-GPU run, no data-path collective); --scaling weak gives every rank the
+whole batch under its own seed instead.  Time = max over ranks.
 """
 from __future__ import annotations
 
@@ -55,6 +57,8 @@ def parse():
     ap.add_argument("--cpu-sweeps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--scaling", default="strong", choices=["strong", "weak"],
+                    help="N > 1: split one batch over the ranks (strong) or give each rank the whole batch (weak)")
     ap.add_argument("--workload", default="uneven512",
                     choices=["uneven512", "potts_q3", "potts_q8", "cpm1024", "ising_small", "grad", "mlp", "dmc",
                              "spinglass", "cpm_batch", "triangular", "nnn", "fit", "rng"])
@@ -519,6 +523,16 @@ def max_over_ranks(x, dist):
     return _max(x, dist, device="cuda")
 
 
+def sum_over_ranks(xs, dist):
+    """Element-wise sums of a list of integers over all ranks."""
+    if dist is None:
+        return [int(x) for x in xs]
+    import torch
+    t = torch.tensor([int(x) for x in xs], dtype=torch.int64, device="cuda")
+    dist.all_reduce(t)
+    return [int(v) for v in t.tolist()]
+
+
 def barrier(dist):
     import torch
     if dist is not None:
@@ -601,14 +615,15 @@ def run_ours(args):
     import numpy as np
     from paper_2304_01772_gb300 import workloads as wl
 
-    lats = wl.uneven512()
-    sites = wl.site_count(lats)
+    lats_all = wl.uneven512()
+    job_sites = wl.site_count(lats_all)     # sites of the whole job per sweep (strong scaling)
+    lats = lats_all
     cpu = None
     rank0_single = args.gpus == 1 and int(os.environ.get("RANK", 0)) == 0
     if rank0_single and not args.no_cpu:
         # before the first GPU call: a process pool forked after it could hang
         cores = os.cpu_count() or 1
-        rate, updates, wall = cpu_oracle_rate(lats, max(1, args.cpu_sweeps), cores)
+        rate, updates, wall = cpu_oracle_rate(lats_all, max(1, args.cpu_sweeps), cores)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"all 512 lattices, {max(1, args.cpu_sweeps)} sweep(s) each ({updates:.3e} updates, "
                          f"{wall:.1f} s wall)"}
@@ -618,8 +633,17 @@ def run_ours(args):
     rank, world, dist = dist_setup(args.gpus)
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     stream = torch.cuda.current_stream()
-    from paper_2304_01772_gb300.dist import job_throughput, rank_seed
-    sim = sm.Sim(sm.SPIN_ISING, lats, seed=rank_seed(SEED, rank), max_record=max(16, args.e2e_steps))
+    from paper_2304_01772_gb300.dist import rank_lattices, rank_seed
+    if args.scaling == "strong":
+        # this rank's share; lattice_id = global index + 1 keeps every lattice's stream
+        lats, _ = rank_lattices(lats_all, rank, world)
+        seed = SEED
+    else:
+        seed = rank_seed(SEED, rank)
+    sites = wl.site_count(lats)             # sites of this rank per sweep
+    # units of the whole job per sweep: the batch (strong) or one batch per rank (weak)
+    units = job_sites if args.scaling == "strong" else job_sites * world
+    sim = sm.Sim(sm.SPIN_ISING, lats, seed=seed, max_record=max(16, args.e2e_steps))
     launch = sim.get_launch() if args.no_tune else sim.autotune(sweeps_per_trial=4)
     sim.sweep(args.warmup)
 
@@ -647,6 +671,15 @@ def run_ours(args):
     e1.record(stream)
     barrier(dist)
     ms_plain = max_over_ranks(e0.elapsed_time(e1), dist)
+    # ---- the batched form's own kernels, one launch per lattice (what batching the launches buys)
+    sim.set_launch(3, True, launch["tile_rows"] or -1, max(256, launch["threads"]))
+    sim.sweep(2)
+    barrier(dist)
+    e0.record(stream)
+    sim.sweep(args.plain_steps)
+    e1.record(stream)
+    barrier(dist)
+    ms_plain3 = max_over_ranks(e0.elapsed_time(e1), dist)
     sim.set_launch(launch["mode"], True, launch["tile_rows"] or -1, launch["threads"])
 
     # ---- kernel time of the batched sweep kernels (CUDA events in the library)
@@ -668,7 +701,7 @@ def run_ours(args):
     host_in.copy_(sim.spins.cpu())
     NB = 3   # contexts in flight
     host_out = [torch.empty(span, dtype=torch.int8, pin_memory=True) for _ in range(NB)]
-    sims = [sim] + [sm.Sim(sm.SPIN_ISING, lats, seed=rank_seed(SEED, rank) + 7919 * b, max_record=4)
+    sims = [sim] + [sm.Sim(sm.SPIN_ISING, lats, seed=seed + 7919 * b, max_record=4)
                     for b in range(1, NB)]
     for x in sims[1:]:
         x.set_launch(launch["mode"], True, launch["tile_rows"] or -1, launch["threads"])
@@ -732,14 +765,17 @@ def run_ours(args):
     e2e_int8_s = e2e_run(False)
     e2e_s = e2e_run(True)
     st_host = h_stats[0]
+    # host<->device bytes of one step of the whole job (every rank's copies)
+    job_bytes = sum_over_ranks([4 * nw, 4 * nw + st_host.numel() * 8, span, span + st_host.numel() * 8], dist)
 
     if rank != 0:
         return 0
-    value = job_throughput(sites * args.steps, world, ms * 1e-3)
+    value = units * args.steps / (ms * 1e-3)
     strip_ms = prof[1][0] / prof[1][1] if prof[1][1] else None
     rng = rng_ceiling(1, (sum(d["L"] ** 2 for d in lats if d["L"] in (512, 1024, 2048)) / (strip_ms * 1e-3))
                       if strip_ms else None, measured_peaks()[0])
-    plain = job_throughput(sites * args.plain_steps, world, ms_plain * 1e-3)
+    plain = units * args.plain_steps / (ms_plain * 1e-3)
+    plain3 = units * args.plain_steps / (ms_plain3 * 1e-3)
     peak, peak_kind = measured_peaks()
     strip_sites = sum(d["L"] ** 2 for d in lats if d["L"] in (512, 1024, 2048))
     cls_sites = [sites - strip_sites, strip_sites]
@@ -769,15 +805,25 @@ def run_ours(args):
     kn = kernels[dom]["launches"] if dom else 0
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattices": len(lats), "sites_per_sweep": sites,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": args.scaling, "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattices": len(lats_all), "sites_per_sweep": job_sites,
+                   "split": ("the batch split over the ranks by site count, lattice_id = global index + 1"
+                             if args.scaling == "strong" else "every rank runs the whole batch, seed + rank"),
+                   "rank0_lattices": len(lats), "rank0_sites_per_sweep": sites,
                    "launch": "batched work-list kernels, CUDA graph replay; autotuned form "
                              + json.dumps(launch),
                    "l2": "inputs larger than L2 (state 409 MB + ping-pong buffer), no flush",
                    "bit_exact": "spins identical to the CPU oracle and across launch forms (tests/)"},
         "plain": {"value": plain, "unit": UNIT, "steps": args.plain_steps,
-                  "ms_per_step": ms_plain / args.plain_steps, "speedup_batched_vs_plain": value / plain},
+                  "ms_per_step": ms_plain / args.plain_steps, "speedup_batched_vs_plain": value / plain,
+                  "form": "two launches per lattice per sweep of the per-chunk plain kernel (launch mode 1)",
+                  "same_kernels_per_lattice": {
+                      "value": plain3, "unit": UNIT, "ms_per_step": ms_plain3 / args.plain_steps,
+                      "speedup_batched_vs_this": value / plain3,
+                      "form": "the batched form's kernels (row-strip for L >= 512, tile below) launched once "
+                              "per lattice per sweep, each lattice cut into its own items (launch mode 3), "
+                              "graph-replayed; identical spins (tests/test_gpu_parity.py)"}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": ncu_traffic(dom),
                      "kernel": dom, "algorithmic_bytes_per_launch": alg_bytes,
@@ -785,15 +831,15 @@ def run_ours(args):
                      "peak_source": f"{peak_kind} hbm_gbs (copy)", "kernels": kernels,
                      "issue": issue_roofline(dom, "uneven512", kms_dom, clk.get("sm_mhz") if clk else None),
                      "rng": rng},
-        "e2e": {"value": sites * args.e2e_steps * world / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": 4 * nw, "d2h_bytes_per_step": 4 * nw + st_host.numel() * 8,
+        "e2e": {"value": units * args.e2e_steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": job_bytes[0], "d2h_bytes_per_step": job_bytes[1],
                 "transfer": "one bit per spin: spin_load_spins_packed uploads the packed state from pinned "
                             "host memory and unpacks it, one sweep, spin_store_spins_packed packs and "
                             "downloads the new state, then that sweep's statistics",
                 "pipeline": "three contexts on three streams; uploads and downloads each first in, first "
                             "out, so the upload of step k+1 overlaps the download of step k",
-                "int8_spins": {"value": sites * args.e2e_steps * world / e2e_int8_s, "unit": UNIT,
-                               "h2d_bytes_per_step": span, "d2h_bytes_per_step": span + st_host.numel() * 8}},
+                "int8_spins": {"value": units * args.e2e_steps / e2e_int8_s, "unit": UNIT,
+                               "h2d_bytes_per_step": job_bytes[2], "d2h_bytes_per_step": job_bytes[3]}},
         "gpu_launches": launches,
         "clocks": clk,
     }

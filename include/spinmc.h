@@ -20,7 +20,9 @@
  * Bonds are counted once.  Lattices are L x L, row-major, periodic, L even.
  *
  * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = (seed low 32
- * bits, seed high 32 bits), counter = (g, lattice index, sweep index, colour),
+ * bits, seed high 32 bits), counter = (g, lattice word, sweep index, colour)
+ * with the lattice word the lattice's index in its batch unless its
+ * descriptor's lattice_id says otherwise,
  * where for a site (x, y) of colour c
  *   Ising: k = (y L + x) >> 1, g = k >> 2, draw = lane k & 3;
  *   Potts: k = (y L + x) >> 1, g = k >> 1, acceptance lane 2(k&1), choice lane 2(k&1)+1,
@@ -84,6 +86,12 @@ typedef struct {
                              lane k & 3 of Philox group k >> 2; Ising only, and a context holds
                              either only such lattices or none; statistics (M, B, B2)            */
     float J2;             /* second-neighbour (diagonal) coupling, geometry 2; otherwise 0    */
+    uint32_t lattice_id;  /* 0: the lattice word of this lattice's Philox counters is its
+                             index in this batch; k > 0: it is k - 1.  A lattice draws the
+                             same numbers (initial state included) in any batch that gives
+                             it the same word, so a batch split over several contexts or
+                             GPUs, each lattice given its index in the whole batch plus one,
+                             runs exactly the chains of the whole batch in one context.  */
     uint64_t spin_offset; /* element offset of this lattice in the caller's spin buffer       */
 } spin_lattice_desc;
 
@@ -198,7 +206,11 @@ int spin_grad_from_limbs(spin_ctx *ctx, const int64_t *limbs, int32_t observable
 int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_params *cpm);
 
 /* Launch form.  mode: 0 = batched persistent work-list launch (default),
- * 1 = plain per-lattice launches (two per lattice per sweep), 2 = resident
+ * 1 = plain per-lattice launches (two per lattice per sweep of a simple
+ * per-chunk kernel), 3 = the kernels of mode 0 launched once per lattice per
+ * sweep (the row-strip kernel for L = 512, 1024, 2048, the tile kernel for
+ * the other sides that are multiples of 16, each lattice cut into its own
+ * items: what batching the launches saves), 2 = resident
  * (Ising only, every L a multiple of 16 and <= 256, or only triangular
  * lattices with L <= 240, or only second-neighbour lattices with L <= 256: one
  * CTA per lattice keeps it in shared memory for all sweeps of a spin_sweep
@@ -290,7 +302,7 @@ uint32_t spin_sweep_index(const spin_ctx *ctx);
 int32_t spin_gpu_launches(const spin_ctx *ctx); /* kernels launched by the last spin_sweep */
 const char *spin_last_error(const spin_ctx *ctx);
 void spin_destroy(spin_ctx *ctx);
-int spin_version(void);
+int spin_version(void);   /* 2: spin_lattice_desc carries lattice_id */
 
 /* ------------------------------------------------------------------------
  * Allocation-free Ising sweep.  The paper has no counterpart: this entry point
@@ -299,13 +311,18 @@ int spin_version(void);
  * reserved up front, embeddings that forbid allocation after start-up).
  *
  * Runs sweeps first_sweep .. first_sweep + n_sweeps - 1 of the Ising chain
- * defined by (seed, lat) on the caller's int8 spins, exactly as spin_sweep
- * would (bit-identical spins and statistics), without a context and without
- * allocating: its scratch (second spin buffer, tables, work list, counters)
- * is a static device array of SPIN_NOALLOC_SCRATCH_BYTES that every GPU which
- * loads the library holds until exit.  The lattices' span (largest
- * spin_offset + L*L) plus descriptors must fit in it, every L must be in
- * [4, 4096] and n_lattices <= 4096; otherwise SPIN_EINVAL.
+ * defined by (seed, lat) on the caller's int8 spins with the result of
+ * spin_sweep (bit-identical spins and statistics), without a context and
+ * without allocating: its scratch (second spin buffer, tables, work list,
+ * counters) is a static device array of SPIN_NOALLOC_SCRATCH_BYTES that every
+ * GPU which loads the library holds until exit.  Its launch plan is simpler
+ * than a context's: lattices with L % 16 == 0 run on the tile kernel (also
+ * L = 512, 1024 and 2048, which spin_sweep gives the faster row-strip
+ * kernel), other even L on the per-site kernel.  Limits (SPIN_EINVAL beyond
+ * them): L even in [4, 2048], n_lattices <= 4096, and the lattices' span
+ * (largest spin_offset + L*L bytes) plus about 2 KB of descriptors per 64
+ * lattices within the 16 MiB array -- for example three 2048^2 lattices fit,
+ * four do not.
  * d_stats: NULL or device int64 [n_sweeps][n_lattices][2] = (M, B) after
  * each sweep.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) and should come before any stream capture.

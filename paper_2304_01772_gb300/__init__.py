@@ -32,7 +32,7 @@ class SpinError(RuntimeError):
 class LatticeDesc(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("q", ctypes.c_int32), ("beta", ctypes.c_float),
                 ("J", ctypes.c_float), ("h", ctypes.c_float), ("geometry", ctypes.c_int32),
-                ("J2", ctypes.c_float), ("spin_offset", ctypes.c_uint64)]
+                ("J2", ctypes.c_float), ("lattice_id", ctypes.c_uint32), ("spin_offset", ctypes.c_uint64)]
 
 
 class CpmParams(ctypes.Structure):
@@ -201,7 +201,7 @@ class Sim:
         for i, d in enumerate(lattices):
             arr[i] = LatticeDesc(int(d["L"]), int(d.get("q", 2)), float(d.get("beta", 0.0)),
                                  float(d.get("J", 1.0)), float(d.get("h", 0.0)), int(d.get("geometry", 0)),
-                                 float(d.get("J2", 0.0)), int(offsets[i]))
+                                 float(d.get("J2", 0.0)), int(d.get("lattice_id", 0)), int(offsets[i]))
         self._desc = arr
         self.lattices = [dict(d) for d in lattices]
         cp = None
@@ -353,7 +353,7 @@ class Sim:
             for i, d in enumerate(lattices):
                 arr[i] = LatticeDesc(int(d["L"]), int(d.get("q", 2)), float(d.get("beta", 0.0)),
                                      float(d.get("J", 1.0)), float(d.get("h", 0.0)), int(d.get("geometry", 0)),
-                                     float(d.get("J2", 0.0)), int(self.offsets[i]))
+                                     float(d.get("J2", 0.0)), int(d.get("lattice_id", 0)), int(self.offsets[i]))
             self._desc = arr
             self.lattices = [dict(d) for d in lattices]
         cp = self._cpm_struct(cpm) if cpm is not None else None

@@ -49,6 +49,12 @@ constexpr int kMaxItemBytes = 65536;   // bounds the per-thread packed counters
 constexpr int kWholeMaxBytes = 16384;  // lattices up to 128 x 128 are one item
 constexpr int kMaxL = 32768;
 
+// The lattice word of a lattice's Philox counters: lattice_id - 1 when the
+// caller gives one, else the lattice's index in this batch.
+uint32_t rng_word(const spin_lattice_desc &d, int index) {
+    return d.lattice_id ? d.lattice_id - 1u : (uint32_t)index;
+}
+
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int launches = 0;
@@ -109,6 +115,13 @@ struct spin_ctx {
     // launch form
     int mode = 0, use_graph = 1, tile_rows = 0, threads = 256;
     int use_strip = 1;
+    // launch mode 3: one launch per lattice, items [first, first + count) of
+    // the strip list (strip = 1) or of the tile list
+    struct LatRange {
+        int strip, first, count;
+    };
+    std::vector<LatRange> per_lattice;
+    int per_sm_strip = 1;
     int grid = 0;
     size_t smem = 0;
     int sm_count = 0;
@@ -411,9 +424,11 @@ int plan(spin_ctx *ctx) {
         }
         smem = std::max(smem, (size_t)(rows + 4) * L);
     }
-    std::stable_sort(items.begin(), items.end(), [&](const Item &a, const Item &b) {
-        return (size_t)a.nrows * ctx->lat[a.lat].L > (size_t)b.nrows * ctx->lat[b.lat].L;
-    });
+    // mode 3 launches lattice by lattice: keep each lattice's items together
+    if (ctx->mode != 3)
+        std::stable_sort(items.begin(), items.end(), [&](const Item &a, const Item &b) {
+            return (size_t)a.nrows * ctx->lat[a.lat].L > (size_t)b.nrows * ctx->lat[b.lat].L;
+        });
     if (ctx->d_items) cudaFree(ctx->d_items);
     ctx->d_items = nullptr;
     ctx->n_items = (int)items.size();
@@ -442,7 +457,11 @@ int plan(spin_ctx *ctx) {
         // lattices over the resident warps in about one wave (the recomputed
         // halo costs one row per item, so items stay as tall as that allows).
         const size_t slots = (size_t)ctx->sm_count * std::max(1, per_sm) * ctx->strip_warps;
-        if (ctx->model == SPIN_ISING && ctx->tile_rows <= 0) {
+        ctx->per_sm_strip = std::max(1, per_sm);
+        if (ctx->mode == 3 && ctx->model == SPIN_ISING && ctx->tile_rows <= 0) {
+            // each lattice alone on the GPU: its own balanced cut
+            for (int id : strip_ids) balanced_strip_items(ctx, std::vector<int>{id}, slots * kStripRounds, strip);
+        } else if (ctx->model == SPIN_ISING && ctx->tile_rows <= 0) {
             balanced_strip_items(ctx, strip_ids, slots * kStripRounds, strip);
         } else {
             for (int id : strip_ids) {
@@ -472,6 +491,21 @@ int plan(spin_ctx *ctx) {
     const int per_sm_thr = 2048 / ctx->threads;
     const int per_sm = std::max(1, std::min(per_sm_smem, per_sm_thr));
     ctx->grid = std::max(1, std::min(ctx->n_items, ctx->sm_count * per_sm));
+    // per-lattice ranges of both lists (items of one lattice are contiguous
+    // in mode 3)
+    ctx->per_lattice.clear();
+    if (ctx->mode == 3) {
+        auto ranges = [&](const std::vector<Item> &v, int is_strip) {
+            for (int i = 0; i < (int)v.size();) {
+                int j = i;
+                while (j < (int)v.size() && v[j].lat == v[i].lat) ++j;
+                ctx->per_lattice.push_back({is_strip, i, j - i});
+                i = j;
+            }
+        };
+        ranges(strip, 1);
+        ranges(items, 0);
+    }
     return SPIN_OK;
 }
 
@@ -497,11 +531,11 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                 const bool timed = prof_begin(ctx, s, 2);
                 if (ctx->model == SPIN_ISING)
                     CK(launch_ising_plain(static_cast<int8_t *>(src) + ctx->lat[id].spin_offset, ctx->d_lats,
-                                          id, L, ctx->d_tabs, ctx->k0, ctx->k1, ctx->d_state,
+                                          id, rng_word(ctx->lat[id], id), L, ctx->d_tabs, ctx->k0, ctx->k1, ctx->d_state,
                                           ctx->st.delta, c, s));
                 else
                     CK(launch_potts_plain(static_cast<uint8_t *>(src) + ctx->lat[id].spin_offset, ctx->d_lats,
-                                          id, L, ctx->lat[id].q, ctx->d_tabs, ctx->k0, ctx->k1,
+                                          id, rng_word(ctx->lat[id], id), L, ctx->lat[id].q, ctx->d_tabs, ctx->k0, ctx->k1,
                                           ctx->d_state, ctx->st.delta, w, c, s));
                 if (timed) prof_end(ctx, s);
                 ++launches;
@@ -554,6 +588,42 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                                         ctx->n_generic, ctx->generic_maxL, ctx->d_lats, ctx->d_tabs,
                                         ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, w, c, s));
             ++launches;
+        }
+        if (ctx->mode == 3) {
+            // one launch per lattice of the same kernels (the plain launch
+            // form of the batched kernels: what batching the launches saves)
+            for (const auto &r : ctx->per_lattice) {
+                const bool timed = prof_begin(ctx, s, 2);
+                if (ctx->model == SPIN_ISING) {
+                    IsingSweepArgs a{(r.strip ? ctx->d_strip : ctx->d_items) + r.first, r.count, ctx->d_lats,
+                                     ctx->d_tabs, static_cast<const int8_t *>(src), static_cast<int8_t *>(dst),
+                                     ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, philox_keys(ctx->k0, ctx->k1)};
+                    if (r.strip)
+                        CK(launch_ising_strip(a, std::min((r.count + ctx->strip_warps - 1) / ctx->strip_warps,
+                                                          ctx->sm_count * ctx->per_sm_strip),
+                                              ctx->strip_warps, s));
+                    else
+                        CK(launch_ising_fused(a, std::min(r.count, ctx->grid), ctx->threads, ctx->smem, s));
+                } else if (r.strip) {
+                    PottsStripArgs a{ctx->d_strip + r.first, r.count, ctx->d_lats, ctx->d_tabs,
+                                     static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst),
+                                     ctx->d_state, ctx->st.delta, ctx->st.cur, w, ctx->strip_chunks,
+                                     philox_keys(ctx->k0, ctx->k1)};
+                    CK(launch_potts_strip(a, std::min((r.count + ctx->strip_warps - 1) / ctx->strip_warps,
+                                                      ctx->sm_count * ctx->per_sm_strip),
+                                          ctx->strip_warps, ctx->strip_qbits, s));
+                } else {
+                    PottsSweepArgs a{ctx->d_items + r.first, r.count, ctx->d_lats, ctx->d_tabs,
+                                     static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst),
+                                     ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, w};
+                    CK(launch_potts_fused(a, std::min(r.count, ctx->grid), ctx->threads, ctx->smem, s));
+                }
+                if (timed) prof_end(ctx, s);
+                ++launches;
+            }
+            CK(launch_finalize(ctx->d_state, ctx->st, record, s));
+            ++launches;
+            return SPIN_OK;
         }
         // The tile kernel (small lattices) and the strip kernel (L >= 512) touch
         // disjoint lattices: fork the tile kernel onto a side stream and join
@@ -612,7 +682,7 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
 
 int launch_cpm_step(spin_ctx *ctx, int record, cudaStream_t s, int &launches) {
     for (int c = 0; c < 4; ++c) {
-        CpmArgs a{static_cast<int32_t *>(ctx->spins), ctx->lat[0].L, 0u, ctx->d_type, ctx->d_J,
+        CpmArgs a{static_cast<int32_t *>(ctx->spins), ctx->lat[0].L, rng_word(ctx->lat[0], 0), ctx->d_type, ctx->d_J,
                   ctx->n_types, ctx->n_cells, ctx->lambda, ctx->target, ctx->d_vol[c & 1], ctx->d_vol[(c + 1) & 1],
                   ctx->d_dvol[c & 1], ctx->d_dvol[(c + 1) & 1], ctx->d_thr, ctx->n_thr, ctx->k0, ctx->k1,
                   ctx->d_state, ctx->st.delta};
@@ -661,7 +731,7 @@ int run_sweeps(spin_ctx *ctx, int n, int record, cudaStream_t s) {
     int launches = 0;
     if (ctx->model == SPIN_CPM && ctx->mode == 2) {
         CpmPersistArgs p{};
-        p.a = CpmArgs{static_cast<int32_t *>(ctx->spins), ctx->lat[0].L, 0u, ctx->d_type, ctx->d_J, ctx->n_types,
+        p.a = CpmArgs{static_cast<int32_t *>(ctx->spins), ctx->lat[0].L, rng_word(ctx->lat[0], 0), ctx->d_type, ctx->d_J, ctx->n_types,
                       ctx->n_cells, ctx->lambda, ctx->target, nullptr, nullptr, nullptr, nullptr, ctx->d_thr,
                       ctx->n_thr, ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta};
         p.vol[0] = ctx->d_vol[0];
@@ -784,7 +854,7 @@ void build_ising_table(const spin_lattice_desc &d, TabEntry *out) { ising_table(
 
 extern "C" {
 
-int spin_version(void) { return 1; }
+int spin_version(void) { return 2; }
 
 const char *spin_last_error(const spin_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
@@ -877,7 +947,7 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
         const auto &d = ctx->lat[i];
         const int geom = model == SPIN_CPM ? 0 : d.geometry;
         ld[i] = LatDev{d.spin_offset, d.L, model == SPIN_POTTS ? d.q : 2,
-                       (geom == 0 && d.L % 16 == 0 && d.spin_offset % 16 == 0) ? 1 : 0, geom};
+                       (geom == 0 && d.L % 16 == 0 && d.spin_offset % 16 == 0) ? 1 : 0, geom, rng_word(d, i), 0};
         ctx->maxL = std::max(ctx->maxL, d.L);
         ctx->span_elems = std::max<size_t>(ctx->span_elems, d.spin_offset + (size_t)d.L * d.L);
         if (geom == 2) {
@@ -967,7 +1037,7 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
             e = cudaMemcpyAsync(ctx->d_type, cpm->cell_type, ctx->n_cells + 1, cudaMemcpyHostToDevice, s);
             if (e) return bail(cuda_fail(ctx, e, "cell types"));
         } else {
-            e = launch_cpm_types(ctx->d_type, ctx->n_cells, 0u, ctx->k0, ctx->k1, s);
+            e = launch_cpm_types(ctx->d_type, ctx->n_cells, rng_word(ctx->lat[0], 0), ctx->k0, ctx->k1, s);
             if (e) return bail(cuda_fail(ctx, e, "cpm types"));
         }
         // the CPM kernels address the lattice at offset 0 of the buffer
@@ -1200,8 +1270,9 @@ int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_
         if (rc) return rc;
         for (int i = 0; i < ctx->n_lat; ++i)
             if (lat[i].L != ctx->lat[i].L || lat[i].q != ctx->lat[i].q ||
-                lat[i].spin_offset != ctx->lat[i].spin_offset || lat[i].geometry != ctx->lat[i].geometry)
-                return fail(ctx, SPIN_EINVAL, "spin_set_params may not change L, q, geometry or offsets");
+                lat[i].spin_offset != ctx->lat[i].spin_offset || lat[i].geometry != ctx->lat[i].geometry ||
+                lat[i].lattice_id != ctx->lat[i].lattice_id)
+                return fail(ctx, SPIN_EINVAL, "spin_set_params may not change L, q, geometry, lattice_id or offsets");
         ctx->lat.assign(lat, lat + ctx->n_lat);
     }
     if (cpm) {
@@ -1246,7 +1317,8 @@ static bool resident_ok(const spin_ctx *ctx) {
 
 int spin_set_launch(spin_ctx *ctx, int32_t mode, int32_t use_graph, int32_t tile_rows, int32_t threads) {
     if (!ctx) return SPIN_EINVAL;
-    if (mode < 0 || mode > 2) return fail(ctx, SPIN_EINVAL, "launch mode must be 0, 1 or 2");
+    if (mode < 0 || mode > 3) return fail(ctx, SPIN_EINVAL, "launch mode must be 0, 1, 2 or 3");
+    if (mode == 3 && ctx->model == SPIN_CPM) return fail(ctx, SPIN_EINVAL, "mode 3 is for Ising and Potts contexts");
     if (mode == 2 && !resident_ok(ctx))
         return fail(ctx, SPIN_EINVAL, "resident form needs Ising lattices with L % 16 == 0 and L <= 256, "
                                       "only triangular lattices with L <= 240, only second-neighbour "

@@ -14,6 +14,8 @@ struct LatDev {
     int32_t q;        // Potts states (2 for Ising)
     int32_t fast;     // 1: L % 16 == 0 and offset % 16 == 0 -> vectorised kernels
     int32_t geom;     // 0: square lattice, 1: triangular, 2: first and second neighbours (Ising)
+    uint32_t rng;     // lattice word of the lattice's Philox counters
+    uint32_t pad;
 };
 
 // One work item of the batched sweep: rows [r0, r0 + nrows) of lattice `lat`.
@@ -113,7 +115,7 @@ cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, s
                                cudaStream_t s);
 // Warp-per-row-strip kernel for L in {512, 1024, 2048}; items are row blocks.
 cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, cudaStream_t s);
-cudaError_t launch_ising_plain(int8_t *spins, const LatDev *lat_dev, int lat, int L,
+cudaError_t launch_ising_plain(int8_t *spins, const LatDev *lat_dev, int lat, uint32_t rng, int L,
                                const TabEntry *tabs, uint32_t k0, uint32_t k1,
                                const DevState *state, int64_t *delta, int colour, cudaStream_t s);
 // Lattices whose side is not a multiple of 16: two passes, src -> dst (colour 0,
@@ -198,7 +200,7 @@ struct PottsStripArgs {
 // qbits: 2 for q <= 4, 3 for q <= 8.
 cudaError_t launch_potts_strip(const PottsStripArgs &a, int grid, int warps, int qbits, cudaStream_t s);
 cudaError_t occupancy_potts_strip(int *blocks_per_sm, int warps, int qbits, int ring_chunks);
-cudaError_t launch_potts_plain(uint8_t *spins, const LatDev *lat_dev, int lat, int L, int q,
+cudaError_t launch_potts_plain(uint8_t *spins, const LatDev *lat_dev, int lat, uint32_t rng, int L, int q,
                                const TabEntry *tabs, uint32_t k0, uint32_t k1,
                                const DevState *state, int64_t *delta, int width, int colour,
                                cudaStream_t s);

@@ -3,9 +3,13 @@
 // Some callers cannot call cudaMalloc: code that runs inside another
 // framework's memory pool or allocator hook, a process whose device memory is
 // fully reserved up front, or an embedding that forbids allocation after
-// start-up.  spin_ising_sweep_noalloc runs the same batched Ising sweep as
-// spin_sweep (same kernels, same Philox stream, bit-identical spins and
-// statistics) without a context: its scratch -- the second spin buffer, the
+// start-up.  spin_ising_sweep_noalloc runs the Ising chain of spin_sweep
+// (same Philox stream, same tables: bit-identical spins and statistics)
+// without a context, on a simpler launch plan: every lattice with L % 16 == 0
+// goes through the tile kernel (whole lattices up to 128^2, row blocks above),
+// the others through the per-site kernel; the row-strip kernel that
+// spin_sweep uses for L = 512, 1024 and 2048 is not used here, so those sizes
+// run slower than through a context.  Its scratch -- the second spin buffer, the
 // acceptance tables, the work list and the statistics counters -- lives in
 // the file-scope array g_noalloc_scratch below, which every GPU that loads
 // the library holds until the process exits.  The caller passes the spins
@@ -44,6 +48,10 @@ int g_sm_count[kMaxDevices] = {0};
 // Host staging for the descriptors copied into the scratch array (no heap).
 constexpr int kMaxLat = 4096;
 constexpr int kMaxItems = 16384;
+// Largest side: a row block of the tile kernel holds 32768 / L rows plus a
+// four-row halo in shared memory, which at L = 4096 (12 rows, 48 KB) exceeds
+// the kernel's 47 KB without a raised limit.
+constexpr int kMaxSide = 2048;
 LatDev g_lat_stage[kMaxLat];
 TabEntry g_tab_stage[kMaxLat * kTabStride];
 Item g_item_stage[kMaxItems];
@@ -78,10 +86,10 @@ extern "C" int spin_ising_sweep_noalloc(uint64_t seed, int32_t n_lattices,
     size_t smem = 16;
     for (int i = 0; i < n_lattices; ++i) {
         const spin_lattice_desc &d = lat[i];
-        if (d.L < 4 || (d.L & 1) || d.L > 4096 || d.geometry != 0 || d.J2 != 0.0f) return SPIN_EINVAL;
+        if (d.L < 4 || (d.L & 1) || d.L > kMaxSide || d.geometry != 0 || d.J2 != 0.0f) return SPIN_EINVAL;
         if (!(d.beta >= 0.0f) || !(d.beta < 3.0e38f) || !(d.J == d.J) || !(d.h == d.h)) return SPIN_EINVAL;
         const bool fast = d.L % 16 == 0 && d.spin_offset % 16 == 0;
-        g_lat_stage[i] = LatDev{d.spin_offset, d.L, 2, fast ? 1 : 0, 0};
+        g_lat_stage[i] = LatDev{d.spin_offset, d.L, 2, fast ? 1 : 0, 0, d.lattice_id ? d.lattice_id - 1u : (uint32_t)i, 0};
         build_ising_table(d, g_tab_stage + (size_t)i * kTabStride);
         span = span > d.spin_offset + (size_t)d.L * d.L ? span : d.spin_offset + (size_t)d.L * d.L;
         maxL = maxL > d.L ? maxL : d.L;

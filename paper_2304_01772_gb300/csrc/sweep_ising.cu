@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kTriResThreads) ising_tri_resident_kernel(Resi
         const uint32_t t = a.t0 + (uint32_t)sweep;
         int acc = 0;
         for (int c = 0; c < 3; ++c) {
-            const PhiloxPrefix P = philox_prefix((uint32_t)lat, t, (uint32_t)c, a.rk);
+            const PhiloxPrefix P = philox_prefix(ld.rng, t, (uint32_t)c, a.rk);
             int gy = y00, gm = m00, goff = (c + y00) % 3;
             for (int grp = threadIdx.x; 4 * grp < nk; grp += kTriResThreads) {
                 const uint4 r = philox_from_prefix((uint32_t)grp, P, a.rk);
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kNnnThreads) ising_nnn_kernel(const int8_t *sr
     const uint32_t t = state->t;
     int dm = 0, db = 0, db2 = 0;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; 4 * g < nk; g += gridDim.x * blockDim.x) {
-        const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)lat, t, (uint32_t)c), k0, k1);
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)g, ld.rng, t, (uint32_t)c), k0, k1);
         if (c == 0)
             nnn_group<true>(S, D, L, half, nk, g, c, r, tab, dm, db, db2);
         else
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kNnnResThreads) ising_nnn_resident_kernel(Resi
             const int dY = (int)blockDim.x / gpr, dq = (int)blockDim.x - dY * gpr;
             int ss = 0, sd1 = 0, sd2 = 0;
             for (int c = 0; c < 4; ++c) {
-                const PhiloxPrefix P = philox_prefix((uint32_t)lat, t, (uint32_t)c, a.rk);
+                const PhiloxPrefix P = philox_prefix(ld.rng, t, (uint32_t)c, a.rk);
                 int Y = Y0, q = q0;
                 for (int g = threadIdx.x; 4 * g < nk; g += blockDim.x) {
                     const uint4 r = philox_from_prefix((uint32_t)g, P, a.rk);
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(kNnnResThreads) ising_nnn_resident_kernel(Resi
         } else {
             for (int c = 0; c < 4; ++c) {
                 for (int g = threadIdx.x; 4 * g < nk; g += blockDim.x) {
-                    const uint4 r = philox4x32_10(make_uint4((uint32_t)g, (uint32_t)lat, t, (uint32_t)c), a.k0, a.k1);
+                    const uint4 r = philox4x32_10(make_uint4((uint32_t)g, ld.rng, t, (uint32_t)c), a.k0, a.k1);
                     nnn_group<false>(S, S, L, half, nk, g, c, r, tab, dm, db, db2);
                 }
                 __syncthreads();
@@ -452,7 +452,7 @@ __global__ void advance_state_kernel(DevState *state, uint32_t n, int record) {
 }
 
 // One lattice, one colour, in place, straight from global memory.
-__global__ void __launch_bounds__(256) ising_plain_kernel(int8_t *spins, int L, uint32_t lat,
+__global__ void __launch_bounds__(256) ising_plain_kernel(int8_t *spins, int L, uint32_t lat, uint32_t rng,
                                                           const TabEntry *tab, uint32_t k0,
                                                           uint32_t k1, const DevState *state,
                                                           int64_t *delta, int c) {
@@ -476,7 +476,7 @@ __global__ void __launch_bounds__(256) ising_plain_kernel(int8_t *spins, int L, 
         const uint32_t rw = S32[((size_t)i * Lv + (j == Lv - 1 ? 0 : j + 1)) * 4];
         const uint32_t g0 = (uint32_t)i * (uint32_t)(L >> 3) + 2u * (uint32_t)j;
         S[(size_t)i * Lv + j] =
-            ising_chunk(Cc, Uc, Dc, lw, rw, g0, (c ^ i) & 1, lat, t, (uint32_t)c, k0, k1, stab,
+            ising_chunk(Cc, Uc, Dc, lw, rw, g0, (c ^ i) & 1, rng, t, (uint32_t)c, k0, k1, stab,
                         true, acc);
     }
     flush_ising_acc<256>(acc, delta + 2 * lat, red);
@@ -515,7 +515,7 @@ __global__ void ising_tri_kernel(const int8_t *src, int8_t *dst, const int32_t *
         const int cdown = s < 0 ? 1 : 0;
         const TabEntry e = tabs[lat * kTabStride + dcount + 7 * cdown];
         const uint32_t k = (uint32_t)(y * (L / 3) + x / 3);
-        const uint4 r = philox4x32_10(make_uint4(k >> 2, (uint32_t)lat, t, (uint32_t)c), k0, k1);
+        const uint4 r = philox4x32_10(make_uint4(k >> 2, ld.rng, t, (uint32_t)c), k0, k1);
         const uint32_t lane = k & 3u;
         const uint32_t u = lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
         const int sv = s < 0 ? -1 : 1;
@@ -575,7 +575,7 @@ __global__ void ising_generic_kernel(const int8_t *src, int8_t *dst, const int32
         const int cdown = s < 0 ? 1 : 0;
         const TabEntry e = tabs[lat * kTabStride + dcount + 5 * cdown];
         const uint32_t k = (uint32_t)i >> 1;
-        const uint4 r = philox4x32_10(make_uint4(k >> 2, (uint32_t)lat, t, (uint32_t)c), k0, k1);
+        const uint4 r = philox4x32_10(make_uint4(k >> 2, ld.rng, t, (uint32_t)c), k0, k1);
         const uint32_t lane = k & 3u;
         const uint32_t u = lane == 0 ? r.x : lane == 1 ? r.y : lane == 2 ? r.z : r.w;
         if (u <= e.thr) {
@@ -614,7 +614,7 @@ __global__ void init_random_kernel(void *spins, int model, const LatDev *lats, u
     const int groups = (ld.L * ld.L) >> 2;
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < groups; g += gridDim.x * blockDim.x) {
         const uint4 r =
-            philox4x32_10(make_uint4((uint32_t)g, blockIdx.y, 0xFFFFFFFFu, 0u), k0, k1);
+            philox4x32_10(make_uint4((uint32_t)g, ld.rng, 0xFFFFFFFFu, 0u), k0, k1);
         const uint32_t u[4] = {r.x, r.y, r.z, r.w};
         if (model == 0) {
             int8_t *S = static_cast<int8_t *>(spins) + ld.offset + 4 * (size_t)g;
@@ -949,8 +949,8 @@ __global__ void __launch_bounds__(WARPS * 32) ising_strip_kernel(IsingSweepArgs 
         x.r0 = w.r0;
         x.nrows = w.nrows;
         x.lane = lane;
-        x.P0 = philox_prefix((uint32_t)w.lat, t, 0u, a.rk);
-        x.P1 = philox_prefix((uint32_t)w.lat, t, 1u, a.rk);
+        x.P0 = philox_prefix(ld.rng, t, 0u, a.rk);
+        x.P1 = philox_prefix(ld.rng, t, 1u, a.rk);
         x.tab_cnt = (uint32_t)__cvta_generic_to_shared(tabs[warp][0]);
         x.tab_halo = (uint32_t)__cvta_generic_to_shared(tabs[warp][1]);
         int dm = 0, db = 0;
@@ -1045,7 +1045,7 @@ __global__ void __launch_bounds__(THREADS) ising_fused_kernel(IsingSweepArgs a) 
             const int lo = w.whole ? 0 : (c == 0 ? 1 : 2);
             const int hi = w.whole ? w.nrows : (c == 0 ? w.nrows + 3 : w.nrows + 2);
             const int n_units = (hi - lo) * Lv;
-            const PhiloxPrefix P = philox_prefix((uint32_t)w.lat, t, (uint32_t)c, a.rk);
+            const PhiloxPrefix P = philox_prefix(ld.rng, t, (uint32_t)c, a.rk);
             int i = lo + i0, j = j0;
             for (int v = threadIdx.x; v < n_units; v += THREADS) {
                 const int iu = (i == 0) ? nload - 1 : i - 1;
@@ -1121,7 +1121,7 @@ __global__ void __launch_bounds__(THREADS) ising_resident_kernel(ResidentArgs a)
         const uint32_t t = a.t0 + (uint32_t)sweep;
         int acc = 0;
         for (int c = 0; c < 2; ++c) {
-            const PhiloxPrefix P = philox_prefix((uint32_t)lat, t, (uint32_t)c, a.rk);
+            const PhiloxPrefix P = philox_prefix(ld.rng, t, (uint32_t)c, a.rk);
             int i = i0, j = j0;
             for (int v = threadIdx.x; v < L * Lv; v += THREADS) {
                 const int iu = i == 0 ? L - 1 : i - 1, id = i == L - 1 ? 0 : i + 1;
@@ -1298,12 +1298,12 @@ cudaError_t launch_ising_tri_resident(const ResidentArgs &a, int n_lat, size_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_ising_plain(int8_t *spins, const LatDev *, int lat, int L, const TabEntry *tabs,
+cudaError_t launch_ising_plain(int8_t *spins, const LatDev *, int lat, uint32_t rng, int L, const TabEntry *tabs,
                                uint32_t k0, uint32_t k1, const DevState *state, int64_t *delta,
                                int colour, cudaStream_t s) {
     const int units = L * (L >> 4);
     ising_plain_kernel<<<(units + 255) / 256, 256, 0, s>>>(
-        spins, L, (uint32_t)lat, tabs + lat * kTabStride, k0, k1, state, delta, colour);
+        spins, L, (uint32_t)lat, rng, tabs + lat * kTabStride, k0, k1, state, delta, colour);
     return cudaGetLastError();
 }
 

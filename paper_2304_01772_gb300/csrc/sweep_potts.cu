@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(THREADS) potts_fused_kernel(PottsSweepArgs a) 
                 const bool count = (i >= halo) && (i < halo + w.nrows);
                 const uint32_t gbase = (uint32_t)gy * (uint32_t)(L >> 2) + 4u * (uint32_t)j;
                 sm4[i * Lv + j] =
-                    potts_chunk(Cc, Uc, Dc, lw, rw, gbase, (c ^ gy) & 1, (uint32_t)w.lat, t,
+                    potts_chunk(Cc, Uc, Dc, lw, rw, gbase, (c ^ gy) & 1, ld.rng, t,
                                 (uint32_t)c, a.k0, a.k1, q, stab, count, acc, shist, small_q);
             }
             __syncthreads();
@@ -430,8 +430,8 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) potts_strip_kernel(Pot
         x.rchunks = a.ring_chunks;
         x.q1 = (uint32_t)ld.q - 1u;
         x.vadd = (0x81u - (uint32_t)ld.q) * kOnes;
-        x.P0 = philox_prefix((uint32_t)w.lat, t, 0u, a.rk);
-        x.P1 = philox_prefix((uint32_t)w.lat, t, 1u, a.rk);
+        x.P0 = philox_prefix(ld.rng, t, 0u, a.rk);
+        x.P1 = philox_prefix(ld.rng, t, 1u, a.rk);
         x.tab_cnt = tabs[warp][0];
         x.tab_halo = tabs[warp][1];
         int acc = 0;
@@ -532,7 +532,7 @@ __global__ void potts_generic_kernel(const uint8_t *src, uint8_t *dst, const int
         const int xl = x == 0 ? L - 1 : x - 1, xr = x == L - 1 ? 0 : x + 1;
         const uint32_t nb[4] = {S[yu * L + x], S[yd * L + x], S[y * L + xl], S[y * L + xr]};
         const uint32_t k = (uint32_t)i >> 1;
-        const uint4 r = philox4x32_10(make_uint4(k >> 1, (uint32_t)lat, t, (uint32_t)c), k0, k1);
+        const uint4 r = philox4x32_10(make_uint4(k >> 1, ld.rng, t, (uint32_t)c), k0, k1);
         const uint32_t u0 = (k & 1u) ? r.z : r.x;
         const uint32_t u1 = (k & 1u) ? r.w : r.y;
         uint32_t sp = s + 1u + __umulhi(u1, q - 1u);
@@ -603,13 +603,13 @@ cudaError_t set_potts_fused_smem(size_t smem) {
     return cudaSuccess;
 }
 
-cudaError_t launch_potts_plain(uint8_t *spins, const LatDev *, int lat, int L, int q,
+cudaError_t launch_potts_plain(uint8_t *spins, const LatDev *, int lat, uint32_t rng, int L, int q,
                                const TabEntry *tabs, uint32_t k0, uint32_t k1,
                                const DevState *state, int64_t *delta, int width, int colour,
                                cudaStream_t s) {
     const int units = L * (L >> 4);
     potts_plain_kernel<<<(units + 255) / 256, 256, 0, s>>>(
-        spins, L, (uint32_t)lat, (uint32_t)q, tabs + lat * kTabStride, k0, k1, state,
+        spins, L, rng, (uint32_t)q, tabs + lat * kTabStride, k0, k1, state,
         delta + (size_t)width * lat, colour);
     return cudaGetLastError();
 }

@@ -1,12 +1,19 @@
-"""Multi-GPU sharding of independent lattice batches (one process per GPU).
+"""Multi-GPU sharding of a lattice batch (one process per GPU).
 
-Lattices never exchange data during sweeps, so N GPUs run N independent
-batches (weak scaling): rank r runs the full batch with seed `seed + r`.
-Throughput is the units processed on all ranks divided by the slowest rank's
-time; that max over ranks is taken after the timed region.  The one exchange
-of the method is the gradient over chains that share theta but live on
-different GPUs: an all-reduce (sum) of the pooled integer moments, carried
-as 32-bit limbs so that the sum is exact (`pooled_gradient`).
+Lattices never exchange data during sweeps, so the batch axis is the natural
+shard (the paper's batch dimension B of its [B, C, H, W] tensor, Sec.
+"Methods"): `partition_by_sites` splits one batch over the ranks by site count
+(greedy largest-first bin packing of the ragged sizes), and `rank_lattices`
+gives each rank its lattices with lattice_id = global index + 1, so that every
+lattice draws the Philox numbers it would draw in the whole batch and the
+ranks together run exactly the one-GPU chains (strong scaling, no data-path
+collective).  The weak-scaling alternative gives every rank the whole batch
+under its own seed (`rank_seed`).  Throughput is the units processed on all
+ranks divided by the slowest rank's time; that max over ranks is taken after
+the timed region.  The one exchange of the method is the gradient over chains
+that share theta but live on different GPUs: an all-reduce (sum) of the pooled
+integer moments, carried as 32-bit limbs so that the sum is exact
+(`pooled_gradient`).
 """
 from __future__ import annotations
 
@@ -21,8 +28,34 @@ def rank_info():
     return rank, world, local
 
 
+def partition_by_sites(sizes, world: int):
+    """Split lattices of sides `sizes` over `world` ranks by site count: the
+    lattices in decreasing L^2 (ties by index) each go to the rank with the
+    fewest sites so far (ties to the lowest rank).  Deterministic: every rank
+    computes the same split.  Returns one ascending list of lattice indices
+    per rank; no rank's load exceeds the mean by more than the largest lattice."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    order = sorted(range(len(sizes)), key=lambda i: (-int(sizes[i]) ** 2, i))
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(i)
+        load[r] += int(sizes[i]) ** 2
+    return [sorted(p) for p in parts]
+
+
+def rank_lattices(lattices, rank: int, world: int):
+    """This rank's share of a batch: (lattice dicts with lattice_id = global
+    index + 1, their global indices)."""
+    idx = partition_by_sites([d["L"] for d in lattices], world)[rank]
+    return [dict(lattices[i], lattice_id=i + 1) for i in idx], idx
+
+
 def rank_seed(seed: int, rank: int) -> int:
-    """Seed of rank `rank`: distinct Philox keys, so the ranks' chains are independent."""
+    """Seed of rank `rank` in the weak-scaling mode (every rank runs the whole
+    batch): distinct Philox keys, so the ranks' chains are independent."""
     return (seed + rank) & ((1 << 64) - 1)
 
 

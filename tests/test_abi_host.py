@@ -24,7 +24,7 @@ def test_library_exports_every_declared_symbol():
     assert len(names) >= 20
     for n in names:
         assert hasattr(lib, n), n
-    assert lib.spin_version() == 1
+    assert lib.spin_version() == 2
     assert lib.spin_mlp_param_count() == 3 * 64 + 64 + 64 * 64 + 64 + 2 * 64 + 2
 
 
@@ -41,14 +41,14 @@ def _init(model, descs, cpm=None):
 
 
 @pytest.mark.parametrize("desc,model", [
-    (sm.LatticeDesc(63, 2, 0.4, 1.0, 0.0, 0, 0.0, 0), sm.SPIN_ISING),          # odd L
-    (sm.LatticeDesc(2, 2, 0.4, 1.0, 0.0, 0, 0.0, 0), sm.SPIN_ISING),           # too small
-    (sm.LatticeDesc(64, 2, float("nan"), 1.0, 0.0, 0, 0.0, 0), sm.SPIN_ISING),  # NaN beta
-    (sm.LatticeDesc(64, 2, -0.1, 1.0, 0.0, 0, 0.0, 0), sm.SPIN_ISING),         # negative beta
-    (sm.LatticeDesc(64, 1, 0.4, 1.0, 0.0, 0, 0.0, 0), sm.SPIN_POTTS),          # q < 2
-    (sm.LatticeDesc(64, 256, 0.4, 1.0, 0.0, 0, 0.0, 0), sm.SPIN_POTTS),        # q > 255
-    (sm.LatticeDesc(64, 3, 0.4, 1.0, 0.1, 0, 0.0, 0), sm.SPIN_POTTS),          # Potts with a field
-    (sm.LatticeDesc(64, 2, 0.4, 1.0, 0.0, 1, 0.0, 0), sm.SPIN_ISING),          # reserved != 0
+    (sm.LatticeDesc(63, 2, 0.4, 1.0, 0.0, 0, 0.0, 0, 0), sm.SPIN_ISING),          # odd L
+    (sm.LatticeDesc(2, 2, 0.4, 1.0, 0.0, 0, 0.0, 0, 0), sm.SPIN_ISING),           # too small
+    (sm.LatticeDesc(64, 2, float("nan"), 1.0, 0.0, 0, 0.0, 0, 0), sm.SPIN_ISING),  # NaN beta
+    (sm.LatticeDesc(64, 2, -0.1, 1.0, 0.0, 0, 0.0, 0, 0), sm.SPIN_ISING),         # negative beta
+    (sm.LatticeDesc(64, 1, 0.4, 1.0, 0.0, 0, 0.0, 0, 0), sm.SPIN_POTTS),          # q < 2
+    (sm.LatticeDesc(64, 256, 0.4, 1.0, 0.0, 0, 0.0, 0, 0), sm.SPIN_POTTS),        # q > 255
+    (sm.LatticeDesc(64, 3, 0.4, 1.0, 0.1, 0, 0.0, 0, 0), sm.SPIN_POTTS),          # Potts with a field
+    (sm.LatticeDesc(64, 2, 0.4, 1.0, 0.0, 1, 0.0, 0, 0), sm.SPIN_ISING),          # reserved != 0
 ])
 def test_invalid_lattices_rejected(desc, model):
     rc, ctx = _init(model, [desc])
@@ -56,21 +56,21 @@ def test_invalid_lattices_rejected(desc, model):
 
 
 def test_overlapping_lattices_rejected():
-    rc, _ = _init(sm.SPIN_ISING, [sm.LatticeDesc(16, 2, 0.4, 1.0, 0.0, 0, 0.0, 0),
-                                  sm.LatticeDesc(16, 2, 0.4, 1.0, 0.0, 0, 0.0, 100)])
+    rc, _ = _init(sm.SPIN_ISING, [sm.LatticeDesc(16, 2, 0.4, 1.0, 0.0, 0, 0.0, 0, 0),
+                                  sm.LatticeDesc(16, 2, 0.4, 1.0, 0.0, 0, 0.0, 0, 100)])
     assert rc == -1
 
 
 def test_cpm_parameter_checks():
     J = (ctypes.c_int32 * 9)(0, 16, 16, 16, 2, 11, 16, 12, 14)   # not symmetric
     cp = sm.CpmParams(3, 1, 400, 10, J, None, 10.0, 4, 5, 0)
-    rc, _ = _init(sm.SPIN_CPM, [sm.LatticeDesc(64, 2, 0.0, 0.0, 0.0, 0, 0.0, 0)], cp)
+    rc, _ = _init(sm.SPIN_CPM, [sm.LatticeDesc(64, 2, 0.0, 0.0, 0.0, 0, 0.0, 0, 0)], cp)
     assert rc == -1
     Jok = (ctypes.c_int32 * 9)(0, 16, 16, 16, 2, 11, 16, 11, 14)
     cp = sm.CpmParams(3, 1, 400, 10, Jok, None, 10.0, 4, 5, 0)
-    rc, _ = _init(sm.SPIN_CPM, [sm.LatticeDesc(66, 2, 0.0, 0.0, 0.0, 0, 0.0, 0)], cp)   # L % 4 != 0
+    rc, _ = _init(sm.SPIN_CPM, [sm.LatticeDesc(66, 2, 0.0, 0.0, 0.0, 0, 0.0, 0, 0)], cp)   # L % 4 != 0
     assert rc == -1
-    rc, _ = _init(sm.SPIN_ISING, [sm.LatticeDesc(64, 2, 0.4, 1.0, 0.0, 0, 0.0, 0)], cp)  # cpm for Ising
+    rc, _ = _init(sm.SPIN_ISING, [sm.LatticeDesc(64, 2, 0.4, 1.0, 0.0, 0, 0.0, 0, 0)], cp)  # cpm for Ising
     assert rc == -1
 
 
@@ -116,12 +116,12 @@ def test_cpm_batch_entry_points_reject_invalid_arguments_on_the_host():
 
 
 @pytest.mark.parametrize("desc,model", [
-    (sm.LatticeDesc(48, 2, 0.4, 1.0, 0.0, 3, 0.0, 0), sm.SPIN_ISING),   # unknown geometry
-    (sm.LatticeDesc(48, 3, 0.4, 1.0, 0.0, 2, 0.5, 0), sm.SPIN_POTTS),   # second neighbours are Ising only
-    (sm.LatticeDesc(48, 2, 0.4, 1.0, 0.0, 0, 0.5, 0), sm.SPIN_ISING),   # J2 without second neighbours
-    (sm.LatticeDesc(48, 2, 0.4, 1.0, 0.0, 2, float("inf"), 0), sm.SPIN_ISING),   # non-finite J2
-    (sm.LatticeDesc(64, 2, 0.4, 1.0, 0.0, 1, 0.0, 0), sm.SPIN_ISING),   # triangular needs L % 6 == 0
-    (sm.LatticeDesc(48, 3, 0.4, 1.0, 0.0, 1, 0.0, 0), sm.SPIN_POTTS),   # triangular is Ising only
+    (sm.LatticeDesc(48, 2, 0.4, 1.0, 0.0, 3, 0.0, 0, 0), sm.SPIN_ISING),   # unknown geometry
+    (sm.LatticeDesc(48, 3, 0.4, 1.0, 0.0, 2, 0.5, 0, 0), sm.SPIN_POTTS),   # second neighbours are Ising only
+    (sm.LatticeDesc(48, 2, 0.4, 1.0, 0.0, 0, 0.5, 0, 0), sm.SPIN_ISING),   # J2 without second neighbours
+    (sm.LatticeDesc(48, 2, 0.4, 1.0, 0.0, 2, float("inf"), 0, 0), sm.SPIN_ISING),   # non-finite J2
+    (sm.LatticeDesc(64, 2, 0.4, 1.0, 0.0, 1, 0.0, 0, 0), sm.SPIN_ISING),   # triangular needs L % 6 == 0
+    (sm.LatticeDesc(48, 3, 0.4, 1.0, 0.0, 1, 0.0, 0, 0), sm.SPIN_POTTS),   # triangular is Ising only
 ])
 def test_geometry_is_validated(desc, model):
     rc, _ = _init(model, [desc])
@@ -129,11 +129,11 @@ def test_geometry_is_validated(desc, model):
 
 
 def test_second_neighbour_lattices_do_not_share_a_context():
-    rc, _ = _init(sm.SPIN_ISING, [sm.LatticeDesc(16, 2, 0.4, 1.0, 0.0, 2, 0.5, 0),
-                                  sm.LatticeDesc(16, 2, 0.4, 1.0, 0.0, 0, 0.0, 256)])
+    rc, _ = _init(sm.SPIN_ISING, [sm.LatticeDesc(16, 2, 0.4, 1.0, 0.0, 2, 0.5, 0, 0),
+                                  sm.LatticeDesc(16, 2, 0.4, 1.0, 0.0, 0, 0.0, 0, 256)])
     assert rc == EINVAL
-    rc, _ = _init(sm.SPIN_ISING, [sm.LatticeDesc(18, 2, 0.4, 1.0, 0.0, 1, 0.0, 0),
-                                  sm.LatticeDesc(16, 2, 0.4, 1.0, 0.0, 2, 0.5, 512)])
+    rc, _ = _init(sm.SPIN_ISING, [sm.LatticeDesc(18, 2, 0.4, 1.0, 0.0, 1, 0.0, 0, 0),
+                                  sm.LatticeDesc(16, 2, 0.4, 1.0, 0.0, 2, 0.5, 0, 512)])
     assert rc == EINVAL
 
 
@@ -146,3 +146,29 @@ def test_barrier_selftest_rejects_invalid_arguments_on_the_host():
     lib = sm.lib()
     for blocks, missing, rounds in [(0, 0, 1), (4, -1, 1), (4, 5, 1), (4, 0, 0)]:
         assert lib.spin_barrier_selftest(blocks, missing, rounds, None) == EINVAL
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """The ctypes structs have the C layout of include/spinmc.h (sizes and
+    field offsets as gcc lays them out)."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    fields = {"spin_lattice_desc": [f for f, _ in sm.LatticeDesc._fields_],
+              "spin_cpm_params": [f if f != "lambda_" else "lambda" for f, _ in sm.CpmParams._fields_]}
+    src = ["#include <stdio.h>", "#include <stddef.h>", '#include "spinmc.h"', "int main(void) {"]
+    for st, fs in fields.items():
+        src.append(f'printf("{st} %zu\\n", sizeof({st}));')
+        for f in fs:
+            src.append(f'printf("{st}.{f} %zu\\n", offsetof({st}, {f}));')
+    src.append("return 0; }")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().splitlines())
+    for st, cls in (("spin_lattice_desc", sm.LatticeDesc), ("spin_cpm_params", sm.CpmParams)):
+        assert int(got[st]) == ctypes.sizeof(cls), st
+        for (f, _), cf in zip(cls._fields_, fields[st]):
+            assert int(got[f"{st}.{cf}"]) == getattr(cls, f).offset, (st, f)

@@ -101,3 +101,79 @@ def test_moment_limbs_sum_exactly_over_two_gloo_ranks():
             assert p.exitcode == 0
         want = [a + b for a, b in zip(*VALUES)]
         assert out[0] == want and out[1] == want
+
+
+def _partition_worker(rank, world, port, out):
+    import numpy as np
+
+    import oracle
+    from paper_2304_01772_gb300 import workloads as wl
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    lats = wl.uneven512(n=24, seed=5, emin=2, emax=5)      # sides 4 .. 32: the oracle runs them at once
+    mine, idx = sdist.rank_lattices(lats, rank, world)
+    # this rank's chains: the lattice word of lattice_id - 1, as the library draws it
+    res = {}
+    for d, gi in zip(mine, idx):
+        assert d["lattice_id"] == gi + 1
+        s = oracle.init_ising(d["L"], 77, d["lattice_id"] - 1).copy()
+        st = oracle.ising_run(s, d["beta"], d["J"], d["h"], 77, d["lattice_id"] - 1, 0, 3)
+        res[gi] = (s.tobytes(), st.tobytes())
+    parts = [None] * world
+    dist.all_gather_object(parts, sdist.partition_by_sites([d["L"] for d in lats], world))
+    gathered = [None] * world
+    dist.all_gather_object(gathered, res)
+    out[rank] = (parts, gathered)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_partitioned_batch_on_two_gloo_ranks_is_the_whole_batch():
+    """Each rank computes the same site-count split independently; the shares
+    cover every lattice once, their loads differ from the mean by less than
+    the largest lattice, and the ranks' chains (lattice word = global index)
+    are the whole batch's chains."""
+    import oracle
+    from paper_2304_01772_gb300 import workloads as wl
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_partition_worker, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(timeout=120)
+            assert p.exitcode == 0
+        res = dict(out)
+    lats = wl.uneven512(n=24, seed=5, emin=2, emax=5)
+    splits, gathered = res[0]                          # the split each rank computed
+    assert splits[0] == splits[1] == res[1][0][0]
+    parts = splits[0]
+    assert sorted(parts[0] + parts[1]) == list(range(len(lats)))
+    loads = [sum(lats[i]["L"] ** 2 for i in p) for p in parts]
+    assert max(loads) - sum(loads) / 2 <= max(d["L"] ** 2 for d in lats)
+    whole = {}
+    for i, d in enumerate(lats):                      # one process, batch index as lattice word
+        s = oracle.init_ising(d["L"], 77, i).copy()
+        st = oracle.ising_run(s, d["beta"], d["J"], d["h"], 77, i, 0, 3)
+        whole[i] = (s.tobytes(), st.tobytes())
+    merged = {**gathered[0], **gathered[1]}
+    assert merged == whole
+
+
+def test_partition_by_sites_balance_and_determinism():
+    from paper_2304_01772_gb300 import workloads as wl
+    lats = wl.uneven512()
+    sizes = [d["L"] for d in lats]
+    total = sum(L * L for L in sizes)
+    for world in (1, 2, 3, 4, 7, 8):
+        parts = sdist.partition_by_sites(sizes, world)
+        assert parts == sdist.partition_by_sites(list(sizes), world)
+        assert sorted(sum(parts, [])) == list(range(len(sizes)))
+        loads = [sum(sizes[i] ** 2 for i in p) for p in parts]
+        assert max(loads) <= total / world + max(L * L for L in sizes)
+    assert sdist.partition_by_sites([4, 6], 3)[2] == []
+    with pytest.raises(ValueError):
+        sdist.partition_by_sites([4], 0)

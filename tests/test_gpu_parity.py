@@ -56,7 +56,8 @@ def test_init_matches_oracle():
 
 @pytest.mark.parametrize("mode,graph,tile,threads", [(0, False, 0, 256), (0, True, 0, 256),
                                                      (0, True, 8, 128), (0, False, 64, 512),
-                                                     (1, False, 0, 256), (1, True, 0, 256)])
+                                                     (1, False, 0, 256), (1, True, 0, 256),
+                                                     (3, True, 0, 512), (3, False, 16, 256)])
 def test_ising_mixed_batch_sweep_by_sweep(mode, graph, tile, threads):
     sim = make_ising(MIXED)
     sim.set_launch(mode, graph, tile, threads)
@@ -111,7 +112,7 @@ def test_launch_forms_bit_identical():
     lats = wl.uneven512(n=40, seed=3, emin=4, emax=9)
     finals = []
     for mode, graph, tile, threads in [(0, True, 0, 256), (0, False, 16, 128), (1, True, 0, 256),
-                                       (0, True, 64, 512)]:
+                                       (0, True, 64, 512), (3, True, 0, 512), (3, False, 0, 256)]:
         sim = make_ising(lats, max_record=16)
         sim.set_launch(mode, graph, tile, threads)
         sim.sweep(9, record=True)
@@ -369,11 +370,11 @@ POTTS_STRIP = [dict(L=L, q=q, beta=b, J=J) for L, q, b, J in [
     (1024, 7, 0.0, 1.0), (512, 6, 4.0, 1.0)]]
 
 
-@pytest.mark.parametrize("tile,threads,graph", [(0, 256, True), (24, 512, False), (8, 256, False),
-                                                (64, 512, True), (1, 256, False)])
-def test_potts_strip_batch(tile, threads, graph):
+@pytest.mark.parametrize("mode,tile,threads,graph", [(0, 0, 256, True), (0, 24, 512, False), (0, 8, 256, False),
+                                                     (0, 64, 512, True), (0, 1, 256, False), (3, 0, 256, True)])
+def test_potts_strip_batch(mode, tile, threads, graph):
     sim = sm.Sim(sm.SPIN_POTTS, POTTS_STRIP, seed=SEED, max_record=8)
-    sim.set_launch(0, graph, tile, threads)
+    sim.set_launch(mode, graph, tile, threads)
     ref = {i: lattice_np(sim, i) for i in range(len(POTTS_STRIP))}
     sim.sweep(1, record=True)
     for i, d in enumerate(POTTS_STRIP):

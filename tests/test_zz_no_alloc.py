@@ -27,7 +27,7 @@ LATS = [dict(L=4, beta=0.3, J=1.0, h=0.0), dict(L=10, beta=0.44, J=-1.0, h=0.1),
 def _descs(lats, offsets):
     arr = (sm.LatticeDesc * len(lats))()
     for i, d in enumerate(lats):
-        arr[i] = sm.LatticeDesc(d["L"], 2, d["beta"], d["J"], d["h"], 0, 0.0, offsets[i])
+        arr[i] = sm.LatticeDesc(d["L"], 2, d["beta"], d["J"], d["h"], 0, 0.0, 0, offsets[i])
     return arr
 
 
@@ -57,10 +57,48 @@ def test_noalloc_matches_context_sweep_over_two_calls():
     assert torch.equal(second_stats, sim.observables(5, 3)[0])
 
 
-def test_noalloc_rejects_lattices_beyond_its_scratch():
-    # 4096^2 int8 alone fills the fixed scratch, so its second buffer cannot fit.
-    lats = [dict(L=4096, beta=0.4, J=1.0, h=0.0)]
+def test_noalloc_rejects_odd_sides():
     spins = torch.zeros(16, dtype=torch.int8, device="cuda")   # never touched: rejected first
-    assert _noalloc(_descs(lats, [0]), 1, spins, 0, 1, None) == -1
     odd = [dict(L=7, beta=0.4, J=1.0, h=0.0)]
     assert _noalloc(_descs(odd, [0]), 1, spins, 0, 1, None) == -1
+
+
+def test_noalloc_near_its_scratch_limit_matches_context_and_oracle():
+    """Three 2048^2 lattices (12 MiB of the 16 MiB scratch with their second
+    buffer) next to small ones: the allocation-free call runs them on the tile
+    kernel, the context on the row-strip kernel; both give the oracle's chain."""
+    import numpy as np
+
+    import oracle
+    lats = [dict(L=2048, beta=0.44, J=1.0, h=0.0), dict(L=32, beta=0.3, J=1.0, h=0.1),
+            dict(L=2048, beta=0.5, J=1.0, h=-0.02), dict(L=10, beta=0.4, J=-1.0, h=0.0),
+            dict(L=2048, beta=0.3, J=0.8, h=0.05)]
+    n = len(lats)
+    sim = sm.Sim(sm.SPIN_ISING, lats, seed=SEED, max_record=8)
+    assert max(o + d["L"] ** 2 for o, d in zip(sim.offsets, lats)) > 12 * 2 ** 20
+    spins = sim.spins.clone()
+    init = {i: sim.lattice(i).cpu().numpy().copy() for i in (0, 1, 3)}
+    desc = _descs(lats, sim.offsets)
+    stats = torch.full((2, n, 2), -7, dtype=torch.int64, device="cuda")
+    assert _noalloc(desc, n, spins, 0, 2, stats) == 0
+    sim.sweep(2, record=True)
+    torch.cuda.synchronize()
+    assert torch.equal(spins, sim.spins)
+    assert torch.equal(stats, sim.observables(0, 2)[0])
+    for i, s0 in init.items():
+        d = lats[i]
+        ref = oracle.ising_run(s0, d["beta"], d["J"], d["h"], SEED, i, 0, 2)
+        L = d["L"]
+        got = spins[sim.offsets[i]:sim.offsets[i] + L * L].view(L, L).cpu().numpy()
+        assert np.array_equal(got, s0), i
+        assert np.array_equal(stats[:, i].cpu().numpy(), ref), i
+
+
+def test_noalloc_rejects_a_span_beyond_its_scratch_and_sides_above_2048():
+    # four 2048^2 lattices pass every per-lattice check, but their span (16 MiB)
+    # plus the descriptors cannot fit in the 16 MiB array
+    lats = [dict(L=2048, beta=0.4, J=1.0, h=0.0)] * 4
+    spins = torch.zeros(16, dtype=torch.int8, device="cuda")   # never touched: rejected first
+    assert _noalloc(_descs(lats, [k * 2048 * 2048 for k in range(4)]), 4, spins, 0, 1, None) == -1
+    big = [dict(L=4096, beta=0.4, J=1.0, h=0.0)]
+    assert _noalloc(_descs(big, [0]), 1, spins, 0, 1, None) == -1
