@@ -25,22 +25,33 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile spin_oracle.c into liboracle.so (plain C, -O2, no fast-math)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+_LIB_SAN = os.path.join(_HERE, "liboracle_san.so")
+# AddressSanitizer + UndefinedBehaviorSanitizer build of the same source: any
+# out-of-bounds access or undefined operation aborts the process.
+_SAN_FLAGS = ["-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
+              "-fno-sanitize-recover=all"]
+
+
+def build(force: bool = False, sanitize: bool = False) -> str:
+    """Compile spin_oracle.c into liboracle.so (plain C, -O2, no fast-math),
+    or with sanitize=True into liboracle_san.so (ASan + UBSan, for the
+    sanitizer tests; loaded instead when SPINMC_ORACLE_SANITIZE=1)."""
+    out = _LIB_SAN if sanitize else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        opt = _SAN_FLAGS if sanitize else ["-O2"]
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math",
+            ["gcc", *opt, "-std=c99", "-fPIC", "-shared", "-fno-fast-math",
              "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
 
 
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            _lib = ctypes.CDLL(build())
+            _lib = ctypes.CDLL(build(sanitize=os.environ.get("SPINMC_ORACLE_SANITIZE") == "1"))
             _declare(_lib)
     return _lib
 

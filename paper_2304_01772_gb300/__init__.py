@@ -17,7 +17,9 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "libspinmc.so")
+# SPINMC_LIBRARY: path of a test build to load instead (libspinmc_check.so,
+# libspinmc_san.so: see build.py); the default is the in-tree libspinmc.so.
+_LIB_PATH = os.environ.get("SPINMC_LIBRARY") or os.path.join(_HERE, "libspinmc.so")
 _lib = None
 _lock = threading.Lock()
 
@@ -124,6 +126,8 @@ def lib():
     with _lock:
         if _lib is None:
             if not os.path.exists(_LIB_PATH):
+                if os.environ.get("SPINMC_LIBRARY"):
+                    raise OSError(f"SPINMC_LIBRARY names a missing library: {_LIB_PATH}")
                 from . import build as _build
                 _build.build()
             L = ctypes.CDLL(_LIB_PATH)
