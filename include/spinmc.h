@@ -298,6 +298,17 @@ int spin_barrier_selftest(int32_t blocks, int32_t missing, int32_t rounds, void 
 int spin_philox_xor(uint64_t seed, uint32_t lattice, uint32_t sweep, uint32_t colour, uint32_t g0,
                     uint32_t n_groups, uint32_t *out, void *stream);
 
+/* Device-side bounds checks (not in the paper: a debugging aid).  The
+ * library built with -DSPIN_CHECK (libspinmc_check.so, build variant "check")
+ * checks every work-list entry, shared-memory ring and queue index and table
+ * address in its sweep kernels before use; a failed check records a code
+ * (1xx: Ising kernels, 12x: Potts, 13x: CPM, 14x: statistics) in a device
+ * word, the access is skipped and nothing traps.  spin_check_status
+ * synchronises the device, writes the first recorded code (0: none) to
+ * *first_code, clears the words, and returns 1 in a check build, 0 in other
+ * builds (whose kernels have no checks), or a negative error code.          */
+int spin_check_status(uint32_t *first_code);
+
 uint32_t spin_sweep_index(const spin_ctx *ctx);
 int32_t spin_gpu_launches(const spin_ctx *ctx); /* kernels launched by the last spin_sweep */
 const char *spin_last_error(const spin_ctx *ctx);

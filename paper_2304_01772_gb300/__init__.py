@@ -80,6 +80,7 @@ _SIGS = {
     "spin_last_error": (ctypes.c_char_p, [_vp]),
     "spin_destroy": (None, [_vp]),
     "spin_version": (_i32, []),
+    "spin_check_status": (_i32, [ctypes.POINTER(ctypes.c_uint32)]),
     "spin_philox_xor": (_i32, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                ctypes.c_uint32, _vp, _vp]),
     "spin_ising_sweep_noalloc": (_i32, [ctypes.c_uint64, _i32, ctypes.POINTER(LatticeDesc), _vp, ctypes.c_uint32,
@@ -424,6 +425,14 @@ def barrier_selftest(blocks, missing=0, rounds=1, stream=None):
     """Run the bounded grid barrier of the CPM persistent form as a self-test;
     returns SPIN_OK (0) or SPIN_ETIMEOUT (-4) (see spin_barrier_selftest)."""
     return int(lib().spin_barrier_selftest(int(blocks), int(missing), int(rounds), _stream(stream)))
+
+
+def check_status():
+    """(built_with_checks, first recorded check code or 0); see spin_check_status."""
+    code = ctypes.c_uint32(0)
+    rc = lib().spin_check_status(ctypes.byref(code))
+    _check(rc, None, "spin_check_status")
+    return bool(rc == 1), int(code.value)
 
 
 def philox_xor(seed, lattice, sweep, colour, g0, n_groups, out=None, stream=None):

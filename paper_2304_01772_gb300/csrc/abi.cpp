@@ -6,6 +6,7 @@
 // autotuner.  Every step of the Monte Carlo path runs in the kernels of the
 // .cu files; this file only plans and launches them.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -48,6 +49,15 @@ namespace {
 constexpr int kMaxItemBytes = 65536;   // bounds the per-thread packed counters
 constexpr int kWholeMaxBytes = 16384;  // lattices up to 128 x 128 are one item
 constexpr int kMaxL = 32768;
+
+// NVTX range around one ABI call (visible in Nsight Systems timelines; no
+// cost beyond two calls when no tool is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // The lattice word of a lattice's Philox counters: lattice_id - 1 when the
 // caller gives one, else the lattice's index in this batch.
@@ -597,7 +607,7 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                 if (ctx->model == SPIN_ISING) {
                     IsingSweepArgs a{(r.strip ? ctx->d_strip : ctx->d_items) + r.first, r.count, ctx->d_lats,
                                      ctx->d_tabs, static_cast<const int8_t *>(src), static_cast<int8_t *>(dst),
-                                     ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, philox_keys(ctx->k0, ctx->k1)};
+                                     ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, philox_keys(ctx->k0, ctx->k1), ctx->n_lat};
                     if (r.strip)
                         CK(launch_ising_strip(a, std::min((r.count + ctx->strip_warps - 1) / ctx->strip_warps,
                                                           ctx->sm_count * ctx->per_sm_strip),
@@ -608,14 +618,14 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                     PottsStripArgs a{ctx->d_strip + r.first, r.count, ctx->d_lats, ctx->d_tabs,
                                      static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst),
                                      ctx->d_state, ctx->st.delta, ctx->st.cur, w, ctx->strip_chunks,
-                                     philox_keys(ctx->k0, ctx->k1)};
+                                     philox_keys(ctx->k0, ctx->k1), ctx->n_lat};
                     CK(launch_potts_strip(a, std::min((r.count + ctx->strip_warps - 1) / ctx->strip_warps,
                                                       ctx->sm_count * ctx->per_sm_strip),
                                           ctx->strip_warps, ctx->strip_qbits, s));
                 } else {
                     PottsSweepArgs a{ctx->d_items + r.first, r.count, ctx->d_lats, ctx->d_tabs,
                                      static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst),
-                                     ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, w};
+                                     ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, w, ctx->n_lat};
                     CK(launch_potts_fused(a, std::min(r.count, ctx->grid), ctx->threads, ctx->smem, s));
                 }
                 if (timed) prof_end(ctx, s);
@@ -641,12 +651,12 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                 IsingSweepArgs a{ctx->d_items, ctx->n_items, ctx->d_lats, ctx->d_tabs,
                                  static_cast<const int8_t *>(src), static_cast<int8_t *>(dst),
                                  ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta,
-                                 philox_keys(ctx->k0, ctx->k1)};
+                                 philox_keys(ctx->k0, ctx->k1), ctx->n_lat};
                 CK(launch_ising_fused(a, ctx->grid, ctx->threads, ctx->smem, ts));
             } else {
                 PottsSweepArgs a{ctx->d_items, ctx->n_items, ctx->d_lats, ctx->d_tabs,
                                  static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst),
-                                 ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, w};
+                                 ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta, w, ctx->n_lat};
                 CK(launch_potts_fused(a, ctx->grid, ctx->threads, ctx->smem, ts));
             }
             if (timed) prof_end(ctx, ts);
@@ -658,13 +668,13 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                 IsingSweepArgs a{ctx->d_strip, ctx->n_strip, ctx->d_lats, ctx->d_tabs,
                                  static_cast<const int8_t *>(src), static_cast<int8_t *>(dst),
                                  ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta,
-                                 philox_keys(ctx->k0, ctx->k1)};
+                                 philox_keys(ctx->k0, ctx->k1), ctx->n_lat};
                 CK(launch_ising_strip(a, ctx->strip_grid, ctx->strip_warps, s));
             } else {
                 PottsStripArgs a{ctx->d_strip, ctx->n_strip, ctx->d_lats, ctx->d_tabs,
                                  static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst),
                                  ctx->d_state, ctx->st.delta, ctx->st.cur, w, ctx->strip_chunks,
-                                 philox_keys(ctx->k0, ctx->k1)};
+                                 philox_keys(ctx->k0, ctx->k1), ctx->n_lat};
                 CK(launch_potts_strip(a, ctx->strip_grid, ctx->strip_warps, ctx->strip_qbits, s));
             }
             if (timed) prof_end(ctx, s);
@@ -899,6 +909,7 @@ void spin_destroy(spin_ctx *ctx) {
 int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
               const spin_lattice_desc *lat, const spin_cpm_params *cpm, void *d_spins,
               int32_t init_mode, int32_t max_record_sweeps, void *stream) {
+    Range range_("spin_init");
     if (!out) return SPIN_EINVAL;
     *out = nullptr;
     spin_ctx *ctx = new spin_ctx();
@@ -1073,6 +1084,7 @@ int spin_init(spin_ctx **out, int32_t model, uint64_t seed, int32_t n_lattices,
 }
 
 int spin_sweep(spin_ctx *ctx, int32_t n_sweeps, int32_t record, void *stream) {
+    Range range_("spin_sweep");
     if (!ctx) return SPIN_EINVAL;
     if (n_sweeps < 0) return fail(ctx, SPIN_EINVAL, "negative sweep count");
     if ((uint64_t)ctx->t + (uint64_t)n_sweeps >= 0xFFFFFFFEull)
@@ -1088,6 +1100,7 @@ int spin_sweep(spin_ctx *ctx, int32_t n_sweeps, int32_t record, void *stream) {
 
 int spin_observables(spin_ctx *ctx, int64_t first, int32_t n, int64_t *stats, float *E, float *M,
                      void *stream) {
+    Range range_("spin_observables");
     if (!ctx) return SPIN_EINVAL;
     int rc = check_records(ctx, first, n);
     if (rc) return rc;
@@ -1133,6 +1146,7 @@ int spin_current_stats(spin_ctx *ctx, int64_t *stats, void *stream) {
 }
 
 int spin_moments(spin_ctx *ctx, int64_t first, int32_t n, int64_t *moments, void *stream) {
+    Range range_("spin_moments");
     if (!ctx || !moments) return SPIN_EINVAL;
     int rc = check_records(ctx, first, n);
     if (rc) return rc;
@@ -1157,6 +1171,7 @@ int spin_moments(spin_ctx *ctx, int64_t first, int32_t n, int64_t *moments, void
 
 int spin_grad(spin_ctx *ctx, int64_t first, int32_t n, int32_t observable, int32_t pool, double *out,
               void *stream) {
+    Range range_("spin_grad");
     if (!ctx || !out) return SPIN_EINVAL;
     if (ctx->model == SPIN_POTTS) return fail(ctx, SPIN_EINVAL, "no gradient for the Potts model");
     if (ctx->model == SPIN_ISING && (observable < 0 || observable > 1))
@@ -1346,6 +1361,7 @@ int spin_get_launch(const spin_ctx *ctx, int32_t out[4]) {
 }
 
 int spin_load_spins(spin_ctx *ctx, const void *host, void *stream) {
+    Range range_("spin_load_spins");
     if (!ctx || !host) return SPIN_EINVAL;
     char *base = static_cast<char *>(ctx->spins);
     cudaStream_t s = S(stream);
@@ -1383,6 +1399,7 @@ static int packed_ready(spin_ctx *ctx) {
 }
 
 int spin_load_spins_packed(spin_ctx *ctx, const uint32_t *host, void *stream) {
+    Range range_("spin_load_spins_packed");
     if (!ctx || !host) return SPIN_EINVAL;
     int rc = packed_ready(ctx);
     if (rc) return rc;
@@ -1402,6 +1419,7 @@ int spin_load_spins_packed(spin_ctx *ctx, const uint32_t *host, void *stream) {
 }
 
 int spin_store_spins_packed(spin_ctx *ctx, uint32_t *host, void *stream) {
+    Range range_("spin_store_spins_packed");
     if (!ctx || !host) return SPIN_EINVAL;
     int rc = packed_ready(ctx);
     if (rc) return rc;
@@ -1414,6 +1432,7 @@ int spin_store_spins_packed(spin_ctx *ctx, uint32_t *host, void *stream) {
 }
 
 int spin_store_spins(spin_ctx *ctx, void *host, void *stream) {
+    Range range_("spin_store_spins");
     if (!ctx || !host) return SPIN_EINVAL;
     const size_t bytes = ctx->model == SPIN_CPM ? (size_t)ctx->lat[0].L * ctx->lat[0].L * 4
                                                 : ctx->span_elems * ctx->elem;
@@ -1432,6 +1451,7 @@ struct CkptHeader {
 };
 
 int spin_checkpoint(spin_ctx *ctx, void *host_blob, size_t *size, void *stream) {
+    Range range_("spin_checkpoint");
     if (!ctx || !size) return SPIN_EINVAL;
     const size_t spin_bytes = ctx->model == SPIN_CPM ? (size_t)ctx->lat[0].L * ctx->lat[0].L * 4
                                                      : ctx->span_elems * ctx->elem;
@@ -1459,6 +1479,7 @@ int spin_checkpoint(spin_ctx *ctx, void *host_blob, size_t *size, void *stream) 
 }
 
 int spin_restore(spin_ctx *ctx, const void *host_blob, size_t size, void *stream) {
+    Range range_("spin_restore");
     if (!ctx || !host_blob || size < sizeof(CkptHeader)) return SPIN_EINVAL;
     CkptHeader h;
     std::memcpy(&h, host_blob, sizeof h);
@@ -1489,6 +1510,7 @@ int spin_restore(spin_ctx *ctx, const void *host_blob, size_t size, void *stream
 }
 
 int spin_autotune(spin_ctx *ctx, int32_t sweeps_per_trial, void *stream) {
+    Range range_("spin_autotune");
     if (!ctx) return SPIN_EINVAL;
     if (ctx->model == SPIN_CPM) return SPIN_OK;
     if (sweeps_per_trial < 2) sweeps_per_trial = 2;
@@ -1677,6 +1699,7 @@ int spin_cpm_batch_init(uint64_t seed, int32_t n_lattices, int32_t L, const spin
 int spin_cpm_batch_run(uint64_t seed, int32_t n_lattices, int32_t L, const spin_cpm_params *cpm, int32_t *ids,
                        const uint8_t *types, int32_t *areas, uint32_t first_step, int32_t n_steps, int64_t *stats,
                        void *workspace, void *stream) {
+    Range range_("spin_cpm_batch_run");
     if (cpm_batch_check(n_lattices, L, cpm) || !ids || !types || !areas || n_steps < 1 || !aligned16(workspace))
         return SPIN_EINVAL;
     if ((uint64_t)first_step + (uint64_t)n_steps >= 0xFFFFFFFEull) return SPIN_EINVAL;
@@ -1787,6 +1810,7 @@ int spin_dmc_step(uint64_t seed, int32_t n_lattices, int32_t L, float beta, floa
                   uint32_t first_sweep, int32_t n_sweeps, float *spins, float *J, float *m, float *v,
                   const float *target, double *loss, int32_t step, float lr, float beta1, float beta2, float eps,
                   void *stream) {
+    Range range_("spin_dmc_step");
     if (!dmc_geom_ok(n_lattices, L, n_sweeps) || !dmc_params_ok(beta, h, alpha)) return SPIN_EINVAL;
     if (n_sweeps > spin_dmc_step_max_sweeps(L) || step < 1 || !std::isfinite(lr)) return SPIN_EINVAL;
     if (!aligned16(spins) || !aligned16(J) || !aligned16(m) || !aligned16(v) || !aligned16(target) || !loss)
@@ -1829,6 +1853,22 @@ int spin_dmc_spin_iter(uint64_t seed, int32_t n_lattices, int32_t L, float beta,
     DmcSpinIterArgs a{n_lattices, L, n_sweeps, first_sweep, beta, h, alpha, eta, (uint32_t)seed,
                       (uint32_t)(seed >> 32), spins, J, energy};
     return launch_dmc_spin_iter(a, S(stream)) == cudaSuccess ? SPIN_OK : SPIN_ECUDA;
+}
+
+int spin_check_status(uint32_t *first_code) {
+    if (!first_code) return SPIN_EINVAL;
+    *first_code = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return SPIN_ECUDA;
+    for (auto fn : {check_word_ising, check_word_potts, check_word_cpm, check_word_stats}) {
+        unsigned w = 0;
+        if (fn(&w, true) != cudaSuccess) return SPIN_ECUDA;
+        if (w && !*first_code) *first_code = w;
+    }
+#ifdef SPIN_CHECK
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 int spin_philox_xor(uint64_t seed, uint32_t lattice, uint32_t sweep, uint32_t colour, uint32_t g0,

@@ -63,6 +63,42 @@ struct StatsBufs {
 };
 
 #ifdef __CUDACC__
+// ------------------------------------------------------------------ SPIN_CHECK
+// Builds with -DSPIN_CHECK (libspinmc_check.so) check work-list entries,
+// shared-memory indices and table addresses before they are used.  A failed
+// check records its code in this translation unit's check word (the first
+// failure wins); the caller skips the access and the kernel carries on, so
+// nothing traps.  spin_check_status reads and clears the words.  Other builds
+// compile every check to `true`.
+#ifdef SPIN_CHECK
+static __device__ unsigned int g_check_word = 0u;
+__device__ __forceinline__ bool spin_ck(bool ok, unsigned code) {
+    if (!ok) atomicCAS(&g_check_word, 0u, code);
+    return ok;
+}
+#define SPIN_CK(cond, code) spin_ck((cond), (code))
+#define SPIN_CHECK_ACCESSOR(fn)                                                              \
+    cudaError_t fn(unsigned *word, bool clear) {                                             \
+        cudaError_t e = cudaMemcpyFromSymbol(word, g_check_word, sizeof(unsigned));          \
+        const unsigned zero = 0u;                                                            \
+        if (!e && clear) e = cudaMemcpyToSymbol(g_check_word, &zero, sizeof(unsigned));      \
+        return e;                                                                            \
+    }
+#else
+#define SPIN_CK(cond, code) true
+#define SPIN_CHECK_ACCESSOR(fn)                \
+    cudaError_t fn(unsigned *word, bool) {     \
+        *word = 0u;                            \
+        return cudaSuccess;                    \
+    }
+#endif
+// Dynamic shared memory of the running launch, in bytes.
+__device__ __forceinline__ unsigned dynamic_smem_bytes() {
+    unsigned v;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
+
 // ---------------------------------------------------------------- Philox4x32-10
 // Salmon, Moraes, Dror, Shaw, SC'11.  Multipliers 0xD2511F53 / 0xCD9E8D57,
 // Weyl key increments 0x9E3779B9 / 0xBB67AE85, ten rounds.
@@ -109,6 +145,7 @@ struct IsingSweepArgs {
     const DevState *state;
     int64_t *delta;   // [n_lat][2]
     PhiloxKeys rk;
+    int n_lat;        // entries of lats (work-list checks of SPIN_CHECK builds)
 };
 
 cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, size_t smem,
@@ -165,6 +202,12 @@ cudaError_t launch_init_random(void *spins, int model, const LatDev *lats, int n
 // g in [g0, g0 + n), into *out (zeroed first).
 cudaError_t launch_philox_xor(uint32_t g0, uint32_t n, uint32_t lat, uint32_t t, uint32_t c,
                               uint32_t k0, uint32_t k1, uint32_t *out, cudaStream_t s);
+// Check words of the translation units with SPIN_CHECK sites (always 0 in
+// other builds); clear = reset after reading.
+cudaError_t check_word_ising(unsigned *word, bool clear);
+cudaError_t check_word_potts(unsigned *word, bool clear);
+cudaError_t check_word_cpm(unsigned *word, bool clear);
+cudaError_t check_word_stats(unsigned *word, bool clear);
 
 struct PottsSweepArgs {
     const Item *items;
@@ -177,6 +220,7 @@ struct PottsSweepArgs {
     const DevState *state;
     int64_t *delta;   // [n_lat][width]
     int width;
+    int n_lat;        // entries of lats (work-list checks of SPIN_CHECK builds)
 };
 cudaError_t launch_potts_fused(const PottsSweepArgs &a, int grid, int threads, size_t smem,
                                cudaStream_t s);
@@ -196,6 +240,7 @@ struct PottsStripArgs {
     int width;
     int ring_chunks;      // 16-byte chunks per ring slot: L / 16 of the widest strip lattice
     PhiloxKeys rk;
+    int n_lat;            // entries of lats (work-list checks of SPIN_CHECK builds)
 };
 // qbits: 2 for q <= 4, 3 for q <= 8.
 cudaError_t launch_potts_strip(const PottsStripArgs &a, int grid, int warps, int qbits, cudaStream_t s);

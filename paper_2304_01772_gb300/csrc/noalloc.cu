@@ -161,7 +161,7 @@ extern "C" int spin_ising_sweep_noalloc(uint64_t seed, int32_t n_lattices,
                                        d_delta, c, s));
         if (n_items) {
             IsingSweepArgs a{d_items, n_items, d_lats, d_tabs, src, dst, k0, k1, state, d_delta,
-                             philox_keys(k0, k1)};
+                             philox_keys(k0, k1), n_lattices};
             NA_CK(launch_ising_fused(a, grid, 256, smem, s));
         }
         NA_CK(launch_finalize(state, st, d_stats ? 1 : 0, s));

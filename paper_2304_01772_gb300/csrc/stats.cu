@@ -169,7 +169,8 @@ __global__ void stats_cpm_kernel(const int32_t *ids, int L, const uint8_t *type,
 }
 
 __global__ void __launch_bounds__(1024) finalize_kernel(DevState *state, StatsBufs st, int record) {
-    const long long slot = (record && st.cap > 0) ? state->n_rec % st.cap : -1;
+    long long slot = (record && st.cap > 0) ? state->n_rec % st.cap : -1;
+    if (!SPIN_CK(slot < (long long)st.cap && state->n_rec >= 0, 141)) slot = -1;
     const int n = st.n_lat * st.width;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
         const int64_t v = st.cur[k] + st.delta[k];
@@ -641,5 +642,7 @@ cudaError_t launch_pack_spins(const int8_t *spins, uint32_t *words, size_t n_wor
     pack_spins_kernel<<<grid, 256, 0, s>>>(spins, words, lats);
     return cudaGetLastError();
 }
+
+SPIN_CHECK_ACCESSOR(check_word_stats)
 
 }  // namespace spinmc

@@ -109,10 +109,14 @@ __device__ void cpm_substep_body(const CpmArgs &a, int c, uint32_t t, CpmShared 
             const int sg0 = a.ids[y * L + x0], sg1 = a.ids[y * L + x1];
             const int sp0 = a.ids[yn0 * L + xn0], sp1 = a.ids[yn1 * L + xn1];
             const unsigned nc = (unsigned)a.n_cells;
-            if (live && sp0 != sg0 && (unsigned)sg0 <= nc && (unsigned)sp0 <= nc)
-                queue[atomicAdd(&qn, 1)] = make_int4((y << 16) | x0, sg0, sp0, (int)r.x);
-            if (live && sp1 != sg1 && (unsigned)sg1 <= nc && (unsigned)sp1 <= nc)
-                queue[atomicAdd(&qn, 1)] = make_int4((y << 16) | x1, sg1, sp1, (int)r.z);
+            if (live && sp0 != sg0 && (unsigned)sg0 <= nc && (unsigned)sp0 <= nc) {
+                const int qi = atomicAdd(&qn, 1);
+                if (SPIN_CK(qi < kCpmQueue, 131)) queue[qi] = make_int4((y << 16) | x0, sg0, sp0, (int)r.x);
+            }
+            if (live && sp1 != sg1 && (unsigned)sg1 <= nc && (unsigned)sp1 <= nc) {
+                const int qi = atomicAdd(&qn, 1);
+                if (SPIN_CK(qi < kCpmQueue, 131)) queue[qi] = make_int4((y << 16) | x1, sg1, sp1, (int)r.z);
+            }
         }
         __syncthreads();
         const int n = qn;
@@ -458,8 +462,11 @@ __global__ void __launch_bounds__(kCpmBatchThreads) cpm_batch_kernel(CpmBatchArg
                             const int nbi = (int)((j ? r.w : r.y) >> 29);
                             const int sg = ids[y * L + x];
                             const int sp = ids[wrapb<POW2>(y + kMooreDy[nbi], L) * L + wrapb<POW2>(x + kMooreDx[nbi], L)];
-                            if (sp != sg && (unsigned)sg <= ncu && (unsigned)sp <= ncu)
-                                queue[atomicAdd(&qn, 1)] = make_int4((y << 16) | x, sg, sp, (int)(j ? r.z : r.x));
+                            if (sp != sg && (unsigned)sg <= ncu && (unsigned)sp <= ncu) {
+                                const int qi = atomicAdd(&qn, 1);
+                                if (SPIN_CK(qi < 2 * kCpmBatchThreads, 132))
+                                    queue[qi] = make_int4((y << 16) | x, sg, sp, (int)(j ? r.z : r.x));
+                            }
                         }
                     }
                     __syncthreads();
@@ -684,5 +691,7 @@ cudaError_t launch_cpm_types(uint8_t *type, int n_cells, uint32_t lat, uint32_t 
     cpm_types_kernel<<<(n_cells + 256) / 256, 256, 0, s>>>(type, n_cells, lat, k0, k1);
     return cudaGetLastError();
 }
+
+SPIN_CHECK_ACCESSOR(check_word_cpm)
 
 }  // namespace spinmc

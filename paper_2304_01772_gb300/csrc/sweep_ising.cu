@@ -804,6 +804,8 @@ __device__ __forceinline__ void update(Words<NW> &act, const Words<NW> &oth, uin
         // the horizontal neighbours are oth (one side) and this shifted copy (other side)
         const uint32_t H = prmt(oth.w[i], nb, selH);
         const uint32_t key = up.w[i] + dn.w[i] + oth.w[i] + H + act.w[i] * 5u;
+        // every key byte is 8 (d + 5 c) <= 72: an entry of the table's first 80 bytes
+        SPIN_CK((key & 0x07070707u) == 0u && ((key + 0x37373737u) & 0x80808080u) == 0u, 104);
         const uint4 r = philox_from_prefix(g + (uint32_t)i, P, rk);
         uint32_t w = act.w[i];
         accept_site(w, acc, r.x, lds_entry(prmt(key, stab, 0x7650u)), 0x00000008u);
@@ -886,6 +888,8 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
         for (int j = 0; j < nc; ++j) {
             const int c = lane + 32 * j;
             const int we = (NW * c + eoff) & (nw - 1);
+            // the chunk and the edge word lie inside the half row
+            if (!SPIN_CK(4 * NW * (c + 1) <= half && we >= 0 && we < nw, 103)) continue;
             const uint32_t eA = reinterpret_cast<const uint32_t *>(q2 + ho)[we];
             Words<NW> act = ld_words<NW>(q2 + hp, c);
             const Words<NW> oth = ld_words<NW>(q2 + ho, c);
@@ -934,7 +938,13 @@ __global__ void __launch_bounds__(WARPS * 32) ising_strip_kernel(IsingSweepArgs 
     const int gw = blockIdx.x * WARPS + warp, nw = gridDim.x * WARPS;
     for (int it = gw; it < a.n_items; it += nw) {
         const Item w = a.items[it];
+        if (!SPIN_CK((unsigned)w.lat < (unsigned)a.n_lat, 101)) continue;
         const LatDev ld = a.lats[w.lat];
+        // the ring holds five rows of at most 2048 bytes
+        if (!SPIN_CK((ld.L == 512 || ld.L == 1024 || ld.L == 2048) && w.r0 >= 0 && w.nrows >= 1 &&
+                         w.r0 + w.nrows <= ld.L && 5u * (unsigned)ld.L <= (unsigned)(kRing * kRowChunks * 16),
+                     102))
+            continue;
         if (lane < kTabStride) {
             const TabEntry e = a.tabs[w.lat * kTabStride + lane];
             tabs[warp][0][lane] = e;
@@ -1008,10 +1018,17 @@ __global__ void __launch_bounds__(THREADS) ising_fused_kernel(IsingSweepArgs a) 
     const uint32_t tb_halo = (uint32_t)__cvta_generic_to_shared(stab[1]);
     for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
         const Item w = a.items[it];
+        if (!SPIN_CK((unsigned)w.lat < (unsigned)a.n_lat, 111)) continue;   // the whole block skips alike
         const LatDev ld = a.lats[w.lat];
         const int L = ld.L, Lv = L >> 4;
         const int halo = w.whole ? 0 : 2;
         const int nload = w.nrows + 2 * halo;
+        // rows in range, and the rows plus halo fit the launch's shared memory
+        if (!SPIN_CK(L >= 16 && (L & 15) == 0 && w.r0 >= 0 && w.nrows >= 1 && w.r0 + w.nrows <= L &&
+                         (!w.whole || (w.r0 == 0 && w.nrows == L)) &&
+                         (unsigned)nload * (unsigned)L <= dynamic_smem_bytes(),
+                     112))
+            continue;
         const uint4 *S = reinterpret_cast<const uint4 *>(a.src + ld.offset);
         uint4 *Dg = reinterpret_cast<uint4 *>(a.dst + ld.offset);
         // chunk v = threadIdx.x + k THREADS of a row range is (row i, column j);
@@ -1105,6 +1122,8 @@ __global__ void __launch_bounds__(THREADS) ising_resident_kernel(ResidentArgs a)
     const int lat = blockIdx.x;
     const LatDev ld = a.lats[lat];
     const int L = ld.L, Lv = L >> 4;
+    // the whole lattice fits the launch's shared memory (one block per lattice)
+    if (!SPIN_CK(L >= 16 && (L & 15) == 0 && (unsigned)(L * L) <= dynamic_smem_bytes(), 113)) return;
     uint4 *sm4 = reinterpret_cast<uint4 *>(sm);
     const uint32_t *sm32 = reinterpret_cast<const uint32_t *>(sm);
     uint4 *G = reinterpret_cast<uint4 *>(a.spins + ld.offset);
@@ -1359,5 +1378,7 @@ cudaError_t launch_init_random(void *spins, int model, const LatDev *lats, int n
     init_random_kernel<<<grid, 256, 0, s>>>(spins, model, lats, k0, k1);
     return cudaGetLastError();
 }
+
+SPIN_CHECK_ACCESSOR(check_word_ising)
 
 }  // namespace spinmc

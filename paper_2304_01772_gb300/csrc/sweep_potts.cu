@@ -138,12 +138,17 @@ __global__ void __launch_bounds__(THREADS) potts_fused_kernel(PottsSweepArgs a) 
     const uint32_t t = a.state->t;
     for (int it = blockIdx.x; it < a.n_items; it += gridDim.x) {
         const Item w = a.items[it];
+        if (!SPIN_CK((unsigned)w.lat < (unsigned)a.n_lat, 123)) continue;   // the whole block skips alike
         const LatDev ld = a.lats[w.lat];
         const int L = ld.L, Lv = L >> 4;
         const uint32_t q = (uint32_t)ld.q;
         const bool small_q = q <= 8;
         const int halo = w.whole ? 0 : 2;
         const int nload = w.nrows + 2 * halo;
+        if (!SPIN_CK(L >= 16 && (L & 15) == 0 && w.r0 >= 0 && w.nrows >= 1 && w.r0 + w.nrows <= L &&
+                         (unsigned)nload * (unsigned)L <= dynamic_smem_bytes(),
+                     124))
+            continue;
         const uint4 *S = reinterpret_cast<const uint4 *>(a.src + ld.offset);
         uint4 *Dg = reinterpret_cast<uint4 *>(a.dst + ld.offset);
         for (int v = threadIdx.x; v < nload * Lv; v += THREADS) {
@@ -410,7 +415,13 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) potts_strip_kernel(Pot
     uint32_t *tot = tots[warp];
     for (int it = gw; it < a.n_items; it += nw) {
         const Item w = a.items[it];
+        if (!SPIN_CK((unsigned)w.lat < (unsigned)a.n_lat, 121)) continue;
         const LatDev ld = a.lats[w.lat];
+        // a ring slot holds a row (ring_chunks chunks of 16 bytes), states fit QB bits
+        if (!SPIN_CK((ld.L == 512 || ld.L == 1024 || ld.L == 2048) && (ld.L >> 4) <= a.ring_chunks &&
+                         w.r0 >= 0 && w.nrows >= 1 && w.r0 + w.nrows <= ld.L && ld.q >= 2 && ld.q <= (1 << QB),
+                     122))
+            continue;
         if (lane < kTabStride) {
             const TabEntry e = a.tabs[w.lat * kTabStride + lane];
             tabs[warp][0][lane] = e;
@@ -666,5 +677,7 @@ cudaError_t launch_potts_strip(const PottsStripArgs &a, int grid, int warps, int
         return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
+
+SPIN_CHECK_ACCESSOR(check_word_potts)
 
 }  // namespace spinmc

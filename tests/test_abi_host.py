@@ -172,3 +172,12 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert int(got[st]) == ctypes.sizeof(cls), st
         for (f, _), cf in zip(cls._fields_, fields[st]):
             assert int(got[f"{st}.{cf}"]) == getattr(cls, f).offset, (st, f)
+
+
+def test_bounds_checked_variant_builds_and_exports_the_abi():
+    """The SPIN_CHECK variant (kernels with no-trap bounds checks) builds and
+    exports every declared symbol, spin_check_status included."""
+    from paper_2304_01772_gb300 import build
+    lib = ctypes.CDLL(build.build(variant="check"))
+    for n in declared_symbols():
+        assert hasattr(lib, n), n
