@@ -63,6 +63,55 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 __device__ __forceinline__ int wrap_row(int y, int L) { return y < 0 ? y + L : (y >= L ? y - L : y); }
 
+// ---- the split form (Ising and Potts strip kernels): a ring row is stored
+// as its two colour-compressed halves, sites of even x then sites of odd x.
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// NW consecutive 32-bit words of a half row (one lane's chunk).
+template <int NW>
+struct Words {
+    uint32_t w[NW];
+};
+
+template <int NW>
+__device__ __forceinline__ Words<NW> ld_words(const unsigned char *half, int c) {
+    Words<NW> r;
+    if constexpr (NW == 4) {
+        const uint4 v = reinterpret_cast<const uint4 *>(half)[c];
+        r.w[0] = v.x, r.w[1] = v.y, r.w[2] = v.z, r.w[3] = v.w;
+    } else {
+        const uint2 v = reinterpret_cast<const uint2 *>(half)[c];
+        r.w[0] = v.x, r.w[1] = v.y;
+    }
+    return r;
+}
+
+template <int NW>
+__device__ __forceinline__ void st_words(unsigned char *half, int c, const Words<NW> &r) {
+    if constexpr (NW == 4)
+        reinterpret_cast<uint4 *>(half)[c] = make_uint4(r.w[0], r.w[1], r.w[2], r.w[3]);
+    else
+        reinterpret_cast<uint2 *>(half)[c] = make_uint2(r.w[0], r.w[1]);
+}
+
+// Row y of an L x L byte lattice S -> dst by cp.async (16 bytes per lane and copy).
+__device__ __forceinline__ void issue_raw(unsigned char *dst, const uint4 *S, int y, int L, int lane) {
+    const uint4 *src = S + (size_t)y * (L >> 4);
+    for (int j = lane; j < (L >> 4); j += 32) cp_async16(reinterpret_cast<uint4 *>(dst) + j, src + j);
+}
+
+// One 8-byte table entry at a shared-memory address.
+__device__ __forceinline__ uint2 lds_u2(uint32_t addr) {
+    uint2 v;
+    asm("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+    return v;
+}
+
 inline size_t strip_ring_bytes(int warps) { return sizeof(uint4) * (size_t)warps * kRing * kRowChunks; }
 
 }  // namespace spinmc

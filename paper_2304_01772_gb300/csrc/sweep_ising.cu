@@ -739,38 +739,6 @@ __device__ __forceinline__ void drain_acc(int &acc, int &dm, int &db) {
 // slot where the raw row s + 2 arrives by cp.async while step s computes.
 namespace split {
 
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
-
-template <int NW>
-struct Words {
-    uint32_t w[NW];
-};
-
-template <int NW>
-__device__ __forceinline__ Words<NW> ld_words(const unsigned char *half, int c) {
-    Words<NW> r;
-    if constexpr (NW == 4) {
-        const uint4 v = reinterpret_cast<const uint4 *>(half)[c];
-        r.w[0] = v.x, r.w[1] = v.y, r.w[2] = v.z, r.w[3] = v.w;
-    } else {
-        const uint2 v = reinterpret_cast<const uint2 *>(half)[c];
-        r.w[0] = v.x, r.w[1] = v.y;
-    }
-    return r;
-}
-
-template <int NW>
-__device__ __forceinline__ void st_words(unsigned char *half, int c, const Words<NW> &r) {
-    if constexpr (NW == 4)
-        reinterpret_cast<uint4 *>(half)[c] = make_uint4(r.w[0], r.w[1], r.w[2], r.w[3]);
-    else
-        reinterpret_cast<uint2 *>(half)[c] = make_uint2(r.w[0], r.w[1]);
-}
-
 // Raw row (L int8 spins, +1 = 0x01, -1 = 0xFF) at src -> split x8 row at dst
 // (dst != src), one 16-byte raw chunk per lane at a time.
 __device__ __forceinline__ void split_row(const unsigned char *src, unsigned char *dst, int L, int lane) {
@@ -783,11 +751,6 @@ __device__ __forceinline__ void split_row(const unsigned char *src, unsigned cha
         E[k] = make_uint2(__byte_perm(a, b, 0x6420), __byte_perm(c, d, 0x6420));
         O[k] = make_uint2(__byte_perm(a, b, 0x7531), __byte_perm(c, d, 0x7531));
     }
-}
-
-__device__ __forceinline__ void issue_raw(unsigned char *dst, const uint4 *S, int y, int L, int lane) {
-    const uint4 *src = S + (size_t)y * (L >> 4);
-    for (int j = lane; j < (L >> 4); j += 32) cp_async16(reinterpret_cast<uint4 *>(dst) + j, src + j);
 }
 
 // Metropolis update of the active words `act` given the other half's words

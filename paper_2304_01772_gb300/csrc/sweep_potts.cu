@@ -194,40 +194,34 @@ __global__ void __launch_bounds__(THREADS) potts_fused_kernel(PottsSweepArgs a) 
 }
 
 // ------------------------------------------------------------ strip kernel
-// Lattices with q <= 8 and L = 512, 1024 or 2048, one warp per block of full
-// rows, walked as in the Ising strip kernel: at step s colour 0 on row s and
-// colour 1 on row s - 1, rows s-2 .. s+2 in a five-slot shared-memory ring
-// (row s + 2 arriving by cp.async), rows -1 and R a recomputed colour-0 halo.
+// Lattices with q <= 8 and L = 512, 1024 or 2048, in the split form of the
+// Ising strip kernel: one warp walks full rows [r0, r0 + R) of one lattice;
+// step s updates colour 0 on row s, then colour 1 on row s - 1, both on the
+// words of half p = y_s & 1 of the rows (rows are held as colour-compressed
+// halves: sites of even x, then of odd x).  Rows s - 2 .. s + 1 sit in four
+// split slots, row s + 2 lands by cp.async in a fifth; rows -1 and R are the
+// recomputed colour-0 halo (the same site-keyed draws as in the neighbouring
+// item), so items never exchange data.
 //
-// A 32-bit word holds four sites; its two active bytes P and P + 2 (P the row
-// parity of the colour) use lanes (0, 1) and (2, 3) of one Philox draw, and
-// both are handled with byte-parallel (SWAR) arithmetic:
-//  * X1 = [U_P, D_P, U_P+2, D_P+2] and X2 = [L_P, R_P, L_P+2, R_P+2] gather
-//    the neighbours, S = [s_P, s_P, s_P+2, s_P+2], S' the proposals likewise;
-//  * for states below 8, (a ^ b) + 7 has bit 3 set exactly when a != b, so
-//    each pair flag 8 [a != b] costs three operations and never carries;
-//  * n1 + n2 + 16 - o1 - o2 holds per byte 8 (two neighbours' [!= s'] - [!= s]
-//    + 2); adding the word shifted up one byte leaves in bytes 1 and 3 the
-//    value 8 (n_same(s) - n_same(s') + 4): the byte offset of the site's
-//    8-byte table entry (index d + 4 for dE = J d).
-// Statistics: an accepted site adds its table delta (the change of the equal-
-// bond count); the state counts are taken on the finished rows (colour-1
-// phase) from bit-plane minterms in per-byte counters, and the item holding
-// row 0 subtracts the old counts, so that `delta` receives the change.
+// All four bytes of a word are active sites.  Sites 0 and 1 of word w use
+// lanes (0, 1) and (2, 3) of Philox block g0 = (y L / 2 + 4 w) / 2 (acceptance
+// draw, proposal draw), sites 2 and 3 those of block g0 + 1.  Per word, byte-
+// parallel for states below 8:
+//  * the proposals s' = (s + 1 + mulhi(u1, q - 1)) mod q: the four offsets
+//    packed into one word, s + offset + 1 (at most 2q - 1) reduced through the
+//    sign bit of (that + 128 - q);
+//  * (a ^ b) + 7 has bit 3 set exactly when a != b, so a flag 8 [a != b] costs
+//    three operations and never carries; over the four neighbour words (up,
+//    down, the other half, the other half shifted by one site)
+//    32 + sum 8 [!= s'] - sum 8 [!= s] = 8 (n_same(s) - n_same(s') + 4) is
+//    the byte offset of the site's 8-byte table entry (index d + 4 for the
+//    energy change J d);
+//  * an accepted site takes its proposal (xor with s ^ s' in its byte) and
+//    adds its table delta (the change of the equal-bond count).
+// State counts are taken on the finished rows from bit-plane minterms in
+// per-byte counters; the item holding row 0 subtracts the old counts, so
+// `delta` receives the change.
 constexpr uint32_t kOnes = 0x01010101u;
-
-// PRMT selectors and byte masks for active bytes P and P + 2 (P = row parity).
-struct PottsPar {
-    uint32_t sel_nb;   // [x_P, y_P, x_P+2, y_P+2] from (x, y)
-    uint32_t sel_s;    // [w_P, w_P, w_P+2, w_P+2]
-    uint32_t sel_x;    // bytes 0 and 2 moved to P and P + 2, zero elsewhere
-    uint32_t mP, mQ;   // byte masks of the two active sites
-};
-
-__device__ __forceinline__ PottsPar potts_par(int P) {
-    return P ? PottsPar{0x7351u, 0x3311u, 0x2404u, 0x0000FF00u, 0xFF000000u}
-             : PottsPar{0x6240u, 0x2200u, 0x4240u, 0x000000FFu, 0x00FF0000u};
-}
 
 // Every byte replaced by copies of its top bit (prmt with sign replication).
 __device__ __forceinline__ uint32_t byte_signs(uint32_t v) {
@@ -251,34 +245,6 @@ __device__ __forceinline__ uint32_t pair_flags(uint32_t a, uint32_t b) {
     return ((a ^ b) + 0x07070707u) & 0x08080808u;
 }
 
-// Colour sub-step of the two active sites of word W (left / right words wl, wr;
-// up / down words U, D; Philox draw r).  vadd = (0x81 - q) * kOnes.
-__device__ __forceinline__ uint32_t potts_word(uint32_t W, uint32_t U, uint32_t D, uint32_t wl,
-                                               uint32_t wr, uint4 r, const PottsPar &pp, uint32_t q1,
-                                               uint32_t vadd, const char *tb, int &acc) {
-    const uint32_t lf = __funnelshift_l(wl, W, 8);
-    const uint32_t rt = __funnelshift_r(W, wr, 8);
-    const uint32_t X1 = __byte_perm(U, D, pp.sel_nb);
-    const uint32_t X2 = __byte_perm(lf, rt, pp.sel_nb);
-    const uint32_t S = __byte_perm(W, 0u, pp.sel_s);
-    // proposals s + 1 + mulhi(u1, q - 1), reduced mod q (at most 2q - 2 < 16)
-    const uint32_t M = __byte_perm(__umulhi(r.y, q1), __umulhi(r.w, q1), 0x4400u);
-    const uint32_t raw = S + M + kOnes;
-    const uint32_t V = S + M + vadd;            // byte top bit set iff raw >= q
-    const uint32_t E = byte_signs(V);
-    const uint32_t SP = (V & 0x7F7F7F7Fu & E) | (raw & ~E);
-    const uint32_t K = pair_flags(X1, SP) + pair_flags(X2, SP) + 0x10101010u - pair_flags(X1, S) -
-                       pair_flags(X2, S);
-    const uint32_t KK = K + (K << 8);
-    const uint2 eP = *reinterpret_cast<const uint2 *>(tb + __byte_perm(KK, 0u, 0x4441u));
-    const uint2 eQ = *reinterpret_cast<const uint2 *>(tb + __byte_perm(KK, 0u, 0x4443u));
-    const uint32_t xm = __byte_perm(S ^ SP, 0u, pp.sel_x);
-    uint32_t nw = W;
-    potts_accept(nw, acc, r.x, eP, xm, pp.mP);
-    potts_accept(nw, acc, r.z, eQ, xm, pp.mQ);
-    return nw;
-}
-
 // Per-byte counters of the states 1 .. 2^QB - 1 in word w (bit-plane minterms;
 // state 0 is the remainder).
 template <int QB>
@@ -288,108 +254,6 @@ __device__ __forceinline__ void count_states(uint32_t w, uint32_t (&h)[(1 << QB)
 #pragma unroll
     for (int k = 1; k < (1 << QB); ++k)
         h[k - 1] += ((k & 1) ? b0 : ~b0) & ((k & 2) ? b1 : ~b1) & ((k & 4) ? b2 : ~b2);
-}
-
-template <int QB>
-struct PottsStrip {
-    const uint4 *S;
-    uint4 *D;
-    uint4 *ring;
-    int L, Lv, r0, nrows, lane, rchunks;
-    uint32_t q1, vadd;
-    PhiloxPrefix P0, P1;
-    const TabEntry *tab_cnt;
-    const TabEntry *tab_halo;
-};
-
-template <int QB>
-__device__ __forceinline__ uint4 *pslot(const PottsStrip<QB> &x, int r) {
-    return x.ring + ((r + 2) % kRing) * x.rchunks;
-}
-
-template <int QB>
-__device__ __forceinline__ void pissue_row(const PottsStrip<QB> &x, int r) {
-    const uint4 *src = x.S + (size_t)wrap_row(x.r0 + r, x.L) * x.Lv;
-    uint4 *dst = pslot(x, r);
-    for (int j = x.lane; j < x.Lv; j += 32) cp_async16(dst + j, src + j);
-}
-
-template <int QB, int COLOUR>
-__device__ __forceinline__ void potts_phase_chunk(const PottsStrip<QB> &x, int j, const PottsPar &pp, uint4 *rc,
-                                                  const uint4 *ru, const uint4 *rd, uint4 *gout,
-                                                  const uint4 &C, uint32_t lw, uint32_t rw,
-                                                  uint32_t gyb, const PhiloxPrefix &PP,
-                                                  const char *tb, const PhiloxKeys &rk, int &acc,
-                                                  uint32_t (&h)[(1 << QB) - 1]) {
-    const uint4 U = ru[j];
-    const uint4 Dn = rd[j];
-    const uint32_t g = gyb + 4u * (uint32_t)j;
-    const uint32_t w[6] = {lw, C.x, C.y, C.z, C.w, rw};
-    const uint32_t up[4] = {U.x, U.y, U.z, U.w};
-    const uint32_t dn[4] = {Dn.x, Dn.y, Dn.z, Dn.w};
-    uint32_t out[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const uint4 r = philox_from_prefix(g + (uint32_t)i, PP, rk);
-        out[i] = potts_word(w[i + 1], up[i], dn[i], w[i], w[i + 2], r, pp, x.q1, x.vadd, tb, acc);
-    }
-    const uint4 N = make_uint4(out[0], out[1], out[2], out[3]);
-    if (COLOUR == 0) {
-        rc[j] = N;
-    } else {
-        gout[j] = N;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) count_states<QB>(out[i], h);
-    }
-}
-
-// One colour on row r of the ring.  Lane l takes chunks l, l + 32, ..; the
-// word left of a chunk comes from lane l - 1 (lane 0: lane 31's previous
-// chunk), the word right of it from lane l + 1 (lane 31: the following
-// chunk's first word).  Rows of 1024 and 2048 bytes take two chunks per
-// iteration (eight independent Philox draws per lane).  Colour 0 writes the
-// row back to the ring, colour 1 to global memory.
-template <int QB, int COLOUR>
-__device__ __forceinline__ void potts_row_phase(const PottsStrip<QB> &x, int r, const PhiloxKeys &rk,
-                                                int &acc, uint32_t (&h)[(1 << QB) - 1]) {
-    const int y = wrap_row(x.r0 + r, x.L);
-    const PottsPar pp = potts_par((COLOUR ^ y) & 1);
-    const PhiloxPrefix &PP = COLOUR ? x.P1 : x.P0;
-    const char *tb = reinterpret_cast<const char *>((r >= 0 && r < x.nrows) ? x.tab_cnt : x.tab_halo);
-    uint4 *rc = pslot(x, r);
-    const uint4 *ru = pslot(x, r - 1);
-    const uint4 *rd = pslot(x, r + 1);
-    const uint32_t gyb = (uint32_t)y * (uint32_t)(x.L >> 2);
-    uint4 *gout = x.D + (size_t)y * x.Lv;
-    const int lane = x.lane, mask = x.Lv - 1;
-    const bool first = lane == 0, last = lane == 31;
-    const int src_l = (lane + 31) & 31, src_r = (lane + 1) & 31;
-    uint32_t carry = reinterpret_cast<const uint32_t *>(rc + mask)[3];
-    if (x.Lv >= 64) {
-        // two chunks per iteration: eight independent Philox chains per lane
-#pragma unroll 1
-        for (int j = lane; j < x.Lv; j += 64) {
-            const uint4 A = rc[j], B = rc[j + 32];
-            const uint32_t nxt = reinterpret_cast<const uint32_t *>(rc + ((j - lane + 64) & mask))[0];
-            const uint32_t al = __shfl_sync(0xFFFFFFFFu, A.w, src_l);
-            const uint32_t ar = __shfl_sync(0xFFFFFFFFu, A.x, src_r);
-            const uint32_t bl = __shfl_sync(0xFFFFFFFFu, B.w, src_l);
-            const uint32_t br = __shfl_sync(0xFFFFFFFFu, B.x, src_r);
-            const uint32_t a31 = __shfl_sync(0xFFFFFFFFu, A.w, 31);
-            const uint32_t b0 = __shfl_sync(0xFFFFFFFFu, B.x, 0);
-            const uint32_t lwA = first ? carry : al, rwA = last ? b0 : ar;
-            const uint32_t lwB = first ? a31 : bl, rwB = last ? nxt : br;
-            carry = __shfl_sync(0xFFFFFFFFu, B.w, 31);
-            potts_phase_chunk<QB, COLOUR>(x, j, pp, rc, ru, rd, gout, A, lwA, rwA, gyb, PP, tb, rk, acc, h);
-            potts_phase_chunk<QB, COLOUR>(x, j + 32, pp, rc, ru, rd, gout, B, lwB, rwB, gyb, PP, tb, rk, acc, h);
-        }
-    } else {
-        const uint4 A = rc[lane];
-        const uint32_t al = __shfl_sync(0xFFFFFFFFu, A.w, src_l);
-        const uint32_t ar = __shfl_sync(0xFFFFFFFFu, A.x, src_r);
-        potts_phase_chunk<QB, COLOUR>(x, lane, pp, rc, ru, rd, gout, A, al, ar, gyb, PP, tb, rk, acc, h);
-    }
-    __syncwarp();
 }
 
 // Per-byte counters -> the warp's totals in shared memory (lane 0 writes).
@@ -403,11 +267,175 @@ __device__ __forceinline__ void drain_counts(uint32_t (&h)[(1 << QB) - 1], uint3
     }
 }
 
+namespace psplit {
+
+// Raw row (L state bytes) at src -> its two halves at dst (dst != src).
+__device__ __forceinline__ void split_row(const unsigned char *src, unsigned char *dst, int L, int lane) {
+    uint2 *E = reinterpret_cast<uint2 *>(dst);
+    uint2 *O = reinterpret_cast<uint2 *>(dst + (L >> 1));
+#pragma unroll 1
+    for (int k = lane; k < (L >> 4); k += 32) {
+        const uint4 v = reinterpret_cast<const uint4 *>(src)[k];
+        E[k] = make_uint2(prmt(v.x, v.y, 0x6420u), prmt(v.z, v.w, 0x6420u));
+        O[k] = make_uint2(prmt(v.x, v.y, 0x7531u), prmt(v.z, v.w, 0x7531u));
+    }
+}
+
+struct Walk {
+    const uint4 *S;
+    uint4 *D;
+    unsigned char *ring;   // 5 * L bytes of this warp: 4 split rows + landing
+    int L, r0, nrows, lane;
+    uint32_t q1, vadd, qq;
+    PhiloxPrefix P0, P1;
+    uint32_t tab_cnt, tab_halo;
+};
+
+// Metropolis update of the active words `act` (see the section comment);
+// `edge` is the other-half word just outside the chunk (before it for p = 0,
+// after it for p = 1); blocks g + 2 i, g + 2 i + 1 serve word i.
+template <int NW>
+__device__ __forceinline__ void update(Words<NW> &act, const Words<NW> &oth, uint32_t edge, const Words<NW> &up,
+                                       const Words<NW> &dn, uint32_t g, const PhiloxPrefix &PP,
+                                       const PhiloxKeys &rk, int p, uint32_t selH, const Walk &x, uint32_t stab,
+                                       int &acc) {
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+        const uint32_t nb = p ? (i + 1 < NW ? oth.w[i + 1] : edge) : (i > 0 ? oth.w[i - 1] : edge);
+        const uint32_t H = prmt(oth.w[i], nb, selH);
+        const uint32_t S = act.w[i];
+        const uint4 ra = philox_from_prefix(g + 2u * (uint32_t)i, PP, rk);
+        const uint4 rb = philox_from_prefix(g + 2u * (uint32_t)i + 1u, PP, rk);
+        const uint32_t m01 = prmt(__umulhi(ra.y, x.q1), __umulhi(ra.w, x.q1), 0x0040u);
+        const uint32_t m23 = prmt(__umulhi(rb.y, x.q1), __umulhi(rb.w, x.q1), 0x0040u);
+        const uint32_t M = prmt(m01, m23, 0x5410u);
+        const uint32_t raw = S + M + kOnes;
+        const uint32_t E = byte_signs(S + M + x.vadd);   // 0xFF where raw >= q
+        const uint32_t SP = raw - (E & x.qq);
+        const uint32_t K = 0x20202020u + pair_flags(up.w[i], SP) + pair_flags(dn.w[i], SP) +
+                           pair_flags(oth.w[i], SP) + pair_flags(H, SP) - pair_flags(up.w[i], S) -
+                           pair_flags(dn.w[i], S) - pair_flags(oth.w[i], S) - pair_flags(H, S);
+        SPIN_CK((K & 0x07070707u) == 0u && ((K + 0x3F3F3F3Fu) & 0x80808080u) == 0u, 125);
+        const uint32_t xm = S ^ SP;
+        uint32_t w = S;
+        potts_accept(w, acc, ra.x, lds_u2(prmt(K, stab, 0x7650u)), xm, 0x000000FFu);
+        potts_accept(w, acc, ra.z, lds_u2(prmt(K, stab, 0x7651u)), xm, 0x0000FF00u);
+        potts_accept(w, acc, rb.x, lds_u2(prmt(K, stab, 0x7652u)), xm, 0x00FF0000u);
+        potts_accept(w, acc, rb.z, lds_u2(prmt(K, stab, 0x7653u)), xm, 0xFF000000u);
+        act.w[i] = w;
+    }
+}
+
+// Final row: halves -> row-major bytes (no conversion: states are bytes).
+template <int NW>
+__device__ __forceinline__ void store_row(uint4 *Drow, int c, const Words<NW> &act, const Words<NW> &oth,
+                                          uint32_t sel0, uint32_t sel1) {
+    uint32_t o[2 * NW];
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+        o[2 * i] = prmt(act.w[i], oth.w[i], sel0);
+        o[2 * i + 1] = prmt(act.w[i], oth.w[i], sel1);
+    }
+    if constexpr (NW == 4) {
+        Drow[2 * c] = make_uint4(o[0], o[1], o[2], o[3]);
+        Drow[2 * c + 1] = make_uint4(o[4], o[5], o[6], o[7]);
+    } else {
+        Drow[c] = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+}
+
+// One item: rows [r0, r0 + nrows) with the recomputed halo rows r0 - 1 and
+// r0 + nrows (colour 0 only, no statistics).  NW: words of a half row per
+// lane chunk (2 for L = 512, else 4).
+template <int NW, int QB>
+__device__ void item(const Walk &x, const PhiloxKeys &rk, int &acc, uint32_t (&h)[(1 << QB) - 1], uint32_t *tot) {
+    const int L = x.L, lane = x.lane, half = L >> 1, nw = L >> 3, nc = nw / (32 * NW);
+    unsigned char *q0 = x.ring + 3 * L, *q1 = x.ring, *q2 = x.ring + L, *q3 = x.ring + 2 * L;
+    unsigned char *land = x.ring + 4 * L;
+    // rows -2 and -1 land in q0 (free until step -1 ends) and the landing slot
+    // and are split into q1 and q2; then row 0 (via q0) into q3, while row 1
+    // stays in flight in the landing slot
+    issue_raw(q0, x.S, wrap_row(x.r0 - 2, L), L, lane);
+    issue_raw(land, x.S, wrap_row(x.r0 - 1, L), L, lane);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncwarp();
+    split_row(q0, q1, L, lane);
+    split_row(land, q2, L, lane);
+    __syncwarp();
+    issue_raw(q0, x.S, wrap_row(x.r0, L), L, lane);
+    cp_async_commit();
+    issue_raw(land, x.S, wrap_row(x.r0 + 1, L), L, lane);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncwarp();
+    split_row(q0, q3, L, lane);
+    __syncwarp();
+    for (int s = -1; s <= x.nrows; ++s) {
+        // q0..q3 hold rows s - 2 .. s + 1
+        const int yA = wrap_row(x.r0 + s, L), yB = yA == 0 ? L - 1 : yA - 1;
+        const int p = yA & 1;
+        const uint32_t selH = p ? 0x4321u : 0x2107u;
+        const uint32_t sel0 = p ? 0x1504u : 0x5140u, sel1 = p ? 0x3726u : 0x7362u;
+        const uint32_t tabA = (s >= 0 && s < x.nrows) ? x.tab_cnt : x.tab_halo;
+        const int hp = p * half, ho = half - hp;
+        const uint32_t gA = (uint32_t)yA * (uint32_t)(L >> 2), gB = (uint32_t)yB * (uint32_t)(L >> 2);
+        uint4 *Drow = x.D + (size_t)yB * (L >> 4);
+        const int eoff = p ? NW : -1;
+        for (int j = 0; j < nc; ++j) {
+            const int c = lane + 32 * j;
+            const int we = (NW * c + eoff) & (nw - 1);
+            if (!SPIN_CK(4 * NW * (c + 1) <= half && we >= 0 && we < nw, 126)) continue;
+            const uint32_t eA = reinterpret_cast<const uint32_t *>(q2 + ho)[we];
+            Words<NW> act = ld_words<NW>(q2 + hp, c);
+            const Words<NW> oth = ld_words<NW>(q2 + ho, c);
+            Words<NW> upA = ld_words<NW>(q1 + hp, c);
+            const Words<NW> dnA = ld_words<NW>(q3 + hp, c);
+            update<NW>(act, oth, eA, upA, dnA, gA + 2u * (uint32_t)(NW * c), x.P0, rk, p, selH, x, tabA, acc);
+            st_words<NW>(q2 + hp, c, act);
+            if (s >= 1) {
+                const uint32_t eB = reinterpret_cast<const uint32_t *>(q1 + ho)[we];
+                const Words<NW> othB = ld_words<NW>(q1 + ho, c);
+                const Words<NW> upB = ld_words<NW>(q0 + hp, c);
+                update<NW>(upA, othB, eB, upB, act, gB + 2u * (uint32_t)(NW * c), x.P1, rk, p, selH, x,
+                           x.tab_cnt, acc);
+                store_row<NW>(Drow, c, upA, othB, sel0, sel1);
+#pragma unroll
+                for (int i = 0; i < NW; ++i) {
+                    count_states<QB>(upA.w[i], h);
+                    count_states<QB>(othB.w[i], h);
+                }
+            }
+        }
+        if ((s & 3) == 3) drain_counts<QB>(h, tot, lane);   // at most 4 steps x 16 words per byte counter
+        __syncwarp();
+        if (s + 2 <= x.nrows + 1) {
+            cp_async_wait_all();
+            __syncwarp();
+            split_row(land, q0, L, lane);          // row s + 2 into the slot of row s - 2
+            __syncwarp();
+            if (s + 3 <= x.nrows + 1) {
+                issue_raw(land, x.S, wrap_row(x.r0 + s + 3, L), L, lane);
+                cp_async_commit();
+            }
+        }
+        unsigned char *t = q0;
+        q0 = q1;
+        q1 = q2;
+        q2 = q3;
+        q3 = t;
+    }
+    drain_counts<QB>(h, tot, lane);
+}
+
+}  // namespace psplit
+
 template <int WARPS, int QB>
 __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) potts_strip_kernel(PottsStripArgs a) {
     constexpr int NK = (1 << QB) - 1;
-    extern __shared__ __align__(16) uint4 ring_all[];
-    __shared__ TabEntry tabs[WARPS][2][kTabStride];
+    extern __shared__ __align__(16) unsigned char ring_bytes[];
+    // 256-byte tables: an entry's address is the table's with byte 0 replaced
+    __shared__ __align__(256) TabEntry tabs[WARPS][2][256 / sizeof(TabEntry)];
     __shared__ uint32_t tots[WARPS][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t t = a.state->t;
@@ -417,7 +445,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) potts_strip_kernel(Pot
         const Item w = a.items[it];
         if (!SPIN_CK((unsigned)w.lat < (unsigned)a.n_lat, 121)) continue;
         const LatDev ld = a.lats[w.lat];
-        // a ring slot holds a row (ring_chunks chunks of 16 bytes), states fit QB bits
+        // the ring holds five rows (ring_chunks chunks of 16 bytes each), states fit QB bits
         if (!SPIN_CK((ld.L == 512 || ld.L == 1024 || ld.L == 2048) && (ld.L >> 4) <= a.ring_chunks &&
                          w.r0 >= 0 && w.nrows >= 1 && w.r0 + w.nrows <= ld.L && ld.q >= 2 && ld.q <= (1 << QB),
                      122))
@@ -429,43 +457,29 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) potts_strip_kernel(Pot
         }
         if (lane < 8) tot[lane] = 0u;
         __syncwarp();
-        PottsStrip<QB> x;
+        psplit::Walk x;
         x.S = reinterpret_cast<const uint4 *>(a.src + ld.offset);
         x.D = reinterpret_cast<uint4 *>(a.dst + ld.offset);
-        x.ring = ring_all + (size_t)warp * kRing * a.ring_chunks;
+        x.ring = ring_bytes + (size_t)warp * kRing * a.ring_chunks * 16;
         x.L = ld.L;
-        x.Lv = ld.L >> 4;
         x.r0 = w.r0;
         x.nrows = w.nrows;
         x.lane = lane;
-        x.rchunks = a.ring_chunks;
         x.q1 = (uint32_t)ld.q - 1u;
         x.vadd = (0x81u - (uint32_t)ld.q) * kOnes;
+        x.qq = (uint32_t)ld.q * kOnes;
         x.P0 = philox_prefix(ld.rng, t, 0u, a.rk);
         x.P1 = philox_prefix(ld.rng, t, 1u, a.rk);
-        x.tab_cnt = tabs[warp][0];
-        x.tab_halo = tabs[warp][1];
+        x.tab_cnt = (uint32_t)__cvta_generic_to_shared(tabs[warp][0]);
+        x.tab_halo = (uint32_t)__cvta_generic_to_shared(tabs[warp][1]);
         int acc = 0;
         uint32_t h[NK];
 #pragma unroll
         for (int k = 0; k < NK; ++k) h[k] = 0u;
-        pissue_row(x, -2);
-        cp_async_commit();
-        pissue_row(x, -1);
-        cp_async_commit();
-        pissue_row(x, 0);
-        cp_async_commit();
-        for (int s = -1; s <= x.nrows; ++s) {
-            if (s + 2 <= x.nrows + 1) pissue_row(x, s + 2);
-            cp_async_commit();
-            cp_async_wait1();           // every row up to s + 1 has landed
-            __syncwarp();
-            potts_row_phase<QB, 0>(x, s, a.rk, acc, h);
-            if (s >= 1) potts_row_phase<QB, 1>(x, s - 1, a.rk, acc, h);
-            if ((s & 7) == 7) drain_counts<QB>(h, tot, lane);   // at most 8 rows x 16 words per byte
-        }
-        drain_counts<QB>(h, tot, lane);
-        cp_async_wait_all();
+        if (ld.L == 512)
+            psplit::item<2, QB>(x, a.rk, acc, h, tot);
+        else
+            psplit::item<4, QB>(x, a.rk, acc, h, tot);
         acc = (int)__reduce_add_sync(0xFFFFFFFFu, (uint32_t)acc);
         __syncwarp();
         // lane k adds the change of statistic k (0: B_eq, 1 + k: n_k)
