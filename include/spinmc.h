@@ -379,9 +379,11 @@ int spin_cpm_batch_run(uint64_t seed, int32_t n_lattices, int32_t L, const spin_
  * BF16 MLP surrogate 3 -> 64 -> 64 -> 2 (ReLU) mapping (beta, J, h) to
  * (<E>/N, <M>/N).  Not in the paper.  Weights live in one device buffer
  * of spin_mlp_param_count() floats (FP32 master copy, layout W1[64][3],
- * b1[64], W2[64][64], b2[64], W3[2][64], b3[2]); the kernels round weights
- * and activations to BF16 and accumulate in FP32.  Inputs are normalised
- * as x' = (x - mu) * inv_sigma (mu, inv_sigma: 3 floats each, device).
+ * b1[64], W2[64][64], b2[64], W3[2][64], b3[2]); the kernels round weights,
+ * activations and the backward signal of the second layer to BF16 and
+ * accumulate in FP32 (the 64-wide products on the tensor cores).  Inputs are
+ * normalised as x' = (x - mu) * inv_sigma (mu, inv_sigma: 3 floats each,
+ * device).
  * ------------------------------------------------------------------------ */
 int spin_mlp_param_count(void);
 /* Y[n][2] = net(X[n][3]). All pointers device. */

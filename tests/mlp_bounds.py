@@ -1,10 +1,11 @@
 """Per-element error scales for the BF16 surrogate MLP kernels against the
 float64 oracle.
 
-The kernels round the weights, the normalised input and both hidden
-activations to BF16 (8 significant bits: one rounding changes a value by at
-most u = 2^-8 of its magnitude) and accumulate in FP32 (unit roundoff
-2^-24).  The oracle runs in float64 with the same BF16 weights, so the two
+The kernels round the weights, the normalised input, both hidden
+activations and the backward signal dz2 (before the tensor-core products
+dz2 W2 and dz2^T h1 and the bias gradient sum) to BF16 (8 significant bits:
+one rounding changes a value by at most u = 2^-8 of its magnitude) and
+accumulate in FP32 (unit roundoff 2^-24).  The oracle runs in float64 with the same BF16 weights, so the two
 differ only by these roundings and their propagation through the network.
 
 Worst-case (Wilkinson) bounds add the magnitudes of all rounding errors; in a
@@ -17,7 +18,7 @@ root-sum-square of its terms' error scales.  Each intermediate value gets
 such a scale, propagated from the oracle's own values and weights:
 
     forward   xn = bf(x') | z1 = W1 xn + b1 | h1 = bf(relu z1) | z2, a2 likewise | Y
-    backward  dy = (Y - T) / n | dz2 = (W3^T dy) [z2 > 0] | dz1 = (W2^T dz2) [z1 > 0]
+    backward  dy = (Y - T) / n | dz2 = bf((W3^T dy) [z2 > 0]) | dz1 = (W2^T dz2) [z1 > 0]
               gradients = sums over samples of products | dX = (W1^T dz1) inv
 
 A ReLU mask may differ between the two sides only where |z| is within K
@@ -76,6 +77,7 @@ def scales(p, X, mu, inv, T, K=K_DEFAULT):
     s_da2 = _rss(_mv(s_dy, W3), acc(np.abs(dy) @ np.abs(W3), 2))
     dz2 = da2 * (z2 > 0.0)
     s_dz2 = np.where(np.abs(z2) <= K * s_z2, np.abs(da2) + s_da2, s_da2 * (z2 > 0.0))
+    s_dz2 = _rss(s_dz2, U_BF16 * np.abs(dz2))       # the BF16 rounding of dz2
     da1 = dz2 @ W2
     s_da1 = _rss(_mv(s_dz2, W2), acc(np.abs(dz2) @ np.abs(W2), 64))
     dz1 = da1 * (z1 > 0.0)
@@ -118,8 +120,8 @@ def worst_ratio(got, vals, sc, floor=1e-30):
 
 def emulate_fp32(p, X, mu, inv, T):
     """The kernels' arithmetic in plain torch float32 on the CPU (BF16 weights
-    p, BF16 rounding of the normalised input and of both hidden activations),
-    with torch's own summation order: {Y, W1, b1, W2, b2, W3, b3, dX}."""
+    p, BF16 rounding of the normalised input, of both hidden activations and
+    of dz2), with torch's own summation order: {Y, W1, b1, W2, b2, W3, b3, dX}."""
     import torch
     bf = lambda t: t.to(torch.bfloat16).float()
     P = {k: torch.as_tensor(np.asarray(v)).float() for k, v in p.items()}
@@ -130,7 +132,7 @@ def emulate_fp32(p, X, mu, inv, T):
     a2 = bf(torch.relu(h1 @ P["W2"].T + P["b2"]))
     Y = a2 @ P["W3"].T + P["b3"]
     dy = (Y - T) / X.shape[0]
-    dz2 = (dy @ P["W3"]) * (a2 > 0)
+    dz2 = bf((dy @ P["W3"]) * (a2 > 0))
     dz1 = (dz2 @ P["W2"]) * (h1 > 0)
     out = {"Y": Y, "W1": dz1.T @ xn, "b1": dz1.sum(0), "W2": dz2.T @ h1, "b2": dz2.sum(0),
            "W3": dy.T @ a2, "b3": dy.sum(0), "dX": (dz1 @ P["W1"]) * inv}
