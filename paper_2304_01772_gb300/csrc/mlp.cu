@@ -7,7 +7,7 @@
 // Parameter layout (floats): W1[64][3] | b1[64] | W2[64][64] | b2[64] |
 // W3[2][64] | b3[2]  (4546 values).
 //
-// A block takes 128 samples (four warps of 32).  The three 64-wide
+// A block takes 64 samples (two warps of 32).  The three 64-wide
 // contractions run on the tensor cores as BF16 mma.sync m16n8k16 with FP32
 // accumulation, from BF16 tiles in shared memory (ldmatrix): the forward
 // z2 = h1 W2^T, and in the backward pass da1 = dz2 W2 and the block's share of
@@ -27,7 +27,9 @@ namespace {
 constexpr int D0 = 3, D1 = 64, D2 = 64, D3 = 2;
 constexpr int OW1 = 0, OB1 = OW1 + D1 * D0, OW2 = OB1 + D1, OB2 = OW2 + D2 * D1, OW3 = OB2 + D2,
               OB3 = OW3 + D3 * D2, NPARAM = OB3 + D3;
-constexpr int TB = 128;  // samples per block
+constexpr int TB = 64;   // samples per block, one thread each
+constexpr int NWARPS = TB / 32;
+constexpr int OMT = 64 / (16 * NWARPS);   // m-tiles of dL/dW2 rows per warp
 constexpr int BS = 72;   // row stride (bf16) of the [rows][64] tiles: 144-byte rows, conflict-free ldmatrix
 constexpr int FS = 65;   // row stride (float) of dz1
 
@@ -274,35 +276,45 @@ __global__ void __launch_bounds__(TB) mlp_backward_kernel(const float *params, c
             }
     }
     float *out = part + (size_t)blockIdx.x * (NPARAM + 1);
-    // the block's dL/dW2 = dz2^T h1 over its samples (tensor cores; warp w: rows o = 16w .. 16w + 15)
+    // the block's dL/dW2 = dz2^T h1 over its samples (tensor cores; warp w:
+    // rows o = 16 OMT w .. 16 OMT (w + 1) - 1)
     {
-        float acc[8][4];
+        float acc[OMT][8][4];
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt)
+        for (int mt = 0; mt < OMT; ++mt)
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[nt][e] = 0.0f;
-#pragma unroll 2
+            for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
+#pragma unroll
         for (int kk = 0; kk < TB / 16; ++kk) {
-            // A[m = o][k = s] = dz2[s][o]: dz2's 16 x 16 tile transposed
-            uint32_t a[4];
-            ldsm_x4_t(a, tile_addr(bdz2, 16 * kk, 16 * warp, lane, true));
+            // A[m = o][k = s] = dz2[s][o]: dz2's 16 x 16 tiles transposed
+            uint32_t a[OMT][4];
+#pragma unroll
+            for (int mt = 0; mt < OMT; ++mt)
+                ldsm_x4_t(a[mt], tile_addr(bdz2, 16 * kk, 16 * (OMT * warp + mt), lane, true));
 #pragma unroll
             for (int nt = 0; nt < 8; nt += 2) {
                 // B[k = s][n = j] = h1[s][j]
                 uint32_t b[4];
                 ldsm_x4_t(b, tile_addr(bh1, 16 * kk, 8 * nt, lane, false));
-                mma16816(acc[nt], a, b[0], b[1]);
-                mma16816(acc[nt + 1], a, b[2], b[3]);
+#pragma unroll
+                for (int mt = 0; mt < OMT; ++mt) {
+                    mma16816(acc[mt][nt], a[mt], b[0], b[1]);
+                    mma16816(acc[mt][nt + 1], a[mt], b[2], b[3]);
+                }
             }
         }
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const int o = 16 * warp + g, j = 8 * nt + 2 * c;
-            out[OW2 + o * D1 + j] = acc[nt][0];
-            out[OW2 + o * D1 + j + 1] = acc[nt][1];
-            out[OW2 + (o + 8) * D1 + j] = acc[nt][2];
-            out[OW2 + (o + 8) * D1 + j + 1] = acc[nt][3];
-        }
+        for (int mt = 0; mt < OMT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int o = 16 * (OMT * warp + mt) + g, j = 8 * nt + 2 * c;
+                out[OW2 + o * D1 + j] = acc[mt][nt][0];
+                out[OW2 + o * D1 + j + 1] = acc[mt][nt][1];
+                out[OW2 + (o + 8) * D1 + j] = acc[mt][nt][2];
+                out[OW2 + (o + 8) * D1 + j + 1] = acc[mt][nt][3];
+            }
     }
     __syncthreads();
     // dX = (W1^T dz1) inv, one sample per thread
@@ -341,14 +353,30 @@ __global__ void __launch_bounds__(TB) mlp_backward_kernel(const float *params, c
     }
 }
 
-__global__ void mlp_reduce_kernel(const float *part, int nblk, float *grad, float *loss) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < NPARAM + 1; p += gridDim.x * blockDim.x) {
-        float acc = 0.0f;
-        for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * (NPARAM + 1) + p];
+// Sum of the blocks' partials per parameter in a fixed order, so every call
+// gives the same bits: a block takes 32 parameters; its eight warps each sum
+// every eighth partial of all 32 (lanes over parameters: coalesced), and
+// warp 0 adds the eight sums in order.
+constexpr int kRedWarps = 8;
+
+__global__ void __launch_bounds__(32 * kRedWarps) mlp_reduce_kernel(const float *part, int nblk, float *grad,
+                                                                    float *loss) {
+    __shared__ float sums[kRedWarps][32];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int p = blockIdx.x * 32 + lane;
+    float acc = 0.0f;
+    if (p < NPARAM + 1)
+        for (int b = wq; b < nblk; b += kRedWarps) acc += part[(size_t)b * (NPARAM + 1) + p];
+    sums[wq][lane] = acc;
+    __syncthreads();
+    if (wq == 0 && p < NPARAM + 1) {
+        float t = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kRedWarps; ++k) t += sums[k][lane];
         if (p < NPARAM)
-            grad[p] = acc;
+            grad[p] = t;
         else if (loss)
-            *loss = acc;
+            *loss = t;
     }
 }
 
@@ -390,7 +418,7 @@ cudaError_t launch_mlp_backward(const float *params, const float *mu, const floa
     e = cudaMallocAsync(reinterpret_cast<void **>(&part), sizeof(float) * (size_t)nblk * (NPARAM + 1), s);
     if (e) return e;
     mlp_backward_kernel<<<nblk, TB, smem, s>>>(params, mu, inv_sigma, X, T, n, part, dX);
-    mlp_reduce_kernel<<<(NPARAM + 256) / 256, 256, 0, s>>>(part, nblk, grad, loss);
+    mlp_reduce_kernel<<<(NPARAM + 1 + 31) / 32, 32 * kRedWarps, 0, s>>>(part, nblk, grad, loss);
     e = cudaGetLastError();
     cudaError_t f = cudaFreeAsync(part, s);
     return e ? e : f;
