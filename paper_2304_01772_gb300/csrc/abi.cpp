@@ -138,7 +138,7 @@ struct spin_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaStream_t side = nullptr;          // tile kernel runs here, beside the strip kernel
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    GraphCache graphs[2][2];    // [record][0: two-sweep ping-pong]
+    GraphCache graphs[2][4];    // [record][two-sweep ping-pong kind: row formats at its ends]
     int last_launches = 0;
     // kernel timing (spin_profile)
     bool prof = false;
@@ -532,7 +532,7 @@ void prof_end(spin_ctx *ctx, cudaStream_t s) {
 }
 
 // One sweep of Ising/Potts lattices, src -> dst (batched) or in place (plain).
-int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s, int &launches) {
+int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s, int &launches, int layout) {
     const int w = ctx->width;
     if (ctx->mode == 1) {
         for (int c = 0; c < 2; ++c) {
@@ -611,7 +611,7 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                     if (r.strip)
                         CK(launch_ising_strip(a, std::min((r.count + ctx->strip_warps - 1) / ctx->strip_warps,
                                                           ctx->sm_count * ctx->per_sm_strip),
-                                              ctx->strip_warps, s));
+                                              ctx->strip_warps, layout, s));
                     else
                         CK(launch_ising_fused(a, std::min(r.count, ctx->grid), ctx->threads, ctx->smem, s));
                 } else if (r.strip) {
@@ -669,7 +669,7 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                                  static_cast<const int8_t *>(src), static_cast<int8_t *>(dst),
                                  ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta,
                                  philox_keys(ctx->k0, ctx->k1), ctx->n_lat};
-                CK(launch_ising_strip(a, ctx->strip_grid, ctx->strip_warps, s));
+                CK(launch_ising_strip(a, ctx->strip_grid, ctx->strip_warps, layout, s));
             } else {
                 PottsStripArgs a{ctx->d_strip, ctx->n_strip, ctx->d_lats, ctx->d_tabs,
                                  static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst),
@@ -706,8 +706,20 @@ int launch_cpm_step(spin_ctx *ctx, int record, cudaStream_t s, int &launches) {
 }
 
 // Record `two sweeps` (A -> B -> A for the batched form) into a graph.
-int get_graph(spin_ctx *ctx, int record, GraphCache *&out) {
-    GraphCache &g = ctx->graphs[record ? 1 : 0][0];
+// Ising strip lattices stay in the strip kernel's split row form between the
+// sweeps of one call (ping-pong launch forms): sweep i of n reads split rows
+// if i > 0 and writes them if i < n - 1, so the buffers hold int8 rows
+// whenever a call returns.
+bool split_rows(const spin_ctx *ctx) { return ctx->model == SPIN_ISING && ctx->mode != 1 && ctx->n_strip > 0; }
+
+int sweep_layout(const spin_ctx *ctx, int i, int n) {
+    return split_rows(ctx) ? (i > 0 ? kSrcSplit : 0) | (i < n - 1 ? kDstSplit : 0) : 0;
+}
+
+// Graph of two sweeps; kind bit 0: its first sweep reads split rows, bit 1:
+// its second sweep writes them (the middle of the pair is always split).
+int get_graph(spin_ctx *ctx, int record, int kind, GraphCache *&out) {
+    GraphCache &g = ctx->graphs[record ? 1 : 0][kind & 3];
     if (!g.exec) {
         if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
         CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -715,11 +727,14 @@ int get_graph(spin_ctx *ctx, int record, GraphCache *&out) {
         if (ctx->model == SPIN_CPM) {
             rc = launch_cpm_step(ctx, record, ctx->cap_stream, launches);
         } else if (ctx->mode == 1) {
-            rc = launch_sweep(ctx, ctx->spins, ctx->spins, record, ctx->cap_stream, launches);
-            if (rc == SPIN_OK) rc = launch_sweep(ctx, ctx->spins, ctx->spins, record, ctx->cap_stream, launches);
+            rc = launch_sweep(ctx, ctx->spins, ctx->spins, record, ctx->cap_stream, launches, 0);
+            if (rc == SPIN_OK) rc = launch_sweep(ctx, ctx->spins, ctx->spins, record, ctx->cap_stream, launches, 0);
         } else {
-            rc = launch_sweep(ctx, ctx->spins, ctx->spins2, record, ctx->cap_stream, launches);
-            if (rc == SPIN_OK) rc = launch_sweep(ctx, ctx->spins2, ctx->spins, record, ctx->cap_stream, launches);
+            const bool sp = split_rows(ctx);
+            const int l0 = sp ? ((kind & 1) ? kSrcSplit : 0) | kDstSplit : 0;
+            const int l1 = sp ? kSrcSplit | ((kind & 2) ? kDstSplit : 0) : 0;
+            rc = launch_sweep(ctx, ctx->spins, ctx->spins2, record, ctx->cap_stream, launches, l0);
+            if (rc == SPIN_OK) rc = launch_sweep(ctx, ctx->spins2, ctx->spins, record, ctx->cap_stream, launches, l1);
         }
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
@@ -778,7 +793,7 @@ int run_sweeps(spin_ctx *ctx, int n, int record, cudaStream_t s) {
         int i = 0;
         if (ctx->use_graph && !ctx->prof && n >= 1) {
             GraphCache *g = nullptr;
-            int rc = get_graph(ctx, record, g);
+            int rc = get_graph(ctx, record, 0, g);
             if (rc) return rc;
             for (; i < n; ++i) {
                 CK(cudaGraphLaunch(g->exec, s));
@@ -794,10 +809,11 @@ int run_sweeps(spin_ctx *ctx, int n, int record, cudaStream_t s) {
     }
     int i = 0;
     if (ctx->use_graph && !ctx->prof && n >= 2) {
-        GraphCache *g = nullptr;
-        int rc = get_graph(ctx, record, g);
-        if (rc) return rc;
+        const bool sp = split_rows(ctx);
         for (; i + 1 < n; i += 2) {
+            GraphCache *g = nullptr;
+            int rc = get_graph(ctx, record, sp ? (i > 0 ? 1 : 0) | (i + 2 < n ? 2 : 0) : 0, g);
+            if (rc) return rc;
             CK(cudaGraphLaunch(g->exec, s));
             launches += g->launches;
         }
@@ -806,7 +822,7 @@ int run_sweeps(spin_ctx *ctx, int n, int record, cudaStream_t s) {
         const bool even = (i & 1) == 0;
         void *src = ctx->mode == 1 ? ctx->spins : (even ? ctx->spins : ctx->spins2);
         void *dst = ctx->mode == 1 ? ctx->spins : (even ? ctx->spins2 : ctx->spins);
-        int rc = launch_sweep(ctx, src, dst, record, s, launches);
+        int rc = launch_sweep(ctx, src, dst, record, s, launches, sweep_layout(ctx, i, n));
         if (rc) return rc;
     }
     if (ctx->mode != 1 && (n & 1)) {

@@ -150,8 +150,13 @@ struct IsingSweepArgs {
 
 cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, size_t smem,
                                cudaStream_t s);
+// Row formats of the Ising strip kernel's global rows (`layout` bits).  0: int8
+// rows (+1 = 0x01, -1 = 0xFF); kSrcSplit: the source rows are in the kernel's
+// split form (the even-x half of a row, then the odd-x half, one byte
+// 8 [s < 0] per site); kDstSplit: the destination rows are written in it.
+constexpr int kSrcSplit = 1, kDstSplit = 2;
 // Warp-per-row-strip kernel for L in {512, 1024, 2048}; items are row blocks.
-cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, cudaStream_t s);
+cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, int layout, cudaStream_t s);
 cudaError_t launch_ising_plain(int8_t *spins, const LatDev *lat_dev, int lat, uint32_t rng, int L,
                                const TabEntry *tabs, uint32_t k0, uint32_t k1,
                                const DevState *state, int64_t *delta, int colour, cudaStream_t s);

@@ -737,6 +737,15 @@ __device__ __forceinline__ void drain_acc(int &acc, int &dm, int &db) {
 //
 // Shared memory per warp: four split rows (s - 2 .. s + 1) and one landing
 // slot where the raw row s + 2 arrives by cp.async while step s computes.
+//
+// Row formats in global memory (LAYOUT): bit 0 set = the source rows are
+// already in the ring's split x8 form (even-x half, then odd-x half, one byte
+// 8 [s < 0] per site), so a landed row becomes a ring slot as it is, with no
+// split pass; bit 1 set = the destination rows are written in that form too,
+// with no re-interleave.  Within a call of several sweeps the ping-pong
+// buffer holds strip lattices in the split form between two sweeps; the
+// first sweep reads and the last one writes the int8 rows of the interface.
+
 namespace split {
 
 // Raw row (L int8 spins, +1 = 0x01, -1 = 0xFF) at src -> split x8 row at dst
@@ -800,6 +809,15 @@ __device__ __forceinline__ void store_raw(uint4 *Drow, int c, const Words<NW> &a
     }
 }
 
+// Final row in the split form: the active half's words at half hp, the other
+// half's at ho (byte offsets into the destination row).
+template <int NW>
+__device__ __forceinline__ void store_split(unsigned char *Drow, int hp, int ho, int c, const Words<NW> &act,
+                                            const Words<NW> &oth) {
+    st_words<NW>(Drow + hp, c, act);
+    st_words<NW>(Drow + ho, c, oth);
+}
+
 struct Walk {
     const uint4 *S;
     uint4 *D;
@@ -811,31 +829,44 @@ struct Walk {
 
 // One item: rows [r0, r0 + nrows) of one lattice, with the recomputed halo
 // rows r0 - 1 and r0 + nrows (colour 0 only, no statistics).  NW: words of a
-// half row per lane chunk (2 for L = 512, else 4).
-template <int NW>
+// half row per lane chunk (2 for L = 512, else 4).  LAYOUT: row formats.
+template <int NW, int LAYOUT>
 __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
+    constexpr bool kSrcS = (LAYOUT & kSrcSplit) != 0, kDstS = (LAYOUT & kDstSplit) != 0;
     const int L = x.L, half = L >> 1, nw = L >> 3, nc = nw / (32 * NW), lane = x.lane;
     unsigned char *q0 = x.ring + 3 * L, *q1 = x.ring, *q2 = x.ring + L, *q3 = x.ring + 2 * L;
     unsigned char *land = x.ring + 4 * L;
-    // rows -2 and -1 land in q0 (free until step -1 ends) and the landing
-    // slot and are split into q1 and q2; then row 0 (via q0) into q3, and
-    // row 1 stays in flight in the landing slot
-    issue_raw(q0, x.S, wrap_row(x.r0 - 2, L), L, lane);
-    issue_raw(land, x.S, wrap_row(x.r0 - 1, L), L, lane);
-    cp_async_commit();
-    cp_async_wait_all();
-    __syncwarp();
-    split_row(q0, q1, L, lane);
-    split_row(land, q2, L, lane);
-    __syncwarp();
-    issue_raw(q0, x.S, wrap_row(x.r0, L), L, lane);
-    cp_async_commit();
-    issue_raw(land, x.S, wrap_row(x.r0 + 1, L), L, lane);
-    cp_async_commit();
-    cp_async_wait1();
-    __syncwarp();
-    split_row(q0, q3, L, lane);
-    __syncwarp();
+    if constexpr (kSrcS) {
+        // rows -2 .. 0 straight into their slots; row 1 in flight in the landing slot
+        issue_raw(q1, x.S, wrap_row(x.r0 - 2, L), L, lane);
+        issue_raw(q2, x.S, wrap_row(x.r0 - 1, L), L, lane);
+        issue_raw(q3, x.S, wrap_row(x.r0, L), L, lane);
+        cp_async_commit();
+        issue_raw(land, x.S, wrap_row(x.r0 + 1, L), L, lane);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncwarp();
+    } else {
+        // rows -2 and -1 land in q0 (free until step -1 ends) and the landing
+        // slot and are split into q1 and q2; then row 0 (via q0) into q3, and
+        // row 1 stays in flight in the landing slot
+        issue_raw(q0, x.S, wrap_row(x.r0 - 2, L), L, lane);
+        issue_raw(land, x.S, wrap_row(x.r0 - 1, L), L, lane);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncwarp();
+        split_row(q0, q1, L, lane);
+        split_row(land, q2, L, lane);
+        __syncwarp();
+        issue_raw(q0, x.S, wrap_row(x.r0, L), L, lane);
+        cp_async_commit();
+        issue_raw(land, x.S, wrap_row(x.r0 + 1, L), L, lane);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncwarp();
+        split_row(q0, q3, L, lane);
+        __syncwarp();
+    }
     int acc = 0;
     for (int s = -1; s <= x.nrows; ++s) {
         // q0..q3 hold rows s - 2 .. s + 1
@@ -847,6 +878,7 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
         const int hp = p * half, ho = half - hp;
         const uint32_t gA = (uint32_t)yA * (uint32_t)(L >> 3), gB = (uint32_t)yB * (uint32_t)(L >> 3);
         uint4 *Drow = x.D + (size_t)yB * (L >> 4);
+        unsigned char *Dsplit = reinterpret_cast<unsigned char *>(Drow);
         const int eoff = p ? NW : -1;
         for (int j = 0; j < nc; ++j) {
             const int c = lane + 32 * j;
@@ -866,7 +898,10 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
                 const Words<NW> othB = ld_words<NW>(q1 + ho, c);
                 const Words<NW> upB = ld_words<NW>(q0 + hp, c);
                 update<NW>(upA, othB, eB, upB, act, gBc, x.P1, rk, p, selH, x.tab_cnt, acc);
-                store_raw<NW>(Drow, c, upA, othB, selO0, selO1);
+                if constexpr (kDstS)
+                    store_split<NW>(Dsplit, hp, ho, c, upA, othB);
+                else
+                    store_raw<NW>(Drow, c, upA, othB, selO0, selO1);
             }
         }
         if ((s & 7) == 7) drain_acc(acc, dm, db);
@@ -874,8 +909,15 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
         if (s + 2 <= x.nrows + 1) {
             cp_async_wait_all();
             __syncwarp();
-            split_row(land, q0, L, lane);          // row s + 2 into the slot of row s - 2
-            __syncwarp();
+            if constexpr (kSrcS) {
+                // row s + 2 takes the slot of row s - 2, which lands the next row
+                unsigned char *t = q0;
+                q0 = land;
+                land = t;
+            } else {
+                split_row(land, q0, L, lane);      // row s + 2 into the slot of row s - 2
+                __syncwarp();
+            }
             if (s + 3 <= x.nrows + 1) {
                 issue_raw(land, x.S, wrap_row(x.r0 + s + 3, L), L, lane);
                 cp_async_commit();
@@ -892,8 +934,10 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
 
 }  // namespace split
 
-template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) ising_strip_kernel(IsingSweepArgs a) {
+// Two blocks of 8 warps (or four of 4) per SM, so up to 128 registers per
+// thread: the compiler interleaves the Philox rounds of a chunk's words.
+template <int WARPS, int LAYOUT>
+__global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) ising_strip_kernel(IsingSweepArgs a) {
     extern __shared__ __align__(16) unsigned char ring_bytes[];
     __shared__ __align__(256) TabEntry tabs[WARPS][2][256 / sizeof(TabEntry)];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -928,9 +972,9 @@ __global__ void __launch_bounds__(WARPS * 32) ising_strip_kernel(IsingSweepArgs 
         x.tab_halo = (uint32_t)__cvta_generic_to_shared(tabs[warp][1]);
         int dm = 0, db = 0;
         if (ld.L == 512)
-            split::item<2>(x, a.rk, dm, db);
+            split::item<2, LAYOUT>(x, a.rk, dm, db);
         else
-            split::item<4>(x, a.rk, dm, db);
+            split::item<4, LAYOUT>(x, a.rk, dm, db);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             dm += __shfl_xor_sync(0xFFFFFFFFu, dm, o);
@@ -1190,13 +1234,23 @@ cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, s
 
 size_t strip_smem(int warps) { return strip_ring_bytes(warps); }
 
-cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, cudaStream_t s) {
-    switch (warps) {
-        case 4:
-            ising_strip_kernel<4><<<grid, 128, strip_smem(4), s>>>(a);
+namespace {
+
+template <int WARPS>
+cudaError_t launch_strip_layout(const IsingSweepArgs &a, int grid, int layout, cudaStream_t s) {
+    const size_t smem = strip_smem(WARPS);
+    switch (layout) {
+        case 0:
+            ising_strip_kernel<WARPS, 0><<<grid, WARPS * 32, smem, s>>>(a);
             break;
-        case 8:
-            ising_strip_kernel<8><<<grid, 256, strip_smem(8), s>>>(a);
+        case kSrcSplit:
+            ising_strip_kernel<WARPS, kSrcSplit><<<grid, WARPS * 32, smem, s>>>(a);
+            break;
+        case kDstSplit:
+            ising_strip_kernel<WARPS, kDstSplit><<<grid, WARPS * 32, smem, s>>>(a);
+            break;
+        case kSrcSplit | kDstSplit:
+            ising_strip_kernel<WARPS, kSrcSplit | kDstSplit><<<grid, WARPS * 32, smem, s>>>(a);
             break;
         default:
             return cudaErrorInvalidValue;
@@ -1204,15 +1258,41 @@ cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, cud
     return cudaGetLastError();
 }
 
+template <int WARPS>
+cudaError_t strip_smem_attributes() {
+    const int smem = (int)strip_smem(WARPS);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(ising_strip_kernel<WARPS, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(ising_strip_kernel<WARPS, kSrcSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(ising_strip_kernel<WARPS, kDstSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+    return cudaFuncSetAttribute(ising_strip_kernel<WARPS, kSrcSplit | kDstSplit>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+}  // namespace
+
+cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, int layout, cudaStream_t s) {
+    switch (warps) {
+        case 4:
+            return launch_strip_layout<4>(a, grid, layout, s);
+        case 8:
+            return launch_strip_layout<8>(a, grid, layout, s);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t occupancy_ising_strip(int *blocks_per_sm, int warps) {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(ising_strip_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip_smem(4))))
-        return e;
-    if ((e = cudaFuncSetAttribute(ising_strip_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)strip_smem(8))))
-        return e;
+    if ((e = strip_smem_attributes<4>())) return e;
+    if ((e = strip_smem_attributes<8>())) return e;
+    // the four row-format instances share one body: their occupancy is alike
     if (warps == 4)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<4>, 128, strip_smem(4));
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<8>, 256, strip_smem(8));
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<4, 0>, 128, strip_smem(4));
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, ising_strip_kernel<8, 0>, 256, strip_smem(8));
 }
 
 // The dynamic shared-memory limit of a kernel is process-wide state: it is

@@ -141,6 +141,28 @@ def test_strip_kernel_rows_and_tail(rows, warps):
         assert np.array_equal(st[:, i, :], ref), i
 
 
+@pytest.mark.parametrize("mode,graph,threads", [(0, True, 512), (0, False, 256), (3, True, 512), (3, False, 512)])
+def test_split_rows_between_the_sweeps_of_a_call(mode, graph, threads):
+    """Within one call of n sweeps the strip lattices stay in the strip kernel's
+    split row form between sweeps (the first sweep reads and the last one
+    writes int8 rows): every sweep count per call, with and without graphs,
+    continues the oracle's chain, and the state is int8 after each call."""
+    lats = [dict(L=512, beta=0.44, J=1.0, h=0.03), dict(L=1024, beta=0.35, J=1.0, h=-0.05),
+            dict(L=64, beta=0.4, J=1.0, h=0.0)]
+    sim = make_ising(lats, max_record=32)
+    sim.set_launch(mode, graph, 0, threads)
+    ref = [lattice_np(sim, i) for i in range(len(lats))]
+    t = 0
+    for n in (1, 2, 3, 4, 5):
+        sim.sweep(n, record=True)
+        st = sim.observables_host(t, n)[0]
+        for i, d in enumerate(lats):
+            exp = oracle.ising_run(ref[i], d["beta"], d["J"], d["h"], SEED, i, t, n)
+            assert np.array_equal(lattice_np(sim, i), ref[i]), (n, i)
+            assert np.array_equal(st[:, i, :], exp), (n, i)
+        t += n
+
+
 def test_contexts_with_different_shared_memory_needs_coexist():
     """A context planned later with smaller work items must not lower the
     shared-memory limit that an earlier context's launches rely on."""
