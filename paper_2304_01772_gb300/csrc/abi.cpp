@@ -621,7 +621,7 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                                      philox_keys(ctx->k0, ctx->k1), ctx->n_lat};
                     CK(launch_potts_strip(a, std::min((r.count + ctx->strip_warps - 1) / ctx->strip_warps,
                                                       ctx->sm_count * ctx->per_sm_strip),
-                                          ctx->strip_warps, ctx->strip_qbits, s));
+                                          ctx->strip_warps, ctx->strip_qbits, layout, s));
                 } else {
                     PottsSweepArgs a{ctx->d_items + r.first, r.count, ctx->d_lats, ctx->d_tabs,
                                      static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst),
@@ -675,7 +675,7 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                                  static_cast<const uint8_t *>(src), static_cast<uint8_t *>(dst),
                                  ctx->d_state, ctx->st.delta, ctx->st.cur, w, ctx->strip_chunks,
                                  philox_keys(ctx->k0, ctx->k1), ctx->n_lat};
-                CK(launch_potts_strip(a, ctx->strip_grid, ctx->strip_warps, ctx->strip_qbits, s));
+                CK(launch_potts_strip(a, ctx->strip_grid, ctx->strip_warps, ctx->strip_qbits, layout, s));
             }
             if (timed) prof_end(ctx, s);
             ++launches;
@@ -706,11 +706,13 @@ int launch_cpm_step(spin_ctx *ctx, int record, cudaStream_t s, int &launches) {
 }
 
 // Record `two sweeps` (A -> B -> A for the batched form) into a graph.
-// Ising strip lattices stay in the strip kernel's split row form between the
-// sweeps of one call (ping-pong launch forms): sweep i of n reads split rows
-// if i > 0 and writes them if i < n - 1, so the buffers hold int8 rows
-// whenever a call returns.
-bool split_rows(const spin_ctx *ctx) { return ctx->model == SPIN_ISING && ctx->mode != 1 && ctx->n_strip > 0; }
+// Strip lattices (Ising and Potts) stay in the strip kernels' split row form
+// between the sweeps of one call (ping-pong launch forms): sweep i of n reads
+// split rows if i > 0 and writes them if i < n - 1, so the buffers hold the
+// interface's rows whenever a call returns.
+bool split_rows(const spin_ctx *ctx) {
+    return (ctx->model == SPIN_ISING || ctx->model == SPIN_POTTS) && ctx->mode != 1 && ctx->n_strip > 0;
+}
 
 int sweep_layout(const spin_ctx *ctx, int i, int n) {
     return split_rows(ctx) ? (i > 0 ? kSrcSplit : 0) | (i < n - 1 ? kDstSplit : 0) : 0;

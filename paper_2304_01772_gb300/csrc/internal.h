@@ -150,10 +150,11 @@ struct IsingSweepArgs {
 
 cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, size_t smem,
                                cudaStream_t s);
-// Row formats of the Ising strip kernel's global rows (`layout` bits).  0: int8
-// rows (+1 = 0x01, -1 = 0xFF); kSrcSplit: the source rows are in the kernel's
-// split form (the even-x half of a row, then the odd-x half, one byte
-// 8 [s < 0] per site); kDstSplit: the destination rows are written in it.
+// Row formats of the strip kernels' global rows (`layout` bits).  0: the
+// interface's rows (Ising int8 +1 = 0x01, -1 = 0xFF; Potts uint8 states);
+// kSrcSplit: the source rows are in the kernel's split form (the even-x half
+// of a row, then the odd-x half; Ising one byte 8 [s < 0] per site, Potts the
+// state bytes); kDstSplit: the destination rows are written in it.
 constexpr int kSrcSplit = 1, kDstSplit = 2;
 // Warp-per-row-strip kernel for L in {512, 1024, 2048}; items are row blocks.
 cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, int layout, cudaStream_t s);
@@ -248,7 +249,7 @@ struct PottsStripArgs {
     int n_lat;            // entries of lats (work-list checks of SPIN_CHECK builds)
 };
 // qbits: 2 for q <= 4, 3 for q <= 8.
-cudaError_t launch_potts_strip(const PottsStripArgs &a, int grid, int warps, int qbits, cudaStream_t s);
+cudaError_t launch_potts_strip(const PottsStripArgs &a, int grid, int warps, int qbits, int layout, cudaStream_t s);
 cudaError_t occupancy_potts_strip(int *blocks_per_sm, int warps, int qbits, int ring_chunks);
 cudaError_t launch_potts_plain(uint8_t *spins, const LatDev *lat_dev, int lat, uint32_t rng, int L, int q,
                                const TabEntry *tabs, uint32_t k0, uint32_t k1,

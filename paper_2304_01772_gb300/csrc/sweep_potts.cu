@@ -221,6 +221,11 @@ __global__ void __launch_bounds__(THREADS) potts_fused_kernel(PottsSweepArgs a) 
 // State counts are taken on the finished rows from bit-plane minterms in
 // per-byte counters; the item holding row 0 subtracts the old counts, so
 // `delta` receives the change.
+//
+// LAYOUT (kSrcSplit, kDstSplit) as in the Ising strip kernel: within a call
+// of several sweeps the ping-pong buffer holds the strip lattices' rows as
+// their two halves (even-x states, then odd-x states), so a landed row is a
+// ring slot as it is and a finished row is stored without re-interleaving.
 constexpr uint32_t kOnes = 0x01010101u;
 
 // Every byte replaced by copies of its top bit (prmt with sign replication).
@@ -326,6 +331,15 @@ __device__ __forceinline__ void update(Words<NW> &act, const Words<NW> &oth, uin
     }
 }
 
+// Final row in the split form: the active half's words at half hp, the other
+// half's at ho (byte offsets into the destination row).
+template <int NW>
+__device__ __forceinline__ void store_halves(unsigned char *Drow, int hp, int ho, int c, const Words<NW> &act,
+                                             const Words<NW> &oth) {
+    st_words<NW>(Drow + hp, c, act);
+    st_words<NW>(Drow + ho, c, oth);
+}
+
 // Final row: halves -> row-major bytes (no conversion: states are bytes).
 template <int NW>
 __device__ __forceinline__ void store_row(uint4 *Drow, int c, const Words<NW> &act, const Words<NW> &oth,
@@ -346,31 +360,44 @@ __device__ __forceinline__ void store_row(uint4 *Drow, int c, const Words<NW> &a
 
 // One item: rows [r0, r0 + nrows) with the recomputed halo rows r0 - 1 and
 // r0 + nrows (colour 0 only, no statistics).  NW: words of a half row per
-// lane chunk (2 for L = 512, else 4).
-template <int NW, int QB>
+// lane chunk (2 for L = 512, else 4).  LAYOUT: row formats.
+template <int NW, int QB, int LAYOUT>
 __device__ void item(const Walk &x, const PhiloxKeys &rk, int &acc, uint32_t (&h)[(1 << QB) - 1], uint32_t *tot) {
+    constexpr bool kSrcS = (LAYOUT & kSrcSplit) != 0, kDstS = (LAYOUT & kDstSplit) != 0;
     const int L = x.L, lane = x.lane, half = L >> 1, nw = L >> 3, nc = nw / (32 * NW);
     unsigned char *q0 = x.ring + 3 * L, *q1 = x.ring, *q2 = x.ring + L, *q3 = x.ring + 2 * L;
     unsigned char *land = x.ring + 4 * L;
-    // rows -2 and -1 land in q0 (free until step -1 ends) and the landing slot
-    // and are split into q1 and q2; then row 0 (via q0) into q3, while row 1
-    // stays in flight in the landing slot
-    issue_raw(q0, x.S, wrap_row(x.r0 - 2, L), L, lane);
-    issue_raw(land, x.S, wrap_row(x.r0 - 1, L), L, lane);
-    cp_async_commit();
-    cp_async_wait_all();
-    __syncwarp();
-    split_row(q0, q1, L, lane);
-    split_row(land, q2, L, lane);
-    __syncwarp();
-    issue_raw(q0, x.S, wrap_row(x.r0, L), L, lane);
-    cp_async_commit();
-    issue_raw(land, x.S, wrap_row(x.r0 + 1, L), L, lane);
-    cp_async_commit();
-    cp_async_wait1();
-    __syncwarp();
-    split_row(q0, q3, L, lane);
-    __syncwarp();
+    if constexpr (kSrcS) {
+        // rows -2 .. 0 straight into their slots; row 1 in flight in the landing slot
+        issue_raw(q1, x.S, wrap_row(x.r0 - 2, L), L, lane);
+        issue_raw(q2, x.S, wrap_row(x.r0 - 1, L), L, lane);
+        issue_raw(q3, x.S, wrap_row(x.r0, L), L, lane);
+        cp_async_commit();
+        issue_raw(land, x.S, wrap_row(x.r0 + 1, L), L, lane);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncwarp();
+    } else {
+        // rows -2 and -1 land in q0 (free until step -1 ends) and the landing slot
+        // and are split into q1 and q2; then row 0 (via q0) into q3, while row 1
+        // stays in flight in the landing slot
+        issue_raw(q0, x.S, wrap_row(x.r0 - 2, L), L, lane);
+        issue_raw(land, x.S, wrap_row(x.r0 - 1, L), L, lane);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncwarp();
+        split_row(q0, q1, L, lane);
+        split_row(land, q2, L, lane);
+        __syncwarp();
+        issue_raw(q0, x.S, wrap_row(x.r0, L), L, lane);
+        cp_async_commit();
+        issue_raw(land, x.S, wrap_row(x.r0 + 1, L), L, lane);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncwarp();
+        split_row(q0, q3, L, lane);
+        __syncwarp();
+    }
     for (int s = -1; s <= x.nrows; ++s) {
         // q0..q3 hold rows s - 2 .. s + 1
         const int yA = wrap_row(x.r0 + s, L), yB = yA == 0 ? L - 1 : yA - 1;
@@ -381,6 +408,7 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &acc, uint32_t (&h
         const int hp = p * half, ho = half - hp;
         const uint32_t gA = (uint32_t)yA * (uint32_t)(L >> 2), gB = (uint32_t)yB * (uint32_t)(L >> 2);
         uint4 *Drow = x.D + (size_t)yB * (L >> 4);
+        unsigned char *Dsplit = reinterpret_cast<unsigned char *>(Drow);
         const int eoff = p ? NW : -1;
         for (int j = 0; j < nc; ++j) {
             const int c = lane + 32 * j;
@@ -399,7 +427,10 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &acc, uint32_t (&h
                 const Words<NW> upB = ld_words<NW>(q0 + hp, c);
                 update<NW>(upA, othB, eB, upB, act, gB + 2u * (uint32_t)(NW * c), x.P1, rk, p, selH, x,
                            x.tab_cnt, acc);
-                store_row<NW>(Drow, c, upA, othB, sel0, sel1);
+                if constexpr (kDstS)
+                    store_halves<NW>(Dsplit, hp, ho, c, upA, othB);
+                else
+                    store_row<NW>(Drow, c, upA, othB, sel0, sel1);
 #pragma unroll
                 for (int i = 0; i < NW; ++i) {
                     count_states<QB>(upA.w[i], h);
@@ -412,8 +443,15 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &acc, uint32_t (&h
         if (s + 2 <= x.nrows + 1) {
             cp_async_wait_all();
             __syncwarp();
-            split_row(land, q0, L, lane);          // row s + 2 into the slot of row s - 2
-            __syncwarp();
+            if constexpr (kSrcS) {
+                // row s + 2 takes the slot of row s - 2, which lands the next row
+                unsigned char *t = q0;
+                q0 = land;
+                land = t;
+            } else {
+                split_row(land, q0, L, lane);      // row s + 2 into the slot of row s - 2
+                __syncwarp();
+            }
             if (s + 3 <= x.nrows + 1) {
                 issue_raw(land, x.S, wrap_row(x.r0 + s + 3, L), L, lane);
                 cp_async_commit();
@@ -430,7 +468,7 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &acc, uint32_t (&h
 
 }  // namespace psplit
 
-template <int WARPS, int QB>
+template <int WARPS, int QB, int LAYOUT>
 __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) potts_strip_kernel(PottsStripArgs a) {
     constexpr int NK = (1 << QB) - 1;
     extern __shared__ __align__(16) unsigned char ring_bytes[];
@@ -477,9 +515,9 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) potts_strip_kernel(Pot
 #pragma unroll
         for (int k = 0; k < NK; ++k) h[k] = 0u;
         if (ld.L == 512)
-            psplit::item<2, QB>(x, a.rk, acc, h, tot);
+            psplit::item<2, QB, LAYOUT>(x, a.rk, acc, h, tot);
         else
-            psplit::item<4, QB>(x, a.rk, acc, h, tot);
+            psplit::item<4, QB, LAYOUT>(x, a.rk, acc, h, tot);
         acc = (int)__reduce_add_sync(0xFFFFFFFFu, (uint32_t)acc);
         __syncwarp();
         // lane k adds the change of statistic k (0: B_eq, 1 + k: n_k)
@@ -655,41 +693,69 @@ static size_t potts_ring_bytes(int warps, int ring_chunks) {
     return sizeof(uint4) * (size_t)warps * kRing * (size_t)ring_chunks;
 }
 
+template <int WARPS, int QB>
+static cudaError_t potts_strip_attrs() {
+    const int smem = (int)strip_ring_bytes(WARPS);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(potts_strip_kernel<WARPS, QB, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(potts_strip_kernel<WARPS, QB, kSrcSplit>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(potts_strip_kernel<WARPS, QB, kDstSplit>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+    return cudaFuncSetAttribute(potts_strip_kernel<WARPS, QB, kSrcSplit | kDstSplit>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 template <int QB>
 static cudaError_t potts_strip_attrs() {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(potts_strip_kernel<4, QB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)strip_ring_bytes(4))))
-        return e;
-    return cudaFuncSetAttribute(potts_strip_kernel<8, QB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)strip_ring_bytes(8));
+    cudaError_t e = potts_strip_attrs<4, QB>();
+    return e ? e : potts_strip_attrs<8, QB>();
 }
 
 cudaError_t occupancy_potts_strip(int *blocks_per_sm, int warps, int qbits, int ring_chunks) {
     cudaError_t e = qbits == 2 ? potts_strip_attrs<2>() : potts_strip_attrs<3>();
     if (e) return e;
     const size_t sm = potts_ring_bytes(warps, ring_chunks);
+    // the four row-format instances share one body: their occupancy is alike
     if (qbits == 2)
-        return warps == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, potts_strip_kernel<4, 2>, 128, sm)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, potts_strip_kernel<8, 2>, 256, sm);
-    return warps == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, potts_strip_kernel<4, 3>, 128, sm)
-                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, potts_strip_kernel<8, 3>, 256, sm);
+        return warps == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, potts_strip_kernel<4, 2, 0>, 128, sm)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, potts_strip_kernel<8, 2, 0>, 256, sm);
+    return warps == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, potts_strip_kernel<4, 3, 0>, 128, sm)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, potts_strip_kernel<8, 3, 0>, 256, sm);
 }
 
-cudaError_t launch_potts_strip(const PottsStripArgs &a, int grid, int warps, int qbits, cudaStream_t s) {
-    if (a.ring_chunks != 32 && a.ring_chunks != 64 && a.ring_chunks != kRowChunks) return cudaErrorInvalidValue;
-    const size_t sm = potts_ring_bytes(warps, a.ring_chunks);
-    if (qbits == 2 && warps == 4)
-        potts_strip_kernel<4, 2><<<grid, 128, sm, s>>>(a);
-    else if (qbits == 2 && warps == 8)
-        potts_strip_kernel<8, 2><<<grid, 256, sm, s>>>(a);
-    else if (qbits == 3 && warps == 4)
-        potts_strip_kernel<4, 3><<<grid, 128, sm, s>>>(a);
-    else if (qbits == 3 && warps == 8)
-        potts_strip_kernel<8, 3><<<grid, 256, sm, s>>>(a);
-    else
-        return cudaErrorInvalidValue;
+template <int WARPS, int QB>
+static cudaError_t launch_potts_strip_layout(const PottsStripArgs &a, int grid, int layout, cudaStream_t s) {
+    const size_t sm = potts_ring_bytes(WARPS, a.ring_chunks);
+    switch (layout) {
+        case 0:
+            potts_strip_kernel<WARPS, QB, 0><<<grid, WARPS * 32, sm, s>>>(a);
+            break;
+        case kSrcSplit:
+            potts_strip_kernel<WARPS, QB, kSrcSplit><<<grid, WARPS * 32, sm, s>>>(a);
+            break;
+        case kDstSplit:
+            potts_strip_kernel<WARPS, QB, kDstSplit><<<grid, WARPS * 32, sm, s>>>(a);
+            break;
+        case kSrcSplit | kDstSplit:
+            potts_strip_kernel<WARPS, QB, kSrcSplit | kDstSplit><<<grid, WARPS * 32, sm, s>>>(a);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
+}
+
+cudaError_t launch_potts_strip(const PottsStripArgs &a, int grid, int warps, int qbits, int layout, cudaStream_t s) {
+    if (a.ring_chunks != 32 && a.ring_chunks != 64 && a.ring_chunks != kRowChunks) return cudaErrorInvalidValue;
+    if (qbits == 2 && warps == 4) return launch_potts_strip_layout<4, 2>(a, grid, layout, s);
+    if (qbits == 2 && warps == 8) return launch_potts_strip_layout<8, 2>(a, grid, layout, s);
+    if (qbits == 3 && warps == 4) return launch_potts_strip_layout<4, 3>(a, grid, layout, s);
+    if (qbits == 3 && warps == 8) return launch_potts_strip_layout<8, 3>(a, grid, layout, s);
+    return cudaErrorInvalidValue;
 }
 
 SPIN_CHECK_ACCESSOR(check_word_potts)

@@ -419,6 +419,25 @@ def test_potts_strip_batch(mode, tile, threads, graph):
         assert np.array_equal(cur[i, :d["q"] + 1], oracle.potts_stats(lattice_np(sim, i), d["q"])), i
 
 
+@pytest.mark.parametrize("mode,graph", [(0, True), (0, False), (3, True)])
+def test_potts_split_rows_between_the_sweeps_of_a_call(mode, graph):
+    """Potts strip lattices, like Ising ones, stay in the split row form between
+    the sweeps of one call: calls of 2, 4 and 5 sweeps continue the oracle's
+    chain, with the recorded statistics of every sweep."""
+    sim = sm.Sim(sm.SPIN_POTTS, POTTS_STRIP, seed=SEED, max_record=16)
+    sim.set_launch(mode, graph, 0, 256)
+    ref = {i: lattice_np(sim, i) for i in range(len(POTTS_STRIP))}
+    t = 0
+    for n in (2, 4, 5):
+        sim.sweep(n, record=True)
+        st = sim.observables_host(t, n)[0]
+        for i, d in enumerate(POTTS_STRIP):
+            exp = oracle.potts_run(ref[i], d["q"], d["beta"], d["J"], SEED, i, t, n)
+            assert np.array_equal(lattice_np(sim, i), ref[i]), (n, i)
+            assert np.array_equal(st[:, i, :d["q"] + 1], exp), (n, i)
+        t += n
+
+
 @pytest.mark.parametrize("q", [3, 8])
 def test_potts_full_size_sampled(q):
     lats = wl.potts_batch(q)
