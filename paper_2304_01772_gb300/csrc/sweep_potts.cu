@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(THREADS) potts_fused_kernel(PottsSweepArgs a) 
 //    energy change J d);
 //  * an accepted site takes its proposal (xor with s ^ s' in its byte) and
 //    adds its table delta (the change of the equal-bond count).
-// State counts are taken on the finished rows from bit-plane minterms in
+// State counts are taken on the finished rows from bit-plane products in
 // per-byte counters; the item holding row 0 subtracts the old counts, so
 // `delta` receives the change.
 //
@@ -250,25 +250,51 @@ __device__ __forceinline__ uint32_t pair_flags(uint32_t a, uint32_t b) {
     return ((a ^ b) + 0x07070707u) & 0x08080808u;
 }
 
-// Per-byte counters of the states 1 .. 2^QB - 1 in word w (bit-plane minterms;
-// state 0 is the remainder).
+// Per-byte counters of the bit planes of the states in the words a and b.
+// QB = 2: h = (b0, b1, b0 b1); QB = 3: h = (b0, b1, b0 b1, b2, b0 b2, b1 b2,
+// b0 b1 b2), bk the bit k of a state.  drain_counts turns them into the counts
+// of the states 1 .. 2^QB - 1 by inclusion-exclusion (state 0 is the rest).
 template <int QB>
-__device__ __forceinline__ void count_states(uint32_t w, uint32_t (&h)[(1 << QB) - 1]) {
-    const uint32_t b0 = w & kOnes, b1 = (w >> 1) & kOnes;
-    const uint32_t b2 = QB > 2 ? (w >> 2) & kOnes : 0u;
-#pragma unroll
-    for (int k = 1; k < (1 << QB); ++k)
-        h[k - 1] += ((k & 1) ? b0 : ~b0) & ((k & 2) ? b1 : ~b1) & ((k & 4) ? b2 : ~b2);
+__device__ __forceinline__ void count_planes(uint32_t a, uint32_t b, uint32_t (&h)[(1 << QB) - 1]) {
+    const uint32_t a1 = a >> 1, b1 = b >> 1;
+    const uint32_t a01 = a & a1, b01 = b & b1;
+    h[0] += (a & kOnes) + (b & kOnes);
+    h[1] += (a1 & kOnes) + (b1 & kOnes);
+    h[2] += (a01 & kOnes) + (b01 & kOnes);
+    if constexpr (QB > 2) {
+        const uint32_t a2 = a >> 2, b2 = b >> 2;
+        h[3] += (a2 & kOnes) + (b2 & kOnes);
+        h[4] += (a & a2 & kOnes) + (b & b2 & kOnes);
+        h[5] += (a1 & a2 & kOnes) + (b1 & b2 & kOnes);
+        h[6] += (a01 & a2 & kOnes) + (b01 & b2 & kOnes);
+    }
 }
 
-// Per-byte counters -> the warp's totals in shared memory (lane 0 writes).
+// Per-byte plane counters -> the warp's state counts in shared memory
+// (tot[k - 1] += n_k; lane 0 writes).
 template <int QB>
 __device__ __forceinline__ void drain_counts(uint32_t (&h)[(1 << QB) - 1], uint32_t *tot, int lane) {
+    uint32_t T[(1 << QB) - 1];
 #pragma unroll
     for (int k = 0; k < (1 << QB) - 1; ++k) {
-        const uint32_t v = __reduce_add_sync(0xFFFFFFFFu, __dp4a(h[k], kOnes, 0u));
-        if (lane == 0) tot[k] += v;
+        T[k] = __reduce_add_sync(0xFFFFFFFFu, __dp4a(h[k], kOnes, 0u));
         h[k] = 0u;
+    }
+    if (lane == 0) {
+        if constexpr (QB == 2) {
+            tot[0] += T[0] - T[2];                    // state 1: b0 only
+            tot[1] += T[1] - T[2];                    // state 2: b1 only
+            tot[2] += T[2];                           // state 3
+        } else {
+            const uint32_t p0 = T[0], p1 = T[1], p01 = T[2], p2 = T[3], p02 = T[4], p12 = T[5], p012 = T[6];
+            tot[0] += p0 - p01 - p02 + p012;          // 1
+            tot[1] += p1 - p01 - p12 + p012;          // 2
+            tot[2] += p01 - p012;                     // 3
+            tot[3] += p2 - p02 - p12 + p012;          // 4
+            tot[4] += p02 - p012;                     // 5
+            tot[5] += p12 - p012;                     // 6
+            tot[6] += p012;                           // 7
+        }
     }
 }
 
@@ -432,10 +458,7 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &acc, uint32_t (&h
                 else
                     store_row<NW>(Drow, c, upA, othB, sel0, sel1);
 #pragma unroll
-                for (int i = 0; i < NW; ++i) {
-                    count_states<QB>(upA.w[i], h);
-                    count_states<QB>(othB.w[i], h);
-                }
+                for (int i = 0; i < NW; ++i) count_planes<QB>(upA.w[i], othB.w[i], h);
             }
         }
         if ((s & 3) == 3) drain_counts<QB>(h, tot, lane);   // at most 4 steps x 16 words per byte counter
