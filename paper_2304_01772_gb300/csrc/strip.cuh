@@ -53,10 +53,6 @@ __device__ __forceinline__ uint4 philox_from_prefix(uint32_t g, const PhiloxPref
     return make_uint4(c0, c1, c2, c3);
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
@@ -78,19 +74,7 @@ struct Words {
     uint32_t w[NW];
 };
 
-template <int NW>
-__device__ __forceinline__ Words<NW> ld_words(const unsigned char *half, int c) {
-    Words<NW> r;
-    if constexpr (NW == 4) {
-        const uint4 v = reinterpret_cast<const uint4 *>(half)[c];
-        r.w[0] = v.x, r.w[1] = v.y, r.w[2] = v.z, r.w[3] = v.w;
-    } else {
-        const uint2 v = reinterpret_cast<const uint2 *>(half)[c];
-        r.w[0] = v.x, r.w[1] = v.y;
-    }
-    return r;
-}
-
+// Chunk c of a half row at a generic address (a destination row in global memory).
 template <int NW>
 __device__ __forceinline__ void st_words(unsigned char *half, int c, const Words<NW> &r) {
     if constexpr (NW == 4)
@@ -99,10 +83,37 @@ __device__ __forceinline__ void st_words(unsigned char *half, int c, const Words
         reinterpret_cast<uint2 *>(half)[c] = make_uint2(r.w[0], r.w[1]);
 }
 
-// Row y of an L x L byte lattice S -> dst by cp.async (16 bytes per lane and copy).
-__device__ __forceinline__ void issue_raw(unsigned char *dst, const uint4 *S, int y, int L, int lane) {
+// Ring accesses by 32-bit shared-memory address (volatile: never merged or
+// moved across the warp's ring hand-offs), and cp.async of row y into the
+// ring at shared address dst.
+__device__ __forceinline__ uint32_t sld1(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+    return v;
+}
+template <int NW>
+__device__ __forceinline__ Words<NW> ldw(uint32_t half, int c) {
+    Words<NW> r;
+    if constexpr (NW == 4)
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(r.w[0]), "=r"(r.w[1]), "=r"(r.w[2]), "=r"(r.w[3]) : "r"(half + 16u * (uint32_t)c));
+    else
+        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.w[0]), "=r"(r.w[1]) : "r"(half + 8u * (uint32_t)c));
+    return r;
+}
+template <int NW>
+__device__ __forceinline__ void stw(uint32_t half, int c, const Words<NW> &r) {
+    if constexpr (NW == 4)
+        asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(half + 16u * (uint32_t)c), "r"(r.w[0]),
+                     "r"(r.w[1]), "r"(r.w[2]), "r"(r.w[3]));
+    else
+        asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(half + 8u * (uint32_t)c), "r"(r.w[0]), "r"(r.w[1]));
+}
+__device__ __forceinline__ void issue_raw_s(uint32_t dst, const uint4 *S, int y, int L, int lane) {
     const uint4 *src = S + (size_t)y * (L >> 4);
-    for (int j = lane; j < (L >> 4); j += 32) cp_async16(reinterpret_cast<uint4 *>(dst) + j, src + j);
+    for (int j = lane; j < (L >> 4); j += 32)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16u * (uint32_t)j), "l"(src + j)
+                     : "memory");
 }
 
 // One 8-byte table entry at a shared-memory address.

@@ -750,15 +750,17 @@ namespace split {
 
 // Raw row (L int8 spins, +1 = 0x01, -1 = 0xFF) at src -> split x8 row at dst
 // (dst != src), one 16-byte raw chunk per lane at a time.
-__device__ __forceinline__ void split_row(const unsigned char *src, unsigned char *dst, int L, int lane) {
-    uint2 *E = reinterpret_cast<uint2 *>(dst);
-    uint2 *O = reinterpret_cast<uint2 *>(dst + (L >> 1));
+__device__ __forceinline__ void split_row(uint32_t src, uint32_t dst, int L, int lane) {
 #pragma unroll 1
     for (int k = lane; k < (L >> 4); k += 32) {
-        const uint4 v = reinterpret_cast<const uint4 *>(src)[k];
+        const Words<4> v4 = ldw<4>(src, k);
+        const uint4 v = make_uint4(v4.w[0], v4.w[1], v4.w[2], v4.w[3]);
         const uint32_t a = v.x & kX8, b = v.y & kX8, c = v.z & kX8, d = v.w & kX8;
-        E[k] = make_uint2(__byte_perm(a, b, 0x6420), __byte_perm(c, d, 0x6420));
-        O[k] = make_uint2(__byte_perm(a, b, 0x7531), __byte_perm(c, d, 0x7531));
+        Words<2> e, o;
+        e.w[0] = __byte_perm(a, b, 0x6420), e.w[1] = __byte_perm(c, d, 0x6420);
+        o.w[0] = __byte_perm(a, b, 0x7531), o.w[1] = __byte_perm(c, d, 0x7531);
+        stw<2>(dst, k, e);
+        stw<2>(dst + (uint32_t)(L >> 1), k, o);
     }
 }
 
@@ -821,7 +823,7 @@ __device__ __forceinline__ void store_split(unsigned char *Drow, int hp, int ho,
 struct Walk {
     const uint4 *S;
     uint4 *D;
-    unsigned char *ring;   // 5 * L bytes of this warp: 4 split rows + landing
+    uint32_t ring;   // shared address of this warp's 5 * L bytes: 4 split rows + landing
     int L, r0, nrows, lane;
     PhiloxPrefix P0, P1;
     uint32_t tab_cnt, tab_halo;
@@ -834,15 +836,16 @@ template <int NW, int LAYOUT>
 __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
     constexpr bool kSrcS = (LAYOUT & kSrcSplit) != 0, kDstS = (LAYOUT & kDstSplit) != 0;
     const int L = x.L, half = L >> 1, nw = L >> 3, nc = nw / (32 * NW), lane = x.lane;
-    unsigned char *q0 = x.ring + 3 * L, *q1 = x.ring, *q2 = x.ring + L, *q3 = x.ring + 2 * L;
-    unsigned char *land = x.ring + 4 * L;
+    const uint32_t uL = (uint32_t)L;
+    uint32_t q0 = x.ring + 3 * uL, q1 = x.ring, q2 = x.ring + uL, q3 = x.ring + 2 * uL;
+    uint32_t land = x.ring + 4 * uL;
     if constexpr (kSrcS) {
         // rows -2 .. 0 straight into their slots; row 1 in flight in the landing slot
-        issue_raw(q1, x.S, wrap_row(x.r0 - 2, L), L, lane);
-        issue_raw(q2, x.S, wrap_row(x.r0 - 1, L), L, lane);
-        issue_raw(q3, x.S, wrap_row(x.r0, L), L, lane);
+        issue_raw_s(q1, x.S, wrap_row(x.r0 - 2, L), L, lane);
+        issue_raw_s(q2, x.S, wrap_row(x.r0 - 1, L), L, lane);
+        issue_raw_s(q3, x.S, wrap_row(x.r0, L), L, lane);
         cp_async_commit();
-        issue_raw(land, x.S, wrap_row(x.r0 + 1, L), L, lane);
+        issue_raw_s(land, x.S, wrap_row(x.r0 + 1, L), L, lane);
         cp_async_commit();
         cp_async_wait1();
         __syncwarp();
@@ -850,17 +853,17 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
         // rows -2 and -1 land in q0 (free until step -1 ends) and the landing
         // slot and are split into q1 and q2; then row 0 (via q0) into q3, and
         // row 1 stays in flight in the landing slot
-        issue_raw(q0, x.S, wrap_row(x.r0 - 2, L), L, lane);
-        issue_raw(land, x.S, wrap_row(x.r0 - 1, L), L, lane);
+        issue_raw_s(q0, x.S, wrap_row(x.r0 - 2, L), L, lane);
+        issue_raw_s(land, x.S, wrap_row(x.r0 - 1, L), L, lane);
         cp_async_commit();
         cp_async_wait_all();
         __syncwarp();
         split_row(q0, q1, L, lane);
         split_row(land, q2, L, lane);
         __syncwarp();
-        issue_raw(q0, x.S, wrap_row(x.r0, L), L, lane);
+        issue_raw_s(q0, x.S, wrap_row(x.r0, L), L, lane);
         cp_async_commit();
-        issue_raw(land, x.S, wrap_row(x.r0 + 1, L), L, lane);
+        issue_raw_s(land, x.S, wrap_row(x.r0 + 1, L), L, lane);
         cp_async_commit();
         cp_async_wait1();
         __syncwarp();
@@ -885,18 +888,18 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
             const int we = (NW * c + eoff) & (nw - 1);
             // the chunk and the edge word lie inside the half row
             if (!SPIN_CK(4 * NW * (c + 1) <= half && we >= 0 && we < nw, 103)) continue;
-            const uint32_t eA = reinterpret_cast<const uint32_t *>(q2 + ho)[we];
-            Words<NW> act = ld_words<NW>(q2 + hp, c);
-            const Words<NW> oth = ld_words<NW>(q2 + ho, c);
-            Words<NW> upA = ld_words<NW>(q1 + hp, c);
-            const Words<NW> dnA = ld_words<NW>(q3 + hp, c);
+            const uint32_t eA = sld1(q2 + (uint32_t)ho + 4u * (uint32_t)we);
+            Words<NW> act = ldw<NW>(q2 + (uint32_t)hp, c);
+            const Words<NW> oth = ldw<NW>(q2 + (uint32_t)ho, c);
+            Words<NW> upA = ldw<NW>(q1 + (uint32_t)hp, c);
+            const Words<NW> dnA = ldw<NW>(q3 + (uint32_t)hp, c);
             update<NW>(act, oth, eA, upA, dnA, gA + (uint32_t)(NW * c), x.P0, rk, p, selH, tabA, acc);
-            st_words<NW>(q2 + hp, c, act);
+            stw<NW>(q2 + (uint32_t)hp, c, act);
             if (s >= 1) {
                 const uint32_t gBc = gB + (uint32_t)(NW * c);
-                const uint32_t eB = reinterpret_cast<const uint32_t *>(q1 + ho)[we];
-                const Words<NW> othB = ld_words<NW>(q1 + ho, c);
-                const Words<NW> upB = ld_words<NW>(q0 + hp, c);
+                const uint32_t eB = sld1(q1 + (uint32_t)ho + 4u * (uint32_t)we);
+                const Words<NW> othB = ldw<NW>(q1 + (uint32_t)ho, c);
+                const Words<NW> upB = ldw<NW>(q0 + (uint32_t)hp, c);
                 update<NW>(upA, othB, eB, upB, act, gBc, x.P1, rk, p, selH, x.tab_cnt, acc);
                 if constexpr (kDstS)
                     store_split<NW>(Dsplit, hp, ho, c, upA, othB);
@@ -911,7 +914,7 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
             __syncwarp();
             if constexpr (kSrcS) {
                 // row s + 2 takes the slot of row s - 2, which lands the next row
-                unsigned char *t = q0;
+                const uint32_t t = q0;
                 q0 = land;
                 land = t;
             } else {
@@ -919,11 +922,11 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
                 __syncwarp();
             }
             if (s + 3 <= x.nrows + 1) {
-                issue_raw(land, x.S, wrap_row(x.r0 + s + 3, L), L, lane);
+                issue_raw_s(land, x.S, wrap_row(x.r0 + s + 3, L), L, lane);
                 cp_async_commit();
             }
         }
-        unsigned char *t = q0;
+        const uint32_t t = q0;
         q0 = q1;
         q1 = q2;
         q2 = q3;
@@ -961,7 +964,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) ising_strip_kernel(Isi
         split::Walk x;
         x.S = reinterpret_cast<const uint4 *>(a.src + ld.offset);
         x.D = reinterpret_cast<uint4 *>(a.dst + ld.offset);
-        x.ring = ring_bytes + (size_t)warp * kRing * kRowChunks * 16;
+        x.ring = (uint32_t)__cvta_generic_to_shared(ring_bytes) + (uint32_t)(warp * kRing * kRowChunks * 16);
         x.L = ld.L;
         x.r0 = w.r0;
         x.nrows = w.nrows;
