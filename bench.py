@@ -392,7 +392,7 @@ def measured_peaks():
 KERNEL_SECTIONS = {
     # kernel: (file, section start, section end, end of the part of internal.h it depends on)
     "ising_strip_kernel": ("sweep_ising.cu",
-                           "// Row-strip kernel in the split form",
+                           "// One 8-byte table entry at a shared-memory address.",   # + accept_site
                            "// Copy every lattice", "cudaError_t launch_ising_strip("),
     "dmc_step_kernel": ("dmc.cu", "// One whole optimisation iteration per lattice",
                         "// loss[lat] = sum (target - s)^2", "cudaError_t launch_dmc_step("),

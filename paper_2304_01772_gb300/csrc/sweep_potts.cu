@@ -235,13 +235,14 @@ __device__ __forceinline__ uint32_t byte_signs(uint32_t v) {
     return r;
 }
 
-// If u <= thr: w ^= (xm & m) (the site takes its proposal) and acc += delta.
+// If u <= thr: w ^= (xm & m) (the site takes its proposal) and acc += delta
+// (an add with an unused carry-out, as in the Ising accept_site).
 __device__ __forceinline__ void potts_accept(uint32_t &w, int &acc, uint32_t u, uint2 e,
                                              uint32_t xm, uint32_t m) {
     asm("{\n\t.reg .pred p;\n\t"
         "setp.le.u32 p, %2, %3;\n\t"
         "@p lop3.b32 %0, %0, %4, %5, 0x78;\n\t"
-        "@p add.s32 %1, %1, %6;\n\t}"
+        "@p add.cc.u32 %1, %1, %6;\n\t}"
         : "+r"(w), "+r"(acc)
         : "r"(u), "r"(e.x), "r"(xm), "r"(m), "r"(e.y));
 }
