@@ -221,7 +221,12 @@ int spin_set_params(spin_ctx *ctx, const spin_lattice_desc *lat, const spin_cpm_
  * height in rows for mode 0 (0 = keep the current value, -1 = default items:
  * about 32 KB for the tile kernel; for the Ising row-strip kernel each strip
  * lattice cut into equal row ranges, at most one item per resident warp of the
- * launch and each as small as that allows, at least 8 rows).  threads: CTA size of the tile kernel (128, 256 or 512; 0 =
+ * launch and each as small as that allows, at least 8 rows); in mode 2, the
+ * CTAs per square Ising lattice: 1 (or -1) = one CTA holds the lattice, 2 or 4
+ * = the lattice's rows are split over a thread-block cluster of that many CTAs
+ * that exchange their edge rows through distributed shared memory after every
+ * colour sub-step (for batches of fewer lattices than SMs; threads 256, 512 or
+ * 1024), 0 = keep.  threads: CTA size of the tile kernel (128, 256 or 512; 0 =
  * keep) and of the square-lattice resident kernel (also 1024 there); the warp
  * row-strip kernel uses 8 warps per CTA for 512, else 4.
  * Results do not depend on any of these. */
@@ -233,7 +238,8 @@ int spin_set_launch(spin_ctx *ctx, int32_t mode, int32_t use_graph, int32_t tile
  * runs sweeps_per_trial sweeps (at least 2), repeated with more sweeps (up to
  * 4096) while it lasts under about a millisecond.                          */
 int spin_autotune(spin_ctx *ctx, int32_t sweeps_per_trial, void *stream);
-/* Current launch form as (mode, use_graph, tile_rows, threads). */
+/* Current launch form as (mode, use_graph, tile_rows, threads); in mode 2
+ * tile_rows is the cluster size (0 for one CTA per lattice). */
 int spin_get_launch(const spin_ctx *ctx, int32_t out[4]);
 
 /* Copy the spins between the context's device state and host memory (the

@@ -124,6 +124,7 @@ struct spin_ctx {
     int64_t n_rec = 0;
     // launch form
     int mode = 0, use_graph = 1, tile_rows = 0, threads = 256;
+    int cluster = 1;                      // resident form: CTAs per lattice (1, 2 or 4)
     int use_strip = 1;
     // launch mode 3: one launch per lattice, items [first, first + count) of
     // the strip list (strip = 1) or of the tile list
@@ -785,6 +786,8 @@ int run_sweeps(spin_ctx *ctx, int n, int record, cudaStream_t s) {
                                          ctx->d_state, s));
         else if (ctx->n_tri == ctx->n_lat)
             CK(launch_ising_tri_resident(a, ctx->n_lat, (size_t)ctx->maxL * ctx->maxL, ctx->d_state, s));
+        else if (ctx->cluster > 1)
+            CK(launch_ising_resident_cluster(a, ctx->n_lat, ctx->threads, ctx->cluster, ctx->maxL, ctx->d_state, s));
         else
             CK(launch_ising_resident(a, ctx->n_lat, ctx->threads, (size_t)ctx->maxL * ctx->maxL,
                                      ctx->d_state, s));
@@ -1360,10 +1363,22 @@ int spin_set_launch(spin_ctx *ctx, int32_t mode, int32_t use_graph, int32_t tile
     if (threads != 0 && threads != 128 && threads != 256 && threads != 512 && !(threads == 1024 && mode == 2))
         return fail(ctx, SPIN_EINVAL, "threads must be 128, 256 or 512 (or 1024 in the resident form)");
     if (tile_rows < -1) return fail(ctx, SPIN_EINVAL, "tile_rows must be >= -1");
+    int cluster = ctx->cluster;
+    if (mode == 2) {   // tile_rows: CTAs per lattice (cluster size) of the square-lattice resident form
+        if (tile_rows == -1 || tile_rows == 1) cluster = 1;
+        else if (tile_rows > 0) cluster = tile_rows;
+        if (cluster != 1 && cluster != 2 && cluster != 4)
+            return fail(ctx, SPIN_EINVAL, "the resident form takes 1, 2 or 4 CTAs per lattice");
+        const int th = threads ? threads : ctx->threads;
+        if (cluster > 1 && (ctx->model != SPIN_ISING || ctx->n_nnn || ctx->n_tri || th < 256))
+            return fail(ctx, SPIN_EINVAL, "a cluster per lattice needs square Ising lattices and 256, 512 or "
+                                          "1024 threads");
+    }
     ctx->mode = mode;
     ctx->use_graph = use_graph ? 1 : 0;
-    if (tile_rows > 0) ctx->tile_rows = tile_rows;
-    if (tile_rows == -1) ctx->tile_rows = 0;
+    if (mode == 2) ctx->cluster = cluster;
+    else if (tile_rows > 0) ctx->tile_rows = tile_rows;
+    else if (tile_rows == -1) ctx->tile_rows = 0;
     if (threads) ctx->threads = threads;
     if (ctx->mode != 2 && ctx->threads > 512) ctx->threads = 512;   // 1024 exists in the resident form only
     return plan(ctx);
@@ -1373,7 +1388,7 @@ int spin_get_launch(const spin_ctx *ctx, int32_t out[4]) {
     if (!ctx || !out) return SPIN_EINVAL;
     out[0] = ctx->mode;
     out[1] = ctx->use_graph;
-    out[2] = ctx->tile_rows;
+    out[2] = ctx->mode == 2 ? (ctx->cluster > 1 ? ctx->cluster : 0) : ctx->tile_rows;
     out[3] = ctx->threads;
     return SPIN_OK;
 }
@@ -1556,8 +1571,13 @@ int spin_autotune(spin_ctx *ctx, int32_t sweeps_per_trial, void *stream) {
     for (int th : {128, 256, 512})
         for (int tr : {0, 8, 16, 32, 64}) cands.push_back({0, tr, th});
     cands.push_back({1, 0, 256});
-    if (resident_ok(ctx))
+    if (resident_ok(ctx)) {
         for (int th : {128, 256, 512, 1024}) cands.push_back({2, 0, th});
+        // square lattices: each lattice split over a cluster of 2 or 4 CTAs
+        if (ctx->model == SPIN_ISING && !ctx->n_nnn && !ctx->n_tri)
+            for (int cs : {2, 4})
+                for (int th : {256, 512, 1024}) cands.push_back({2, cs, th});
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));

@@ -189,6 +189,11 @@ struct ResidentArgs {
 };
 cudaError_t launch_ising_resident(const ResidentArgs &a, int n_lat, int threads, size_t smem,
                                   DevState *state, cudaStream_t s);
+// The same with each lattice split over a cluster of cs CTAs (2 or 4), CTA r
+// holding rows [r L/cs, (r+1) L/cs); max_l: the largest side (a multiple of
+// 16 cs), which sizes the shared memory.
+cudaError_t launch_ising_resident_cluster(const ResidentArgs &a, int n_lat, int threads, int cs, int max_l,
+                                          DevState *state, cudaStream_t s);
 // The same for batches made only of triangular lattices (L <= 240).
 cudaError_t launch_ising_tri_resident(const ResidentArgs &a, int n_lat, size_t smem, DevState *state,
                                       cudaStream_t s);

@@ -19,6 +19,8 @@
 //  * ising_plain_kernel: one lattice, one colour, in place (two launches per
 //    lattice per sweep: the plain launch form the batched one is compared to).
 //  * ising_generic_kernel: any even L (not a multiple of 16), one thread per site.
+#include <cooperative_groups.h>
+
 #include "internal.h"
 #include "strip.cuh"
 
@@ -1210,6 +1212,143 @@ __global__ void __launch_bounds__(THREADS) ising_resident_kernel(ResidentArgs a)
     if (threadIdx.x < 2) a.st.cur[2 * lat + threadIdx.x] = cur_s[threadIdx.x];
 }
 
+// ---------------------------------------------------------------------------
+// Resident kernel split over a thread-block cluster: lattice l is held by the
+// CS CTAs of cluster l, CTA r owning rows [r L/CS, (r+1) L/CS) in shared
+// memory for every sweep of a call.  A batch of fewer lattices than SMs (the
+// one-CTA form leaves SMs idle) then spreads over CS times as many CTAs.
+//
+// Each CTA keeps its rows plus two halo rows (the row above its first and the
+// row below its last) in two buffers.  Sub-step k (k = 2 sweep + c) reads
+// halo buffer k & 1; a thread that finishes a chunk of its first or last row
+// also stores it, through distributed shared memory, into the halo buffer
+// (k + 1) & 1 of the CTA owning the rows above or below.  One cluster barrier
+// ends each sub-step: it orders those stores before the next sub-step's reads,
+// and the buffer a sub-step writes was last read in the sub-step before that
+// barrier.  Draws are those of the one-CTA form (site-keyed Philox counters),
+// so the chains are bit-identical.  Statistics: each CTA reduces its changes
+// after colour 1 and CTA 0 of the cluster adds the CTAs' parts, read one
+// barrier later, to the lattice's running values and records them.
+template <int THREADS, int CS>
+__global__ void __cluster_dims__(CS, 1, 1) __launch_bounds__(THREADS)
+    ising_resident_cluster_kernel(ResidentArgs a) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char sm[];
+    __shared__ __align__(256) TabEntry stab[256 / sizeof(TabEntry)];
+    __shared__ int red[2 * (THREADS / 32)];
+    __shared__ long long part[2][CS][2];   // CTA 0: each CTA's (dM, dB) of a sweep, by sweep parity
+    __shared__ long long cur_s[2];
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int lat = blockIdx.x / CS;
+    const LatDev ld = a.lats[lat];
+    const int L = ld.L, Lv = L >> 4, R = L / CS, y0 = rank * R;
+    // every CTA of the cluster holds the same lattice, so all return together
+    if (!SPIN_CK(L >= 16 && (L & 15) == 0 && L % CS == 0 && (unsigned)((R + 4) * L) <= dynamic_smem_bytes(), 114))
+        return;
+    uint4 *own = reinterpret_cast<uint4 *>(sm);               // [R][Lv]
+    uint4 *halo = own + R * Lv;                               // [2 buffers][top, bottom][Lv]
+    const uint32_t *own32 = reinterpret_cast<const uint32_t *>(sm);
+    const int up = (rank + CS - 1) % CS, dn = (rank + 1) % CS;
+    uint4 *up_halo = cl.map_shared_rank(halo, up);            // its bottom halo holds our first row
+    uint4 *dn_halo = cl.map_shared_rank(halo, dn);            // its top halo holds our last row
+    long long(*part0)[CS][2] = cl.map_shared_rank(part, 0);
+    const uint4 *G = reinterpret_cast<const uint4 *>(a.spins + ld.offset);
+    for (int v = threadIdx.x; v < R * Lv; v += THREADS) own[v] = to_x8(G[(size_t)y0 * Lv + v]);
+    for (int v = threadIdx.x; v < 2 * Lv; v += THREADS) {
+        const int y = v < Lv ? (y0 + L - 1) % L : (y0 + R) % L;
+        halo[v] = to_x8(G[(size_t)y * Lv + (v < Lv ? v : v - Lv)]);
+    }
+    if (threadIdx.x < kTabStride) stab[threadIdx.x] = a.tabs[lat * kTabStride + threadIdx.x];
+    if (rank == 0 && threadIdx.x < 2) cur_s[threadIdx.x] = a.st.cur[2 * lat + threadIdx.x];
+    const uint32_t tb = (uint32_t)__cvta_generic_to_shared(stab);
+    const int di = THREADS / Lv, dj = THREADS - di * Lv;
+    const int i0 = (int)threadIdx.x / Lv, j0 = (int)threadIdx.x - i0 * Lv;
+    // the CTA 0 side of the statistics: add the parts of sweep s to the running values
+    auto record = [&](int s) {
+        long long dm = 0, db = 0;
+        for (int r = 0; r < CS; ++r) {
+            dm += part[s & 1][r][0];
+            db += part[s & 1][r][1];
+        }
+        cur_s[0] += dm;
+        cur_s[1] += db;
+        if (a.record && a.st.cap > 0) {
+            const long long slot = (a.rec0 + s) % a.st.cap;
+            a.st.ring[(slot * a.st.n_lat + lat) * 2] = cur_s[0];
+            a.st.ring[(slot * a.st.n_lat + lat) * 2 + 1] = cur_s[1];
+        }
+    };
+    cl.sync();   // own rows, halos, table and running values in place in every CTA
+    for (int sweep = 0; sweep < a.n_sweeps; ++sweep) {
+        const uint32_t t = a.t0 + (uint32_t)sweep;
+        int acc = 0;
+        for (int c = 0; c < 2; ++c) {
+            const int b = c;   // k & 1 with k = 2 sweep + c
+            const uint4 *top = halo + (2 * b) * Lv, *bot = halo + (2 * b + 1) * Lv;
+            uint4 *up_dst = up_halo + (2 * (b ^ 1) + 1) * Lv, *dn_dst = dn_halo + (2 * (b ^ 1)) * Lv;
+            const PhiloxPrefix P = philox_prefix(ld.rng, t, (uint32_t)c, a.rk);
+            int i = i0, j = j0;
+            for (int v = threadIdx.x; v < R * Lv; v += THREADS) {
+                const int y = y0 + i, row = i * Lv;
+                const uint4 Cc = own[v];
+                const uint4 Uc = i == 0 ? top[j] : own[v - Lv];
+                const uint4 Dc = i == R - 1 ? bot[j] : own[v + Lv];
+                const uint32_t lw = own32[(row + (j == 0 ? Lv - 1 : j - 1)) * 4 + 3];
+                const uint32_t rw = own32[(row + (j == Lv - 1 ? 0 : j + 1)) * 4];
+                const uint32_t g0 = (uint32_t)y * (uint32_t)(L >> 3) + 2u * (uint32_t)j;
+                const uint4 nv = chunk_x8(Cc, Uc, Dc, lw, rw, philox_from_prefix(g0, P, a.rk),
+                                          philox_from_prefix(g0 + 1u, P, a.rk), row_par((c ^ y) & 1), tb, acc);
+                own[v] = nv;
+                if (i == 0) up_dst[j] = nv;
+                if (i == R - 1) dn_dst[j] = nv;
+                i += di;
+                j += dj;
+                if (j >= Lv) {
+                    j -= Lv;
+                    ++i;
+                }
+            }
+            if (c == 1) {
+                int dm = (int)(int16_t)(acc & 0xFFFF);
+                int db = (acc - dm) >> 16;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    dm += __shfl_xor_sync(0xFFFFFFFFu, dm, o);
+                    db += __shfl_xor_sync(0xFFFFFFFFu, db, o);
+                }
+                if ((threadIdx.x & 31) == 0) {
+                    red[2 * (threadIdx.x >> 5)] = dm;
+                    red[2 * (threadIdx.x >> 5) + 1] = db;
+                }
+            }
+            cl.sync();
+            // CTA 0: the parts of the previous sweep arrived before this barrier
+            if (c == 0 && sweep > 0 && rank == 0 && threadIdx.x == 0) record(sweep - 1);
+        }
+        if (threadIdx.x == 0) {   // this CTA's part of the sweep, into CTA 0
+            long long sm_ = 0, sb_ = 0;
+            for (int w = 0; w < THREADS / 32; ++w) {
+                sm_ += red[2 * w];
+                sb_ += red[2 * w + 1];
+            }
+            part0[sweep & 1][rank][0] = sm_;
+            part0[sweep & 1][rank][1] = sb_;
+        }
+    }
+    cl.sync();   // the last sweep's parts are in CTA 0
+    if (a.n_sweeps > 0 && rank == 0 && threadIdx.x == 0) record(a.n_sweeps - 1);
+    uint4 *Gw = reinterpret_cast<uint4 *>(a.spins + ld.offset);
+    for (int v = threadIdx.x; v < R * Lv; v += THREADS) {
+        const uint4 w = own[v];
+        Gw[(size_t)y0 * Lv + v] = make_uint4(from_x8(w.x), from_x8(w.y), from_x8(w.z), from_x8(w.w));
+    }
+    if (rank == 0) {
+        __syncthreads();
+        if (threadIdx.x < 2) a.st.cur[2 * lat + threadIdx.x] = cur_s[threadIdx.x];
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_copy_lattices(const void *src, void *dst, const LatDev *lats, int n_lat,
@@ -1351,6 +1490,37 @@ cudaError_t launch_ising_resident(const ResidentArgs &a, int n_lat, int threads,
             return cudaErrorInvalidValue;
     }
     if ((e = cudaGetLastError())) return e;
+    advance_state_kernel<<<1, 1, 0, s>>>(state, (uint32_t)a.n_sweeps, a.record);
+    return cudaGetLastError();
+}
+
+namespace {
+template <int THREADS, int CS>
+cudaError_t launch_resident_cluster(const ResidentArgs &a, int n_lat, size_t smem, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(ising_resident_cluster_kernel<THREADS, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)))
+        return e;
+    ising_resident_cluster_kernel<THREADS, CS><<<n_lat * CS, THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_ising_resident_cluster(const ResidentArgs &a, int n_lat, int threads, int cs, int max_l,
+                                          DevState *state, cudaStream_t s) {
+    if ((cs != 2 && cs != 4) || max_l < 16 || max_l % 16 != 0) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(max_l / cs + 4) * (size_t)max_l;
+    cudaError_t e;
+    switch (threads * 10 + cs) {
+        case 2562: e = launch_resident_cluster<256, 2>(a, n_lat, smem, s); break;
+        case 5122: e = launch_resident_cluster<512, 2>(a, n_lat, smem, s); break;
+        case 10242: e = launch_resident_cluster<1024, 2>(a, n_lat, smem, s); break;
+        case 2564: e = launch_resident_cluster<256, 4>(a, n_lat, smem, s); break;
+        case 5124: e = launch_resident_cluster<512, 4>(a, n_lat, smem, s); break;
+        case 10244: e = launch_resident_cluster<1024, 4>(a, n_lat, smem, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e) return e;
     advance_state_kernel<<<1, 1, 0, s>>>(state, (uint32_t)a.n_sweeps, a.record);
     return cudaGetLastError();
 }

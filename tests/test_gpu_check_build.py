@@ -39,9 +39,15 @@ for mode, threads in ((0, 512), (0, 256), (3, 256), (1, 256)):
         assert np.array_equal(st[:, i], ref), (mode, i)
     assert sm.check_status() == (True, 0), (mode, sm.check_status())
 small = [dict(L=L, beta=0.4, J=1.0, h=0.0) for L in (16, 32, 64, 128)]
-r = sm.Sim(sm.SPIN_ISING, small, seed=SEED, max_record=4)
-r.set_launch(2, False, 0, 256)
-r.sweep(3, record=True)
+for cs in (1, 2, 4):   # one CTA per lattice, or a cluster of 2 or 4
+    r = sm.Sim(sm.SPIN_ISING, small, seed=SEED, max_record=4)
+    r.set_launch(2, False, cs, 256)
+    init = [r.lattice(i).cpu().numpy().copy() for i in range(len(small))]
+    r.sweep(3, record=True)
+    for i, d in enumerate(small):
+        oracle.ising_run(init[i], d["beta"], d["J"], d["h"], SEED, i, 0, 3)
+        assert np.array_equal(r.lattice(i).cpu().numpy(), init[i]), (cs, i)
+    assert sm.check_status() == (True, 0), (cs, sm.check_status())
 potts = [dict(L=L, q=q, beta=1.0, J=1.0) for L, q in ((512, 3), (1024, 8), (64, 3), (48, 5))]
 ps = sm.Sim(sm.SPIN_POTTS, potts, seed=SEED, max_record=4)
 p0 = [ps.lattice(i).cpu().numpy().copy() for i in range(len(potts))]

@@ -108,6 +108,51 @@ def test_resident_form_matches_oracle_and_batched(threads):
     assert torch.equal(sim.current_stats(), sim.observables(10, 1)[0][0])
 
 
+@pytest.mark.parametrize("cs,threads", [(2, 256), (2, 1024), (4, 512), (4, 1024)])
+def test_resident_cluster_form_matches_oracle(cs, threads):
+    """Each lattice split over a cluster of cs CTAs (rows exchanged through
+    distributed shared memory): bit-identical to the oracle sweep by sweep,
+    over calls of several sweeps, and to the one-CTA resident form."""
+    lats = [dict(L=L, beta=b, J=J, h=h) for L, b, J, h in [
+        (16, 0.3, 1.0, 0.0), (32, 0.44, 1.0, 0.1), (64, 0.6, -1.0, 0.0), (128, 0.4, 0.8, -0.05),
+        (256, 0.5, 1.0, 0.02), (64, 0.2, 1.0, 0.0), (256, 0.44, 1.0, 0.0)]]
+    sim = make_ising(lats, max_record=32)
+    sim.set_launch(2, False, cs, threads)
+    assert sim.get_launch() == {"mode": 2, "use_graph": 0, "tile_rows": cs, "threads": threads}
+    ref = {i: lattice_np(sim, i) for i in range(len(lats))}
+    for t in range(2):
+        sim.sweep(1, record=True)
+        for i, d in enumerate(lats):
+            oracle.ising_sweep(ref[i], d["beta"], d["J"], d["h"], SEED, i, t)
+            assert np.array_equal(lattice_np(sim, i), ref[i]), (t, i)
+    sim.sweep(3, record=True)
+    sim.sweep(6, record=True)
+    st = sim.observables_host(0, 11)[0]
+    for i, d in enumerate(lats):
+        o = oracle.ising_run(ref[i], d["beta"], d["J"], d["h"], SEED, i, 2, 9)
+        assert np.array_equal(lattice_np(sim, i), ref[i]), i
+        assert np.array_equal(st[2:, i], o), i
+    other = make_ising(lats, max_record=32)
+    other.set_launch(2, True, -1, 512)
+    other.sweep(11, record=True)
+    assert torch.equal(other.spins, sim.spins)
+    assert np.array_equal(other.observables_host(0, 11)[0], st)
+    assert torch.equal(sim.current_stats(), sim.observables(10, 1)[0][0])
+
+
+def test_resident_cluster_form_in_a_graph_and_back():
+    """The cluster form replayed from a graph, then the batched form, continue one chain."""
+    lats = wl.fit256(n=6, L=256) + [dict(L=128, beta=0.3, J=1.0, h=0.1)]
+    a, b = make_ising(lats), make_ising(lats)
+    a.set_launch(2, True, 4, 1024)
+    a.sweep(5, record=True)
+    a.set_launch(0, True, -1, 512)
+    a.sweep(3, record=True)
+    b.sweep(8, record=True)
+    assert torch.equal(a.spins, b.spins)
+    assert np.array_equal(a.observables_host(0, 8)[0], b.observables_host(0, 8)[0])
+
+
 def test_launch_forms_bit_identical():
     lats = wl.uneven512(n=40, seed=3, emin=4, emax=9)
     finals = []
