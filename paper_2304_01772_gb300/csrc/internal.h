@@ -189,11 +189,6 @@ struct ResidentArgs {
 };
 cudaError_t launch_ising_resident(const ResidentArgs &a, int n_lat, int threads, size_t smem,
                                   DevState *state, cudaStream_t s);
-// The same with each lattice split over a cluster of cs CTAs (2 or 4), CTA r
-// holding rows [r L/cs, (r+1) L/cs); max_l: the largest side (a multiple of
-// 16 cs), which sizes the shared memory.
-cudaError_t launch_ising_resident_cluster(const ResidentArgs &a, int n_lat, int threads, int cs, int max_l,
-                                          DevState *state, cudaStream_t s);
 // The same for batches made only of triangular lattices (L <= 240).
 cudaError_t launch_ising_tri_resident(const ResidentArgs &a, int n_lat, size_t smem, DevState *state,
                                       cudaStream_t s);
@@ -471,5 +466,12 @@ cudaError_t launch_unpack_spins(const uint32_t *words, int8_t *spins, const LatD
                                 int64_t *cur, cudaStream_t s);
 cudaError_t launch_pack_spins(const int8_t *spins, uint32_t *words, size_t n_words, const LatDev *lats, int n_lat,
                               int maxL, cudaStream_t s);
+
+// The square-lattice resident form (launch_ising_resident) with each lattice
+// split over a thread-block cluster of cs CTAs (2 or 4), CTA r holding rows
+// [r L/cs, (r+1) L/cs); max_l: the largest side (a multiple of 16), which
+// sizes the shared memory.
+cudaError_t launch_ising_resident_cluster(const ResidentArgs &a, int n_lat, int threads, int cs, int max_l,
+                                          DevState *state, cudaStream_t s);
 
 }  // namespace spinmc
