@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--scaling", default="strong", choices=["strong", "weak"],
                     help="N > 1: split one batch over the ranks (strong) or give each rank the whole batch (weak)")
     ap.add_argument("--workload", default="uneven512",
-                    choices=["uneven512", "potts_q3", "potts_q8", "cpm1024", "ising_small", "grad", "mlp", "dmc",
+                    choices=["uneven512", "potts_q3", "potts_q8", "cpm1024", "ising_small", "few256", "grad", "mlp", "dmc",
                              "spinglass", "cpm_batch", "triangular", "nnn", "fit", "rng"])
     return ap.parse_args()
 
@@ -228,6 +228,12 @@ def cpu_oracle_pool(fn, tasks, cores):
     return units / wall, units, wall
 
 
+def few256():
+    """16 Ising lattices 256^2 across the critical point: a batch of fewer
+    lattices than SMs (the resident form can split each over a cluster)."""
+    return [dict(L=256, beta=0.3 + 0.25 * k / 15, J=1.0, h=0.0) for k in range(16)]
+
+
 def cpu_baseline_secondary(workload, cores):
     """The oracle on a bounded sample of a secondary workload (before any GPU call)."""
     import numpy as np
@@ -273,6 +279,11 @@ def cpu_baseline_secondary(workload, cores):
         rate, units, wall = cpu_oracle_pool(_oracle_nnn, [(b * per, per) for b in range(cores)], cores)
         return {"value": rate, "unit": "site-updates/s", "cores": cores, "kind": "oracle",
                 "sample": f"{per * cores} of the 256 lattices, one sweep each ({wall:.1f} s wall)"}
+    if workload == "few256":
+        lats = few256()
+        rate, units, wall = cpu_oracle_rate(lats, 40, min(cores, len(lats)))
+        return {"value": rate, "unit": "site-updates/s", "cores": min(cores, len(lats)), "kind": "oracle",
+                "sample": f"the 16 lattices x 40 sweeps ({wall:.1f} s wall)"}
     if workload == "ising_small":
         lats = wl.ising_small()
         rate, units, wall = cpu_oracle_rate(lats, 1000, min(cores, len(lats)))
@@ -856,6 +867,7 @@ def run_secondary(args):
     potts_q3 / potts_q8: 64 Potts lattices 1024^2 at beta_c(q) * [0.8, 1.2];
     cpm1024: cellular Potts 1024^2, 2000 cells (a step = one Monte Carlo step);
     ising_small: 8 Ising lattices 64^2, statistics recorded every sweep;
+    few256: 16 Ising lattices 256^2, statistics recorded every sweep;
     grad: the fluctuation-estimator gradient over recorded statistics;
     mlp: one training step of the BF16 surrogate."""
     cpu = None if args.no_cpu else cpu_baseline_secondary(args.workload, os.cpu_count() or 1)
@@ -911,6 +923,12 @@ def run_secondary(args):
                               T=p["T"], side=p["side"], cols=p["cols"]))
         units, unit = p["L"] ** 2, "copy-attempts/s"
         desc = "cellular Potts 1024^2, 2000 cells of 20x20, J=[[0,16,16],[16,2,11],[16,11,14]], A=400, lambda=1, T=10"
+    elif args.workload == "few256":
+        lats = few256()
+        sim = sm.Sim(sm.SPIN_ISING, lats, seed=SEED, max_record=args.steps)
+        units, unit = wl.site_count(lats), "site-updates/s"
+        record = True
+        desc = "16 Ising lattices 256^2, beta = linspace(0.3, 0.55, 16), J = 1, h = 0, E and M recorded every sweep"
     else:
         lats = wl.ising_small()
         sim = sm.Sim(sm.SPIN_ISING, lats, seed=SEED, max_record=args.steps)
