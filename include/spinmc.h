@@ -260,6 +260,19 @@ int spin_store_spins(spin_ctx *ctx, void *host, void *stream);
 int32_t spin_packed_words(const spin_ctx *ctx);
 int spin_load_spins_packed(spin_ctx *ctx, const uint32_t *host, void *stream);
 int spin_store_spins_packed(spin_ctx *ctx, uint32_t *host, void *stream);
+/* One host-to-host job in one call: spin_load_spins_packed(host_in) (skipped
+ * when host_in is NULL), spin_sweep(n_sweeps, record), then
+ * spin_store_spins_packed(host_out) (skipped when host_out is NULL), with the
+ * same spins, statistics, records and sweep counter as those three calls.
+ * With an odd n_sweeps in launch mode 0 or 3 the loaded state is unpacked
+ * into the context's ping-pong buffer, so the last sweep lands in the
+ * caller's spin buffer and the copy that ends an odd spin_sweep call is not
+ * needed.  host_in / host_out: pinned host memory for asynchronous copies,
+ * spin_packed_words(ctx) words each; asynchronous on the stream.  Errors as
+ * the three calls (SPIN_EINVAL for non-Ising contexts or offsets % 32 != 0).
+ * Not in the paper.                                                        */
+int spin_sweep_packed(spin_ctx *ctx, const uint32_t *host_in, uint32_t *host_out, int32_t n_sweeps,
+                      int32_t record, void *stream);
 
 /* Checkpoint = (sweep counter, record count, CPM areas, spins).  With
  * host_blob == NULL, *size receives the size needed. Restoring into a

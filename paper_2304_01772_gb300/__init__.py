@@ -75,6 +75,7 @@ _SIGS = {
     "spin_packed_words": (_i32, [_vp]),
     "spin_load_spins_packed": (_i32, [_vp, _vp, _vp]),
     "spin_store_spins_packed": (_i32, [_vp, _vp, _vp]),
+    "spin_sweep_packed": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp]),
     "spin_sweep_index": (ctypes.c_uint32, [_vp]),
     "spin_gpu_launches": (_i32, [_vp]),
     "spin_last_error": (ctypes.c_char_p, [_vp]),
@@ -408,6 +409,13 @@ class Sim:
     def store_spins_packed(self, host, stream=None):
         _check(lib().spin_store_spins_packed(self.ctx, _ptr(host), _stream(stream)), self.ctx,
                "spin_store_spins_packed")
+
+    def sweep_packed(self, host_in, host_out, n=1, record=False, stream=None):
+        """load_spins_packed(host_in) + sweep(n, record) + store_spins_packed(host_out)
+        in one call (either buffer may be None)."""
+        _check(lib().spin_sweep_packed(self.ctx, None if host_in is None else _ptr(host_in),
+                                       None if host_out is None else _ptr(host_out), int(n),
+                                       1 if record else 0, _stream(stream)), self.ctx, "spin_sweep_packed")
 
     def checkpoint(self, stream=None):
         size = ctypes.c_size_t(0)

@@ -755,7 +755,11 @@ int get_graph(spin_ctx *ctx, int record, int kind, GraphCache *&out) {
     return SPIN_OK;
 }
 
-int run_sweeps(spin_ctx *ctx, int n, int record, cudaStream_t s) {
+// from_tmp (n odd, launch modes 0 and 3): the state to sweep is in the
+// ping-pong buffer, so the first sweep goes from it into the caller's buffer
+// and the rest pair up as usual: the call ends in the caller's buffer with no
+// copy.
+int run_sweeps(spin_ctx *ctx, int n, int record, cudaStream_t s, bool from_tmp = false) {
     int launches = 0;
     if (ctx->model == SPIN_CPM && ctx->mode == 2) {
         CpmPersistArgs p{};
@@ -813,6 +817,11 @@ int run_sweeps(spin_ctx *ctx, int n, int record, cudaStream_t s) {
         return SPIN_OK;
     }
     int i = 0;
+    if (from_tmp) {
+        int rc = launch_sweep(ctx, ctx->spins2, ctx->spins, record, s, launches, sweep_layout(ctx, 0, n));
+        if (rc) return rc;
+        i = 1;
+    }
     if (ctx->use_graph && !ctx->prof && n >= 2) {
         const bool sp = split_rows(ctx);
         for (; i + 1 < n; i += 2) {
@@ -824,13 +833,13 @@ int run_sweeps(spin_ctx *ctx, int n, int record, cudaStream_t s) {
         }
     }
     for (; i < n; ++i) {
-        const bool even = (i & 1) == 0;
+        const bool even = ((i + (from_tmp ? 1 : 0)) & 1) == 0;
         void *src = ctx->mode == 1 ? ctx->spins : (even ? ctx->spins : ctx->spins2);
         void *dst = ctx->mode == 1 ? ctx->spins : (even ? ctx->spins2 : ctx->spins);
         int rc = launch_sweep(ctx, src, dst, record, s, launches, sweep_layout(ctx, i, n));
         if (rc) return rc;
     }
-    if (ctx->mode != 1 && (n & 1)) {
+    if (ctx->mode != 1 && (n & 1) && !from_tmp) {
         CK(launch_copy_lattices(ctx->spins2, ctx->spins, ctx->d_lats, ctx->n_lat, (int)ctx->elem, s));
         ++launches;
     }
@@ -1431,24 +1440,34 @@ static int packed_ready(spin_ctx *ctx) {
     return SPIN_OK;
 }
 
+static bool all_square(const spin_ctx *ctx) {
+    for (const auto &d : ctx->lat)
+        if (d.geometry != 0) return false;
+    return true;
+}
+
+// Upload one bit per spin and unpack it into `target` (the caller's buffer
+// or the ping-pong buffer), with the running statistics of the loaded state.
+static int load_packed_into(spin_ctx *ctx, const uint32_t *host, void *target, cudaStream_t s) {
+    const size_t nw = (ctx->span_elems + 31) / 32;
+    CK(cudaMemcpyAsync(ctx->d_packed, host, sizeof(uint32_t) * nw, cudaMemcpyHostToDevice, s));
+    // square lattices: the statistics of the loaded state are counted from the bits
+    // while unpacking; other geometries are recounted from the unpacked state
+    const bool square = all_square(ctx);
+    CK(launch_unpack_spins(ctx->d_packed, static_cast<int8_t *>(target), ctx->d_lats, ctx->n_lat, ctx->maxL,
+                           square ? ctx->st.cur : nullptr, s));
+    if (!square)
+        CK(launch_stats_from_state(target, ctx->model, ctx->d_lats, ctx->n_lat, ctx->maxL, ctx->width,
+                                   ctx->d_type, ctx->n_types, ctx->d_vol[0], ctx->n_cells, ctx->target, ctx->st.cur, s));
+    return SPIN_OK;
+}
+
 int spin_load_spins_packed(spin_ctx *ctx, const uint32_t *host, void *stream) {
     Range range_("spin_load_spins_packed");
     if (!ctx || !host) return SPIN_EINVAL;
     int rc = packed_ready(ctx);
     if (rc) return rc;
-    cudaStream_t s = S(stream);
-    const size_t nw = (ctx->span_elems + 31) / 32;
-    CK(cudaMemcpyAsync(ctx->d_packed, host, sizeof(uint32_t) * nw, cudaMemcpyHostToDevice, s));
-    // square lattices: the statistics of the loaded state are counted from the bits
-    // while unpacking; other geometries are recounted from the unpacked state
-    bool square = true;
-    for (const auto &d : ctx->lat) square = square && d.geometry == 0;
-    CK(launch_unpack_spins(ctx->d_packed, static_cast<int8_t *>(ctx->spins), ctx->d_lats, ctx->n_lat, ctx->maxL,
-                           square ? ctx->st.cur : nullptr, s));
-    if (!square)
-        CK(launch_stats_from_state(ctx->spins, ctx->model, ctx->d_lats, ctx->n_lat, ctx->maxL, ctx->width,
-                                   ctx->d_type, ctx->n_types, ctx->d_vol[0], ctx->n_cells, ctx->target, ctx->st.cur, s));
-    return SPIN_OK;
+    return load_packed_into(ctx, host, ctx->spins, S(stream));
 }
 
 int spin_store_spins_packed(spin_ctx *ctx, uint32_t *host, void *stream) {
@@ -1461,6 +1480,34 @@ int spin_store_spins_packed(spin_ctx *ctx, uint32_t *host, void *stream) {
     CK(launch_pack_spins(static_cast<const int8_t *>(ctx->spins), ctx->d_packed, nw, ctx->d_lats, ctx->n_lat,
                          ctx->maxL, s));
     CK(cudaMemcpyAsync(host, ctx->d_packed, sizeof(uint32_t) * nw, cudaMemcpyDeviceToHost, s));
+    return SPIN_OK;
+}
+
+int spin_sweep_packed(spin_ctx *ctx, const uint32_t *host_in, uint32_t *host_out, int32_t n_sweeps, int32_t record,
+                      void *stream) {
+    Range range_("spin_sweep_packed");
+    if (!ctx) return SPIN_EINVAL;
+    int rc = packed_ready(ctx);
+    if (rc) return rc;
+    if (n_sweeps < 0) return fail(ctx, SPIN_EINVAL, "negative sweep count");
+    if ((uint64_t)ctx->t + (uint64_t)n_sweeps >= 0xFFFFFFFEull)
+        return fail(ctx, SPIN_ESTATE, "sweep counter would reach the values reserved for initialisation");
+    if (record && n_sweeps > 0 && ctx->st.cap <= 0) return fail(ctx, SPIN_ESTATE, "no record ring (max_record_sweeps = 0)");
+    cudaStream_t s = S(stream);
+    // an odd number of sweeps in a ping-pong launch form: unpack into the
+    // ping-pong buffer, so that the last sweep lands in the caller's buffer
+    const bool tmp = host_in && (n_sweeps & 1) && (ctx->mode == 0 || ctx->mode == 3);
+    if (host_in) {
+        rc = load_packed_into(ctx, host_in, tmp ? ctx->spins2 : ctx->spins, s);
+        if (rc) return rc;
+    }
+    if (n_sweeps > 0) {
+        rc = run_sweeps(ctx, n_sweeps, record ? 1 : 0, s, tmp);
+        if (rc) return rc;
+        ctx->t += (uint32_t)n_sweeps;
+        if (record) ctx->n_rec += n_sweeps;
+    }
+    if (host_out) return spin_store_spins_packed(ctx, host_out, stream);
     return SPIN_OK;
 }
 

@@ -726,3 +726,52 @@ def test_bit_packed_transfer():
     for i in range(len(lats)):
         assert np.array_equal(lattice_np(sim, i), out[i]), i
         assert np.array_equal(st[:, i, :], stats[i]), i
+
+
+@pytest.mark.parametrize("mode,graph,n", [(0, True, 1), (0, True, 2), (0, True, 3), (0, False, 3), (3, True, 1),
+                                          (2, True, 1)])
+def test_sweep_packed_equals_load_sweep_store(mode, graph, n):
+    """spin_sweep_packed (upload, n sweeps, download in one call; an odd n in a
+    ping-pong form starts from the other buffer and needs no final copy) gives
+    the bits, spins, records and counter of load + sweep + store, and the
+    oracle's chain from the loaded state."""
+    lats = ([dict(L=L, beta=b, J=1.0, h=h) for L, b, h in [(16, 0.3, 0.0), (64, 0.44, 0.05), (128, 0.5, 0.0),
+                                                            (256, 0.4, -0.02)]] if mode == 2 else
+            [dict(L=L, beta=b, J=1.0, h=h) for L, b, h in [(512, 0.44, 0.0), (16, 0.3, 0.1), (1024, 0.5, -0.02),
+                                                            (10, 0.4, 0.0), (64, 0.6, 0.0), (2048, 0.35, 0.01)]])
+    a, b = make_ising(lats, max_record=8), make_ising(lats, max_record=8)
+    for x in (a, b):
+        x.set_launch(mode, graph, -1, 512)
+        x.sweep(2, record=True)
+    nw = a.packed_words
+    rng = np.random.default_rng(31 + n)
+    bits = torch.from_numpy(rng.integers(-2 ** 31, 2 ** 31, nw, dtype=np.int64).astype(np.int32)).pin_memory()
+    out_a = torch.zeros(nw, dtype=torch.int32).pin_memory()
+    out_b = torch.ones(nw, dtype=torch.int32).pin_memory()
+    a.load_spins_packed(bits)
+    loaded = {i: lattice_np(a, i) for i in range(len(lats))}
+    a.sweep(n, record=True)
+    a.store_spins_packed(out_a)
+    b.sweep_packed(bits, out_b, n, record=True)
+    torch.cuda.synchronize()
+    assert torch.equal(out_a, out_b)
+    assert torch.equal(a.spins, b.spins)
+    assert a.t == b.t == 2 + n and a.n_records == b.n_records == 2 + n
+    assert np.array_equal(a.observables_host(2, n)[0], b.observables_host(2, n)[0])
+    assert torch.equal(a.current_stats(), b.current_stats())
+    st = b.observables_host(2, n)[0]
+    for i in (0, 1, len(lats) - 1):
+        d, s = lats[i], loaded[i].copy()
+        ref = oracle.ising_run(s, d["beta"], d["J"], d["h"], SEED, i, 2, n)
+        assert np.array_equal(lattice_np(b, i), s), i
+        assert np.array_equal(st[:, i], ref), i
+
+
+def test_sweep_packed_without_buffers_is_a_sweep():
+    lats = MIXED[:6]
+    a, b = make_ising(lats, max_record=4), make_ising(lats, max_record=4)
+    a.sweep(3, record=True)
+    b.sweep_packed(None, None, 3, record=True)
+    torch.cuda.synchronize()
+    assert torch.equal(a.spins, b.spins)
+    assert np.array_equal(a.observables_host(0, 3)[0], b.observables_host(0, 3)[0])
