@@ -118,7 +118,8 @@ struct spin_ctx {
     void *d_scratch = nullptr;  // moments etc.
     size_t scratch_bytes = 0;
     int *d_flag = nullptr;
-    uint32_t *d_packed = nullptr;   // bit-packed transfer buffer (allocated at first use)      // [0] moment overflow, [1] a device wait gave up
+    uint32_t *d_packed = nullptr;   // bit-packed transfer buffer (allocated at first use)
+    uint32_t *d_packed2 = nullptr;  // second one: spin_sweep_packed's output bits      // [0] moment overflow, [1] a device wait gave up
     // host mirrors
     uint32_t t = 0;
     int64_t n_rec = 0;
@@ -533,7 +534,8 @@ void prof_end(spin_ctx *ctx, cudaStream_t s) {
 }
 
 // One sweep of Ising/Potts lattices, src -> dst (batched) or in place (plain).
-int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s, int &launches, int layout) {
+int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s, int &launches, int layout,
+                 const uint32_t *src_bits = nullptr, uint32_t *dst_bits = nullptr) {
     const int w = ctx->width;
     if (ctx->mode == 1) {
         for (int c = 0; c < 2; ++c) {
@@ -669,7 +671,7 @@ int launch_sweep(spin_ctx *ctx, void *src, void *dst, int record, cudaStream_t s
                 IsingSweepArgs a{ctx->d_strip, ctx->n_strip, ctx->d_lats, ctx->d_tabs,
                                  static_cast<const int8_t *>(src), static_cast<int8_t *>(dst),
                                  ctx->k0, ctx->k1, ctx->d_state, ctx->st.delta,
-                                 philox_keys(ctx->k0, ctx->k1), ctx->n_lat};
+                                 philox_keys(ctx->k0, ctx->k1), ctx->n_lat, src_bits, dst_bits};
                 CK(launch_ising_strip(a, ctx->strip_grid, ctx->strip_warps, layout, s));
             } else {
                 PottsStripArgs a{ctx->d_strip, ctx->n_strip, ctx->d_lats, ctx->d_tabs,
@@ -925,7 +927,7 @@ void spin_destroy(spin_ctx *ctx) {
                     ctx->d_dvol[0], ctx->d_dvol[1],
                     ctx->d_state, ctx->st.cur, ctx->st.delta, ctx->st.ring, ctx->d_type,
                     ctx->d_J, ctx->d_vol[0], ctx->d_vol[1], ctx->d_thr, ctx->d_latp,
-                    ctx->d_cpmJ, ctx->d_scratch, ctx->d_flag, ctx->d_cpm_acc, ctx->d_cpm_bar, ctx->d_packed};
+                    ctx->d_cpmJ, ctx->d_scratch, ctx->d_flag, ctx->d_cpm_acc, ctx->d_cpm_bar, ctx->d_packed, ctx->d_packed2};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -1446,6 +1448,16 @@ static bool all_square(const spin_ctx *ctx) {
     return true;
 }
 
+// spin_sweep_packed's one-sweep path with the strip kernel's bit layouts:
+// square Ising lattices in the batched form, every strip lattice's packed rows
+// on 16-byte boundaries.
+static bool bits_path_ok(const spin_ctx *ctx) {
+    if (ctx->model != SPIN_ISING || ctx->mode != 0 || !ctx->n_strip || !all_square(ctx)) return false;
+    for (const auto &d : ctx->lat)
+        if ((d.L == 512 || d.L == 1024 || d.L == 2048) && d.spin_offset % 128) return false;
+    return true;
+}
+
 // Upload one bit per spin and unpack it into `target` (the caller's buffer
 // or the ping-pong buffer), with the running statistics of the loaded state.
 static int load_packed_into(spin_ctx *ctx, const uint32_t *host, void *target, cudaStream_t s) {
@@ -1494,6 +1506,33 @@ int spin_sweep_packed(spin_ctx *ctx, const uint32_t *host_in, uint32_t *host_out
         return fail(ctx, SPIN_ESTATE, "sweep counter would reach the values reserved for initialisation");
     if (record && n_sweeps > 0 && ctx->st.cap <= 0) return fail(ctx, SPIN_ESTATE, "no record ring (max_record_sweeps = 0)");
     cudaStream_t s = S(stream);
+    if (host_in && host_out && n_sweeps == 1 && bits_path_ok(ctx)) {
+        // One sweep between the transfers: the strip kernel reads its lattices'
+        // rows from the uploaded bits and writes their bits beside the int8 rows;
+        // only the other lattices are unpacked (into the ping-pong buffer, which
+        // the sweep reads) and packed; the loaded state's statistics are counted
+        // from all the bits.
+        const size_t nw = (ctx->span_elems + 31) / 32;
+        if (!ctx->d_packed2 && cudaMalloc(&ctx->d_packed2, sizeof(uint32_t) * nw) != cudaSuccess) {
+            ctx->d_packed2 = nullptr;
+            return fail(ctx, SPIN_ENOMEM, "packed transfer buffer");
+        }
+        CK(cudaMemcpyAsync(ctx->d_packed, host_in, sizeof(uint32_t) * nw, cudaMemcpyHostToDevice, s));
+        CK(launch_unpack_spins(ctx->d_packed, static_cast<int8_t *>(ctx->spins2), ctx->d_lats, ctx->n_lat, ctx->maxL,
+                               ctx->st.cur, s, true));
+        CK(cudaMemsetAsync(ctx->d_packed2, 0, sizeof(uint32_t) * nw, s));
+        int launches = 0;
+        rc = launch_sweep(ctx, ctx->spins2, ctx->spins, record ? 1 : 0, s, launches, kSrcBits | kDstBits,
+                          ctx->d_packed, ctx->d_packed2);
+        if (rc) return rc;
+        ctx->last_launches = launches;
+        ctx->t += 1;
+        if (record) ctx->n_rec += 1;
+        CK(launch_pack_spins(static_cast<const int8_t *>(ctx->spins), ctx->d_packed2, nw, ctx->d_lats, ctx->n_lat,
+                             ctx->maxL, s, true));
+        CK(cudaMemcpyAsync(host_out, ctx->d_packed2, sizeof(uint32_t) * nw, cudaMemcpyDeviceToHost, s));
+        return SPIN_OK;
+    }
     // an odd number of sweeps in a ping-pong launch form: unpack into the
     // ping-pong buffer, so that the last sweep lands in the caller's buffer
     const bool tmp = host_in && (n_sweeps & 1) && (ctx->mode == 0 || ctx->mode == 3);

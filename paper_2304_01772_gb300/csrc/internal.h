@@ -146,6 +146,10 @@ struct IsingSweepArgs {
     int64_t *delta;   // [n_lat][2]
     PhiloxKeys rk;
     int n_lat;        // entries of lats (work-list checks of SPIN_CHECK builds)
+    // strip kernel, layouts with kSrcBits / kDstBits: one bit per spin (1 = -1),
+    // element e at bit e % 32 of word e / 32 (the bit-packed host format)
+    const uint32_t *src_bits;
+    uint32_t *dst_bits;
 };
 
 cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, size_t smem,
@@ -156,6 +160,12 @@ cudaError_t launch_ising_fused(const IsingSweepArgs &a, int grid, int threads, s
 // of a row, then the odd-x half; Ising one byte 8 [s < 0] per site, Potts the
 // state bytes); kDstSplit: the destination rows are written in it.
 constexpr int kSrcSplit = 1, kDstSplit = 2;
+// Strip kernel only: kSrcBits: the strip lattices' source rows are read from
+// src_bits (one bit per spin; lattice offsets multiples of 128) instead of
+// src; kDstBits: each finished row is also written to dst_bits, beside its
+// int8 row in dst.  Used together, for a sweep between two bit-packed
+// transfers (spin_sweep_packed).
+constexpr int kSrcBits = 4, kDstBits = 8;
 // Warp-per-row-strip kernel for L in {512, 1024, 2048}; items are row blocks.
 cudaError_t launch_ising_strip(const IsingSweepArgs &a, int grid, int warps, int layout, cudaStream_t s);
 cudaError_t launch_ising_plain(int8_t *spins, const LatDev *lat_dev, int lat, uint32_t rng, int L,
@@ -462,10 +472,13 @@ cudaError_t launch_dmc_step(const DmcStepArgs &a, cudaStream_t s);
 // the loaded state's statistics into cur [n_lat][2] = (M, B) of square lattices
 // when cur is not null / pack them into
 // words (bits outside the lattices 0).  Lattice offsets are multiples of 32.
+// skip_strip: lattices of side 512, 1024 or 2048 are left to the strip
+// kernel's bit layouts (unpack: their statistics are still counted; pack:
+// their words are not written, nor cleared: the caller clears the buffer).
 cudaError_t launch_unpack_spins(const uint32_t *words, int8_t *spins, const LatDev *lats, int n_lat, int maxL,
-                                int64_t *cur, cudaStream_t s);
+                                int64_t *cur, cudaStream_t s, bool skip_strip = false);
 cudaError_t launch_pack_spins(const int8_t *spins, uint32_t *words, size_t n_words, const LatDev *lats, int n_lat,
-                              int maxL, cudaStream_t s);
+                              int maxL, cudaStream_t s, bool skip_strip = false);
 
 // The square-lattice resident form (launch_ising_resident) with each lattice
 // split over a thread-block cluster of cs CTAs (2 or 4), CTA r holding rows

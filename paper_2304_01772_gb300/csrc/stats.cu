@@ -505,10 +505,15 @@ __device__ __forceinline__ uint32_t nibble_bytes(uint32_t n) {
     return 0x01010101u + spread * 0xFEu;
 }
 
+// Sides the row-strip kernel takes (with skip_strip, the pack and unpack
+// kernels leave those lattices' spins to the strip kernel's bit layouts).
+__device__ __forceinline__ bool strip_side(int L) { return L == 512 || L == 1024 || L == 2048; }
+
 // One thread per 32-bit word of the packed buffer overlapping lattice
 // blockIdx.y (offsets are multiples of 32, so no word holds two lattices).
-__global__ void pack_spins_kernel(const int8_t *spins, uint32_t *words, const LatDev *lats) {
+__global__ void pack_spins_kernel(const int8_t *spins, uint32_t *words, const LatDev *lats, int skip_strip) {
     const LatDev ld = lats[blockIdx.y];
+    if (skip_strip && strip_side(ld.L)) return;
     const size_t o = ld.offset, end = o + (size_t)ld.L * ld.L;
     for (size_t w = (o >> 5) + blockIdx.x * (size_t)blockDim.x + threadIdx.x; (w << 5) < end;
          w += (size_t)gridDim.x * blockDim.x) {
@@ -537,11 +542,13 @@ __device__ __forceinline__ int packed_bit(const uint32_t *words, size_t e) { ret
 // by one with bit 0 of the next word of the row (or of the row's first word),
 // its down neighbours the word of the next row, and unequal pairs are popcounts
 // of xors.  Other sides count bond by bond.
-__global__ void unpack_spins_kernel(const uint32_t *words, int8_t *spins, const LatDev *lats, int64_t *cur) {
+__global__ void unpack_spins_kernel(const uint32_t *words, int8_t *spins, const LatDev *lats, int64_t *cur,
+                                    int skip_strip) {
     __shared__ long long red[2][8];
     const int lat = blockIdx.y;
     const LatDev ld = lats[lat];
     const int L = ld.L;
+    const bool write = !(skip_strip && strip_side(L));   // else statistics only
     const size_t o = ld.offset, end = o + (size_t)L * L;
     const bool rows_whole = (L & 31) == 0;
     const int wpr = L >> 5;   // words per row when rows_whole
@@ -563,7 +570,8 @@ __global__ void unpack_spins_kernel(const uint32_t *words, int8_t *spins, const 
         const size_t w = (o >> 5) + wl;
         const size_t e0 = w << 5;
         const uint32_t bits = words[w];
-        if (e0 + 32 <= end && ((reinterpret_cast<uintptr_t>(spins + e0) & 15) == 0)) {
+        if (!write) {
+        } else if (e0 + 32 <= end && ((reinterpret_cast<uintptr_t>(spins + e0) & 15) == 0)) {
             uint32_t v[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) v[k] = nibble_bytes((bits >> (4 * k)) & 0xFu);
@@ -622,24 +630,26 @@ __global__ void unpack_spins_kernel(const uint32_t *words, int8_t *spins, const 
 }  // namespace
 
 cudaError_t launch_unpack_spins(const uint32_t *words, int8_t *spins, const LatDev *lats, int n_lat, int maxL,
-                                int64_t *cur, cudaStream_t s) {
+                                int64_t *cur, cudaStream_t s, bool skip_strip) {
     if (cur) {
         cudaError_t e = cudaMemsetAsync(cur, 0, sizeof(int64_t) * 2 * (size_t)n_lat, s);
         if (e) return e;
     }
     const int wpl = (int)(((size_t)maxL * maxL + 31) / 32) + 1;
     dim3 grid((wpl + 255) / 256 < 64 ? (wpl + 255) / 256 : 64, n_lat);
-    unpack_spins_kernel<<<grid, 256, 0, s>>>(words, spins, lats, cur);
+    unpack_spins_kernel<<<grid, 256, 0, s>>>(words, spins, lats, cur, skip_strip ? 1 : 0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack_spins(const int8_t *spins, uint32_t *words, size_t n_words, const LatDev *lats, int n_lat,
-                              int maxL, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(words, 0, n_words * sizeof(uint32_t), s);
-    if (e) return e;
+                              int maxL, cudaStream_t s, bool skip_strip) {
+    if (!skip_strip) {   // with skip_strip the caller has cleared the words before the strip kernel wrote its own
+        cudaError_t e = cudaMemsetAsync(words, 0, n_words * sizeof(uint32_t), s);
+        if (e) return e;
+    }
     const int wpl = (int)(((size_t)maxL * maxL + 31) / 32) + 1;
     dim3 grid((wpl + 255) / 256 < 64 ? (wpl + 255) / 256 : 64, n_lat);
-    pack_spins_kernel<<<grid, 256, 0, s>>>(spins, words, lats);
+    pack_spins_kernel<<<grid, 256, 0, s>>>(spins, words, lats, skip_strip ? 1 : 0);
     return cudaGetLastError();
 }
 

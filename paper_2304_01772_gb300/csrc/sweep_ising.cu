@@ -769,6 +769,69 @@ __device__ __forceinline__ void split_row(uint32_t src, uint32_t dst, int L, int
     }
 }
 
+// Bit-packed rows (one bit per spin, 1 = -1; site x of a row is bit x % 32 of
+// the row's word x / 32).  Row y of L bits is L / 128 chunks of 16 bytes.
+__device__ __forceinline__ void issue_bits_s(uint32_t dst, const uint4 *Sb, int y, int L, int lane) {
+    const uint4 *src = Sb + (size_t)y * (L >> 7);
+    if (lane < (L >> 7))
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16u * (uint32_t)lane), "l"(src + lane)
+                     : "memory");
+}
+
+// Packed row at src -> split x8 row at dst.  Byte i of packed word m holds
+// sites 32 m + 8 i .. + 7; its even sites are bytes 0..3 of word 4 m + i of
+// half 0, its odd sites those of half 1: lut[byte] = (even word, odd word).
+__device__ __forceinline__ void bits_to_split(uint32_t src, uint32_t dst, int L, int lane, uint32_t lut) {
+#pragma unroll 1
+    for (int m = lane; m < (L >> 5); m += 32) {
+        const uint32_t W = sld1(src + 4u * (uint32_t)m);
+        Words<4> e, o;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint2 t = lds_u2(lut + 8u * ((W >> (8 * i)) & 0xFFu));
+            e.w[i] = t.x;
+            o.w[i] = t.y;
+        }
+        stw<4>(dst, m, e);
+        stw<4>(dst + (uint32_t)(L >> 1), m, o);
+    }
+}
+
+// The lookup table of bits_to_split: entry b = (x8 bytes of bits 0, 2, 4, 6 of
+// b, x8 bytes of bits 1, 3, 5, 7 of b).
+__device__ __forceinline__ uint2 bits_lut_entry(uint32_t b) {
+    uint32_t e = 0, o = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        e |= ((b >> (2 * j)) & 1u) << (8 * j + 3);
+        o |= ((b >> (2 * j + 1)) & 1u) << (8 * j + 3);
+    }
+    return make_uint2(e, o);
+}
+
+// Eight sites as one byte of packed bits: e, o are x8 words of the even and
+// odd sites of the same half-row position (bit 3 of each byte); z has site
+// 2 j + s at bit 8 j + 3 + s, and the product with 1 + 2^6 + 2^12 + 2^18 puts
+// it at bit 21 + 2 j + s (all other partial products land outside bits 21..28
+// and on distinct positions, so nothing carries).
+__device__ __forceinline__ uint32_t x8_pair_byte(uint32_t e, uint32_t o) {
+    return ((e + (o << 1)) * 0x00041041u >> 21) & 0xFFu;
+}
+
+// Final row chunk c (half words NW c .. NW c + NW - 1 of both halves) as bits:
+// NW = 4: packed word c of the row; NW = 2: its 16-bit half c.
+template <int NW>
+__device__ __forceinline__ void store_bits(uint32_t *Db, int y, int L, int c, const Words<NW> &h0,
+                                           const Words<NW> &h1) {
+    uint32_t v = 0;
+#pragma unroll
+    for (int i = 0; i < NW; ++i) v |= x8_pair_byte(h0.w[i], h1.w[i]) << (8 * i);
+    if constexpr (NW == 4)
+        Db[(size_t)y * (L >> 5) + c] = v;
+    else
+        reinterpret_cast<uint16_t *>(Db)[(size_t)y * (L >> 4) + c] = (uint16_t)v;
+}
+
 // Metropolis update of the active words `act` given the other half's words
 // `oth` (plus `edge`, the other-half word just outside the chunk: before it
 // for p = 0, after it for p = 1), the aligned words of the rows above and
@@ -828,7 +891,10 @@ __device__ __forceinline__ void store_split(unsigned char *Drow, int hp, int ho,
 struct Walk {
     const uint4 *S;
     uint4 *D;
+    const uint4 *Sb;   // kSrcBits: the lattice's packed rows
+    uint32_t *Db;      // kDstBits: the lattice's packed rows
     uint32_t ring;   // shared address of this warp's 5 * L bytes: 4 split rows + landing
+    uint32_t lut;    // kSrcBits: shared address of the bits_to_split table
     int L, r0, nrows, lane;
     PhiloxPrefix P0, P1;
     uint32_t tab_cnt, tab_halo;
@@ -840,11 +906,30 @@ struct Walk {
 template <int NW, int LAYOUT>
 __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
     constexpr bool kSrcS = (LAYOUT & kSrcSplit) != 0, kDstS = (LAYOUT & kDstSplit) != 0;
+    constexpr bool kSrcB = (LAYOUT & kSrcBits) != 0, kDstB = (LAYOUT & kDstBits) != 0;
     const int L = x.L, half = L >> 1, nw = L >> 3, nc = nw / (32 * NW), lane = x.lane;
     const uint32_t uL = (uint32_t)L;
     uint32_t q0 = x.ring + 3 * uL, q1 = x.ring, q2 = x.ring + uL, q3 = x.ring + 2 * uL;
     uint32_t land = x.ring + 4 * uL;
-    if constexpr (kSrcS) {
+    if constexpr (kSrcB) {
+        // as for int8 rows below, with packed rows landing and bits_to_split
+        issue_bits_s(q0, x.Sb, wrap_row(x.r0 - 2, L), L, lane);
+        issue_bits_s(land, x.Sb, wrap_row(x.r0 - 1, L), L, lane);
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncwarp();
+        bits_to_split(q0, q1, L, lane, x.lut);
+        bits_to_split(land, q2, L, lane, x.lut);
+        __syncwarp();
+        issue_bits_s(q0, x.Sb, wrap_row(x.r0, L), L, lane);
+        cp_async_commit();
+        issue_bits_s(land, x.Sb, wrap_row(x.r0 + 1, L), L, lane);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncwarp();
+        bits_to_split(q0, q3, L, lane, x.lut);
+        __syncwarp();
+    } else if constexpr (kSrcS) {
         // rows -2 .. 0 straight into their slots; row 1 in flight in the landing slot
         issue_raw_s(q1, x.S, wrap_row(x.r0 - 2, L), L, lane);
         issue_raw_s(q2, x.S, wrap_row(x.r0 - 1, L), L, lane);
@@ -910,6 +995,12 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
                     store_split<NW>(Dsplit, hp, ho, c, upA, othB);
                 else
                     store_raw<NW>(Drow, c, upA, othB, selO0, selO1);
+                if constexpr (kDstB) {
+                    if (p)
+                        store_bits<NW>(x.Db, yB, L, c, othB, upA);
+                    else
+                        store_bits<NW>(x.Db, yB, L, c, upA, othB);
+                }
             }
         }
         if ((s & 7) == 7) drain_acc(acc, dm, db);
@@ -917,7 +1008,10 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
         if (s + 2 <= x.nrows + 1) {
             cp_async_wait_all();
             __syncwarp();
-            if constexpr (kSrcS) {
+            if constexpr (kSrcB) {
+                bits_to_split(land, q0, L, lane, x.lut);   // row s + 2 into the slot of row s - 2
+                __syncwarp();
+            } else if constexpr (kSrcS) {
                 // row s + 2 takes the slot of row s - 2, which lands the next row
                 const uint32_t t = q0;
                 q0 = land;
@@ -927,7 +1021,10 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
                 __syncwarp();
             }
             if (s + 3 <= x.nrows + 1) {
-                issue_raw_s(land, x.S, wrap_row(x.r0 + s + 3, L), L, lane);
+                if constexpr (kSrcB)
+                    issue_bits_s(land, x.Sb, wrap_row(x.r0 + s + 3, L), L, lane);
+                else
+                    issue_raw_s(land, x.S, wrap_row(x.r0 + s + 3, L), L, lane);
                 cp_async_commit();
             }
         }
@@ -946,11 +1043,17 @@ __device__ void item(const Walk &x, const PhiloxKeys &rk, int &dm, int &db) {
 // thread: the compiler interleaves the Philox rounds of a chunk's words.
 template <int WARPS, int LAYOUT>
 __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) ising_strip_kernel(IsingSweepArgs a) {
+    constexpr bool kBits = (LAYOUT & (kSrcBits | kDstBits)) != 0;
     extern __shared__ __align__(16) unsigned char ring_bytes[];
     __shared__ __align__(256) TabEntry tabs[WARPS][2][256 / sizeof(TabEntry)];
+    __shared__ uint2 lut[(LAYOUT & kSrcBits) ? 256 : 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t t = a.state->t;
     const int gw = blockIdx.x * WARPS + warp, nw = gridDim.x * WARPS;
+    if constexpr ((LAYOUT & kSrcBits) != 0) {
+        for (int k = threadIdx.x; k < 256; k += WARPS * 32) lut[k] = split::bits_lut_entry((uint32_t)k);
+        __syncthreads();
+    }
     for (int it = gw; it < a.n_items; it += nw) {
         const Item w = a.items[it];
         if (!SPIN_CK((unsigned)w.lat < (unsigned)a.n_lat, 101)) continue;
@@ -960,6 +1063,8 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) ising_strip_kernel(Isi
                          w.r0 + w.nrows <= ld.L && 5u * (unsigned)ld.L <= (unsigned)(kRing * kRowChunks * 16),
                      102))
             continue;
+        // packed rows start on 16-byte boundaries
+        if (kBits && !SPIN_CK((ld.offset & 127u) == 0, 105)) continue;
         if (lane < kTabStride) {
             const TabEntry e = a.tabs[w.lat * kTabStride + lane];
             tabs[warp][0][lane] = e;
@@ -978,6 +1083,9 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) ising_strip_kernel(Isi
         x.P1 = philox_prefix(ld.rng, t, 1u, a.rk);
         x.tab_cnt = (uint32_t)__cvta_generic_to_shared(tabs[warp][0]);
         x.tab_halo = (uint32_t)__cvta_generic_to_shared(tabs[warp][1]);
+        x.Sb = (LAYOUT & kSrcBits) ? reinterpret_cast<const uint4 *>(a.src_bits + (ld.offset >> 5)) : nullptr;
+        x.Db = (LAYOUT & kDstBits) ? a.dst_bits + (ld.offset >> 5) : nullptr;
+        x.lut = (uint32_t)__cvta_generic_to_shared(lut);
         int dm = 0, db = 0;
         if (ld.L == 512)
             split::item<2, LAYOUT>(x, a.rk, dm, db);
@@ -1397,6 +1505,9 @@ cudaError_t launch_strip_layout(const IsingSweepArgs &a, int grid, int layout, c
         case kSrcSplit | kDstSplit:
             ising_strip_kernel<WARPS, kSrcSplit | kDstSplit><<<grid, WARPS * 32, smem, s>>>(a);
             break;
+        case kSrcBits | kDstBits:
+            ising_strip_kernel<WARPS, kSrcBits | kDstBits><<<grid, WARPS * 32, smem, s>>>(a);
+            break;
         default:
             return cudaErrorInvalidValue;
     }
@@ -1412,6 +1523,9 @@ cudaError_t strip_smem_attributes() {
     if ((e = cudaFuncSetAttribute(ising_strip_kernel<WARPS, kSrcSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
         return e;
     if ((e = cudaFuncSetAttribute(ising_strip_kernel<WARPS, kDstSplit>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(ising_strip_kernel<WARPS, kSrcBits | kDstBits>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)))
         return e;
     return cudaFuncSetAttribute(ising_strip_kernel<WARPS, kSrcSplit | kDstSplit>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

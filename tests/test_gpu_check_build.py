@@ -38,6 +38,19 @@ for mode, threads in ((0, 512), (0, 256), (3, 256), (1, 256)):
         assert np.array_equal(sim.lattice(i).cpu().numpy(), init[i]), (mode, i)
         assert np.array_equal(st[:, i], ref), (mode, i)
     assert sm.check_status() == (True, 0), (mode, sm.check_status())
+# one sweep between bit-packed transfers (strip kernel reading and writing packed rows)
+pa, pb = (sm.Sim(sm.SPIN_ISING, lats, seed=SEED, max_record=4) for _ in range(2))
+nwp = pa.packed_words
+bits = torch.from_numpy(np.random.default_rng(5).integers(-2 ** 31, 2 ** 31, nwp, dtype=np.int64)
+                        .astype(np.int32)).pin_memory()
+oa, ob = torch.zeros(nwp, dtype=torch.int32).pin_memory(), torch.ones(nwp, dtype=torch.int32).pin_memory()
+pa.load_spins_packed(bits)
+pa.sweep(1, record=True)
+pa.store_spins_packed(oa)
+pb.sweep_packed(bits, ob, 1, record=True)
+torch.cuda.synchronize()
+assert torch.equal(oa, ob) and torch.equal(pa.spins, pb.spins)
+assert sm.check_status() == (True, 0), ("packed", sm.check_status())
 small = [dict(L=L, beta=0.4, J=1.0, h=0.0) for L in (16, 32, 64, 128)]
 for cs in (1, 2, 4):   # one CTA per lattice, or a cluster of 2 or 4
     r = sm.Sim(sm.SPIN_ISING, small, seed=SEED, max_record=4)

@@ -775,3 +775,28 @@ def test_sweep_packed_without_buffers_is_a_sweep():
     torch.cuda.synchronize()
     assert torch.equal(a.spins, b.spins)
     assert np.array_equal(a.observables_host(0, 3)[0], b.observables_host(0, 3)[0])
+
+
+def test_sweep_packed_full_size_uneven512():
+    """The one-sweep bit-layout path on the benchmark's batch (512 lattices,
+    the strip kernel reading and writing packed rows) against load + sweep +
+    store, twice in a row."""
+    lats = wl.uneven512()
+    a, b = make_ising(lats, max_record=4), make_ising(lats, max_record=4)
+    for x in (a, b):
+        x.set_launch(0, True, 0, 512)
+    nw = a.packed_words
+    rng = np.random.default_rng(77)
+    bits = torch.from_numpy(rng.integers(-2 ** 31, 2 ** 31, nw, dtype=np.int64).astype(np.int32)).pin_memory()
+    for k in range(2):
+        out_a = torch.zeros(nw, dtype=torch.int32).pin_memory()
+        out_b = torch.ones(nw, dtype=torch.int32).pin_memory()
+        a.load_spins_packed(bits)
+        a.sweep(1, record=True)
+        a.store_spins_packed(out_a)
+        b.sweep_packed(bits, out_b, 1, record=True)
+        torch.cuda.synchronize()
+        assert torch.equal(out_a, out_b), k
+        assert torch.equal(a.spins, b.spins), k
+        assert np.array_equal(a.observables_host(k, 1)[0], b.observables_host(k, 1)[0]), k
+        bits = out_b.clone().pin_memory()
