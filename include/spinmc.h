@@ -267,7 +267,12 @@ int spin_store_spins_packed(spin_ctx *ctx, uint32_t *host, void *stream);
  * With an odd n_sweeps in launch mode 0 or 3 the loaded state is unpacked
  * into the context's ping-pong buffer, so the last sweep lands in the
  * caller's spin buffer and the copy that ends an odd spin_sweep call is not
- * needed.  host_in / host_out: pinned host memory for asynchronous copies,
+ * needed.  One sweep with both buffers in launch mode 0 (square lattices,
+ * offsets of the L = 512, 1024, 2048 lattices multiples of 128): the row-strip
+ * kernel reads those lattices' rows from the uploaded bits and writes their
+ * bits beside the int8 rows, and only the other lattices are unpacked and
+ * packed by separate kernels.  A second packed buffer of the context holds
+ * the output bits.  host_in / host_out: pinned host memory for asynchronous copies,
  * spin_packed_words(ctx) words each; asynchronous on the stream.  Errors as
  * the three calls (SPIN_EINVAL for non-Ising contexts or offsets % 32 != 0).
  * Not in the paper.                                                        */
