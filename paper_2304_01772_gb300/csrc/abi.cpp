@@ -119,7 +119,11 @@ struct spin_ctx {
     size_t scratch_bytes = 0;
     int *d_flag = nullptr;
     uint32_t *d_packed = nullptr;   // bit-packed transfer buffer (allocated at first use)
-    uint32_t *d_packed2 = nullptr;  // second one: spin_sweep_packed's output bits      // [0] moment overflow, [1] a device wait gave up
+    uint32_t *d_packed2 = nullptr;  // second one: spin_sweep_packed's output bits
+    // block ranges of the pack / unpack launches per lattice: every lattice, and
+    // only the lattices below the strip sides (allocated with d_packed)
+    int32_t *d_blk_all = nullptr, *d_blk_small = nullptr;
+    int nblk_all = 0, nblk_small = 0;      // [0] moment overflow, [1] a device wait gave up
     // host mirrors
     uint32_t t = 0;
     int64_t n_rec = 0;
@@ -927,7 +931,8 @@ void spin_destroy(spin_ctx *ctx) {
                     ctx->d_dvol[0], ctx->d_dvol[1],
                     ctx->d_state, ctx->st.cur, ctx->st.delta, ctx->st.ring, ctx->d_type,
                     ctx->d_J, ctx->d_vol[0], ctx->d_vol[1], ctx->d_thr, ctx->d_latp,
-                    ctx->d_cpmJ, ctx->d_scratch, ctx->d_flag, ctx->d_cpm_acc, ctx->d_cpm_bar, ctx->d_packed, ctx->d_packed2};
+                    ctx->d_cpmJ, ctx->d_scratch, ctx->d_flag, ctx->d_cpm_acc, ctx->d_cpm_bar, ctx->d_packed, ctx->d_packed2,
+                    ctx->d_blk_all, ctx->d_blk_small};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -1439,6 +1444,24 @@ static int packed_ready(spin_ctx *ctx) {
         ctx->d_packed = nullptr;
         return fail(ctx, SPIN_ENOMEM, "packed transfer buffer");
     }
+    if (!ctx->d_blk_all) {
+        // about 16 words per thread of a 256-thread block, at least one block per lattice
+        std::vector<int32_t> all(ctx->n_lat + 1, 0), small(ctx->n_lat + 1, 0);
+        for (int i = 0; i < ctx->n_lat; ++i) {
+            const int L = ctx->lat[i].L;
+            const int64_t words = ((int64_t)L * L + 31) / 32;
+            const int b = (int)std::max<int64_t>(1, (words + 4095) / 4096);
+            all[i + 1] = all[i] + b;
+            small[i + 1] = small[i] + ((L == 512 || L == 1024 || L == 2048) ? 0 : b);
+        }
+        if (cudaMalloc(&ctx->d_blk_all, sizeof(int32_t) * all.size()) != cudaSuccess ||
+            cudaMalloc(&ctx->d_blk_small, sizeof(int32_t) * small.size()) != cudaSuccess)
+            return fail(ctx, SPIN_ENOMEM, "packed transfer block ranges");
+        CK(cudaMemcpy(ctx->d_blk_all, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(ctx->d_blk_small, small.data(), sizeof(int32_t) * small.size(), cudaMemcpyHostToDevice));
+        ctx->nblk_all = all.back();
+        ctx->nblk_small = small.back();
+    }
     return SPIN_OK;
 }
 
@@ -1466,8 +1489,8 @@ static int load_packed_into(spin_ctx *ctx, const uint32_t *host, void *target, c
     // square lattices: the statistics of the loaded state are counted from the bits
     // while unpacking; other geometries are recounted from the unpacked state
     const bool square = all_square(ctx);
-    CK(launch_unpack_spins(ctx->d_packed, static_cast<int8_t *>(target), ctx->d_lats, ctx->n_lat, ctx->maxL,
-                           square ? ctx->st.cur : nullptr, s));
+    CK(launch_unpack_spins(ctx->d_packed, static_cast<int8_t *>(target), ctx->d_lats, ctx->n_lat, ctx->d_blk_all,
+                           ctx->nblk_all, square ? ctx->st.cur : nullptr, s));
     if (!square)
         CK(launch_stats_from_state(target, ctx->model, ctx->d_lats, ctx->n_lat, ctx->maxL, ctx->width,
                                    ctx->d_type, ctx->n_types, ctx->d_vol[0], ctx->n_cells, ctx->target, ctx->st.cur, s));
@@ -1490,7 +1513,7 @@ int spin_store_spins_packed(spin_ctx *ctx, uint32_t *host, void *stream) {
     cudaStream_t s = S(stream);
     const size_t nw = (ctx->span_elems + 31) / 32;
     CK(launch_pack_spins(static_cast<const int8_t *>(ctx->spins), ctx->d_packed, nw, ctx->d_lats, ctx->n_lat,
-                         ctx->maxL, s));
+                         ctx->d_blk_all, ctx->nblk_all, s));
     CK(cudaMemcpyAsync(host, ctx->d_packed, sizeof(uint32_t) * nw, cudaMemcpyDeviceToHost, s));
     return SPIN_OK;
 }
@@ -1518,8 +1541,8 @@ int spin_sweep_packed(spin_ctx *ctx, const uint32_t *host_in, uint32_t *host_out
             return fail(ctx, SPIN_ENOMEM, "packed transfer buffer");
         }
         CK(cudaMemcpyAsync(ctx->d_packed, host_in, sizeof(uint32_t) * nw, cudaMemcpyHostToDevice, s));
-        CK(launch_unpack_spins(ctx->d_packed, static_cast<int8_t *>(ctx->spins2), ctx->d_lats, ctx->n_lat, ctx->maxL,
-                               ctx->st.cur, s, true));
+        CK(launch_unpack_spins(ctx->d_packed, static_cast<int8_t *>(ctx->spins2), ctx->d_lats, ctx->n_lat,
+                               ctx->d_blk_all, ctx->nblk_all, ctx->st.cur, s, true));
         CK(cudaMemsetAsync(ctx->d_packed2, 0, sizeof(uint32_t) * nw, s));
         int launches = 0;
         rc = launch_sweep(ctx, ctx->spins2, ctx->spins, record ? 1 : 0, s, launches, kSrcBits | kDstBits,
@@ -1529,7 +1552,7 @@ int spin_sweep_packed(spin_ctx *ctx, const uint32_t *host_in, uint32_t *host_out
         ctx->t += 1;
         if (record) ctx->n_rec += 1;
         CK(launch_pack_spins(static_cast<const int8_t *>(ctx->spins), ctx->d_packed2, nw, ctx->d_lats, ctx->n_lat,
-                             ctx->maxL, s, true));
+                             ctx->d_blk_small, ctx->nblk_small, s, true));
         CK(cudaMemcpyAsync(host_out, ctx->d_packed2, sizeof(uint32_t) * nw, cudaMemcpyDeviceToHost, s));
         return SPIN_OK;
     }

@@ -472,13 +472,16 @@ cudaError_t launch_dmc_step(const DmcStepArgs &a, cudaStream_t s);
 // the loaded state's statistics into cur [n_lat][2] = (M, B) of square lattices
 // when cur is not null / pack them into
 // words (bits outside the lattices 0).  Lattice offsets are multiples of 32.
-// skip_strip: lattices of side 512, 1024 or 2048 are left to the strip
-// kernel's bit layouts (unpack: their statistics are still counted; pack:
-// their words are not written, nor cleared: the caller clears the buffer).
-cudaError_t launch_unpack_spins(const uint32_t *words, int8_t *spins, const LatDev *lats, int n_lat, int maxL,
-                                int64_t *cur, cudaStream_t s, bool skip_strip = false);
+// blk: per-lattice block ranges of the launch (n_lat + 1 prefix entries,
+// n_blocks = blk[n_lat]).  skip_strip: lattices of side 512, 1024 or 2048 are
+// left to the strip kernel's bit layouts (unpack: their statistics are still
+// counted; pack: their words are not written, nor cleared: the caller clears
+// the buffer, and blk may give them no blocks).
+cudaError_t launch_unpack_spins(const uint32_t *words, int8_t *spins, const LatDev *lats, int n_lat,
+                                const int32_t *blk, int n_blocks, int64_t *cur, cudaStream_t s,
+                                bool skip_strip = false);
 cudaError_t launch_pack_spins(const int8_t *spins, uint32_t *words, size_t n_words, const LatDev *lats, int n_lat,
-                              int maxL, cudaStream_t s, bool skip_strip = false);
+                              const int32_t *blk, int n_blocks, cudaStream_t s, bool skip_strip = false);
 
 // The square-lattice resident form (launch_ising_resident) with each lattice
 // split over a thread-block cluster of cs CTAs (2 or 4), CTA r holding rows

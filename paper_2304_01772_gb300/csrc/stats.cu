@@ -509,14 +509,31 @@ __device__ __forceinline__ uint32_t nibble_bytes(uint32_t n) {
 // kernels leave those lattices' spins to the strip kernel's bit layouts).
 __device__ __forceinline__ bool strip_side(int L) { return L == 512 || L == 1024 || L == 2048; }
 
-// One thread per 32-bit word of the packed buffer overlapping lattice
-// blockIdx.y (offsets are multiples of 32, so no word holds two lattices).
-__global__ void pack_spins_kernel(const int8_t *spins, uint32_t *words, const LatDev *lats, int skip_strip) {
-    const LatDev ld = lats[blockIdx.y];
+// The blocks of a pack or unpack launch are cut per lattice: lattice l owns
+// blocks [blk[l], blk[l + 1]) (a host-built prefix of per-lattice counts that
+// follow its word count, so small lattices take one block and no block idles).
+// Block b finds its lattice by bisection.
+__device__ __forceinline__ int block_lattice(const int32_t *blk, int n_lat, int b) {
+    int lo = 0, hi = n_lat - 1;   // the last lattice whose first block is <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (blk[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One thread per 32-bit word of the packed buffer overlapping its lattice
+// (offsets are multiples of 32, so no word holds two lattices).
+__global__ void pack_spins_kernel(const int8_t *spins, uint32_t *words, const LatDev *lats, const int32_t *blk,
+                                  int n_lat, int skip_strip) {
+    const int lat = block_lattice(blk, n_lat, (int)blockIdx.x);
+    const int lb = (int)blockIdx.x - blk[lat], nb = blk[lat + 1] - blk[lat];
+    const LatDev ld = lats[lat];
     if (skip_strip && strip_side(ld.L)) return;
     const size_t o = ld.offset, end = o + (size_t)ld.L * ld.L;
-    for (size_t w = (o >> 5) + blockIdx.x * (size_t)blockDim.x + threadIdx.x; (w << 5) < end;
-         w += (size_t)gridDim.x * blockDim.x) {
+    for (size_t w = (o >> 5) + lb * (size_t)blockDim.x + threadIdx.x; (w << 5) < end;
+         w += (size_t)nb * blockDim.x) {
         const size_t e0 = w << 5;
         uint32_t bits = 0;
         if (e0 + 32 <= end && ((reinterpret_cast<uintptr_t>(spins + e0) & 15) == 0)) {
@@ -542,10 +559,11 @@ __device__ __forceinline__ int packed_bit(const uint32_t *words, size_t e) { ret
 // by one with bit 0 of the next word of the row (or of the row's first word),
 // its down neighbours the word of the next row, and unequal pairs are popcounts
 // of xors.  Other sides count bond by bond.
-__global__ void unpack_spins_kernel(const uint32_t *words, int8_t *spins, const LatDev *lats, int64_t *cur,
-                                    int skip_strip) {
+__global__ void unpack_spins_kernel(const uint32_t *words, int8_t *spins, const LatDev *lats, const int32_t *blk,
+                                    int n_lat, int64_t *cur, int skip_strip) {
     __shared__ long long red[2][8];
-    const int lat = blockIdx.y;
+    const int lat = block_lattice(blk, n_lat, (int)blockIdx.x);
+    const int lb = (int)blockIdx.x - blk[lat], nb = blk[lat + 1] - blk[lat];
     const LatDev ld = lats[lat];
     const int L = ld.L;
     const bool write = !(skip_strip && strip_side(L));   // else statistics only
@@ -556,8 +574,8 @@ __global__ void unpack_spins_kernel(const uint32_t *words, int8_t *spins, const 
     // (r, q) = (row, word in the row) of wl, advanced by the grid stride as rows
     // and words instead of dividing
     const uint32_t n_wl = (uint32_t)(((size_t)L * L + 31) >> 5);
-    const uint32_t stride = gridDim.x * blockDim.x;
-    uint32_t wl = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t stride = (uint32_t)nb * blockDim.x;
+    uint32_t wl = (uint32_t)lb * blockDim.x + threadIdx.x;
     int r = 0, q = 0, dr = 0, dq = 0;
     if (rows_whole) {
         r = (int)(wl / (uint32_t)wpr);
@@ -629,27 +647,25 @@ __global__ void unpack_spins_kernel(const uint32_t *words, int8_t *spins, const 
 
 }  // namespace
 
-cudaError_t launch_unpack_spins(const uint32_t *words, int8_t *spins, const LatDev *lats, int n_lat, int maxL,
-                                int64_t *cur, cudaStream_t s, bool skip_strip) {
+cudaError_t launch_unpack_spins(const uint32_t *words, int8_t *spins, const LatDev *lats, int n_lat,
+                                const int32_t *blk, int n_blocks, int64_t *cur, cudaStream_t s, bool skip_strip) {
     if (cur) {
         cudaError_t e = cudaMemsetAsync(cur, 0, sizeof(int64_t) * 2 * (size_t)n_lat, s);
         if (e) return e;
     }
-    const int wpl = (int)(((size_t)maxL * maxL + 31) / 32) + 1;
-    dim3 grid((wpl + 255) / 256 < 64 ? (wpl + 255) / 256 : 64, n_lat);
-    unpack_spins_kernel<<<grid, 256, 0, s>>>(words, spins, lats, cur, skip_strip ? 1 : 0);
+    if (n_blocks <= 0) return cudaSuccess;
+    unpack_spins_kernel<<<n_blocks, 256, 0, s>>>(words, spins, lats, blk, n_lat, cur, skip_strip ? 1 : 0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pack_spins(const int8_t *spins, uint32_t *words, size_t n_words, const LatDev *lats, int n_lat,
-                              int maxL, cudaStream_t s, bool skip_strip) {
+                              const int32_t *blk, int n_blocks, cudaStream_t s, bool skip_strip) {
     if (!skip_strip) {   // with skip_strip the caller has cleared the words before the strip kernel wrote its own
         cudaError_t e = cudaMemsetAsync(words, 0, n_words * sizeof(uint32_t), s);
         if (e) return e;
     }
-    const int wpl = (int)(((size_t)maxL * maxL + 31) / 32) + 1;
-    dim3 grid((wpl + 255) / 256 < 64 ? (wpl + 255) / 256 : 64, n_lat);
-    pack_spins_kernel<<<grid, 256, 0, s>>>(spins, words, lats, skip_strip ? 1 : 0);
+    if (n_blocks <= 0) return cudaSuccess;
+    pack_spins_kernel<<<n_blocks, 256, 0, s>>>(spins, words, lats, blk, n_lat, skip_strip ? 1 : 0);
     return cudaGetLastError();
 }
 
