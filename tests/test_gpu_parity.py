@@ -800,3 +800,40 @@ def test_sweep_packed_full_size_uneven512():
         assert torch.equal(a.spins, b.spins), k
         assert np.array_equal(a.observables_host(k, 1)[0], b.observables_host(k, 1)[0]), k
         bits = out_b.clone().pin_memory()
+
+
+def test_sweep_packed_offsets_off_the_bit_layout_and_edge_calls():
+    """A strip lattice whose packed rows would not start on 16-byte boundaries
+    (offset % 128 != 0) takes the unpack / pack path; a call with no sweep is a
+    load and a store; one with only an output is a sweep and a store."""
+    lats = [dict(L=16, beta=0.3, J=1.0, h=0.0), dict(L=6, beta=0.5, J=1.0, h=0.1),
+            dict(L=512, beta=0.44, J=1.0, h=0.0), dict(L=1024, beta=0.5, J=1.0, h=-0.02)]
+    offsets, _ = sm.pack_offsets([d["L"] for d in lats], 1, 32)
+    assert offsets[2] % 128 != 0
+    a, b = make_ising(lats, max_record=8, offsets=offsets), make_ising(lats, max_record=8, offsets=offsets)
+    nw = a.packed_words
+    rng = np.random.default_rng(5)
+    bits = torch.from_numpy(rng.integers(-2 ** 31, 2 ** 31, nw, dtype=np.int64).astype(np.int32)).pin_memory()
+    out_a, out_b = (torch.zeros(nw, dtype=torch.int32).pin_memory() for _ in range(2))
+    a.load_spins_packed(bits)
+    a.sweep(1, record=True)
+    a.store_spins_packed(out_a)
+    b.sweep_packed(bits, out_b, 1, record=True)
+    torch.cuda.synchronize()
+    assert torch.equal(out_a, out_b) and torch.equal(a.spins, b.spins)
+    assert np.array_equal(a.observables_host(0, 1)[0], b.observables_host(0, 1)[0])
+    # no sweep: load then store
+    out_c = torch.ones(nw, dtype=torch.int32).pin_memory()
+    b.sweep_packed(bits, out_c, 0)
+    a.load_spins_packed(bits)
+    a.store_spins_packed(out_a)
+    torch.cuda.synchronize()
+    assert torch.equal(out_a, out_c) and torch.equal(a.spins, b.spins)
+    assert torch.equal(a.current_stats(), b.current_stats())
+    # only an output: sweeps then a store
+    a.sweep(2, record=True)
+    a.store_spins_packed(out_a)
+    b.sweep_packed(None, out_c, 2, record=True)
+    torch.cuda.synchronize()
+    assert torch.equal(out_a, out_c) and torch.equal(a.spins, b.spins)
+    assert a.t == b.t == 3
