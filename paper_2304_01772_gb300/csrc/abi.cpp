@@ -1536,14 +1536,18 @@ int spin_sweep_packed(spin_ctx *ctx, const uint32_t *host_in, uint32_t *host_out
         // the sweep reads) and packed; the loaded state's statistics are counted
         // from all the bits.
         const size_t nw = (ctx->span_elems + 31) / 32;
-        if (!ctx->d_packed2 && cudaMalloc(&ctx->d_packed2, sizeof(uint32_t) * nw) != cudaSuccess) {
-            ctx->d_packed2 = nullptr;
-            return fail(ctx, SPIN_ENOMEM, "packed transfer buffer");
+        if (!ctx->d_packed2) {
+            // cleared once: the words between and after the lattices are never written
+            // again (the strip kernel and the pack kernel write whole lattice words only)
+            if (cudaMalloc(&ctx->d_packed2, sizeof(uint32_t) * nw) != cudaSuccess) {
+                ctx->d_packed2 = nullptr;
+                return fail(ctx, SPIN_ENOMEM, "packed transfer buffer");
+            }
+            CK(cudaMemsetAsync(ctx->d_packed2, 0, sizeof(uint32_t) * nw, s));
         }
         CK(cudaMemcpyAsync(ctx->d_packed, host_in, sizeof(uint32_t) * nw, cudaMemcpyHostToDevice, s));
         CK(launch_unpack_spins(ctx->d_packed, static_cast<int8_t *>(ctx->spins2), ctx->d_lats, ctx->n_lat,
                                ctx->d_blk_all, ctx->nblk_all, ctx->st.cur, s, true));
-        CK(cudaMemsetAsync(ctx->d_packed2, 0, sizeof(uint32_t) * nw, s));
         int launches = 0;
         rc = launch_sweep(ctx, ctx->spins2, ctx->spins, record ? 1 : 0, s, launches, kSrcBits | kDstBits,
                           ctx->d_packed, ctx->d_packed2);

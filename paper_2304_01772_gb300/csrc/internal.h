@@ -475,8 +475,8 @@ cudaError_t launch_dmc_step(const DmcStepArgs &a, cudaStream_t s);
 // blk: per-lattice block ranges of the launch (n_lat + 1 prefix entries,
 // n_blocks = blk[n_lat]).  skip_strip: lattices of side 512, 1024 or 2048 are
 // left to the strip kernel's bit layouts (unpack: their statistics are still
-// counted; pack: their words are not written, nor cleared: the caller clears
-// the buffer, and blk may give them no blocks).
+// counted; pack: their words are not written, nor cleared: the caller keeps
+// the buffer's other words, and blk may give them no blocks).
 cudaError_t launch_unpack_spins(const uint32_t *words, int8_t *spins, const LatDev *lats, int n_lat,
                                 const int32_t *blk, int n_blocks, int64_t *cur, cudaStream_t s,
                                 bool skip_strip = false);

@@ -660,7 +660,7 @@ cudaError_t launch_unpack_spins(const uint32_t *words, int8_t *spins, const LatD
 
 cudaError_t launch_pack_spins(const int8_t *spins, uint32_t *words, size_t n_words, const LatDev *lats, int n_lat,
                               const int32_t *blk, int n_blocks, cudaStream_t s, bool skip_strip) {
-    if (!skip_strip) {   // with skip_strip the caller has cleared the words before the strip kernel wrote its own
+    if (!skip_strip) {   // with skip_strip the caller keeps the other words (cleared, or written by the strip kernel)
         cudaError_t e = cudaMemsetAsync(words, 0, n_words * sizeof(uint32_t), s);
         if (e) return e;
     }
