@@ -117,13 +117,13 @@ struct spin_ctx {
     double *d_cpmJ = nullptr;   // [pairs]
     void *d_scratch = nullptr;  // moments etc.
     size_t scratch_bytes = 0;
-    int *d_flag = nullptr;
+    int *d_flag = nullptr;      // [0] moment overflow, [1] a device wait gave up
     uint32_t *d_packed = nullptr;   // bit-packed transfer buffer (allocated at first use)
     uint32_t *d_packed2 = nullptr;  // second one: spin_sweep_packed's output bits
     // block ranges of the pack / unpack launches per lattice: every lattice, and
     // only the lattices below the strip sides (allocated with d_packed)
     int32_t *d_blk_all = nullptr, *d_blk_small = nullptr;
-    int nblk_all = 0, nblk_small = 0;      // [0] moment overflow, [1] a device wait gave up
+    int nblk_all = 0, nblk_small = 0;
     // host mirrors
     uint32_t t = 0;
     int64_t n_rec = 0;
